@@ -1,0 +1,98 @@
+"""Pins of the oracle's PCG, LM step and adjoint."""
+import numpy as np
+import scipy.linalg as sla
+
+from conftest import scene
+from oracle import adjoint, camera, lm, pcg, schur
+
+
+def test_pcg_multigrid_matches_dense_cholesky():
+    s = scene("ring", seed=0)
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+    dc, dp, it, rel = lm.solve_step(sch, s.cams, "mg", rtol=1e-13, coarse_max_nodes=4)
+    ref = sla.cho_solve(sla.cho_factor(sch.S.toarray()), sch.b)
+    assert np.linalg.norm(dc - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_iterations_fall_as_the_preconditioner_strengthens():
+    # Section 5: multigrid needs fewer CG iterations than point block Jacobi
+    s = scene("street_chain", n_cams=300, n_pts=30000)
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+    its = {}
+    for pc in ("none", "jacobi", "mg"):
+        _, _, its[pc], rel = lm.solve_step(sch, s.cams, pc, rtol=1e-6, max_iters=3000, coarse_max_nodes=16)
+        if pc != "none":               # unpreconditioned CG stalls on the badly scaled system
+            assert rel <= 1e-6
+    assert its["none"] > its["jacobi"] > its["mg"]
+
+
+def test_pcg_zero_rhs_and_identity():
+    x, it, rel, _ = pcg.pcg(lambda v: 2 * v, np.zeros(5))
+    assert it == 0 and np.all(x == 0)
+    b = np.arange(1.0, 6.0)
+    x, it, rel, _ = pcg.pcg(lambda v: 2 * v, b)
+    assert it == 1 and np.allclose(x, b / 2)
+
+
+def test_lm_step_decreases_cost_and_updates_lambda():
+    s = scene("ring", seed=0)
+    c1, p1, lam1, nu1, acc, cost0, cost1, info = lm.lm_step(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, 1e-4,
+                                                             rtol=1e-10, coarse_max_nodes=4)
+    assert acc and cost1 < cost0
+    rho = info["rho"]
+    assert np.isclose(lam1, 1e-4 * max(1 / 3, 1 - (2 * rho - 1) ** 3))
+    assert np.isclose(camera.cost(c1, p1, s.cam_idx, s.pt_idx, s.obs), cost1)
+
+
+def test_lm_step_rejects_and_raises_lambda():
+    s = scene("ring", seed=0)
+    # a huge damping step that overshoots is impossible; instead force rejection by a tiny
+    # damping on a badly perturbed start
+    cams = s.cams.copy()
+    cams[:, 3:6] += 3.0
+    out = lm.lm_step(cams, s.pts, s.cam_idx, s.pt_idx, s.obs, 1e-12, rtol=1e-10, coarse_max_nodes=4)
+    c1, p1, lam1, nu1, acc = out[:5]
+    if not acc:
+        assert lam1 == 1e-12 * 2.0 and nu1 == 4.0 and np.all(c1 == cams)
+
+
+def _fd_loss(s, vbar, cams, pts, obs, lam):
+    sch = schur.linearize(cams, pts, s.cam_idx, s.pt_idx, obs, lam)
+    dc, dp = adjoint.solve_delta(sch)
+    return vbar @ np.concatenate([dc, dp])
+
+
+def test_adjoint_matches_central_differences():
+    s = scene("ring", seed=5, n_cams=6, n_pts=40, kmin=2, kmax=4)
+    lam = 1e-2
+    rng = np.random.default_rng(0)
+    vbar = rng.normal(size=9 * s.n_cams + 3 * s.n_pts)
+    go, gc, gp, _ = adjoint.adjoint(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, lam, vbar)
+    for (arr, grad, which) in ((s.obs, go, "obs"), (s.cams, gc, "cams"), (s.pts, gp, "pts")):
+        for _ in range(6):
+            i = rng.integers(arr.shape[0])
+            j = rng.integers(arr.shape[1])
+            # kappa(S) ~ 1e7 here: h = 1e-4 balances truncation against amplified rounding
+            h = 1e-4 * max(1.0, abs(arr[i, j]))
+            ap, am = arr.copy(), arr.copy()
+            ap[i, j] += h
+            am[i, j] -= h
+            args = {"cams": s.cams, "pts": s.pts, "obs": s.obs}
+            args[which] = ap
+            lp = _fd_loss(s, vbar, args["cams"], args["pts"], args["obs"], lam)
+            args[which] = am
+            lm_ = _fd_loss(s, vbar, args["cams"], args["pts"], args["obs"], lam)
+            fd = (lp - lm_) / (2 * h)
+            scale = np.abs(grad).max()
+            assert abs(fd - grad[i, j]) <= 1e-5 * max(abs(fd), 1e-3 * scale), (which, i, j, fd, grad[i, j])
+
+
+def test_adjoint_is_linear_in_the_cotangent():
+    s = scene("ring", seed=5, n_cams=6, n_pts=40, kmin=2, kmax=4)
+    rng = np.random.default_rng(1)
+    v1, v2 = rng.normal(size=(2, 9 * s.n_cams + 3 * s.n_pts))
+    a = adjoint.adjoint(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, 1e-3, v1)
+    b = adjoint.adjoint(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, 1e-3, v2)
+    c = adjoint.adjoint(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, 1e-3, 2 * v1 - v2)
+    for k in range(3):
+        assert np.allclose(c[k], 2 * a[k] - b[k], rtol=1e-9, atol=1e-9 * np.abs(a[k]).max())
