@@ -1,0 +1,214 @@
+/*
+ * ba.h - C ABI of the GB300 (sm_103a) linear-solve library for Levenberg-Marquardt
+ * bundle adjustment, after "Multigrid for Bundle Adjustment" (Konolige & Brown).
+ *
+ * The library solves, once per LM step, the damped normal equations of Section 2.1,
+ *     (J^T J + D) delta = -J^T f,
+ * by eliminating the points (Schur complement S = A - F^T E C^-1 E^T F, Section 2.1)
+ * and running preconditioned conjugate gradients on S, applied implicitly from the
+ * per-observation Jacobian blocks (Section 3.6), with the unsmoothed-aggregation
+ * multigrid V-cycle of Section 3 (Algorithm 1, Algorithm 2) as the preconditioner.
+ *
+ * Conventions (all entry points):
+ *  - Array arguments are DEVICE pointers unless the comment says "host".  Callers own
+ *    them; the library never keeps a pointer past the call, except as stated for
+ *    ba_create.  float64, row-major, densely packed.
+ *  - cams: n_cams x 9 rows [r0 r1 r2 (angle-axis), t0 t1 t2, f, k1, k2];
+ *    pts: n_pts x 3; obs: n_obs x 2 pixel coordinates, in the caller's observation
+ *    order (the order of cam_idx / pt_idx given to ba_create).
+ *  - Camera vectors (rhs, delta_c, dL_dcams): n_cams x 9; point vectors n_pts x 3.
+ *  - All GPU work is enqueued on the stream given to ba_create.  Entry points that
+ *    return host scalars synchronise that stream before returning.
+ *  - Errors are returned as a ba_status and never trap the GPU; ba_last_error gives
+ *    a message.  A failed call leaves the problem usable (the next ba_linearize
+ *    starts afresh) unless the status is BA_ERR_CUDA.
+ *  - The problem object is not thread-safe; use one per host thread.
+ */
+#ifndef BA_H_
+#define BA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ba_problem ba_problem; /* opaque, owned by the library */
+
+typedef enum {
+  BA_OK = 0,
+  BA_ERR_INVALID_ARG = 1,   /* bad size, index out of range, duplicate (camera, point) pair */
+  BA_ERR_CUDA = 2,          /* a CUDA call failed; the problem should be destroyed */
+  BA_ERR_OOM = 3,           /* device allocation failed */
+  BA_ERR_NOT_SPD = 4,       /* a 3x3 point block, a Jacobi block or the coarse matrix is not SPD */
+  BA_ERR_BREAKDOWN = 5,     /* PCG breakdown: p^T S p <= 0 or a non-finite scalar */
+  BA_ERR_NOT_CONVERGED = 6, /* max_iters reached; delta_c still holds the last iterate */
+  BA_ERR_LIMIT = 7,         /* a documented capacity limit was exceeded (see ba_last_error) */
+  BA_ERR_STATE = 8          /* entry points called out of order (e.g. solve before setup) */
+} ba_status;
+
+typedef enum { BA_FP64 = 0, BA_MIXED = 1 } ba_precision;
+typedef enum { BA_PRECOND_NONE = 0, BA_PRECOND_JACOBI = 1, BA_PRECOND_MG = 2 } ba_precond;
+typedef enum { BA_DAMP_MARQUARDT = 0, BA_DAMP_IDENTITY = 1 } ba_damping;
+
+typedef struct {
+  double lambda;        /* LM damping used by ba_lm_step's first call (Section 5: 1/1e4) */
+  double rtol;          /* PCG stop: |r_k| <= rtol |b|, r the recursive residual */
+  int max_iters;        /* PCG iteration cap (1000) */
+  int precision;        /* ba_precision: BA_FP64 all-double; BA_MIXED FP32 V-cycle */
+  int preconditioner;   /* ba_precond (BA_PRECOND_MG) */
+  int damping;          /* ba_damping: D = lambda*max(diag(J^T J),1e-6) or lambda*I */
+  int recompute_jacobian; /* ba_adjoint rebuilds F, E from cams/pts (always on); reserved */
+  int max_agg;          /* Algorithm 2 aggregate size cap (20, Section 3.2) */
+  int pre_smooth;       /* Chebyshev steps before the coarse correction (2, Section 3.4) */
+  int post_smooth;      /* Chebyshev steps after (2) */
+  int lanczos_steps;    /* operator applications for lambda_max (5, Section 3.4) */
+  int coarse_max_nodes; /* stop coarsening at <= this many nodes (64) */
+  int max_levels;       /* hierarchy depth cap (10) */
+  double cheb_lo;       /* Chebyshev interval [cheb_lo, cheb_hi] * lambda_max (0.3, 1.1) */
+  double cheb_hi;
+} ba_options;
+
+/* Fills *opt with the defaults listed above. */
+void ba_default_options(ba_options* opt);
+
+/* Creates a problem for a fixed observation graph (Section 2.1: cameras x_c, points x_p).
+ * cam_idx, pt_idx: device int32 [n_obs], the camera and point of each observation; they
+ * are copied (and sorted internally by point, then camera) during the call and not kept.
+ * Every (camera, point) pair may appear at most once.  opt may be NULL (defaults).
+ * stream: a cudaStream_t (NULL = legacy default stream).  *out receives the problem.
+ * Limits: n_obs < 2^31; a camera may be covisible with at most 8192 other cameras. */
+ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx,
+                    const int32_t* pt_idx, const ba_options* opt, void* stream,
+                    ba_problem** out);
+
+/* Frees every device and host resource of the problem (NULL is ignored). */
+void ba_destroy(ba_problem* prob);
+
+/* Message describing the last non-OK status returned for this problem ("" if none). */
+const char* ba_last_error(const ba_problem* prob);
+
+/* Linearises at (cams, pts) (Section 2.1, Eq. 1-2): residuals f_o = pi(cam, X) - obs_o,
+ * F_o = df_o/dcam (2x9), E_o = df_o/dX (2x3) for the 9-parameter angle-axis camera.
+ * cost_out: host double, receives 1/2 sum |f_o|^2 (may be NULL). */
+ba_status ba_linearize(ba_problem* prob, const double* cams, const double* pts,
+                       const double* obs, double* cost_out);
+
+/* Schur reduction for damping lambda (Section 2.1, Eq. 3-4): D, C_p^-1 (FP64), the
+ * gradient g = -J^T f, the reduced right-hand side b = g_c - F^T E C^-1 g_p and the
+ * point-block-Jacobi blocks S_cc^-1.  Requires ba_linearize. */
+ba_status ba_schur_setup(ba_problem* prob, double lambda);
+
+/* Multigrid setup (Section 3): covisibility, Algorithm 2 aggregation, near-nullspace
+ * and per-aggregate QR prolongators (3.1, 3.3), Galerkin coarse operators P^T A P
+ * (Section 2.3), Jacobi blocks, Lanczos lambda_max (3.4) and the coarsest direct
+ * solver.  Requires ba_schur_setup.  No-op unless preconditioner == BA_PRECOND_MG. */
+ba_status ba_mg_setup(ba_problem* prob);
+
+/* PCG on S delta_c = rhs (Section 3.6) from delta_c = 0 with the configured
+ * preconditioner.  rhs: device n_cams x 9, or NULL for the reduced RHS b.
+ * delta_c: device n_cams x 9 output.  iters, rel_res: host outputs (may be NULL):
+ * the number of S products and |r|/|rhs| of the recursive residual. */
+ba_status ba_pcg_solve(ba_problem* prob, const double* rhs, double* delta_c, int* iters,
+                       double* rel_res);
+
+/* Point step delta_p = C^-1 (g_p - E^T F delta_c) (Section 2.1), n_pts x 3 output. */
+ba_status ba_back_substitute(ba_problem* prob, const double* delta_c, double* delta_p);
+
+/* One LM step (Section 2.1; step control of Section 5 read as the gain-ratio rule):
+ * linearise at (cams, pts), solve with damping *lambda_inout, evaluate the cost at
+ * x + delta, accept if rho > 1e-3 (cams/pts updated in place) and update lambda.
+ * accepted, cost_out: host outputs (cost at the returned cams/pts). */
+ba_status ba_lm_step(ba_problem* prob, double* cams, double* pts, const double* obs,
+                     double* lambda_inout, int* accepted, double* cost_out);
+
+/* Adjoint of the last solve: given dL/ddelta (device, 9 n_cams + 3 n_pts: camera
+ * part then point part) returns dL/dobs (n_obs x 2, caller order), dL/dcams
+ * (n_cams x 9) and dL/dpts (n_pts x 3) at the linearisation point, holding lambda
+ * fixed and differentiating through D = lambda diag(J^T J).  Uses a second PCG solve
+ * with S and the same multigrid hierarchy.  Requires a completed ba_pcg_solve with
+ * rhs = NULL.  Any output may be NULL. */
+ba_status ba_adjoint(ba_problem* prob, const double* dL_ddelta, double* dL_dobs,
+                     double* dL_dcams, double* dL_dpts);
+
+/* ---------------------------------------------------------------------------------
+ * Inspection entry points (used by the parity tests; not needed to solve).
+ * --------------------------------------------------------------------------------- */
+
+/* y = S x with the implicit operator of Section 3.6 (x, y: device n_cams x 9, FP64).
+ * precision BA_MIXED runs the FP32-storage kernel used inside the V-cycle. */
+ba_status ba_schur_matvec(ba_problem* prob, const double* x, double* y, int precision);
+
+/* z = M^-1 r for the configured preconditioner (one V-cycle of Algorithm 1 for MG). */
+ba_status ba_precond_apply(ba_problem* prob, const double* r, double* z);
+
+typedef struct {
+  int n_levels;           /* multigrid levels (0 if no hierarchy) */
+  int level_nodes[16];    /* nodes per level */
+  int level_block[16];    /* dofs per node per level (9 at level 0, 16 below) */
+  int level_nnzb[16];     /* block nonzeros of the level operator (0 for coarsest) */
+  double level_lambda_max[16]; /* Lanczos estimate per smoothed level */
+  int pcg_iters;          /* last ba_pcg_solve */
+  double pcg_rel_res;
+  double cost;            /* last ba_linearize */
+  double lambda;          /* last ba_schur_setup */
+  long long kernel_launches; /* kernels launched by this problem so far */
+} ba_info;
+
+ba_status ba_get_info(ba_problem* prob, ba_info* info);
+
+/* Arrays that ba_get_array can copy out.  Per-observation arrays come out in the
+ * caller's observation order, per-point arrays in the caller's point order. */
+typedef enum {
+  BA_ARR_RESIDUAL = 0,   /* double [n_obs][2] */
+  BA_ARR_JAC_F = 1,      /* double [n_obs][2][9] */
+  BA_ARR_JAC_E = 2,      /* double [n_obs][2][3] */
+  BA_ARR_DAMP_C = 3,     /* double [n_cams][9] */
+  BA_ARR_DAMP_P = 4,     /* double [n_pts][3] */
+  BA_ARR_CINV = 5,       /* double [n_pts][3][3] */
+  BA_ARR_GRAD_C = 6,     /* double [n_cams][9]  g_c = -F^T f */
+  BA_ARR_GRAD_P = 7,     /* double [n_pts][3]   g_p = -E^T f */
+  BA_ARR_RHS = 8,        /* double [n_cams][9]  reduced RHS b */
+  BA_ARR_LEVEL_ROWPTR = 9,  /* int32 [n_l + 1]  BSR row pointers of level l's operator */
+  BA_ARR_LEVEL_COLS = 10,   /* int32 [nnzb]     BSR block columns (sorted per row) */
+  BA_ARR_LEVEL_VALS = 11,   /* double [nnzb][b][b] operator blocks (level 0 = explicit S) */
+  BA_ARR_LEVEL_W = 12,      /* int64 [nnzb]     covisibility counts W on the same pattern */
+  BA_ARR_STRENGTH_PTR = 13, /* int32 [n_l + 1]  strength-ordered neighbour lists */
+  BA_ARR_STRENGTH_IDX = 14, /* int32 [...] */
+  BA_ARR_AGG = 15,          /* int32 [n_l]      aggregate of each node of level l */
+  BA_ARR_NULLSPACE = 16,    /* double [n_l][b][16] near-nullspace rows of level l */
+  BA_ARR_PROLONG = 17,      /* double [n_l][b][16] Q blocks (P restricted to each node) */
+  BA_ARR_KEPT = 18,         /* uint32 [n_{l+1}] bit s set if coarse dof s is kept */
+  BA_ARR_JACOBI_INV = 19,   /* double [n_l][b][b] inverse diagonal blocks of level l */
+  BA_ARR_COARSE_INV = 20,   /* double [N][N] inverse of the coarsest operator */
+  BA_ARR_SCC_INV = 21       /* double [n_cams][9][9] point-block-Jacobi blocks S_cc^-1 */
+} ba_array;
+
+/* Kernel classes whose launches can be timed with CUDA events on the problem's stream. */
+typedef enum {
+  BA_KT_SCHUR_FP64 = 0,  /* implicit Schur product, FP64 storage (outer PCG operator) */
+  BA_KT_SCHUR_FP32 = 1,  /* implicit Schur product, FP32 storage (inside the V-cycle) */
+  BA_KT_LINEARIZE = 2,   /* residual + Jacobian kernel */
+  BA_KT_COUNT = 3
+} ba_kernel_class;
+
+/* enable != 0 starts recording a CUDA event pair around every launch of the timed
+ * classes (and clears earlier records); 0 stops recording. */
+ba_status ba_set_kernel_timing(ba_problem* prob, int enable);
+
+/* Sum of the recorded launch durations (ms, host) and the launch count (host) of one
+ * kernel class since timing was enabled.  Synchronises the stream. */
+ba_status ba_get_kernel_timing(ba_problem* prob, int kernel_class, double* total_ms,
+                               long long* launches);
+
+/* Copies internal array `which` (of multigrid level `level` where relevant) into dst
+ * (device memory, capacity `bytes`).  *needed (host, may be NULL) receives the size;
+ * with dst == NULL only the size is returned. */
+ba_status ba_get_array(ba_problem* prob, int which, int level, void* dst, size_t bytes,
+                       size_t* needed);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BA_H_ */

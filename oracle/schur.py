@@ -66,7 +66,8 @@ def blockdiag_sparse(blocks):
 class Schur:
     """All pieces of one linearisation's reduced camera system."""
 
-    def __init__(self, F, E, f, cam_idx, pt_idx, n_cams, n_pts, lam, damping_mode="marquardt"):
+    def __init__(self, F, E, f, cam_idx, pt_idx, n_cams, n_pts, lam, damping_mode="marquardt",
+                 explicit=True):
         self.n_cams, self.n_pts = n_cams, n_pts
         self.Fb, self.Eb, self.f = F, E, f
         self.cam_idx, self.pt_idx = cam_idx, pt_idx
@@ -81,8 +82,10 @@ class Schur:
         self.C = (Em.T @ Em + sp.diags(self.Dp)).tocsr()
         self.Cinv, self.C_blocks, self.Cinv_blocks = block_diag_inverse(self.C, 3)
         self.B = (Fm.T @ Em).tocsr()                       # F^T E
-        self.S = (self.A - self.B @ self.Cinv @ self.B.T).tocsr()
-        self.S.sum_duplicates()
+        self.S = None
+        if explicit:                                       # large problems use the implicit product
+            self.S = (self.A - self.B @ self.Cinv @ self.B.T).tocsr()
+            self.S.sum_duplicates()
         self.b = self.g_c - self.B @ (self.Cinv @ self.g_p)
 
     def implicit_matvec(self, x):
@@ -107,8 +110,8 @@ class Schur:
         return 0.5 * (dg + dDd)
 
 
-def linearize(cams, pts, cam_idx, pt_idx, obs, lam, damping_mode="marquardt"):
+def linearize(cams, pts, cam_idx, pt_idx, obs, lam, damping_mode="marquardt", explicit=True):
     from . import camera
     f = camera.residuals(cams, pts, cam_idx, pt_idx, obs)
     F, E = camera.jacobians(cams, pts, cam_idx, pt_idx)
-    return Schur(F, E, f, cam_idx, pt_idx, cams.shape[0], pts.shape[0], lam, damping_mode)
+    return Schur(F, E, f, cam_idx, pt_idx, cams.shape[0], pts.shape[0], lam, damping_mode, explicit)

@@ -1,0 +1,246 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ba.h"
+
+namespace ba {
+
+constexpr int kNull = 16;        // near-nullspace dimension (Section 3.3)
+constexpr int kScalars = 64;     // device scalar slots per problem
+
+// Error raised inside the library; converted to a ba_status at the C boundary.
+struct Error : std::runtime_error {
+  ba_status status;
+  Error(ba_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define BA_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      throw ::ba::Error(e_ == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));       \
+  } while (0)
+
+#define BA_REQUIRE(cond, status, msg)                   \
+  do {                                                  \
+    if (!(cond)) throw ::ba::Error((status), (msg));    \
+  } while (0)
+
+// Device buffer that keeps its capacity across calls.
+struct DBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+  void ensure(size_t bytes) {
+    if (bytes <= cap && p) return;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t b = bytes ? bytes : 16;
+    BA_CUDA(cudaMalloc(&p, b));
+    cap = b;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+// Slots of the device scalar array.
+enum Scalar : int {
+  S_COST = 0,      // 1/2 sum |f|^2
+  S_RR = 1,        // r.r
+  S_RZ = 2,        // r.z (current)
+  S_PQ = 3,        // p.q
+  S_ALPHA = 4,
+  S_BETA = 5,
+  S_BB = 6,        // b.b
+  S_TMP0 = 7,
+  S_TMP1 = 8,
+  S_TMP2 = 9,
+  S_MODEL = 10,    // model reduction terms
+  S_COST_NEW = 11,
+  S_LANCZOS = 16,  // 16 .. 31: alphas / betas of the Lanczos recurrences
+  S_LANCZOS_END = 32,
+};
+
+// Device error flags.
+enum Flag : int {
+  F_NOT_SPD_POINT = 0,
+  F_NOT_SPD_JACOBI = 1,
+  F_NOT_SPD_COARSE = 2,
+  F_BREAKDOWN = 3,
+  F_HASH_OVERFLOW = 4,
+  F_NONFINITE = 5,
+  F_COUNT = 8
+};
+
+struct Level {
+  int n = 0, bs = 0;            // nodes, dofs per node
+  int nnzb = 0;                 // block nonzeros of the operator / covisibility pattern
+  DBuf row_ptr, cols, W;        // BSR pattern (int32) and covisibility counts (int64)
+  DBuf vals64, vals32;          // operator blocks [nnzb][bs][bs]
+  DBuf sptr, sidx;              // strength-ordered neighbour lists
+  int n_strength = 0;
+  DBuf agg;                     // int32 [n] aggregate (= next-level node) of each node
+  int n_agg = 0;
+  DBuf agg_ptr, agg_mem;        // member lists of the next-level nodes
+  DBuf K;                       // double [n][bs][16] near-nullspace rows
+  DBuf Q64, Q32;                // double/float [n][bs][16] prolongator blocks
+  DBuf kept;                    // uint32 [n] kept-dof masks of this level's nodes
+  DBuf Dblk, Dinv64, Dinv32;    // diagonal blocks and their inverses [n][bs][bs]
+  DBuf cheb;                    // double[4]: theta, delta, sigma1, lambda_max
+  double lam_max = 0.0;
+  bool coarsest = false;
+  int N = 0;                    // coarsest: dense size n*bs
+  DBuf Ainv;                    // coarsest: double [N][N]
+  DBuf vx, vb, vr, vd, vq, vt, vs;  // V-cycle vectors in the level's precision
+};
+
+}  // namespace ba
+
+struct ba_problem {
+  ba_options opt;
+  cudaStream_t stream = nullptr;
+  int n_c = 0, n_p = 0, n_o = 0;
+  int n_p_obs = 0;              // points with at least one observation (internal prefix)
+  int n_sm = 0;
+  std::string err;
+  long long launches = 0;
+  int stage = 0;                // 0 created, 1 linearized, 2 schur, 3 mg, 4 solved
+
+  // observation graph in internal order (points sorted by first camera, obs by point, camera)
+  ba::DBuf obs_user;            // int32 [n_o] internal obs -> caller obs index
+  ba::DBuf obs_cam;             // int32 [n_o] camera of each internal obs
+  ba::DBuf obs_ptu;             // int32 [n_o] caller point index of each internal obs
+  ba::DBuf obs_pt;              // int32 [n_o] internal point of each internal obs
+  ba::DBuf pt_ptr;              // int32 [n_p + 1]
+  ba::DBuf pt_user;             // int32 [n_p] internal point -> caller point
+  ba::DBuf cam_ptr, cam_obs;    // camera-major CSR over internal obs
+  int n_tiles = 0, n_chunks = 0, k3_window = 0;
+  ba::DBuf tile_pt;             // int32 [n_tiles + 1] point ranges of <=32-obs warp tiles
+  ba::DBuf chunk_tile;          // int32 [n_chunks + 1] tile ranges per matvec CTA
+  ba::DBuf chunk_cam;           // int32 [2 n_chunks] lowest / highest camera of a chunk
+  size_t ld = 0;                // leading dimension of per-observation SoA arrays
+  size_t ldp = 0;               // leading dimension of per-point SoA arrays
+  int max_row_contrib = 0;      // max_c sum_{o in c} |obs(point(o))| (hash sizing)
+
+  // linearisation (SoA, internal order)
+  ba::DBuf camx;                // double [n_c][24] per-camera rotation data
+  ba::DBuf fres;                // double [2][ld]
+  ba::DBuf F64, E64;            // double [18][ld], [6][ld]
+  ba::DBuf F32, E32;            // float copies (mixed precision)
+  ba::DBuf cams_lin, pts_lin;   // copies of the linearisation point (adjoint, nullspace)
+  ba::DBuf obs_lin;             // copy of the observations of the last linearisation
+
+  // Schur reduction
+  double lambda = 0.0;
+  ba::DBuf Dc, Dp;              // double [n_c*9], [ldp][3] (internal points, SoA)
+  ba::DBuf Cinv64, Cinv32;      // [6][ldp]
+  ba::DBuf gc, gp, wp, rhs;     // g_c [n_c*9], g_p [3][ldp], C^-1 g_p [3][ldp], b [n_c*9]
+  ba::DBuf Dc32;                // float copy of D_c
+  ba::DBuf Scc;                 // double [n_c][81] diagonal blocks S_cc
+  ba::DBuf Scc_inv, Scc_inv32;  // their inverses (point-block-Jacobi), FP64 and FP32
+
+  // multigrid hierarchy
+  std::vector<ba::Level> levels;
+  int n_levels = 0;
+
+  // PCG
+  ba::DBuf x, r, z, p, q, y32a, y32b;
+  ba::DBuf delta_c, delta_p;    // last solve (internal layout: [n_c*9], [3][ldp])
+  int pcg_iters = 0;
+  double pcg_rel = 0.0;
+  double cost = 0.0;
+  double lm_nu = 2.0;
+
+  // reductions and flags
+  ba::DBuf scal;                // double [kScalars]
+  ba::DBuf partial;             // double [partial_cap]
+  ba::DBuf counter;             // unsigned [8]
+  ba::DBuf flags;               // int [F_COUNT]
+  double* h_scal = nullptr;     // pinned host mirror
+  int* h_flags = nullptr;
+  ba::DBuf scratch;             // general scratch
+  ba::DBuf scratch2;
+
+  // optional CUDA-event timing of selected kernel classes
+  bool ktime = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct KRec { int cls; cudaEvent_t a, b; };
+  std::vector<KRec> krec;
+};
+
+namespace ba {
+// Records a CUDA event pair around the launches made during its lifetime when
+// kernel timing is enabled on the problem.
+struct KernelTimer {
+  ba_problem* P;
+  int cls;
+  cudaEvent_t a = nullptr, b = nullptr;
+  KernelTimer(ba_problem* p, int c);
+  ~KernelTimer();
+};
+void kernel_timing_enable(ba_problem* P, bool on);
+void kernel_timing_get(ba_problem* P, int cls, double* ms, long long* n);
+}  // namespace ba
+
+namespace ba {
+
+// ---- stream helpers -------------------------------------------------------
+void sync(ba_problem* P);
+void fetch_scalars(ba_problem* P, int first, int count);  // async copy + sync
+void check_flags(ba_problem* P);                          // sync, read, raise
+void clear_flags(ba_problem* P);
+void launched(ba_problem* P);                              // count + check launch error
+
+// ---- graph preprocessing (graph.cu) ----------------------------------------
+void build_graph(ba_problem* P, const int32_t* cam_idx_dev, const int32_t* pt_idx_dev);
+
+// ---- linearisation (linearize.cu) ------------------------------------------
+void linearize(ba_problem* P, const double* cams, const double* pts, const double* obs);
+double cost_at(ba_problem* P, const double* cams, const double* pts, const double* obs);
+
+// ---- Schur reduction and implicit operator (schur.cu) -----------------------
+void schur_setup(ba_problem* P, double lambda);
+// y = S x on internal camera vectors; T selects the FP64 or FP32 storage kernel.
+void matvec64(ba_problem* P, const double* x, double* y);
+void matvec32(ba_problem* P, const float* x, float* y);
+void explicit_schur(ba_problem* P, Level& L0, bool fp32);
+void back_substitute_to(ba_problem* P, const double* dc, double* out_int, double* out_user);
+void reduced_rhs(ba_problem* P, const double* vc, const double* vp_user, double* out);
+
+// ---- multigrid setup (mg_setup.cu) ------------------------------------------
+void mg_setup(ba_problem* P);
+void covisibility_level0(ba_problem* P, Level& L);
+void jacobi_blocks(ba_problem* P, Level& L, bool from_vals64);
+
+// ---- solve (solve.cu) -------------------------------------------------------
+void precond_apply(ba_problem* P, const double* r, double* z);
+void pcg(ba_problem* P, const double* rhs, double* dc);
+void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double* lam,
+             int* accepted, double* cost);
+
+// ---- adjoint (adjoint.cu) ---------------------------------------------------
+void adjoint(ba_problem* P, const double* dL_ddelta, double* dL_dobs, double* dL_dcams,
+             double* dL_dpts);
+
+// ---- reductions (reduce.cu) -------------------------------------------------
+// out_slot = sum_i a_i b_i (a, b of type T, length n), deterministic two-stage.
+void dot64(ba_problem* P, const double* a, const double* b, size_t n, int slot);
+void dot32(ba_problem* P, const float* a, const float* b, size_t n, int slot);
+int reduce_blocks(ba_problem* P, size_t n);
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace ba

@@ -1,0 +1,108 @@
+// Device-side helpers shared by the kernels: warp/block reductions, the
+// deterministic two-stage grid reduction and small dense block routines.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace ba {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+  return v;
+}
+
+// Sum over a block of BS threads; result valid in thread 0.
+template <int BS>
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red_smem[BS / 32];
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red_smem[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = (l < BS / 32) ? red_smem[l] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+// Deterministic grid reduction: every block writes its partial sum; the last
+// block to finish adds the partials in block order and stores the total.
+template <int BS>
+__device__ __forceinline__ void grid_sum_store(double v, double* partial, unsigned* counter,
+                                               double* out) {
+  __shared__ bool am_last;
+  double s = block_sum<BS>(v);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) {
+    __threadfence();
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += BS) acc += __ldcg(partial + i);
+    acc = block_sum<BS>(acc);
+    if (threadIdx.x == 0) {
+      *out = acc;
+      *counter = 0u;
+    }
+  }
+}
+
+// In-place inverse of an n x n SPD matrix (row-major, n <= 16) held by one thread,
+// via Cholesky A = L L^T, L^-1 and A^-1 = L^-T L^-1.  Returns false if a pivot is
+// not positive (the matrix is then left partially overwritten).
+template <int NMAX>
+__device__ bool spd_inverse(double* a, int n) {
+  // Cholesky, lower triangle in place
+  for (int j = 0; j < n; ++j) {
+    double d = a[j * n + j];
+    for (int k = 0; k < j; ++k) d -= a[j * n + k] * a[j * n + k];
+    if (!(d > 0.0)) return false;
+    d = sqrt(d);
+    a[j * n + j] = d;
+    const double inv = 1.0 / d;
+    for (int i = j + 1; i < n; ++i) {
+      double s = a[i * n + j];
+      for (int k = 0; k < j; ++k) s -= a[i * n + k] * a[j * n + k];
+      a[i * n + j] = s * inv;
+    }
+  }
+  // L^-1 in place (lower triangle)
+  for (int j = 0; j < n; ++j) {
+    a[j * n + j] = 1.0 / a[j * n + j];
+    for (int i = j + 1; i < n; ++i) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s -= a[i * n + k] * a[k * n + j];
+      a[i * n + j] = s / a[i * n + i];
+    }
+  }
+  // A^-1 = L^-T L^-1 ; compute lower triangle then mirror
+  double tmp[NMAX];
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = 0.0;
+      for (int k = i; k < n; ++k) s += a[k * n + i] * a[k * n + j];
+      tmp[j] = s;
+    }
+    // row i of result lower part stored after finishing (entries a[k*n+i] for k>=i are
+    // still needed by later rows i' > i only through columns >= i', untouched here)
+    for (int j = 0; j <= i; ++j) a[i * n + j] = tmp[j];
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) a[i * n + j] = a[j * n + i];
+  return true;
+}
+
+}  // namespace ba

@@ -1,0 +1,248 @@
+// K1: residuals and Jacobian blocks of the 9-parameter camera (Section 2.1, Eq. 1-2).
+//
+// Camera model (BAL convention, see ba.h): P = R(r) X + t, p = -P_xy / P_z,
+// d = 1 + k1 |p|^2 + k2 |p|^4, f_o = f d p - obs_o.
+//
+// Formulation used on the GPU: per camera, R(r) and the left Jacobian of SO(3)
+// J_l(r) = I + ((1-cos th)/th^2) [r]_x + ((th - sin th)/th^3) [r]_x^2 are computed
+// once; per observation d(RX)/dr = -[R X]_x J_l(r) and d(RX)/dX = R.  For
+// th^2 < 1e-16 the rotation is taken to first order: R X = X + r x X with
+// d(RX)/dr = -[X]_x and d(RX)/dX = I + [r]_x.
+#include "ba_internal.h"
+#include "device_util.cuh"
+
+namespace ba {
+
+constexpr int kCamx = 24;   // doubles of per-camera rotation data
+constexpr int kLinBS = 256;
+
+__global__ void k_camera_rotation(const double* __restrict__ cams, int n_c, double* __restrict__ camx) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_c) return;
+  const double r0 = cams[9 * c + 0], r1 = cams[9 * c + 1], r2 = cams[9 * c + 2];
+  const double th2 = r0 * r0 + r1 * r1 + r2 * r2;
+  double* o = camx + (size_t)kCamx * c;
+  if (th2 < 1e-16) {
+    // first-order rotation; J_l unused
+    const double R[9] = {1.0, -r2, r1, r2, 1.0, -r0, -r1, r0, 1.0};
+    for (int i = 0; i < 9; ++i) o[i] = R[i];
+    for (int i = 0; i < 9; ++i) o[9 + i] = (i % 4 == 0) ? 1.0 : 0.0;
+    o[18] = 1.0;
+    return;
+  }
+  const double th = sqrt(th2);
+  double s, co;
+  sincos(th, &s, &co);
+  const double a = (1.0 - co) / th2;           // (1 - cos)/th^2
+  const double b = (th - s) / (th2 * th);      // (th - sin)/th^3
+  const double al = s / th;                    // sin/th
+  // K = [r]_x ; K^2 = r r^T - th^2 I
+  const double K[9] = {0.0, -r2, r1, r2, 0.0, -r0, -r1, r0, 0.0};
+  const double rv[3] = {r0, r1, r2};
+  double K2[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) K2[3 * i + j] = rv[i] * rv[j] - (i == j ? th2 : 0.0);
+  for (int i = 0; i < 9; ++i) {
+    const double I = (i % 4 == 0) ? 1.0 : 0.0;
+    o[i] = I + al * K[i] + a * K2[i];          // Rodrigues R = I + sin/th K + (1-cos)/th^2 K^2
+    o[9 + i] = I + a * K[i] + b * K2[i];       // J_l
+  }
+  o[18] = 0.0;
+}
+
+struct CamObs {
+  double res[2];
+  double F[18];
+  double E[6];
+};
+
+template <bool JAC>
+__device__ __forceinline__ void project_obs(const double* __restrict__ cam, const double* __restrict__ cx,
+                                            const double X[3], const double ob[2], CamObs& out) {
+  const bool small = cx[18] != 0.0;
+  double RX[3];
+  if (small) {
+    const double r0 = cam[0], r1 = cam[1], r2 = cam[2];
+    RX[0] = X[0] + (r1 * X[2] - r2 * X[1]);
+    RX[1] = X[1] + (r2 * X[0] - r0 * X[2]);
+    RX[2] = X[2] + (r0 * X[1] - r1 * X[0]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) RX[i] = cx[3 * i] * X[0] + cx[3 * i + 1] * X[1] + cx[3 * i + 2] * X[2];
+  }
+  const double P0 = RX[0] + cam[3], P1 = RX[1] + cam[4], P2 = RX[2] + cam[5];
+  const double iz = 1.0 / P2;
+  const double px = -P0 * iz, py = -P1 * iz;
+  const double f = cam[6], k1 = cam[7], k2 = cam[8];
+  const double r2 = px * px + py * py;
+  const double d = 1.0 + k1 * r2 + k2 * r2 * r2;
+  out.res[0] = f * d * px - ob[0];
+  out.res[1] = f * d * py - ob[1];
+  if (!JAC) return;
+  // d pi / d p = f (d I + p (grad d)^T),  grad d = 2 (k1 + 2 k2 r2) p
+  const double gd = 2.0 * (k1 + 2.0 * k2 * r2);
+  const double A00 = f * (d + px * gd * px), A01 = f * (px * gd * py);
+  const double A10 = f * (py * gd * px), A11 = f * (d + py * gd * py);
+  // d p / d P = [[-iz, 0, P0 iz^2], [0, -iz, P1 iz^2]]
+  const double iz2 = iz * iz;
+  double G[6];  // d pi / d P (2x3)
+  G[0] = -A00 * iz;
+  G[1] = -A01 * iz;
+  G[2] = (A00 * P0 + A01 * P1) * iz2;
+  G[3] = -A10 * iz;
+  G[4] = -A11 * iz;
+  G[5] = (A10 * P0 + A11 * P1) * iz2;
+  // d P / d r
+  double Dr[9];
+  if (small) {
+    // -[X]_x
+    Dr[0] = 0.0;    Dr[1] = X[2];   Dr[2] = -X[1];
+    Dr[3] = -X[2];  Dr[4] = 0.0;    Dr[5] = X[0];
+    Dr[6] = X[1];   Dr[7] = -X[0];  Dr[8] = 0.0;
+  } else {
+    // -[RX]_x J_l : column j = -(RX x J_l[:, j])
+    const double* J = cx + 9;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double m0 = J[j], m1 = J[3 + j], m2 = J[6 + j];
+      Dr[0 + j] = -(RX[1] * m2 - RX[2] * m1);
+      Dr[3 + j] = -(RX[2] * m0 - RX[0] * m2);
+      Dr[6 + j] = -(RX[0] * m1 - RX[1] * m0);
+    }
+  }
+  // d P / d X
+  double Dx[9];
+  if (small) {
+    const double r0 = cam[0], r1 = cam[1], r2c = cam[2];
+    Dx[0] = 1.0;  Dx[1] = -r2c; Dx[2] = r1;
+    Dx[3] = r2c;  Dx[4] = 1.0;  Dx[5] = -r0;
+    Dx[6] = -r1;  Dx[7] = r0;   Dx[8] = 1.0;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Dx[i] = cx[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      out.F[9 * i + j] = G[3 * i] * Dr[j] + G[3 * i + 1] * Dr[3 + j] + G[3 * i + 2] * Dr[6 + j];
+      out.F[9 * i + 3 + j] = G[3 * i + j];
+      out.E[3 * i + j] = G[3 * i] * Dx[j] + G[3 * i + 1] * Dx[3 + j] + G[3 * i + 2] * Dx[6 + j];
+    }
+  }
+  out.F[6] = d * px;
+  out.F[15] = d * py;
+  out.F[7] = f * r2 * px;
+  out.F[16] = f * r2 * py;
+  out.F[8] = f * r2 * r2 * px;
+  out.F[17] = f * r2 * r2 * py;
+}
+
+template <bool JAC, bool MIXED>
+__global__ void __launch_bounds__(kLinBS)
+k_linearize(const double* __restrict__ cams, const double* __restrict__ pts,
+            const double* __restrict__ obs, const double* __restrict__ camx,
+            const int* __restrict__ obs_cam, const int* __restrict__ obs_ptu,
+            const int* __restrict__ obs_user, int n_o, size_t ld, double* __restrict__ fres,
+            double* __restrict__ F64, double* __restrict__ E64, float* __restrict__ F32,
+            float* __restrict__ E32, double* partial, unsigned* counter, double* cost_out,
+            int* flags) {
+  double acc = 0.0;
+  for (int o = blockIdx.x * kLinBS + threadIdx.x; o < n_o; o += gridDim.x * kLinBS) {
+    const int c = obs_cam[o];
+    const int pu = obs_ptu[o];
+    const int ou = obs_user[o];
+    const double X[3] = {pts[3 * pu], pts[3 * pu + 1], pts[3 * pu + 2]};
+    const double ob[2] = {obs[2 * ou], obs[2 * ou + 1]};
+    CamObs v;
+    project_obs<JAC>(cams + 9 * c, camx + (size_t)kCamx * c, X, ob, v);
+    acc += 0.5 * (v.res[0] * v.res[0] + v.res[1] * v.res[1]);
+    if (fres) {
+      fres[o] = v.res[0];
+      fres[ld + o] = v.res[1];
+    }
+    if (JAC) {
+      bool finite = isfinite(v.res[0]) && isfinite(v.res[1]);
+#pragma unroll
+      for (int k = 0; k < 18; ++k) {
+        F64[k * ld + o] = v.F[k];
+        finite = finite && isfinite(v.F[k]);
+        if (MIXED) F32[k * ld + o] = (float)v.F[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        E64[k * ld + o] = v.E[k];
+        finite = finite && isfinite(v.E[k]);
+        if (MIXED) E32[k * ld + o] = (float)v.E[k];
+      }
+      if (!finite) flags[F_NONFINITE] = 1;
+    }
+  }
+  grid_sum_store<kLinBS>(acc, partial, counter, cost_out);
+}
+
+static void camera_rotation(ba_problem* P, const double* cams, double* camx) {
+  k_camera_rotation<<<cdiv(P->n_c, 128), 128, 0, P->stream>>>(cams, P->n_c, camx);
+  launched(P);
+}
+
+static int lin_grid(ba_problem* P) {
+  int g = cdiv(P->n_o, kLinBS);
+  return std::max(1, std::min(g, P->n_sm * 8));
+}
+
+void linearize(ba_problem* P, const double* cams, const double* pts, const double* obs) {
+  const size_t ld = P->ld;
+  const bool mixed = P->opt.precision == BA_MIXED;
+  P->camx.ensure(sizeof(double) * kCamx * std::max(P->n_c, 1));
+  P->fres.ensure(sizeof(double) * 2 * ld);
+  P->F64.ensure(sizeof(double) * 18 * ld);
+  P->E64.ensure(sizeof(double) * 6 * ld);
+  if (mixed) {
+    P->F32.ensure(sizeof(float) * 18 * ld);
+    P->E32.ensure(sizeof(float) * 6 * ld);
+  }
+  // keep the linearisation point (near-nullspace and adjoint use it)
+  P->cams_lin.ensure(sizeof(double) * 9 * std::max(P->n_c, 1));
+  P->pts_lin.ensure(sizeof(double) * 3 * std::max(P->n_p, 1));
+  BA_CUDA(cudaMemcpyAsync(P->cams_lin.p, cams, sizeof(double) * 9 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
+  if (P->n_p)
+    BA_CUDA(cudaMemcpyAsync(P->pts_lin.p, pts, sizeof(double) * 3 * P->n_p, cudaMemcpyDeviceToDevice, P->stream));
+  P->obs_lin.ensure(sizeof(double) * 2 * std::max(P->n_o, 1));
+  if (P->n_o)
+    BA_CUDA(cudaMemcpyAsync(P->obs_lin.p, obs, sizeof(double) * 2 * P->n_o, cudaMemcpyDeviceToDevice, P->stream));
+  clear_flags(P);
+  camera_rotation(P, cams, P->camx.as<double>());
+  int g = lin_grid(P);
+  double* cost = P->scal.as<double>() + S_COST;
+  KernelTimer kt(P, BA_KT_LINEARIZE);
+  if (mixed)
+    k_linearize<true, true><<<g, kLinBS, 0, P->stream>>>(
+        cams, pts, obs, P->camx.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
+        P->obs_user.as<int>(), P->n_o, ld, P->fres.as<double>(), P->F64.as<double>(),
+        P->E64.as<double>(), P->F32.as<float>(), P->E32.as<float>(), P->partial.as<double>(),
+        P->counter.as<unsigned>(), cost, P->flags.as<int>());
+  else
+    k_linearize<true, false><<<g, kLinBS, 0, P->stream>>>(
+        cams, pts, obs, P->camx.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
+        P->obs_user.as<int>(), P->n_o, ld, P->fres.as<double>(), P->F64.as<double>(),
+        P->E64.as<double>(), nullptr, nullptr, P->partial.as<double>(), P->counter.as<unsigned>(),
+        cost, P->flags.as<int>());
+  launched(P);
+}
+
+double cost_at(ba_problem* P, const double* cams, const double* pts, const double* obs) {
+  P->scratch2.ensure(sizeof(double) * kCamx * std::max(P->n_c, 1));
+  camera_rotation(P, cams, P->scratch2.as<double>());
+  int g = lin_grid(P);
+  k_linearize<false, false><<<g, kLinBS, 0, P->stream>>>(
+      cams, pts, obs, P->scratch2.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
+      P->obs_user.as<int>(), P->n_o, P->ld, nullptr, nullptr, nullptr, nullptr, nullptr,
+      P->partial.as<double>(), P->counter.as<unsigned>(), P->scal.as<double>() + S_COST_NEW,
+      P->flags.as<int>());
+  launched(P);
+  fetch_scalars(P, S_COST_NEW, 1);
+  return P->h_scal[S_COST_NEW];
+}
+
+}  // namespace ba

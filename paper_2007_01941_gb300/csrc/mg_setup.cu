@@ -1,0 +1,1060 @@
+// Multigrid setup of Section 3 on the GPU:
+//   covisibility counts W = V^T V and the block pattern of S (K5),
+//   strength-of-connection ordering (Section 3.2) and Algorithm 2 aggregation (K6),
+//   near-nullspace (Section 3.1) and per-aggregate QR prolongators (Section 3.3, K7),
+//   Galerkin coarse operators P^T A P (Section 2.3, K8),
+//   block-Jacobi inverses (K4), Lanczos lambda_max (Section 3.4, K10) and the
+//   coarsest direct solver (an explicit FP64 inverse, K12).
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <climits>
+
+#include "ba_internal.h"
+#include "device_util.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ba {
+
+void block_inverse(ba_problem* P, const double* in, int n, int bs, double* out64, float* out32,
+                   int flag_slot);
+void level_matvec(ba_problem* P, int l, const void* x, void* y);
+bool level_fp32(ba_problem* P);
+
+// ---------------------------------------------------------------------------
+// exclusive scan of n ints (single CTA; n is at most a few million)
+// ---------------------------------------------------------------------------
+constexpr int kScanBS = 1024;
+__global__ void __launch_bounds__(kScanBS) k_scan_exclusive(const int* __restrict__ in, int* __restrict__ out,
+                                                            int n) {
+  __shared__ int s[kScanBS];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += kScanBS) {
+    const int i = base + threadIdx.x;
+    const int v = (i < n) ? in[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int d = 1; d < kScanBS; d <<= 1) {
+      const int t = (threadIdx.x >= d) ? s[threadIdx.x - d] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < n) out[i] = carry + s[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == kScanBS - 1) carry += s[kScanBS - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
+static int scan(ba_problem* P, const int* in, int* out, int n) {
+  k_scan_exclusive<<<1, kScanBS, 0, P->stream>>>(in, out, n);
+  launched(P);
+  int total = 0;
+  BA_CUDA(cudaMemcpyAsync(&total, out + n, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  sync(P);
+  return total;
+}
+
+// ---------------------------------------------------------------------------
+// Row-wise accumulation of (key, value) contributions in a shared-memory hash
+// table; then the distinct keys of the row sorted ascending.  MODE 0: level 0,
+// contributions of camera c are the cameras of every point c sees (value 1), plus
+// the diagonal key.  MODE 1: coarse level, contributions of aggregate a are
+// (agg[j], W_ij) for every entry (i, j) of every member i.
+// ---------------------------------------------------------------------------
+constexpr int kHashBS = 256;
+constexpr int kEmpty = INT_MAX;
+
+template <int MODE>
+__global__ void __launch_bounds__(kHashBS)
+k_row_hash(int n_rows, int H, const int* __restrict__ a_ptr, const int* __restrict__ a_list,
+           const int* __restrict__ b_ptr, const int* __restrict__ b_idx, const int* __restrict__ map,
+           const long long* __restrict__ Win, const int* __restrict__ out_ptr, int* __restrict__ out_cnt,
+           int* __restrict__ out_cols, long long* __restrict__ out_W, int* flags) {
+  extern __shared__ __align__(16) unsigned char hsm[];
+  long long* hv = reinterpret_cast<long long*>(hsm);      // [H]
+  int* hk = reinterpret_cast<int*>(hv + H);                 // [H]
+  int* ck = hk + H;                                          // [H] slots of the distinct keys
+  __shared__ int n_keys;
+  __shared__ int overflow;
+  const int row = blockIdx.x;
+  if (row >= n_rows) return;
+  for (int i = threadIdx.x; i < H; i += kHashBS) {
+    hk[i] = kEmpty;
+    hv[i] = 0;
+  }
+  if (threadIdx.x == 0) {
+    n_keys = 0;
+    overflow = 0;
+  }
+  __syncthreads();
+  auto insert = [&](int key, long long val) {
+    unsigned h = ((unsigned)key * 2654435761u) & (unsigned)(H - 1);
+    for (int probe = 0; probe < H; ++probe) {
+      const int prev = atomicCAS(hk + h, kEmpty, key);
+      if (prev == kEmpty || prev == key) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(hv + h), (unsigned long long)val);
+        return;
+      }
+      h = (h + 1) & (unsigned)(H - 1);
+    }
+    overflow = 1;
+  };
+  if (MODE == 0) {
+    if (threadIdx.x == 0) insert(row, 0);
+    // a_ptr/a_list: camera -> internal obs; b_ptr: point -> obs range; b_idx: obs -> point;
+    // map: obs -> camera
+    const int ab = a_ptr[row], ae = a_ptr[row + 1];
+    for (int k = ab + (threadIdx.x >> 5); k < ae; k += kHashBS / 32) {
+      const int o = a_list[k];
+      const int ip = b_idx[o];
+      for (int q = b_ptr[ip] + (threadIdx.x & 31); q < b_ptr[ip + 1]; q += 32) insert(map[q], 1);
+    }
+  } else {
+    // a_ptr/a_list: members of aggregate; b_ptr/b_idx: BSR pattern of the fine level;
+    // map: fine node -> aggregate; Win: fine W
+    const int ab = a_ptr[row], ae = a_ptr[row + 1];
+    for (int k = ab; k < ae; ++k) {
+      const int i = a_list[k];
+      for (int e = b_ptr[i] + threadIdx.x; e < b_ptr[i + 1]; e += kHashBS) insert(map[b_idx[e]], Win[e]);
+    }
+  }
+  __syncthreads();
+  if (overflow) {
+    if (threadIdx.x == 0) flags[F_HASH_OVERFLOW] = 1;
+    return;
+  }
+  // compact keys (order is fixed later by the sort)
+  for (int i = threadIdx.x; i < H; i += kHashBS) {
+    if (hk[i] != kEmpty) {
+      const int pos = atomicAdd(&n_keys, 1);
+      ck[pos] = i;  // slot index
+    }
+  }
+  __syncthreads();
+  const int nk = n_keys;
+  int m = 1;
+  while (m < nk) m <<= 1;
+  // sort slot indices by key (bitonic, keys looked up through the slots)
+  for (int i = nk + threadIdx.x; i < m; i += kHashBS) ck[i] = -1;
+  __syncthreads();
+  for (int size = 2; size <= m; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < m; i += kHashBS) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const int si = ck[i], sj = ck[j];
+          const int ki = si < 0 ? INT_MAX : hk[si];
+          const int kj = sj < 0 ? INT_MAX : hk[sj];
+          const bool up = (i & size) == 0;
+          if ((ki > kj) == up) {
+            ck[i] = sj;
+            ck[j] = si;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (out_cnt) {
+    if (threadIdx.x == 0) out_cnt[row] = nk;
+  } else {
+    const int base = out_ptr[row];
+    for (int i = threadIdx.x; i < nk; i += kHashBS) {
+      out_cols[base + i] = hk[ck[i]];
+      out_W[base + i] = hv[ck[i]];
+    }
+  }
+}
+
+static int hash_size(int bound) {
+  int H = 64;
+  while (H < 2 * bound && H < 8192) H <<= 1;
+  return H;
+}
+
+static size_t hash_smem(int H) { return (size_t)H * (8 + 4 + 4); }
+
+template <int MODE>
+static void row_hash(ba_problem* P, int n_rows, int H, const int* a_ptr, const int* a_list,
+                     const int* b_ptr, const int* b_idx, const int* map, const long long* Win,
+                     Level& out) {
+  const size_t smem = hash_smem(H);
+  BA_CUDA(cudaFuncSetAttribute(k_row_hash<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // pass 1: counts
+  P->scratch.ensure(sizeof(int) * ((size_t)n_rows + 1) * 2 + 64);
+  int* cnt = P->scratch.as<int>();
+  clear_flags(P);
+  k_row_hash<MODE><<<n_rows, kHashBS, smem, P->stream>>>(n_rows, H, a_ptr, a_list, b_ptr, b_idx, map, Win,
+                                                         nullptr, cnt, nullptr, nullptr, P->flags.as<int>());
+  launched(P);
+  check_flags(P);
+  out.row_ptr.ensure(sizeof(int) * ((size_t)n_rows + 1));
+  out.nnzb = scan(P, cnt, out.row_ptr.as<int>(), n_rows);
+  out.cols.ensure(sizeof(int) * (size_t)std::max(out.nnzb, 1));
+  out.W.ensure(sizeof(long long) * (size_t)std::max(out.nnzb, 1));
+  k_row_hash<MODE><<<n_rows, kHashBS, smem, P->stream>>>(n_rows, H, a_ptr, a_list, b_ptr, b_idx, map, Win,
+                                                         out.row_ptr.as<int>(), nullptr, out.cols.as<int>(),
+                                                         out.W.as<long long>(), P->flags.as<int>());
+  launched(P);
+  check_flags(P);
+}
+
+void covisibility_level0(ba_problem* P, Level& L) {
+  L.n = P->n_c;
+  L.bs = 9;
+  const int H = hash_size(std::min(P->n_c, std::max(P->max_row_contrib, 1)));
+  row_hash<0>(P, P->n_c, H, P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->pt_ptr.as<int>(),
+              P->obs_pt.as<int>(), P->obs_cam.as<int>(), nullptr, L);
+}
+
+// ---------------------------------------------------------------------------
+// strength ordering: neighbours j != i by decreasing W_ij / sqrt(W_jj) (the
+// common factor sqrt(W_ii) does not change the order), compared exactly as
+// W_ij^2 W_kk > W_ik^2 W_jj in 128-bit integers; ties to the smaller index.
+// ---------------------------------------------------------------------------
+__global__ void k_diag_w(int n, const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                         const long long* __restrict__ W, long long* __restrict__ Wd) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  long long d = 0;
+  for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+    if (cols[e] == i) d = W[e];
+  Wd[i] = d;
+}
+
+struct StrengthKey {
+  int j;
+  long long w;   // W_ij
+  long long wd;  // W_jj
+};
+
+__device__ __forceinline__ bool stronger(const StrengthKey& a, const StrengthKey& b) {
+  // true if a precedes b
+  const unsigned __int128 lhs = (unsigned __int128)((unsigned long long)a.w * (unsigned long long)a.w) *
+                                (unsigned long long)b.wd;
+  const unsigned __int128 rhs = (unsigned __int128)((unsigned long long)b.w * (unsigned long long)b.w) *
+                                (unsigned long long)a.wd;
+  if (lhs != rhs) return lhs > rhs;
+  return a.j < b.j;
+}
+
+constexpr int kStrBS = 128;
+__global__ void __launch_bounds__(kStrBS)
+k_strength_order(int n, const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                 const long long* __restrict__ W, const long long* __restrict__ Wd,
+                 int* __restrict__ sptr_out, int* __restrict__ sidx) {
+  extern __shared__ __align__(16) unsigned char ssm[];
+  StrengthKey* keys = reinterpret_cast<StrengthKey*>(ssm);
+  __shared__ int cnt;
+  const int i = blockIdx.x;
+  const int rb = row_ptr[i], re = row_ptr[i + 1];
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int m = 1;
+  while (m < re - rb) m <<= 1;
+  for (int e = rb + threadIdx.x; e < re; e += kStrBS) {
+    const int j = cols[e];
+    if (j != i && W[e] > 0) {
+      const int pos = atomicAdd(&cnt, 1);
+      keys[pos] = StrengthKey{j, W[e], Wd[j]};
+    }
+  }
+  __syncthreads();
+  const int nk = cnt;
+  for (int k = nk + threadIdx.x; k < m; k += kStrBS) keys[k] = StrengthKey{INT_MAX, 0, 1};
+  __syncthreads();
+  for (int size = 2; size <= m; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int a = threadIdx.x; a < m; a += kStrBS) {
+        const int b = a ^ stride;
+        if (b > a) {
+          const StrengthKey ka = keys[a], kb = keys[b];
+          const bool up = (a & size) == 0;
+          // padding (j == INT_MAX) always sorts last
+          bool a_first;
+          if (ka.j == INT_MAX) a_first = false;
+          else if (kb.j == INT_MAX) a_first = true;
+          else a_first = stronger(ka, kb);
+          if (a_first != up) {
+            keys[a] = kb;
+            keys[b] = ka;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const int base = sptr_out[i];
+  for (int k = threadIdx.x; k < nk; k += kStrBS) sidx[base + k] = keys[k].j;
+}
+
+__global__ void k_strength_count(int n, const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                                 const long long* __restrict__ W, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = 0;
+  for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) c += (cols[e] != i && W[e] > 0);
+  cnt[i] = c;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 2 (sequential greedy pass; one thread, state in shared memory when it
+// fits).  A node left unaggregated becomes a singleton aggregate afterwards.
+// ---------------------------------------------------------------------------
+template <bool SMEM>
+__global__ void k_aggregate(int n, const int* __restrict__ sptr, const int* __restrict__ sidx,
+                            int max_agg, int* __restrict__ agg_out, int* __restrict__ gsize,
+                            int* __restrict__ n_agg_out) {
+  extern __shared__ __align__(16) unsigned char asm_[];
+  int* agg = SMEM ? reinterpret_cast<int*>(asm_) : agg_out;
+  int* size = SMEM ? (agg + n) : gsize;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    agg[i] = -1;
+    size[i] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int na = 0;
+    for (int i = 0; i < n; ++i) {
+      if (agg[i] >= 0) continue;
+      const int e1 = sptr[i + 1];
+      for (int e = sptr[i]; e < e1; ++e) {
+        const int j = __ldg(sidx + e);
+        const int k = agg[j];
+        if (k < 0) {
+          agg[i] = na;
+          agg[j] = na;
+          size[na] = 2;
+          ++na;
+          break;
+        }
+        if (size[k] < max_agg) {
+          agg[i] = k;
+          size[k] += 1;
+          break;
+        }
+      }
+    }
+    for (int i = 0; i < n; ++i)
+      if (agg[i] < 0) agg[i] = na++;
+    *n_agg_out = na;
+  }
+  __syncthreads();
+  if (SMEM)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) agg_out[i] = agg[i];
+}
+
+__global__ void k_count_members(int n, const int* __restrict__ agg, int* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(cnt + agg[i], 1);
+}
+
+__global__ void k_fill_members(int n, const int* __restrict__ agg, const int* __restrict__ ptr,
+                               int* __restrict__ fill, int* __restrict__ mem) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const int a = agg[i];
+    mem[ptr[a] + atomicAdd(fill + a, 1)] = i;
+  }
+}
+
+__global__ void k_sort_members(int n_agg, const int* __restrict__ ptr, int* __restrict__ mem) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_agg) return;
+  const int b = ptr[a], e = ptr[a + 1];
+  for (int i = b + 1; i < e; ++i) {
+    const int v = mem[i];
+    int j = i - 1;
+    while (j >= b && mem[j] > v) {
+      mem[j + 1] = mem[j];
+      --j;
+    }
+    mem[j + 1] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// near-nullspace of level 0 (Section 3.1): per camera, 9 x 16 rows
+//   translation e_k: dt = -R e_k;  rotation e_k: dr = -J_l(r)^-1 R e_k;  scale: dt = t;
+//   then the 9 per-parameter constant columns.
+// J_l^-1 = I - 1/2 [r]_x + (1/th^2 - (1 + cos th) / (2 th sin th)) [r]_x^2 (1/12 for th < 1e-6).
+// ---------------------------------------------------------------------------
+__global__ void k_nullspace0(const double* __restrict__ cams, int n_c, double* __restrict__ K) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_c) return;
+  const double* cam = cams + 9 * c;
+  const double r0 = cam[0], r1 = cam[1], r2 = cam[2];
+  const double th2 = r0 * r0 + r1 * r1 + r2 * r2;
+  const double Km[9] = {0.0, -r2, r1, r2, 0.0, -r0, -r1, r0, 0.0};
+  double K2[9];
+  const double rv[3] = {r0, r1, r2};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) K2[3 * i + j] = rv[i] * rv[j] - (i == j ? th2 : 0.0);
+  double R[9], Jli[9];
+  if (th2 < 1e-16) {
+    for (int i = 0; i < 9; ++i) R[i] = ((i % 4 == 0) ? 1.0 : 0.0) + Km[i];
+  } else {
+    const double th = sqrt(th2);
+    double s, co;
+    sincos(th, &s, &co);
+    for (int i = 0; i < 9; ++i) R[i] = ((i % 4 == 0) ? 1.0 : 0.0) + s / th * Km[i] + (1.0 - co) / th2 * K2[i];
+  }
+  double coef;
+  if (sqrt(th2) < 1e-6) {
+    coef = 1.0 / 12.0;
+  } else {
+    const double th = sqrt(th2);
+    double s, co;
+    sincos(th, &s, &co);
+    coef = 1.0 / th2 - (1.0 + co) / (2.0 * th * s);
+  }
+  for (int i = 0; i < 9; ++i) Jli[i] = ((i % 4 == 0) ? 1.0 : 0.0) - 0.5 * Km[i] + coef * K2[i];
+  double* out = K + (size_t)c * 9 * kNull;
+  for (int i = 0; i < 9 * kNull; ++i) out[i] = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    // translation: rows 3..5 of column k = -R e_k
+    for (int i = 0; i < 3; ++i) out[(3 + i) * kNull + k] = -R[3 * i + k];
+    // rotation: rows 0..2 of column 3+k = -J_l^-1 R e_k
+    for (int i = 0; i < 3; ++i) {
+      double v = 0.0;
+      for (int m = 0; m < 3; ++m) v += Jli[3 * i + m] * R[3 * m + k];
+      out[i * kNull + 3 + k] = -v;
+    }
+  }
+  for (int i = 0; i < 3; ++i) out[(3 + i) * kNull + 6] = cam[3 + i];
+  for (int i = 0; i < 9; ++i) out[i * kNull + 7 + i] = 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// per-aggregate thin QR (Section 3.3) by modified Gram-Schmidt with one
+// re-orthogonalisation pass; a column whose remaining norm is <= 1e-10 of its
+// original norm is dropped (zero Q column, zero R row).  One warp per aggregate.
+// ---------------------------------------------------------------------------
+__global__ void k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, const int* __restrict__ mem,
+                               const double* __restrict__ K, double* __restrict__ Q64, float* __restrict__ Q32,
+                               double* __restrict__ Kc, unsigned* __restrict__ kept_out) {
+  extern __shared__ __align__(16) unsigned char qsm[];
+  double* A = reinterpret_cast<double*>(qsm);  // [rows][16]
+  const int a = blockIdx.x;
+  const int lane = threadIdx.x;
+  const int mb = mptr[a], me = mptr[a + 1];
+  const int rows = (me - mb) * bs;
+  for (int r = lane; r < rows; r += 32) {
+    const int s = r / bs, u = r - s * bs;
+    const double* src = K + ((size_t)mem[mb + s] * bs + u) * kNull;
+    for (int j = 0; j < kNull; ++j) A[r * kNull + j] = src[j];
+  }
+  __syncwarp();
+  double R[kNull];  // column j of R is produced at step j; lane j keeps row j of R
+  for (int j = 0; j < kNull; ++j) R[j] = 0.0;
+  unsigned kept = 0;
+  for (int j = 0; j < kNull; ++j) {
+    double n0 = 0.0;
+    for (int r = lane; r < rows; r += 32) n0 += A[r * kNull + j] * A[r * kNull + j];
+    n0 = sqrt(warp_sum(n0));
+    double rcol[kNull];
+    for (int i = 0; i < kNull; ++i) rcol[i] = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i = 0; i < j; ++i) {
+        if (!(kept >> i & 1u)) continue;
+        double h = 0.0;
+        for (int r = lane; r < rows; r += 32) h += A[r * kNull + i] * A[r * kNull + j];
+        h = warp_sum(h);
+        for (int r = lane; r < rows; r += 32) A[r * kNull + j] -= h * A[r * kNull + i];
+        __syncwarp();
+        rcol[i] += h;
+      }
+    }
+    double nv = 0.0;
+    for (int r = lane; r < rows; r += 32) nv += A[r * kNull + j] * A[r * kNull + j];
+    nv = sqrt(warp_sum(nv));
+    const bool keep = n0 > 0.0 && nv > 1e-10 * n0;
+    const double scale = keep ? 1.0 / nv : 0.0;
+    for (int r = lane; r < rows; r += 32) A[r * kNull + j] *= scale;
+    __syncwarp();
+    if (keep) {
+      rcol[j] = nv;
+      kept |= 1u << j;
+    }
+    // lane i stores R[i][j]
+    for (int i = 0; i < kNull; ++i)
+      if (lane == i) R[j] = rcol[i];
+  }
+  // Q blocks back to the member nodes
+  for (int r = lane; r < rows; r += 32) {
+    const int s = r / bs, u = r - s * bs;
+    const size_t dst = ((size_t)mem[mb + s] * bs + u) * kNull;
+    for (int j = 0; j < kNull; ++j) {
+      Q64[dst + j] = A[r * kNull + j];
+      Q32[dst + j] = (float)A[r * kNull + j];
+    }
+  }
+  if (lane < kNull)
+    for (int j = 0; j < kNull; ++j) Kc[((size_t)a * kNull + lane) * kNull + j] = R[j];
+  if (lane == 0) kept_out[a] = kept;
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin product A_{l+1} = P^T A_l P (Section 2.3) on the coarse pattern; one CTA
+// per coarse row, thread (r, s) owns entry (r, s) of every block of the row.
+// ---------------------------------------------------------------------------
+constexpr int kGalBS = 256;
+template <typename T>
+__global__ void __launch_bounds__(kGalBS)
+k_galerkin(int bs, const int* __restrict__ row_ptr, const int* __restrict__ cols, const T* __restrict__ vals,
+           const T* __restrict__ Q, const int* __restrict__ agg, const int* __restrict__ mptr,
+           const int* __restrict__ mem, const int* __restrict__ crow_ptr, const int* __restrict__ ccols,
+           const unsigned* __restrict__ ckept, T* __restrict__ cvals) {
+  __shared__ T sA[16 * 16];
+  __shared__ T sQj[16 * 16];
+  __shared__ T sQi[16 * 16];
+  __shared__ T sU[16 * 16];
+  const int a = blockIdx.x;
+  const int t = threadIdx.x;
+  const int r = t >> 4, s = t & 15;
+  const int cb = crow_ptr[a], ce = crow_ptr[a + 1];
+  for (int e = cb; e < ce; ++e) cvals[(size_t)e * 256 + t] = T(0);
+  for (int k = mptr[a]; k < mptr[a + 1]; ++k) {
+    const int i = mem[k];
+    __syncthreads();
+    if (t < bs * 16) sQi[t] = Q[(size_t)i * bs * 16 + t];
+    for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int j = cols[e];
+      const int aj = agg[j];
+      // slot of aj in coarse row a
+      int lo = cb, hi = ce - 1, slot = -1;
+      while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int v = ccols[mid];
+        if (v == aj) { slot = mid; break; }
+        if (v < aj) lo = mid + 1; else hi = mid - 1;
+      }
+      __syncthreads();
+      if (t < bs * bs) sA[t] = vals[(size_t)e * bs * bs + t];
+      if (t < bs * 16) sQj[t] = Q[(size_t)j * bs * 16 + t];
+      __syncthreads();
+      if (t < bs * 16) {
+        const int u = t >> 4;
+        T acc = T(0);
+        for (int v = 0; v < bs; ++v) acc += sA[u * bs + v] * sQj[v * 16 + s];
+        sU[t] = acc;
+      }
+      __syncthreads();
+      T acc = T(0);
+      for (int u = 0; u < bs; ++u) acc += sQi[u * 16 + r] * sU[u * 16 + s];
+      if (slot >= 0) cvals[(size_t)slot * 256 + t] += acc;
+    }
+  }
+  __syncthreads();
+  // dropped coarse dofs: unit diagonal (decoupled)
+  if (r == s && !((ckept[a] >> r) & 1u)) {
+    for (int e = cb; e < ce; ++e)
+      if (ccols[e] == a) cvals[(size_t)e * 256 + t] = T(1);
+  }
+}
+
+// diagonal blocks of a BSR level as double
+template <typename T>
+__global__ void k_extract_diag(int n, int bs, const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                               const T* __restrict__ vals, double* __restrict__ D) {
+  int i = blockIdx.x;
+  int t = threadIdx.x;
+  if (t >= bs * bs) return;
+  double v = 0.0;
+  for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+    if (cols[e] == i) v = (double)vals[(size_t)e * bs * bs + t];
+  D[(size_t)i * bs * bs + t] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos helpers (D-inner product): start vector from SplitMix64, block-diagonal
+// products, recurrence updates with scalars read from device memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long i) {
+  unsigned long long z = 0x9E3779B97F4A7C15ull * (i + 1ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void k_start_vector(T* __restrict__ v, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = (T)(2.0 * ((double)(splitmix64(i) >> 11) * 0x1.0p-53) - 1.0);
+}
+
+// y = B x for block-diagonal B (double blocks), T vectors
+template <typename T>
+__global__ void k_blockdiag_apply(int n, int bs, const double* __restrict__ B, const T* __restrict__ x,
+                                  T* __restrict__ y) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * bs) return;
+  const size_t i = idx / bs;
+  const int u = (int)(idx - i * bs);
+  const double* b = B + (i * bs + u) * bs;
+  const T* xi = x + i * bs;
+  double acc = 0.0;
+  for (int v = 0; v < bs; ++v) acc += b[v] * (double)xi[v];
+  y[idx] = (T)acc;
+}
+
+// q = v / sqrt(scal[s])
+template <typename T>
+__global__ void k_scale_rsqrt(size_t n, const T* __restrict__ v, T* __restrict__ q, const double* __restrict__ scal,
+                              int s) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double f = 1.0 / sqrt(scal[s]);
+  if (i < n) q[i] = (T)((double)v[i] * f);
+}
+
+// w = Dinv Aq - alpha q - beta qprev  (Dinv applied blockwise), alpha = scal[sa], beta = scal[sb] or 0
+template <typename T>
+__global__ void k_lanczos_w(int n, int bs, const double* __restrict__ Dinv, const T* __restrict__ Aq,
+                            const T* __restrict__ q, const T* __restrict__ qprev, const double* __restrict__ scal,
+                            int sa, int sb, T* __restrict__ w) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * bs) return;
+  const size_t i = idx / bs;
+  const int u = (int)(idx - i * bs);
+  const double* b = Dinv + (i * bs + u) * bs;
+  double acc = 0.0;
+  for (int v = 0; v < bs; ++v) acc += b[v] * (double)Aq[i * bs + v];
+  const double alpha = scal[sa];
+  const double beta = sb >= 0 ? scal[sb] : 0.0;
+  acc -= alpha * (double)q[idx];
+  if (sb >= 0) acc -= beta * (double)qprev[idx];
+  w[idx] = (T)acc;
+}
+
+__global__ void k_sqrt_slot(double* scal, int src, int dst) {
+  if (threadIdx.x == 0) scal[dst] = sqrt(scal[src]);
+}
+
+// largest eigenvalue of the symmetric tridiagonal (alpha[0..m), beta[0..m-1)) by
+// bisection with Sturm counts; writes Chebyshev parameters
+__global__ void k_tridiag_lambda_max(const double* __restrict__ scal, int s_alpha, int s_beta, int m,
+                                     double lo_f, double hi_f, double* __restrict__ cheb) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double al[16], be[16];
+  int mm = m;
+  for (int j = 0; j < m; ++j) al[j] = scal[s_alpha + j];
+  for (int j = 0; j + 1 < m; ++j) {
+    be[j] = scal[s_beta + j];
+    if (!(be[j] > 0.0)) {  // invariant subspace found: truncate
+      mm = j + 1;
+      break;
+    }
+  }
+  double lo = al[0], hi = al[0];
+  for (int j = 0; j < mm; ++j) {
+    const double rad = (j > 0 ? fabs(be[j - 1]) : 0.0) + (j + 1 < mm ? fabs(be[j]) : 0.0);
+    lo = fmin(lo, al[j] - rad);
+    hi = fmax(hi, al[j] + rad);
+  }
+  // count of eigenvalues < x
+  auto count_below = [&](double x) {
+    int c = 0;
+    double d = al[0] - x;
+    if (d < 0) ++c;
+    for (int j = 1; j < mm; ++j) {
+      const double prev = (d == 0.0) ? 1e-300 : d;
+      d = (al[j] - x) - be[j - 1] * be[j - 1] / prev;
+      if (d < 0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (count_below(mid) >= mm) hi = mid;
+    else lo = mid;
+  }
+  const double lam = hi;
+  const double a = lo_f * lam, b = hi_f * lam;
+  cheb[0] = 0.5 * (b + a);          // theta
+  cheb[1] = 0.5 * (b - a);          // delta
+  cheb[2] = cheb[0] / cheb[1];      // sigma_1
+  cheb[3] = lam;
+}
+
+template <typename T>
+static void lanczos(ba_problem* P, int l) {
+  Level& L = P->levels[l];
+  const size_t n = (size_t)L.n * L.bs;
+  const int m = std::min(std::max(P->opt.lanczos_steps, 1), 8);
+  P->scratch2.ensure(sizeof(T) * n * 5 + 256);
+  T* v = P->scratch2.as<T>();
+  T* q = v + n;
+  T* qprev = q + n;
+  T* w = qprev + n;
+  T* Aq = w + n;
+  const int g = cdiv((long long)n, 256);
+  double* scal = P->scal.as<double>();
+  k_start_vector<T><<<g, 256, 0, P->stream>>>(v, n);
+  launched(P);
+  k_blockdiag_apply<T><<<g, 256, 0, P->stream>>>(L.n, L.bs, L.Dblk.as<double>(), v, w);
+  launched(P);
+  if (sizeof(T) == 8) dot64(P, (const double*)v, (const double*)w, n, S_TMP0);
+  else dot32(P, (const float*)v, (const float*)w, n, S_TMP0);
+  k_scale_rsqrt<T><<<g, 256, 0, P->stream>>>(n, v, q, scal, S_TMP0);
+  launched(P);
+  for (int j = 0; j < m; ++j) {
+    level_matvec(P, l, q, Aq);
+    if (sizeof(T) == 8) dot64(P, (const double*)q, (const double*)Aq, n, S_LANCZOS + j);
+    else dot32(P, (const float*)q, (const float*)Aq, n, S_LANCZOS + j);
+    k_lanczos_w<T><<<g, 256, 0, P->stream>>>(L.n, L.bs, L.Dinv64.as<double>(), Aq, q, qprev, scal,
+                                            S_LANCZOS + j, j > 0 ? S_LANCZOS + 8 + j - 1 : -1, w);
+    launched(P);
+    if (j == m - 1) break;
+    k_blockdiag_apply<T><<<g, 256, 0, P->stream>>>(L.n, L.bs, L.Dblk.as<double>(), w, v);
+    launched(P);
+    if (sizeof(T) == 8) dot64(P, (const double*)w, (const double*)v, n, S_TMP1);
+    else dot32(P, (const float*)w, (const float*)v, n, S_TMP1);
+    // beta_j = sqrt(w.Dw); q_prev <- q; q <- w / beta_j
+    k_scale_rsqrt<T><<<g, 256, 0, P->stream>>>(n, w, v, scal, S_TMP1);  // v = w / beta
+    launched(P);
+    std::swap(qprev, q);   // qprev = old q
+    std::swap(q, v);       // q = w / beta, v free
+    k_sqrt_slot<<<1, 1, 0, P->stream>>>(scal, S_TMP1, S_LANCZOS + 8 + j);  // beta_j
+    launched(P);
+  }
+  L.cheb.ensure(sizeof(double) * 4);
+  k_tridiag_lambda_max<<<1, 1, 0, P->stream>>>(scal, S_LANCZOS, S_LANCZOS + 8, m, P->opt.cheb_lo,
+                                               P->opt.cheb_hi, L.cheb.as<double>());
+  launched(P);
+}
+
+// ---------------------------------------------------------------------------
+// coarsest level: dense FP64 matrix from the BSR blocks, padded with identity to a
+// multiple of 32, inverted in place by blocked Gauss-Jordan (SPD, no pivoting) in a
+// cooperative kernel: per 32-wide pivot block, the pivot row/column panels are
+// copied out, the grid synchronises, every tile is updated, the grid synchronises.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_bsr_to_dense(int n, int bs, const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                               const T* __restrict__ vals, int Np, double* __restrict__ A) {
+  const int i = blockIdx.x;
+  for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+    const int j = cols[e];
+    for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {
+      const int u = t / bs, v = t - u * bs;
+      A[(size_t)(i * bs + u) * Np + j * bs + v] = (double)vals[(size_t)e * bs * bs + t];
+    }
+  }
+}
+
+__global__ void k_dense_identity_pad(int N, int Np, double* __restrict__ A) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)Np * Np) return;
+  const int i = (int)(idx / Np), j = (int)(idx % Np);
+  if (i >= N || j >= N) A[idx] = (i == j) ? 1.0 : 0.0;
+}
+
+constexpr int kGJ = 32;
+constexpr int kGJBS = 256;
+__global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* __restrict__ A, int Np, double* __restrict__ prow,
+                                                        double* __restrict__ pcol, int* flags) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double piv[kGJ][kGJ + 1];
+  __shared__ double tA[kGJ][kGJ + 1];
+  __shared__ double tB[kGJ][kGJ + 1];
+  __shared__ double tC[kGJ][kGJ + 1];
+  const int nb = Np / kGJ;
+  const int t = threadIdx.x;
+  for (int K = 0; K < nb; ++K) {
+    const int K0 = K * kGJ;
+    // copy pivot row panel (kGJ x Np) and column panel (Np x kGJ)
+    for (size_t idx = (size_t)blockIdx.x * kGJBS + t; idx < (size_t)kGJ * Np; idx += (size_t)gridDim.x * kGJBS) {
+      const int r = (int)(idx / Np), c = (int)(idx % Np);
+      prow[idx] = A[(size_t)(K0 + r) * Np + c];
+      pcol[(size_t)c * kGJ + r] = A[(size_t)c * Np + K0 + r];
+    }
+    grid.sync();
+    // every CTA inverts the pivot block (Gauss-Jordan in shared memory)
+    for (int e = t; e < kGJ * kGJ; e += kGJBS) piv[e / kGJ][e % kGJ] = prow[(size_t)(e / kGJ) * Np + K0 + e % kGJ];
+    __syncthreads();
+    bool bad = false;
+    for (int k = 0; k < kGJ; ++k) {
+      const double p = piv[k][k];
+      if (!(p > 0.0)) bad = true;
+      const double ip = 1.0 / p;
+      __syncthreads();
+      // update using old row k / column k
+      double newv[4];
+      int cnt = 0;
+      for (int e = t; e < kGJ * kGJ; e += kGJBS) {
+        const int i = e / kGJ, j = e % kGJ;
+        double v;
+        if (i == k && j == k) v = ip;
+        else if (i == k) v = piv[k][j] * ip;
+        else if (j == k) v = -piv[i][k] * ip;
+        else v = piv[i][j] - piv[i][k] * piv[k][j] * ip;
+        newv[cnt++] = v;
+      }
+      __syncthreads();
+      cnt = 0;
+      for (int e = t; e < kGJ * kGJ; e += kGJBS) piv[e / kGJ][e % kGJ] = newv[cnt++];
+      __syncthreads();
+    }
+    if (bad && blockIdx.x == 0 && t == 0) flags[F_NOT_SPD_COARSE] = 1;
+    // tiles (I, J): I, J block indices
+    for (int tile = blockIdx.x; tile < nb * nb; tile += gridDim.x) {
+      const int I = tile / nb, J = tile % nb;
+      const int I0 = I * kGJ, J0 = J * kGJ;
+      // tA = A_IK (old column panel rows I0..), tB = A_KJ (old row panel cols J0..)
+      for (int e = t; e < kGJ * kGJ; e += kGJBS) {
+        const int u = e / kGJ, v = e % kGJ;
+        tA[u][v] = pcol[(size_t)(I0 + u) * kGJ + v];
+        tB[u][v] = prow[(size_t)u * Np + J0 + v];
+      }
+      __syncthreads();
+      // tC = Pinv A_KJ
+      for (int e = t; e < kGJ * kGJ; e += kGJBS) {
+        const int u = e / kGJ, v = e % kGJ;
+        double s = 0.0;
+        for (int k = 0; k < kGJ; ++k) s += piv[u][k] * tB[k][v];
+        tC[u][v] = s;
+      }
+      __syncthreads();
+      for (int e = t; e < kGJ * kGJ; e += kGJBS) {
+        const int u = e / kGJ, v = e % kGJ;
+        double val;
+        if (I == K && J == K) {
+          val = piv[u][v];
+        } else if (I == K) {
+          val = tC[u][v];                       // Pinv A_KJ
+        } else if (J == K) {
+          double s = 0.0;                       // -A_IK Pinv
+          for (int k = 0; k < kGJ; ++k) s += tA[u][k] * piv[k][v];
+          val = -s;
+        } else {
+          double s = 0.0;                       // A_IJ - A_IK Pinv A_KJ
+          for (int k = 0; k < kGJ; ++k) s += tA[u][k] * tC[k][v];
+          val = A[(size_t)(I0 + u) * Np + J0 + v] - s;
+        }
+        A[(size_t)(I0 + u) * Np + J0 + v] = val;
+      }
+      __syncthreads();
+    }
+    grid.sync();
+  }
+}
+
+static void dense_inverse(ba_problem* P, Level& L) {
+  const int N = L.n * L.bs;
+  const int Np = (N + kGJ - 1) / kGJ * kGJ;
+  BA_REQUIRE(Np <= 16384, BA_ERR_LIMIT, "coarsest level too large for the dense solver (" + std::to_string(N) + " dofs)");
+  L.N = Np;
+  L.Ainv.ensure(sizeof(double) * (size_t)Np * Np);
+  double* A = L.Ainv.as<double>();
+  BA_CUDA(cudaMemsetAsync(A, 0, sizeof(double) * (size_t)Np * Np, P->stream));
+  if (level_fp32(P) && !L.vals32.p) throw Error(BA_ERR_STATE, "missing coarse operator");
+  if (level_fp32(P))
+    k_bsr_to_dense<float><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                      L.vals32.as<float>(), Np, A);
+  else
+    k_bsr_to_dense<double><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                       L.vals64.as<double>(), Np, A);
+  launched(P);
+  k_dense_identity_pad<<<cdiv((long long)Np * Np, 256), 256, 0, P->stream>>>(N, Np, A);
+  launched(P);
+  P->scratch.ensure(sizeof(double) * 2 * (size_t)kGJ * Np + 64);
+  double* prow = P->scratch.as<double>();
+  double* pcol = prow + (size_t)kGJ * Np;
+  int nblk = 0;
+  BA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, k_gauss_jordan, kGJBS, 0));
+  int grid = std::max(1, std::min(nblk * P->n_sm, (Np / kGJ) * (Np / kGJ)));
+  int* flags = P->flags.as<int>();
+  void* args[] = {(void*)&A, (void*)&Np, (void*)&prow, (void*)&pcol, (void*)&flags};
+  BA_CUDA(cudaLaunchCooperativeKernel((void*)k_gauss_jordan, grid, kGJBS, args, 0, P->stream));
+  launched(P);
+}
+
+// ---------------------------------------------------------------------------
+// orchestration
+// ---------------------------------------------------------------------------
+void mg_setup(ba_problem* P) {
+  const bool fp32 = level_fp32(P);
+  const ba_options& o = P->opt;
+  clear_flags(P);
+  if ((int)P->levels.size() < 1) P->levels.resize(1);
+  Level& L0 = P->levels[0];
+  covisibility_level0(P, L0);
+  L0.n = P->n_c;
+  L0.bs = 9;
+  explicit_schur(P, L0, fp32);
+  // level-0 smoother blocks: S_cc from the Schur setup
+  L0.Dblk.ensure(sizeof(double) * 81 * (size_t)P->n_c + 64);
+  L0.Dinv64.ensure(sizeof(double) * 81 * (size_t)P->n_c + 64);
+  L0.Dinv32.ensure(sizeof(float) * 81 * (size_t)P->n_c + 64);
+  BA_CUDA(cudaMemcpyAsync(L0.Dblk.p, P->Scc.p, sizeof(double) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
+  BA_CUDA(cudaMemcpyAsync(L0.Dinv64.p, P->Scc_inv.p, sizeof(double) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
+  BA_CUDA(cudaMemcpyAsync(L0.Dinv32.p, P->Scc_inv32.p, sizeof(float) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
+  L0.K.ensure(sizeof(double) * 9 * kNull * (size_t)P->n_c + 64);
+  k_nullspace0<<<cdiv(P->n_c, 128), 128, 0, P->stream>>>(P->cams_lin.as<double>(), P->n_c, L0.K.as<double>());
+  launched(P);
+  L0.kept.ensure(sizeof(unsigned) * P->n_c + 64);
+  BA_CUDA(cudaMemsetAsync(L0.kept.p, 0xff, sizeof(unsigned) * P->n_c, P->stream));
+
+  int l = 0;
+  while (true) {
+    Level& L = P->levels[l];
+    L.coarsest = false;
+    bool coarsest = L.n <= o.coarse_max_nodes || l + 1 >= o.max_levels || l + 1 >= 16;
+    if (!coarsest) {
+      // strength ordering
+      L.sptr.ensure(sizeof(int) * ((size_t)L.n + 1));
+      P->scratch.ensure(sizeof(int) * ((size_t)L.n + 1) + sizeof(long long) * (size_t)L.n + 64);
+      int* cnt = P->scratch.as<int>();
+      k_strength_count<<<cdiv(L.n, 128), 128, 0, P->stream>>>(L.n, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                              L.W.as<long long>(), cnt);
+      launched(P);
+      L.n_strength = scan(P, cnt, L.sptr.as<int>(), L.n);
+      L.sidx.ensure(sizeof(int) * (size_t)std::max(L.n_strength, 1));
+      P->scratch2.ensure(sizeof(long long) * (size_t)L.n + 64);
+      long long* Wd = P->scratch2.as<long long>();
+      k_diag_w<<<cdiv(L.n, 128), 128, 0, P->stream>>>(L.n, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                     L.W.as<long long>(), Wd);
+      launched(P);
+      // max row length for the sort buffer
+      std::vector<int> hptr(L.n + 1);
+      BA_CUDA(cudaMemcpyAsync(hptr.data(), L.row_ptr.p, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost, P->stream));
+      sync(P);
+      int maxrow = 1;
+      for (int i = 0; i < L.n; ++i) maxrow = std::max(maxrow, hptr[i + 1] - hptr[i]);
+      int mpow = 1;
+      while (mpow < maxrow) mpow <<= 1;
+      const size_t ssm = sizeof(StrengthKey) * mpow;
+      BA_REQUIRE(ssm <= 200 * 1024, BA_ERR_LIMIT, "too many covisible neighbours for the strength sort");
+      BA_CUDA(cudaFuncSetAttribute(k_strength_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
+      k_strength_order<<<L.n, kStrBS, ssm, P->stream>>>(L.n, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                        L.W.as<long long>(), Wd, L.sptr.as<int>(), L.sidx.as<int>());
+      launched(P);
+      // Algorithm 2
+      L.agg.ensure(sizeof(int) * (size_t)L.n + 64);
+      P->scratch.ensure(sizeof(int) * (2 * (size_t)L.n + 8));
+      int* gsize = P->scratch.as<int>();
+      int* d_nagg = gsize + L.n + 4;
+      const size_t asmem = sizeof(int) * 2 * (size_t)L.n;
+      if (asmem <= 160 * 1024) {
+        BA_CUDA(cudaFuncSetAttribute(k_aggregate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem));
+        k_aggregate<true><<<1, 256, asmem, P->stream>>>(L.n, L.sptr.as<int>(), L.sidx.as<int>(), o.max_agg,
+                                                        L.agg.as<int>(), gsize, d_nagg);
+      } else {
+        k_aggregate<false><<<1, 256, 0, P->stream>>>(L.n, L.sptr.as<int>(), L.sidx.as<int>(), o.max_agg,
+                                                     L.agg.as<int>(), gsize, d_nagg);
+      }
+      launched(P);
+      BA_CUDA(cudaMemcpyAsync(&L.n_agg, d_nagg, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+      sync(P);
+      if (L.n_agg >= L.n) coarsest = true;
+    }
+    if (coarsest) {
+      L.coarsest = true;
+      dense_inverse(P, L);
+      check_flags(P);
+      break;
+    }
+    // smoother for this level
+    if (l > 0) {
+      L.Dblk.ensure(sizeof(double) * L.bs * L.bs * (size_t)L.n + 64);
+      L.Dinv64.ensure(sizeof(double) * L.bs * L.bs * (size_t)L.n + 64);
+      L.Dinv32.ensure(sizeof(float) * L.bs * L.bs * (size_t)L.n + 64);
+      if (fp32)
+        k_extract_diag<float><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                          L.vals32.as<float>(), L.Dblk.as<double>());
+      else
+        k_extract_diag<double><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                           L.vals64.as<double>(), L.Dblk.as<double>());
+      launched(P);
+      block_inverse(P, L.Dblk.as<double>(), L.n, L.bs, L.Dinv64.as<double>(), L.Dinv32.as<float>(), F_NOT_SPD_JACOBI);
+    }
+    if (fp32) lanczos<float>(P, l);
+    else lanczos<double>(P, l);
+    // members of each aggregate
+    L.agg_ptr.ensure(sizeof(int) * ((size_t)L.n_agg + 1));
+    L.agg_mem.ensure(sizeof(int) * (size_t)L.n + 64);
+    P->scratch.ensure(sizeof(int) * 2 * ((size_t)L.n_agg + 1) + 64);
+    int* mc = P->scratch.as<int>();
+    int* fill = mc + L.n_agg + 1;
+    BA_CUDA(cudaMemsetAsync(mc, 0, sizeof(int) * 2 * (L.n_agg + 1), P->stream));
+    k_count_members<<<cdiv(L.n, 256), 256, 0, P->stream>>>(L.n, L.agg.as<int>(), mc);
+    launched(P);
+    scan(P, mc, L.agg_ptr.as<int>(), L.n_agg);
+    k_fill_members<<<cdiv(L.n, 256), 256, 0, P->stream>>>(L.n, L.agg.as<int>(), L.agg_ptr.as<int>(), fill,
+                                                          L.agg_mem.as<int>());
+    launched(P);
+    k_sort_members<<<cdiv(L.n_agg, 128), 128, 0, P->stream>>>(L.n_agg, L.agg_ptr.as<int>(), L.agg_mem.as<int>());
+    launched(P);
+    // next level
+    if ((int)P->levels.size() < l + 2) P->levels.resize(l + 2);
+    Level& L1 = P->levels[l + 1];
+    Level& Lc = P->levels[l];  // re-take reference after resize
+    L1.n = Lc.n_agg;
+    L1.bs = kNull;
+    // QR prolongators, coarse nullspace and kept masks
+    Lc.Q64.ensure(sizeof(double) * Lc.bs * kNull * (size_t)Lc.n + 64);
+    Lc.Q32.ensure(sizeof(float) * Lc.bs * kNull * (size_t)Lc.n + 64);
+    L1.K.ensure(sizeof(double) * kNull * kNull * (size_t)L1.n + 64);
+    L1.kept.ensure(sizeof(unsigned) * (size_t)L1.n + 64);
+    const size_t qsm = sizeof(double) * (size_t)o.max_agg * Lc.bs * kNull;
+    BA_REQUIRE(qsm <= 200 * 1024, BA_ERR_LIMIT, "max_agg too large for the aggregate QR");
+    BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
+    k_aggregate_qr<<<L1.n, 32, qsm, P->stream>>>(L1.n, Lc.bs, Lc.agg_ptr.as<int>(), Lc.agg_mem.as<int>(),
+                                                Lc.K.as<double>(), Lc.Q64.as<double>(), Lc.Q32.as<float>(),
+                                                L1.K.as<double>(), L1.kept.as<unsigned>());
+    launched(P);
+    // coarse pattern and covisibility W_{l+1} = Agg^T W_l Agg
+    const int H = hash_size(std::min(L1.n, 4096));
+    row_hash<1>(P, L1.n, H, Lc.agg_ptr.as<int>(), Lc.agg_mem.as<int>(), Lc.row_ptr.as<int>(), Lc.cols.as<int>(),
+                Lc.agg.as<int>(), Lc.W.as<long long>(), L1);
+    // Galerkin
+    if (fp32) {
+      L1.vals32.ensure(sizeof(float) * 256 * (size_t)L1.nnzb + 64);
+      k_galerkin<float><<<L1.n, kGalBS, 0, P->stream>>>(Lc.bs, Lc.row_ptr.as<int>(), Lc.cols.as<int>(),
+                                                        Lc.vals32.as<float>(), Lc.Q32.as<float>(), Lc.agg.as<int>(),
+                                                        Lc.agg_ptr.as<int>(), Lc.agg_mem.as<int>(),
+                                                        L1.row_ptr.as<int>(), L1.cols.as<int>(),
+                                                        L1.kept.as<unsigned>(), L1.vals32.as<float>());
+    } else {
+      L1.vals64.ensure(sizeof(double) * 256 * (size_t)L1.nnzb + 64);
+      k_galerkin<double><<<L1.n, kGalBS, 0, P->stream>>>(Lc.bs, Lc.row_ptr.as<int>(), Lc.cols.as<int>(),
+                                                         Lc.vals64.as<double>(), Lc.Q64.as<double>(), Lc.agg.as<int>(),
+                                                         Lc.agg_ptr.as<int>(), Lc.agg_mem.as<int>(),
+                                                         L1.row_ptr.as<int>(), L1.cols.as<int>(),
+                                                         L1.kept.as<unsigned>(), L1.vals64.as<double>());
+    }
+    launched(P);
+    check_flags(P);
+    ++l;
+  }
+  P->n_levels = l + 1;
+  // host copies of lambda_max
+  for (int k = 0; k + 1 < P->n_levels; ++k) {
+    double c[4];
+    BA_CUDA(cudaMemcpyAsync(c, P->levels[k].cheb.p, sizeof(c), cudaMemcpyDeviceToHost, P->stream));
+    sync(P);
+    P->levels[k].lam_max = c[3];
+  }
+  // V-cycle work vectors
+  for (int k = 0; k < P->n_levels; ++k) {
+    Level& L = P->levels[k];
+    const size_t n = (size_t)(L.coarsest ? L.N : L.n * L.bs) + 64;
+    const size_t es = fp32 ? sizeof(float) : sizeof(double);
+    L.vx.ensure(es * n);
+    L.vb.ensure(es * n);
+    L.vr.ensure(es * n);
+    L.vd.ensure(es * n);
+    L.vq.ensure(es * n);
+    L.vt.ensure(es * n);
+    L.vs.ensure(es * n);
+  }
+}
+
+}  // namespace ba

@@ -1,0 +1,729 @@
+// K2: Schur reduction (Section 2.1, Eq. 3-4) and K3: the implicit Schur product of
+// Section 3.6, S x = A x - F^T (E (C^-1 (E^T (F x)))), with A = F^T F + D_c.
+//
+// Per-observation arrays are SoA with leading dimension ld (18 rows of F, 6 of E);
+// per-point arrays SoA with leading dimension ldp; camera vectors are [n_c][9].
+#include <algorithm>
+
+#include "ba_internal.h"
+#include "device_util.cuh"
+
+namespace ba {
+
+// ---------------------------------------------------------------------------
+// point pass: C_p = sum E^T E + D_p, C_p^-1, g_p = -sum E^T f, w_p = C_p^-1 g_p
+// ---------------------------------------------------------------------------
+__global__ void k_point_setup(const double* __restrict__ E, const double* __restrict__ fres,
+                              size_t ld, const int* __restrict__ pt_ptr, int n_p, int n_p_obs,
+                              size_t ldp, double lambda, int damp_identity, double* __restrict__ Dp,
+                              double* __restrict__ Cinv, float* __restrict__ Cinv32,
+                              double* __restrict__ gp, double* __restrict__ wp, int* flags) {
+  int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= n_p) return;
+  double c00 = 0, c01 = 0, c02 = 0, c11 = 0, c12 = 0, c22 = 0, g0 = 0, g1 = 0, g2 = 0;
+  const int b = pt_ptr[ip], e = pt_ptr[ip + 1];
+  for (int o = b; o < e; ++o) {
+    const double a0 = E[o], a1 = E[ld + o], a2 = E[2 * ld + o];
+    const double b0 = E[3 * ld + o], b1 = E[4 * ld + o], b2 = E[5 * ld + o];
+    const double f0 = fres[o], f1 = fres[ld + o];
+    c00 += a0 * a0 + b0 * b0;
+    c01 += a0 * a1 + b0 * b1;
+    c02 += a0 * a2 + b0 * b2;
+    c11 += a1 * a1 + b1 * b1;
+    c12 += a1 * a2 + b1 * b2;
+    c22 += a2 * a2 + b2 * b2;
+    g0 -= a0 * f0 + b0 * f1;
+    g1 -= a1 * f0 + b1 * f1;
+    g2 -= a2 * f0 + b2 * f1;
+  }
+  double d0, d1, d2;
+  if (damp_identity) {
+    d0 = d1 = d2 = lambda;
+  } else {
+    d0 = lambda * fmax(c00, 1e-6);
+    d1 = lambda * fmax(c11, 1e-6);
+    d2 = lambda * fmax(c22, 1e-6);
+  }
+  Dp[ip] = d0;
+  Dp[ldp + ip] = d1;
+  Dp[2 * ldp + ip] = d2;
+  gp[ip] = g0;
+  gp[ldp + ip] = g1;
+  gp[2 * ldp + ip] = g2;
+  double inv[6] = {0, 0, 0, 0, 0, 0};
+  if (ip < n_p_obs) {
+    double a[9] = {c00 + d0, c01, c02, c01, c11 + d1, c12, c02, c12, c22 + d2};
+    if (!spd_inverse<3>(a, 3)) {
+      flags[F_NOT_SPD_POINT] = 1;
+    } else {
+      inv[0] = a[0]; inv[1] = a[1]; inv[2] = a[2]; inv[3] = a[4]; inv[4] = a[5]; inv[5] = a[8];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    Cinv[k * ldp + ip] = inv[k];
+    if (Cinv32) Cinv32[k * ldp + ip] = (float)inv[k];
+  }
+  wp[ip] = inv[0] * g0 + inv[1] * g1 + inv[2] * g2;
+  wp[ldp + ip] = inv[1] * g0 + inv[3] * g1 + inv[4] * g2;
+  wp[2 * ldp + ip] = inv[2] * g0 + inv[4] * g1 + inv[5] * g2;
+}
+
+// ---------------------------------------------------------------------------
+// camera pass (warp per camera): D_c, g_c = -F^T f, b_c = g_c - sum F^T E w_p
+// ---------------------------------------------------------------------------
+__global__ void k_camera_setup(const double* __restrict__ F, const double* __restrict__ E,
+                               const double* __restrict__ fres, size_t ld,
+                               const int* __restrict__ cam_ptr, const int* __restrict__ cam_obs,
+                               const int* __restrict__ obs_pt, const double* __restrict__ wp,
+                               size_t ldp, int n_c, double lambda, int damp_identity,
+                               double* __restrict__ Dc, float* __restrict__ Dc32,
+                               double* __restrict__ gc, double* __restrict__ rhs) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= n_c) return;
+  double dg[9], g[9], bb[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) dg[k] = g[k] = bb[k] = 0.0;
+  for (int i = cam_ptr[c] + lane; i < cam_ptr[c + 1]; i += 32) {
+    const int o = cam_obs[i];
+    const int ip = obs_pt[o];
+    const double f0 = fres[o], f1 = fres[ld + o];
+    const double w0 = wp[ip], w1 = wp[ldp + ip], w2 = wp[2 * ldp + ip];
+    const double h0 = f0 + E[o] * w0 + E[ld + o] * w1 + E[2 * ld + o] * w2;
+    const double h1 = f1 + E[3 * ld + o] * w0 + E[4 * ld + o] * w1 + E[5 * ld + o] * w2;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double a = F[k * ld + o], b = F[(9 + k) * ld + o];
+      dg[k] += a * a + b * b;
+      g[k] -= a * f0 + b * f1;
+      bb[k] -= a * h0 + b * h1;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    dg[k] = warp_sum(dg[k]);
+    g[k] = warp_sum(g[k]);
+    bb[k] = warp_sum(bb[k]);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double d = damp_identity ? lambda : lambda * fmax(dg[k], 1e-6);
+      Dc[9 * c + k] = d;
+      Dc32[9 * c + k] = (float)d;
+      gc[9 * c + k] = g[k];
+      rhs[9 * c + k] = bb[k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// S_cc = D_c + sum_{o in c} F_o^T (I - E_o C_p^-1 E_o^T) F_o   (warp per camera)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_scc(const T* __restrict__ F, const T* __restrict__ E, size_t ld,
+                      const T* __restrict__ Cinv, size_t ldp, const int* __restrict__ cam_ptr,
+                      const int* __restrict__ cam_obs, const int* __restrict__ obs_pt,
+                      const double* __restrict__ Dc, int n_c, double* __restrict__ Scc) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= n_c) return;
+  T acc[45];
+#pragma unroll
+  for (int k = 0; k < 45; ++k) acc[k] = 0;
+  for (int i = cam_ptr[c] + lane; i < cam_ptr[c + 1]; i += 32) {
+    const int o = cam_obs[i];
+    const int ip = obs_pt[o];
+    T e[6], ci[6], f[18];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) e[k] = E[k * ld + o];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ci[k] = Cinv[k * ldp + ip];
+#pragma unroll
+    for (int k = 0; k < 18; ++k) f[k] = F[k * ld + o];
+    // Y = E C^-1 (2x3)
+    T y0[3], y1[3];
+    y0[0] = e[0] * ci[0] + e[1] * ci[1] + e[2] * ci[2];
+    y0[1] = e[0] * ci[1] + e[1] * ci[3] + e[2] * ci[4];
+    y0[2] = e[0] * ci[2] + e[1] * ci[4] + e[2] * ci[5];
+    y1[0] = e[3] * ci[0] + e[4] * ci[1] + e[5] * ci[2];
+    y1[1] = e[3] * ci[1] + e[4] * ci[3] + e[5] * ci[4];
+    y1[2] = e[3] * ci[2] + e[4] * ci[4] + e[5] * ci[5];
+    // N = I - Y E^T (2x2, symmetric)
+    const T n00 = T(1) - (y0[0] * e[0] + y0[1] * e[1] + y0[2] * e[2]);
+    const T n01 = -(y0[0] * e[3] + y0[1] * e[4] + y0[2] * e[5]);
+    const T n11 = T(1) - (y1[0] * e[3] + y1[1] * e[4] + y1[2] * e[5]);
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const T ga0 = f[a] * n00 + f[9 + a] * n01;
+      const T ga1 = f[a] * n01 + f[9 + a] * n11;
+#pragma unroll
+      for (int b = a; b < 9; ++b) acc[t++] += ga0 * f[b] + ga1 * f[9 + b];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 45; ++k) acc[k] = warp_sum(acc[k]);
+  if (lane == 0) {
+    double* out = Scc + 81 * (size_t)c;
+    int t = 0;
+    for (int a = 0; a < 9; ++a)
+      for (int b = a; b < 9; ++b) {
+        double v = (double)acc[t++];
+        if (a == b) v += Dc[9 * c + a];
+        out[9 * a + b] = v;
+        out[9 * b + a] = v;
+      }
+  }
+}
+
+// inverse of SPD blocks: in [n][BS*BS] -> out64 (and out32)
+template <int BS>
+__global__ void k_block_inverse(const double* __restrict__ in, int n, double* __restrict__ out64,
+                                float* __restrict__ out32, int* flags, int flag_slot) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a[BS * BS];
+  for (int k = 0; k < BS * BS; ++k) a[k] = in[(size_t)BS * BS * i + k];
+  if (!spd_inverse<BS>(a, BS)) {
+    flags[flag_slot] = 1;
+    for (int k = 0; k < BS * BS; ++k) a[k] = 0.0;
+  }
+  for (int k = 0; k < BS * BS; ++k) {
+    out64[(size_t)BS * BS * i + k] = a[k];
+    if (out32) out32[(size_t)BS * BS * i + k] = (float)a[k];
+  }
+}
+
+void block_inverse(ba_problem* P, const double* in, int n, int bs, double* out64, float* out32,
+                   int flag_slot) {
+  if (n == 0) return;
+  if (bs == 9)
+    k_block_inverse<9><<<cdiv(n, 64), 64, 0, P->stream>>>(in, n, out64, out32, P->flags.as<int>(), flag_slot);
+  else
+    k_block_inverse<16><<<cdiv(n, 64), 64, 0, P->stream>>>(in, n, out64, out32, P->flags.as<int>(), flag_slot);
+  launched(P);
+}
+
+void schur_setup(ba_problem* P, double lambda) {
+  const bool mixed = P->opt.precision == BA_MIXED;
+  const int n_c = P->n_c, n_p = P->n_p;
+  const size_t ldp = P->ldp;
+  P->lambda = lambda;
+  P->Dc.ensure(sizeof(double) * 9 * n_c + 64);
+  P->Dc32.ensure(sizeof(float) * 9 * n_c + 64);
+  P->Dp.ensure(sizeof(double) * 3 * ldp);
+  P->Cinv64.ensure(sizeof(double) * 6 * ldp);
+  if (mixed) P->Cinv32.ensure(sizeof(float) * 6 * ldp);
+  P->gc.ensure(sizeof(double) * 9 * n_c + 64);
+  P->gp.ensure(sizeof(double) * 3 * ldp);
+  P->wp.ensure(sizeof(double) * 3 * ldp);
+  P->rhs.ensure(sizeof(double) * 9 * n_c + 64);
+  P->Scc.ensure(sizeof(double) * 81 * n_c + 64);
+  P->Scc_inv.ensure(sizeof(double) * 81 * n_c + 64);
+  P->Scc_inv32.ensure(sizeof(float) * 81 * n_c + 64);
+  clear_flags(P);
+  const int damp_id = P->opt.damping == BA_DAMP_IDENTITY;
+  if (n_p) {
+    k_point_setup<<<cdiv(n_p, 128), 128, 0, P->stream>>>(
+        P->E64.as<double>(), P->fres.as<double>(), P->ld, P->pt_ptr.as<int>(), n_p, P->n_p_obs, ldp,
+        lambda, damp_id, P->Dp.as<double>(), P->Cinv64.as<double>(),
+        mixed ? P->Cinv32.as<float>() : nullptr, P->gp.as<double>(), P->wp.as<double>(),
+        P->flags.as<int>());
+    launched(P);
+  }
+  k_camera_setup<<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
+      P->F64.as<double>(), P->E64.as<double>(), P->fres.as<double>(), P->ld, P->cam_ptr.as<int>(),
+      P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->wp.as<double>(), ldp, n_c, lambda, damp_id,
+      P->Dc.as<double>(), P->Dc32.as<float>(), P->gc.as<double>(), P->rhs.as<double>());
+  launched(P);
+  // point-block-Jacobi blocks S_cc (in the mode's storage precision) and FP64 inverses
+  double* Scc = P->Scc.as<double>();
+  if (mixed)
+    k_scc<float><<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
+        P->F32.as<float>(), P->E32.as<float>(), P->ld, P->Cinv32.as<float>(), ldp, P->cam_ptr.as<int>(),
+        P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->Dc.as<double>(), n_c, Scc);
+  else
+    k_scc<double><<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
+        P->F64.as<double>(), P->E64.as<double>(), P->ld, P->Cinv64.as<double>(), ldp,
+        P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->Dc.as<double>(), n_c, Scc);
+  launched(P);
+  block_inverse(P, Scc, n_c, 9, P->Scc_inv.as<double>(), P->Scc_inv32.as<float>(), F_NOT_SPD_JACOBI);
+  check_flags(P);
+}
+
+// ---------------------------------------------------------------------------
+// K3: implicit Schur product.  One CTA per chunk of consecutive warp tiles; a warp
+// tile is a run of whole points with <= 32 observations (a point with more is a
+// tile of its own and is processed in 32-observation passes).  Lane l of a warp
+// handles observation ob + l:
+//   u_o = F_o x_c ; t_o = E_o^T u_o ; v_p = sum_{o in p} t_o (segmented warp scan)
+//   z_p = C_p^-1 v_p ; w_o = u_o - E_o z_p ; y_c += F_o^T w_o
+// The camera sums y_c go to a shared-memory window of the chunk's cameras
+// (points are ordered by their first camera, so a chunk touches a narrow camera
+// range) and are flushed once per CTA; cameras outside the window go straight to
+// global memory.  y must hold D_c x on entry.
+// ---------------------------------------------------------------------------
+constexpr int kK3Warps = 8;
+
+template <typename T>
+__device__ __forceinline__ void k3_scatter(T* acc, T* __restrict__ y, int c, int cam_lo, int span,
+                                           const T yv[9]) {
+  const int rel = c - cam_lo;
+  if (rel < span) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) atomicAdd(acc + 9 * rel + k, yv[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) atomicAdd(y + 9 * (size_t)c + k, yv[k]);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kK3Warps * 32)
+k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, size_t ld,
+               const T* __restrict__ Cinv, size_t ldp, const int* __restrict__ obs_cam,
+               const int* __restrict__ pt_ptr, const int* __restrict__ tile_pt,
+               const int* __restrict__ chunk_tile, const int* __restrict__ chunk_cam,
+               const T* __restrict__ x, T* __restrict__ y, int win) {
+  extern __shared__ __align__(16) unsigned char k3_smem[];
+  T* acc = reinterpret_cast<T*>(k3_smem);
+  const int chunk = blockIdx.x;
+  const int cam_lo = chunk_cam[2 * chunk];
+  const int cam_hi = chunk_cam[2 * chunk + 1];
+  const int span = min(cam_hi - cam_lo + 1, win);
+  for (int i = threadIdx.x; i < span * 9; i += blockDim.x) acc[i] = T(0);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t_end = chunk_tile[chunk + 1];
+  for (int t = chunk_tile[chunk] + warp; t < t_end; t += kK3Warps) {
+    const int p0 = tile_pt[t], p1 = tile_pt[t + 1];
+    const int ob = pt_ptr[p0];
+    const int nobs = pt_ptr[p1] - ob;
+    if (nobs <= 32) {
+      const int np = p1 - p0;
+      const int sj = (lane < np) ? (pt_ptr[p0 + lane] - ob) : 0;
+      const unsigned startmask = __reduce_or_sync(kFull, (lane < np) ? (1u << sj) : 0u);
+      const bool active = lane < nobs;
+      const unsigned le = (lane == 31) ? kFull : ((2u << lane) - 1u);
+      const int seg_head = 31 - __clz(startmask & le);
+      const unsigned after = startmask & ~le;
+      const int seg_end = active ? (after ? (__ffs(after) - 2) : (nobs - 1)) : lane;
+      const int ip = p0 + __popc(startmask & le) - 1;
+      const int o = ob + lane;
+      T f[18], e[6];
+      T u0 = T(0), u1 = T(0);
+      int c = 0;
+      if (active) {
+        c = obs_cam[o];
+#pragma unroll
+        for (int k = 0; k < 18; ++k) f[k] = F[k * ld + o];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) e[k] = E[k * ld + o];
+        const T* xc = x + 9 * (size_t)c;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          const T xv = xc[k];
+          u0 += f[k] * xv;
+          u1 += f[9 + k] * xv;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 18; ++k) f[k] = T(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) e[k] = T(0);
+      }
+      T s0 = e[0] * u0 + e[3] * u1;
+      T s1 = e[1] * u0 + e[4] * u1;
+      T s2 = e[2] * u0 + e[5] * u1;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const T a0 = __shfl_down_sync(kFull, s0, d);
+        const T a1 = __shfl_down_sync(kFull, s1, d);
+        const T a2 = __shfl_down_sync(kFull, s2, d);
+        if (lane + d <= seg_end) {
+          s0 += a0;
+          s1 += a1;
+          s2 += a2;
+        }
+      }
+      const T v0 = __shfl_sync(kFull, s0, seg_head);
+      const T v1 = __shfl_sync(kFull, s1, seg_head);
+      const T v2 = __shfl_sync(kFull, s2, seg_head);
+      if (active) {
+        const T c00 = Cinv[ip], c01 = Cinv[ldp + ip], c02 = Cinv[2 * ldp + ip];
+        const T c11 = Cinv[3 * ldp + ip], c12 = Cinv[4 * ldp + ip], c22 = Cinv[5 * ldp + ip];
+        const T z0 = c00 * v0 + c01 * v1 + c02 * v2;
+        const T z1 = c01 * v0 + c11 * v1 + c12 * v2;
+        const T z2 = c02 * v0 + c12 * v1 + c22 * v2;
+        const T w0 = u0 - (e[0] * z0 + e[1] * z1 + e[2] * z2);
+        const T w1 = u1 - (e[3] * z0 + e[4] * z1 + e[5] * z2);
+        T yv[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) yv[k] = f[k] * w0 + f[9 + k] * w1;
+        k3_scatter(acc, y, c, cam_lo, span, yv);
+      }
+    } else {
+      // one point with more than 32 observations
+      const int ip = p0;
+      T s0 = T(0), s1 = T(0), s2 = T(0);
+      for (int base = 0; base < nobs; base += 32) {
+        const int o = ob + base + lane;
+        if (base + lane < nobs) {
+          const int c = obs_cam[o];
+          const T* xc = x + 9 * (size_t)c;
+          T u0 = T(0), u1 = T(0);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            u0 += F[k * ld + o] * xc[k];
+            u1 += F[(9 + k) * ld + o] * xc[k];
+          }
+          s0 += E[o] * u0 + E[3 * ld + o] * u1;
+          s1 += E[ld + o] * u0 + E[4 * ld + o] * u1;
+          s2 += E[2 * ld + o] * u0 + E[5 * ld + o] * u1;
+        }
+      }
+      s0 = warp_sum(s0);
+      s1 = warp_sum(s1);
+      s2 = warp_sum(s2);
+      const T c00 = Cinv[ip], c01 = Cinv[ldp + ip], c02 = Cinv[2 * ldp + ip];
+      const T c11 = Cinv[3 * ldp + ip], c12 = Cinv[4 * ldp + ip], c22 = Cinv[5 * ldp + ip];
+      const T z0 = c00 * s0 + c01 * s1 + c02 * s2;
+      const T z1 = c01 * s0 + c11 * s1 + c12 * s2;
+      const T z2 = c02 * s0 + c12 * s1 + c22 * s2;
+      for (int base = 0; base < nobs; base += 32) {
+        const int o = ob + base + lane;
+        if (base + lane < nobs) {
+          const int c = obs_cam[o];
+          const T* xc = x + 9 * (size_t)c;
+          T f[18];
+#pragma unroll
+          for (int k = 0; k < 18; ++k) f[k] = F[k * ld + o];
+          T u0 = T(0), u1 = T(0);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            u0 += f[k] * xc[k];
+            u1 += f[9 + k] * xc[k];
+          }
+          const T w0 = u0 - (E[o] * z0 + E[ld + o] * z1 + E[2 * ld + o] * z2);
+          const T w1 = u1 - (E[3 * ld + o] * z0 + E[4 * ld + o] * z1 + E[5 * ld + o] * z2);
+          T yv[9];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) yv[k] = f[k] * w0 + f[9 + k] * w1;
+          k3_scatter(acc, y, c, cam_lo, span, yv);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  T* yb = y + 9 * (size_t)cam_lo;
+  for (int i = threadIdx.x; i < span * 9; i += blockDim.x) {
+    const T v = acc[i];
+    if (v != T(0)) atomicAdd(yb + i, v);
+  }
+}
+
+template <typename TD, typename T>
+__global__ void k_diag_init(const TD* __restrict__ Dc, const T* __restrict__ x, T* __restrict__ y, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (T)Dc[i] * x[i];
+}
+
+template <typename T>
+static void launch_matvec(ba_problem* P, const T* F, const T* E, const T* Cinv, const T* x, T* y) {
+  if (P->n_chunks == 0) return;
+  const size_t smem = sizeof(T) * 9 * (size_t)P->k3_window;
+  static bool attr_set[2] = {false, false};
+  const int which = sizeof(T) == 8;
+  if (!attr_set[which]) {
+    BA_CUDA(cudaFuncSetAttribute(k_schur_matvec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(T) * 9 * 1024)));
+    attr_set[which] = true;
+  }
+  KernelTimer kt(P, sizeof(T) == 8 ? BA_KT_SCHUR_FP64 : BA_KT_SCHUR_FP32);
+  k_schur_matvec<T><<<P->n_chunks, kK3Warps * 32, smem, P->stream>>>(
+      F, E, P->ld, Cinv, P->ldp, P->obs_cam.as<int>(), P->pt_ptr.as<int>(), P->tile_pt.as<int>(),
+      P->chunk_tile.as<int>(), P->chunk_cam.as<int>(), x, y, P->k3_window);
+  launched(P);
+}
+
+void matvec64(ba_problem* P, const double* x, double* y) {
+  const int n = 9 * P->n_c;
+  k_diag_init<double, double><<<cdiv(n, 256), 256, 0, P->stream>>>(P->Dc.as<double>(), x, y, n);
+  launched(P);
+  launch_matvec<double>(P, P->F64.as<double>(), P->E64.as<double>(), P->Cinv64.as<double>(), x, y);
+}
+
+void matvec32(ba_problem* P, const float* x, float* y) {
+  const int n = 9 * P->n_c;
+  k_diag_init<float, float><<<cdiv(n, 256), 256, 0, P->stream>>>(P->Dc32.as<float>(), x, y, n);
+  launched(P);
+  launch_matvec<float>(P, P->F32.as<float>(), P->E32.as<float>(), P->Cinv32.as<float>(), x, y);
+}
+
+// ---------------------------------------------------------------------------
+// explicit level-0 operator blocks S_cc' (for the Galerkin product), one CTA per
+// camera row.  For every observation o = (c, p) of the row, in order, the
+// contributions -F_o^T (E_o C_p^-1 E_o'^T - [o' == o] I) F_o' of all o' in p are
+// added to the row's blocks in shared memory; within one o all o' belong to
+// different cameras, so each (block, entry) has a single writer per step.
+// ---------------------------------------------------------------------------
+constexpr int kExBS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kExBS)
+k_explicit_schur(const T* __restrict__ F, const T* __restrict__ E, size_t ld,
+                 const T* __restrict__ Cinv, size_t ldp, const int* __restrict__ cam_ptr,
+                 const int* __restrict__ cam_obs, const int* __restrict__ obs_pt,
+                 const int* __restrict__ obs_cam, const int* __restrict__ pt_ptr,
+                 const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                 const double* __restrict__ Dc, int slot_base_cap, T* __restrict__ vals) {
+  extern __shared__ __align__(16) unsigned char ex_smem[];
+  const int c = blockIdx.x;
+  const int rb = row_ptr[c], re = row_ptr[c + 1];
+  const int nslots = re - rb;
+  // shared layout: acc [cap][81] T | cols [cap] int | per-o' staging
+  T* acc = reinterpret_cast<T*>(ex_smem);
+  const int cap = slot_base_cap;
+  int* scol = reinterpret_cast<int*>(acc + (size_t)cap * 81);
+  T* sF = reinterpret_cast<T*>(scol + cap + (cap & 1));     // [32][18] F_o'
+  T* sM = sF + 32 * 18;                                       // [32][4]  M_o'
+  int* sslot = reinterpret_cast<int*>(sM + 32 * 4);          // [32]
+  T* sFo = reinterpret_cast<T*>(sslot + 32);                  // [18]
+  for (int pass_base = 0; pass_base < nslots; pass_base += cap) {
+    const int pass_n = min(cap, nslots - pass_base);
+    for (int i = threadIdx.x; i < pass_n * 81; i += kExBS) acc[i] = T(0);
+    for (int i = threadIdx.x; i < pass_n; i += kExBS) scol[i] = cols[rb + pass_base + i];
+    __syncthreads();
+    for (int k = cam_ptr[c]; k < cam_ptr[c + 1]; ++k) {
+      const int o = cam_obs[k];
+      const int ip = obs_pt[o];
+      const int ob = pt_ptr[ip], np = pt_ptr[ip + 1] - ob;
+      for (int jb = 0; jb < np; jb += 32) {
+        const int nj = min(32, np - jb);
+        if (threadIdx.x < 32) {
+          const int j = threadIdx.x;
+          // Y = E_o C_p^-1, computed redundantly per lane (cheap)
+          const T ci0 = Cinv[ip], ci1 = Cinv[ldp + ip], ci2 = Cinv[2 * ldp + ip];
+          const T ci3 = Cinv[3 * ldp + ip], ci4 = Cinv[4 * ldp + ip], ci5 = Cinv[5 * ldp + ip];
+          const T e0 = E[o], e1 = E[ld + o], e2 = E[2 * ld + o];
+          const T e3 = E[3 * ld + o], e4 = E[4 * ld + o], e5 = E[5 * ld + o];
+          const T y00 = e0 * ci0 + e1 * ci1 + e2 * ci2, y01 = e0 * ci1 + e1 * ci3 + e2 * ci4,
+                  y02 = e0 * ci2 + e1 * ci4 + e2 * ci5;
+          const T y10 = e3 * ci0 + e4 * ci1 + e5 * ci2, y11 = e3 * ci1 + e4 * ci3 + e5 * ci4,
+                  y12 = e3 * ci2 + e4 * ci4 + e5 * ci5;
+          if (j < nj) {
+            const int o2 = ob + jb + j;
+            const int c2 = obs_cam[o2];
+            const T a0 = E[o2], a1 = E[ld + o2], a2 = E[2 * ld + o2];
+            const T b0 = E[3 * ld + o2], b1 = E[4 * ld + o2], b2 = E[5 * ld + o2];
+            T m00 = y00 * a0 + y01 * a1 + y02 * a2;
+            T m01 = y00 * b0 + y01 * b1 + y02 * b2;
+            T m10 = y10 * a0 + y11 * a1 + y12 * a2;
+            T m11 = y10 * b0 + y11 * b1 + y12 * b2;
+            if (o2 == o) {
+              m00 -= T(1);
+              m11 -= T(1);
+            }
+            sM[4 * j + 0] = m00;
+            sM[4 * j + 1] = m01;
+            sM[4 * j + 2] = m10;
+            sM[4 * j + 3] = m11;
+#pragma unroll
+            for (int q = 0; q < 18; ++q) sF[18 * j + q] = F[q * ld + o2];
+            // slot of camera c2 in this pass (binary search), -1 if outside
+            int lo = 0, hi = pass_n - 1, s = -1;
+            while (lo <= hi) {
+              const int mid = (lo + hi) >> 1;
+              const int v = scol[mid];
+              if (v == c2) { s = mid; break; }
+              if (v < c2) lo = mid + 1; else hi = mid - 1;
+            }
+            sslot[j] = s;
+          }
+          if (j < 18) sFo[j] = F[j * ld + o];
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < nj * 81; it += kExBS) {
+          const int j = it / 81, e = it - 81 * j;
+          const int s = sslot[j];
+          if (s < 0) continue;
+          const int a = e / 9, b = e - 9 * a;
+          const T* M = sM + 4 * j;
+          const T g0 = sFo[a] * M[0] + sFo[9 + a] * M[2];
+          const T g1 = sFo[a] * M[1] + sFo[9 + a] * M[3];
+          acc[81 * s + e] -= g0 * sF[18 * j + b] + g1 * sF[18 * j + 9 + b];
+        }
+        __syncthreads();
+      }
+    }
+    // add D_c on the diagonal block and write out
+    for (int i = threadIdx.x; i < pass_n * 81; i += kExBS) {
+      const int s = i / 81, e = i - 81 * s;
+      T v = acc[i];
+      const int a = e / 9, b = e - 9 * a;
+      if (scol[s] == c && a == b) v += (T)Dc[9 * c + a];
+      vals[(size_t)(rb + pass_base + s) * 81 + e] = v;
+    }
+    __syncthreads();
+  }
+}
+
+void explicit_schur(ba_problem* P, Level& L0, bool fp32) {
+  const int cap = fp32 ? 256 : 128;
+  const size_t elem = fp32 ? 4 : 8;
+  size_t smem = elem * 81 * cap + sizeof(int) * (cap + 2) + elem * (32 * 18 + 32 * 4) +
+                sizeof(int) * 32 + elem * 18 + 64;
+  static bool attr[2] = {false, false};
+  if (!attr[fp32]) {
+    if (fp32)
+      BA_CUDA(cudaFuncSetAttribute(k_explicit_schur<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    else
+      BA_CUDA(cudaFuncSetAttribute(k_explicit_schur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr[fp32] = true;
+  }
+  if (fp32) {
+    L0.vals32.ensure(sizeof(float) * 81 * (size_t)L0.nnzb + 64);
+    k_explicit_schur<float><<<P->n_c, kExBS, smem, P->stream>>>(
+        P->F32.as<float>(), P->E32.as<float>(), P->ld, P->Cinv32.as<float>(), P->ldp, P->cam_ptr.as<int>(),
+        P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(), P->pt_ptr.as<int>(),
+        L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Dc.as<double>(), cap, L0.vals32.as<float>());
+  } else {
+    L0.vals64.ensure(sizeof(double) * 81 * (size_t)L0.nnzb + 64);
+    k_explicit_schur<double><<<P->n_c, kExBS, smem, P->stream>>>(
+        P->F64.as<double>(), P->E64.as<double>(), P->ld, P->Cinv64.as<double>(), P->ldp,
+        P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
+        P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Dc.as<double>(), cap,
+        L0.vals64.as<double>());
+  }
+  launched(P);
+}
+
+// ---------------------------------------------------------------------------
+// back-substitution delta_p = C_p^-1 (v_p - sum_{o in p} E_o^T F_o delta_c)
+// (v_p = g_p, or a caller vector for the adjoint); writes the internal SoA layout
+// and, if out_user is given, the caller's [n_p][3] layout.
+// ---------------------------------------------------------------------------
+__global__ void k_back_substitute(const double* __restrict__ F, const double* __restrict__ E, size_t ld,
+                                  const double* __restrict__ Cinv, size_t ldp,
+                                  const int* __restrict__ pt_ptr, const int* __restrict__ obs_cam,
+                                  const int* __restrict__ pt_user, const double* __restrict__ vp,
+                                  int vp_user, const double* __restrict__ dc, int n_p,
+                                  double* __restrict__ out_int, double* __restrict__ out_user) {
+  int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= n_p) return;
+  const int pu = pt_user[ip];
+  double h0, h1, h2;
+  if (vp_user) {
+    h0 = vp[3 * pu];
+    h1 = vp[3 * pu + 1];
+    h2 = vp[3 * pu + 2];
+  } else {
+    h0 = vp[ip];
+    h1 = vp[ldp + ip];
+    h2 = vp[2 * ldp + ip];
+  }
+  for (int o = pt_ptr[ip]; o < pt_ptr[ip + 1]; ++o) {
+    const double* x = dc + 9 * (size_t)obs_cam[o];
+    double u0 = 0, u1 = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      u0 += F[k * ld + o] * x[k];
+      u1 += F[(9 + k) * ld + o] * x[k];
+    }
+    h0 -= E[o] * u0 + E[3 * ld + o] * u1;
+    h1 -= E[ld + o] * u0 + E[4 * ld + o] * u1;
+    h2 -= E[2 * ld + o] * u0 + E[5 * ld + o] * u1;
+  }
+  const double c00 = Cinv[ip], c01 = Cinv[ldp + ip], c02 = Cinv[2 * ldp + ip];
+  const double c11 = Cinv[3 * ldp + ip], c12 = Cinv[4 * ldp + ip], c22 = Cinv[5 * ldp + ip];
+  const double d0 = c00 * h0 + c01 * h1 + c02 * h2;
+  const double d1 = c01 * h0 + c11 * h1 + c12 * h2;
+  const double d2 = c02 * h0 + c12 * h1 + c22 * h2;
+  if (out_int) {
+    out_int[ip] = d0;
+    out_int[ldp + ip] = d1;
+    out_int[2 * ldp + ip] = d2;
+  }
+  if (out_user) {
+    out_user[3 * pu] = d0;
+    out_user[3 * pu + 1] = d1;
+    out_user[3 * pu + 2] = d2;
+  }
+}
+
+void back_substitute_to(ba_problem* P, const double* dc, double* out_int, double* out_user) {
+  if (P->n_p == 0) return;
+  k_back_substitute<<<cdiv(P->n_p, 128), 128, 0, P->stream>>>(
+      P->F64.as<double>(), P->E64.as<double>(), P->ld, P->Cinv64.as<double>(), P->ldp,
+      P->pt_ptr.as<int>(), P->obs_cam.as<int>(), P->pt_user.as<int>(), P->gp.as<double>(), 0, dc,
+      P->n_p, out_int, out_user);
+  launched(P);
+}
+
+void back_substitute_general(ba_problem* P, const double* vp_user, const double* dc, double* out_int,
+                             double* out_user) {
+  if (P->n_p == 0) return;
+  k_back_substitute<<<cdiv(P->n_p, 128), 128, 0, P->stream>>>(
+      P->F64.as<double>(), P->E64.as<double>(), P->ld, P->Cinv64.as<double>(), P->ldp,
+      P->pt_ptr.as<int>(), P->obs_cam.as<int>(), P->pt_user.as<int>(), vp_user, 1, dc, P->n_p,
+      out_int, out_user);
+  launched(P);
+}
+
+// reduced RHS for a general right-hand side: out_c = v_c - sum_o F_o^T E_o C_p^-1 v_p
+__global__ void k_point_cinv_apply(const double* __restrict__ Cinv, size_t ldp, const int* __restrict__ pt_user,
+                                   const double* __restrict__ vp_user, int n_p, double* __restrict__ wp) {
+  int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= n_p) return;
+  const int pu = pt_user[ip];
+  const double h0 = vp_user[3 * pu], h1 = vp_user[3 * pu + 1], h2 = vp_user[3 * pu + 2];
+  const double c00 = Cinv[ip], c01 = Cinv[ldp + ip], c02 = Cinv[2 * ldp + ip];
+  const double c11 = Cinv[3 * ldp + ip], c12 = Cinv[4 * ldp + ip], c22 = Cinv[5 * ldp + ip];
+  wp[ip] = c00 * h0 + c01 * h1 + c02 * h2;
+  wp[ldp + ip] = c01 * h0 + c11 * h1 + c12 * h2;
+  wp[2 * ldp + ip] = c02 * h0 + c12 * h1 + c22 * h2;
+}
+
+__global__ void k_camera_reduce_rhs(const double* __restrict__ F, const double* __restrict__ E, size_t ld,
+                                    const int* __restrict__ cam_ptr, const int* __restrict__ cam_obs,
+                                    const int* __restrict__ obs_pt, const double* __restrict__ wp,
+                                    size_t ldp, const double* __restrict__ vc, int n_c,
+                                    double* __restrict__ out) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= n_c) return;
+  double bb[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) bb[k] = 0.0;
+  for (int i = cam_ptr[c] + lane; i < cam_ptr[c + 1]; i += 32) {
+    const int o = cam_obs[i];
+    const int ip = obs_pt[o];
+    const double w0 = wp[ip], w1 = wp[ldp + ip], w2 = wp[2 * ldp + ip];
+    const double h0 = E[o] * w0 + E[ld + o] * w1 + E[2 * ld + o] * w2;
+    const double h1 = E[3 * ld + o] * w0 + E[4 * ld + o] * w1 + E[5 * ld + o] * w2;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) bb[k] += F[k * ld + o] * h0 + F[(9 + k) * ld + o] * h1;
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) bb[k] = warp_sum(bb[k]);
+  if (lane == 0)
+    for (int k = 0; k < 9; ++k) out[9 * c + k] = vc[9 * c + k] - bb[k];
+}
+
+void reduced_rhs(ba_problem* P, const double* vc, const double* vp_user, double* out) {
+  P->scratch2.ensure(sizeof(double) * 3 * P->ldp + 64);
+  double* w = P->scratch2.as<double>();
+  if (P->n_p) {
+    k_point_cinv_apply<<<cdiv(P->n_p, 128), 128, 0, P->stream>>>(P->Cinv64.as<double>(), P->ldp,
+                                                                P->pt_user.as<int>(), vp_user, P->n_p, w);
+    launched(P);
+  }
+  k_camera_reduce_rhs<<<cdiv((long long)P->n_c * 32, 128), 128, 0, P->stream>>>(
+      P->F64.as<double>(), P->E64.as<double>(), P->ld, P->cam_ptr.as<int>(), P->cam_obs.as<int>(),
+      P->obs_pt.as<int>(), w, P->ldp, vc, P->n_c, out);
+  launched(P);
+}
+
+}  // namespace ba

@@ -1,0 +1,250 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Sizes span several warp tiles, CTA chunks and multigrid levels with ragged tails.
+Tolerances: FP64 kernels 1e-12 (rounding-order differences only, relative to the
+array's scale); integer and index work bit-exact; FP32 storage 1e-4.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import torch
+
+from conftest import scene
+from oracle import adjoint as oadj
+from oracle import camera, lm, multigrid, schur
+
+pytestmark = pytest.mark.gpu
+
+
+def _api():
+    from paper_2007_01941_gb300 import _ffi, api
+    return api, _ffi
+
+
+def _prob(s, dev, **opt):
+    api, _ = _api()
+    return api.from_scene(s, device=dev, **opt)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+CHAIN = dict(n_cams=300, n_pts=30000)
+
+
+def test_linearize_matches_oracle(gpu):
+    api, F_ = _api()
+    for s in (scene("ring", seed=0), scene("street_chain", **CHAIN)):
+        prob, cams, pts, obs = _prob(s, gpu)
+        cost = prob.linearize(cams, pts, obs)
+        f = camera.residuals(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs)
+        F, E = camera.jacobians(s.cams, s.pts, s.cam_idx, s.pt_idx)
+        assert rel(_np(prob.get_array(F_.BA_ARR_RESIDUAL)).reshape(-1, 2), f) < 1e-12
+        Fg = _np(prob.get_array(F_.BA_ARR_JAC_F)).reshape(-1, 2, 9)
+        for j in range(9):
+            assert rel(Fg[:, :, j], F[:, :, j]) < 1e-12, j
+        assert rel(_np(prob.get_array(F_.BA_ARR_JAC_E)).reshape(-1, 2, 3), E) < 1e-12
+        assert abs(cost - 0.5 * np.sum(f * f)) <= 1e-12 * cost
+
+
+def test_schur_setup_matches_oracle(gpu):
+    api, F_ = _api()
+    s = scene("street_chain", **CHAIN)
+    prob, cams, pts, obs = _prob(s, gpu)
+    prob.linearize(cams, pts, obs)
+    prob.schur_setup(s.lam)
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+    assert rel(_np(prob.get_array(F_.BA_ARR_DAMP_C)), sch.Dc) < 1e-12
+    assert rel(_np(prob.get_array(F_.BA_ARR_DAMP_P)), sch.Dp) < 1e-12
+    assert rel(_np(prob.get_array(F_.BA_ARR_CINV)).reshape(-1, 3, 3), sch.Cinv_blocks) < 1e-11
+    assert rel(_np(prob.get_array(F_.BA_ARR_GRAD_C)), sch.g_c) < 1e-11
+    assert rel(_np(prob.get_array(F_.BA_ARR_GRAD_P)), sch.g_p) < 1e-11
+    assert rel(_np(prob.get_array(F_.BA_ARR_RHS)), sch.b) < 1e-9
+    blocks = multigrid.diag_blocks(sch.S, 9)
+    assert rel(_np(prob.get_array(F_.BA_ARR_SCC_INV)).reshape(-1, 9, 9), np.linalg.inv(blocks)) < 1e-8
+
+
+@pytest.mark.parametrize("which", ["ring", "chain", "bigpoints"])
+def test_implicit_schur_product_matches_explicit_oracle(gpu, which):
+    api, F_ = _api()
+    s = {"ring": lambda: scene("ring", seed=0),
+         "chain": lambda: scene("street_chain", **CHAIN),
+         # points seen by up to 48 cameras: the >32-observation tile path
+         "bigpoints": lambda: scene("ring", seed=7, n_cams=48, n_pts=300, kmin=20, kmax=48)}[which]()
+    for prec in (F_.BA_FP64, F_.BA_MIXED):
+        prob, cams, pts, obs = _prob(s, gpu, precision=prec)
+        prob.linearize(cams, pts, obs)
+        prob.schur_setup(s.lam)
+        sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+        x = np.random.default_rng(3).normal(size=(s.n_cams, 9))
+        ref = sch.S @ x.ravel()
+        xt = torch.tensor(x, device=gpu)
+        y = _np(prob.schur_matvec(xt)).ravel()
+        assert np.linalg.norm(y - ref) <= 1e-12 * np.linalg.norm(ref)
+        if prec == F_.BA_MIXED:
+            y32 = _np(prob.schur_matvec(xt, F_.BA_MIXED)).ravel()
+            assert np.linalg.norm(y32 - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
+def _bsr_dense(rowptr, cols, vals, b):
+    n = len(rowptr) - 1
+    A = np.zeros((n * b, n * b))
+    for i in range(n):
+        for e in range(rowptr[i], rowptr[i + 1]):
+            j = cols[e]
+            A[i * b:(i + 1) * b, j * b:(j + 1) * b] = vals[e]
+    return A
+
+
+def _oracle_hierarchy(s, cmax):
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+    W = multigrid.covisibility(s.cam_idx, s.pt_idx, s.n_cams, s.n_pts)
+    return sch, multigrid.Hierarchy(sch.S, W, s.cams, coarse_max_nodes=cmax)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_hierarchy_matches_oracle(gpu, prec):
+    api, F_ = _api()
+    s = scene("street_chain", **CHAIN)
+    p = F_.BA_FP64 if prec == "fp64" else F_.BA_MIXED
+    prob, cams, pts, obs = _prob(s, gpu, precision=p, coarse_max_nodes=16)
+    prob.linearize(cams, pts, obs)
+    prob.schur_setup(s.lam)
+    prob.mg_setup()
+    sch, H = _oracle_hierarchy(s, 16)
+    info = prob.info()
+    assert info["n_levels"] == len(H.levels)
+    tol = 1e-10 if prec == "fp64" else 2e-4
+    for l, L in enumerate(H.levels):
+        assert info["level_nodes"][l] == L.n
+        rp = _np(prob.get_array(F_.BA_ARR_LEVEL_ROWPTR, l))
+        cols = _np(prob.get_array(F_.BA_ARR_LEVEL_COLS, l))
+        Wc = L.W.tocsr()
+        Wc.sort_indices()
+        assert np.array_equal(rp, Wc.indptr) and np.array_equal(cols, Wc.indices)          # bit-exact
+        assert np.array_equal(_np(prob.get_array(F_.BA_ARR_LEVEL_W, l)), Wc.data)           # bit-exact
+        vals = _np(prob.get_array(F_.BA_ARR_LEVEL_VALS, l)).reshape(-1, L.b, L.b)
+        Ad = _bsr_dense(rp, cols, vals, L.b)
+        assert rel(Ad, L.A.toarray()) < tol, l
+        K = _np(prob.get_array(F_.BA_ARR_NULLSPACE, l)).reshape(L.n, L.b, 16)
+        assert rel(K, L.K) < (1e-11 if l == 0 else 1e-8), l
+        if l == len(H.levels) - 1:
+            Ainv = _np(prob.get_array(F_.BA_ARR_COARSE_INV, l))
+            N = L.n * L.b
+            Np = int(round(np.sqrt(Ainv.size)))
+            ref = np.linalg.inv(L.dense)
+            assert rel(Ainv.reshape(Np, Np)[:N, :N], ref) < (1e-7 if prec == "fp64" else 5e-3)
+            continue
+        sptr = _np(prob.get_array(F_.BA_ARR_STRENGTH_PTR, l))
+        sidx = _np(prob.get_array(F_.BA_ARR_STRENGTH_IDX, l))
+        for i in range(L.n):
+            assert list(sidx[sptr[i]:sptr[i + 1]]) == L.order[i], (l, i)                     # bit-exact
+        assert np.array_equal(_np(prob.get_array(F_.BA_ARR_AGG, l)), L.agg)                 # bit-exact
+        kept = _np(prob.get_array(F_.BA_ARR_KEPT, l + 1)).view(np.uint32)
+        assert np.array_equal(kept, (L.kept * (1 << np.arange(16))).sum(axis=1).astype(np.uint32))
+        Q = _np(prob.get_array(F_.BA_ARR_PROLONG, l)).reshape(L.n, L.b, 16)
+        assert np.abs(Q - L.Q).max() < 1e-9, l
+        lam_gpu = info["level_lambda_max"][l]
+        assert abs(lam_gpu - L.lam_max) <= (1e-9 if prec == "fp64" else 1e-3) * L.lam_max, l
+
+
+def test_vcycle_matches_oracle(gpu):
+    api, F_ = _api()
+    s = scene("street_chain", **CHAIN)
+    prob, cams, pts, obs = _prob(s, gpu, coarse_max_nodes=16)
+    prob.linearize(cams, pts, obs)
+    prob.schur_setup(s.lam)
+    prob.mg_setup()
+    sch, H = _oracle_hierarchy(s, 16)
+    for seed in range(2):
+        r = np.random.default_rng(seed).normal(size=9 * s.n_cams)
+        z = _np(prob.precond_apply(torch.tensor(r, device=gpu)))
+        ref = H.apply(r)
+        assert np.linalg.norm(z - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("pc", ["mg", "jacobi"])
+def test_pcg_matches_oracle(gpu, pc):
+    api, F_ = _api()
+    s = scene("street_chain", **CHAIN)
+    code = {"mg": F_.BA_PRECOND_MG, "jacobi": F_.BA_PRECOND_JACOBI}[pc]
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+    exact = sla.cho_solve(sla.cho_factor(sch.S.toarray()), sch.b)
+    for rtol in (1e-6, 1e-12):
+        prob, cams, pts, obs = _prob(s, gpu, preconditioner=code, coarse_max_nodes=16, rtol=rtol, max_iters=5000)
+        dc, dp, it, relres = prob.solve(cams, pts, obs, s.lam)
+        _, _, it_ref, _ = lm.solve_step(sch, s.cams, pc, rtol=rtol, max_iters=5000, coarse_max_nodes=16)
+        assert relres <= rtol
+        assert abs(it - it_ref) <= max(1, it_ref // 20), (it, it_ref)
+        if rtol == 1e-12:
+            assert np.linalg.norm(_np(dc).ravel() - exact) <= 1e-8 * np.linalg.norm(exact)
+            dp_ref = sch.back_substitute(exact)
+            assert np.linalg.norm(_np(dp).ravel() - dp_ref) <= 1e-8 * np.linalg.norm(dp_ref)
+
+
+def test_mixed_precision_solution_matches_oracle(gpu):
+    api, F_ = _api()
+    s = scene("street_chain", **CHAIN)
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+    exact = sla.cho_solve(sla.cho_factor(sch.S.toarray()), sch.b)
+    prob, cams, pts, obs = _prob(s, gpu, precision=F_.BA_MIXED, coarse_max_nodes=16, rtol=1e-10)
+    dc, dp, it, relres = prob.solve(cams, pts, obs, s.lam)
+    assert relres <= 1e-10
+    # the outer operator is FP64, so the true FP64 residual reaches the target too
+    d = _np(dc).ravel()
+    true_rel = np.linalg.norm(sch.b - sch.S @ d) / np.linalg.norm(sch.b)
+    assert true_rel <= 2e-10
+    assert np.linalg.norm(d - exact) <= 1e-6 * np.linalg.norm(exact)
+
+
+def test_lm_step_matches_oracle(gpu):
+    api, F_ = _api()
+    s = scene("ring", seed=0)
+    prob, cams, pts, obs = _prob(s, gpu, coarse_max_nodes=4, rtol=1e-12)
+    lam, acc, cost = prob.lm_step(cams, pts, obs, 1e-4)
+    c1, p1, lam1, nu1, acc1, cost0, cost1, info = lm.lm_step(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, 1e-4,
+                                                             rtol=1e-12, coarse_max_nodes=4)
+    assert acc == acc1
+    assert abs(cost - cost1) <= 1e-9 * cost1
+    assert abs(lam - lam1) <= 1e-6 * lam1
+    assert rel(_np(cams), c1) < 1e-9 and rel(_np(pts), p1) < 1e-9
+
+
+@pytest.mark.parametrize("damping", ["marquardt", "identity"])
+def test_adjoint_matches_oracle(gpu, damping):
+    api, F_ = _api()
+    s = scene("ring", seed=5, n_cams=12, n_pts=300, kmin=2, kmax=6)
+    lam = 1e-2
+    dm = F_.BA_DAMP_MARQUARDT if damping == "marquardt" else F_.BA_DAMP_IDENTITY
+    prob, cams, pts, obs = _prob(s, gpu, coarse_max_nodes=4, rtol=1e-13, damping=dm)
+    prob.solve(cams, pts, obs, lam)
+    vbar = np.random.default_rng(2).normal(size=9 * s.n_cams + 3 * s.n_pts)
+    go, gc, gp = prob.adjoint(torch.tensor(vbar, device=gpu))
+    ro, rc, rp, _ = oadj.adjoint(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, lam, vbar, damping)
+    assert rel(_np(go), ro) < 1e-7
+    assert rel(_np(gc), rc) < 1e-7
+    assert rel(_np(gp), rp) < 1e-7
+
+
+def test_autograd_function_matches_oracle(gpu):
+    api, F_ = _api()
+    from paper_2007_01941_gb300.autograd import lm_step_delta
+    s = scene("ring", seed=5, n_cams=12, n_pts=300, kmin=2, kmax=6)
+    lam = 1e-2
+    prob, cams, pts, obs = _prob(s, gpu, coarse_max_nodes=4, rtol=1e-13)
+    obs.requires_grad_(True)
+    cams.requires_grad_(True)
+    pts.requires_grad_(True)
+    delta = lm_step_delta(prob, cams, pts, obs, lam)
+    vbar = torch.tensor(np.random.default_rng(3).normal(size=delta.numel()), device=gpu)
+    (delta * vbar).sum().backward()
+    ro, rc, rp, rdelta = oadj.adjoint(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, lam, _np(vbar))
+    assert rel(_np(delta), rdelta) < 1e-8
+    assert rel(_np(obs.grad), ro) < 1e-7
+    assert rel(_np(cams.grad), rc) < 1e-7
+    assert rel(_np(pts.grad), rp) < 1e-7
