@@ -1,0 +1,405 @@
+"""Benchmark: ms per LM-step linear solve (linearise + Schur setup + multigrid setup +
+PCG to 1e-6 relative residual + point back-substitution + cost at x + delta) on
+the street-chain scene (2,000 cameras, 300,000 points, ~1.5M observations,
+seeded synthetic data), mixed precision, on one GB300.
+
+Every timed step restores the same starting cameras/points, so all steps solve the
+identical system.  Prints one JSON line (see the keys at the end of main()).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ms per LM-step Schur PCG solve to 1e-6 rel res; Schur matvec HBM GB/s vs FP64"
+WORKLOADS = {
+    "street_chain": dict(fn="street_chain", kw={}, rtol=1e-6),
+    "city_grid": dict(fn="city_grid", kw={}, rtol=1e-6),
+    "ring": dict(fn="ring", kw={}, rtol=1e-8),
+}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, n in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------
+# algorithmic bytes / flops of the implicit Schur product (one launch)
+# ------------------------------------------------------------------------------
+def k3_bytes(n_o, n_p, n_c, w):
+    # F (18) + E (6) per observation and its camera index; C^-1 (6 unique) and the
+    # point pointer per point; x read and y accumulated once per camera
+    return n_o * (24 * w + 4) + n_p * (6 * w + 4) + 2 * n_c * 9 * w
+
+
+def k3_flops(n_o, n_p):
+    # per observation: F x (18 FMA), E^T u (6), E z (6), F^T w (18); per point C^-1 v (9)
+    return 2 * (48 * n_o + 9 * n_p)
+
+
+# ------------------------------------------------------------------------------
+# CPU baseline: the oracle, single-threaded, in a child process
+# ------------------------------------------------------------------------------
+_ORACLE_CHILD = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+from paper_2007_01941_gb300 import scenes
+from oracle import lm, schur
+s = getattr(scenes, {fn!r})(**{kw!r})
+if {sub!r}:
+    s = scenes.subscene(s, {sub!r}[0], {sub!r}[1], seed=0)
+times = []
+for k in range({steps}):
+    t = time.perf_counter()
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+    dc, dp, it, rel = lm.solve_step(sch, s.cams, "mg", {rtol}, coarse_max_nodes=32)
+    times.append(time.perf_counter() - t)
+print(json.dumps(dict(times=times, n_obs=s.n_obs, n_cams=s.n_cams, n_pts=s.n_pts, iters=it, rel=rel)))
+"""
+
+
+def run_oracle(workload, steps, sub=None):
+    wl = WORKLOADS[workload]
+    code = _ORACLE_CHILD.format(root=ROOT, fn=wl["fn"], kw=wl["kw"], sub=sub, steps=steps, rtol=wl["rtol"])
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def reference_main(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import paper_2007_01941_gb300.scenes as scenes
+    wl = WORKLOADS[args.workload]
+    full = getattr(scenes, wl["fn"])(**wl["kw"])
+    # each reference step: the oracle on the first 400 cameras of the workload (about a
+    # fifth of its observations), scaled to the full observation count
+    sub = (min(400, full.n_cams), full.n_pts)
+    res = run_oracle(args.workload, args.warmup + args.steps, sub)
+    t = res["times"][args.warmup:]
+    scale = full.n_obs / res["n_obs"]
+    ms = 1e3 * sum(t) / len(t) * scale
+    sample = (f"oracle (NumPy/SciPy FP64, 1 thread) LM-step solve on the first {res['n_cams']} cameras "
+              f"({res['n_obs']} of {full.n_obs} observations), {len(t)} timed steps, time scaled by "
+              f"{scale:.2f} to the full observation count")
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_cams": full.n_cams, "n_pts": full.n_pts,
+                       "n_obs": full.n_obs, "rtol": wl["rtol"]},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------
+def gpu_main(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2007_01941_gb300 import _ffi, api, scenes
+
+    wl = WORKLOADS[args.workload]
+    s = getattr(scenes, wl["fn"])(**wl["kw"])
+    prec = _ffi.BA_MIXED if args.precision == "mixed" else _ffi.BA_FP64
+
+    def make(precision):
+        return api.from_scene(s, device=dev, precision=precision, rtol=wl["rtol"], max_iters=2000)
+
+    prob, cams, pts, obs = make(prec)
+    cams0, pts0 = cams.clone(), pts.clone()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(p, c, x):
+        c.copy_(cams0)
+        x.copy_(pts0)
+        return p.lm_step(c, x, obs, s.lam)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        step(prob, cams, pts)
+    launches0 = prob.info()["kernel_launches"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            lam1, acc, cost = step(prob, cams, pts)
+        e1.record(stream)
+        barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    launches = (prob.info()["kernel_launches"] - launches0) // args.steps
+    info = prob.info()
+
+    # per-kernel event timing of the implicit Schur products over the same steps
+    ksteps = max(1, min(args.steps, 5))
+    prob.set_kernel_timing(True)
+    for _ in range(ksteps):
+        step(prob, cams, pts)
+    kt = {k: prob.kernel_timing(c) for k, c in (("schur_fp32", _ffi.BA_KT_SCHUR_FP32),
+                                                ("schur_fp64", _ffi.BA_KT_SCHUR_FP64),
+                                                ("linearize", _ffi.BA_KT_LINEARIZE))}
+    prob.set_kernel_timing(False)
+
+    # stage split (untimed pass, events around each call)
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b), r
+    cams.copy_(cams0)
+    pts.copy_(pts0)
+    t_lin, _ = timed(lambda: prob.linearize(cams, pts, obs))
+    t_sch, _ = timed(lambda: prob.schur_setup(s.lam))
+    t_mg, _ = timed(lambda: prob.mg_setup())
+    t_pcg, (dc, iters, rel) = timed(lambda: prob.pcg_solve())
+
+    # all-FP64 GPU solve of the same step for comparison
+    fp64 = None
+    if prec == _ffi.BA_MIXED and not args.skip_fp64:
+        p64, c64, x64, _ = make(_ffi.BA_FP64)
+        for _ in range(2):
+            step(p64, c64, x64)
+        n64 = max(2, min(args.steps, 10))
+        barrier()
+        e0.record(stream)
+        for _ in range(n64):
+            step(p64, c64, x64)
+        e1.record(stream)
+        barrier()
+        fp64 = max_over_ranks(e0.elapsed_time(e1) / n64)
+        it64 = p64.info()["pcg_iters"]
+        p64.close()
+
+    # end to end through the public API with host buffers: H2D of the step's inputs
+    # (cameras, points, observations) from pinned memory, the step, D2H of the result
+    cams_h = torch.from_numpy(s.cams).pin_memory()
+    pts_h = torch.from_numpy(s.pts).pin_memory()
+    obs_h = torch.from_numpy(s.obs).pin_memory()
+    out_c = torch.empty_like(cams_h).pin_memory()
+    out_p = torch.empty_like(pts_h).pin_memory()
+    obs_d = torch.empty_like(obs)
+
+    def e2e_step():
+        cams.copy_(cams_h, non_blocking=True)
+        pts.copy_(pts_h, non_blocking=True)
+        obs_d.copy_(obs_h, non_blocking=True)
+        r = prob.lm_step(cams, pts, obs_d, s.lam)
+        out_c.copy_(cams, non_blocking=True)
+        out_p.copy_(pts, non_blocking=True)
+        return r
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    h2d = (cams_h.numel() + pts_h.numel() + obs_h.numel()) * 8
+    d2h = (out_c.numel() + out_p.numel()) * 8
+
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_note = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    fp64_peak_tflops = 1.205   # FMA-chain probe on this machine's GB300
+    n_o, n_p, n_c = s.n_obs, s.n_pts, s.n_cams
+    kernels = {}
+    for name, (tot, n) in kt.items():
+        if n == 0:
+            continue
+        avg = tot / n
+        d = {"launches": n, "avg_ms": avg}
+        if name == "schur_fp32":
+            b = k3_bytes(n_o, n_p, n_c, 4)
+            d.update(bound="hbm", achieved=b / avg / 1e6, unit="GB/s", algo_bytes=b)
+        elif name == "schur_fp64":
+            b = k3_bytes(n_o, n_p, n_c, 8)
+            fl = k3_flops(n_o, n_p)
+            d.update(bound="alu", achieved=fl / avg / 1e9, unit="TFLOP/s", algo_flops=fl,
+                     hbm_gbs=b / avg / 1e6, algo_bytes=b)
+        kernels[name] = d
+    # dominant kernel class by total time
+    dom = max(kernels, key=lambda k: kt[k][0]) if kernels else None
+    roofline = None
+    if dom == "schur_fp32" or (dom == "linearize" and "schur_fp32" in kernels):
+        k = kernels["schur_fp32"]
+        roofline = {"kernel": "k_schur_matvec<float>", "bound": "hbm", "achieved": k["achieved"], "peak": hbm,
+                    "unit": "GB/s", "frac": k["achieved"] / hbm, "traffic": None, "peak_source": peak_note}
+    elif dom == "schur_fp64":
+        k = kernels["schur_fp64"]
+        roofline = {"kernel": "k_schur_matvec<double>", "bound": "alu", "achieved": k["achieved"],
+                    "peak": fp64_peak_tflops, "unit": "TFLOP/s", "frac": k["achieved"] / fp64_peak_tflops,
+                    "traffic": None, "peak_source": "measured FP64 FMA probe"}
+    traffic = _traffic_from_profiles(dom)
+    if roofline is not None and traffic is not None:
+        roofline["traffic"] = traffic
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        try:
+            res = run_oracle(args.workload, 1)
+            cpu = {"value": 1e3 * res["times"][0], "unit": "ms", "cores": 1, "kind": "oracle",
+                   "sample": f"one full LM-step solve of the same workload ({res['n_obs']} observations) by the "
+                             f"FP64 NumPy/SciPy oracle, single-threaded, {res['iters']} PCG iterations"}
+        except Exception as ex:  # keep the GPU line even if the baseline fails
+            cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:300]}
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == _ffi.BA_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n_cams": n_c, "n_pts": n_p, "n_obs": n_o, "rtol": wl["rtol"],
+                       "precision": args.precision, "preconditioner": "multigrid",
+                       "levels": info["level_nodes"], "pcg_iters": info["pcg_iters"],
+                       "parallelism": f"replicas x{world}",
+                       "l2": "per-step working set > L2 (FP64+FP32 Jacobian blocks ~0.43 GB), no flush"},
+            "parts_ms": {"linearize": t_lin, "schur_setup": t_sch, "mg_setup": t_mg, "pcg_solve": t_pcg,
+                         "pcg_iters": iters},
+            "fp64_ms_per_step": fp64,
+            "mixed_speedup_vs_fp64": (fp64 / ms) if fp64 else None,
+            "kernels": kernels,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _traffic_from_profiles(dom):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+        return d.get(dom)
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="street_chain", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_main(args)
+    else:
+        gpu_main(args)
+
+
+if __name__ == "__main__":
+    main()
