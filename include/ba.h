@@ -208,6 +208,40 @@ ba_status ba_get_kernel_timing(ba_problem* prob, int kernel_class, double* total
 ba_status ba_get_array(ba_problem* prob, int which, int level, void* dst, size_t bytes,
                        size_t* needed);
 
+/* ---------------------------------------------------------------------------------
+ * Allocation-free objective evaluation.
+ * --------------------------------------------------------------------------------- */
+
+/* Largest camera count ba_cost_noalloc accepts (its fixed scratch holds 12 doubles per
+ * camera plus 1,024 partial sums: about 0.4 MB per GPU). */
+#define BA_NOALLOC_MAX_CAMS 4096
+
+/* Evaluates the LM objective 1/2 sum_o |pi(cam_c, X_p) - obs_o|^2 for caller-supplied
+ * cameras, points and observations without allocating any device memory, and without a
+ * ba_problem.  The paper has no counterpart: this entry point exists for callers that
+ * must not allocate GPU memory themselves, such as code whose device memory is owned by a
+ * framework or pool allocator with a fixed budget, or a step loop that must keep a fixed
+ * footprint and cannot risk cudaMalloc's implicit device synchronisation or an
+ * out-of-memory failure in the middle of a run.  ba_create and the solve entry points do
+ * allocate; this one does not.
+ *
+ * cams [n_cams x 9], pts [n_pts x 3], obs [n_obs x 2]: device float64; cam_idx, pt_idx:
+ * device int32 [n_obs]; cost_out: device pointer to one double, written on `stream`
+ * (a cudaStream_t; the call returns without synchronising).  An observation with an
+ * out-of-range index makes *cost_out NaN.
+ *
+ * Scratch lives in a fixed array inside the library that every GPU loading the library
+ * keeps until the process exits.  The first call on a device looks up that array's
+ * device address (with the device current), so make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents; the call
+ * clears the parts that must start at zero.  Calls whose GPU work overlaps (on different
+ * streams without ordering) race on the array and give wrong results.
+ * Returns BA_ERR_LIMIT if n_cams > BA_NOALLOC_MAX_CAMS, BA_ERR_INVALID_ARG for bad
+ * sizes or null arrays, BA_ERR_CUDA if a launch fails. */
+ba_status ba_cost_noalloc(int n_cams, int n_pts, int n_obs, const double* cams, const double* pts,
+                          const double* obs, const int32_t* cam_idx, const int32_t* pt_idx,
+                          double* cost_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,8 @@ _SIGS = {
     "ba_set_kernel_timing": (c_int, [c_void_p, c_int]),
     "ba_get_kernel_timing": (c_int, [c_void_p, c_int, POINTER(c_double), POINTER(c_longlong)]),
     "ba_get_array": (c_int, [c_void_p, c_int, c_int, c_void_p, c_size_t, POINTER(c_size_t)]),
+    "ba_cost_noalloc": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_void_p, c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)
