@@ -189,7 +189,8 @@ def gpu_main(args):
     prec = _ffi.BA_MIXED if args.precision == "mixed" else _ffi.BA_FP64
 
     def make(precision):
-        return api.from_scene(s, device=dev, precision=precision, rtol=wl["rtol"], max_iters=2000)
+        return api.from_scene(s, device=dev, precision=precision, rtol=wl["rtol"], max_iters=2000,
+                              coarse_max_nodes=args.coarse_max_nodes)
 
     prob, cams, pts, obs = make(prec)
     cams0, pts0 = cams.clone(), pts.clone()
@@ -353,6 +354,7 @@ def gpu_main(args):
             "vs_baseline": None, "dtype": "f32+f64" if prec == _ffi.BA_MIXED else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n_cams": n_c, "n_pts": n_p, "n_obs": n_o, "rtol": wl["rtol"],
                        "precision": args.precision, "preconditioner": "multigrid",
+                       "coarse_max_nodes": args.coarse_max_nodes,
                        "levels": info["level_nodes"], "pcg_iters": info["pcg_iters"],
                        "parallelism": f"replicas x{world}",
                        "l2": "per-step working set > L2 (FP64+FP32 Jacobian blocks ~0.43 GB), no flush"},
@@ -373,10 +375,15 @@ def gpu_main(args):
 
 
 def _traffic_from_profiles(dom):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if any."""
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if the
+    kernel source is still the one the counters were taken on (else None)."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
+        src = open(os.path.join(ROOT, "paper_2007_01941_gb300", "csrc", "schur.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != d.get("schur_cu_sha256"):
+            return None
         return d.get(dom)
     except Exception:
         return None
@@ -392,6 +399,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--coarse-max-nodes", type=int, default=32)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include "ba_internal.h"
+#include "device_util.cuh"
 
 namespace ba {
 void back_substitute_to(ba_problem* P, const double* dc, double* out_int, double* out_user);
@@ -38,6 +39,15 @@ __global__ void k_soa_to_user(const double* __restrict__ src, size_t ld, int row
   if (i >= n) return;
   const int u = perm[i];
   for (int k = 0; k < rows; ++k) dst[(size_t)u * rows + k] = src[k * ld + i];
+}
+
+// interleaved per-observation records (stride values each, `rows` of them from `offset`)
+__global__ void k_rec_to_user(const double* __restrict__ src, int stride, int offset, int rows, int n,
+                              const int* __restrict__ perm, double* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int u = perm[i];
+  for (int k = 0; k < rows; ++k) dst[(size_t)u * rows + k] = src[(size_t)i * stride + offset + k];
 }
 
 __global__ void k_cinv_to_user(const double* __restrict__ src, size_t ldp, int n, const int* __restrict__ perm,
@@ -119,6 +129,7 @@ ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx, co
     BA_CUDA(cudaMemsetAsync(P->flags.p, 0, sizeof(int) * ba::F_COUNT, P->stream));
     BA_CUDA(cudaMallocHost(&P->h_scal, sizeof(double) * ba::kScalars));
     BA_CUDA(cudaMallocHost(&P->h_flags, sizeof(int) * ba::F_COUNT));
+    BA_CUDA(cudaMallocHost(&P->h_cheb, sizeof(double) * 16 * ba::kChebSlots));
     ba::build_graph(P, cam_idx, pt_idx);
   });
   if (st != BA_OK) {
@@ -133,8 +144,8 @@ void ba_destroy(ba_problem* P) {
   if (!P) return;
   cudaStreamSynchronize(P->stream);
   ba::DBuf* bufs[] = {&P->obs_user, &P->obs_cam, &P->obs_ptu, &P->obs_pt, &P->pt_ptr, &P->pt_user, &P->cam_ptr,
-                      &P->cam_obs, &P->tile_pt, &P->chunk_tile, &P->chunk_cam, &P->camx, &P->fres, &P->F64,
-                      &P->E64, &P->F32, &P->E32, &P->cams_lin, &P->pts_lin, &P->obs_lin, &P->Dc, &P->Dp,
+                      &P->cam_obs, &P->tile_pt, &P->tile_desc, &P->chunk_tile, &P->chunk_cam, &P->camx, &P->fres, &P->J64,
+                      &P->J64, &P->J32, &P->J32, &P->cams_lin, &P->pts_lin, &P->obs_lin, &P->Dc, &P->Dp,
                       &P->Cinv64, &P->Cinv32, &P->gc, &P->gp, &P->wp, &P->rhs, &P->Dc32, &P->Scc, &P->Scc_inv,
                       &P->Scc_inv32, &P->x, &P->r, &P->z, &P->p, &P->q, &P->y32a, &P->y32b, &P->delta_c,
                       &P->delta_p, &P->scal, &P->partial, &P->counter, &P->flags, &P->scratch, &P->scratch2};
@@ -147,11 +158,14 @@ void ba_destroy(ba_problem* P) {
   }
   if (P->h_scal) cudaFreeHost(P->h_scal);
   if (P->h_flags) cudaFreeHost(P->h_flags);
+  if (P->h_cheb) cudaFreeHost(P->h_cheb);
   for (auto& r : P->krec) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
+  if (P->pcg_exec) cudaGraphExecDestroy(P->pcg_exec);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   delete P;
 }
 
@@ -360,11 +374,11 @@ ba_status ba_get_array(ba_problem* P, int which, int level, void* dst, size_t by
     const int go = ba::cdiv(std::max(n_o, 1), 256), gp = ba::cdiv(std::max(n_p, 1), 256);
     switch (which) {
       case BA_ARR_RESIDUAL:
-        k_soa_to_user<<<go, 256, 0, P->stream>>>(P->fres.as<double>(), P->ld, 2, n_o, P->obs_user.as<int>(), d); break;
+        k_rec_to_user<<<go, 256, 0, P->stream>>>(P->fres.as<double>(), 2, 0, 2, n_o, P->obs_user.as<int>(), d); break;
       case BA_ARR_JAC_F:
-        k_soa_to_user<<<go, 256, 0, P->stream>>>(P->F64.as<double>(), P->ld, 18, n_o, P->obs_user.as<int>(), d); break;
+        k_rec_to_user<<<go, 256, 0, P->stream>>>(P->J64.as<double>(), ba::kRec, 0, 18, n_o, P->obs_user.as<int>(), d); break;
       case BA_ARR_JAC_E:
-        k_soa_to_user<<<go, 256, 0, P->stream>>>(P->E64.as<double>(), P->ld, 6, n_o, P->obs_user.as<int>(), d); break;
+        k_rec_to_user<<<go, 256, 0, P->stream>>>(P->J64.as<double>(), ba::kRec, 18, 6, n_o, P->obs_user.as<int>(), d); break;
       case BA_ARR_DAMP_C: D2D(P->Dc.p, need); break;
       case BA_ARR_GRAD_C: D2D(P->gc.p, need); break;
       case BA_ARR_RHS: D2D(P->rhs.p, need); break;

@@ -14,6 +14,7 @@
 namespace ba {
 
 constexpr int kNull = 16;        // near-nullspace dimension (Section 3.3)
+constexpr int kChebSlots = 24;   // per level: theta, delta, sigma_1, lambda_max, pad, alphas, betas
 constexpr int kScalars = 64;     // device scalar slots per problem
 
 // Error raised inside the library; converted to a ba_status at the C boundary.
@@ -70,6 +71,7 @@ enum Scalar : int {
   S_TMP2 = 9,
   S_MODEL = 10,    // model reduction terms
   S_COST_NEW = 11,
+  S_ITER = 12,     // PCG iterations done (graph path)
   S_LANCZOS = 16,  // 16 .. 31: alphas / betas of the Lanczos recurrences
   S_LANCZOS_END = 32,
 };
@@ -88,6 +90,7 @@ enum Flag : int {
 struct Level {
   int n = 0, bs = 0;            // nodes, dofs per node
   int nnzb = 0;                 // block nonzeros of the operator / covisibility pattern
+  int maxrow = 1;               // longest block row
   DBuf row_ptr, cols, W;        // BSR pattern (int32) and covisibility counts (int64)
   DBuf vals64, vals32;          // operator blocks [nnzb][bs][bs]
   DBuf sptr, sidx;              // strength-ordered neighbour lists
@@ -128,18 +131,21 @@ struct ba_problem {
   ba::DBuf pt_user;             // int32 [n_p] internal point -> caller point
   ba::DBuf cam_ptr, cam_obs;    // camera-major CSR over internal obs
   int n_tiles = 0, n_chunks = 0, k3_window = 0;
+  unsigned k3_calls = 0;        // alternates the tile order of successive Schur products
   ba::DBuf tile_pt;             // int32 [n_tiles + 1] point ranges of <=32-obs warp tiles
+  ba::DBuf tile_desc;           // int4 [n_tiles] {first obs, obs count, first point, start mask}
   ba::DBuf chunk_tile;          // int32 [n_chunks + 1] tile ranges per matvec CTA
   ba::DBuf chunk_cam;           // int32 [2 n_chunks] lowest / highest camera of a chunk
   size_t ld = 0;                // leading dimension of per-observation SoA arrays
   size_t ldp = 0;               // leading dimension of per-point SoA arrays
   int max_row_contrib = 0;      // max_c sum_{o in c} |obs(point(o))| (hash sizing)
+  int max_pt_obs = 0;           // most observations of one point
 
   // linearisation (SoA, internal order)
   ba::DBuf camx;                // double [n_c][24] per-camera rotation data
-  ba::DBuf fres;                // double [2][ld]
-  ba::DBuf F64, E64;            // double [18][ld], [6][ld]
-  ba::DBuf F32, E32;            // float copies (mixed precision)
+  ba::DBuf fres;                // double [n_o][2] residuals
+  ba::DBuf J64;                 // double [n_o][24] Jacobian records (F row-major, then E)
+  ba::DBuf J32;                 // float copy of the records (mixed precision)
   ba::DBuf cams_lin, pts_lin;   // copies of the linearisation point (adjoint, nullspace)
   ba::DBuf obs_lin;             // copy of the observations of the last linearisation
 
@@ -155,6 +161,7 @@ struct ba_problem {
   // multigrid hierarchy
   std::vector<ba::Level> levels;
   int n_levels = 0;
+  bool sym_ready = false;       // symbolic hierarchy built (depends on the graph only)
 
   // PCG
   ba::DBuf x, r, z, p, q, y32a, y32b;
@@ -170,9 +177,19 @@ struct ba_problem {
   ba::DBuf counter;             // unsigned [8]
   ba::DBuf flags;               // int [F_COUNT]
   double* h_scal = nullptr;     // pinned host mirror
+  double* h_cheb = nullptr;     // pinned [16][kChebSlots] Lanczos data of the levels
   int* h_flags = nullptr;
   ba::DBuf scratch;             // general scratch
   ba::DBuf scratch2;
+
+  // PCG as one CUDA graph (a first iteration, then a device-driven while loop);
+  // rebuilt whenever a setup call may have moved buffers
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t pcg_exec = nullptr;
+  int graph_epoch = 0;          // bumped by every setup call
+  int pcg_graph_epoch = -1;     // epoch the graph was built for
+  bool graphs_ok = true;        // false after a failed build: eager fallback
+  long long pcg_graph_head = 0, pcg_graph_body = 0;  // kernels per graph part
 
   // optional CUDA-event timing of selected kernel classes
   bool ktime = false;
@@ -216,6 +233,9 @@ void schur_setup(ba_problem* P, double lambda);
 // y = S x on internal camera vectors; T selects the FP64 or FP32 storage kernel.
 void matvec64(ba_problem* P, const double* x, double* y);
 void matvec32(ba_problem* P, const float* x, float* y);
+// the same products without writing D_c x first (y must already hold it)
+void matvec64_accumulate(ba_problem* P, const double* x, double* y);
+void matvec32_accumulate(ba_problem* P, const float* x, float* y);
 void explicit_schur(ba_problem* P, Level& L0, bool fp32);
 void back_substitute_to(ba_problem* P, const double* dc, double* out_int, double* out_user);
 void reduced_rhs(ba_problem* P, const double* vc, const double* vp_user, double* out);

@@ -10,6 +10,48 @@ namespace ba {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Per-observation Jacobian record: F_o (2 x 9, row-major) then E_o (2 x 3, row-major),
+// 24 values, 96 bytes in FP32 / 192 bytes in FP64 (16-byte aligned).
+constexpr int kRec = 24;
+#define JF(J, o, k) (J)[(size_t)(o) * ::ba::kRec + (k)]
+#define JE(J, o, k) (J)[(size_t)(o) * ::ba::kRec + 18 + (k)]
+
+__device__ __forceinline__ void load_record(const float* __restrict__ r, float f[18], float e[6]) {
+  const float4* v = reinterpret_cast<const float4*>(r);
+  float4 q[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) q[i] = __ldcs(v + i);
+  float t[24];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    t[4 * i] = q[i].x;
+    t[4 * i + 1] = q[i].y;
+    t[4 * i + 2] = q[i].z;
+    t[4 * i + 3] = q[i].w;
+  }
+#pragma unroll
+  for (int k = 0; k < 18; ++k) f[k] = t[k];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) e[k] = t[18 + k];
+}
+
+__device__ __forceinline__ void load_record(const double* __restrict__ r, double f[18], double e[6]) {
+  const double2* v = reinterpret_cast<const double2*>(r);
+  double2 q[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) q[i] = __ldcs(v + i);
+  double t[24];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    t[2 * i] = q[i].x;
+    t[2 * i + 1] = q[i].y;
+  }
+#pragma unroll
+  for (int k = 0; k < 18; ++k) f[k] = t[k];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) e[k] = t[18 + k];
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

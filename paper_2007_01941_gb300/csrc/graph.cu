@@ -52,9 +52,13 @@ void build_graph(ba_problem* P, const int32_t* cam_idx_dev, const int32_t* pt_id
     pt_user[ip] = p;
     pt_int[p] = ip;
   }
-  int n_p_obs = 0;
-  for (int p = 0; p < n_p; ++p) n_p_obs += cnt[p] > 0;
+  int n_p_obs = 0, max_pt_obs = 0;
+  for (int p = 0; p < n_p; ++p) {
+    n_p_obs += cnt[p] > 0;
+    max_pt_obs = std::max(max_pt_obs, cnt[p]);
+  }
   P->n_p_obs = n_p_obs;
+  P->max_pt_obs = max_pt_obs;
   // observations grouped by internal point, sorted by camera inside each point
   std::vector<int32_t> pt_ptr(n_p + 1, 0);
   for (int ip = 0; ip < n_p; ++ip) pt_ptr[ip + 1] = pt_ptr[ip] + cnt[pt_user[ip]];
@@ -107,6 +111,17 @@ void build_graph(ba_problem* P, const int32_t* cam_idx_dev, const int32_t* pt_id
     }
   }
   const int n_tiles = (int)tile_pt.size() - 1;
+  // per-tile descriptor for the Schur product: first observation, observation count,
+  // first point and the mask of lanes that start a point (bit i: observation ob + i)
+  std::vector<int4> tile_desc(std::max(n_tiles, 1));
+  for (int t = 0; t < n_tiles; ++t) {
+    const int p0 = tile_pt[t], p1 = tile_pt[t + 1];
+    const int ob = pt_ptr[p0], nobs = pt_ptr[p1] - ob;
+    unsigned mask = 1u;
+    if (nobs <= 32)
+      for (int p = p0; p < p1; ++p) mask |= 1u << (pt_ptr[p] - ob);
+    tile_desc[t] = make_int4(ob, nobs, p0, (int)mask);
+  }
   // CTA chunks: contiguous tile ranges with about equal observation counts
   int want = std::max(1, std::min(P->n_sm * 3, n_tiles / 8));
   if (n_tiles == 0) want = 0;
@@ -148,6 +163,7 @@ void build_graph(ba_problem* P, const int32_t* cam_idx_dev, const int32_t* pt_id
   upload(P, P->cam_ptr, cam_ptr);
   upload(P, P->cam_obs, cam_obs);
   upload(P, P->tile_pt, tile_pt);
+  upload(P, P->tile_desc, tile_desc);
   upload(P, P->chunk_tile, chunk_tile);
   upload(P, P->chunk_cam, chunk_cam);
   sync(P);

@@ -157,23 +157,24 @@ k_linearize(const double* __restrict__ cams, const double* __restrict__ pts,
     CamObs v;
     project_obs<JAC>(cams + 9 * c, camx + (size_t)kCamx * c, X, ob, v);
     acc += 0.5 * (v.res[0] * v.res[0] + v.res[1] * v.res[1]);
-    if (fres) {
-      fres[o] = v.res[0];
-      fres[ld + o] = v.res[1];
-    }
+    if (fres) reinterpret_cast<double2*>(fres)[o] = make_double2(v.res[0], v.res[1]);
     if (JAC) {
       bool finite = isfinite(v.res[0]) && isfinite(v.res[1]);
+      double rec[kRec];
 #pragma unroll
-      for (int k = 0; k < 18; ++k) {
-        F64[k * ld + o] = v.F[k];
-        finite = finite && isfinite(v.F[k]);
-        if (MIXED) F32[k * ld + o] = (float)v.F[k];
-      }
+      for (int k = 0; k < 18; ++k) rec[k] = v.F[k];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        E64[k * ld + o] = v.E[k];
-        finite = finite && isfinite(v.E[k]);
-        if (MIXED) E32[k * ld + o] = (float)v.E[k];
+      for (int k = 0; k < 6; ++k) rec[18 + k] = v.E[k];
+#pragma unroll
+      for (int k = 0; k < kRec; ++k) finite = finite && isfinite(rec[k]);
+      double2* d64 = reinterpret_cast<double2*>(F64 + (size_t)o * kRec);
+#pragma unroll
+      for (int k = 0; k < kRec / 2; ++k) d64[k] = make_double2(rec[2 * k], rec[2 * k + 1]);
+      if (MIXED) {
+        float4* d32 = reinterpret_cast<float4*>(F32 + (size_t)o * kRec);
+#pragma unroll
+        for (int k = 0; k < kRec / 4; ++k)
+          d32[k] = make_float4((float)rec[4 * k], (float)rec[4 * k + 1], (float)rec[4 * k + 2], (float)rec[4 * k + 3]);
       }
       if (!finite) flags[F_NONFINITE] = 1;
     }
@@ -194,14 +195,11 @@ static int lin_grid(ba_problem* P) {
 void linearize(ba_problem* P, const double* cams, const double* pts, const double* obs) {
   const size_t ld = P->ld;
   const bool mixed = P->opt.precision == BA_MIXED;
+  P->graph_epoch++;
   P->camx.ensure(sizeof(double) * kCamx * std::max(P->n_c, 1));
   P->fres.ensure(sizeof(double) * 2 * ld);
-  P->F64.ensure(sizeof(double) * 18 * ld);
-  P->E64.ensure(sizeof(double) * 6 * ld);
-  if (mixed) {
-    P->F32.ensure(sizeof(float) * 18 * ld);
-    P->E32.ensure(sizeof(float) * 6 * ld);
-  }
+  P->J64.ensure(sizeof(double) * kRec * ld);
+  if (mixed) P->J32.ensure(sizeof(float) * kRec * ld);
   // keep the linearisation point (near-nullspace and adjoint use it)
   P->cams_lin.ensure(sizeof(double) * 9 * std::max(P->n_c, 1));
   P->pts_lin.ensure(sizeof(double) * 3 * std::max(P->n_p, 1));
@@ -219,14 +217,14 @@ void linearize(ba_problem* P, const double* cams, const double* pts, const doubl
   if (mixed)
     k_linearize<true, true><<<g, kLinBS, 0, P->stream>>>(
         cams, pts, obs, P->camx.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
-        P->obs_user.as<int>(), P->n_o, ld, P->fres.as<double>(), P->F64.as<double>(),
-        P->E64.as<double>(), P->F32.as<float>(), P->E32.as<float>(), P->partial.as<double>(),
+        P->obs_user.as<int>(), P->n_o, ld, P->fres.as<double>(), P->J64.as<double>(),
+        P->J64.as<double>(), P->J32.as<float>(), P->J32.as<float>(), P->partial.as<double>(),
         P->counter.as<unsigned>(), cost, P->flags.as<int>());
   else
     k_linearize<true, false><<<g, kLinBS, 0, P->stream>>>(
         cams, pts, obs, P->camx.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
-        P->obs_user.as<int>(), P->n_o, ld, P->fres.as<double>(), P->F64.as<double>(),
-        P->E64.as<double>(), nullptr, nullptr, P->partial.as<double>(), P->counter.as<unsigned>(),
+        P->obs_user.as<int>(), P->n_o, ld, P->fres.as<double>(), P->J64.as<double>(),
+        P->J64.as<double>(), nullptr, nullptr, P->partial.as<double>(), P->counter.as<unsigned>(),
         cost, P->flags.as<int>());
   launched(P);
 }

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 
 #include "ba_internal.h"
 #include "device_util.cuh"
@@ -19,7 +20,7 @@ namespace ba {
 
 void block_inverse(ba_problem* P, const double* in, int n, int bs, double* out64, float* out32,
                    int flag_slot);
-void level_matvec(ba_problem* P, int l, const void* x, void* y);
+void level_matvec(ba_problem* P, int l, const void* x, void* y, bool ready);
 bool level_fp32(ba_problem* P);
 
 // ---------------------------------------------------------------------------
@@ -307,40 +308,69 @@ __global__ void k_strength_count(int n, const int* __restrict__ row_ptr, const i
 // Algorithm 2 (sequential greedy pass; one thread, state in shared memory when it
 // fits).  A node left unaggregated becomes a singleton aggregate afterwards.
 // ---------------------------------------------------------------------------
+// Two warps: warp 1 prefetches, for the next 32 nodes, the bounds of their strength
+// lists and their strongest neighbour into shared memory while lane 0 of warp 0 runs
+// the greedy pass over the current 32 nodes (further neighbours, rarely needed, are
+// read from global memory).
 template <bool SMEM>
-__global__ void k_aggregate(int n, const int* __restrict__ sptr, const int* __restrict__ sidx,
-                            int max_agg, int* __restrict__ agg_out, int* __restrict__ gsize,
-                            int* __restrict__ n_agg_out) {
+__global__ void __launch_bounds__(64) k_aggregate(int n, const int* __restrict__ sptr, const int* __restrict__ sidx,
+                                                  int max_agg, int* __restrict__ agg_out, int* __restrict__ gsize,
+                                                  int* __restrict__ n_agg_out) {
   extern __shared__ __align__(16) unsigned char asm_[];
+  __shared__ int pb[2][32], pe[2][32], pf[2][32];
   int* agg = SMEM ? reinterpret_cast<int*>(asm_) : agg_out;
   int* size = SMEM ? (agg + n) : gsize;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     agg[i] = -1;
     size[i] = 0;
   }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto prefetch = [&](int chunk) {
+    const int i = chunk * 32 + lane;
+    int b = 0, e = 0, f = -1;
+    if (i < n) {
+      b = sptr[i];
+      e = sptr[i + 1];
+      if (b < e) f = __ldg(sidx + b);
+    }
+    pb[chunk & 1][lane] = b;
+    pe[chunk & 1][lane] = e;
+    pf[chunk & 1][lane] = f;
+  };
+  if (warp == 1) prefetch(0);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int na = 0;
-    for (int i = 0; i < n; ++i) {
-      if (agg[i] >= 0) continue;
-      const int e1 = sptr[i + 1];
-      for (int e = sptr[i]; e < e1; ++e) {
-        const int j = __ldg(sidx + e);
-        const int k = agg[j];
-        if (k < 0) {
-          agg[i] = na;
-          agg[j] = na;
-          size[na] = 2;
-          ++na;
-          break;
-        }
-        if (size[k] < max_agg) {
-          agg[i] = k;
-          size[k] += 1;
-          break;
+  const int nchunks = (n + 31) / 32;
+  int na = 0;
+  for (int c = 0; c < nchunks; ++c) {
+    if (warp == 1 && c + 1 < nchunks) prefetch(c + 1);
+    if (threadIdx.x == 0) {
+      const int buf = c & 1;
+      for (int k = 0; k < 32; ++k) {
+        const int i = c * 32 + k;
+        if (i >= n) break;
+        if (agg[i] >= 0) continue;
+        const int e1 = pe[buf][k];
+        for (int e = pb[buf][k]; e < e1; ++e) {
+          const int j = (e == pb[buf][k]) ? pf[buf][k] : __ldg(sidx + e);
+          const int a = agg[j];
+          if (a < 0) {
+            agg[i] = na;
+            agg[j] = na;
+            size[na] = 2;
+            ++na;
+            break;
+          }
+          if (size[a] < max_agg) {
+            agg[i] = a;
+            size[a] += 1;
+            break;
+          }
         }
       }
     }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
     for (int i = 0; i < n; ++i)
       if (agg[i] < 0) agg[i] = na++;
     *n_agg_out = na;
@@ -436,6 +466,10 @@ __global__ void k_nullspace0(const double* __restrict__ cams, int n_c, double* _
 // re-orthogonalisation pass; a column whose remaining norm is <= 1e-10 of its
 // original norm is dropped (zero Q column, zero R row).  One warp per aggregate.
 // ---------------------------------------------------------------------------
+// row stride of the aggregate matrix in shared memory: 17 doubles, so the 32 rows
+// a warp touches at once fall in different banks (16 would put them all in one)
+constexpr int kQrStride = kNull + 1;
+
 __global__ void k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, const int* __restrict__ mem,
                                const double* __restrict__ K, double* __restrict__ Q64, float* __restrict__ Q32,
                                double* __restrict__ Kc, unsigned* __restrict__ kept_out) {
@@ -448,7 +482,7 @@ __global__ void k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, 
   for (int r = lane; r < rows; r += 32) {
     const int s = r / bs, u = r - s * bs;
     const double* src = K + ((size_t)mem[mb + s] * bs + u) * kNull;
-    for (int j = 0; j < kNull; ++j) A[r * kNull + j] = src[j];
+    for (int j = 0; j < kNull; ++j) A[r * kQrStride + j] = src[j];
   }
   __syncwarp();
   double R[kNull];  // column j of R is produced at step j; lane j keeps row j of R
@@ -456,7 +490,7 @@ __global__ void k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, 
   unsigned kept = 0;
   for (int j = 0; j < kNull; ++j) {
     double n0 = 0.0;
-    for (int r = lane; r < rows; r += 32) n0 += A[r * kNull + j] * A[r * kNull + j];
+    for (int r = lane; r < rows; r += 32) n0 += A[r * kQrStride + j] * A[r * kQrStride + j];
     n0 = sqrt(warp_sum(n0));
     double rcol[kNull];
     for (int i = 0; i < kNull; ++i) rcol[i] = 0.0;
@@ -464,19 +498,19 @@ __global__ void k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, 
       for (int i = 0; i < j; ++i) {
         if (!(kept >> i & 1u)) continue;
         double h = 0.0;
-        for (int r = lane; r < rows; r += 32) h += A[r * kNull + i] * A[r * kNull + j];
+        for (int r = lane; r < rows; r += 32) h += A[r * kQrStride + i] * A[r * kQrStride + j];
         h = warp_sum(h);
-        for (int r = lane; r < rows; r += 32) A[r * kNull + j] -= h * A[r * kNull + i];
+        for (int r = lane; r < rows; r += 32) A[r * kQrStride + j] -= h * A[r * kQrStride + i];
         __syncwarp();
         rcol[i] += h;
       }
     }
     double nv = 0.0;
-    for (int r = lane; r < rows; r += 32) nv += A[r * kNull + j] * A[r * kNull + j];
+    for (int r = lane; r < rows; r += 32) nv += A[r * kQrStride + j] * A[r * kQrStride + j];
     nv = sqrt(warp_sum(nv));
     const bool keep = n0 > 0.0 && nv > 1e-10 * n0;
     const double scale = keep ? 1.0 / nv : 0.0;
-    for (int r = lane; r < rows; r += 32) A[r * kNull + j] *= scale;
+    for (int r = lane; r < rows; r += 32) A[r * kQrStride + j] *= scale;
     __syncwarp();
     if (keep) {
       rcol[j] = nv;
@@ -491,8 +525,8 @@ __global__ void k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, 
     const int s = r / bs, u = r - s * bs;
     const size_t dst = ((size_t)mem[mb + s] * bs + u) * kNull;
     for (int j = 0; j < kNull; ++j) {
-      Q64[dst + j] = A[r * kNull + j];
-      Q32[dst + j] = (float)A[r * kNull + j];
+      Q64[dst + j] = A[r * kQrStride + j];
+      Q32[dst + j] = (float)A[r * kQrStride + j];
     }
   }
   if (lane < kNull)
@@ -671,7 +705,7 @@ __global__ void k_tridiag_lambda_max(const double* __restrict__ scal, int s_alph
   };
   for (int it = 0; it < 200; ++it) {
     const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
+    if (mid <= lo || mid >= hi || hi - lo <= 1e-14 * fmax(fabs(lo), fabs(hi))) break;
     if (count_below(mid) >= mm) hi = mid;
     else lo = mid;
   }
@@ -705,7 +739,7 @@ static void lanczos(ba_problem* P, int l) {
   k_scale_rsqrt<T><<<g, 256, 0, P->stream>>>(n, v, q, scal, S_TMP0);
   launched(P);
   for (int j = 0; j < m; ++j) {
-    level_matvec(P, l, q, Aq);
+    level_matvec(P, l, q, Aq, false);
     if (sizeof(T) == 8) dot64(P, (const double*)q, (const double*)Aq, n, S_LANCZOS + j);
     else dot32(P, (const float*)q, (const float*)Aq, n, S_LANCZOS + j);
     k_lanczos_w<T><<<g, 256, 0, P->stream>>>(L.n, L.bs, L.Dinv64.as<double>(), Aq, q, qprev, scal,
@@ -724,10 +758,74 @@ static void lanczos(ba_problem* P, int l) {
     k_sqrt_slot<<<1, 1, 0, P->stream>>>(scal, S_TMP1, S_LANCZOS + 8 + j);  // beta_j
     launched(P);
   }
-  L.cheb.ensure(sizeof(double) * 4);
-  k_tridiag_lambda_max<<<1, 1, 0, P->stream>>>(scal, S_LANCZOS, S_LANCZOS + 8, m, P->opt.cheb_lo,
-                                               P->opt.cheb_hi, L.cheb.as<double>());
-  launched(P);
+  // park alpha_0..7 and beta_0..7 in the level's buffer (slots 8..23); the largest Ritz
+  // value is computed on the host once every level is done (finish_lanczos)
+  L.cheb.ensure(sizeof(double) * kChebSlots);
+  BA_CUDA(cudaMemcpyAsync(L.cheb.as<double>() + 8, scal + S_LANCZOS, sizeof(double) * 16, cudaMemcpyDeviceToDevice,
+                          P->stream));
+}
+
+// Largest eigenvalue of the symmetric tridiagonal (alpha[0..m), beta[0..m-1)) by bisection
+// with Sturm counts (host); returns the Chebyshev parameters {theta, delta, sigma_1, lam}.
+static void tridiag_cheb(const double* al_in, const double* be_in, int m, double lo_f, double hi_f, double out[4]) {
+  double al[16], be[16];
+  int mm = m;
+  for (int j = 0; j < m; ++j) al[j] = al_in[j];
+  for (int j = 0; j + 1 < m; ++j) {
+    be[j] = be_in[j];
+    if (!(be[j] > 0.0)) {  // invariant subspace found: truncate
+      mm = j + 1;
+      break;
+    }
+  }
+  double lo = al[0], hi = al[0];
+  for (int j = 0; j < mm; ++j) {
+    const double rad = (j > 0 ? std::fabs(be[j - 1]) : 0.0) + (j + 1 < mm ? std::fabs(be[j]) : 0.0);
+    lo = std::min(lo, al[j] - rad);
+    hi = std::max(hi, al[j] + rad);
+  }
+  auto count_below = [&](double x) {
+    int c = 0;
+    double d = al[0] - x;
+    if (d < 0) ++c;
+    for (int j = 1; j < mm; ++j) {
+      const double prev = (d == 0.0) ? 1e-300 : d;
+      d = (al[j] - x) - be[j - 1] * be[j - 1] / prev;
+      if (d < 0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (count_below(mid) >= mm) hi = mid;
+    else lo = mid;
+  }
+  const double lam = hi;
+  const double a = lo_f * lam, b = hi_f * lam;
+  out[0] = 0.5 * (b + a);
+  out[1] = 0.5 * (b - a);
+  out[2] = out[0] / out[1];
+  out[3] = lam;
+}
+
+// Ritz values of every smoothed level (one synchronisation for all levels) and their
+// Chebyshev parameters written back to the devices' level buffers.
+static void finish_lanczos(ba_problem* P) {
+  const int nl = P->n_levels - 1;
+  if (nl <= 0) return;
+  double* h = P->h_cheb;
+  for (int k = 0; k < nl; ++k)
+    BA_CUDA(cudaMemcpyAsync(h + kChebSlots * k, P->levels[k].cheb.p, sizeof(double) * kChebSlots,
+                            cudaMemcpyDeviceToHost, P->stream));
+  sync(P);
+  const int m = std::min(std::max(P->opt.lanczos_steps, 1), 8);
+  for (int k = 0; k < nl; ++k) {
+    double* c = h + kChebSlots * k;
+    tridiag_cheb(c + 8, c + 16, m, P->opt.cheb_lo, P->opt.cheb_hi, c);
+    P->levels[k].lam_max = c[3];
+    BA_CUDA(cudaMemcpyAsync(P->levels[k].cheb.p, c, sizeof(double) * 4, cudaMemcpyHostToDevice, P->stream));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -878,30 +976,31 @@ static void dense_inverse(ba_problem* P, Level& L) {
 
 // ---------------------------------------------------------------------------
 // orchestration
+//
+// The symbolic hierarchy (covisibility counts and block patterns of every level,
+// strength orderings, Algorithm 2 aggregates and their member lists) depends only on
+// the observation graph, so it is built on the first call and reused by every later
+// LM step; each call recomputes only the numerical parts (level-0 blocks, the
+// near-nullspace at the current cameras, QR prolongators, Galerkin products,
+// smoother blocks, Lanczos estimates and the coarsest inverse).
 // ---------------------------------------------------------------------------
-void mg_setup(ba_problem* P) {
-  const bool fp32 = level_fp32(P);
+static int max_row_length(ba_problem* P, const Level& L) {
+  std::vector<int> hptr(L.n + 1);
+  BA_CUDA(cudaMemcpyAsync(hptr.data(), L.row_ptr.p, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost, P->stream));
+  sync(P);
+  int maxrow = 1;
+  for (int i = 0; i < L.n; ++i) maxrow = std::max(maxrow, hptr[i + 1] - hptr[i]);
+  return maxrow;
+}
+
+static void mg_symbolic(ba_problem* P) {
   const ba_options& o = P->opt;
-  clear_flags(P);
   if ((int)P->levels.size() < 1) P->levels.resize(1);
   Level& L0 = P->levels[0];
   covisibility_level0(P, L0);
   L0.n = P->n_c;
   L0.bs = 9;
-  explicit_schur(P, L0, fp32);
-  // level-0 smoother blocks: S_cc from the Schur setup
-  L0.Dblk.ensure(sizeof(double) * 81 * (size_t)P->n_c + 64);
-  L0.Dinv64.ensure(sizeof(double) * 81 * (size_t)P->n_c + 64);
-  L0.Dinv32.ensure(sizeof(float) * 81 * (size_t)P->n_c + 64);
-  BA_CUDA(cudaMemcpyAsync(L0.Dblk.p, P->Scc.p, sizeof(double) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
-  BA_CUDA(cudaMemcpyAsync(L0.Dinv64.p, P->Scc_inv.p, sizeof(double) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
-  BA_CUDA(cudaMemcpyAsync(L0.Dinv32.p, P->Scc_inv32.p, sizeof(float) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
-  L0.K.ensure(sizeof(double) * 9 * kNull * (size_t)P->n_c + 64);
-  k_nullspace0<<<cdiv(P->n_c, 128), 128, 0, P->stream>>>(P->cams_lin.as<double>(), P->n_c, L0.K.as<double>());
-  launched(P);
-  L0.kept.ensure(sizeof(unsigned) * P->n_c + 64);
-  BA_CUDA(cudaMemsetAsync(L0.kept.p, 0xff, sizeof(unsigned) * P->n_c, P->stream));
-
+  L0.maxrow = max_row_length(P, L0);
   int l = 0;
   while (true) {
     Level& L = P->levels[l];
@@ -922,14 +1021,8 @@ void mg_setup(ba_problem* P) {
       k_diag_w<<<cdiv(L.n, 128), 128, 0, P->stream>>>(L.n, L.row_ptr.as<int>(), L.cols.as<int>(),
                                                      L.W.as<long long>(), Wd);
       launched(P);
-      // max row length for the sort buffer
-      std::vector<int> hptr(L.n + 1);
-      BA_CUDA(cudaMemcpyAsync(hptr.data(), L.row_ptr.p, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost, P->stream));
-      sync(P);
-      int maxrow = 1;
-      for (int i = 0; i < L.n; ++i) maxrow = std::max(maxrow, hptr[i + 1] - hptr[i]);
       int mpow = 1;
-      while (mpow < maxrow) mpow <<= 1;
+      while (mpow < L.maxrow) mpow <<= 1;
       const size_t ssm = sizeof(StrengthKey) * mpow;
       BA_REQUIRE(ssm <= 200 * 1024, BA_ERR_LIMIT, "too many covisible neighbours for the strength sort");
       BA_CUDA(cudaFuncSetAttribute(k_strength_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm));
@@ -944,10 +1037,10 @@ void mg_setup(ba_problem* P) {
       const size_t asmem = sizeof(int) * 2 * (size_t)L.n;
       if (asmem <= 160 * 1024) {
         BA_CUDA(cudaFuncSetAttribute(k_aggregate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asmem));
-        k_aggregate<true><<<1, 256, asmem, P->stream>>>(L.n, L.sptr.as<int>(), L.sidx.as<int>(), o.max_agg,
+        k_aggregate<true><<<1, 64, asmem, P->stream>>>(L.n, L.sptr.as<int>(), L.sidx.as<int>(), o.max_agg,
                                                         L.agg.as<int>(), gsize, d_nagg);
       } else {
-        k_aggregate<false><<<1, 256, 0, P->stream>>>(L.n, L.sptr.as<int>(), L.sidx.as<int>(), o.max_agg,
+        k_aggregate<false><<<1, 64, 0, P->stream>>>(L.n, L.sptr.as<int>(), L.sidx.as<int>(), o.max_agg,
                                                      L.agg.as<int>(), gsize, d_nagg);
       }
       launched(P);
@@ -957,26 +1050,8 @@ void mg_setup(ba_problem* P) {
     }
     if (coarsest) {
       L.coarsest = true;
-      dense_inverse(P, L);
-      check_flags(P);
       break;
     }
-    // smoother for this level
-    if (l > 0) {
-      L.Dblk.ensure(sizeof(double) * L.bs * L.bs * (size_t)L.n + 64);
-      L.Dinv64.ensure(sizeof(double) * L.bs * L.bs * (size_t)L.n + 64);
-      L.Dinv32.ensure(sizeof(float) * L.bs * L.bs * (size_t)L.n + 64);
-      if (fp32)
-        k_extract_diag<float><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
-                                                          L.vals32.as<float>(), L.Dblk.as<double>());
-      else
-        k_extract_diag<double><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
-                                                           L.vals64.as<double>(), L.Dblk.as<double>());
-      launched(P);
-      block_inverse(P, L.Dblk.as<double>(), L.n, L.bs, L.Dinv64.as<double>(), L.Dinv32.as<float>(), F_NOT_SPD_JACOBI);
-    }
-    if (fp32) lanczos<float>(P, l);
-    else lanczos<double>(P, l);
     // members of each aggregate
     L.agg_ptr.ensure(sizeof(int) * ((size_t)L.n_agg + 1));
     L.agg_mem.ensure(sizeof(int) * (size_t)L.n + 64);
@@ -992,56 +1067,100 @@ void mg_setup(ba_problem* P) {
     launched(P);
     k_sort_members<<<cdiv(L.n_agg, 128), 128, 0, P->stream>>>(L.n_agg, L.agg_ptr.as<int>(), L.agg_mem.as<int>());
     launched(P);
-    // next level
+    // next level's pattern and covisibility W_{l+1} = Agg^T W_l Agg
     if ((int)P->levels.size() < l + 2) P->levels.resize(l + 2);
     Level& L1 = P->levels[l + 1];
-    Level& Lc = P->levels[l];  // re-take reference after resize
+    Level& Lc = P->levels[l];
     L1.n = Lc.n_agg;
     L1.bs = kNull;
-    // QR prolongators, coarse nullspace and kept masks
-    Lc.Q64.ensure(sizeof(double) * Lc.bs * kNull * (size_t)Lc.n + 64);
-    Lc.Q32.ensure(sizeof(float) * Lc.bs * kNull * (size_t)Lc.n + 64);
-    L1.K.ensure(sizeof(double) * kNull * kNull * (size_t)L1.n + 64);
-    L1.kept.ensure(sizeof(unsigned) * (size_t)L1.n + 64);
-    const size_t qsm = sizeof(double) * (size_t)o.max_agg * Lc.bs * kNull;
-    BA_REQUIRE(qsm <= 200 * 1024, BA_ERR_LIMIT, "max_agg too large for the aggregate QR");
-    BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
-    k_aggregate_qr<<<L1.n, 32, qsm, P->stream>>>(L1.n, Lc.bs, Lc.agg_ptr.as<int>(), Lc.agg_mem.as<int>(),
-                                                Lc.K.as<double>(), Lc.Q64.as<double>(), Lc.Q32.as<float>(),
-                                                L1.K.as<double>(), L1.kept.as<unsigned>());
-    launched(P);
-    // coarse pattern and covisibility W_{l+1} = Agg^T W_l Agg
     const int H = hash_size(std::min(L1.n, 4096));
     row_hash<1>(P, L1.n, H, Lc.agg_ptr.as<int>(), Lc.agg_mem.as<int>(), Lc.row_ptr.as<int>(), Lc.cols.as<int>(),
                 Lc.agg.as<int>(), Lc.W.as<long long>(), L1);
+    L1.maxrow = max_row_length(P, L1);
+    ++l;
+  }
+  P->n_levels = l + 1;
+  P->sym_ready = true;
+}
+
+void mg_setup(ba_problem* P) {
+  const bool fp32 = level_fp32(P);
+  const ba_options& o = P->opt;
+  P->graph_epoch++;
+  clear_flags(P);
+  if (!P->sym_ready) mg_symbolic(P);
+  Level& L0 = P->levels[0];
+  explicit_schur(P, L0, fp32);
+  // level-0 smoother blocks: S_cc from the Schur setup
+  L0.Dblk.ensure(sizeof(double) * 81 * (size_t)P->n_c + 64);
+  L0.Dinv64.ensure(sizeof(double) * 81 * (size_t)P->n_c + 64);
+  L0.Dinv32.ensure(sizeof(float) * 81 * (size_t)P->n_c + 64);
+  BA_CUDA(cudaMemcpyAsync(L0.Dblk.p, P->Scc.p, sizeof(double) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
+  BA_CUDA(cudaMemcpyAsync(L0.Dinv64.p, P->Scc_inv.p, sizeof(double) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
+  BA_CUDA(cudaMemcpyAsync(L0.Dinv32.p, P->Scc_inv32.p, sizeof(float) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
+  L0.K.ensure(sizeof(double) * 9 * kNull * (size_t)P->n_c + 64);
+  k_nullspace0<<<cdiv(P->n_c, 128), 128, 0, P->stream>>>(P->cams_lin.as<double>(), P->n_c, L0.K.as<double>());
+  launched(P);
+  L0.kept.ensure(sizeof(unsigned) * P->n_c + 64);
+  BA_CUDA(cudaMemsetAsync(L0.kept.p, 0xff, sizeof(unsigned) * P->n_c, P->stream));
+
+  for (int l = 0; l < P->n_levels; ++l) {
+    Level& L = P->levels[l];
+    if (l > 0) {
+      L.Dblk.ensure(sizeof(double) * L.bs * L.bs * (size_t)L.n + 64);
+      L.Dinv64.ensure(sizeof(double) * L.bs * L.bs * (size_t)L.n + 64);
+      L.Dinv32.ensure(sizeof(float) * L.bs * L.bs * (size_t)L.n + 64);
+    }
+    if (L.coarsest) {
+      dense_inverse(P, L);
+      break;
+    }
+    // smoother for this level
+    if (l > 0) {
+      if (fp32)
+        k_extract_diag<float><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                          L.vals32.as<float>(), L.Dblk.as<double>());
+      else
+        k_extract_diag<double><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                           L.vals64.as<double>(), L.Dblk.as<double>());
+      launched(P);
+      block_inverse(P, L.Dblk.as<double>(), L.n, L.bs, L.Dinv64.as<double>(), L.Dinv32.as<float>(), F_NOT_SPD_JACOBI);
+    }
+    if (fp32) lanczos<float>(P, l);
+    else lanczos<double>(P, l);
+    Level& L1 = P->levels[l + 1];
+    // QR prolongators, coarse nullspace and kept masks
+    L.Q64.ensure(sizeof(double) * L.bs * kNull * (size_t)L.n + 64);
+    L.Q32.ensure(sizeof(float) * L.bs * kNull * (size_t)L.n + 64);
+    L1.K.ensure(sizeof(double) * kNull * kNull * (size_t)L1.n + 64);
+    L1.kept.ensure(sizeof(unsigned) * (size_t)L1.n + 64);
+    const size_t qsm = sizeof(double) * (size_t)o.max_agg * L.bs * kQrStride;
+    BA_REQUIRE(qsm <= 200 * 1024, BA_ERR_LIMIT, "max_agg too large for the aggregate QR");
+    BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
+    k_aggregate_qr<<<L1.n, 32, qsm, P->stream>>>(L1.n, L.bs, L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
+                                                L.K.as<double>(), L.Q64.as<double>(), L.Q32.as<float>(),
+                                                L1.K.as<double>(), L1.kept.as<unsigned>());
+    launched(P);
     // Galerkin
     if (fp32) {
       L1.vals32.ensure(sizeof(float) * 256 * (size_t)L1.nnzb + 64);
-      k_galerkin<float><<<L1.n, kGalBS, 0, P->stream>>>(Lc.bs, Lc.row_ptr.as<int>(), Lc.cols.as<int>(),
-                                                        Lc.vals32.as<float>(), Lc.Q32.as<float>(), Lc.agg.as<int>(),
-                                                        Lc.agg_ptr.as<int>(), Lc.agg_mem.as<int>(),
+      k_galerkin<float><<<L1.n, kGalBS, 0, P->stream>>>(L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                        L.vals32.as<float>(), L.Q32.as<float>(), L.agg.as<int>(),
+                                                        L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
                                                         L1.row_ptr.as<int>(), L1.cols.as<int>(),
                                                         L1.kept.as<unsigned>(), L1.vals32.as<float>());
     } else {
       L1.vals64.ensure(sizeof(double) * 256 * (size_t)L1.nnzb + 64);
-      k_galerkin<double><<<L1.n, kGalBS, 0, P->stream>>>(Lc.bs, Lc.row_ptr.as<int>(), Lc.cols.as<int>(),
-                                                         Lc.vals64.as<double>(), Lc.Q64.as<double>(), Lc.agg.as<int>(),
-                                                         Lc.agg_ptr.as<int>(), Lc.agg_mem.as<int>(),
+      k_galerkin<double><<<L1.n, kGalBS, 0, P->stream>>>(L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                         L.vals64.as<double>(), L.Q64.as<double>(), L.agg.as<int>(),
+                                                         L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
                                                          L1.row_ptr.as<int>(), L1.cols.as<int>(),
                                                          L1.kept.as<unsigned>(), L1.vals64.as<double>());
     }
     launched(P);
-    check_flags(P);
-    ++l;
   }
-  P->n_levels = l + 1;
-  // host copies of lambda_max
-  for (int k = 0; k + 1 < P->n_levels; ++k) {
-    double c[4];
-    BA_CUDA(cudaMemcpyAsync(c, P->levels[k].cheb.p, sizeof(c), cudaMemcpyDeviceToHost, P->stream));
-    sync(P);
-    P->levels[k].lam_max = c[3];
-  }
+  finish_lanczos(P);
+  check_flags(P);
   // V-cycle work vectors
   for (int k = 0; k < P->n_levels; ++k) {
     Level& L = P->levels[k];

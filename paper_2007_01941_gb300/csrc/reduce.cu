@@ -61,6 +61,8 @@ static cudaEvent_t take_event(ba_problem* P) {
 
 KernelTimer::KernelTimer(ba_problem* p, int c) : P(p), cls(c) {
   if (!P->ktime) return;
+  cudaStreamCaptureStatus st;
+  if (cudaStreamIsCapturing(P->stream, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone) return;
   a = take_event(P);
   b = take_event(P);
   cudaEventRecord(a, P->stream);

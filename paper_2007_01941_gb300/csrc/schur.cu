@@ -23,9 +23,9 @@ __global__ void k_point_setup(const double* __restrict__ E, const double* __rest
   double c00 = 0, c01 = 0, c02 = 0, c11 = 0, c12 = 0, c22 = 0, g0 = 0, g1 = 0, g2 = 0;
   const int b = pt_ptr[ip], e = pt_ptr[ip + 1];
   for (int o = b; o < e; ++o) {
-    const double a0 = E[o], a1 = E[ld + o], a2 = E[2 * ld + o];
-    const double b0 = E[3 * ld + o], b1 = E[4 * ld + o], b2 = E[5 * ld + o];
-    const double f0 = fres[o], f1 = fres[ld + o];
+    const double a0 = JE(E, o, 0), a1 = JE(E, o, 1), a2 = JE(E, o, 2);
+    const double b0 = JE(E, o, 3), b1 = JE(E, o, 4), b2 = JE(E, o, 5);
+    const double f0 = fres[2 * (size_t)o], f1 = fres[2 * (size_t)o + 1];
     c00 += a0 * a0 + b0 * b0;
     c01 += a0 * a1 + b0 * b1;
     c02 += a0 * a2 + b0 * b2;
@@ -88,13 +88,13 @@ __global__ void k_camera_setup(const double* __restrict__ F, const double* __res
   for (int i = cam_ptr[c] + lane; i < cam_ptr[c + 1]; i += 32) {
     const int o = cam_obs[i];
     const int ip = obs_pt[o];
-    const double f0 = fres[o], f1 = fres[ld + o];
+    const double f0 = fres[2 * (size_t)o], f1 = fres[2 * (size_t)o + 1];
     const double w0 = wp[ip], w1 = wp[ldp + ip], w2 = wp[2 * ldp + ip];
-    const double h0 = f0 + E[o] * w0 + E[ld + o] * w1 + E[2 * ld + o] * w2;
-    const double h1 = f1 + E[3 * ld + o] * w0 + E[4 * ld + o] * w1 + E[5 * ld + o] * w2;
+    const double h0 = f0 + JE(E, o, 0) * w0 + JE(E, o, 1) * w1 + JE(E, o, 2) * w2;
+    const double h1 = f1 + JE(E, o, 3) * w0 + JE(E, o, 4) * w1 + JE(E, o, 5) * w2;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      const double a = F[k * ld + o], b = F[(9 + k) * ld + o];
+      const double a = JF(F, o, k), b = JF(F, o, 9 + k);
       dg[k] += a * a + b * b;
       g[k] -= a * f0 + b * f1;
       bb[k] -= a * h0 + b * h1;
@@ -137,11 +137,11 @@ __global__ void k_scc(const T* __restrict__ F, const T* __restrict__ E, size_t l
     const int ip = obs_pt[o];
     T e[6], ci[6], f[18];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) e[k] = E[k * ld + o];
+    for (int k = 0; k < 6; ++k) e[k] = JE(E, o, k);
 #pragma unroll
     for (int k = 0; k < 6; ++k) ci[k] = Cinv[k * ldp + ip];
 #pragma unroll
-    for (int k = 0; k < 18; ++k) f[k] = F[k * ld + o];
+    for (int k = 0; k < 18; ++k) f[k] = JF(F, o, k);
     // Y = E C^-1 (2x3)
     T y0[3], y1[3];
     y0[0] = e[0] * ci[0] + e[1] * ci[1] + e[2] * ci[2];
@@ -196,13 +196,65 @@ __global__ void k_block_inverse(const double* __restrict__ in, int n, double* __
   }
 }
 
+// inverse of SPD blocks, one warp per block: Gauss-Jordan elimination without pivoting
+// (the pivots of an SPD matrix are its positive Schur-complement diagonals); each
+// lane owns BS*BS/32 entries, every step reads the old pivot row and column before
+// any lane writes.  A non-positive pivot raises the flag and zeroes the block.
+template <int BS>
+__global__ void __launch_bounds__(256) k_block_inverse_warp(const double* __restrict__ in, int n,
+                                                            double* __restrict__ out64, float* __restrict__ out32,
+                                                            int* flags, int flag_slot) {
+  constexpr int PER = (BS * BS + 31) / 32;
+  __shared__ double sa[8][BS * BS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int blk = blockIdx.x * 8 + warp;
+  if (blk >= n) return;
+  double* a = sa[warp];
+  const double* src = in + (size_t)blk * BS * BS;
+  for (int e = lane; e < BS * BS; e += 32) a[e] = src[e];
+  __syncwarp();
+  bool ok = true;
+  for (int k = 0; k < BS; ++k) {
+    const double p = a[k * BS + k];
+    if (!(p > 0.0)) ok = false;
+    const double ip = 1.0 / p;
+    double nv[PER];
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int e = lane + 32 * t;
+      if (e < BS * BS) {
+        const int i = e / BS, j = e - (e / BS) * BS;
+        double v;
+        if (i == k && j == k) v = ip;
+        else if (i == k) v = a[k * BS + j] * ip;
+        else if (j == k) v = -a[i * BS + k] * ip;
+        else v = a[e] - a[i * BS + k] * a[k * BS + j] * ip;
+        nv[t] = v;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int e = lane + 32 * t;
+      if (e < BS * BS) a[e] = nv[t];
+    }
+    __syncwarp();
+  }
+  if (!ok && lane == 0) flags[flag_slot] = 1;
+  for (int e = lane; e < BS * BS; e += 32) {
+    const double v = ok ? 0.5 * (a[e] + a[(e % BS) * BS + e / BS]) : 0.0;  // symmetrise
+    out64[(size_t)blk * BS * BS + e] = v;
+    if (out32) out32[(size_t)blk * BS * BS + e] = (float)v;
+  }
+}
+
 void block_inverse(ba_problem* P, const double* in, int n, int bs, double* out64, float* out32,
                    int flag_slot) {
   if (n == 0) return;
   if (bs == 9)
-    k_block_inverse<9><<<cdiv(n, 64), 64, 0, P->stream>>>(in, n, out64, out32, P->flags.as<int>(), flag_slot);
+    k_block_inverse_warp<9><<<cdiv(n, 8), 256, 0, P->stream>>>(in, n, out64, out32, P->flags.as<int>(), flag_slot);
   else
-    k_block_inverse<16><<<cdiv(n, 64), 64, 0, P->stream>>>(in, n, out64, out32, P->flags.as<int>(), flag_slot);
+    k_block_inverse_warp<16><<<cdiv(n, 8), 256, 0, P->stream>>>(in, n, out64, out32, P->flags.as<int>(), flag_slot);
   launched(P);
 }
 
@@ -211,6 +263,7 @@ void schur_setup(ba_problem* P, double lambda) {
   const int n_c = P->n_c, n_p = P->n_p;
   const size_t ldp = P->ldp;
   P->lambda = lambda;
+  P->graph_epoch++;
   P->Dc.ensure(sizeof(double) * 9 * n_c + 64);
   P->Dc32.ensure(sizeof(float) * 9 * n_c + 64);
   P->Dp.ensure(sizeof(double) * 3 * ldp);
@@ -227,14 +280,14 @@ void schur_setup(ba_problem* P, double lambda) {
   const int damp_id = P->opt.damping == BA_DAMP_IDENTITY;
   if (n_p) {
     k_point_setup<<<cdiv(n_p, 128), 128, 0, P->stream>>>(
-        P->E64.as<double>(), P->fres.as<double>(), P->ld, P->pt_ptr.as<int>(), n_p, P->n_p_obs, ldp,
+        P->J64.as<double>(), P->fres.as<double>(), P->ld, P->pt_ptr.as<int>(), n_p, P->n_p_obs, ldp,
         lambda, damp_id, P->Dp.as<double>(), P->Cinv64.as<double>(),
         mixed ? P->Cinv32.as<float>() : nullptr, P->gp.as<double>(), P->wp.as<double>(),
         P->flags.as<int>());
     launched(P);
   }
   k_camera_setup<<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
-      P->F64.as<double>(), P->E64.as<double>(), P->fres.as<double>(), P->ld, P->cam_ptr.as<int>(),
+      P->J64.as<double>(), P->J64.as<double>(), P->fres.as<double>(), P->ld, P->cam_ptr.as<int>(),
       P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->wp.as<double>(), ldp, n_c, lambda, damp_id,
       P->Dc.as<double>(), P->Dc32.as<float>(), P->gc.as<double>(), P->rhs.as<double>());
   launched(P);
@@ -242,11 +295,11 @@ void schur_setup(ba_problem* P, double lambda) {
   double* Scc = P->Scc.as<double>();
   if (mixed)
     k_scc<float><<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
-        P->F32.as<float>(), P->E32.as<float>(), P->ld, P->Cinv32.as<float>(), ldp, P->cam_ptr.as<int>(),
+        P->J32.as<float>(), P->J32.as<float>(), P->ld, P->Cinv32.as<float>(), ldp, P->cam_ptr.as<int>(),
         P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->Dc.as<double>(), n_c, Scc);
   else
     k_scc<double><<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
-        P->F64.as<double>(), P->E64.as<double>(), P->ld, P->Cinv64.as<double>(), ldp,
+        P->J64.as<double>(), P->J64.as<double>(), P->ld, P->Cinv64.as<double>(), ldp,
         P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->Dc.as<double>(), n_c, Scc);
   launched(P);
   block_inverse(P, Scc, n_c, 9, P->Scc_inv.as<double>(), P->Scc_inv32.as<float>(), F_NOT_SPD_JACOBI);
@@ -256,83 +309,82 @@ void schur_setup(ba_problem* P, double lambda) {
 // ---------------------------------------------------------------------------
 // K3: implicit Schur product.  One CTA per chunk of consecutive warp tiles; a warp
 // tile is a run of whole points with <= 32 observations (a point with more is a
-// tile of its own and is processed in 32-observation passes).  Lane l of a warp
-// handles observation ob + l:
+// tile of its own and is processed in 32-observation passes), described by one
+// int4 {first observation, count, first point, mask of lanes that start a point}.
+// Lane l of a warp handles observation ob + l:
 //   u_o = F_o x_c ; t_o = E_o^T u_o ; v_p = sum_{o in p} t_o (segmented warp scan)
 //   z_p = C_p^-1 v_p ; w_o = u_o - E_o z_p ; y_c += F_o^T w_o
-// The camera sums y_c go to a shared-memory window of the chunk's cameras
-// (points are ordered by their first camera, so a chunk touches a narrow camera
-// range) and are flushed once per CTA; cameras outside the window go straight to
-// global memory.  y must hold D_c x on entry.
+// Camera sums: with WINDOW (FP32) they go to a shared-memory window of the chunk's
+// cameras (points are ordered by their first camera, so a chunk touches a narrow
+// camera range), flushed once per CTA, and cameras outside the window go straight
+// to global memory; without WINDOW (FP64, whose shared-memory atomics are slow
+// compare-and-swap loops on this GPU) every contribution is a global L2 atomic.
+// y must hold D_c x on entry.
 // ---------------------------------------------------------------------------
 constexpr int kK3Warps = 8;
 
-template <typename T>
+template <typename T, bool WINDOW>
 __device__ __forceinline__ void k3_scatter(T* acc, T* __restrict__ y, int c, int cam_lo, int span,
                                            const T yv[9]) {
   const int rel = c - cam_lo;
-  if (rel < span) {
+  if (WINDOW && rel < span) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) atomicAdd(acc + 9 * rel + k, yv[k]);
   } else {
+    T* yc = y + 9 * (size_t)c;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) atomicAdd(y + 9 * (size_t)c + k, yv[k]);
+    for (int k = 0; k < 9; ++k) atomicAdd(yc + k, yv[k]);
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kK3Warps * 32)
-k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, size_t ld,
-               const T* __restrict__ Cinv, size_t ldp, const int* __restrict__ obs_cam,
-               const int* __restrict__ pt_ptr, const int* __restrict__ tile_pt,
-               const int* __restrict__ chunk_tile, const int* __restrict__ chunk_cam,
-               const T* __restrict__ x, T* __restrict__ y, int win) {
+template <typename T, bool WINDOW>
+__global__ void __launch_bounds__(kK3Warps * 32, 3)
+k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, int ld,
+               const T* __restrict__ Cinv, int ldp, const int* __restrict__ obs_cam,
+               const int4* __restrict__ tile_desc, const int* __restrict__ chunk_tile,
+               const int* __restrict__ chunk_cam, const T* __restrict__ x, T* __restrict__ y, int win,
+               int reverse) {
   extern __shared__ __align__(16) unsigned char k3_smem[];
   T* acc = reinterpret_cast<T*>(k3_smem);
   const int chunk = blockIdx.x;
   const int cam_lo = chunk_cam[2 * chunk];
   const int cam_hi = chunk_cam[2 * chunk + 1];
-  const int span = min(cam_hi - cam_lo + 1, win);
-  for (int i = threadIdx.x; i < span * 9; i += blockDim.x) acc[i] = T(0);
-  __syncthreads();
+  const int span = WINDOW ? min(cam_hi - cam_lo + 1, win) : 0;
+  if (WINDOW) {
+    for (int i = threadIdx.x; i < span * 9; i += blockDim.x) acc[i] = T(0);
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int t_end = chunk_tile[chunk + 1];
-  for (int t = chunk_tile[chunk] + warp; t < t_end; t += kK3Warps) {
-    const int p0 = tile_pt[t], p1 = tile_pt[t + 1];
-    const int ob = pt_ptr[p0];
-    const int nobs = pt_ptr[p1] - ob;
+  // reverse != 0 walks the chunk's tiles from its end, where the previous product left
+  // the most recently used lines in L2
+  const int t_begin = chunk_tile[chunk], t_end = chunk_tile[chunk + 1];
+  for (int i = warp; i < t_end - t_begin; i += kK3Warps) {
+    const int t = reverse ? t_end - 1 - i : t_begin + i;
+    const int4 desc = __ldg(tile_desc + t);
+    const int ob = desc.x, nobs = desc.y, p0 = desc.z;
     if (nobs <= 32) {
-      const int np = p1 - p0;
-      const int sj = (lane < np) ? (pt_ptr[p0 + lane] - ob) : 0;
-      const unsigned startmask = __reduce_or_sync(kFull, (lane < np) ? (1u << sj) : 0u);
+      const unsigned startmask = (unsigned)desc.w;
       const bool active = lane < nobs;
       const unsigned le = (lane == 31) ? kFull : ((2u << lane) - 1u);
       const int seg_head = 31 - __clz(startmask & le);
       const unsigned after = startmask & ~le;
       const int seg_end = active ? (after ? (__ffs(after) - 2) : (nobs - 1)) : lane;
       const int ip = p0 + __popc(startmask & le) - 1;
-      const int o = ob + lane;
+      const int o = active ? ob + lane : ob;
+      const int c = __ldg(obs_cam + o);
       T f[18], e[6];
+      load_record(F + (size_t)o * kRec, f, e);
+      const T* xc = x + 9 * (size_t)c;
       T u0 = T(0), u1 = T(0);
-      int c = 0;
-      if (active) {
-        c = obs_cam[o];
 #pragma unroll
-        for (int k = 0; k < 18; ++k) f[k] = F[k * ld + o];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) e[k] = E[k * ld + o];
-        const T* xc = x + 9 * (size_t)c;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          const T xv = xc[k];
-          u0 += f[k] * xv;
-          u1 += f[9 + k] * xv;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 18; ++k) f[k] = T(0);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) e[k] = T(0);
+      for (int k = 0; k < 9; ++k) {
+        const T xv = __ldg(xc + k);
+        u0 += f[k] * xv;
+        u1 += f[9 + k] * xv;
+      }
+      if (!active) {
+        u0 = T(0);
+        u1 = T(0);
       }
       T s0 = e[0] * u0 + e[3] * u1;
       T s1 = e[1] * u0 + e[4] * u1;
@@ -352,8 +404,9 @@ k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, size_t ld,
       const T v1 = __shfl_sync(kFull, s1, seg_head);
       const T v2 = __shfl_sync(kFull, s2, seg_head);
       if (active) {
-        const T c00 = Cinv[ip], c01 = Cinv[ldp + ip], c02 = Cinv[2 * ldp + ip];
-        const T c11 = Cinv[3 * ldp + ip], c12 = Cinv[4 * ldp + ip], c22 = Cinv[5 * ldp + ip];
+        const T* Ci = Cinv + ip;
+        const T c00 = __ldg(Ci), c01 = __ldg(Ci + ldp), c02 = __ldg(Ci + 2 * ldp);
+        const T c11 = __ldg(Ci + 3 * ldp), c12 = __ldg(Ci + 4 * ldp), c22 = __ldg(Ci + 5 * ldp);
         const T z0 = c00 * v0 + c01 * v1 + c02 * v2;
         const T z1 = c01 * v0 + c11 * v1 + c12 * v2;
         const T z2 = c02 * v0 + c12 * v1 + c22 * v2;
@@ -362,7 +415,7 @@ k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, size_t ld,
         T yv[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) yv[k] = f[k] * w0 + f[9 + k] * w1;
-        k3_scatter(acc, y, c, cam_lo, span, yv);
+        k3_scatter<T, WINDOW>(acc, y, c, cam_lo, span, yv);
       }
     } else {
       // one point with more than 32 observations
@@ -376,12 +429,12 @@ k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, size_t ld,
           T u0 = T(0), u1 = T(0);
 #pragma unroll
           for (int k = 0; k < 9; ++k) {
-            u0 += F[k * ld + o] * xc[k];
-            u1 += F[(9 + k) * ld + o] * xc[k];
+            u0 += JF(F, o, k) * xc[k];
+            u1 += JF(F, o, 9 + k) * xc[k];
           }
-          s0 += E[o] * u0 + E[3 * ld + o] * u1;
-          s1 += E[ld + o] * u0 + E[4 * ld + o] * u1;
-          s2 += E[2 * ld + o] * u0 + E[5 * ld + o] * u1;
+          s0 += JE(E, o, 0) * u0 + JE(E, o, 3) * u1;
+          s1 += JE(E, o, 1) * u0 + JE(E, o, 4) * u1;
+          s2 += JE(E, o, 2) * u0 + JE(E, o, 5) * u1;
         }
       }
       s0 = warp_sum(s0);
@@ -399,28 +452,30 @@ k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, size_t ld,
           const T* xc = x + 9 * (size_t)c;
           T f[18];
 #pragma unroll
-          for (int k = 0; k < 18; ++k) f[k] = F[k * ld + o];
+          for (int k = 0; k < 18; ++k) f[k] = JF(F, o, k);
           T u0 = T(0), u1 = T(0);
 #pragma unroll
           for (int k = 0; k < 9; ++k) {
             u0 += f[k] * xc[k];
             u1 += f[9 + k] * xc[k];
           }
-          const T w0 = u0 - (E[o] * z0 + E[ld + o] * z1 + E[2 * ld + o] * z2);
-          const T w1 = u1 - (E[3 * ld + o] * z0 + E[4 * ld + o] * z1 + E[5 * ld + o] * z2);
+          const T w0 = u0 - (JE(E, o, 0) * z0 + JE(E, o, 1) * z1 + JE(E, o, 2) * z2);
+          const T w1 = u1 - (JE(E, o, 3) * z0 + JE(E, o, 4) * z1 + JE(E, o, 5) * z2);
           T yv[9];
 #pragma unroll
           for (int k = 0; k < 9; ++k) yv[k] = f[k] * w0 + f[9 + k] * w1;
-          k3_scatter(acc, y, c, cam_lo, span, yv);
+          k3_scatter<T, WINDOW>(acc, y, c, cam_lo, span, yv);
         }
       }
     }
   }
-  __syncthreads();
-  T* yb = y + 9 * (size_t)cam_lo;
-  for (int i = threadIdx.x; i < span * 9; i += blockDim.x) {
-    const T v = acc[i];
-    if (v != T(0)) atomicAdd(yb + i, v);
+  if (WINDOW) {
+    __syncthreads();
+    T* yb = y + 9 * (size_t)cam_lo;
+    for (int i = threadIdx.x; i < span * 9; i += blockDim.x) {
+      const T v = acc[i];
+      if (v != T(0)) atomicAdd(yb + i, v);
+    }
   }
 }
 
@@ -433,18 +488,18 @@ __global__ void k_diag_init(const TD* __restrict__ Dc, const T* __restrict__ x, 
 template <typename T>
 static void launch_matvec(ba_problem* P, const T* F, const T* E, const T* Cinv, const T* x, T* y) {
   if (P->n_chunks == 0) return;
-  const size_t smem = sizeof(T) * 9 * (size_t)P->k3_window;
-  static bool attr_set[2] = {false, false};
-  const int which = sizeof(T) == 8;
-  if (!attr_set[which]) {
-    BA_CUDA(cudaFuncSetAttribute(k_schur_matvec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  constexpr bool window = sizeof(T) == 4;
+  const size_t smem = window ? sizeof(T) * 9 * (size_t)P->k3_window : 0;
+  static bool attr_set = false;
+  if (window && !attr_set) {
+    BA_CUDA(cudaFuncSetAttribute(k_schur_matvec<T, window>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(T) * 9 * 1024)));
-    attr_set[which] = true;
+    attr_set = true;
   }
   KernelTimer kt(P, sizeof(T) == 8 ? BA_KT_SCHUR_FP64 : BA_KT_SCHUR_FP32);
-  k_schur_matvec<T><<<P->n_chunks, kK3Warps * 32, smem, P->stream>>>(
-      F, E, P->ld, Cinv, P->ldp, P->obs_cam.as<int>(), P->pt_ptr.as<int>(), P->tile_pt.as<int>(),
-      P->chunk_tile.as<int>(), P->chunk_cam.as<int>(), x, y, P->k3_window);
+  k_schur_matvec<T, window><<<P->n_chunks, kK3Warps * 32, smem, P->stream>>>(
+      F, E, (int)P->ld, Cinv, (int)P->ldp, P->obs_cam.as<int>(), P->tile_desc.as<int4>(),
+      P->chunk_tile.as<int>(), P->chunk_cam.as<int>(), x, y, P->k3_window, (P->k3_calls++) & 1);
   launched(P);
 }
 
@@ -452,116 +507,391 @@ void matvec64(ba_problem* P, const double* x, double* y) {
   const int n = 9 * P->n_c;
   k_diag_init<double, double><<<cdiv(n, 256), 256, 0, P->stream>>>(P->Dc.as<double>(), x, y, n);
   launched(P);
-  launch_matvec<double>(P, P->F64.as<double>(), P->E64.as<double>(), P->Cinv64.as<double>(), x, y);
+  launch_matvec<double>(P, P->J64.as<double>(), P->J64.as<double>(), P->Cinv64.as<double>(), x, y);
 }
 
 void matvec32(ba_problem* P, const float* x, float* y) {
   const int n = 9 * P->n_c;
   k_diag_init<float, float><<<cdiv(n, 256), 256, 0, P->stream>>>(P->Dc32.as<float>(), x, y, n);
   launched(P);
-  launch_matvec<float>(P, P->F32.as<float>(), P->E32.as<float>(), P->Cinv32.as<float>(), x, y);
+  launch_matvec<float>(P, P->J32.as<float>(), P->J32.as<float>(), P->Cinv32.as<float>(), x, y);
+}
+
+// the products alone, for callers whose producing kernel already wrote y = D_c x
+void matvec64_accumulate(ba_problem* P, const double* x, double* y) {
+  launch_matvec<double>(P, P->J64.as<double>(), P->J64.as<double>(), P->Cinv64.as<double>(), x, y);
+}
+void matvec32_accumulate(ba_problem* P, const float* x, float* y) {
+  launch_matvec<float>(P, P->J32.as<float>(), P->J32.as<float>(), P->Cinv32.as<float>(), x, y);
 }
 
 // ---------------------------------------------------------------------------
 // explicit level-0 operator blocks S_cc' (for the Galerkin product), one CTA per
-// camera row.  For every observation o = (c, p) of the row, in order, the
-// contributions -F_o^T (E_o C_p^-1 E_o'^T - [o' == o] I) F_o' of all o' in p are
-// added to the row's blocks in shared memory; within one o all o' belong to
-// different cameras, so each (block, entry) has a single writer per step.
+// camera row c.  Warp w takes the observations o = (c, p) of the row in turn; lane j
+// takes the j-th observation o' = (c', p) of the same point and adds
+//   -F_o^T (E_o C_p^-1 E_o'^T - [o' == o] I) F_o'
+// to block (c, c').  The o' of one point belong to distinct cameras, so within a
+// warp every lane updates a different block: each warp accumulates into its own
+// copy of the row in shared memory with plain read-modify-writes, and the copies
+// are summed in warp order at the end (deterministic, no atomics).  A row with more
+// blocks than fit is processed in several passes over block ranges.
 // ---------------------------------------------------------------------------
-constexpr int kExBS = 256;
+constexpr int kExWarps = 4;
 
 template <typename T>
-__global__ void __launch_bounds__(kExBS)
-k_explicit_schur(const T* __restrict__ F, const T* __restrict__ E, size_t ld,
-                 const T* __restrict__ Cinv, size_t ldp, const int* __restrict__ cam_ptr,
+__global__ void __launch_bounds__(kExWarps * 32)
+k_explicit_schur(const T* __restrict__ F, const T* __restrict__ E, int ld,
+                 const T* __restrict__ Cinv, int ldp, const int* __restrict__ cam_ptr,
                  const int* __restrict__ cam_obs, const int* __restrict__ obs_pt,
                  const int* __restrict__ obs_cam, const int* __restrict__ pt_ptr,
                  const int* __restrict__ row_ptr, const int* __restrict__ cols,
-                 const double* __restrict__ Dc, int slot_base_cap, T* __restrict__ vals) {
+                 const double* __restrict__ Dc, int cap, T* __restrict__ vals) {
   extern __shared__ __align__(16) unsigned char ex_smem[];
   const int c = blockIdx.x;
   const int rb = row_ptr[c], re = row_ptr[c + 1];
   const int nslots = re - rb;
-  // shared layout: acc [cap][81] T | cols [cap] int | per-o' staging
-  T* acc = reinterpret_cast<T*>(ex_smem);
-  const int cap = slot_base_cap;
-  int* scol = reinterpret_cast<int*>(acc + (size_t)cap * 81);
-  T* sF = reinterpret_cast<T*>(scol + cap + (cap & 1));     // [32][18] F_o'
-  T* sM = sF + 32 * 18;                                       // [32][4]  M_o'
-  int* sslot = reinterpret_cast<int*>(sM + 32 * 4);          // [32]
-  T* sFo = reinterpret_cast<T*>(sslot + 32);                  // [18]
+  T* acc = reinterpret_cast<T*>(ex_smem);                         // [kExWarps][cap][81]
+  int* scol = reinterpret_cast<int*>(acc + (size_t)kExWarps * cap * 81);  // [cap]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* my = acc + (size_t)warp * cap * 81;
   for (int pass_base = 0; pass_base < nslots; pass_base += cap) {
     const int pass_n = min(cap, nslots - pass_base);
-    for (int i = threadIdx.x; i < pass_n * 81; i += kExBS) acc[i] = T(0);
-    for (int i = threadIdx.x; i < pass_n; i += kExBS) scol[i] = cols[rb + pass_base + i];
+    for (int i = threadIdx.x; i < kExWarps * cap * 81; i += blockDim.x) acc[i] = T(0);
+    for (int i = threadIdx.x; i < pass_n; i += blockDim.x) scol[i] = cols[rb + pass_base + i];
     __syncthreads();
-    for (int k = cam_ptr[c]; k < cam_ptr[c + 1]; ++k) {
+    for (int k = cam_ptr[c] + warp; k < cam_ptr[c + 1]; k += kExWarps) {
       const int o = cam_obs[k];
       const int ip = obs_pt[o];
       const int ob = pt_ptr[ip], np = pt_ptr[ip + 1] - ob;
-      for (int jb = 0; jb < np; jb += 32) {
-        const int nj = min(32, np - jb);
-        if (threadIdx.x < 32) {
-          const int j = threadIdx.x;
-          // Y = E_o C_p^-1, computed redundantly per lane (cheap)
-          const T ci0 = Cinv[ip], ci1 = Cinv[ldp + ip], ci2 = Cinv[2 * ldp + ip];
-          const T ci3 = Cinv[3 * ldp + ip], ci4 = Cinv[4 * ldp + ip], ci5 = Cinv[5 * ldp + ip];
-          const T e0 = E[o], e1 = E[ld + o], e2 = E[2 * ld + o];
-          const T e3 = E[3 * ld + o], e4 = E[4 * ld + o], e5 = E[5 * ld + o];
-          const T y00 = e0 * ci0 + e1 * ci1 + e2 * ci2, y01 = e0 * ci1 + e1 * ci3 + e2 * ci4,
-                  y02 = e0 * ci2 + e1 * ci4 + e2 * ci5;
-          const T y10 = e3 * ci0 + e4 * ci1 + e5 * ci2, y11 = e3 * ci1 + e4 * ci3 + e5 * ci4,
-                  y12 = e3 * ci2 + e4 * ci4 + e5 * ci5;
-          if (j < nj) {
-            const int o2 = ob + jb + j;
-            const int c2 = obs_cam[o2];
-            const T a0 = E[o2], a1 = E[ld + o2], a2 = E[2 * ld + o2];
-            const T b0 = E[3 * ld + o2], b1 = E[4 * ld + o2], b2 = E[5 * ld + o2];
-            T m00 = y00 * a0 + y01 * a1 + y02 * a2;
-            T m01 = y00 * b0 + y01 * b1 + y02 * b2;
-            T m10 = y10 * a0 + y11 * a1 + y12 * a2;
-            T m11 = y10 * b0 + y11 * b1 + y12 * b2;
-            if (o2 == o) {
-              m00 -= T(1);
-              m11 -= T(1);
-            }
-            sM[4 * j + 0] = m00;
-            sM[4 * j + 1] = m01;
-            sM[4 * j + 2] = m10;
-            sM[4 * j + 3] = m11;
+      T fo[18];
 #pragma unroll
-            for (int q = 0; q < 18; ++q) sF[18 * j + q] = F[q * ld + o2];
-            // slot of camera c2 in this pass (binary search), -1 if outside
-            int lo = 0, hi = pass_n - 1, s = -1;
-            while (lo <= hi) {
-              const int mid = (lo + hi) >> 1;
-              const int v = scol[mid];
-              if (v == c2) { s = mid; break; }
-              if (v < c2) lo = mid + 1; else hi = mid - 1;
-            }
-            sslot[j] = s;
-          }
-          if (j < 18) sFo[j] = F[j * ld + o];
+      for (int q = 0; q < 18; ++q) fo[q] = JF(F, o, q);
+      const T ci0 = Cinv[ip], ci1 = Cinv[ldp + ip], ci2 = Cinv[2 * ldp + ip];
+      const T ci3 = Cinv[3 * ldp + ip], ci4 = Cinv[4 * ldp + ip], ci5 = Cinv[5 * ldp + ip];
+      const T e0 = JE(E, o, 0), e1 = JE(E, o, 1), e2 = JE(E, o, 2);
+      const T e3 = JE(E, o, 3), e4 = JE(E, o, 4), e5 = JE(E, o, 5);
+      // Y = E_o C_p^-1 (2 x 3)
+      const T y00 = e0 * ci0 + e1 * ci1 + e2 * ci2, y01 = e0 * ci1 + e1 * ci3 + e2 * ci4,
+              y02 = e0 * ci2 + e1 * ci4 + e2 * ci5;
+      const T y10 = e3 * ci0 + e4 * ci1 + e5 * ci2, y11 = e3 * ci1 + e4 * ci3 + e5 * ci4,
+              y12 = e3 * ci2 + e4 * ci4 + e5 * ci5;
+      for (int jb = 0; jb < np; jb += 32) {
+        const int j = jb + lane;
+        if (j >= np) continue;
+        const int o2 = ob + j;
+        const int c2 = obs_cam[o2];
+        int lo = 0, hi = pass_n - 1, s = -1;
+        while (lo <= hi) {
+          const int mid = (lo + hi) >> 1;
+          const int v = scol[mid];
+          if (v == c2) { s = mid; break; }
+          if (v < c2) lo = mid + 1; else hi = mid - 1;
         }
-        __syncthreads();
-        for (int it = threadIdx.x; it < nj * 81; it += kExBS) {
-          const int j = it / 81, e = it - 81 * j;
-          const int s = sslot[j];
-          if (s < 0) continue;
-          const int a = e / 9, b = e - 9 * a;
-          const T* M = sM + 4 * j;
-          const T g0 = sFo[a] * M[0] + sFo[9 + a] * M[2];
-          const T g1 = sFo[a] * M[1] + sFo[9 + a] * M[3];
-          acc[81 * s + e] -= g0 * sF[18 * j + b] + g1 * sF[18 * j + 9 + b];
+        if (s < 0) continue;
+        const T a0 = JE(E, o2, 0), a1 = JE(E, o2, 1), a2 = JE(E, o2, 2);
+        const T b0 = JE(E, o2, 3), b1 = JE(E, o2, 4), b2 = JE(E, o2, 5);
+        T m00 = y00 * a0 + y01 * a1 + y02 * a2;
+        T m01 = y00 * b0 + y01 * b1 + y02 * b2;
+        T m10 = y10 * a0 + y11 * a1 + y12 * a2;
+        T m11 = y10 * b0 + y11 * b1 + y12 * b2;
+        if (o2 == o) {
+          m00 -= T(1);
+          m11 -= T(1);
         }
-        __syncthreads();
+        T f2[18];
+#pragma unroll
+        for (int q = 0; q < 18; ++q) f2[q] = JF(F, o2, q);
+        T* blk = my + (size_t)s * 81;
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+          const T g0 = fo[a] * m00 + fo[9 + a] * m10;
+          const T g1 = fo[a] * m01 + fo[9 + a] * m11;
+#pragma unroll
+          for (int b = 0; b < 9; ++b) blk[9 * a + b] -= g0 * f2[b] + g1 * f2[9 + b];
+        }
       }
     }
-    // add D_c on the diagonal block and write out
-    for (int i = threadIdx.x; i < pass_n * 81; i += kExBS) {
+    __syncthreads();
+    // sum the warps' copies, add D_c on the diagonal block, write out
+    for (int i = threadIdx.x; i < pass_n * 81; i += blockDim.x) {
+      T v = T(0);
+#pragma unroll
+      for (int w = 0; w < kExWarps; ++w) v += acc[(size_t)w * cap * 81 + i];
       const int s = i / 81, e = i - 81 * s;
+      const int a = e / 9, b = e - 9 * a;
+      if (scol[s] == c && a == b) v += (T)Dc[9 * c + a];
+      vals[(size_t)(rb + pass_base + s) * 81 + e] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// FP32 variant with every thread of the CTA on its own (o, o') pair of the row: the
+// row's observations are taken in batches of kPairBatch; a block-wide prefix of the
+// batch's point sizes maps a thread's pair index to (o, j); contributions go to the
+// single shared copy of the row with FP32 shared atomics (native on this GPU).
+constexpr int kPairBS = 256;
+constexpr int kPairBatch = 256;
+
+__global__ void __launch_bounds__(kPairBS)
+k_explicit_schur_pairs(const float* __restrict__ F, const float* __restrict__ E, int ld,
+                       const float* __restrict__ Cinv, int ldp, const int* __restrict__ cam_ptr,
+                       const int* __restrict__ cam_obs, const int* __restrict__ obs_pt,
+                       const int* __restrict__ obs_cam, const int* __restrict__ pt_ptr,
+                       const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                       const double* __restrict__ Dc, int cap, float* __restrict__ vals) {
+  extern __shared__ __align__(16) unsigned char px_smem[];
+  __shared__ int bo[kPairBatch], bip[kPairBatch], bob[kPairBatch], bpre[kPairBatch + 1];
+  const int c = blockIdx.x;
+  const int rb = row_ptr[c], re = row_ptr[c + 1];
+  const int nslots = re - rb;
+  float* acc = reinterpret_cast<float*>(px_smem);                          // [cap][81]
+  int* scol = reinterpret_cast<int*>(acc + (size_t)cap * 81);              // [cap]
+  const int t = threadIdx.x;
+  const int ob0 = cam_ptr[c], nrow = cam_ptr[c + 1] - ob0;
+  for (int pass_base = 0; pass_base < nslots; pass_base += cap) {
+    const int pass_n = min(cap, nslots - pass_base);
+    for (int i = t; i < cap * 81; i += kPairBS) acc[i] = 0.0f;
+    for (int i = t; i < pass_n; i += kPairBS) scol[i] = cols[rb + pass_base + i];
+    __syncthreads();  // a row without observations goes straight to the write-out
+    for (int b0 = 0; b0 < nrow; b0 += kPairBatch) {
+      const int nb = min(kPairBatch, nrow - b0);
+      int cnt = 0;
+      if (t < nb) {
+        const int o = cam_obs[ob0 + b0 + t];
+        const int ip = obs_pt[o];
+        const int s = pt_ptr[ip];
+        bo[t] = o;
+        bip[t] = ip;
+        bob[t] = s;
+        cnt = pt_ptr[ip + 1] - s;
+      }
+      // exclusive prefix of the pair counts (Hillis-Steele in shared memory)
+      bpre[t + 1] = cnt;
+      if (t == 0) bpre[0] = 0;
+      __syncthreads();
+      for (int d = 1; d < kPairBatch; d <<= 1) {
+        const int v = (t + 1 - d >= 1) ? bpre[t + 1 - d] : 0;
+        __syncthreads();
+        bpre[t + 1] += v;
+        __syncthreads();
+      }
+      const int total = bpre[nb];
+      for (int pi = t; pi < total; pi += kPairBS) {
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {  // last i with bpre[i] <= pi
+          const int mid = (lo + hi + 1) >> 1;
+          if (bpre[mid] <= pi) lo = mid; else hi = mid - 1;
+        }
+        const int i = lo;
+        const int o = bo[i], ip = bip[i];
+        const int o2 = bob[i] + (pi - bpre[i]);
+        const int c2 = obs_cam[o2];
+        int a = 0, z = pass_n - 1, s = -1;
+        while (a <= z) {
+          const int mid = (a + z) >> 1;
+          const int v = scol[mid];
+          if (v == c2) { s = mid; break; }
+          if (v < c2) a = mid + 1; else z = mid - 1;
+        }
+        if (s < 0) continue;
+        const float ci0 = Cinv[ip], ci1 = Cinv[ldp + ip], ci2 = Cinv[2 * ldp + ip];
+        const float ci3 = Cinv[3 * ldp + ip], ci4 = Cinv[4 * ldp + ip], ci5 = Cinv[5 * ldp + ip];
+        const float e0 = JE(E, o, 0), e1 = JE(E, o, 1), e2 = JE(E, o, 2);
+        const float e3 = JE(E, o, 3), e4 = JE(E, o, 4), e5 = JE(E, o, 5);
+        const float y00 = e0 * ci0 + e1 * ci1 + e2 * ci2, y01 = e0 * ci1 + e1 * ci3 + e2 * ci4,
+                    y02 = e0 * ci2 + e1 * ci4 + e2 * ci5;
+        const float y10 = e3 * ci0 + e4 * ci1 + e5 * ci2, y11 = e3 * ci1 + e4 * ci3 + e5 * ci4,
+                    y12 = e3 * ci2 + e4 * ci4 + e5 * ci5;
+        const float a0 = JE(E, o2, 0), a1 = JE(E, o2, 1), a2 = JE(E, o2, 2);
+        const float g0 = JE(E, o2, 3), g1 = JE(E, o2, 4), g2 = JE(E, o2, 5);
+        float m00 = y00 * a0 + y01 * a1 + y02 * a2;
+        float m01 = y00 * g0 + y01 * g1 + y02 * g2;
+        float m10 = y10 * a0 + y11 * a1 + y12 * a2;
+        float m11 = y10 * g0 + y11 * g1 + y12 * g2;
+        if (o2 == o) {
+          m00 -= 1.0f;
+          m11 -= 1.0f;
+        }
+        float f2[18];
+#pragma unroll
+        for (int q = 0; q < 18; ++q) f2[q] = JF(F, o2, q);
+        float* blk = acc + (size_t)s * 81;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+          const float fa = JF(F, o, r), fb = JF(F, o, 9 + r);
+          const float h0 = fa * m00 + fb * m10;
+          const float h1 = fa * m01 + fb * m11;
+#pragma unroll
+          for (int q = 0; q < 9; ++q) atomicAdd(blk + 9 * r + q, -(h0 * f2[q] + h1 * f2[9 + q]));
+        }
+      }
+      __syncthreads();
+    }
+    for (int i = t; i < pass_n * 81; i += kPairBS) {
+      float v = acc[i];
+      const int s = i / 81, e = i - 81 * s;
+      const int a = e / 9, b = e - 9 * a;
+      if (scol[s] == c && a == b) v += (float)Dc[9 * c + a];
+      vals[(size_t)(rb + pass_base + s) * 81 + e] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Sorted variant (no atomics): the row's observations are taken in batches of kSB; for
+// every (o, o') pair of a batch, G = F_o^T M (9 x 2) and F_o' (2 x 9) are staged in
+// shared memory grouped by target block (counting sort on the block slot); then warp w
+// owns the blocks s = w (mod 8) and accumulates each in registers, lane (a, g) holding
+// entries (a, 3g .. 3g+2) of the 9 x 9 block.
+constexpr int kSortBS = 256;
+constexpr int kSortPairs = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kSortBS)
+k_explicit_schur_sorted(const T* __restrict__ F, const T* __restrict__ E, int ld,
+                        const T* __restrict__ Cinv, int ldp, const int* __restrict__ cam_ptr,
+                        const int* __restrict__ cam_obs, const int* __restrict__ obs_pt,
+                        const int* __restrict__ obs_cam, const int* __restrict__ pt_ptr,
+                        const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                        const double* __restrict__ Dc, int cap, int batch, T* __restrict__ vals) {
+  extern __shared__ __align__(16) unsigned char so_smem[];
+  T* acc = reinterpret_cast<T*>(so_smem);                              // [cap][81]
+  T* rec = acc + (size_t)cap * 81;                                     // [kSortPairs][36]
+  int* scol = reinterpret_cast<int*>(rec + (size_t)kSortPairs * 36);   // [cap]
+  int* scnt = scol + cap;                                              // [cap]
+  int* soff = scnt + cap;                                              // [cap + 1]
+  __shared__ int bo[64], bip[64], bob[64], bpre[65];
+  const int c = blockIdx.x;
+  const int rb = row_ptr[c], re = row_ptr[c + 1];
+  const int nslots = re - rb;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int ob0 = cam_ptr[c], nrow = cam_ptr[c + 1] - ob0;
+  const int la = lane / 3, lg = lane - 3 * (lane / 3);   // lane -> (row a, column group g)
+  for (int pass_base = 0; pass_base < nslots; pass_base += cap) {
+    const int pass_n = min(cap, nslots - pass_base);
+    for (int i = t; i < cap * 81; i += kSortBS) acc[i] = T(0);
+    for (int i = t; i < pass_n; i += kSortBS) scol[i] = cols[rb + pass_base + i];
+    __syncthreads();  // a row without observations goes straight to the write-out
+    for (int b0 = 0; b0 < nrow; b0 += batch) {
+      const int nb = min(batch, nrow - b0);
+      for (int i = t; i < pass_n; i += kSortBS) scnt[i] = 0;
+      if (t < nb) {
+        const int o = cam_obs[ob0 + b0 + t];
+        const int ip = obs_pt[o];
+        const int s0 = pt_ptr[ip];
+        bo[t] = o;
+        bip[t] = ip;
+        bob[t] = s0;
+        bpre[t + 1] = pt_ptr[ip + 1] - s0;   // pair count, turned into a prefix below
+      }
+      __syncthreads();
+      if (t == 0) {
+        bpre[0] = 0;
+        for (int i = 0; i < nb; ++i) bpre[i + 1] += bpre[i];
+      }
+      __syncthreads();
+      const int total = bpre[nb];
+      // pass 1: block slot of every pair, counted
+      for (int pi = t; pi < total; pi += kSortBS) {
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (bpre[mid] <= pi) lo = mid; else hi = mid - 1;
+        }
+        const int c2 = obs_cam[bob[lo] + (pi - bpre[lo])];
+        int a = 0, z = pass_n - 1, s = -1;
+        while (a <= z) {
+          const int mid = (a + z) >> 1;
+          const int v = scol[mid];
+          if (v == c2) { s = mid; break; }
+          if (v < c2) a = mid + 1; else z = mid - 1;
+        }
+        if (s >= 0) atomicAdd(scnt + s, 1);
+      }
+      __syncthreads();
+      if (t == 0) {
+        int a = 0;
+        for (int s = 0; s < pass_n; ++s) {
+          soff[s] = a;
+          a += scnt[s];
+          scnt[s] = 0;
+        }
+        soff[pass_n] = a;
+      }
+      __syncthreads();
+      // pass 2: stage G = F_o^T M and F_o' of every pair at its slot's position
+      for (int pi = t; pi < total; pi += kSortBS) {
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (bpre[mid] <= pi) lo = mid; else hi = mid - 1;
+        }
+        const int o = bo[lo], ip = bip[lo];
+        const int o2 = bob[lo] + (pi - bpre[lo]);
+        const int c2 = obs_cam[o2];
+        int a = 0, z = pass_n - 1, s = -1;
+        while (a <= z) {
+          const int mid = (a + z) >> 1;
+          const int v = scol[mid];
+          if (v == c2) { s = mid; break; }
+          if (v < c2) a = mid + 1; else z = mid - 1;
+        }
+        if (s < 0) continue;
+        const T ci0 = Cinv[ip], ci1 = Cinv[ldp + ip], ci2 = Cinv[2 * ldp + ip];
+        const T ci3 = Cinv[3 * ldp + ip], ci4 = Cinv[4 * ldp + ip], ci5 = Cinv[5 * ldp + ip];
+        const T e0 = JE(E, o, 0), e1 = JE(E, o, 1), e2 = JE(E, o, 2);
+        const T e3 = JE(E, o, 3), e4 = JE(E, o, 4), e5 = JE(E, o, 5);
+        const T y00 = e0 * ci0 + e1 * ci1 + e2 * ci2, y01 = e0 * ci1 + e1 * ci3 + e2 * ci4,
+                y02 = e0 * ci2 + e1 * ci4 + e2 * ci5;
+        const T y10 = e3 * ci0 + e4 * ci1 + e5 * ci2, y11 = e3 * ci1 + e4 * ci3 + e5 * ci4,
+                y12 = e3 * ci2 + e4 * ci4 + e5 * ci5;
+        const T a0 = JE(E, o2, 0), a1 = JE(E, o2, 1), a2 = JE(E, o2, 2);
+        const T g0 = JE(E, o2, 3), g1 = JE(E, o2, 4), g2 = JE(E, o2, 5);
+        T m00 = y00 * a0 + y01 * a1 + y02 * a2;
+        T m01 = y00 * g0 + y01 * g1 + y02 * g2;
+        T m10 = y10 * a0 + y11 * a1 + y12 * a2;
+        T m11 = y10 * g0 + y11 * g1 + y12 * g2;
+        if (o2 == o) {
+          m00 -= T(1);
+          m11 -= T(1);
+        }
+        T* r = rec + (size_t)(soff[s] + atomicAdd(scnt + s, 1)) * 36;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          const T fa = JF(F, o, q), fb = JF(F, o, 9 + q);
+          r[2 * q] = fa * m00 + fb * m10;       // G[q][0]
+          r[2 * q + 1] = fa * m01 + fb * m11;   // G[q][1]
+        }
+#pragma unroll
+        for (int q = 0; q < 18; ++q) r[18 + q] = JF(F, o2, q);
+      }
+      __syncthreads();
+      // accumulate: warp w owns slots w, w + 8, ...
+      if (lane < 27) {
+        for (int s = warp; s < pass_n; s += kSortBS / 32) {
+          const int p0 = soff[s], p1 = soff[s + 1];
+          if (p0 == p1) continue;
+          T* blk = acc + (size_t)s * 81 + 9 * la + 3 * lg;
+          T s0 = blk[0], s1 = blk[1], s2 = blk[2];
+          for (int p = p0; p < p1; ++p) {
+            const T* r = rec + (size_t)p * 36;
+            const T h0 = r[2 * la], h1 = r[2 * la + 1];
+            const T* f2 = r + 18;
+            s0 -= h0 * f2[3 * lg] + h1 * f2[9 + 3 * lg];
+            s1 -= h0 * f2[3 * lg + 1] + h1 * f2[9 + 3 * lg + 1];
+            s2 -= h0 * f2[3 * lg + 2] + h1 * f2[9 + 3 * lg + 2];
+          }
+          blk[0] = s0;
+          blk[1] = s1;
+          blk[2] = s2;
+        }
+      }
+      __syncthreads();
+    }
+    for (int i = t; i < pass_n * 81; i += kSortBS) {
       T v = acc[i];
+      const int s = i / 81, e = i - 81 * s;
       const int a = e / 9, b = e - 9 * a;
       if (scol[s] == c && a == b) v += (T)Dc[9 * c + a];
       vals[(size_t)(rb + pass_base + s) * 81 + e] = v;
@@ -571,28 +901,54 @@ k_explicit_schur(const T* __restrict__ F, const T* __restrict__ E, size_t ld,
 }
 
 void explicit_schur(ba_problem* P, Level& L0, bool fp32) {
-  const int cap = fp32 ? 256 : 128;
   const size_t elem = fp32 ? 4 : 8;
-  size_t smem = elem * 81 * cap + sizeof(int) * (cap + 2) + elem * (32 * 18 + 32 * 4) +
-                sizeof(int) * 32 + elem * 18 + 64;
-  static bool attr[2] = {false, false};
-  if (!attr[fp32]) {
-    if (fp32)
-      BA_CUDA(cudaFuncSetAttribute(k_explicit_schur<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    else
-      BA_CUDA(cudaFuncSetAttribute(k_explicit_schur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr[fp32] = true;
+  const int maxrow = L0.maxrow;
+  // observations per batch so that a batch's pairs fit the staging area
+  const int batch = std::max(1, std::min(64, kSortPairs / std::max(P->max_pt_obs, 1)));
+  if (P->max_pt_obs <= kSortPairs) {
+    const int cap = std::min(maxrow, 96);
+    const size_t smem = (size_t)cap * 81 * elem + (size_t)kSortPairs * 36 * elem + sizeof(int) * (3 * cap + 4);
+    if (fp32) {
+      BA_CUDA(cudaFuncSetAttribute(k_explicit_schur_sorted<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+      L0.vals32.ensure(sizeof(float) * 81 * (size_t)L0.nnzb + 64);
+      k_explicit_schur_sorted<float><<<P->n_c, kSortBS, smem, P->stream>>>(
+          P->J32.as<float>(), P->J32.as<float>(), (int)P->ld, P->Cinv32.as<float>(), (int)P->ldp,
+          P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
+          P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Dc.as<double>(), cap, batch,
+          L0.vals32.as<float>());
+    } else {
+      BA_CUDA(cudaFuncSetAttribute(k_explicit_schur_sorted<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+      L0.vals64.ensure(sizeof(double) * 81 * (size_t)L0.nnzb + 64);
+      k_explicit_schur_sorted<double><<<P->n_c, kSortBS, smem, P->stream>>>(
+          P->J64.as<double>(), P->J64.as<double>(), (int)P->ld, P->Cinv64.as<double>(), (int)P->ldp,
+          P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
+          P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Dc.as<double>(), cap, batch,
+          L0.vals64.as<double>());
+    }
+    launched(P);
+    return;
   }
+  // points seen by more than kSortPairs cameras: per-warp accumulation kernels
   if (fp32) {
+    const int cap = std::min(maxrow, (int)((160 * 1024) / (81 * 4 + 4)));
+    const size_t smem = (size_t)cap * 81 * 4 + sizeof(int) * (cap + 4);
+    BA_CUDA(cudaFuncSetAttribute(k_explicit_schur_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     L0.vals32.ensure(sizeof(float) * 81 * (size_t)L0.nnzb + 64);
-    k_explicit_schur<float><<<P->n_c, kExBS, smem, P->stream>>>(
-        P->F32.as<float>(), P->E32.as<float>(), P->ld, P->Cinv32.as<float>(), P->ldp, P->cam_ptr.as<int>(),
-        P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(), P->pt_ptr.as<int>(),
-        L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Dc.as<double>(), cap, L0.vals32.as<float>());
+    k_explicit_schur_pairs<<<P->n_c, kPairBS, smem, P->stream>>>(
+        P->J32.as<float>(), P->J32.as<float>(), (int)P->ld, P->Cinv32.as<float>(), (int)P->ldp,
+        P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
+        P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Dc.as<double>(), cap,
+        L0.vals32.as<float>());
   } else {
+    const int cap_max = (int)((160 * 1024) / (kExWarps * 81 * elem + 4));
+    const int cap = std::min(maxrow, cap_max);
+    const size_t smem = (size_t)kExWarps * cap * 81 * elem + sizeof(int) * (cap + 4);
+    BA_CUDA(cudaFuncSetAttribute(k_explicit_schur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     L0.vals64.ensure(sizeof(double) * 81 * (size_t)L0.nnzb + 64);
-    k_explicit_schur<double><<<P->n_c, kExBS, smem, P->stream>>>(
-        P->F64.as<double>(), P->E64.as<double>(), P->ld, P->Cinv64.as<double>(), P->ldp,
+    k_explicit_schur<double><<<P->n_c, kExWarps * 32, smem, P->stream>>>(
+        P->J64.as<double>(), P->J64.as<double>(), (int)P->ld, P->Cinv64.as<double>(), (int)P->ldp,
         P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
         P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Dc.as<double>(), cap,
         L0.vals64.as<double>());
@@ -629,12 +985,12 @@ __global__ void k_back_substitute(const double* __restrict__ F, const double* __
     double u0 = 0, u1 = 0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      u0 += F[k * ld + o] * x[k];
-      u1 += F[(9 + k) * ld + o] * x[k];
+      u0 += JF(F, o, k) * x[k];
+      u1 += JF(F, o, 9 + k) * x[k];
     }
-    h0 -= E[o] * u0 + E[3 * ld + o] * u1;
-    h1 -= E[ld + o] * u0 + E[4 * ld + o] * u1;
-    h2 -= E[2 * ld + o] * u0 + E[5 * ld + o] * u1;
+    h0 -= JE(E, o, 0) * u0 + JE(E, o, 3) * u1;
+    h1 -= JE(E, o, 1) * u0 + JE(E, o, 4) * u1;
+    h2 -= JE(E, o, 2) * u0 + JE(E, o, 5) * u1;
   }
   const double c00 = Cinv[ip], c01 = Cinv[ldp + ip], c02 = Cinv[2 * ldp + ip];
   const double c11 = Cinv[3 * ldp + ip], c12 = Cinv[4 * ldp + ip], c22 = Cinv[5 * ldp + ip];
@@ -656,7 +1012,7 @@ __global__ void k_back_substitute(const double* __restrict__ F, const double* __
 void back_substitute_to(ba_problem* P, const double* dc, double* out_int, double* out_user) {
   if (P->n_p == 0) return;
   k_back_substitute<<<cdiv(P->n_p, 128), 128, 0, P->stream>>>(
-      P->F64.as<double>(), P->E64.as<double>(), P->ld, P->Cinv64.as<double>(), P->ldp,
+      P->J64.as<double>(), P->J64.as<double>(), P->ld, P->Cinv64.as<double>(), P->ldp,
       P->pt_ptr.as<int>(), P->obs_cam.as<int>(), P->pt_user.as<int>(), P->gp.as<double>(), 0, dc,
       P->n_p, out_int, out_user);
   launched(P);
@@ -666,7 +1022,7 @@ void back_substitute_general(ba_problem* P, const double* vp_user, const double*
                              double* out_user) {
   if (P->n_p == 0) return;
   k_back_substitute<<<cdiv(P->n_p, 128), 128, 0, P->stream>>>(
-      P->F64.as<double>(), P->E64.as<double>(), P->ld, P->Cinv64.as<double>(), P->ldp,
+      P->J64.as<double>(), P->J64.as<double>(), P->ld, P->Cinv64.as<double>(), P->ldp,
       P->pt_ptr.as<int>(), P->obs_cam.as<int>(), P->pt_user.as<int>(), vp_user, 1, dc, P->n_p,
       out_int, out_user);
   launched(P);
@@ -701,10 +1057,10 @@ __global__ void k_camera_reduce_rhs(const double* __restrict__ F, const double* 
     const int o = cam_obs[i];
     const int ip = obs_pt[o];
     const double w0 = wp[ip], w1 = wp[ldp + ip], w2 = wp[2 * ldp + ip];
-    const double h0 = E[o] * w0 + E[ld + o] * w1 + E[2 * ld + o] * w2;
-    const double h1 = E[3 * ld + o] * w0 + E[4 * ld + o] * w1 + E[5 * ld + o] * w2;
+    const double h0 = JE(E, o, 0) * w0 + JE(E, o, 1) * w1 + JE(E, o, 2) * w2;
+    const double h1 = JE(E, o, 3) * w0 + JE(E, o, 4) * w1 + JE(E, o, 5) * w2;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) bb[k] += F[k * ld + o] * h0 + F[(9 + k) * ld + o] * h1;
+    for (int k = 0; k < 9; ++k) bb[k] += JF(F, o, k) * h0 + JF(F, o, 9 + k) * h1;
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) bb[k] = warp_sum(bb[k]);
@@ -721,7 +1077,7 @@ void reduced_rhs(ba_problem* P, const double* vc, const double* vp_user, double*
     launched(P);
   }
   k_camera_reduce_rhs<<<cdiv((long long)P->n_c * 32, 128), 128, 0, P->stream>>>(
-      P->F64.as<double>(), P->E64.as<double>(), P->ld, P->cam_ptr.as<int>(), P->cam_obs.as<int>(),
+      P->J64.as<double>(), P->J64.as<double>(), P->ld, P->cam_ptr.as<int>(), P->cam_obs.as<int>(),
       P->obs_pt.as<int>(), w, P->ldp, vc, P->n_c, out);
   launched(P);
 }

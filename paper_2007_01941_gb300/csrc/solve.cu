@@ -36,20 +36,27 @@ __global__ void k_bsr16_spmv(int n, const int* __restrict__ row_ptr, const int* 
   y[(size_t)i * 16 + u] = sizeof(T) == 4 ? (T)accf : (T)accd;
 }
 
-void level_matvec(ba_problem* P, int l, const void* x, void* y) {
+// y = A_l x.  At level 0 with `ready`, y already holds D_c x (written by the kernel
+// that produced x) and the product only accumulates.
+void level_matvec(ba_problem* P, int l, const void* x, void* y, bool ready) {
   Level& L = P->levels[l];
   const bool fp32 = level_fp32(P);
   if (l == 0) {
-    if (fp32) matvec32(P, (const float*)x, (float*)y);
-    else matvec64(P, (const double*)x, (double*)y);
+    if (fp32) {
+      if (ready) matvec32_accumulate(P, (const float*)x, (float*)y);
+      else matvec32(P, (const float*)x, (float*)y);
+    } else {
+      if (ready) matvec64_accumulate(P, (const double*)x, (double*)y);
+      else matvec64(P, (const double*)x, (double*)y);
+    }
     return;
   }
-  const int g = cdiv((long long)L.n * 16, 256);
+  const int g = cdiv((long long)L.n * 16, 64);   // small blocks: spread coarse rows over all SMs
   if (fp32)
-    k_bsr16_spmv<float><<<g, 256, 0, P->stream>>>(L.n, L.row_ptr.as<int>(), L.cols.as<int>(), L.vals32.as<float>(),
+    k_bsr16_spmv<float><<<g, 64, 0, P->stream>>>(L.n, L.row_ptr.as<int>(), L.cols.as<int>(), L.vals32.as<float>(),
                                                   (const float*)x, (float*)y);
   else
-    k_bsr16_spmv<double><<<g, 256, 0, P->stream>>>(L.n, L.row_ptr.as<int>(), L.cols.as<int>(),
+    k_bsr16_spmv<double><<<g, 64, 0, P->stream>>>(L.n, L.row_ptr.as<int>(), L.cols.as<int>(),
                                                    L.vals64.as<double>(), (const double*)x, (double*)y);
   launched(P);
 }
@@ -65,11 +72,16 @@ __device__ __forceinline__ double cheb_rho(const double* cheb, int k) {
   return rho;
 }
 
-// step 0: r = b - q (q may be null: x = 0), d = D^-1 r / theta, x = x + d
+// Every kernel that produces the vector a level-0 product is applied to next also writes
+// yn = Dn o (that vector), the product's diagonal term, so the product itself only
+// accumulates (Dn = null at the block-sparse coarse levels).
+
+// step 0: r = b - q (q null: x = 0), d = D^-1 r / theta, x = x + d, yn = Dn o d
 template <typename T>
 __global__ void k_cheb_first(int n, int bs, const T* __restrict__ Dinv, const T* __restrict__ b,
                              const T* __restrict__ q, T* __restrict__ r, T* __restrict__ d, T* __restrict__ x,
-                             int x_zero, const double* __restrict__ cheb) {
+                             int x_zero, const double* __restrict__ cheb, const T* __restrict__ Dn,
+                             T* __restrict__ yn) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)n * bs) return;
   const size_t i = idx / bs;
@@ -84,31 +96,31 @@ __global__ void k_cheb_first(int n, int bs, const T* __restrict__ Dinv, const T*
   r[idx] = ri;
   d[idx] = di;
   x[idx] = x_zero ? di : x[idx] + di;
+  if (Dn) yn[idx] = Dn[idx] * di;
 }
 
-// step k >= 1: r = r - q; d = rho_k rho_{k-1} d + (2 rho_k / delta) D^-1 r; x = x + d
-// (r is updated by a separate pass first so every thread sees the new r)
+// step k >= 1: r_out = r_in - q; d = rho_k rho_{k-1} d + (2 rho_k / delta) D^-1 r_out;
+// x = x + d; yn = Dn o d   (r_in and r_out are different buffers)
 template <typename T>
-__global__ void k_sub(size_t n, T* __restrict__ r, const T* __restrict__ q) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) r[i] -= q[i];
-}
-
-template <typename T>
-__global__ void k_cheb_step(int n, int bs, const T* __restrict__ Dinv, const T* __restrict__ r,
-                            T* __restrict__ d, T* __restrict__ x, const double* __restrict__ cheb, int k) {
+__global__ void k_cheb_step(int n, int bs, const T* __restrict__ Dinv, const T* __restrict__ r_in,
+                            const T* __restrict__ q, T* __restrict__ r_out, T* __restrict__ d, T* __restrict__ x,
+                            const double* __restrict__ cheb, int k, const T* __restrict__ Dn,
+                            T* __restrict__ yn) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)n * bs) return;
   const size_t i = idx / bs;
   const int u = (int)(idx - i * bs);
   const T* Di = Dinv + (i * bs + u) * bs;
-  const T* ri = r + i * bs;
+  const T* ri = r_in + i * bs;
+  const T* qi = q + i * bs;
   T acc = T(0);
-  for (int v = 0; v < bs; ++v) acc += Di[v] * ri[v];
+  for (int v = 0; v < bs; ++v) acc += Di[v] * (ri[v] - qi[v]);
+  r_out[idx] = r_in[idx] - q[idx];
   const double rk = cheb_rho(cheb, k), rk1 = cheb_rho(cheb, k - 1);
   const T dn = (T)(rk * rk1) * d[idx] + (T)(2.0 * rk / cheb[1]) * acc;
   d[idx] = dn;
   x[idx] += dn;
+  if (Dn) yn[idx] = Dn[idx] * dn;
 }
 
 // rc[a][s] = sum_{i in a} sum_u Q_i[u][s] (r_i[u] - q_i[u])   (restriction R = P^T)
@@ -131,10 +143,11 @@ __global__ void k_restrict(int n_agg, int bs, const int* __restrict__ mptr, cons
   rc[(size_t)a * 16 + s] = acc;
 }
 
-// x_i += Q_i xc_{agg(i)}   (prolongation)
+// x_i += Q_i xc_{agg(i)} (prolongation); yn = Dn o x
 template <typename T>
 __global__ void k_prolong(int n, int bs, const int* __restrict__ agg, const T* __restrict__ Q,
-                          const T* __restrict__ xc, T* __restrict__ x) {
+                          const T* __restrict__ xc, T* __restrict__ x, const T* __restrict__ Dn,
+                          T* __restrict__ yn) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)n * bs) return;
   const size_t i = idx / bs;
@@ -144,7 +157,9 @@ __global__ void k_prolong(int n, int bs, const int* __restrict__ agg, const T* _
   T acc = T(0);
 #pragma unroll
   for (int s = 0; s < 16; ++s) acc += Qi[s] * xa[s];
-  x[idx] += acc;
+  const T xn = x[idx] + acc;
+  x[idx] = xn;
+  if (Dn) yn[idx] = Dn[idx] * xn;
 }
 
 // coarsest level: x = Ainv b (FP64 inverse, padded to Np; b beyond N is zero)
@@ -169,28 +184,41 @@ template <typename T>
 static const T* qblk(Level& L) {
   return sizeof(T) == 4 ? (const T*)L.Q32.p : (const T*)L.Q64.p;
 }
-
-// smooth(x, b) with `steps` Chebyshev steps; x_zero: x = 0 on entry.  On exit r holds
-// the residual b - A x_{steps-1} and d the last update (so b - A x = r - A d).
+// D_c in the V-cycle's precision (level 0 only)
 template <typename T>
-static void smooth(ba_problem* P, int l, T* x, const T* b, T* r, T* d, T* q, int steps, bool x_zero) {
+static const T* diag0(ba_problem* P, int l) {
+  if (l != 0) return nullptr;
+  return sizeof(T) == 4 ? (const T*)P->Dc32.p : (const T*)P->Dc.p;
+}
+
+// Chebyshev smoothing of A x = b with residual buffers rr[2] and product buffers qq[2].
+// On entry with x_zero false, qq[qi] holds A x.  On exit rr[ri] = b - A (x - d), d is
+// the last update and (level 0) qq[qi] holds D_c d, ready for the product A d.
+template <typename T>
+static void smooth(ba_problem* P, int l, T* x, const T* b, T** rr, int& ri, T* d, T** qq, int& qi, int steps,
+                   bool x_zero) {
   Level& L = P->levels[l];
   const size_t n = (size_t)L.n * L.bs;
   const int g = cdiv((long long)n, 256);
   const double* cheb = L.cheb.as<double>();
-  if (!x_zero) level_matvec(P, l, x, q);
-  k_cheb_first<T><<<g, 256, 0, P->stream>>>(L.n, L.bs, dinv<T>(L), b, x_zero ? nullptr : q, r, d, x, x_zero, cheb);
+  const T* Dn = diag0<T>(P, l);
+  const T* qin = x_zero ? nullptr : qq[qi];
+  const int qn = x_zero ? qi : 1 - qi;
+  k_cheb_first<T><<<g, 256, 0, P->stream>>>(L.n, L.bs, dinv<T>(L), b, qin, rr[ri], d, x, x_zero, cheb, Dn, qq[qn]);
   launched(P);
+  qi = qn;
   for (int k = 1; k < steps; ++k) {
-    level_matvec(P, l, d, q);
-    k_sub<T><<<g, 256, 0, P->stream>>>(n, r, q);
+    level_matvec(P, l, d, qq[qi], true);
+    const int qn2 = 1 - qi;
+    k_cheb_step<T><<<g, 256, 0, P->stream>>>(L.n, L.bs, dinv<T>(L), rr[ri], qq[qi], rr[1 - ri], d, x, cheb, k, Dn,
+                                            qq[qn2]);
     launched(P);
-    k_cheb_step<T><<<g, 256, 0, P->stream>>>(L.n, L.bs, dinv<T>(L), r, d, x, cheb, k);
-    launched(P);
+    ri = 1 - ri;
+    qi = qn2;
   }
 }
 
-// x = mgcycle(l, 0, b)
+// x = mgcycle(l, 0, b)   (Algorithm 1)
 template <typename T>
 static void vcycle(ba_problem* P, int l, const T* b, T* x) {
   Level& L = P->levels[l];
@@ -200,23 +228,27 @@ static void vcycle(ba_problem* P, int l, const T* b, T* x) {
     launched(P);
     return;
   }
-  T* r = L.vr.as<T>();
+  T* rr[2] = {L.vr.as<T>(), L.vs.as<T>()};
+  T* qq[2] = {L.vq.as<T>(), L.vt.as<T>()};
   T* d = L.vd.as<T>();
-  T* q = L.vq.as<T>();
+  int ri = 0, qi = 0;
   const int pre = std::max(1, P->opt.pre_smooth), post = std::max(1, P->opt.post_smooth);
-  smooth<T>(P, l, x, b, r, d, q, pre, true);                   // pre-smoothing
-  level_matvec(P, l, d, q);                                     // residual b - A x = r - A d
+  smooth<T>(P, l, x, b, rr, ri, d, qq, qi, pre, true);         // pre-smoothing
+  level_matvec(P, l, d, qq[qi], true);                         // residual b - A x = r - A d
   Level& C = P->levels[l + 1];
   T* rc = C.vb.as<T>();
   T* xc = C.vx.as<T>();
-  k_restrict<T><<<cdiv((long long)C.n * 16, 256), 256, 0, P->stream>>>(C.n, L.bs, L.agg_ptr.as<int>(),
-                                                                     L.agg_mem.as<int>(), qblk<T>(L), r, q, rc);
-  launched(P);                                                  // restriction
-  vcycle<T>(P, l + 1, rc, xc);                                  // coarse-level solve
+  k_restrict<T><<<cdiv((long long)C.n * 16, 64), 64, 0, P->stream>>>(C.n, L.bs, L.agg_ptr.as<int>(),
+                                                                   L.agg_mem.as<int>(), qblk<T>(L), rr[ri],
+                                                                   qq[qi], rc);
+  launched(P);                                                 // restriction
+  vcycle<T>(P, l + 1, rc, xc);                                 // coarse-level solve
+  qi = 1 - qi;
   k_prolong<T><<<cdiv((long long)L.n * L.bs, 256), 256, 0, P->stream>>>(L.n, L.bs, L.agg.as<int>(), qblk<T>(L),
-                                                                      xc, x);
-  launched(P);                                                  // prolongation
-  smooth<T>(P, l, x, b, r, d, q, post, false);                  // post-smoothing
+                                                                      xc, x, diag0<T>(P, l), qq[qi]);
+  launched(P);                                                 // prolongation
+  level_matvec(P, l, x, qq[qi], true);                         // A x for the post-smoothing
+  smooth<T>(P, l, x, b, rr, ri, d, qq, qi, post, false);       // post-smoothing
 }
 
 // ---------------------------------------------------------------------------
@@ -301,12 +333,127 @@ k_pcg_update(size_t n, double* __restrict__ x, double* __restrict__ r, const dou
   grid_sum_store<kVecBS>(acc, partial, counter, scal + S_RR);
 }
 
-// p = z + beta p, beta = scal[rz_new] / scal[rz_old]
+// p = z + beta p, beta = scal[rz_new] / scal[rz_old] (s_new < 0: p = z); q = D_c p, the
+// diagonal term of the next product S p
 __global__ void k_pcg_direction(size_t n, double* __restrict__ p, const double* __restrict__ z,
-                                const double* __restrict__ scal, int s_new, int s_old) {
-  const double beta = scal[s_new] / scal[s_old];
+                                const double* __restrict__ scal, int s_new, int s_old,
+                                const double* __restrict__ Dc, double* __restrict__ q) {
+  const double beta = s_new >= 0 ? scal[s_new] / scal[s_old] : 0.0;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = z[i] + beta * p[i];
+  if (i < n) {
+    const double pi = s_new >= 0 ? z[i] + beta * p[i] : z[i];
+    p[i] = pi;
+    q[i] = Dc[i] * pi;
+  }
+}
+
+// one PCG iteration's head: q = S p; alpha = rz / p.q; x += alpha p; r -= alpha q; rr = r.r
+static void pcg_head(ba_problem* P, double* x) {
+  const size_t n = (size_t)P->n_c * 9;
+  double *r = P->r.as<double>(), *p = P->p.as<double>(), *q = P->q.as<double>();
+  matvec64_accumulate(P, p, q);  // q = D_c p was written with p
+  dot64(P, p, q, n, S_PQ);
+  k_pcg_update<<<reduce_blocks(P, n), kVecBS, 0, P->stream>>>(n, x, r, p, q, P->scal.as<double>(), S_RZ,
+                                                              P->partial.as<double>(), P->counter.as<unsigned>(),
+                                                              P->flags.as<int>());
+  launched(P);
+}
+
+// counts the iteration and sets the loop condition: continue while |r|^2 > rtol^2 |b|^2,
+// no breakdown and fewer than max_iters iterations
+__global__ void k_pcg_check(double* scal, const int* flags, int max_iters, double rtol2,
+                            cudaGraphConditionalHandle h) {
+  const double it = scal[S_ITER] + 1.0;
+  scal[S_ITER] = it;
+  const double rr = scal[S_RR], bb = scal[S_BB];
+  const bool stop = !(rr > rtol2 * bb) || flags[F_BREAKDOWN] != 0 || it >= (double)max_iters;
+  cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+__global__ void k_copy_slot(double* scal, int dst, int src) {
+  if (threadIdx.x == 0) scal[dst] = scal[src];
+}
+
+// one PCG iteration's tail: z = M r; beta = r.z / rz; p = z + beta p; rz = r.z
+static void pcg_tail(ba_problem* P) {
+  const size_t n = (size_t)P->n_c * 9;
+  double *r = P->r.as<double>(), *z = P->z.as<double>(), *p = P->p.as<double>();
+  precond_apply(P, r, z);
+  dot64(P, r, z, n, S_TMP2);
+  k_pcg_direction<<<cdiv((long long)n, 256), 256, 0, P->stream>>>(n, p, z, P->scal.as<double>(), S_TMP2, S_RZ,
+                                                                   P->Dc.as<double>(), P->q.as<double>());
+  launched(P);
+  k_copy_slot<<<1, 32, 0, P->stream>>>(P->scal.as<double>(), S_RZ, S_TMP2);
+  launched(P);
+}
+
+// Builds [head, check] -> while(cond) { tail, head, check } as one executable graph that
+// works on the problem's own vectors (x = P->x).
+static void build_pcg_graph(ba_problem* P) {
+  if (P->pcg_exec) {
+    cudaGraphExecDestroy(P->pcg_exec);
+    P->pcg_exec = nullptr;
+  }
+  if (!P->cap_stream) BA_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = P->stream;
+  const long long launches0 = P->launches;
+  cudaGraph_t g = nullptr;
+  try {
+    const double rtol2 = P->opt.rtol * P->opt.rtol;
+    double* x = P->x.as<double>();
+    BA_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    BA_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    P->stream = P->cap_stream;
+    BA_CUDA(cudaStreamBeginCaptureToGraph(P->cap_stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    pcg_head(P, x);
+    k_pcg_check<<<1, 1, 0, P->stream>>>(P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2, h);
+    launched(P);
+    const long long head_kernels = P->launches - launches0;
+    cudaStreamCaptureStatus status;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t ndeps = 0;
+    cudaGraph_t cg_graph = nullptr;
+    BA_CUDA(cudaStreamGetCaptureInfo(P->cap_stream, &status, nullptr, &cg_graph, &deps, &edges, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    BA_CUDA(cudaGraphAddNode(&cnode, cg_graph, deps, edges, ndeps, &cp));
+    BA_CUDA(cudaStreamUpdateCaptureDependencies(P->cap_stream, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    BA_CUDA(cudaStreamEndCapture(P->cap_stream, &g));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    BA_CUDA(cudaStreamBeginCaptureToGraph(P->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const long long body0 = P->launches;
+    pcg_tail(P);
+    pcg_head(P, x);
+    k_pcg_check<<<1, 1, 0, P->stream>>>(P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2, h);
+    launched(P);
+    BA_CUDA(cudaStreamEndCapture(P->cap_stream, &body));
+    BA_CUDA(cudaGraphInstantiate(&P->pcg_exec, g, 0));
+    cudaGraphDestroy(g);
+    P->pcg_graph_head = head_kernels;
+    P->pcg_graph_body = P->launches - body0;
+    P->stream = user;
+    P->launches = launches0;
+    P->pcg_graph_epoch = P->graph_epoch;
+  } catch (...) {
+    cudaStreamCaptureStatus st;
+    if (cudaStreamIsCapturing(P->cap_stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(P->cap_stream, &junk);
+      if (junk) cudaGraphDestroy(junk);
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    P->stream = user;
+    P->launches = launches0;
+    P->pcg_exec = nullptr;
+    P->graphs_ok = false;
+  }
 }
 
 void pcg(ba_problem* P, const double* rhs, double* dc) {
@@ -316,6 +463,7 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
   P->z.ensure(sizeof(double) * n + 64);
   P->p.ensure(sizeof(double) * n + 64);
   P->q.ensure(sizeof(double) * n + 64);
+  P->x.ensure(sizeof(double) * n + 64);
   double *r = P->r.as<double>(), *z = P->z.as<double>(), *p = P->p.as<double>(), *q = P->q.as<double>();
   double* scal = P->scal.as<double>();
   clear_flags(P);
@@ -333,12 +481,35 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
   precond_apply(P, r, z);
   int s_rz = S_RZ, s_new = S_TMP2;
   dot64(P, r, z, n, s_rz);
-  BA_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream));
+  k_pcg_direction<<<g, 256, 0, P->stream>>>(n, p, z, scal, -1, 0, P->Dc.as<double>(), q);  // p = z
+  launched(P);
   const int rg = reduce_blocks(P, n);
   double rel = 1.0;
   int it = 0;
+  // graph-driven loop: no host round trip per iteration
+  if (!P->ktime && P->graphs_ok) {
+    if (P->pcg_graph_epoch != P->graph_epoch || !P->pcg_exec) build_pcg_graph(P);
+    if (P->pcg_exec) {
+      double* x = P->x.as<double>();
+      BA_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, P->stream));
+      BA_CUDA(cudaMemsetAsync(scal + S_ITER, 0, sizeof(double), P->stream));
+      BA_CUDA(cudaGraphLaunch(P->pcg_exec, P->stream));
+      BA_CUDA(cudaMemcpyAsync(dc, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream));
+      fetch_scalars(P, S_RR, S_ITER - S_RR + 1);
+      check_flags(P);
+      it = (int)P->h_scal[S_ITER];
+      P->launches += P->pcg_graph_head + (long long)std::max(it - 1, 0) * P->pcg_graph_body;
+      rel = std::sqrt(P->h_scal[S_RR] / bb);
+      BA_REQUIRE(std::isfinite(rel), BA_ERR_BREAKDOWN, "non-finite PCG residual");
+      P->pcg_iters = it;
+      P->pcg_rel = rel;
+      if (rel > P->opt.rtol)
+        throw Error(BA_ERR_NOT_CONVERGED, "PCG reached max_iters with relative residual " + std::to_string(rel));
+      return;
+    }
+  }
   while (it < P->opt.max_iters) {
-    matvec64(P, p, q);
+    matvec64_accumulate(P, p, q);  // q = D_c p was written with p
     dot64(P, p, q, n, S_PQ);
     k_pcg_update<<<rg, kVecBS, 0, P->stream>>>(n, dc, r, p, q, scal, s_rz, P->partial.as<double>(),
                                                P->counter.as<unsigned>(), P->flags.as<int>());
@@ -351,7 +522,7 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
     if (rel <= P->opt.rtol) break;
     precond_apply(P, r, z);
     dot64(P, r, z, n, s_new);
-    k_pcg_direction<<<g, 256, 0, P->stream>>>(n, p, z, scal, s_new, s_rz);
+    k_pcg_direction<<<g, 256, 0, P->stream>>>(n, p, z, scal, s_new, s_rz, P->Dc.as<double>(), q);
     launched(P);
     std::swap(s_rz, s_new);
   }
