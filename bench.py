@@ -190,7 +190,9 @@ def gpu_main(args):
 
     def make(precision):
         return api.from_scene(s, device=dev, precision=precision, rtol=wl["rtol"], max_iters=2000,
-                              coarse_max_nodes=args.coarse_max_nodes)
+                              coarse_max_nodes=args.coarse_max_nodes,
+                              level0_operator={"implicit": _ffi.BA_OP_IMPLICIT, "explicit": _ffi.BA_OP_EXPLICIT,
+                                               "auto": _ffi.BA_OP_AUTO}[args.level0])
 
     prob, cams, pts, obs = make(prec)
     cams0, pts0 = cams.clone(), pts.clone()
@@ -355,6 +357,7 @@ def gpu_main(args):
             "config": {"workload": args.workload, "n_cams": n_c, "n_pts": n_p, "n_obs": n_o, "rtol": wl["rtol"],
                        "precision": args.precision, "preconditioner": "multigrid",
                        "coarse_max_nodes": args.coarse_max_nodes,
+                       "level0_operator": ("assembled" if info["level0_explicit"] else "implicit"),
                        "levels": info["level_nodes"], "pcg_iters": info["pcg_iters"],
                        "parallelism": f"replicas x{world}",
                        "l2": "per-step working set > L2 (FP64+FP32 Jacobian blocks ~0.43 GB), no flush"},
@@ -400,6 +403,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--coarse-max-nodes", type=int, default=32)
+    ap.add_argument("--level0", default="implicit", choices=["implicit", "explicit", "auto"],
+                    help="V-cycle finest-level operator: implicit Jacobian stream or the assembled S")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -51,6 +51,13 @@ typedef enum {
 typedef enum { BA_FP64 = 0, BA_MIXED = 1 } ba_precision;
 typedef enum { BA_PRECOND_NONE = 0, BA_PRECOND_JACOBI = 1, BA_PRECOND_MG = 2 } ba_precond;
 typedef enum { BA_DAMP_MARQUARDT = 0, BA_DAMP_IDENTITY = 1 } ba_damping;
+/* Level-0 operator of the V-cycle (Section 3.6 weighs applying the camera system
+ * implicitly from the Jacobian blocks against assembling it): IMPLICIT streams the
+ * per-observation blocks on every product; EXPLICIT uses the 9x9 block-sparse S that
+ * ba_mg_setup assembles anyway for the Galerkin product; AUTO picks EXPLICIT when its
+ * blocks take fewer bytes than one implicit pass over the Jacobian.  The outer PCG
+ * product is implicit in every case. */
+typedef enum { BA_OP_IMPLICIT = 0, BA_OP_EXPLICIT = 1, BA_OP_AUTO = 2 } ba_operator;
 
 typedef struct {
   double lambda;        /* LM damping used by ba_lm_step's first call (Section 5: 1/1e4) */
@@ -68,6 +75,7 @@ typedef struct {
   int max_levels;       /* hierarchy depth cap (10) */
   double cheb_lo;       /* Chebyshev interval [cheb_lo, cheb_hi] * lambda_max (0.3, 1.1) */
   double cheb_hi;
+  int level0_operator;  /* ba_operator of the V-cycle's finest level (BA_OP_IMPLICIT) */
 } ba_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -154,6 +162,7 @@ typedef struct {
   double cost;            /* last ba_linearize */
   double lambda;          /* last ba_schur_setup */
   long long kernel_launches; /* kernels launched by this problem so far */
+  int level0_explicit;    /* 1 if the last ba_mg_setup chose the assembled level-0 operator */
 } ba_info;
 
 ba_status ba_get_info(ba_problem* prob, ba_info* info);

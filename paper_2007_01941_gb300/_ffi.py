@@ -14,6 +14,7 @@ STATUS_NAMES = {0: "BA_OK", 1: "BA_ERR_INVALID_ARG", 2: "BA_ERR_CUDA", 3: "BA_ER
                 7: "BA_ERR_LIMIT", 8: "BA_ERR_STATE"}
 BA_FP64, BA_MIXED = 0, 1
 BA_PRECOND_NONE, BA_PRECOND_JACOBI, BA_PRECOND_MG = 0, 1, 2
+BA_OP_IMPLICIT, BA_OP_EXPLICIT, BA_OP_AUTO = 0, 1, 2
 BA_DAMP_MARQUARDT, BA_DAMP_IDENTITY = 0, 1
 BA_KT_SCHUR_FP64, BA_KT_SCHUR_FP32, BA_KT_LINEARIZE = 0, 1, 2
 
@@ -29,14 +30,16 @@ class Options(ctypes.Structure):
                 ("precision", c_int), ("preconditioner", c_int), ("damping", c_int),
                 ("recompute_jacobian", c_int), ("max_agg", c_int), ("pre_smooth", c_int),
                 ("post_smooth", c_int), ("lanczos_steps", c_int), ("coarse_max_nodes", c_int),
-                ("max_levels", c_int), ("cheb_lo", c_double), ("cheb_hi", c_double)]
+                ("max_levels", c_int), ("cheb_lo", c_double), ("cheb_hi", c_double),
+                ("level0_operator", c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("n_levels", c_int), ("level_nodes", c_int * 16), ("level_block", c_int * 16),
                 ("level_nnzb", c_int * 16), ("level_lambda_max", c_double * 16),
                 ("pcg_iters", c_int), ("pcg_rel_res", c_double), ("cost", c_double),
-                ("lambda_", c_double), ("kernel_launches", c_longlong)]
+                ("lambda_", c_double), ("kernel_launches", c_longlong),
+                ("level0_explicit", c_int)]
 
 
 _lib = None

@@ -171,7 +171,8 @@ class Problem:
         return dict(n_levels=n, level_nodes=list(inf.level_nodes[:n]), level_block=list(inf.level_block[:n]),
                     level_nnzb=list(inf.level_nnzb[:n]), level_lambda_max=list(inf.level_lambda_max[:n]),
                     pcg_iters=inf.pcg_iters, pcg_rel_res=inf.pcg_rel_res, cost=inf.cost,
-                    lam=inf.lambda_, kernel_launches=inf.kernel_launches)
+                    lam=inf.lambda_, kernel_launches=inf.kernel_launches,
+                    level0_explicit=bool(inf.level0_explicit))
 
     _ARR_DTYPE = {
         _ffi.BA_ARR_LEVEL_ROWPTR: torch.int32, _ffi.BA_ARR_LEVEL_COLS: torch.int32,

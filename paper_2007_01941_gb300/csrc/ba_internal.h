@@ -131,9 +131,12 @@ struct ba_problem {
   ba::DBuf pt_user;             // int32 [n_p] internal point -> caller point
   ba::DBuf cam_ptr, cam_obs;    // camera-major CSR over internal obs
   int n_tiles = 0, n_chunks = 0, k3_window = 0;
+  int k3_grid[2] = {0, 0};
+  bool l0_explicit = false;     // V-cycle level 0 uses the assembled S (set by the multigrid setup)       // Schur product CTAs per launch (FP32, FP64), set at first use
   unsigned k3_calls = 0;        // alternates the tile order of successive Schur products
   ba::DBuf tile_pt;             // int32 [n_tiles + 1] point ranges of <=32-obs warp tiles
   ba::DBuf tile_desc;           // int4 [n_tiles] {first obs, obs count, first point, start mask}
+  ba::DBuf tile_perm;           // uint8 [n_tiles][32] camera order of a tile's lanes (bit 7: run start)
   ba::DBuf chunk_tile;          // int32 [n_chunks + 1] tile ranges per matvec CTA
   ba::DBuf chunk_cam;           // int32 [2 n_chunks] lowest / highest camera of a chunk
   size_t ld = 0;                // leading dimension of per-observation SoA arrays

@@ -122,8 +122,25 @@ void build_graph(ba_problem* P, const int32_t* cam_idx_dev, const int32_t* pt_id
       for (int p = p0; p < p1; ++p) mask |= 1u << (pt_ptr[p] - ob);
     tile_desc[t] = make_int4(ob, nobs, p0, (int)mask);
   }
-  // CTA chunks: contiguous tile ranges with about equal observation counts
-  int want = std::max(1, std::min(P->n_sm * 3, n_tiles / 8));
+  // per-tile camera order of the lanes, for the camera-side reduction of the FP32 Schur
+  // product: byte j of tile t = (lane holding the j-th observation in camera order) |
+  // 128 if position j starts a run of equal cameras; positions >= the observation
+  // count map to themselves and start their own run
+  std::vector<uint8_t> tile_perm((size_t)std::max(n_tiles, 1) * 32);
+  for (int t = 0; t < n_tiles; ++t) {
+    const int ob = tile_desc[t].x, nobs = tile_desc[t].y;
+    int idx[32];
+    for (int j = 0; j < 32; ++j) idx[j] = j;
+    if (nobs <= 32)
+      std::stable_sort(idx, idx + nobs, [&](int a, int b) { return obs_cam[ob + a] < obs_cam[ob + b]; });
+    for (int j = 0; j < 32; ++j) {
+      const bool head = nobs > 32 || j >= nobs || j == 0 || obs_cam[ob + idx[j]] != obs_cam[ob + idx[j - 1]];
+      tile_perm[(size_t)t * 32 + j] = (uint8_t)(idx[j] | (head ? 128 : 0));
+    }
+  }
+  // CTA chunks: contiguous tile ranges with about equal observation counts, a dozen per
+  // SM so that CTAs looping over them stay balanced
+  int want = std::max(1, std::min(P->n_sm * 12, n_tiles / 8));
   if (n_tiles == 0) want = 0;
   std::vector<int32_t> chunk_tile(1, 0), chunk_cam;
   if (n_tiles > 0) {
@@ -164,6 +181,7 @@ void build_graph(ba_problem* P, const int32_t* cam_idx_dev, const int32_t* pt_id
   upload(P, P->cam_obs, cam_obs);
   upload(P, P->tile_pt, tile_pt);
   upload(P, P->tile_desc, tile_desc);
+  upload(P, P->tile_perm, tile_perm);
   upload(P, P->chunk_tile, chunk_tile);
   upload(P, P->chunk_cam, chunk_cam);
   sync(P);

@@ -323,158 +323,217 @@ void schur_setup(ba_problem* P, double lambda) {
 // ---------------------------------------------------------------------------
 constexpr int kK3Warps = 8;
 
-template <typename T, bool WINDOW>
-__device__ __forceinline__ void k3_scatter(T* acc, T* __restrict__ y, int c, int cam_lo, int span,
-                                           const T yv[9]) {
-  const int rel = c - cam_lo;
-  if (WINDOW && rel < span) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) atomicAdd(acc + 9 * rel + k, yv[k]);
-  } else {
-    T* yc = y + 9 * (size_t)c;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) atomicAdd(yc + k, yv[k]);
-  }
+// component k of a lane's 9-vector is camera component rot_index(rot, k)
+__device__ __forceinline__ int rot_index(int rot, int k) {
+  const int j = rot + k;
+  return j >= 9 ? j - 9 : j;
 }
 
 template <typename T, bool WINDOW>
-__global__ void __launch_bounds__(kK3Warps * 32, 3)
+__device__ __forceinline__ void k3_scatter(T* acc, T* __restrict__ y, int c, int cam_lo, int span,
+                                           const T yv[9], int rot) {
+  const int rel = c - cam_lo;
+  T* dst = (WINDOW && rel < span) ? acc + 9 * rel : y + 9 * (size_t)c;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) atomicAdd(dst + rot_index(rot, k), yv[k]);
+}
+
+template <typename T, bool WINDOW>
+__global__ void __launch_bounds__(kK3Warps * 32, sizeof(T) == 4 ? 4 : 3)
 k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, int ld,
                const T* __restrict__ Cinv, int ldp, const int* __restrict__ obs_cam,
-               const int4* __restrict__ tile_desc, const int* __restrict__ chunk_tile,
-               const int* __restrict__ chunk_cam, const T* __restrict__ x, T* __restrict__ y, int win,
-               int reverse) {
+               const int4* __restrict__ tile_desc, const unsigned char* __restrict__ tile_perm,
+               const int* __restrict__ chunk_tile, const int* __restrict__ chunk_cam, int n_chunks, const T* __restrict__ x,
+               T* __restrict__ y, int win, int reverse) {
+  constexpr bool kPermute = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char k3_smem[];
   T* acc = reinterpret_cast<T*>(k3_smem);
-  const int chunk = blockIdx.x;
-  const int cam_lo = chunk_cam[2 * chunk];
-  const int cam_hi = chunk_cam[2 * chunk + 1];
-  const int span = WINDOW ? min(cam_hi - cam_lo + 1, win) : 0;
-  if (WINDOW) {
-    for (int i = threadIdx.x; i < span * 9; i += blockDim.x) acc[i] = T(0);
-    __syncthreads();
-  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // reverse != 0 walks the chunk's tiles from its end, where the previous product left
-  // the most recently used lines in L2
-  const int t_begin = chunk_tile[chunk], t_end = chunk_tile[chunk + 1];
-  for (int i = warp; i < t_end - t_begin; i += kK3Warps) {
-    const int t = reverse ? t_end - 1 - i : t_begin + i;
-    const int4 desc = __ldg(tile_desc + t);
-    const int ob = desc.x, nobs = desc.y, p0 = desc.z;
-    if (nobs <= 32) {
-      const unsigned startmask = (unsigned)desc.w;
-      const bool active = lane < nobs;
-      const unsigned le = (lane == 31) ? kFull : ((2u << lane) - 1u);
-      const int seg_head = 31 - __clz(startmask & le);
-      const unsigned after = startmask & ~le;
-      const int seg_end = active ? (after ? (__ffs(after) - 2) : (nobs - 1)) : lane;
-      const int ip = p0 + __popc(startmask & le) - 1;
-      const int o = active ? ob + lane : ob;
-      const int c = __ldg(obs_cam + o);
-      T f[18], e[6];
-      load_record(F + (size_t)o * kRec, f, e);
-      const T* xc = x + 9 * (size_t)c;
-      T u0 = T(0), u1 = T(0);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        const T xv = __ldg(xc + k);
-        u0 += f[k] * xv;
-        u1 += f[9 + k] * xv;
-      }
-      if (!active) {
-        u0 = T(0);
-        u1 = T(0);
-      }
-      T s0 = e[0] * u0 + e[3] * u1;
-      T s1 = e[1] * u0 + e[4] * u1;
-      T s2 = e[2] * u0 + e[5] * u1;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const T a0 = __shfl_down_sync(kFull, s0, d);
-        const T a1 = __shfl_down_sync(kFull, s1, d);
-        const T a2 = __shfl_down_sync(kFull, s2, d);
-        if (lane + d <= seg_end) {
-          s0 += a0;
-          s1 += a1;
-          s2 += a2;
-        }
-      }
-      const T v0 = __shfl_sync(kFull, s0, seg_head);
-      const T v1 = __shfl_sync(kFull, s1, seg_head);
-      const T v2 = __shfl_sync(kFull, s2, seg_head);
-      if (active) {
+  // a CTA takes chunks blockIdx.x, blockIdx.x + gridDim.x, ...: the grid is one wave of
+  // resident CTAs and the chunks are small enough to balance the SMs
+  for (int chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
+    const int cam_lo = chunk_cam[2 * chunk];
+    const int cam_hi = chunk_cam[2 * chunk + 1];
+    const int span = WINDOW ? min(cam_hi - cam_lo + 1, win) : 0;
+    if (WINDOW) {
+      for (int i = threadIdx.x; i < span * 9; i += blockDim.x) acc[i] = T(0);
+      __syncthreads();
+    }
+    // reverse != 0 walks the chunk's tiles from its end, where the previous product left
+    // the most recently used lines in L2
+    const int t_begin = chunk_tile[chunk], t_end = chunk_tile[chunk + 1];
+    for (int i = warp; i < t_end - t_begin; i += kK3Warps) {
+      const int t = reverse ? t_end - 1 - i : t_begin + i;
+      const int4 desc = __ldg(tile_desc + t);
+      const unsigned pb = kPermute ? (unsigned)__ldg(tile_perm + (size_t)t * 32 + lane) : 0u;
+      const int ob = desc.x, nobs = desc.y, p0 = desc.z;
+      if (nobs <= 32) {
+        const unsigned startmask = (unsigned)desc.w;
+        const bool active = lane < nobs;
+        const unsigned le = (lane == 31) ? kFull : ((2u << lane) - 1u);
+        const int seg_head = 31 - __clz(startmask & le);
+        const unsigned after = startmask & ~le;
+        const int seg_end = active ? (after ? (__ffs(after) - 2) : (nobs - 1)) : lane;
+        const int ip = p0 + __popc(startmask & le) - 1;
+        const int o = active ? ob + lane : ob;
+        // C_p^-1 is needed only after the point sums; in FP32 its loads go out now so that
+        // they overlap the record loads instead of adding a round trip after the scan (the
+        // FP64 kernel is arithmetic-bound and has no registers to spare for them)
         const T* Ci = Cinv + ip;
-        const T c00 = __ldg(Ci), c01 = __ldg(Ci + ldp), c02 = __ldg(Ci + 2 * ldp);
-        const T c11 = __ldg(Ci + 3 * ldp), c12 = __ldg(Ci + 4 * ldp), c22 = __ldg(Ci + 5 * ldp);
+        T c00, c01, c02, c11, c12, c22;
+        if constexpr (kPermute) {
+          c00 = __ldg(Ci), c01 = __ldg(Ci + ldp), c02 = __ldg(Ci + 2 * ldp);
+          c11 = __ldg(Ci + 3 * ldp), c12 = __ldg(Ci + 4 * ldp), c22 = __ldg(Ci + 5 * ldp);
+        }
+        const int c = __ldg(obs_cam + o);
+        // FP64: lane l visits the 9 camera components starting at l mod 9, so that lanes
+        // of one camera add into different words of y at the same time
+        const int rot = kPermute ? 0 : lane % 9;
+        T f[18], e[6];
+        if constexpr (kPermute) {
+          load_record(F + (size_t)o * kRec, f, e);
+        } else {
+          const T* r = F + (size_t)o * kRec;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const int j = rot_index(rot, k);
+            f[k] = __ldcs(r + j);
+            f[9 + k] = __ldcs(r + 9 + j);
+          }
+#pragma unroll
+          for (int k = 0; k < 6; ++k) e[k] = __ldcs(r + 18 + k);
+        }
+        // scan steps needed: ceil(log2(longest point segment of the tile))
+        const int seglen = __reduce_max_sync(kFull, (unsigned)(seg_end - seg_head + 1));
+        const T* xc = x + 9 * (size_t)c;
+        T u0 = T(0), u1 = T(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          const T xv = __ldg(xc + rot_index(rot, k));
+          u0 += f[k] * xv;
+          u1 += f[9 + k] * xv;
+        }
+        if (!active) {
+          u0 = T(0);
+          u1 = T(0);
+        }
+        T s0 = e[0] * u0 + e[3] * u1;
+        T s1 = e[1] * u0 + e[4] * u1;
+        T s2 = e[2] * u0 + e[5] * u1;
+        for (int d = 1; d < seglen; d <<= 1) {
+          const T a0 = __shfl_down_sync(kFull, s0, d);
+          const T a1 = __shfl_down_sync(kFull, s1, d);
+          const T a2 = __shfl_down_sync(kFull, s2, d);
+          if (lane + d <= seg_end) {
+            s0 += a0;
+            s1 += a1;
+            s2 += a2;
+          }
+        }
+        const T v0 = __shfl_sync(kFull, s0, seg_head);
+        const T v1 = __shfl_sync(kFull, s1, seg_head);
+        const T v2 = __shfl_sync(kFull, s2, seg_head);
+        if constexpr (!kPermute) {
+          c00 = __ldg(Ci), c01 = __ldg(Ci + ldp), c02 = __ldg(Ci + 2 * ldp);
+          c11 = __ldg(Ci + 3 * ldp), c12 = __ldg(Ci + 4 * ldp), c22 = __ldg(Ci + 5 * ldp);
+        }
         const T z0 = c00 * v0 + c01 * v1 + c02 * v2;
         const T z1 = c01 * v0 + c11 * v1 + c12 * v2;
         const T z2 = c02 * v0 + c12 * v1 + c22 * v2;
-        const T w0 = u0 - (e[0] * z0 + e[1] * z1 + e[2] * z2);
-        const T w1 = u1 - (e[3] * z0 + e[4] * z1 + e[5] * z2);
+        T w0 = u0 - (e[0] * z0 + e[1] * z1 + e[2] * z2);
+        T w1 = u1 - (e[3] * z0 + e[4] * z1 + e[5] * z2);
+        if (!active) {
+          w0 = T(0);
+          w1 = T(0);
+        }
         T yv[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) yv[k] = f[k] * w0 + f[9 + k] * w1;
-        k3_scatter<T, WINDOW>(acc, y, c, cam_lo, span, yv);
-      }
-    } else {
-      // one point with more than 32 observations
-      const int ip = p0;
-      T s0 = T(0), s1 = T(0), s2 = T(0);
-      for (int base = 0; base < nobs; base += 32) {
-        const int o = ob + base + lane;
-        if (base + lane < nobs) {
-          const int c = obs_cam[o];
-          const T* xc = x + 9 * (size_t)c;
-          T u0 = T(0), u1 = T(0);
+        if constexpr (kPermute) {
+          // camera sums: move the lanes into the tile's camera order, add each run of
+          // equal cameras into its first lane with a segmented shuffle reduction, and let
+          // that lane alone add the camera's 9 values into the window (no two lanes of a
+          // warp then update one address)
+          const int src = pb & 31;
+          const bool run_head = (pb >> 7) != 0;
 #pragma unroll
-          for (int k = 0; k < 9; ++k) {
-            u0 += JF(F, o, k) * xc[k];
-            u1 += JF(F, o, 9 + k) * xc[k];
+          for (int k = 0; k < 9; ++k) yv[k] = __shfl_sync(kFull, yv[k], src);
+          const int cs = __shfl_sync(kFull, c, src);
+          const unsigned heads = __ballot_sync(kFull, run_head);
+          const unsigned later = heads & ~le;
+          const int run_end = later ? __ffs(later) - 2 : 31;
+          const int runlen = __reduce_max_sync(kFull, run_head ? (unsigned)(run_end - lane + 1) : 1u);
+          for (int d = 1; d < runlen; d <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+              const T a = __shfl_down_sync(kFull, yv[k], d);
+              if (lane + d <= run_end) yv[k] += a;
+            }
           }
-          s0 += JE(E, o, 0) * u0 + JE(E, o, 3) * u1;
-          s1 += JE(E, o, 1) * u0 + JE(E, o, 4) * u1;
-          s2 += JE(E, o, 2) * u0 + JE(E, o, 5) * u1;
+          if (run_head && lane < nobs) k3_scatter<T, WINDOW>(acc, y, cs, cam_lo, span, yv, 0);
+        } else if (active) {
+          k3_scatter<T, WINDOW>(acc, y, c, cam_lo, span, yv, rot);
         }
-      }
-      s0 = warp_sum(s0);
-      s1 = warp_sum(s1);
-      s2 = warp_sum(s2);
-      const T c00 = Cinv[ip], c01 = Cinv[ldp + ip], c02 = Cinv[2 * ldp + ip];
-      const T c11 = Cinv[3 * ldp + ip], c12 = Cinv[4 * ldp + ip], c22 = Cinv[5 * ldp + ip];
-      const T z0 = c00 * s0 + c01 * s1 + c02 * s2;
-      const T z1 = c01 * s0 + c11 * s1 + c12 * s2;
-      const T z2 = c02 * s0 + c12 * s1 + c22 * s2;
-      for (int base = 0; base < nobs; base += 32) {
-        const int o = ob + base + lane;
-        if (base + lane < nobs) {
-          const int c = obs_cam[o];
-          const T* xc = x + 9 * (size_t)c;
-          T f[18];
+      } else {
+        // one point with more than 32 observations
+        const int ip = p0;
+        T s0 = T(0), s1 = T(0), s2 = T(0);
+        for (int base = 0; base < nobs; base += 32) {
+          const int o = ob + base + lane;
+          if (base + lane < nobs) {
+            const int c = obs_cam[o];
+            const T* xc = x + 9 * (size_t)c;
+            T u0 = T(0), u1 = T(0);
 #pragma unroll
-          for (int k = 0; k < 18; ++k) f[k] = JF(F, o, k);
-          T u0 = T(0), u1 = T(0);
-#pragma unroll
-          for (int k = 0; k < 9; ++k) {
-            u0 += f[k] * xc[k];
-            u1 += f[9 + k] * xc[k];
+            for (int k = 0; k < 9; ++k) {
+              u0 += JF(F, o, k) * xc[k];
+              u1 += JF(F, o, 9 + k) * xc[k];
+            }
+            s0 += JE(E, o, 0) * u0 + JE(E, o, 3) * u1;
+            s1 += JE(E, o, 1) * u0 + JE(E, o, 4) * u1;
+            s2 += JE(E, o, 2) * u0 + JE(E, o, 5) * u1;
           }
-          const T w0 = u0 - (JE(E, o, 0) * z0 + JE(E, o, 1) * z1 + JE(E, o, 2) * z2);
-          const T w1 = u1 - (JE(E, o, 3) * z0 + JE(E, o, 4) * z1 + JE(E, o, 5) * z2);
-          T yv[9];
+        }
+        s0 = warp_sum(s0);
+        s1 = warp_sum(s1);
+        s2 = warp_sum(s2);
+        const T c00 = Cinv[ip], c01 = Cinv[ldp + ip], c02 = Cinv[2 * ldp + ip];
+        const T c11 = Cinv[3 * ldp + ip], c12 = Cinv[4 * ldp + ip], c22 = Cinv[5 * ldp + ip];
+        const T z0 = c00 * s0 + c01 * s1 + c02 * s2;
+        const T z1 = c01 * s0 + c11 * s1 + c12 * s2;
+        const T z2 = c02 * s0 + c12 * s1 + c22 * s2;
+        for (int base = 0; base < nobs; base += 32) {
+          const int o = ob + base + lane;
+          if (base + lane < nobs) {
+            const int c = obs_cam[o];
+            const T* xc = x + 9 * (size_t)c;
+            T f[18];
 #pragma unroll
-          for (int k = 0; k < 9; ++k) yv[k] = f[k] * w0 + f[9 + k] * w1;
-          k3_scatter<T, WINDOW>(acc, y, c, cam_lo, span, yv);
+            for (int k = 0; k < 18; ++k) f[k] = JF(F, o, k);
+            T u0 = T(0), u1 = T(0);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+              u0 += f[k] * xc[k];
+              u1 += f[9 + k] * xc[k];
+            }
+            const T w0 = u0 - (JE(E, o, 0) * z0 + JE(E, o, 1) * z1 + JE(E, o, 2) * z2);
+            const T w1 = u1 - (JE(E, o, 3) * z0 + JE(E, o, 4) * z1 + JE(E, o, 5) * z2);
+            T yv[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) yv[k] = f[k] * w0 + f[9 + k] * w1;
+            k3_scatter<T, WINDOW>(acc, y, c, cam_lo, span, yv, 0);
+          }
         }
       }
     }
-  }
-  if (WINDOW) {
-    __syncthreads();
-    T* yb = y + 9 * (size_t)cam_lo;
-    for (int i = threadIdx.x; i < span * 9; i += blockDim.x) {
-      const T v = acc[i];
-      if (v != T(0)) atomicAdd(yb + i, v);
+    if (WINDOW) {
+      __syncthreads();
+      T* yb = y + 9 * (size_t)cam_lo;
+      for (int i = threadIdx.x; i < span * 9; i += blockDim.x) {
+        const T v = acc[i];
+        if (v != T(0)) atomicAdd(yb + i, v);
+      }
+      __syncthreads();
     }
   }
 }
@@ -496,10 +555,19 @@ static void launch_matvec(ba_problem* P, const T* F, const T* E, const T* Cinv, 
                                  (int)(sizeof(T) * 9 * 1024)));
     attr_set = true;
   }
+  int& grid = P->k3_grid[sizeof(T) == 8];
+  if (grid == 0) {
+    // one wave: every SM holds as many CTAs as registers and shared memory allow
+    int per_sm = 0;
+    BA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_schur_matvec<T, window>,
+                                                          kK3Warps * 32, smem));
+    grid = std::max(1, std::min(P->n_chunks, P->n_sm * std::max(per_sm, 1)));
+  }
   KernelTimer kt(P, sizeof(T) == 8 ? BA_KT_SCHUR_FP64 : BA_KT_SCHUR_FP32);
-  k_schur_matvec<T, window><<<P->n_chunks, kK3Warps * 32, smem, P->stream>>>(
+  k_schur_matvec<T, window><<<grid, kK3Warps * 32, smem, P->stream>>>(
       F, E, (int)P->ld, Cinv, (int)P->ldp, P->obs_cam.as<int>(), P->tile_desc.as<int4>(),
-      P->chunk_tile.as<int>(), P->chunk_cam.as<int>(), x, y, P->k3_window, (P->k3_calls++) & 1);
+      P->tile_perm.as<unsigned char>(), P->chunk_tile.as<int>(), P->chunk_cam.as<int>(), P->n_chunks, x, y, P->k3_window,
+      (P->k3_calls++) & 1);
   launched(P);
 }
 

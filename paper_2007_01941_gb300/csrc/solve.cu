@@ -36,11 +36,48 @@ __global__ void k_bsr16_spmv(int n, const int* __restrict__ row_ptr, const int* 
   y[(size_t)i * 16 + u] = sizeof(T) == 4 ? (T)accf : (T)accd;
 }
 
+// y = S x for the assembled 9x9-block camera system: one warp per block row; lane
+// r + 9k (k < 3) takes output row r of blocks k, k+3, ... of the row, and the three
+// partial sums of row r meet in lane r.
+template <typename T>
+__global__ void k_bsr9_spmv(int n, const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                            const T* __restrict__ vals, const T* __restrict__ x, T* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const int r = lane % 9, k = lane / 9;
+  T acc = T(0);
+  if (k < 3) {
+    const int e1 = row_ptr[i + 1];
+    for (int e = row_ptr[i] + k; e < e1; e += 3) {
+      const T* a = vals + (size_t)e * 81 + r * 9;
+      const T* xv = x + (size_t)cols[e] * 9;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) acc += __ldg(a + c) * __ldg(xv + c);
+    }
+  }
+  const T a1 = __shfl_sync(kFull, acc, min(lane + 9, 31));
+  const T a2 = __shfl_sync(kFull, acc, min(lane + 18, 31));
+  if (lane < 9) y[(size_t)i * 9 + r] = acc + a1 + a2;
+}
+
 // y = A_l x.  At level 0 with `ready`, y already holds D_c x (written by the kernel
 // that produced x) and the product only accumulates.
 void level_matvec(ba_problem* P, int l, const void* x, void* y, bool ready) {
   Level& L = P->levels[l];
   const bool fp32 = level_fp32(P);
+  if (l == 0 && P->l0_explicit) {
+    // the assembled S already holds D_c: overwrite y
+    const int g = cdiv(L.n, 4);
+    if (fp32)
+      k_bsr9_spmv<float><<<g, 128, 0, P->stream>>>(L.n, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                   L.vals32.as<float>(), (const float*)x, (float*)y);
+    else
+      k_bsr9_spmv<double><<<g, 128, 0, P->stream>>>(L.n, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                    L.vals64.as<double>(), (const double*)x, (double*)y);
+    launched(P);
+    return;
+  }
   if (l == 0) {
     if (fp32) {
       if (ready) matvec32_accumulate(P, (const float*)x, (float*)y);

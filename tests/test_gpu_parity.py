@@ -153,13 +153,16 @@ def test_hierarchy_matches_oracle(gpu, prec):
         assert abs(lam_gpu - L.lam_max) <= (1e-9 if prec == "fp64" else 1e-3) * L.lam_max, l
 
 
-def test_vcycle_matches_oracle(gpu):
+@pytest.mark.parametrize("level0", ["implicit", "explicit"])
+def test_vcycle_matches_oracle(gpu, level0):
     api, F_ = _api()
     s = scene("street_chain", **CHAIN)
-    prob, cams, pts, obs = _prob(s, gpu, coarse_max_nodes=16)
+    op = {"implicit": F_.BA_OP_IMPLICIT, "explicit": F_.BA_OP_EXPLICIT}[level0]
+    prob, cams, pts, obs = _prob(s, gpu, coarse_max_nodes=16, level0_operator=op)
     prob.linearize(cams, pts, obs)
     prob.schur_setup(s.lam)
     prob.mg_setup()
+    assert prob.info()["level0_explicit"] == (level0 == "explicit")
     sch, H = _oracle_hierarchy(s, 16)
     for seed in range(2):
         r = np.random.default_rng(seed).normal(size=9 * s.n_cams)
@@ -200,6 +203,33 @@ def test_mixed_precision_solution_matches_oracle(gpu):
     true_rel = np.linalg.norm(sch.b - sch.S @ d) / np.linalg.norm(sch.b)
     assert true_rel <= 2e-10
     assert np.linalg.norm(d - exact) <= 1e-6 * np.linalg.norm(exact)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pcg_assembled_level0_matches_oracle(gpu, precision):
+    """V-cycle on the assembled 9x9-block S (Section 3.6's explicit choice): same
+    solution as the dense solve, iteration counts as with the implicit level 0."""
+    api, F_ = _api()
+    s = scene("street_chain", **CHAIN)
+    prec = {"fp64": F_.BA_FP64, "mixed": F_.BA_MIXED}[precision]
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+    exact = sla.cho_solve(sla.cho_factor(sch.S.toarray()), sch.b)
+    res = {}
+    # forward error <= cond(S) x residual: the FP64 check needs the tighter residual
+    rtol = 1e-12 if precision == "fp64" else 1e-10
+    for op in (F_.BA_OP_IMPLICIT, F_.BA_OP_EXPLICIT, F_.BA_OP_AUTO):
+        prob, cams, pts, obs = _prob(s, gpu, precision=prec, coarse_max_nodes=16, rtol=rtol,
+                                     level0_operator=op, max_iters=5000)
+        dc, dp, it, relres = prob.solve(cams, pts, obs, s.lam)
+        assert relres <= rtol
+        d = _np(dc).ravel()
+        assert np.linalg.norm(d - exact) <= (1e-8 if precision == "fp64" else 1e-6) * np.linalg.norm(exact)
+        res[op] = (it, prob.info()["level0_explicit"])
+    assert res[F_.BA_OP_EXPLICIT][1] and not res[F_.BA_OP_IMPLICIT][1]
+    # the assembled blocks take far fewer bytes than the Jacobian stream here
+    assert res[F_.BA_OP_AUTO][1]
+    it_imp, it_exp = res[F_.BA_OP_IMPLICIT][0], res[F_.BA_OP_EXPLICIT][0]
+    assert abs(it_imp - it_exp) <= max(1, it_imp // 10), (it_imp, it_exp)
 
 
 def test_lm_step_matches_oracle(gpu):
