@@ -188,11 +188,12 @@ def gpu_main(args):
     s = getattr(scenes, wl["fn"])(**wl["kw"])
     prec = _ffi.BA_MIXED if args.precision == "mixed" else _ffi.BA_FP64
 
-    def make(precision):
+    L0 = {"implicit": _ffi.BA_OP_IMPLICIT, "explicit": _ffi.BA_OP_EXPLICIT, "auto": _ffi.BA_OP_AUTO}
+
+    def make(precision, level0=None):
         return api.from_scene(s, device=dev, precision=precision, rtol=wl["rtol"], max_iters=2000,
                               coarse_max_nodes=args.coarse_max_nodes,
-                              level0_operator={"implicit": _ffi.BA_OP_IMPLICIT, "explicit": _ffi.BA_OP_EXPLICIT,
-                                               "auto": _ffi.BA_OP_AUTO}[args.level0])
+                              level0_operator=L0[level0 or args.level0])
 
     prob, cams, pts, obs = make(prec)
     cams0, pts0 = cams.clone(), pts.clone()
@@ -237,6 +238,7 @@ def gpu_main(args):
         step(prob, cams, pts)
     kt = {k: prob.kernel_timing(c) for k, c in (("schur_fp32", _ffi.BA_KT_SCHUR_FP32),
                                                 ("schur_fp64", _ffi.BA_KT_SCHUR_FP64),
+                                                ("schur_df", _ffi.BA_KT_SCHUR_DF),
                                                 ("linearize", _ffi.BA_KT_LINEARIZE))}
     prob.set_kernel_timing(False)
 
@@ -271,6 +273,32 @@ def gpu_main(args):
         fp64 = max_over_ranks(e0.elapsed_time(e1) / n64)
         it64 = p64.info()["pcg_iters"]
         p64.close()
+
+    # the same step with the implicit level-0 operator (Jacobian stream in every V-cycle
+    # product), for comparison and for the FP32 implicit-product kernel timing
+    implicit = None
+    kt_var = {}
+    if not info["level0_explicit"] or args.skip_variants:
+        pass
+    else:
+        pim, cim, xim, _ = make(prec, "implicit")
+        for _ in range(2):
+            step(pim, cim, xim)
+        nim = max(2, min(args.steps, 10))
+        barrier()
+        e0.record(stream)
+        for _ in range(nim):
+            step(pim, cim, xim)
+        e1.record(stream)
+        barrier()
+        implicit = {"ms_per_step": max_over_ranks(e0.elapsed_time(e1) / nim),
+                    "pcg_iters": pim.info()["pcg_iters"]}
+        pim.set_kernel_timing(True)
+        for _ in range(2):
+            step(pim, cim, xim)
+        kt_var["schur_fp32"] = pim.kernel_timing(_ffi.BA_KT_SCHUR_FP32)
+        pim.set_kernel_timing(False)
+        pim.close()
 
     # end to end through the public API with host buffers: H2D of the step's inputs
     # (cameras, points, observations) from pinned memory, the step, D2H of the result
@@ -308,13 +336,18 @@ def gpu_main(args):
     fp64_peak_tflops = 1.205   # FMA-chain probe on this machine's GB300
     n_o, n_p, n_c = s.n_obs, s.n_pts, s.n_cams
     kernels = {}
-    for name, (tot, n) in kt.items():
+    for name, (tot, n) in list(kt.items()) + list(kt_var.items()):
         if n == 0:
             continue
         avg = tot / n
         d = {"launches": n, "avg_ms": avg}
+        if name in kt_var:
+            d["run"] = "implicit level-0 variant"
         if name == "schur_fp32":
             b = k3_bytes(n_o, n_p, n_c, 4)
+            d.update(bound="hbm", achieved=b / avg / 1e6, unit="GB/s", algo_bytes=b)
+        elif name == "schur_df":
+            b = k3_bytes(n_o, n_p, n_c, 8)   # hi + lo floats: the FP64 byte count
             d.update(bound="hbm", achieved=b / avg / 1e6, unit="GB/s", algo_bytes=b)
         elif name == "schur_fp64":
             b = k3_bytes(n_o, n_p, n_c, 8)
@@ -323,11 +356,15 @@ def gpu_main(args):
                      hbm_gbs=b / avg / 1e6, algo_bytes=b)
         kernels[name] = d
     # dominant kernel class by total time
-    dom = max(kernels, key=lambda k: kt[k][0]) if kernels else None
+    dom = max((k for k in kernels if k in kt and kt[k][1] > 0), key=lambda k: kt[k][0], default=None)
     roofline = None
     if dom == "schur_fp32" or (dom == "linearize" and "schur_fp32" in kernels):
         k = kernels["schur_fp32"]
         roofline = {"kernel": "k_schur_matvec<float>", "bound": "hbm", "achieved": k["achieved"], "peak": hbm,
+                    "unit": "GB/s", "frac": k["achieved"] / hbm, "traffic": None, "peak_source": peak_note}
+    elif dom == "schur_df":
+        k = kernels["schur_df"]
+        roofline = {"kernel": "k_schur_matvec_df", "bound": "hbm", "achieved": k["achieved"], "peak": hbm,
                     "unit": "GB/s", "frac": k["achieved"] / hbm, "traffic": None, "peak_source": peak_note}
     elif dom == "schur_fp64":
         k = kernels["schur_fp64"]
@@ -364,6 +401,7 @@ def gpu_main(args):
             "parts_ms": {"linearize": t_lin, "schur_setup": t_sch, "mg_setup": t_mg, "pcg_solve": t_pcg,
                          "pcg_iters": iters},
             "fp64_ms_per_step": fp64,
+            "implicit_level0": implicit,
             "mixed_speedup_vs_fp64": (fp64 / ms) if fp64 else None,
             "kernels": kernels,
             "roofline": roofline,
@@ -378,16 +416,16 @@ def gpu_main(args):
 
 
 def _traffic_from_profiles(dom):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if the
-    kernel source is still the one the counters were taken on (else None)."""
+    """DRAM bytes per launch of the dominant kernel class from the committed ncu summary,
+    if the kernel's source file is still the one the counters were taken on (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        d = json.load(open(path))
-        src = open(os.path.join(ROOT, "paper_2007_01941_gb300", "csrc", "schur.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest() != d.get("schur_cu_sha256"):
+        entry = json.load(open(path))["kernels"][dom]
+        src = open(os.path.join(ROOT, "paper_2007_01941_gb300", entry["file"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != entry["sha256"]:
             return None
-        return d.get(dom)
+        return entry["bytes"]
     except Exception:
         return None
 
@@ -403,8 +441,10 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--coarse-max-nodes", type=int, default=32)
-    ap.add_argument("--level0", default="implicit", choices=["implicit", "explicit", "auto"],
-                    help="V-cycle finest-level operator: implicit Jacobian stream or the assembled S")
+    ap.add_argument("--level0", default="auto", choices=["implicit", "explicit", "auto"],
+                    help="V-cycle finest-level operator: implicit Jacobian stream, the assembled S, "
+                         "or the cheaper of the two (Section 3.6)")
+    ap.add_argument("--skip-variants", action="store_true", help="skip the implicit level-0 comparison run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -58,6 +58,12 @@ typedef enum { BA_DAMP_MARQUARDT = 0, BA_DAMP_IDENTITY = 1 } ba_damping;
  * blocks take fewer bytes than one implicit pass over the Jacobian.  The outer PCG
  * product is implicit in every case. */
 typedef enum { BA_OP_IMPLICIT = 0, BA_OP_EXPLICIT = 1, BA_OP_AUTO = 2 } ba_operator;
+/* Arithmetic of the outer PCG product S p in BA_MIXED (BA_FP64 always uses FP64):
+ * FP64 instructions, or FP64-valued operands carried as pairs of floats (hi + lo, about
+ * 48 significant bits) and combined with error-free FP32 transformations, which this
+ * GPU issues at many times its FP64 rate.  The PCG vectors, dot products, residual and
+ * the product's accumulation stay FP64 either way. */
+typedef enum { BA_OUTER_FP64 = 0, BA_OUTER_PAIRED_FP32 = 1 } ba_outer_product;
 
 typedef struct {
   double lambda;        /* LM damping used by ba_lm_step's first call (Section 5: 1/1e4) */
@@ -75,7 +81,10 @@ typedef struct {
   int max_levels;       /* hierarchy depth cap (10) */
   double cheb_lo;       /* Chebyshev interval [cheb_lo, cheb_hi] * lambda_max (0.3, 1.1) */
   double cheb_hi;
-  int level0_operator;  /* ba_operator of the V-cycle's finest level (BA_OP_IMPLICIT) */
+  int level0_operator;  /* ba_operator of the V-cycle's finest level (BA_OP_AUTO) */
+  int fused_vcycle;     /* 1: with an assembled level 0, fuse each block-sparse product of the
+                           V-cycle into the smoothing or restriction step that consumes it (1) */
+  int outer_product;    /* ba_outer_product used by BA_MIXED (BA_OUTER_PAIRED_FP32) */
 } ba_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -199,7 +208,8 @@ typedef enum {
   BA_KT_SCHUR_FP64 = 0,  /* implicit Schur product, FP64 storage (outer PCG operator) */
   BA_KT_SCHUR_FP32 = 1,  /* implicit Schur product, FP32 storage (inside the V-cycle) */
   BA_KT_LINEARIZE = 2,   /* residual + Jacobian kernel */
-  BA_KT_COUNT = 3
+  BA_KT_SCHUR_DF = 3,    /* implicit Schur product in paired FP32 (outer operator, mixed mode) */
+  BA_KT_COUNT = 4
 } ba_kernel_class;
 
 /* enable != 0 starts recording a CUDA event pair around every launch of the timed

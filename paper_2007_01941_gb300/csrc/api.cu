@@ -90,7 +90,9 @@ void ba_default_options(ba_options* o) {
   o->max_levels = 10;
   o->cheb_lo = 0.3;
   o->cheb_hi = 1.1;
-  o->level0_operator = BA_OP_IMPLICIT;
+  o->level0_operator = BA_OP_AUTO;
+  o->fused_vcycle = 1;
+  o->outer_product = BA_OUTER_PAIRED_FP32;
 }
 
 ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx, const int32_t* pt_idx,
@@ -119,6 +121,8 @@ ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx, co
     BA_REQUIRE(o.max_levels >= 1 && o.coarse_max_nodes >= 1, BA_ERR_INVALID_ARG, "bad hierarchy limits");
     BA_REQUIRE(o.level0_operator >= BA_OP_IMPLICIT && o.level0_operator <= BA_OP_AUTO, BA_ERR_INVALID_ARG,
                "bad level0_operator");
+    BA_REQUIRE(o.outer_product == BA_OUTER_FP64 || o.outer_product == BA_OUTER_PAIRED_FP32, BA_ERR_INVALID_ARG,
+               "bad outer_product");
     int dev = 0;
     BA_CUDA(cudaGetDevice(&dev));
     BA_CUDA(cudaDeviceGetAttribute(&P->n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -148,8 +152,8 @@ void ba_destroy(ba_problem* P) {
   cudaStreamSynchronize(P->stream);
   ba::DBuf* bufs[] = {&P->obs_user, &P->obs_cam, &P->obs_ptu, &P->obs_pt, &P->pt_ptr, &P->pt_user, &P->cam_ptr,
                       &P->cam_obs, &P->tile_pt, &P->tile_desc, &P->tile_perm, &P->chunk_tile, &P->chunk_cam, &P->camx, &P->fres, &P->J64,
-                      &P->J64, &P->J32, &P->J32, &P->cams_lin, &P->pts_lin, &P->obs_lin, &P->Dc, &P->Dp,
-                      &P->Cinv64, &P->Cinv32, &P->gc, &P->gp, &P->wp, &P->rhs, &P->Dc32, &P->Scc, &P->Scc_inv,
+                      &P->J64, &P->J32, &P->J32lo, &P->cams_lin, &P->pts_lin, &P->obs_lin, &P->Dc, &P->Dp,
+                      &P->Cinv64, &P->Cinv32, &P->Cinv32lo, &P->xsplit, &P->gc, &P->gp, &P->wp, &P->rhs, &P->Dc32, &P->Scc, &P->Scc_inv,
                       &P->Scc_inv32, &P->x, &P->r, &P->z, &P->p, &P->q, &P->y32a, &P->y32b, &P->delta_c,
                       &P->delta_p, &P->scal, &P->partial, &P->counter, &P->flags, &P->scratch, &P->scratch2};
   for (ba::DBuf* b : bufs) b->release();

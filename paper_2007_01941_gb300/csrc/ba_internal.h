@@ -103,6 +103,7 @@ struct Level {
   DBuf kept;                    // uint32 [n] kept-dof masks of this level's nodes
   DBuf Dblk, Dinv64, Dinv32;    // diagonal blocks and their inverses [n][bs][bs]
   DBuf cheb;                    // double[4]: theta, delta, sigma1, lambda_max
+  double cheb_host[4] = {1, 1, 1, 1};  // host copy of the same
   double lam_max = 0.0;
   bool coarsest = false;
   int N = 0;                    // coarsest: dense size n*bs
@@ -131,8 +132,10 @@ struct ba_problem {
   ba::DBuf pt_user;             // int32 [n_p] internal point -> caller point
   ba::DBuf cam_ptr, cam_obs;    // camera-major CSR over internal obs
   int n_tiles = 0, n_chunks = 0, k3_window = 0;
-  int k3_grid[2] = {0, 0};
-  bool l0_explicit = false;     // V-cycle level 0 uses the assembled S (set by the multigrid setup)       // Schur product CTAs per launch (FP32, FP64), set at first use
+  int k3_grid[2] = {0, 0};       // Schur product CTAs per launch (FP32, FP64), set at first use
+  int k3_grid_df = 0;           // the same for the paired-FP32 product
+  bool l0_explicit = false;     // V-cycle level 0 uses the assembled S (set by the multigrid setup)
+  bool vc_ready = false;        // the fused-phase V-cycle applies (set by the multigrid setup)
   unsigned k3_calls = 0;        // alternates the tile order of successive Schur products
   ba::DBuf tile_pt;             // int32 [n_tiles + 1] point ranges of <=32-obs warp tiles
   ba::DBuf tile_desc;           // int4 [n_tiles] {first obs, obs count, first point, start mask}
@@ -149,6 +152,7 @@ struct ba_problem {
   ba::DBuf fres;                // double [n_o][2] residuals
   ba::DBuf J64;                 // double [n_o][24] Jacobian records (F row-major, then E)
   ba::DBuf J32;                 // float copy of the records (mixed precision)
+  ba::DBuf J32lo;               // float rounding residual J64 - J32 (mixed precision)
   ba::DBuf cams_lin, pts_lin;   // copies of the linearisation point (adjoint, nullspace)
   ba::DBuf obs_lin;             // copy of the observations of the last linearisation
 
@@ -156,6 +160,8 @@ struct ba_problem {
   double lambda = 0.0;
   ba::DBuf Dc, Dp;              // double [n_c*9], [ldp][3] (internal points, SoA)
   ba::DBuf Cinv64, Cinv32;      // [6][ldp]
+  ba::DBuf Cinv32lo;            // [6][ldp] float rounding residual Cinv64 - Cinv32
+  ba::DBuf xsplit;              // float2 [n_c][9] hi/lo split of a camera vector
   ba::DBuf gc, gp, wp, rhs;     // g_c [n_c*9], g_p [3][ldp], C^-1 g_p [3][ldp], b [n_c*9]
   ba::DBuf Dc32;                // float copy of D_c
   ba::DBuf Scc;                 // double [n_c][81] diagonal blocks S_cc
@@ -239,6 +245,11 @@ void matvec32(ba_problem* P, const float* x, float* y);
 // the same products without writing D_c x first (y must already hold it)
 void matvec64_accumulate(ba_problem* P, const double* x, double* y);
 void matvec32_accumulate(ba_problem* P, const float* x, float* y);
+bool outer_df(ba_problem* P);                                         // mixed mode, paired-FP32 outer product
+void split_vector(ba_problem* P, const double* x, const double* Dc, double* y);  // xsplit = split(x); y = Dc o x
+void matvec_df_accumulate(ba_problem* P, double* y);                   // y += S x - Dc x from xsplit
+void fused_vcycle_setup(ba_problem* P);
+void fused_vcycle(ba_problem* P, const double* r, double* z);
 void explicit_schur(ba_problem* P, Level& L0, bool fp32);
 void back_substitute_to(ba_problem* P, const double* dc, double* out_int, double* out_user);
 void reduced_rhs(ba_problem* P, const double* vc, const double* vp_user, double* out);

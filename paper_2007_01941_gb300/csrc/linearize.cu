@@ -144,9 +144,8 @@ k_linearize(const double* __restrict__ cams, const double* __restrict__ pts,
             const double* __restrict__ obs, const double* __restrict__ camx,
             const int* __restrict__ obs_cam, const int* __restrict__ obs_ptu,
             const int* __restrict__ obs_user, int n_o, size_t ld, double* __restrict__ fres,
-            double* __restrict__ F64, double* __restrict__ E64, float* __restrict__ F32,
-            float* __restrict__ E32, double* partial, unsigned* counter, double* cost_out,
-            int* flags) {
+            double* __restrict__ J64, float* __restrict__ J32, float* __restrict__ J32lo,
+            double* partial, unsigned* counter, double* cost_out, int* flags) {
   double acc = 0.0;
   for (int o = blockIdx.x * kLinBS + threadIdx.x; o < n_o; o += gridDim.x * kLinBS) {
     const int c = obs_cam[o];
@@ -167,14 +166,24 @@ k_linearize(const double* __restrict__ cams, const double* __restrict__ pts,
       for (int k = 0; k < 6; ++k) rec[18 + k] = v.E[k];
 #pragma unroll
       for (int k = 0; k < kRec; ++k) finite = finite && isfinite(rec[k]);
-      double2* d64 = reinterpret_cast<double2*>(F64 + (size_t)o * kRec);
+      double2* d64 = reinterpret_cast<double2*>(J64 + (size_t)o * kRec);
 #pragma unroll
       for (int k = 0; k < kRec / 2; ++k) d64[k] = make_double2(rec[2 * k], rec[2 * k + 1]);
       if (MIXED) {
-        float4* d32 = reinterpret_cast<float4*>(F32 + (size_t)o * kRec);
+        // FP32 copy (hi) and the rounding residual (lo): hi + lo carries ~48 bits
+        float hi[kRec], lo[kRec];
 #pragma unroll
-        for (int k = 0; k < kRec / 4; ++k)
-          d32[k] = make_float4((float)rec[4 * k], (float)rec[4 * k + 1], (float)rec[4 * k + 2], (float)rec[4 * k + 3]);
+        for (int k = 0; k < kRec; ++k) {
+          hi[k] = (float)rec[k];
+          lo[k] = (float)(rec[k] - (double)hi[k]);
+        }
+        float4* d32 = reinterpret_cast<float4*>(J32 + (size_t)o * kRec);
+        float4* l32 = reinterpret_cast<float4*>(J32lo + (size_t)o * kRec);
+#pragma unroll
+        for (int k = 0; k < kRec / 4; ++k) {
+          d32[k] = make_float4(hi[4 * k], hi[4 * k + 1], hi[4 * k + 2], hi[4 * k + 3]);
+          l32[k] = make_float4(lo[4 * k], lo[4 * k + 1], lo[4 * k + 2], lo[4 * k + 3]);
+        }
       }
       if (!finite) flags[F_NONFINITE] = 1;
     }
@@ -199,7 +208,10 @@ void linearize(ba_problem* P, const double* cams, const double* pts, const doubl
   P->camx.ensure(sizeof(double) * kCamx * std::max(P->n_c, 1));
   P->fres.ensure(sizeof(double) * 2 * ld);
   P->J64.ensure(sizeof(double) * kRec * ld);
-  if (mixed) P->J32.ensure(sizeof(float) * kRec * ld);
+  if (mixed) {
+    P->J32.ensure(sizeof(float) * kRec * ld);
+    P->J32lo.ensure(sizeof(float) * kRec * ld);
+  }
   // keep the linearisation point (near-nullspace and adjoint use it)
   P->cams_lin.ensure(sizeof(double) * 9 * std::max(P->n_c, 1));
   P->pts_lin.ensure(sizeof(double) * 3 * std::max(P->n_p, 1));
@@ -217,15 +229,13 @@ void linearize(ba_problem* P, const double* cams, const double* pts, const doubl
   if (mixed)
     k_linearize<true, true><<<g, kLinBS, 0, P->stream>>>(
         cams, pts, obs, P->camx.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
-        P->obs_user.as<int>(), P->n_o, ld, P->fres.as<double>(), P->J64.as<double>(),
-        P->J64.as<double>(), P->J32.as<float>(), P->J32.as<float>(), P->partial.as<double>(),
-        P->counter.as<unsigned>(), cost, P->flags.as<int>());
+        P->obs_user.as<int>(), P->n_o, ld, P->fres.as<double>(), P->J64.as<double>(), P->J32.as<float>(),
+        P->J32lo.as<float>(), P->partial.as<double>(), P->counter.as<unsigned>(), cost, P->flags.as<int>());
   else
     k_linearize<true, false><<<g, kLinBS, 0, P->stream>>>(
         cams, pts, obs, P->camx.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
-        P->obs_user.as<int>(), P->n_o, ld, P->fres.as<double>(), P->J64.as<double>(),
-        P->J64.as<double>(), nullptr, nullptr, P->partial.as<double>(), P->counter.as<unsigned>(),
-        cost, P->flags.as<int>());
+        P->obs_user.as<int>(), P->n_o, ld, P->fres.as<double>(), P->J64.as<double>(), nullptr, nullptr,
+        P->partial.as<double>(), P->counter.as<unsigned>(), cost, P->flags.as<int>());
   launched(P);
 }
 
@@ -235,7 +245,7 @@ double cost_at(ba_problem* P, const double* cams, const double* pts, const doubl
   int g = lin_grid(P);
   k_linearize<false, false><<<g, kLinBS, 0, P->stream>>>(
       cams, pts, obs, P->scratch2.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
-      P->obs_user.as<int>(), P->n_o, P->ld, nullptr, nullptr, nullptr, nullptr, nullptr,
+      P->obs_user.as<int>(), P->n_o, P->ld, nullptr, nullptr, nullptr, nullptr,
       P->partial.as<double>(), P->counter.as<unsigned>(), P->scal.as<double>() + S_COST_NEW,
       P->flags.as<int>());
   launched(P);

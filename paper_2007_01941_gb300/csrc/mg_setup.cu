@@ -824,6 +824,7 @@ static void finish_lanczos(ba_problem* P) {
     double* c = h + kChebSlots * k;
     tridiag_cheb(c + 8, c + 16, m, P->opt.cheb_lo, P->opt.cheb_hi, c);
     P->levels[k].lam_max = c[3];
+    for (int j = 0; j < 4; ++j) P->levels[k].cheb_host[j] = c[j];
     BA_CUDA(cudaMemcpyAsync(P->levels[k].cheb.p, c, sizeof(double) * 4, cudaMemcpyHostToDevice, P->stream));
   }
 }
@@ -1182,6 +1183,7 @@ void mg_setup(ba_problem* P) {
     L.vt.ensure(es * n);
     L.vs.ensure(es * n);
   }
+  fused_vcycle_setup(P);
 }
 
 }  // namespace ba

@@ -17,7 +17,8 @@ __global__ void k_point_setup(const double* __restrict__ E, const double* __rest
                               size_t ld, const int* __restrict__ pt_ptr, int n_p, int n_p_obs,
                               size_t ldp, double lambda, int damp_identity, double* __restrict__ Dp,
                               double* __restrict__ Cinv, float* __restrict__ Cinv32,
-                              double* __restrict__ gp, double* __restrict__ wp, int* flags) {
+                              float* __restrict__ Cinv32lo, double* __restrict__ gp, double* __restrict__ wp,
+                              int* flags) {
   int ip = blockIdx.x * blockDim.x + threadIdx.x;
   if (ip >= n_p) return;
   double c00 = 0, c01 = 0, c02 = 0, c11 = 0, c12 = 0, c22 = 0, g0 = 0, g1 = 0, g2 = 0;
@@ -62,7 +63,11 @@ __global__ void k_point_setup(const double* __restrict__ E, const double* __rest
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     Cinv[k * ldp + ip] = inv[k];
-    if (Cinv32) Cinv32[k * ldp + ip] = (float)inv[k];
+    if (Cinv32) {
+      const float hi = (float)inv[k];
+      Cinv32[k * ldp + ip] = hi;
+      Cinv32lo[k * ldp + ip] = (float)(inv[k] - (double)hi);
+    }
   }
   wp[ip] = inv[0] * g0 + inv[1] * g1 + inv[2] * g2;
   wp[ldp + ip] = inv[1] * g0 + inv[3] * g1 + inv[4] * g2;
@@ -268,7 +273,10 @@ void schur_setup(ba_problem* P, double lambda) {
   P->Dc32.ensure(sizeof(float) * 9 * n_c + 64);
   P->Dp.ensure(sizeof(double) * 3 * ldp);
   P->Cinv64.ensure(sizeof(double) * 6 * ldp);
-  if (mixed) P->Cinv32.ensure(sizeof(float) * 6 * ldp);
+  if (mixed) {
+    P->Cinv32.ensure(sizeof(float) * 6 * ldp);
+    P->Cinv32lo.ensure(sizeof(float) * 6 * ldp);
+  }
   P->gc.ensure(sizeof(double) * 9 * n_c + 64);
   P->gp.ensure(sizeof(double) * 3 * ldp);
   P->wp.ensure(sizeof(double) * 3 * ldp);
@@ -282,8 +290,8 @@ void schur_setup(ba_problem* P, double lambda) {
     k_point_setup<<<cdiv(n_p, 128), 128, 0, P->stream>>>(
         P->J64.as<double>(), P->fres.as<double>(), P->ld, P->pt_ptr.as<int>(), n_p, P->n_p_obs, ldp,
         lambda, damp_id, P->Dp.as<double>(), P->Cinv64.as<double>(),
-        mixed ? P->Cinv32.as<float>() : nullptr, P->gp.as<double>(), P->wp.as<double>(),
-        P->flags.as<int>());
+        mixed ? P->Cinv32.as<float>() : nullptr, mixed ? P->Cinv32lo.as<float>() : nullptr,
+        P->gp.as<double>(), P->wp.as<double>(), P->flags.as<int>());
     launched(P);
   }
   k_camera_setup<<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
@@ -572,6 +580,11 @@ static void launch_matvec(ba_problem* P, const T* F, const T* E, const T* Cinv, 
 }
 
 void matvec64(ba_problem* P, const double* x, double* y) {
+  if (outer_df(P)) {
+    split_vector(P, x, P->Dc.as<double>(), y);
+    matvec_df_accumulate(P, y);
+    return;
+  }
   const int n = 9 * P->n_c;
   k_diag_init<double, double><<<cdiv(n, 256), 256, 0, P->stream>>>(P->Dc.as<double>(), x, y, n);
   launched(P);
@@ -585,8 +598,13 @@ void matvec32(ba_problem* P, const float* x, float* y) {
   launch_matvec<float>(P, P->J32.as<float>(), P->J32.as<float>(), P->Cinv32.as<float>(), x, y);
 }
 
-// the products alone, for callers whose producing kernel already wrote y = D_c x
+// the products alone, for callers whose producing kernel already wrote y = D_c x (and,
+// for the paired-FP32 product, the split of x into P->xsplit)
 void matvec64_accumulate(ba_problem* P, const double* x, double* y) {
+  if (outer_df(P)) {
+    matvec_df_accumulate(P, y);
+    return;
+  }
   launch_matvec<double>(P, P->J64.as<double>(), P->J64.as<double>(), P->Cinv64.as<double>(), x, y);
 }
 void matvec32_accumulate(ba_problem* P, const float* x, float* y) {

@@ -327,6 +327,10 @@ void precond_apply(ba_problem* P, const double* r, double* z) {
     return;
   }
   BA_REQUIRE(P->n_levels > 0, BA_ERR_STATE, "ba_mg_setup has not been run");
+  if (P->vc_ready) {
+    fused_vcycle(P, r, z);
+    return;
+  }
   Level& L0 = P->levels[0];
   if (level_fp32(P)) {
     float* b = L0.vb.as<float>();
@@ -371,17 +375,28 @@ k_pcg_update(size_t n, double* __restrict__ x, double* __restrict__ r, const dou
 }
 
 // p = z + beta p, beta = scal[rz_new] / scal[rz_old] (s_new < 0: p = z); q = D_c p, the
-// diagonal term of the next product S p
+// diagonal term of the next product S p; ps (if given) = hi/lo float split of p, the
+// input of the paired-FP32 product
 __global__ void k_pcg_direction(size_t n, double* __restrict__ p, const double* __restrict__ z,
                                 const double* __restrict__ scal, int s_new, int s_old,
-                                const double* __restrict__ Dc, double* __restrict__ q) {
+                                const double* __restrict__ Dc, double* __restrict__ q, float2* __restrict__ ps) {
   const double beta = s_new >= 0 ? scal[s_new] / scal[s_old] : 0.0;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     const double pi = s_new >= 0 ? z[i] + beta * p[i] : z[i];
     p[i] = pi;
     q[i] = Dc[i] * pi;
+    if (ps) {
+      const float h = (float)pi;
+      ps[i] = make_float2(h, (float)(pi - (double)h));
+    }
   }
+}
+
+static float2* split_target(ba_problem* P) {
+  if (!outer_df(P)) return nullptr;
+  P->xsplit.ensure(sizeof(float2) * 9 * (size_t)P->n_c + 64);
+  return P->xsplit.as<float2>();
 }
 
 // one PCG iteration's head: q = S p; alpha = rz / p.q; x += alpha p; r -= alpha q; rr = r.r
@@ -418,7 +433,8 @@ static void pcg_tail(ba_problem* P) {
   precond_apply(P, r, z);
   dot64(P, r, z, n, S_TMP2);
   k_pcg_direction<<<cdiv((long long)n, 256), 256, 0, P->stream>>>(n, p, z, P->scal.as<double>(), S_TMP2, S_RZ,
-                                                                   P->Dc.as<double>(), P->q.as<double>());
+                                                                   P->Dc.as<double>(), P->q.as<double>(),
+                                                                   split_target(P));
   launched(P);
   k_copy_slot<<<1, 32, 0, P->stream>>>(P->scal.as<double>(), S_RZ, S_TMP2);
   launched(P);
@@ -518,7 +534,8 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
   precond_apply(P, r, z);
   int s_rz = S_RZ, s_new = S_TMP2;
   dot64(P, r, z, n, s_rz);
-  k_pcg_direction<<<g, 256, 0, P->stream>>>(n, p, z, scal, -1, 0, P->Dc.as<double>(), q);  // p = z
+  k_pcg_direction<<<g, 256, 0, P->stream>>>(n, p, z, scal, -1, 0, P->Dc.as<double>(), q,
+                                            split_target(P));  // p = z
   launched(P);
   const int rg = reduce_blocks(P, n);
   double rel = 1.0;
@@ -559,7 +576,8 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
     if (rel <= P->opt.rtol) break;
     precond_apply(P, r, z);
     dot64(P, r, z, n, s_new);
-    k_pcg_direction<<<g, 256, 0, P->stream>>>(n, p, z, scal, s_new, s_rz, P->Dc.as<double>(), q);
+    k_pcg_direction<<<g, 256, 0, P->stream>>>(n, p, z, scal, s_new, s_rz, P->Dc.as<double>(), q,
+                                              split_target(P));
     launched(P);
     std::swap(s_rz, s_new);
   }
