@@ -18,8 +18,10 @@ from . import camera, multigrid, pcg as pcg_mod, schur
 MIN_RELATIVE_DECREASE = 1e-3
 
 
-def solve_step(sch: schur.Schur, cams, precond="mg", rtol=1e-8, max_iters=1000, **mg_kw):
-    """delta_c by PCG on S (with the chosen preconditioner) and delta_p by back-substitution."""
+def solve_step(sch: schur.Schur, cams, precond="mg", rtol=1e-8, max_iters=1000, stop="relres", tau=0.1,
+               **mg_kw):
+    """delta_c by PCG on S (with the chosen preconditioner and stopping rule) and delta_p
+    by back-substitution."""
     if precond == "mg":
         W = multigrid.covisibility(sch.cam_idx, sch.pt_idx, sch.n_cams, sch.n_pts)
         H = multigrid.Hierarchy(sch.S, W, cams, **mg_kw)
@@ -30,7 +32,7 @@ def solve_step(sch: schur.Schur, cams, precond="mg", rtol=1e-8, max_iters=1000, 
         M = lambda r: Minv @ r
     else:
         M = None
-    dc, it, rel, hist = pcg_mod.pcg(lambda v: sch.S @ v, sch.b, M, rtol, max_iters)
+    dc, it, rel, hist = pcg_mod.pcg(lambda v: sch.S @ v, sch.b, M, rtol, max_iters, stop=stop, tau=tau)
     dp = sch.back_substitute(dc)
     return dc, dp, it, rel
 

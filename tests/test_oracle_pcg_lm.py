@@ -26,6 +26,64 @@ def test_iterations_fall_as_the_preconditioner_strengthens():
     assert its["none"] > its["jacobi"] > its["mg"]
 
 
+def _spd(n, cond, seed):
+    rng = np.random.default_rng(seed)
+    Qm, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    return (Qm * np.geomspace(1.0, cond, n)) @ Qm.T, rng.normal(size=n)
+
+
+def test_nash_sofer_stop_matches_textbook_cg_and_definition():
+    """Section 2.1's forcing rule: the stop is the first i with i (Q_i - Q_{i-1}) / Q_i <= tau,
+    Q_i = 1/2 x_i^T A x_i - x_i^T b, Q_0 = 0.  A textbook CG loop written here, with Q
+    from a dense product, finds the same i."""
+    A, b = _spd(120, 1e4, 3)
+    for tau in (0.5, 0.1, 0.01):
+        x_o, it_o, _, _ = pcg.pcg(lambda v: A @ v, b, None, rtol=0.0, max_iters=500, stop="nash_sofer", tau=tau)
+        x = np.zeros_like(b)
+        r = b.copy()
+        d = r.copy()
+        q_prev, stop_at = 0.0, None
+        for i in range(1, 500):
+            Ad = A @ d
+            a = (r @ r) / (d @ Ad)
+            x = x + a * d
+            r_new = r - a * Ad
+            d = r_new + ((r_new @ r_new) / (r @ r)) * d
+            r = r_new
+            q = 0.5 * x @ A @ x - x @ b
+            if i * (q - q_prev) / q <= tau:
+                stop_at = i
+                break
+            q_prev = q
+        assert stop_at is not None and it_o == stop_at, (tau, it_o, stop_at)
+        assert np.linalg.norm(x_o - x) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_quadratic_model_decreases_to_its_minimum():
+    # CG minimises Q over growing Krylov spaces: Q_i decreases towards -1/2 b^T A^-1 b
+    A, b = _spd(60, 1e3, 4)
+    qs = []
+    for it in list(range(1, 40)) + [400]:
+        x, _, _, _ = pcg.pcg(lambda v: A @ v, b, None, rtol=0.0, max_iters=it)
+        qs.append(pcg.quadratic_model(lambda v: A @ v, b, x))
+    assert all(q1 <= q0 + 1e-9 * abs(q0) for q0, q1 in zip(qs, qs[1:]))
+    qmin = -0.5 * b @ np.linalg.solve(A, b)
+    assert abs(qs[-1] - qmin) <= 1e-10 * abs(qmin)
+
+
+def test_nash_sofer_solves_tighter_with_the_stronger_preconditioner():
+    # Section 2.1: the iteration count in the rule makes a stronger preconditioner stop
+    # at a tighter tolerance
+    s = scene("street_chain", n_cams=300, n_pts=30000)
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+    res = {}
+    for pc in ("jacobi", "mg"):
+        dc, _, it, _ = lm.solve_step(sch, s.cams, pc, rtol=0.0, max_iters=3000, stop="nash_sofer", tau=0.1,
+                                     coarse_max_nodes=16)
+        res[pc] = np.linalg.norm(sch.b - sch.S @ dc) / np.linalg.norm(sch.b)
+    assert res["mg"] < res["jacobi"]
+
+
 def test_pcg_zero_rhs_and_identity():
     x, it, rel, _ = pcg.pcg(lambda v: 2 * v, np.zeros(5))
     assert it == 0 and np.all(x == 0)
