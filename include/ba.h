@@ -64,6 +64,11 @@ typedef enum { BA_OP_IMPLICIT = 0, BA_OP_EXPLICIT = 1, BA_OP_AUTO = 2 } ba_opera
  * GPU issues at many times its FP64 rate.  The PCG vectors, dot products, residual and
  * the product's accumulation stay FP64 either way. */
 typedef enum { BA_OUTER_FP64 = 0, BA_OUTER_PAIRED_FP32 = 1 } ba_outer_product;
+/* PCG stopping rule: the relative recursive residual |r_i| <= rtol |b|, or the
+ * Nash-Sofer forcing rule of Section 2.1, i (Q_i - Q_{i-1}) / Q_i <= tau with the
+ * quadratic model Q_i = 1/2 x_i^T S x_i - x_i^T b (Q_0 = 0), evaluated from the CG
+ * recurrence Q_i - Q_{i-1} = -alpha_i (r_{i-1}^T z_{i-1}) / 2. */
+typedef enum { BA_STOP_RELRES = 0, BA_STOP_NASH_SOFER = 1 } ba_stop_rule;
 
 typedef struct {
   double lambda;        /* LM damping used by ba_lm_step's first call (Section 5: 1/1e4) */
@@ -85,6 +90,8 @@ typedef struct {
   int fused_vcycle;     /* 1: with an assembled level 0, fuse each block-sparse product of the
                            V-cycle into the smoothing or restriction step that consumes it (1) */
   int outer_product;    /* ba_outer_product used by BA_MIXED (BA_OUTER_PAIRED_FP32) */
+  int stop_rule;        /* ba_stop_rule (BA_STOP_RELRES) */
+  double tau;           /* Nash-Sofer tolerance (0.1; Section 5 uses 0.1 and 0.01) */
 } ba_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -18,6 +18,7 @@ BA_OP_IMPLICIT, BA_OP_EXPLICIT, BA_OP_AUTO = 0, 1, 2
 BA_DAMP_MARQUARDT, BA_DAMP_IDENTITY = 0, 1
 BA_KT_SCHUR_FP64, BA_KT_SCHUR_FP32, BA_KT_LINEARIZE, BA_KT_SCHUR_DF = 0, 1, 2, 3
 BA_OUTER_FP64, BA_OUTER_PAIRED_FP32 = 0, 1
+BA_STOP_RELRES, BA_STOP_NASH_SOFER = 0, 1
 
 (BA_ARR_RESIDUAL, BA_ARR_JAC_F, BA_ARR_JAC_E, BA_ARR_DAMP_C, BA_ARR_DAMP_P, BA_ARR_CINV,
  BA_ARR_GRAD_C, BA_ARR_GRAD_P, BA_ARR_RHS, BA_ARR_LEVEL_ROWPTR, BA_ARR_LEVEL_COLS,
@@ -32,7 +33,8 @@ class Options(ctypes.Structure):
                 ("recompute_jacobian", c_int), ("max_agg", c_int), ("pre_smooth", c_int),
                 ("post_smooth", c_int), ("lanczos_steps", c_int), ("coarse_max_nodes", c_int),
                 ("max_levels", c_int), ("cheb_lo", c_double), ("cheb_hi", c_double),
-                ("level0_operator", c_int), ("fused_vcycle", c_int), ("outer_product", c_int)]
+                ("level0_operator", c_int), ("fused_vcycle", c_int), ("outer_product", c_int),
+                ("stop_rule", c_int), ("tau", c_double)]
 
 
 class Info(ctypes.Structure):

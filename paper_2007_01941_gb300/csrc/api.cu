@@ -93,6 +93,8 @@ void ba_default_options(ba_options* o) {
   o->level0_operator = BA_OP_AUTO;
   o->fused_vcycle = 1;
   o->outer_product = BA_OUTER_PAIRED_FP32;
+  o->stop_rule = BA_STOP_RELRES;
+  o->tau = 0.1;
 }
 
 ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx, const int32_t* pt_idx,
@@ -123,6 +125,8 @@ ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx, co
                "bad level0_operator");
     BA_REQUIRE(o.outer_product == BA_OUTER_FP64 || o.outer_product == BA_OUTER_PAIRED_FP32, BA_ERR_INVALID_ARG,
                "bad outer_product");
+    BA_REQUIRE(o.stop_rule == BA_STOP_RELRES || (o.stop_rule == BA_STOP_NASH_SOFER && o.tau > 0.0),
+               BA_ERR_INVALID_ARG, "bad stop_rule / tau");
     int dev = 0;
     BA_CUDA(cudaGetDevice(&dev));
     BA_CUDA(cudaDeviceGetAttribute(&P->n_sm, cudaDevAttrMultiProcessorCount, dev));

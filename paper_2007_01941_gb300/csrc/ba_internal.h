@@ -72,6 +72,8 @@ enum Scalar : int {
   S_MODEL = 10,    // model reduction terms
   S_COST_NEW = 11,
   S_ITER = 12,     // PCG iterations done (graph path)
+  S_Q = 13,        // PCG quadratic model Q_i = 1/2 x^T S x - x^T b
+  S_DQ = 14,       // Q_i - Q_{i-1}
   S_LANCZOS = 16,  // 16 .. 31: alphas / betas of the Lanczos recurrences
   S_LANCZOS_END = 32,
 };

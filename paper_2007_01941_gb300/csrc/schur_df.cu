@@ -59,7 +59,23 @@ __device__ __forceinline__ F2 f2_shfl_xor(F2 v, int d) {
   return {__shfl_xor_sync(kFull, v.h, d), __shfl_xor_sync(kFull, v.l, d)};
 }
 
-__device__ __forceinline__ double f2_to_double(F2 v) { return (double)v.h + (double)v.l; }
+// exact float -> double by bit manipulation on the integer pipe (this GPU runs FP64
+// conversions on its narrow FP64 unit); zeros and subnormals map to signed zero,
+// infinities and NaNs keep their class
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned s = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;
+  const unsigned hi = e == 0u ? s : (s | (ed << 20) | (m >> 3));
+  const unsigned lo = e == 0u ? 0u : (m & 7u) << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// y += hi + lo as two FP64 atomic additions (the addition happens in the L2)
+__device__ __forceinline__ void f2_atomic_add(double* y, F2 v) {
+  atomicAdd(y, f2d_bits(v.h));
+  atomicAdd(y, f2d_bits(v.l));
+}
 
 __device__ __forceinline__ void load_record_pair(const float* __restrict__ hi, const float* __restrict__ lo,
                                                  F2 J[kRec]) {
@@ -191,7 +207,7 @@ k_schur_matvec_df(const float* __restrict__ Jh, const float* __restrict__ Jl, co
         if (run_head && lane < nobs) {
           double* yc = y + 9 * (size_t)cs;
 #pragma unroll
-          for (int k = 0; k < 9; ++k) atomicAdd(yc + k, f2_to_double(yv[k]));
+          for (int k = 0; k < 9; ++k) f2_atomic_add(yc + k, yv[k]);
         }
       } else {
         // one point with more than 32 observations: two passes over them
@@ -254,7 +270,7 @@ k_schur_matvec_df(const float* __restrict__ Jh, const float* __restrict__ Jl, co
             for (int k = 0; k < 9; ++k) {
               F2 v = f2_mul(J[k], w0);
               f2_fma(v, J[9 + k], w1);
-              atomicAdd(yc + k, f2_to_double(v));
+              f2_atomic_add(yc + k, v);
             }
           }
         }

@@ -370,7 +370,13 @@ k_pcg_update(size_t n, double* __restrict__ x, double* __restrict__ r, const dou
     }
     acc += ri * ri;
   }
-  if (!ok && blockIdx.x == 0 && threadIdx.x == 0) flags[F_BREAKDOWN] = 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!ok) flags[F_BREAKDOWN] = 1;
+    // quadratic model: Q_i - Q_{i-1} = -alpha (r.z) / 2
+    const double dq = ok ? -0.5 * alpha * scal[s_rz] : 0.0;
+    scal[S_DQ] = dq;
+    scal[S_Q] += dq;
+  }
   grid_sum_store<kVecBS>(acc, partial, counter, scal + S_RR);
 }
 
@@ -413,12 +419,19 @@ static void pcg_head(ba_problem* P, double* x) {
 
 // counts the iteration and sets the loop condition: continue while |r|^2 > rtol^2 |b|^2,
 // no breakdown and fewer than max_iters iterations
-__global__ void k_pcg_check(double* scal, const int* flags, int max_iters, double rtol2,
+__device__ __host__ inline bool pcg_converged(int rule, double it, double rr, double bb, double rtol2, double q,
+                                              double dq, double tau) {
+  if (rule == BA_STOP_NASH_SOFER) return q < 0.0 && it * dq / q <= tau;
+  return !(rr > rtol2 * bb);
+}
+
+__global__ void k_pcg_check(double* scal, const int* flags, int max_iters, double rtol2, int rule, double tau,
                             cudaGraphConditionalHandle h) {
   const double it = scal[S_ITER] + 1.0;
   scal[S_ITER] = it;
   const double rr = scal[S_RR], bb = scal[S_BB];
-  const bool stop = !(rr > rtol2 * bb) || flags[F_BREAKDOWN] != 0 || it >= (double)max_iters;
+  const bool stop = pcg_converged(rule, it, rr, bb, rtol2, scal[S_Q], scal[S_DQ], tau) ||
+                    flags[F_BREAKDOWN] != 0 || it >= (double)max_iters;
   cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
@@ -460,7 +473,8 @@ static void build_pcg_graph(ba_problem* P) {
     P->stream = P->cap_stream;
     BA_CUDA(cudaStreamBeginCaptureToGraph(P->cap_stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     pcg_head(P, x);
-    k_pcg_check<<<1, 1, 0, P->stream>>>(P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2, h);
+    k_pcg_check<<<1, 1, 0, P->stream>>>(P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2,
+                                         P->opt.stop_rule, P->opt.tau, h);
     launched(P);
     const long long head_kernels = P->launches - launches0;
     cudaStreamCaptureStatus status;
@@ -483,7 +497,8 @@ static void build_pcg_graph(ba_problem* P) {
     const long long body0 = P->launches;
     pcg_tail(P);
     pcg_head(P, x);
-    k_pcg_check<<<1, 1, 0, P->stream>>>(P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2, h);
+    k_pcg_check<<<1, 1, 0, P->stream>>>(P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2,
+                                         P->opt.stop_rule, P->opt.tau, h);
     launched(P);
     BA_CUDA(cudaStreamEndCapture(P->cap_stream, &body));
     BA_CUDA(cudaGraphInstantiate(&P->pcg_exec, g, 0));
@@ -538,26 +553,32 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
                                             split_target(P));  // p = z
   launched(P);
   const int rg = reduce_blocks(P, n);
+  const double rtol2 = P->opt.rtol * P->opt.rtol;
   double rel = 1.0;
   int it = 0;
+  bool done = false;
+  // S_ITER, S_Q, S_DQ start at 0
+  static_assert(S_Q == S_ITER + 1 && S_DQ == S_ITER + 2, "scalar slots");
+  BA_CUDA(cudaMemsetAsync(scal + S_ITER, 0, 3 * sizeof(double), P->stream));
   // graph-driven loop: no host round trip per iteration
   if (!P->ktime && P->graphs_ok) {
     if (P->pcg_graph_epoch != P->graph_epoch || !P->pcg_exec) build_pcg_graph(P);
     if (P->pcg_exec) {
       double* x = P->x.as<double>();
       BA_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, P->stream));
-      BA_CUDA(cudaMemsetAsync(scal + S_ITER, 0, sizeof(double), P->stream));
       BA_CUDA(cudaGraphLaunch(P->pcg_exec, P->stream));
       BA_CUDA(cudaMemcpyAsync(dc, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream));
-      fetch_scalars(P, S_RR, S_ITER - S_RR + 1);
+      fetch_scalars(P, S_RR, S_DQ - S_RR + 1);
       check_flags(P);
       it = (int)P->h_scal[S_ITER];
       P->launches += P->pcg_graph_head + (long long)std::max(it - 1, 0) * P->pcg_graph_body;
       rel = std::sqrt(P->h_scal[S_RR] / bb);
       BA_REQUIRE(std::isfinite(rel), BA_ERR_BREAKDOWN, "non-finite PCG residual");
+      done = pcg_converged(P->opt.stop_rule, (double)it, P->h_scal[S_RR], bb, rtol2, P->h_scal[S_Q],
+                           P->h_scal[S_DQ], P->opt.tau);
       P->pcg_iters = it;
       P->pcg_rel = rel;
-      if (rel > P->opt.rtol)
+      if (!done)
         throw Error(BA_ERR_NOT_CONVERGED, "PCG reached max_iters with relative residual " + std::to_string(rel));
       return;
     }
@@ -569,11 +590,13 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
                                                P->counter.as<unsigned>(), P->flags.as<int>());
     launched(P);
     ++it;
-    fetch_scalars(P, S_RR, 1);
+    fetch_scalars(P, S_RR, S_DQ - S_RR + 1);
     rel = std::sqrt(P->h_scal[S_RR] / bb);
     check_flags(P);
     BA_REQUIRE(std::isfinite(rel), BA_ERR_BREAKDOWN, "non-finite PCG residual");
-    if (rel <= P->opt.rtol) break;
+    done = pcg_converged(P->opt.stop_rule, (double)it, P->h_scal[S_RR], bb, rtol2, P->h_scal[S_Q],
+                         P->h_scal[S_DQ], P->opt.tau);
+    if (done) break;
     precond_apply(P, r, z);
     dot64(P, r, z, n, s_new);
     k_pcg_direction<<<g, 256, 0, P->stream>>>(n, p, z, scal, s_new, s_rz, P->Dc.as<double>(), q,
@@ -583,7 +606,7 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
   }
   P->pcg_iters = it;
   P->pcg_rel = rel;
-  if (rel > P->opt.rtol)
+  if (!done)
     throw Error(BA_ERR_NOT_CONVERGED, "PCG reached max_iters with relative residual " + std::to_string(rel));
 }
 

@@ -6,11 +6,13 @@
 // the level-0 operator is assembled.
 //
 // Each block-sparse product is fused into the kernel of the element-wise step that
-// consumes it, because the warp that owns a block row holds the whole row of the
-// product; one launch per phase:
+// consumes it: one CTA owns a block row, its threads split the row's blocks, and the
+// row of the product meets in shared memory next to the row's vector entries.  One
+// launch per phase:
 //   pre-smoothing  step 0:   r = b, d = D^-1 r / theta, x = d
 //                  step k:   q = A d; r' = r - q; d' = rho_k rho_{k-1} d + 2 rho_k / delta D^-1 r'; x += d'
-//   restriction:             b_c[a] = sum_{i in a} Q_i^T (r_i - (A d)_i)     (one warp per aggregate)
+//   residual:                s = r - A d
+//   restriction:             b_c[a] = sum_{i in a} Q_i^T s_i     (one warp per aggregate)
 //   coarsest:                x_c = A_c^-1 b_c
 //   prolongation:            x_i += Q_i x_c[agg(i)]
 //   post-smoothing step 0:   q = A x; r = b - q; d = D^-1 r / theta; x' = x + d
@@ -44,48 +46,8 @@ struct VLevel {
   T* d[2];
 };
 
-__device__ __forceinline__ double vc_rho(const double* cheb, int k) {
-  double rho = 1.0 / cheb[2];
-  for (int j = 1; j <= k; ++j) rho = 1.0 / (2.0 * cheb[2] - rho);
-  return rho;
-}
-
-// (A v)_i for block row i, computed by one warp: lane u < BS returns component u.
-// The row's block columns are read once, coalesced, and handed out by shuffles, so the
-// loads of the blocks and of v are independent of each other and can all be in flight.
-template <typename T, int BS>
-__device__ __forceinline__ T row_product(const VLevel<T>& L, int i, const T* __restrict__ v, int lane) {
-  const int e0 = L.row_ptr[i], e1 = L.row_ptr[i + 1];
-  const int nb = e1 - e0;
-  T acc = T(0);
-  // BS = 9: lane = r + 9k (k < 3) takes row r of blocks k, k+3, ...; BS = 16: lane =
-  // u + 16h takes row u of blocks h, h+2, ...
-  constexpr int kGroups = BS == 9 ? 3 : 2;
-  const int r = BS == 9 ? lane % 9 : (lane & 15);
-  const int k = BS == 9 ? lane / 9 : (lane >> 4);
-  for (int base = 0; base < nb; base += 32) {
-    const int cl = base + lane < nb ? L.cols[e0 + base + lane] : 0;
-    const int lim = min(32, nb - base);
-    const int steps = (lim + kGroups - 1) / kGroups;   // the same in every lane
-#pragma unroll 2
-    for (int m = 0; m < steps; ++m) {
-      const int j = k + m * kGroups;
-      const int col = __shfl_sync(kFull, cl, j & 31);
-      if (k < kGroups && j < lim) {
-        const T* a = L.vals + (size_t)(e0 + base + j) * (BS * BS) + r * BS;
-        const T* xv = v + (size_t)col * BS;
-#pragma unroll
-        for (int c = 0; c < BS; ++c) acc += a[c] * xv[c];
-      }
-    }
-  }
-  if (BS == 9) {
-    const T a1 = __shfl_sync(kFull, acc, min(lane + 9, 31));
-    const T a2 = __shfl_sync(kFull, acc, min(lane + 18, 31));
-    return acc + a1 + a2;
-  }
-  return acc + __shfl_xor_sync(kFull, acc, 16);
-}
+constexpr int kPhaseBS = 256;
+constexpr int kPhaseWarps = kPhaseBS / 32;
 
 // (D_i^-1 w)_u where lane v < BS holds w_v
 template <typename T, int BS>
@@ -100,11 +62,57 @@ __device__ __forceinline__ T block_apply(const T* __restrict__ Dinv_i, T w, int 
   return lane < BS ? acc : T(0);
 }
 
+// CTA shape of the row phases: G groups of BS threads split a block row's blocks
+template <int BS>
+struct RowCta {
+  static constexpr int G = BS == 16 ? 8 : 10;
+  static constexpr int kThreads = BS == 16 ? 128 : 96;
+};
+
+// q = (A v)_i by the whole CTA; on return q[u], u < BS, in shared memory (all threads)
+template <typename T, int BS>
+__device__ __forceinline__ void cta_row_product(const VLevel<T>& L, int i, const T* __restrict__ v, T* part,
+                                                T* q) {
+  constexpr int G = RowCta<BS>::G;
+  const int t = threadIdx.x;
+  const int u = t % BS, h = t / BS;
+  if (h < G) {
+    const int e1 = L.row_ptr[i + 1];
+    T acc = T(0);
+#pragma unroll 2
+    for (int e = L.row_ptr[i] + h; e < e1; e += G) {
+      const T* a = L.vals + (size_t)e * (BS * BS) + u * BS;
+      const T* xv = v + (size_t)L.cols[e] * BS;
+#pragma unroll
+      for (int c = 0; c < BS; ++c) acc += a[c] * xv[c];
+    }
+    part[h * BS + u] = acc;
+  }
+  __syncthreads();
+  if (t < BS) {
+    T s = T(0);
+#pragma unroll
+    for (int g = 0; g < G; ++g) s += part[g * BS + t];
+    q[t] = s;
+  }
+  __syncthreads();
+}
+
+// Dinv_i row u times the vector w held in shared memory
+template <typename T, int BS>
+__device__ __forceinline__ T row_dinv(const T* __restrict__ Dinv_i, const T* w, int u) {
+  T acc = T(0);
+#pragma unroll
+  for (int v = 0; v < BS; ++v) acc += Dinv_i[u * BS + v] * w[v];
+  return acc;
+}
+
 // pre-smoothing step 0 with x = 0: r = b, d = D^-1 b / theta, x = d (one warp per row);
 // on level 0 b comes in as the FP64 right-hand side
 template <typename T, int BS>
-__device__ __forceinline__ void phase_first(const VLevel<T>& L, const double* __restrict__ in, int gw, int nw,
-                                            int lane) {
+__global__ void __launch_bounds__(256) k_ph_first(VLevel<T> L, const double* __restrict__ in) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const T inv_theta = (T)(1.0 / L.cheb[0]);
   for (int i = gw; i < L.n; i += nw) {
     const size_t idx = (size_t)i * BS + lane;
@@ -122,96 +130,65 @@ __device__ __forceinline__ void phase_first(const VLevel<T>& L, const double* __
   }
 }
 
-// Chebyshev step k >= 1: q = A din; rout = rin - q; dout = c1 din + c2 D^-1 rout; x += dout
+// Chebyshev step k >= 1 on row blockIdx.x: q = A din; rout = rin - q;
+// dout = c1 din + c2 D^-1 rout; x += dout (out: FP64 copy of the new x, level 0's last step)
 template <typename T, int BS>
-__device__ __forceinline__ void phase_step(const VLevel<T>& L, const T* __restrict__ din, T* __restrict__ dout,
-                                           const T* __restrict__ rin, T* __restrict__ rout, T* __restrict__ x,
-                                           T c1, T c2, double* __restrict__ out, int gw, int nw, int lane) {
-  for (int i = gw; i < L.n; i += nw) {
-    const T q = row_product<T, BS>(L, i, din, lane);
-    const size_t idx = (size_t)i * BS + lane;
-    const T rv = lane < BS ? rin[idx] - q : T(0);
-    const T acc = block_apply<T, BS>(L.Dinv + (size_t)i * BS * BS, rv, lane);
-    if (lane < BS) {
-      const T dn = c1 * din[idx] + c2 * acc;
-      const T xn = x[idx] + dn;
-      rout[idx] = rv;
-      dout[idx] = dn;
-      x[idx] = xn;
-      if (out) out[idx] = (double)xn;
-    }
+__global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_step(VLevel<T> L, int dc, int rc, int xc, T c1, T c2,
+                                                                 double* __restrict__ out) {
+  __shared__ T part[RowCta<BS>::G * BS];
+  __shared__ T q[BS], w[BS];
+  const int i = blockIdx.x, t = threadIdx.x;
+  const T* din = L.d[dc];
+  cta_row_product<T, BS>(L, i, din, part, q);
+  const size_t idx = (size_t)i * BS + t;
+  if (t < BS) w[t] = L.r[rc][idx] - q[t];
+  __syncthreads();
+  if (t < BS) {
+    const T acc = row_dinv<T, BS>(L.Dinv + (size_t)i * BS * BS, w, t);
+    const T dn = c1 * din[idx] + c2 * acc;
+    const T xn = L.x[xc][idx] + dn;
+    L.r[1 - rc][idx] = w[t];
+    L.d[1 - dc][idx] = dn;
+    L.x[xc][idx] = xn;
+    if (out) out[idx] = (double)xn;
   }
 }
 
-// restriction b_c[a] = sum_{i in a} Q_i^T (r_i - (A d)_i), one warp per aggregate
+// residual of the pre-smoothed iterate on row blockIdx.x: s = r - A d, into the free r buffer
 template <typename T, int BS>
-__device__ __forceinline__ void phase_restrict(const VLevel<T>& L, const VLevel<T>& C, const T* __restrict__ dv,
-                                               const T* __restrict__ rv, int gw, int nw, int lane) {
-  for (int a = gw; a < C.n; a += nw) {
-    T acc = T(0);
-    for (int m = L.agg_ptr[a]; m < L.agg_ptr[a + 1]; ++m) {
-      const int i = L.agg_mem[m];
-      const T q = row_product<T, BS>(L, i, dv, lane);
-      const T res = lane < BS ? rv[(size_t)i * BS + lane] - q : T(0);
-      const T* Qi = L.Q + (size_t)i * BS * 16 + (lane & 15);
-      T qv[BS];
+__global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_residual(VLevel<T> L, int dc, int rc) {
+  __shared__ T part[RowCta<BS>::G * BS];
+  __shared__ T q[BS];
+  const int i = blockIdx.x, t = threadIdx.x;
+  cta_row_product<T, BS>(L, i, L.d[dc], part, q);
+  if (t < BS) {
+    const size_t idx = (size_t)i * BS + t;
+    L.r[1 - rc][idx] = L.r[rc][idx] - q[t];
+  }
+}
+
+// restriction b_c[a] = sum_{i in a} Q_i^T s_i (one warp per aggregate, lane s < 16)
+template <typename T, int BS>
+__global__ void __launch_bounds__(256) k_ph_restrict(VLevel<T> L, VLevel<T> C, const T* __restrict__ res) {
+  const int lane = threadIdx.x & 31;
+  const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (a >= C.n || lane >= 16) return;
+  T acc = T(0);
+  for (int m = L.agg_ptr[a]; m < L.agg_ptr[a + 1]; ++m) {
+    const int i = L.agg_mem[m];
+    const T* Qi = L.Q + (size_t)i * BS * 16 + lane;
+    const T* ri = res + (size_t)i * BS;
 #pragma unroll
-      for (int u = 0; u < BS; ++u) qv[u] = Qi[u * 16];
-#pragma unroll
-      for (int u = 0; u < BS; ++u) acc += qv[u] * __shfl_sync(kFull, res, u);
-    }
-    if (lane < 16) C.b[(size_t)a * 16 + lane] = acc;
+    for (int u = 0; u < BS; ++u) acc += Qi[u * 16] * ri[u];
   }
-}
-
-// post-smoothing step 0: q = A xin; r = b - q; d = D^-1 r / theta; xout = xin + d
-template <typename T, int BS>
-__device__ __forceinline__ void phase_post_first(const VLevel<T>& L, const T* __restrict__ xin, T* __restrict__ xout,
-                                                 T* __restrict__ r, T* __restrict__ d, double* __restrict__ out,
-                                                 int gw, int nw, int lane) {
-  const T inv_theta = (T)(1.0 / L.cheb[0]);
-  for (int i = gw; i < L.n; i += nw) {
-    const T q = row_product<T, BS>(L, i, xin, lane);
-    const size_t idx = (size_t)i * BS + lane;
-    const T rv = lane < BS ? L.b[idx] - q : T(0);
-    const T dv = block_apply<T, BS>(L.Dinv + (size_t)i * BS * BS, rv, lane) * inv_theta;
-    if (lane < BS) {
-      const T xn = xin[idx] + dv;
-      r[idx] = rv;
-      d[idx] = dv;
-      xout[idx] = xn;
-      if (out) out[idx] = (double)xn;
-    }
-  }
-}
-
-constexpr int kPhaseBS = 256;
-constexpr int kPhaseWarps = kPhaseBS / 32;
-
-__device__ __forceinline__ int warp_id() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
-__device__ __forceinline__ int warp_count() { return (gridDim.x * blockDim.x) >> 5; }
-
-template <typename T, int BS>
-__global__ void __launch_bounds__(kPhaseBS) k_ph_first(VLevel<T> L, const double* __restrict__ in) {
-  phase_first<T, BS>(L, in, warp_id(), warp_count(), threadIdx.x & 31);
-}
-
-template <typename T, int BS>
-__global__ void __launch_bounds__(kPhaseBS) k_ph_step(VLevel<T> L, int dc, int rc, int xc, T c1, T c2,
-                                                     double* __restrict__ out) {
-  phase_step<T, BS>(L, L.d[dc], L.d[1 - dc], L.r[rc], L.r[1 - rc], L.x[xc], c1, c2, out, warp_id(), warp_count(),
-                    threadIdx.x & 31);
-}
-
-template <typename T, int BS>
-__global__ void __launch_bounds__(kPhaseBS) k_ph_restrict(VLevel<T> L, VLevel<T> C, int dc, int rc) {
-  phase_restrict<T, BS>(L, C, L.d[dc], L.r[rc], warp_id(), warp_count(), threadIdx.x & 31);
+  C.b[(size_t)a * 16 + lane] = acc;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kPhaseBS) k_ph_coarsest(VLevel<T> C) {
+__global__ void __launch_bounds__(256) k_ph_coarsest(VLevel<T> C) {
   const int lane = threadIdx.x & 31;
-  for (int row = warp_id(); row < C.N; row += warp_count()) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int row = gw; row < C.N; row += nw) {
     const double* a = C.Ainv + (size_t)row * C.Np;
     double acc = 0.0;
     for (int j = lane; j < C.N; j += 32) acc += a[j] * (double)C.b[j];
@@ -220,8 +197,9 @@ __global__ void __launch_bounds__(kPhaseBS) k_ph_coarsest(VLevel<T> C) {
   }
 }
 
+// x_i += Q_i x_c[agg(i)]
 template <typename T>
-__global__ void __launch_bounds__(kPhaseBS) k_ph_prolong(VLevel<T> L, VLevel<T> C, int xl, int xcl) {
+__global__ void __launch_bounds__(256) k_ph_prolong(VLevel<T> L, VLevel<T> C, int xl, int xcl) {
   const int bs = L.bs;
   T* x = L.x[xl];
   const T* xc = C.x[xcl];
@@ -236,11 +214,26 @@ __global__ void __launch_bounds__(kPhaseBS) k_ph_prolong(VLevel<T> L, VLevel<T> 
   }
 }
 
+// post-smoothing step 0 on row blockIdx.x: q = A x; r = b - q; d = D^-1 r / theta; x' = x + d
 template <typename T, int BS>
-__global__ void __launch_bounds__(kPhaseBS) k_ph_post_first(VLevel<T> L, int xc, int rc, int dc,
-                                                           double* __restrict__ out) {
-  phase_post_first<T, BS>(L, L.x[xc], L.x[1 - xc], L.r[rc], L.d[dc], out, warp_id(), warp_count(),
-                          threadIdx.x & 31);
+__global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first(VLevel<T> L, int xc, int rc, int dc,
+                                                                       double* __restrict__ out) {
+  __shared__ T part[RowCta<BS>::G * BS];
+  __shared__ T q[BS], w[BS];
+  const int i = blockIdx.x, t = threadIdx.x;
+  const T* xin = L.x[xc];
+  cta_row_product<T, BS>(L, i, xin, part, q);
+  const size_t idx = (size_t)i * BS + t;
+  if (t < BS) w[t] = L.b[idx] - q[t];
+  __syncthreads();
+  if (t < BS) {
+    const T dv = row_dinv<T, BS>(L.Dinv + (size_t)i * BS * BS, w, t) * (T)(1.0 / L.cheb[0]);
+    const T xn = xin[idx] + dv;
+    L.r[rc][idx] = w[t];
+    L.d[dc][idx] = dv;
+    L.x[1 - xc][idx] = xn;
+    if (out) out[idx] = (double)xn;
+  }
 }
 
 template <typename T>
@@ -305,16 +298,22 @@ static void run(ba_problem* P, const double* r, double* z) {
       double c1, c2;
       cheb_coeffs(P->levels[l], k, c1, c2);
       if (L.bs == 9)
-        k_ph_step<T, 9><<<g, kPhaseBS, 0, st>>>(L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2, nullptr);
+        k_ph_step<T, 9><<<L.n, RowCta<9>::kThreads, 0, st>>>(L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2,
+                                                             nullptr);
       else
-        k_ph_step<T, 16><<<g, kPhaseBS, 0, st>>>(L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2, nullptr);
+        k_ph_step<T, 16><<<L.n, RowCta<16>::kThreads, 0, st>>>(L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1,
+                                                               (T)c2, nullptr);
       launched(P);
       rm ^= 1u << l;
       dm ^= 1u << l;
     }
+    if (L.bs == 9) k_ph_residual<T, 9><<<L.n, RowCta<9>::kThreads, 0, st>>>(L, bit(dm, l), bit(rm, l));
+    else k_ph_residual<T, 16><<<L.n, RowCta<16>::kThreads, 0, st>>>(L, bit(dm, l), bit(rm, l));
+    launched(P);
+    const T* res = L.r[1 - bit(rm, l)];
     const int gc = warps_grid(V[l + 1].n);
-    if (L.bs == 9) k_ph_restrict<T, 9><<<gc, kPhaseBS, 0, st>>>(L, V[l + 1], bit(dm, l), bit(rm, l));
-    else k_ph_restrict<T, 16><<<gc, kPhaseBS, 0, st>>>(L, V[l + 1], bit(dm, l), bit(rm, l));
+    if (L.bs == 9) k_ph_restrict<T, 9><<<gc, kPhaseBS, 0, st>>>(L, V[l + 1], res);
+    else k_ph_restrict<T, 16><<<gc, kPhaseBS, 0, st>>>(L, V[l + 1], res);
     launched(P);
   }
   k_ph_coarsest<T><<<warps_grid(V[nl - 1].N), kPhaseBS, 0, st>>>(V[nl - 1]);
@@ -326,8 +325,10 @@ static void run(ba_problem* P, const double* r, double* z) {
                                                                                bit(xm, l + 1));
     launched(P);
     double* o = (l == 0 && post == 1) ? z : nullptr;
-    if (L.bs == 9) k_ph_post_first<T, 9><<<g, kPhaseBS, 0, st>>>(L, bit(xm, l), bit(rm, l), bit(dm, l), o);
-    else k_ph_post_first<T, 16><<<g, kPhaseBS, 0, st>>>(L, bit(xm, l), bit(rm, l), bit(dm, l), o);
+    if (L.bs == 9)
+      k_ph_post_first<T, 9><<<L.n, RowCta<9>::kThreads, 0, st>>>(L, bit(xm, l), bit(rm, l), bit(dm, l), o);
+    else
+      k_ph_post_first<T, 16><<<L.n, RowCta<16>::kThreads, 0, st>>>(L, bit(xm, l), bit(rm, l), bit(dm, l), o);
     launched(P);
     xm ^= 1u << l;
     for (int k = 1; k < post; ++k) {
@@ -335,9 +336,11 @@ static void run(ba_problem* P, const double* r, double* z) {
       cheb_coeffs(P->levels[l], k, c1, c2);
       double* ok = (l == 0 && k == post - 1) ? z : nullptr;
       if (L.bs == 9)
-        k_ph_step<T, 9><<<g, kPhaseBS, 0, st>>>(L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2, ok);
+        k_ph_step<T, 9><<<L.n, RowCta<9>::kThreads, 0, st>>>(L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2,
+                                                             ok);
       else
-        k_ph_step<T, 16><<<g, kPhaseBS, 0, st>>>(L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2, ok);
+        k_ph_step<T, 16><<<L.n, RowCta<16>::kThreads, 0, st>>>(L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1,
+                                                               (T)c2, ok);
       launched(P);
       rm ^= 1u << l;
       dm ^= 1u << l;

@@ -190,6 +190,29 @@ def test_pcg_matches_oracle(gpu, pc):
             assert np.linalg.norm(_np(dp).ravel() - dp_ref) <= 1e-8 * np.linalg.norm(dp_ref)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pcg_nash_sofer_matches_oracle(gpu, precision):
+    """Section 2.1's forcing rule: same stopping iteration as the oracle, same iterate,
+    and (the paper's remark) a tighter solve with multigrid than with block Jacobi."""
+    api, F_ = _api()
+    s = scene("street_chain", **CHAIN)
+    prec = {"fp64": F_.BA_FP64, "mixed": F_.BA_MIXED}[precision]
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+    true_rel = {}
+    for pc, code in (("mg", F_.BA_PRECOND_MG), ("jacobi", F_.BA_PRECOND_JACOBI)):
+        prob, cams, pts, obs = _prob(s, gpu, precision=prec, preconditioner=code, coarse_max_nodes=16,
+                                     stop_rule=F_.BA_STOP_NASH_SOFER, tau=0.1, max_iters=3000)
+        dc, dp, it, relres = prob.solve(cams, pts, obs, s.lam)
+        ref, _, it_ref, _ = lm.solve_step(sch, s.cams, pc, rtol=0.0, max_iters=3000, stop="nash_sofer", tau=0.1,
+                                          coarse_max_nodes=16)
+        d = _np(dc).ravel()
+        assert abs(it - it_ref) <= 1, (pc, it, it_ref)
+        if it == it_ref and precision == "fp64":
+            assert np.linalg.norm(d - ref) <= 1e-6 * np.linalg.norm(ref)
+        true_rel[pc] = np.linalg.norm(sch.b - sch.S @ d) / np.linalg.norm(sch.b)
+    assert true_rel["mg"] < true_rel["jacobi"]
+
+
 def test_mixed_precision_solution_matches_oracle(gpu):
     api, F_ = _api()
     s = scene("street_chain", **CHAIN)
