@@ -612,374 +612,109 @@ void matvec32_accumulate(ba_problem* P, const float* x, float* y) {
 }
 
 // ---------------------------------------------------------------------------
-// explicit level-0 operator blocks S_cc' (for the Galerkin product), one CTA per
-// camera row c.  Warp w takes the observations o = (c, p) of the row in turn; lane j
-// takes the j-th observation o' = (c', p) of the same point and adds
-//   -F_o^T (E_o C_p^-1 E_o'^T - [o' == o] I) F_o'
-// to block (c, c').  The o' of one point belong to distinct cameras, so within a
-// warp every lane updates a different block: each warp accumulates into its own
-// copy of the row in shared memory with plain read-modify-writes, and the copies
-// are summed in warp order at the end (deterministic, no atomics).  A row with more
-// blocks than fit is processed in several passes over block ranges.
+// explicit level-0 operator S (for the Galerkin product and, when chosen, the V-cycle's
+// finest level).  With C_p^-1 = L_p L_p^T (Cholesky) and W_o = L_p^T E_o^T F_o (3 x 9)
+// per observation o = (c, p), an off-diagonal block is
+//   S_cc' = - sum_{p seen by c and c'} W_(c,p)^T W_(c',p),
+// and the diagonal block S_cc is the one the Schur setup already formed.
+// k_schur_w writes W (one thread per observation); k_explicit_w takes one CTA per
+// camera row c: warp w walks the row's observations o in turn and, for every other
+// observation o' of the same point, lane (a, g) (27 lanes) adds entries (a, 3g..3g+2)
+// of -W_o^T W_o' to the block (c, cam(o')) in a shared-memory copy of the row.  A row
+// with more blocks than fit is done in several passes over block ranges.
 // ---------------------------------------------------------------------------
-constexpr int kExWarps = 4;
+template <typename T>
+__global__ void k_schur_w(const T* __restrict__ J, const T* __restrict__ Cinv, int ldp,
+                          const int* __restrict__ obs_pt, int n_o, T* __restrict__ W) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_o) return;
+  const int ip = obs_pt[o];
+  T f[18], e[6];
+  load_record(J + (size_t)o * kRec, f, e);
+  // H = E^T F (3 x 9): H[t][b] = E[0][t] F[0][b] + E[1][t] F[1][b]
+  T h[27];
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
+#pragma unroll
+    for (int b = 0; b < 9; ++b) h[9 * t + b] = e[t] * f[b] + e[3 + t] * f[9 + b];
+  const T c00 = Cinv[ip], c01 = Cinv[ldp + ip], c02 = Cinv[2 * ldp + ip];
+  const T c11 = Cinv[3 * ldp + ip], c12 = Cinv[4 * ldp + ip], c22 = Cinv[5 * ldp + ip];
+  // lower Cholesky factor of C_p^-1 (clamped at zero if rounding makes a pivot negative)
+  const T l00 = sqrt(c00 > T(0) ? c00 : T(0));
+  const T i00 = l00 > T(0) ? T(1) / l00 : T(0);
+  const T l10 = c01 * i00, l20 = c02 * i00;
+  const T p11 = c11 - l10 * l10;
+  const T l11 = sqrt(p11 > T(0) ? p11 : T(0));
+  const T i11 = l11 > T(0) ? T(1) / l11 : T(0);
+  const T l21 = (c12 - l20 * l10) * i11;
+  const T p22 = c22 - l20 * l20 - l21 * l21;
+  const T l22 = sqrt(p22 > T(0) ? p22 : T(0));
+  // W = L^T H
+  T* w = W + (size_t)o * 27;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    w[b] = l00 * h[b] + l10 * h[9 + b] + l20 * h[18 + b];
+    w[9 + b] = l11 * h[9 + b] + l21 * h[18 + b];
+    w[18 + b] = l22 * h[18 + b];
+  }
+}
+
+constexpr int kExBS = 256;
 
 template <typename T>
-__global__ void __launch_bounds__(kExWarps * 32)
-k_explicit_schur(const T* __restrict__ F, const T* __restrict__ E, int ld,
-                 const T* __restrict__ Cinv, int ldp, const int* __restrict__ cam_ptr,
-                 const int* __restrict__ cam_obs, const int* __restrict__ obs_pt,
-                 const int* __restrict__ obs_cam, const int* __restrict__ pt_ptr,
-                 const int* __restrict__ row_ptr, const int* __restrict__ cols,
-                 const double* __restrict__ Dc, int cap, T* __restrict__ vals) {
-  extern __shared__ __align__(16) unsigned char ex_smem[];
+__global__ void __launch_bounds__(kExBS)
+k_explicit_w(const T* __restrict__ W, const int* __restrict__ cam_ptr, const int* __restrict__ cam_obs,
+             const int* __restrict__ obs_pt, const int* __restrict__ obs_cam, const int* __restrict__ pt_ptr,
+             const int* __restrict__ row_ptr, const int* __restrict__ cols, const double* __restrict__ Scc,
+             int cap, T* __restrict__ vals) {
+  extern __shared__ __align__(16) unsigned char ew_smem[];
+  T* acc = reinterpret_cast<T*>(ew_smem);                       // [cap][81]
+  int* scol = reinterpret_cast<int*>(acc + (size_t)cap * 81);   // [cap]
   const int c = blockIdx.x;
-  const int rb = row_ptr[c], re = row_ptr[c + 1];
-  const int nslots = re - rb;
-  T* acc = reinterpret_cast<T*>(ex_smem);                         // [kExWarps][cap][81]
-  int* scol = reinterpret_cast<int*>(acc + (size_t)kExWarps * cap * 81);  // [cap]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* my = acc + (size_t)warp * cap * 81;
+  const int rb = row_ptr[c], nslots = row_ptr[c + 1] - rb;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int la = lane / 3, lg = lane - 3 * la;   // lane -> (row a, column group g)
+  const int ob0 = cam_ptr[c], nrow = cam_ptr[c + 1] - ob0;
   for (int pass_base = 0; pass_base < nslots; pass_base += cap) {
     const int pass_n = min(cap, nslots - pass_base);
-    for (int i = threadIdx.x; i < kExWarps * cap * 81; i += blockDim.x) acc[i] = T(0);
-    for (int i = threadIdx.x; i < pass_n; i += blockDim.x) scol[i] = cols[rb + pass_base + i];
+    for (int i = t; i < pass_n * 81; i += kExBS) acc[i] = T(0);
+    for (int i = t; i < pass_n; i += kExBS) scol[i] = cols[rb + pass_base + i];
     __syncthreads();
-    for (int k = cam_ptr[c] + warp; k < cam_ptr[c + 1]; k += kExWarps) {
-      const int o = cam_obs[k];
+    for (int k = warp; k < nrow; k += kExBS / 32) {
+      const int o = cam_obs[ob0 + k];
       const int ip = obs_pt[o];
-      const int ob = pt_ptr[ip], np = pt_ptr[ip + 1] - ob;
-      T fo[18];
-#pragma unroll
-      for (int q = 0; q < 18; ++q) fo[q] = JF(F, o, q);
-      const T ci0 = Cinv[ip], ci1 = Cinv[ldp + ip], ci2 = Cinv[2 * ldp + ip];
-      const T ci3 = Cinv[3 * ldp + ip], ci4 = Cinv[4 * ldp + ip], ci5 = Cinv[5 * ldp + ip];
-      const T e0 = JE(E, o, 0), e1 = JE(E, o, 1), e2 = JE(E, o, 2);
-      const T e3 = JE(E, o, 3), e4 = JE(E, o, 4), e5 = JE(E, o, 5);
-      // Y = E_o C_p^-1 (2 x 3)
-      const T y00 = e0 * ci0 + e1 * ci1 + e2 * ci2, y01 = e0 * ci1 + e1 * ci3 + e2 * ci4,
-              y02 = e0 * ci2 + e1 * ci4 + e2 * ci5;
-      const T y10 = e3 * ci0 + e4 * ci1 + e5 * ci2, y11 = e3 * ci1 + e4 * ci3 + e5 * ci4,
-              y12 = e3 * ci2 + e4 * ci4 + e5 * ci5;
-      for (int jb = 0; jb < np; jb += 32) {
-        const int j = jb + lane;
-        if (j >= np) continue;
-        const int o2 = ob + j;
-        const int c2 = obs_cam[o2];
+      T wi0 = T(0), wi1 = T(0), wi2 = T(0);
+      if (lane < 27) {
+        const T* wo = W + (size_t)o * 27 + la;
+        wi0 = wo[0];
+        wi1 = wo[9];
+        wi2 = wo[18];
+      }
+      for (int q = pt_ptr[ip]; q < pt_ptr[ip + 1]; ++q) {
+        if (q == o) continue;
+        const int c2 = obs_cam[q];
         int lo = 0, hi = pass_n - 1, s = -1;
         while (lo <= hi) {
           const int mid = (lo + hi) >> 1;
           const int v = scol[mid];
-          if (v == c2) { s = mid; break; }
-          if (v < c2) lo = mid + 1; else hi = mid - 1;
-        }
-        if (s < 0) continue;
-        const T a0 = JE(E, o2, 0), a1 = JE(E, o2, 1), a2 = JE(E, o2, 2);
-        const T b0 = JE(E, o2, 3), b1 = JE(E, o2, 4), b2 = JE(E, o2, 5);
-        T m00 = y00 * a0 + y01 * a1 + y02 * a2;
-        T m01 = y00 * b0 + y01 * b1 + y02 * b2;
-        T m10 = y10 * a0 + y11 * a1 + y12 * a2;
-        T m11 = y10 * b0 + y11 * b1 + y12 * b2;
-        if (o2 == o) {
-          m00 -= T(1);
-          m11 -= T(1);
-        }
-        T f2[18];
-#pragma unroll
-        for (int q = 0; q < 18; ++q) f2[q] = JF(F, o2, q);
-        T* blk = my + (size_t)s * 81;
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-          const T g0 = fo[a] * m00 + fo[9 + a] * m10;
-          const T g1 = fo[a] * m01 + fo[9 + a] * m11;
-#pragma unroll
-          for (int b = 0; b < 9; ++b) blk[9 * a + b] -= g0 * f2[b] + g1 * f2[9 + b];
-        }
-      }
-    }
-    __syncthreads();
-    // sum the warps' copies, add D_c on the diagonal block, write out
-    for (int i = threadIdx.x; i < pass_n * 81; i += blockDim.x) {
-      T v = T(0);
-#pragma unroll
-      for (int w = 0; w < kExWarps; ++w) v += acc[(size_t)w * cap * 81 + i];
-      const int s = i / 81, e = i - 81 * s;
-      const int a = e / 9, b = e - 9 * a;
-      if (scol[s] == c && a == b) v += (T)Dc[9 * c + a];
-      vals[(size_t)(rb + pass_base + s) * 81 + e] = v;
-    }
-    __syncthreads();
-  }
-}
-
-// FP32 variant with every thread of the CTA on its own (o, o') pair of the row: the
-// row's observations are taken in batches of kPairBatch; a block-wide prefix of the
-// batch's point sizes maps a thread's pair index to (o, j); contributions go to the
-// single shared copy of the row with FP32 shared atomics (native on this GPU).
-constexpr int kPairBS = 256;
-constexpr int kPairBatch = 256;
-
-__global__ void __launch_bounds__(kPairBS)
-k_explicit_schur_pairs(const float* __restrict__ F, const float* __restrict__ E, int ld,
-                       const float* __restrict__ Cinv, int ldp, const int* __restrict__ cam_ptr,
-                       const int* __restrict__ cam_obs, const int* __restrict__ obs_pt,
-                       const int* __restrict__ obs_cam, const int* __restrict__ pt_ptr,
-                       const int* __restrict__ row_ptr, const int* __restrict__ cols,
-                       const double* __restrict__ Dc, int cap, float* __restrict__ vals) {
-  extern __shared__ __align__(16) unsigned char px_smem[];
-  __shared__ int bo[kPairBatch], bip[kPairBatch], bob[kPairBatch], bpre[kPairBatch + 1];
-  const int c = blockIdx.x;
-  const int rb = row_ptr[c], re = row_ptr[c + 1];
-  const int nslots = re - rb;
-  float* acc = reinterpret_cast<float*>(px_smem);                          // [cap][81]
-  int* scol = reinterpret_cast<int*>(acc + (size_t)cap * 81);              // [cap]
-  const int t = threadIdx.x;
-  const int ob0 = cam_ptr[c], nrow = cam_ptr[c + 1] - ob0;
-  for (int pass_base = 0; pass_base < nslots; pass_base += cap) {
-    const int pass_n = min(cap, nslots - pass_base);
-    for (int i = t; i < cap * 81; i += kPairBS) acc[i] = 0.0f;
-    for (int i = t; i < pass_n; i += kPairBS) scol[i] = cols[rb + pass_base + i];
-    __syncthreads();  // a row without observations goes straight to the write-out
-    for (int b0 = 0; b0 < nrow; b0 += kPairBatch) {
-      const int nb = min(kPairBatch, nrow - b0);
-      int cnt = 0;
-      if (t < nb) {
-        const int o = cam_obs[ob0 + b0 + t];
-        const int ip = obs_pt[o];
-        const int s = pt_ptr[ip];
-        bo[t] = o;
-        bip[t] = ip;
-        bob[t] = s;
-        cnt = pt_ptr[ip + 1] - s;
-      }
-      // exclusive prefix of the pair counts (Hillis-Steele in shared memory)
-      bpre[t + 1] = cnt;
-      if (t == 0) bpre[0] = 0;
-      __syncthreads();
-      for (int d = 1; d < kPairBatch; d <<= 1) {
-        const int v = (t + 1 - d >= 1) ? bpre[t + 1 - d] : 0;
-        __syncthreads();
-        bpre[t + 1] += v;
-        __syncthreads();
-      }
-      const int total = bpre[nb];
-      for (int pi = t; pi < total; pi += kPairBS) {
-        int lo = 0, hi = nb - 1;
-        while (lo < hi) {  // last i with bpre[i] <= pi
-          const int mid = (lo + hi + 1) >> 1;
-          if (bpre[mid] <= pi) lo = mid; else hi = mid - 1;
-        }
-        const int i = lo;
-        const int o = bo[i], ip = bip[i];
-        const int o2 = bob[i] + (pi - bpre[i]);
-        const int c2 = obs_cam[o2];
-        int a = 0, z = pass_n - 1, s = -1;
-        while (a <= z) {
-          const int mid = (a + z) >> 1;
-          const int v = scol[mid];
-          if (v == c2) { s = mid; break; }
-          if (v < c2) a = mid + 1; else z = mid - 1;
-        }
-        if (s < 0) continue;
-        const float ci0 = Cinv[ip], ci1 = Cinv[ldp + ip], ci2 = Cinv[2 * ldp + ip];
-        const float ci3 = Cinv[3 * ldp + ip], ci4 = Cinv[4 * ldp + ip], ci5 = Cinv[5 * ldp + ip];
-        const float e0 = JE(E, o, 0), e1 = JE(E, o, 1), e2 = JE(E, o, 2);
-        const float e3 = JE(E, o, 3), e4 = JE(E, o, 4), e5 = JE(E, o, 5);
-        const float y00 = e0 * ci0 + e1 * ci1 + e2 * ci2, y01 = e0 * ci1 + e1 * ci3 + e2 * ci4,
-                    y02 = e0 * ci2 + e1 * ci4 + e2 * ci5;
-        const float y10 = e3 * ci0 + e4 * ci1 + e5 * ci2, y11 = e3 * ci1 + e4 * ci3 + e5 * ci4,
-                    y12 = e3 * ci2 + e4 * ci4 + e5 * ci5;
-        const float a0 = JE(E, o2, 0), a1 = JE(E, o2, 1), a2 = JE(E, o2, 2);
-        const float g0 = JE(E, o2, 3), g1 = JE(E, o2, 4), g2 = JE(E, o2, 5);
-        float m00 = y00 * a0 + y01 * a1 + y02 * a2;
-        float m01 = y00 * g0 + y01 * g1 + y02 * g2;
-        float m10 = y10 * a0 + y11 * a1 + y12 * a2;
-        float m11 = y10 * g0 + y11 * g1 + y12 * g2;
-        if (o2 == o) {
-          m00 -= 1.0f;
-          m11 -= 1.0f;
-        }
-        float f2[18];
-#pragma unroll
-        for (int q = 0; q < 18; ++q) f2[q] = JF(F, o2, q);
-        float* blk = acc + (size_t)s * 81;
-#pragma unroll
-        for (int r = 0; r < 9; ++r) {
-          const float fa = JF(F, o, r), fb = JF(F, o, 9 + r);
-          const float h0 = fa * m00 + fb * m10;
-          const float h1 = fa * m01 + fb * m11;
-#pragma unroll
-          for (int q = 0; q < 9; ++q) atomicAdd(blk + 9 * r + q, -(h0 * f2[q] + h1 * f2[9 + q]));
-        }
-      }
-      __syncthreads();
-    }
-    for (int i = t; i < pass_n * 81; i += kPairBS) {
-      float v = acc[i];
-      const int s = i / 81, e = i - 81 * s;
-      const int a = e / 9, b = e - 9 * a;
-      if (scol[s] == c && a == b) v += (float)Dc[9 * c + a];
-      vals[(size_t)(rb + pass_base + s) * 81 + e] = v;
-    }
-    __syncthreads();
-  }
-}
-
-// Sorted variant (no atomics): the row's observations are taken in batches of kSB; for
-// every (o, o') pair of a batch, G = F_o^T M (9 x 2) and F_o' (2 x 9) are staged in
-// shared memory grouped by target block (counting sort on the block slot); then warp w
-// owns the blocks s = w (mod 8) and accumulates each in registers, lane (a, g) holding
-// entries (a, 3g .. 3g+2) of the 9 x 9 block.
-constexpr int kSortBS = 256;
-constexpr int kSortPairs = 512;
-
-template <typename T>
-__global__ void __launch_bounds__(kSortBS)
-k_explicit_schur_sorted(const T* __restrict__ F, const T* __restrict__ E, int ld,
-                        const T* __restrict__ Cinv, int ldp, const int* __restrict__ cam_ptr,
-                        const int* __restrict__ cam_obs, const int* __restrict__ obs_pt,
-                        const int* __restrict__ obs_cam, const int* __restrict__ pt_ptr,
-                        const int* __restrict__ row_ptr, const int* __restrict__ cols,
-                        const double* __restrict__ Dc, int cap, int batch, T* __restrict__ vals) {
-  extern __shared__ __align__(16) unsigned char so_smem[];
-  T* acc = reinterpret_cast<T*>(so_smem);                              // [cap][81]
-  T* rec = acc + (size_t)cap * 81;                                     // [kSortPairs][36]
-  int* scol = reinterpret_cast<int*>(rec + (size_t)kSortPairs * 36);   // [cap]
-  int* scnt = scol + cap;                                              // [cap]
-  int* soff = scnt + cap;                                              // [cap + 1]
-  __shared__ int bo[64], bip[64], bob[64], bpre[65];
-  const int c = blockIdx.x;
-  const int rb = row_ptr[c], re = row_ptr[c + 1];
-  const int nslots = re - rb;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int ob0 = cam_ptr[c], nrow = cam_ptr[c + 1] - ob0;
-  const int la = lane / 3, lg = lane - 3 * (lane / 3);   // lane -> (row a, column group g)
-  for (int pass_base = 0; pass_base < nslots; pass_base += cap) {
-    const int pass_n = min(cap, nslots - pass_base);
-    for (int i = t; i < cap * 81; i += kSortBS) acc[i] = T(0);
-    for (int i = t; i < pass_n; i += kSortBS) scol[i] = cols[rb + pass_base + i];
-    __syncthreads();  // a row without observations goes straight to the write-out
-    for (int b0 = 0; b0 < nrow; b0 += batch) {
-      const int nb = min(batch, nrow - b0);
-      for (int i = t; i < pass_n; i += kSortBS) scnt[i] = 0;
-      if (t < nb) {
-        const int o = cam_obs[ob0 + b0 + t];
-        const int ip = obs_pt[o];
-        const int s0 = pt_ptr[ip];
-        bo[t] = o;
-        bip[t] = ip;
-        bob[t] = s0;
-        bpre[t + 1] = pt_ptr[ip + 1] - s0;   // pair count, turned into a prefix below
-      }
-      __syncthreads();
-      if (t == 0) {
-        bpre[0] = 0;
-        for (int i = 0; i < nb; ++i) bpre[i + 1] += bpre[i];
-      }
-      __syncthreads();
-      const int total = bpre[nb];
-      // pass 1: block slot of every pair, counted
-      for (int pi = t; pi < total; pi += kSortBS) {
-        int lo = 0, hi = nb - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (bpre[mid] <= pi) lo = mid; else hi = mid - 1;
-        }
-        const int c2 = obs_cam[bob[lo] + (pi - bpre[lo])];
-        int a = 0, z = pass_n - 1, s = -1;
-        while (a <= z) {
-          const int mid = (a + z) >> 1;
-          const int v = scol[mid];
-          if (v == c2) { s = mid; break; }
-          if (v < c2) a = mid + 1; else z = mid - 1;
-        }
-        if (s >= 0) atomicAdd(scnt + s, 1);
-      }
-      __syncthreads();
-      if (t == 0) {
-        int a = 0;
-        for (int s = 0; s < pass_n; ++s) {
-          soff[s] = a;
-          a += scnt[s];
-          scnt[s] = 0;
-        }
-        soff[pass_n] = a;
-      }
-      __syncthreads();
-      // pass 2: stage G = F_o^T M and F_o' of every pair at its slot's position
-      for (int pi = t; pi < total; pi += kSortBS) {
-        int lo = 0, hi = nb - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (bpre[mid] <= pi) lo = mid; else hi = mid - 1;
-        }
-        const int o = bo[lo], ip = bip[lo];
-        const int o2 = bob[lo] + (pi - bpre[lo]);
-        const int c2 = obs_cam[o2];
-        int a = 0, z = pass_n - 1, s = -1;
-        while (a <= z) {
-          const int mid = (a + z) >> 1;
-          const int v = scol[mid];
-          if (v == c2) { s = mid; break; }
-          if (v < c2) a = mid + 1; else z = mid - 1;
-        }
-        if (s < 0) continue;
-        const T ci0 = Cinv[ip], ci1 = Cinv[ldp + ip], ci2 = Cinv[2 * ldp + ip];
-        const T ci3 = Cinv[3 * ldp + ip], ci4 = Cinv[4 * ldp + ip], ci5 = Cinv[5 * ldp + ip];
-        const T e0 = JE(E, o, 0), e1 = JE(E, o, 1), e2 = JE(E, o, 2);
-        const T e3 = JE(E, o, 3), e4 = JE(E, o, 4), e5 = JE(E, o, 5);
-        const T y00 = e0 * ci0 + e1 * ci1 + e2 * ci2, y01 = e0 * ci1 + e1 * ci3 + e2 * ci4,
-                y02 = e0 * ci2 + e1 * ci4 + e2 * ci5;
-        const T y10 = e3 * ci0 + e4 * ci1 + e5 * ci2, y11 = e3 * ci1 + e4 * ci3 + e5 * ci4,
-                y12 = e3 * ci2 + e4 * ci4 + e5 * ci5;
-        const T a0 = JE(E, o2, 0), a1 = JE(E, o2, 1), a2 = JE(E, o2, 2);
-        const T g0 = JE(E, o2, 3), g1 = JE(E, o2, 4), g2 = JE(E, o2, 5);
-        T m00 = y00 * a0 + y01 * a1 + y02 * a2;
-        T m01 = y00 * g0 + y01 * g1 + y02 * g2;
-        T m10 = y10 * a0 + y11 * a1 + y12 * a2;
-        T m11 = y10 * g0 + y11 * g1 + y12 * g2;
-        if (o2 == o) {
-          m00 -= T(1);
-          m11 -= T(1);
-        }
-        T* r = rec + (size_t)(soff[s] + atomicAdd(scnt + s, 1)) * 36;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-          const T fa = JF(F, o, q), fb = JF(F, o, 9 + q);
-          r[2 * q] = fa * m00 + fb * m10;       // G[q][0]
-          r[2 * q + 1] = fa * m01 + fb * m11;   // G[q][1]
-        }
-#pragma unroll
-        for (int q = 0; q < 18; ++q) r[18 + q] = JF(F, o2, q);
-      }
-      __syncthreads();
-      // accumulate: warp w owns slots w, w + 8, ...
-      if (lane < 27) {
-        for (int s = warp; s < pass_n; s += kSortBS / 32) {
-          const int p0 = soff[s], p1 = soff[s + 1];
-          if (p0 == p1) continue;
-          T* blk = acc + (size_t)s * 81 + 9 * la + 3 * lg;
-          T s0 = blk[0], s1 = blk[1], s2 = blk[2];
-          for (int p = p0; p < p1; ++p) {
-            const T* r = rec + (size_t)p * 36;
-            const T h0 = r[2 * la], h1 = r[2 * la + 1];
-            const T* f2 = r + 18;
-            s0 -= h0 * f2[3 * lg] + h1 * f2[9 + 3 * lg];
-            s1 -= h0 * f2[3 * lg + 1] + h1 * f2[9 + 3 * lg + 1];
-            s2 -= h0 * f2[3 * lg + 2] + h1 * f2[9 + 3 * lg + 2];
+          if (v == c2) {
+            s = mid;
+            break;
           }
-          blk[0] = s0;
-          blk[1] = s1;
-          blk[2] = s2;
+          if (v < c2) lo = mid + 1;
+          else hi = mid - 1;
         }
+        if (s < 0 || lane >= 27) continue;
+        const T* wq = W + (size_t)q * 27 + 3 * lg;
+        T* blk = acc + (size_t)s * 81 + 9 * la + 3 * lg;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) atomicAdd(blk + j, -(wi0 * wq[j] + wi1 * wq[9 + j] + wi2 * wq[18 + j]));
       }
-      __syncthreads();
     }
-    for (int i = t; i < pass_n * 81; i += kSortBS) {
-      T v = acc[i];
+    __syncthreads();
+    for (int i = t; i < pass_n * 81; i += kExBS) {
       const int s = i / 81, e = i - 81 * s;
-      const int a = e / 9, b = e - 9 * a;
-      if (scol[s] == c && a == b) v += (T)Dc[9 * c + a];
+      const T v = scol[s] == c ? (T)Scc[(size_t)c * 81 + e] : acc[i];
       vals[(size_t)(rb + pass_base + s) * 81 + e] = v;
     }
     __syncthreads();
@@ -988,55 +723,35 @@ k_explicit_schur_sorted(const T* __restrict__ F, const T* __restrict__ E, int ld
 
 void explicit_schur(ba_problem* P, Level& L0, bool fp32) {
   const size_t elem = fp32 ? 4 : 8;
-  const int maxrow = L0.maxrow;
-  // observations per batch so that a batch's pairs fit the staging area
-  const int batch = std::max(1, std::min(64, kSortPairs / std::max(P->max_pt_obs, 1)));
-  if (P->max_pt_obs <= kSortPairs) {
-    const int cap = std::min(maxrow, 96);
-    const size_t smem = (size_t)cap * 81 * elem + (size_t)kSortPairs * 36 * elem + sizeof(int) * (3 * cap + 4);
-    if (fp32) {
-      BA_CUDA(cudaFuncSetAttribute(k_explicit_schur_sorted<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
-      L0.vals32.ensure(sizeof(float) * 81 * (size_t)L0.nnzb + 64);
-      k_explicit_schur_sorted<float><<<P->n_c, kSortBS, smem, P->stream>>>(
-          P->J32.as<float>(), P->J32.as<float>(), (int)P->ld, P->Cinv32.as<float>(), (int)P->ldp,
-          P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
-          P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Dc.as<double>(), cap, batch,
-          L0.vals32.as<float>());
-    } else {
-      BA_CUDA(cudaFuncSetAttribute(k_explicit_schur_sorted<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
-      L0.vals64.ensure(sizeof(double) * 81 * (size_t)L0.nnzb + 64);
-      k_explicit_schur_sorted<double><<<P->n_c, kSortBS, smem, P->stream>>>(
-          P->J64.as<double>(), P->J64.as<double>(), (int)P->ld, P->Cinv64.as<double>(), (int)P->ldp,
-          P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
-          P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Dc.as<double>(), cap, batch,
-          L0.vals64.as<double>());
-    }
-    launched(P);
-    return;
-  }
-  // points seen by more than kSortPairs cameras: per-warp accumulation kernels
+  const int cap = std::max(1, std::min(L0.maxrow, (int)((200 * 1024) / (81 * elem + 4))));
+  const size_t smem = (size_t)cap * 81 * elem + sizeof(int) * (size_t)cap;
+  P->scratch.ensure(elem * 27 * (size_t)std::max(P->n_o, 1) + 64);
+  const int g = cdiv(std::max(P->n_o, 1), 128);
   if (fp32) {
-    const int cap = std::min(maxrow, (int)((160 * 1024) / (81 * 4 + 4)));
-    const size_t smem = (size_t)cap * 81 * 4 + sizeof(int) * (cap + 4);
-    BA_CUDA(cudaFuncSetAttribute(k_explicit_schur_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     L0.vals32.ensure(sizeof(float) * 81 * (size_t)L0.nnzb + 64);
-    k_explicit_schur_pairs<<<P->n_c, kPairBS, smem, P->stream>>>(
-        P->J32.as<float>(), P->J32.as<float>(), (int)P->ld, P->Cinv32.as<float>(), (int)P->ldp,
-        P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
-        P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Dc.as<double>(), cap,
+    float* W = P->scratch.as<float>();
+    if (P->n_o) {
+      k_schur_w<float><<<g, 128, 0, P->stream>>>(P->J32.as<float>(), P->Cinv32.as<float>(), (int)P->ldp,
+                                                 P->obs_pt.as<int>(), P->n_o, W);
+      launched(P);
+    }
+    BA_CUDA(cudaFuncSetAttribute(k_explicit_w<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_explicit_w<float><<<P->n_c, kExBS, smem, P->stream>>>(
+        W, P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
+        P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Scc.as<double>(), cap,
         L0.vals32.as<float>());
   } else {
-    const int cap_max = (int)((160 * 1024) / (kExWarps * 81 * elem + 4));
-    const int cap = std::min(maxrow, cap_max);
-    const size_t smem = (size_t)kExWarps * cap * 81 * elem + sizeof(int) * (cap + 4);
-    BA_CUDA(cudaFuncSetAttribute(k_explicit_schur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     L0.vals64.ensure(sizeof(double) * 81 * (size_t)L0.nnzb + 64);
-    k_explicit_schur<double><<<P->n_c, kExWarps * 32, smem, P->stream>>>(
-        P->J64.as<double>(), P->J64.as<double>(), (int)P->ld, P->Cinv64.as<double>(), (int)P->ldp,
-        P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
-        P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Dc.as<double>(), cap,
+    double* W = P->scratch.as<double>();
+    if (P->n_o) {
+      k_schur_w<double><<<g, 128, 0, P->stream>>>(P->J64.as<double>(), P->Cinv64.as<double>(), (int)P->ldp,
+                                                  P->obs_pt.as<int>(), P->n_o, W);
+      launched(P);
+    }
+    BA_CUDA(cudaFuncSetAttribute(k_explicit_w<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_explicit_w<double><<<P->n_c, kExBS, smem, P->stream>>>(
+        W, P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
+        P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Scc.as<double>(), cap,
         L0.vals64.as<double>());
   }
   launched(P);

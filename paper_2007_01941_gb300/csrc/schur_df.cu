@@ -71,10 +71,9 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-// y += hi + lo as two FP64 atomic additions (the addition happens in the L2)
+// y += hi + lo: one FP64 addition (exact: the pair's bits fit a double) and one atomic
 __device__ __forceinline__ void f2_atomic_add(double* y, F2 v) {
-  atomicAdd(y, f2d_bits(v.h));
-  atomicAdd(y, f2d_bits(v.l));
+  atomicAdd(y, f2d_bits(v.h) + f2d_bits(v.l));
 }
 
 __device__ __forceinline__ void load_record_pair(const float* __restrict__ hi, const float* __restrict__ lo,
