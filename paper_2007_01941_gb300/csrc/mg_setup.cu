@@ -462,76 +462,141 @@ __global__ void k_nullspace0(const double* __restrict__ cams, int n_c, double* _
 }
 
 // ---------------------------------------------------------------------------
-// per-aggregate thin QR (Section 3.3) by modified Gram-Schmidt with one
-// re-orthogonalisation pass; a column whose remaining norm is <= 1e-10 of its
-// original norm is dropped (zero Q column, zero R row).  One warp per aggregate.
+// per-aggregate thin QR (Section 3.3) by Gram-Schmidt with one re-orthogonalisation
+// pass; a column whose remaining norm is <= 1e-10 of its original norm is dropped
+// (zero Q column, zero R row).  One CTA of kQrBS threads per aggregate, rows spread
+// over the threads.  Each pass projects column j on all earlier columns at once
+// (classical Gram-Schmidt: the j inner products come out of one block reduction, so
+// the dependency chain per column is two reductions long instead of 2j); with the
+// second pass this is as accurate as the modified variant with re-orthogonalisation.
 // ---------------------------------------------------------------------------
-// row stride of the aggregate matrix in shared memory: 17 doubles, so the 32 rows
-// a warp touches at once fall in different banks (16 would put them all in one)
+// row stride of the aggregate matrix in shared memory: 17 doubles, so the rows that
+// consecutive threads touch fall in different banks
 constexpr int kQrStride = kNull + 1;
+constexpr int kQrBS = 128;
+constexpr int kQrWarps = kQrBS / 32;
 
-__global__ void k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, const int* __restrict__ mem,
-                               const double* __restrict__ K, double* __restrict__ Q64, float* __restrict__ Q32,
-                               double* __restrict__ Kc, unsigned* __restrict__ kept_out) {
+// sum over the CTA of v (one value per thread); result in every thread
+__device__ __forceinline__ double qr_block_sum1(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < kQrWarps; ++w) s += red[w];
+  return s;
+}
+
+// sums over the CTA of p[0..15] (16 values per thread); h[0..15] in shared memory on
+// return.  Within a warp, each step halves the values a lane carries (it keeps one half
+// and adds its partner's copy of that half), so the 16 sums take 15 shuffles.
+__device__ __forceinline__ void qr_block_sum16(double p[kNull], double* red /*[kQrWarps][16]*/, double* h) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int half = 8, off = 16; half >= 1; half >>= 1, off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const double send = up ? p[k] : p[k + half];
+      const double keep = up ? p[k + half] : p[k];
+      p[k] = keep + __shfl_xor_sync(kFull, send, off);
+    }
+  }
+  // p[0] now holds the warp's partial of index idx; lanes l and l ^ 1 hold the same index
+  const double v = p[0] + __shfl_xor_sync(kFull, p[0], 1);
+  const int idx = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+  __syncthreads();
+  if ((lane & 1) == 0) red[warp * kNull + idx] = v;
+  __syncthreads();
+  if (threadIdx.x < kNull) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kQrWarps; ++w) s += red[w * kNull + threadIdx.x];
+    h[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kQrBS)
+k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, const int* __restrict__ mem,
+               const double* __restrict__ K, double* __restrict__ Q64, float* __restrict__ Q32,
+               double* __restrict__ Kc, unsigned* __restrict__ kept_out) {
   extern __shared__ __align__(16) unsigned char qsm[];
-  double* A = reinterpret_cast<double*>(qsm);  // [rows][16]
+  double* A = reinterpret_cast<double*>(qsm);  // [rows][kQrStride]
+  __shared__ double red[kQrWarps * kNull];
+  __shared__ double h[kNull];
+  __shared__ double Rs[kNull][kNull + 1];
   const int a = blockIdx.x;
-  const int lane = threadIdx.x;
+  const int t = threadIdx.x;
   const int mb = mptr[a], me = mptr[a + 1];
   const int rows = (me - mb) * bs;
-  for (int r = lane; r < rows; r += 32) {
+  for (int e = t; e < rows * kNull; e += kQrBS) {
+    const int r = e / kNull, j = e - r * kNull;
     const int s = r / bs, u = r - s * bs;
-    const double* src = K + ((size_t)mem[mb + s] * bs + u) * kNull;
-    for (int j = 0; j < kNull; ++j) A[r * kQrStride + j] = src[j];
+    A[r * kQrStride + j] = K[((size_t)mem[mb + s] * bs + u) * kNull + j];
   }
-  __syncwarp();
-  double R[kNull];  // column j of R is produced at step j; lane j keeps row j of R
-  for (int j = 0; j < kNull; ++j) R[j] = 0.0;
+  for (int e = t; e < kNull * kNull; e += kQrBS) Rs[e / kNull][e % kNull] = 0.0;
+  __syncthreads();
   unsigned kept = 0;
   for (int j = 0; j < kNull; ++j) {
-    double n0 = 0.0;
-    for (int r = lane; r < rows; r += 32) n0 += A[r * kQrStride + j] * A[r * kQrStride + j];
-    n0 = sqrt(warp_sum(n0));
-    double rcol[kNull];
-    for (int i = 0; i < kNull; ++i) rcol[i] = 0.0;
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int i = 0; i < j; ++i) {
-        if (!(kept >> i & 1u)) continue;
-        double h = 0.0;
-        for (int r = lane; r < rows; r += 32) h += A[r * kQrStride + i] * A[r * kQrStride + j];
-        h = warp_sum(h);
-        for (int r = lane; r < rows; r += 32) A[r * kQrStride + j] -= h * A[r * kQrStride + i];
-        __syncwarp();
-        rcol[i] += h;
+    double n2 = 0.0;
+    for (int r = t; r < rows; r += kQrBS) n2 += A[r * kQrStride + j] * A[r * kQrStride + j];
+    const double n0 = sqrt(qr_block_sum1(n2, red));
+    double rc[kNull];
+#pragma unroll
+    for (int i = 0; i < kNull; ++i) rc[i] = 0.0;
+    if (j > 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        double p[kNull];
+#pragma unroll
+        for (int i = 0; i < kNull; ++i) p[i] = 0.0;
+        for (int r = t; r < rows; r += kQrBS) {
+          const double aj = A[r * kQrStride + j];
+#pragma unroll
+          for (int i = 0; i < kNull; ++i)
+            if (i < j) p[i] += A[r * kQrStride + i] * aj;
+        }
+        qr_block_sum16(p, red, h);
+        for (int r = t; r < rows; r += kQrBS) {
+          double aj = A[r * kQrStride + j];
+#pragma unroll
+          for (int i = 0; i < kNull; ++i)
+            if (i < j) aj -= h[i] * A[r * kQrStride + i];
+          A[r * kQrStride + j] = aj;
+        }
+#pragma unroll
+        for (int i = 0; i < kNull; ++i)
+          if (i < j) rc[i] += h[i];
+        __syncthreads();
       }
     }
-    double nv = 0.0;
-    for (int r = lane; r < rows; r += 32) nv += A[r * kQrStride + j] * A[r * kQrStride + j];
-    nv = sqrt(warp_sum(nv));
+    double v2 = 0.0;
+    for (int r = t; r < rows; r += kQrBS) v2 += A[r * kQrStride + j] * A[r * kQrStride + j];
+    const double nv = sqrt(qr_block_sum1(v2, red));
     const bool keep = n0 > 0.0 && nv > 1e-10 * n0;
     const double scale = keep ? 1.0 / nv : 0.0;
-    for (int r = lane; r < rows; r += 32) A[r * kQrStride + j] *= scale;
-    __syncwarp();
+    for (int r = t; r < rows; r += kQrBS) A[r * kQrStride + j] *= scale;
     if (keep) {
-      rcol[j] = nv;
+      rc[j] = nv;
       kept |= 1u << j;
     }
-    // lane i stores R[i][j]
-    for (int i = 0; i < kNull; ++i)
-      if (lane == i) R[j] = rcol[i];
+    if (t == 0)
+      for (int i = 0; i < kNull; ++i) Rs[i][j] = rc[i];
+    __syncthreads();
   }
   // Q blocks back to the member nodes
-  for (int r = lane; r < rows; r += 32) {
+  for (int e = t; e < rows * kNull; e += kQrBS) {
+    const int r = e / kNull, j = e - r * kNull;
     const int s = r / bs, u = r - s * bs;
-    const size_t dst = ((size_t)mem[mb + s] * bs + u) * kNull;
-    for (int j = 0; j < kNull; ++j) {
-      Q64[dst + j] = A[r * kQrStride + j];
-      Q32[dst + j] = (float)A[r * kQrStride + j];
-    }
+    const size_t dst = ((size_t)mem[mb + s] * bs + u) * kNull + j;
+    const double q = A[r * kQrStride + j];
+    Q64[dst] = q;
+    Q32[dst] = (float)q;
   }
-  if (lane < kNull)
-    for (int j = 0; j < kNull; ++j) Kc[((size_t)a * kNull + lane) * kNull + j] = R[j];
-  if (lane == 0) kept_out[a] = kept;
+  for (int e = t; e < kNull * kNull; e += kQrBS) Kc[(size_t)a * kNull * kNull + e] = Rs[e / kNull][e % kNull];
+  if (t == 0) kept_out[a] = kept;
 }
 
 // ---------------------------------------------------------------------------
@@ -857,89 +922,124 @@ __global__ void k_dense_identity_pad(int N, int Np, double* __restrict__ A) {
 
 constexpr int kGJ = 32;
 constexpr int kGJBS = 256;
-__global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* __restrict__ A, int Np, double* __restrict__ prow,
-                                                        double* __restrict__ pcol, int* flags) {
+// Per pivot block K (kGJ wide):
+//   phase 1: CTA 0 inverts P = A_KK in shared memory (Gauss-Jordan, SPD, no pivoting) into
+//            pinv; every CTA copies the column panel A_IK into pcol;
+//   phase 2: new row panel prow_J = P^-1 A_KJ (J != K), prow_K = P^-1;
+//   phase 3: A_IJ <- A_IJ - A_IK prow_J and A_IK <- -A_IK P^-1 (I != K), A_KJ <- prow_J.
+// Products are split into work items of kGJ/4 rows of one tile; grid-wide syncs
+// separate the phases, and no phase writes a tile that it also reads.
+constexpr int kGJRows = kGJ / 4;
+
+// out (kGJRows x kGJ rows r0.. of the tile) = a (rows r0.. of an kGJ x kGJ tile, ld_a) * b (kGJ x kGJ, ld_b)
+__device__ __forceinline__ void gj_rows_product(const double* __restrict__ a, size_t ld_a, const double* __restrict__ b,
+                                                size_t ld_b, double sa[kGJRows][kGJ + 1], double sb[kGJ][kGJ + 1],
+                                                double acc[kGJRows * kGJ / kGJBS]) {
+  const int t = threadIdx.x;
+  for (int e = t; e < kGJRows * kGJ; e += kGJBS) sa[e / kGJ][e % kGJ] = a[(size_t)(e / kGJ) * ld_a + e % kGJ];
+  for (int e = t; e < kGJ * kGJ; e += kGJBS) sb[e / kGJ][e % kGJ] = b[(size_t)(e / kGJ) * ld_b + e % kGJ];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < kGJRows * kGJ / kGJBS; ++q) {
+    const int e = t + q * kGJBS, u = e / kGJ, v = e % kGJ;
+    double s = 0.0;
+#pragma unroll 8
+    for (int k = 0; k < kGJ; ++k) s += sa[u][k] * sb[k][v];
+    acc[q] = s;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* __restrict__ A, int Np, double* __restrict__ pinv,
+                                                        double* __restrict__ pcol, double* __restrict__ prow,
+                                                        int* flags) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double piv[kGJ][kGJ + 1];
-  __shared__ double tA[kGJ][kGJ + 1];
-  __shared__ double tB[kGJ][kGJ + 1];
-  __shared__ double tC[kGJ][kGJ + 1];
+  __shared__ double sa[kGJRows][kGJ + 1];
+  __shared__ double sb[kGJ][kGJ + 1];
+  constexpr int kPer = kGJRows * kGJ / kGJBS;   // outputs per thread in a work item
   const int nb = Np / kGJ;
   const int t = threadIdx.x;
   for (int K = 0; K < nb; ++K) {
     const int K0 = K * kGJ;
-    // copy pivot row panel (kGJ x Np) and column panel (Np x kGJ)
-    for (size_t idx = (size_t)blockIdx.x * kGJBS + t; idx < (size_t)kGJ * Np; idx += (size_t)gridDim.x * kGJBS) {
-      const int r = (int)(idx / Np), c = (int)(idx % Np);
-      prow[idx] = A[(size_t)(K0 + r) * Np + c];
-      pcol[(size_t)c * kGJ + r] = A[(size_t)c * Np + K0 + r];
+    // phase 1
+    for (size_t idx = (size_t)blockIdx.x * kGJBS + t; idx < (size_t)Np * kGJ; idx += (size_t)gridDim.x * kGJBS) {
+      const int r = (int)(idx / kGJ), c = (int)(idx % kGJ);
+      pcol[idx] = A[(size_t)r * Np + K0 + c];
+    }
+    if (blockIdx.x == 0) {
+      for (int e = t; e < kGJ * kGJ; e += kGJBS) piv[e / kGJ][e % kGJ] = A[(size_t)(K0 + e / kGJ) * Np + K0 + e % kGJ];
+      __syncthreads();
+      bool bad = false;
+      for (int k = 0; k < kGJ; ++k) {
+        const double pk = piv[k][k];
+        if (!(pk > 0.0)) bad = true;
+        const double ip = 1.0 / pk;
+        __syncthreads();
+        double newv[kGJ * kGJ / kGJBS];
+        int cnt = 0;
+        for (int e = t; e < kGJ * kGJ; e += kGJBS) {
+          const int i = e / kGJ, j = e % kGJ;
+          double v;
+          if (i == k && j == k) v = ip;
+          else if (i == k) v = piv[k][j] * ip;
+          else if (j == k) v = -piv[i][k] * ip;
+          else v = piv[i][j] - piv[i][k] * (piv[k][j] * ip);
+          newv[cnt++] = v;
+        }
+        __syncthreads();
+        cnt = 0;
+        for (int e = t; e < kGJ * kGJ; e += kGJBS) piv[e / kGJ][e % kGJ] = newv[cnt++];
+      }
+      __syncthreads();
+      if (bad && t == 0) flags[F_NOT_SPD_COARSE] = 1;
+      for (int e = t; e < kGJ * kGJ; e += kGJBS) pinv[e] = piv[e / kGJ][e % kGJ];
     }
     grid.sync();
-    // every CTA inverts the pivot block (Gauss-Jordan in shared memory)
-    for (int e = t; e < kGJ * kGJ; e += kGJBS) piv[e / kGJ][e % kGJ] = prow[(size_t)(e / kGJ) * Np + K0 + e % kGJ];
-    __syncthreads();
-    bool bad = false;
-    for (int k = 0; k < kGJ; ++k) {
-      const double p = piv[k][k];
-      if (!(p > 0.0)) bad = true;
-      const double ip = 1.0 / p;
-      __syncthreads();
-      // update using old row k / column k
-      double newv[4];
-      int cnt = 0;
-      for (int e = t; e < kGJ * kGJ; e += kGJBS) {
-        const int i = e / kGJ, j = e % kGJ;
-        double v;
-        if (i == k && j == k) v = ip;
-        else if (i == k) v = piv[k][j] * ip;
-        else if (j == k) v = -piv[i][k] * ip;
-        else v = piv[i][j] - piv[i][k] * piv[k][j] * ip;
-        newv[cnt++] = v;
-      }
-      __syncthreads();
-      cnt = 0;
-      for (int e = t; e < kGJ * kGJ; e += kGJBS) piv[e / kGJ][e % kGJ] = newv[cnt++];
-      __syncthreads();
-    }
-    if (bad && blockIdx.x == 0 && t == 0) flags[F_NOT_SPD_COARSE] = 1;
-    // tiles (I, J): I, J block indices
-    for (int tile = blockIdx.x; tile < nb * nb; tile += gridDim.x) {
-      const int I = tile / nb, J = tile % nb;
-      const int I0 = I * kGJ, J0 = J * kGJ;
-      // tA = A_IK (old column panel rows I0..), tB = A_KJ (old row panel cols J0..)
-      for (int e = t; e < kGJ * kGJ; e += kGJBS) {
-        const int u = e / kGJ, v = e % kGJ;
-        tA[u][v] = pcol[(size_t)(I0 + u) * kGJ + v];
-        tB[u][v] = prow[(size_t)u * Np + J0 + v];
-      }
-      __syncthreads();
-      // tC = Pinv A_KJ
-      for (int e = t; e < kGJ * kGJ; e += kGJBS) {
-        const int u = e / kGJ, v = e % kGJ;
-        double s = 0.0;
-        for (int k = 0; k < kGJ; ++k) s += piv[u][k] * tB[k][v];
-        tC[u][v] = s;
-      }
-      __syncthreads();
-      for (int e = t; e < kGJ * kGJ; e += kGJBS) {
-        const int u = e / kGJ, v = e % kGJ;
-        double val;
-        if (I == K && J == K) {
-          val = piv[u][v];
-        } else if (I == K) {
-          val = tC[u][v];                       // Pinv A_KJ
-        } else if (J == K) {
-          double s = 0.0;                       // -A_IK Pinv
-          for (int k = 0; k < kGJ; ++k) s += tA[u][k] * piv[k][v];
-          val = -s;
-        } else {
-          double s = 0.0;                       // A_IJ - A_IK Pinv A_KJ
-          for (int k = 0; k < kGJ; ++k) s += tA[u][k] * tC[k][v];
-          val = A[(size_t)(I0 + u) * Np + J0 + v] - s;
+    // phase 2: work items (J, row quarter) of the row panel
+    for (int w = blockIdx.x; w < nb * 4; w += gridDim.x) {
+      const int J = w >> 2, r0 = (w & 3) * kGJRows;
+      double acc[kPer];
+      if (J == K) {
+        for (int q = 0; q < kPer; ++q) {
+          const int e = t + q * kGJBS;
+          acc[q] = pinv[(r0 + e / kGJ) * kGJ + e % kGJ];
         }
-        A[(size_t)(I0 + u) * Np + J0 + v] = val;
+      } else {
+        gj_rows_product(pinv + (size_t)r0 * kGJ, kGJ, A + (size_t)K0 * Np + J * kGJ, Np, sa, sb, acc);
       }
-      __syncthreads();
+      for (int q = 0; q < kPer; ++q) {
+        const int e = t + q * kGJBS;
+        prow[(size_t)(r0 + e / kGJ) * Np + J * kGJ + e % kGJ] = acc[q];
+      }
+    }
+    grid.sync();
+    // phase 3: work items (I, J, row quarter)
+    for (int w = blockIdx.x; w < nb * nb * 4; w += gridDim.x) {
+      const int I = w / (nb * 4);
+      const int rem = w - I * nb * 4;
+      const int J = rem >> 2, r0 = (rem & 3) * kGJRows;
+      if (I == K) {
+        for (int e = t; e < kGJRows * kGJ; e += kGJBS)
+          A[(size_t)(K0 + r0 + e / kGJ) * Np + J * kGJ + e % kGJ] = prow[(size_t)(r0 + e / kGJ) * Np + J * kGJ + e % kGJ];
+        continue;
+      }
+      double acc[kPer];
+      const double* a = pcol + (size_t)(I * kGJ + r0) * kGJ;   // old A_IK rows
+      if (J == K) {
+        gj_rows_product(a, kGJ, pinv, kGJ, sa, sb, acc);
+        for (int q = 0; q < kPer; ++q) {
+          const int e = t + q * kGJBS;
+          A[(size_t)(I * kGJ + r0 + e / kGJ) * Np + K0 + e % kGJ] = -acc[q];
+        }
+      } else {
+        gj_rows_product(a, kGJ, prow + (size_t)J * kGJ, Np, sa, sb, acc);
+        for (int q = 0; q < kPer; ++q) {
+          const int e = t + q * kGJBS;
+          double* dst = A + (size_t)(I * kGJ + r0 + e / kGJ) * Np + J * kGJ + e % kGJ;
+          *dst -= acc[q];
+        }
+      }
     }
     grid.sync();
   }
@@ -963,14 +1063,16 @@ static void dense_inverse(ba_problem* P, Level& L) {
   launched(P);
   k_dense_identity_pad<<<cdiv((long long)Np * Np, 256), 256, 0, P->stream>>>(N, Np, A);
   launched(P);
-  P->scratch.ensure(sizeof(double) * 2 * (size_t)kGJ * Np + 64);
-  double* prow = P->scratch.as<double>();
-  double* pcol = prow + (size_t)kGJ * Np;
+  P->scratch.ensure(sizeof(double) * (2 * (size_t)kGJ * Np + kGJ * kGJ) + 64);
+  double* pinv = P->scratch.as<double>();
+  double* pcol = pinv + (size_t)kGJ * kGJ;
+  double* prow = pcol + (size_t)kGJ * Np;
   int nblk = 0;
   BA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, k_gauss_jordan, kGJBS, 0));
-  int grid = std::max(1, std::min(nblk * P->n_sm, (Np / kGJ) * (Np / kGJ)));
+  const int nbk = Np / kGJ;
+  int grid = std::max(1, std::min(nblk * P->n_sm, nbk * nbk * 4));
   int* flags = P->flags.as<int>();
-  void* args[] = {(void*)&A, (void*)&Np, (void*)&prow, (void*)&pcol, (void*)&flags};
+  void* args[] = {(void*)&A, (void*)&Np, (void*)&pinv, (void*)&pcol, (void*)&prow, (void*)&flags};
   BA_CUDA(cudaLaunchCooperativeKernel((void*)k_gauss_jordan, grid, kGJBS, args, 0, P->stream));
   launched(P);
 }
@@ -1146,7 +1248,7 @@ void mg_setup(ba_problem* P) {
     const size_t qsm = sizeof(double) * (size_t)o.max_agg * L.bs * kQrStride;
     BA_REQUIRE(qsm <= 200 * 1024, BA_ERR_LIMIT, "max_agg too large for the aggregate QR");
     BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
-    k_aggregate_qr<<<L1.n, 32, qsm, P->stream>>>(L1.n, L.bs, L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
+    k_aggregate_qr<<<L1.n, kQrBS, qsm, P->stream>>>(L1.n, L.bs, L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
                                                 L.K.as<double>(), L.Q64.as<double>(), L.Q32.as<float>(),
                                                 L1.K.as<double>(), L1.kept.as<unsigned>());
     launched(P);
