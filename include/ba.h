@@ -92,6 +92,8 @@ typedef struct {
   int outer_product;    /* ba_outer_product used by BA_MIXED (BA_OUTER_PAIRED_FP32) */
   int stop_rule;        /* ba_stop_rule (BA_STOP_RELRES) */
   double tau;           /* Nash-Sofer tolerance (0.1; Section 5 uses 0.1 and 0.01) */
+  int overlap_launches; /* 1: launch the PCG loop's kernels as programmatic dependent launches,
+                           so each is scheduled while its predecessor finishes (1) */
 } ba_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
                 ("post_smooth", c_int), ("lanczos_steps", c_int), ("coarse_max_nodes", c_int),
                 ("max_levels", c_int), ("cheb_lo", c_double), ("cheb_hi", c_double),
                 ("level0_operator", c_int), ("fused_vcycle", c_int), ("outer_product", c_int),
-                ("stop_rule", c_int), ("tau", c_double)]
+                ("stop_rule", c_int), ("tau", c_double), ("overlap_launches", c_int)]
 
 
 class Info(ctypes.Structure):

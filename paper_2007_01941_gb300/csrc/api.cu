@@ -95,6 +95,7 @@ void ba_default_options(ba_options* o) {
   o->outer_product = BA_OUTER_PAIRED_FP32;
   o->stop_rule = BA_STOP_RELRES;
   o->tau = 0.1;
+  o->overlap_launches = 1;
 }
 
 ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx, const int32_t* pt_idx,

@@ -232,6 +232,24 @@ void check_flags(ba_problem* P);                          // sync, read, raise
 void clear_flags(ba_problem* P);
 void launched(ba_problem* P);                              // count + check launch error
 
+// Launches kern on the problem's stream; with opt.overlap_launches as a programmatic
+// dependent launch (the kernel must call pdl_wait() before it touches memory).
+template <typename... KArgs, typename... Args>
+void launch_k(ba_problem* P, void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = P->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = P->opt.overlap_launches ? 1 : 0;
+  BA_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+  launched(P);
+}
+
 // ---- graph preprocessing (graph.cu) ----------------------------------------
 void build_graph(ba_problem* P, const int32_t* cam_idx_dev, const int32_t* pt_idx_dev);
 

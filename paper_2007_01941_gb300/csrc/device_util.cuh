@@ -10,6 +10,13 @@ namespace ba {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Programmatic dependent launch (launch_k with overlap): a kernel may be scheduled
+// while the previous kernel of the stream is still running; pdl_wait() blocks until
+// that kernel has completed and its writes are visible, pdl_trigger() lets the next
+// kernel be scheduled.  Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Per-observation Jacobian record: F_o (2 x 9, row-major) then E_o (2 x 3, row-major),
 // 24 values, 96 bytes in FP32 / 192 bytes in FP64 (16-byte aligned).
 constexpr int kRec = 24;

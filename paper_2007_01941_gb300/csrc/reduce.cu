@@ -10,6 +10,8 @@ template <typename T>
 __global__ void __launch_bounds__(kRedBS) k_dot(const T* __restrict__ a, const T* __restrict__ b,
                                                 size_t n, double* partial, unsigned* counter,
                                                 double* out) {
+  pdl_wait();
+  pdl_trigger();
   double acc = 0.0;
   for (size_t i = (size_t)blockIdx.x * kRedBS + threadIdx.x; i < n; i += (size_t)gridDim.x * kRedBS)
     acc += (double)a[i] * (double)b[i];
@@ -25,16 +27,14 @@ int reduce_blocks(ba_problem* P, size_t n) {
 
 void dot64(ba_problem* P, const double* a, const double* b, size_t n, int slot) {
   int g = reduce_blocks(P, n);
-  k_dot<double><<<g, kRedBS, 0, P->stream>>>(a, b, n, P->partial.as<double>(),
-                                             P->counter.as<unsigned>(), P->scal.as<double>() + slot);
-  launched(P);
+  launch_k(P, k_dot<double>, g, kRedBS, 0, a, b, n, P->partial.as<double>(), P->counter.as<unsigned>(),
+           P->scal.as<double>() + slot);
 }
 
 void dot32(ba_problem* P, const float* a, const float* b, size_t n, int slot) {
   int g = reduce_blocks(P, n);
-  k_dot<float><<<g, kRedBS, 0, P->stream>>>(a, b, n, P->partial.as<double>(),
-                                             P->counter.as<unsigned>(), P->scal.as<double>() + slot);
-  launched(P);
+  launch_k(P, k_dot<float>, g, kRedBS, 0, a, b, n, P->partial.as<double>(), P->counter.as<unsigned>(),
+           P->scal.as<double>() + slot);
 }
 
 void launched(ba_problem* P) {

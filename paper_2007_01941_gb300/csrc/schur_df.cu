@@ -117,6 +117,8 @@ k_schur_matvec_df(const float* __restrict__ Jh, const float* __restrict__ Jl, co
                   const int4* __restrict__ tile_desc, const unsigned char* __restrict__ tile_perm,
                   const int* __restrict__ chunk_tile, int n_chunks, const float2* __restrict__ xs,
                   double* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned le = (lane == 31) ? kFull : ((2u << lane) - 1u);
   for (int chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
@@ -281,6 +283,8 @@ k_schur_matvec_df(const float* __restrict__ Jh, const float* __restrict__ Jl, co
 // xs = hi/lo split of x; with Dc, also y = Dc o x (the product's diagonal term)
 __global__ void k_split_diag(size_t n, const double* __restrict__ x, float2* __restrict__ xs,
                              const double* __restrict__ Dc, double* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double v = x[i];
@@ -294,8 +298,7 @@ bool outer_df(ba_problem* P) { return P->opt.precision == BA_MIXED && P->opt.out
 void split_vector(ba_problem* P, const double* x, const double* Dc, double* y) {
   const size_t n = (size_t)P->n_c * 9;
   P->xsplit.ensure(sizeof(float2) * n + 64);
-  k_split_diag<<<cdiv((long long)n, 256), 256, 0, P->stream>>>(n, x, P->xsplit.as<float2>(), Dc, y);
-  launched(P);
+  launch_k(P, k_split_diag, cdiv((long long)n, 256), 256, 0, n, x, P->xsplit.as<float2>(), Dc, y);
 }
 
 // y += S x without the diagonal term; P->xsplit must hold the split of x
@@ -308,11 +311,10 @@ void matvec_df_accumulate(ba_problem* P, double* y) {
     grid = std::max(1, std::min(P->n_chunks, P->n_sm * std::max(per_sm, 1)));
   }
   KernelTimer kt(P, BA_KT_SCHUR_DF);
-  k_schur_matvec_df<<<grid, kDfWarps * 32, 0, P->stream>>>(
-      P->J32.as<float>(), P->J32lo.as<float>(), P->Cinv32.as<float>(), P->Cinv32lo.as<float>(), (int)P->ldp,
-      P->obs_cam.as<int>(), P->tile_desc.as<int4>(), P->tile_perm.as<unsigned char>(), P->chunk_tile.as<int>(),
-      P->n_chunks, P->xsplit.as<float2>(), y);
-  launched(P);
+  launch_k(P, k_schur_matvec_df, grid, kDfWarps * 32, 0, P->J32.as<float>(), P->J32lo.as<float>(),
+           P->Cinv32.as<float>(), P->Cinv32lo.as<float>(), (int)P->ldp, P->obs_cam.as<int>(),
+           P->tile_desc.as<int4>(), P->tile_perm.as<unsigned char>(), P->chunk_tile.as<int>(), P->n_chunks,
+           P->xsplit.as<float2>(), y);
 }
 
 }  // namespace ba

@@ -292,10 +292,14 @@ static void vcycle(ba_problem* P, int l, const T* b, T* x) {
 // preconditioner application on FP64 camera vectors
 // ---------------------------------------------------------------------------
 __global__ void k_to_float(size_t n, const double* __restrict__ a, float* __restrict__ b) {
+  pdl_wait();
+  pdl_trigger();
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
 }
 __global__ void k_to_double(size_t n, const float* __restrict__ a, double* __restrict__ b) {
+  pdl_wait();
+  pdl_trigger();
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (double)a[i];
 }
@@ -335,11 +339,9 @@ void precond_apply(ba_problem* P, const double* r, double* z) {
   if (level_fp32(P)) {
     float* b = L0.vb.as<float>();
     float* x = L0.vx.as<float>();
-    k_to_float<<<g, 256, 0, P->stream>>>(n, r, b);
-    launched(P);
+    launch_k(P, k_to_float, g, 256, 0, n, r, b);
     vcycle<float>(P, 0, b, x);
-    k_to_double<<<g, 256, 0, P->stream>>>(n, x, z);
-    launched(P);
+    launch_k(P, k_to_double, g, 256, 0, n, x, z);
   } else {
     double* b = L0.vb.as<double>();
     BA_CUDA(cudaMemcpyAsync(b, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream));
@@ -357,6 +359,8 @@ __global__ void __launch_bounds__(kVecBS)
 k_pcg_update(size_t n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
              const double* __restrict__ q, double* scal, int s_rz, double* partial, unsigned* counter,
              int* flags) {
+  pdl_wait();
+  pdl_trigger();
   const double pq = scal[S_PQ];
   const double alpha = scal[s_rz] / pq;
   const bool ok = pq > 0.0 && isfinite(alpha);
@@ -386,6 +390,8 @@ k_pcg_update(size_t n, double* __restrict__ x, double* __restrict__ r, const dou
 __global__ void k_pcg_direction(size_t n, double* __restrict__ p, const double* __restrict__ z,
                                 const double* __restrict__ scal, int s_new, int s_old,
                                 const double* __restrict__ Dc, double* __restrict__ q, float2* __restrict__ ps) {
+  pdl_wait();
+  pdl_trigger();
   const double beta = s_new >= 0 ? scal[s_new] / scal[s_old] : 0.0;
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
@@ -411,10 +417,9 @@ static void pcg_head(ba_problem* P, double* x) {
   double *r = P->r.as<double>(), *p = P->p.as<double>(), *q = P->q.as<double>();
   matvec64_accumulate(P, p, q);  // q = D_c p was written with p
   dot64(P, p, q, n, S_PQ);
-  k_pcg_update<<<reduce_blocks(P, n), kVecBS, 0, P->stream>>>(n, x, r, p, q, P->scal.as<double>(), S_RZ,
+  launch_k(P, k_pcg_update, reduce_blocks(P, n), kVecBS, 0, n, x, r, p, q, P->scal.as<double>(), S_RZ,
                                                               P->partial.as<double>(), P->counter.as<unsigned>(),
                                                               P->flags.as<int>());
-  launched(P);
 }
 
 // counts the iteration and sets the loop condition: continue while |r|^2 > rtol^2 |b|^2,
@@ -427,6 +432,8 @@ __device__ __host__ inline bool pcg_converged(int rule, double it, double rr, do
 
 __global__ void k_pcg_check(double* scal, const int* flags, int max_iters, double rtol2, int rule, double tau,
                             cudaGraphConditionalHandle h) {
+  pdl_wait();
+  pdl_trigger();
   const double it = scal[S_ITER] + 1.0;
   scal[S_ITER] = it;
   const double rr = scal[S_RR], bb = scal[S_BB];
@@ -436,6 +443,8 @@ __global__ void k_pcg_check(double* scal, const int* flags, int max_iters, doubl
 }
 
 __global__ void k_copy_slot(double* scal, int dst, int src) {
+  pdl_wait();
+  pdl_trigger();
   if (threadIdx.x == 0) scal[dst] = scal[src];
 }
 
@@ -445,12 +454,10 @@ static void pcg_tail(ba_problem* P) {
   double *r = P->r.as<double>(), *z = P->z.as<double>(), *p = P->p.as<double>();
   precond_apply(P, r, z);
   dot64(P, r, z, n, S_TMP2);
-  k_pcg_direction<<<cdiv((long long)n, 256), 256, 0, P->stream>>>(n, p, z, P->scal.as<double>(), S_TMP2, S_RZ,
+  launch_k(P, k_pcg_direction, cdiv((long long)n, 256), 256, 0, n, p, z, P->scal.as<double>(), S_TMP2, S_RZ,
                                                                    P->Dc.as<double>(), P->q.as<double>(),
                                                                    split_target(P));
-  launched(P);
-  k_copy_slot<<<1, 32, 0, P->stream>>>(P->scal.as<double>(), S_RZ, S_TMP2);
-  launched(P);
+  launch_k(P, k_copy_slot, 1, 32, 0, P->scal.as<double>(), S_RZ, S_TMP2);
 }
 
 // Builds [head, check] -> while(cond) { tail, head, check } as one executable graph that
@@ -473,9 +480,8 @@ static void build_pcg_graph(ba_problem* P) {
     P->stream = P->cap_stream;
     BA_CUDA(cudaStreamBeginCaptureToGraph(P->cap_stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     pcg_head(P, x);
-    k_pcg_check<<<1, 1, 0, P->stream>>>(P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2,
+    launch_k(P, k_pcg_check, 1, 1, 0, P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2,
                                          P->opt.stop_rule, P->opt.tau, h);
-    launched(P);
     const long long head_kernels = P->launches - launches0;
     cudaStreamCaptureStatus status;
     const cudaGraphNode_t* deps = nullptr;
@@ -497,9 +503,8 @@ static void build_pcg_graph(ba_problem* P) {
     const long long body0 = P->launches;
     pcg_tail(P);
     pcg_head(P, x);
-    k_pcg_check<<<1, 1, 0, P->stream>>>(P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2,
+    launch_k(P, k_pcg_check, 1, 1, 0, P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2,
                                          P->opt.stop_rule, P->opt.tau, h);
-    launched(P);
     BA_CUDA(cudaStreamEndCapture(P->cap_stream, &body));
     BA_CUDA(cudaGraphInstantiate(&P->pcg_exec, g, 0));
     cudaGraphDestroy(g);
@@ -549,9 +554,8 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
   precond_apply(P, r, z);
   int s_rz = S_RZ, s_new = S_TMP2;
   dot64(P, r, z, n, s_rz);
-  k_pcg_direction<<<g, 256, 0, P->stream>>>(n, p, z, scal, -1, 0, P->Dc.as<double>(), q,
+  launch_k(P, k_pcg_direction, g, 256, 0, n, p, z, scal, -1, 0, P->Dc.as<double>(), q,
                                             split_target(P));  // p = z
-  launched(P);
   const int rg = reduce_blocks(P, n);
   const double rtol2 = P->opt.rtol * P->opt.rtol;
   double rel = 1.0;
@@ -586,9 +590,8 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
   while (it < P->opt.max_iters) {
     matvec64_accumulate(P, p, q);  // q = D_c p was written with p
     dot64(P, p, q, n, S_PQ);
-    k_pcg_update<<<rg, kVecBS, 0, P->stream>>>(n, dc, r, p, q, scal, s_rz, P->partial.as<double>(),
+    launch_k(P, k_pcg_update, rg, kVecBS, 0, n, dc, r, p, q, scal, s_rz, P->partial.as<double>(),
                                                P->counter.as<unsigned>(), P->flags.as<int>());
-    launched(P);
     ++it;
     fetch_scalars(P, S_RR, S_DQ - S_RR + 1);
     rel = std::sqrt(P->h_scal[S_RR] / bb);
@@ -599,9 +602,8 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
     if (done) break;
     precond_apply(P, r, z);
     dot64(P, r, z, n, s_new);
-    k_pcg_direction<<<g, 256, 0, P->stream>>>(n, p, z, scal, s_new, s_rz, P->Dc.as<double>(), q,
+    launch_k(P, k_pcg_direction, g, 256, 0, n, p, z, scal, s_new, s_rz, P->Dc.as<double>(), q,
                                               split_target(P));
-    launched(P);
     std::swap(s_rz, s_new);
   }
   P->pcg_iters = it;

@@ -111,6 +111,8 @@ __device__ __forceinline__ T row_dinv(const T* __restrict__ Dinv_i, const T* w, 
 // on level 0 b comes in as the FP64 right-hand side
 template <typename T, int BS>
 __global__ void __launch_bounds__(256) k_ph_first(VLevel<T> L, const double* __restrict__ in) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const T inv_theta = (T)(1.0 / L.cheb[0]);
@@ -135,6 +137,8 @@ __global__ void __launch_bounds__(256) k_ph_first(VLevel<T> L, const double* __r
 template <typename T, int BS>
 __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_step(VLevel<T> L, int dc, int rc, int xc, T c1, T c2,
                                                                  double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ T part[RowCta<BS>::G * BS];
   __shared__ T q[BS], w[BS];
   const int i = blockIdx.x, t = threadIdx.x;
@@ -157,6 +161,8 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_step(VLevel<T> L, i
 // residual of the pre-smoothed iterate on row blockIdx.x: s = r - A d, into the free r buffer
 template <typename T, int BS>
 __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_residual(VLevel<T> L, int dc, int rc) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ T part[RowCta<BS>::G * BS];
   __shared__ T q[BS];
   const int i = blockIdx.x, t = threadIdx.x;
@@ -170,6 +176,8 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_residual(VLevel<T> 
 // restriction b_c[a] = sum_{i in a} Q_i^T s_i (one warp per aggregate, lane s < 16)
 template <typename T, int BS>
 __global__ void __launch_bounds__(256) k_ph_restrict(VLevel<T> L, VLevel<T> C, const T* __restrict__ res) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (a >= C.n || lane >= 16) return;
@@ -186,6 +194,8 @@ __global__ void __launch_bounds__(256) k_ph_restrict(VLevel<T> L, VLevel<T> C, c
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_ph_coarsest(VLevel<T> C) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   for (int row = gw; row < C.N; row += nw) {
@@ -200,6 +210,8 @@ __global__ void __launch_bounds__(256) k_ph_coarsest(VLevel<T> C) {
 // x_i += Q_i x_c[agg(i)]
 template <typename T>
 __global__ void __launch_bounds__(256) k_ph_prolong(VLevel<T> L, VLevel<T> C, int xl, int xcl) {
+  pdl_wait();
+  pdl_trigger();
   const int bs = L.bs;
   T* x = L.x[xl];
   const T* xc = C.x[xcl];
@@ -218,6 +230,8 @@ __global__ void __launch_bounds__(256) k_ph_prolong(VLevel<T> L, VLevel<T> C, in
 template <typename T, int BS>
 __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first(VLevel<T> L, int xc, int rc, int dc,
                                                                        double* __restrict__ out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ T part[RowCta<BS>::G * BS];
   __shared__ T q[BS], w[BS];
   const int i = blockIdx.x, t = threadIdx.x;
@@ -291,57 +305,49 @@ static void run(ba_problem* P, const double* r, double* z) {
   for (int l = 0; l + 1 < nl; ++l) {
     const VLevel<T>& L = V[l];
     const int g = warps_grid(L.n);
-    if (L.bs == 9) k_ph_first<T, 9><<<g, kPhaseBS, 0, st>>>(L, l == 0 ? r : nullptr);
-    else k_ph_first<T, 16><<<g, kPhaseBS, 0, st>>>(L, l == 0 ? r : nullptr);
-    launched(P);
+    if (L.bs == 9) launch_k(P, k_ph_first<T, 9>, g, kPhaseBS, 0, L, l == 0 ? r : nullptr);
+    else launch_k(P, k_ph_first<T, 16>, g, kPhaseBS, 0, L, l == 0 ? r : nullptr);
     for (int k = 1; k < pre; ++k) {
       double c1, c2;
       cheb_coeffs(P->levels[l], k, c1, c2);
       if (L.bs == 9)
-        k_ph_step<T, 9><<<L.n, RowCta<9>::kThreads, 0, st>>>(L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2,
+        launch_k(P, k_ph_step<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2,
                                                              nullptr);
       else
-        k_ph_step<T, 16><<<L.n, RowCta<16>::kThreads, 0, st>>>(L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1,
+        launch_k(P, k_ph_step<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1,
                                                                (T)c2, nullptr);
-      launched(P);
       rm ^= 1u << l;
       dm ^= 1u << l;
     }
-    if (L.bs == 9) k_ph_residual<T, 9><<<L.n, RowCta<9>::kThreads, 0, st>>>(L, bit(dm, l), bit(rm, l));
-    else k_ph_residual<T, 16><<<L.n, RowCta<16>::kThreads, 0, st>>>(L, bit(dm, l), bit(rm, l));
-    launched(P);
+    if (L.bs == 9) launch_k(P, k_ph_residual<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(dm, l), bit(rm, l));
+    else launch_k(P, k_ph_residual<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(dm, l), bit(rm, l));
     const T* res = L.r[1 - bit(rm, l)];
     const int gc = warps_grid(V[l + 1].n);
-    if (L.bs == 9) k_ph_restrict<T, 9><<<gc, kPhaseBS, 0, st>>>(L, V[l + 1], res);
-    else k_ph_restrict<T, 16><<<gc, kPhaseBS, 0, st>>>(L, V[l + 1], res);
-    launched(P);
+    if (L.bs == 9) launch_k(P, k_ph_restrict<T, 9>, gc, kPhaseBS, 0, L, V[l + 1], res);
+    else launch_k(P, k_ph_restrict<T, 16>, gc, kPhaseBS, 0, L, V[l + 1], res);
   }
-  k_ph_coarsest<T><<<warps_grid(V[nl - 1].N), kPhaseBS, 0, st>>>(V[nl - 1]);
-  launched(P);
+  launch_k(P, k_ph_coarsest<T>, warps_grid(V[nl - 1].N), kPhaseBS, 0, V[nl - 1]);
   for (int l = nl - 2; l >= 0; --l) {
     const VLevel<T>& L = V[l];
     const int g = warps_grid(L.n);
-    k_ph_prolong<T><<<cdiv((long long)L.n * L.bs, kPhaseBS), kPhaseBS, 0, st>>>(L, V[l + 1], bit(xm, l),
+    launch_k(P, k_ph_prolong<T>, cdiv((long long)L.n * L.bs, kPhaseBS), kPhaseBS, 0, L, V[l + 1], bit(xm, l),
                                                                                bit(xm, l + 1));
-    launched(P);
     double* o = (l == 0 && post == 1) ? z : nullptr;
     if (L.bs == 9)
-      k_ph_post_first<T, 9><<<L.n, RowCta<9>::kThreads, 0, st>>>(L, bit(xm, l), bit(rm, l), bit(dm, l), o);
+      launch_k(P, k_ph_post_first<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(xm, l), bit(rm, l), bit(dm, l), o);
     else
-      k_ph_post_first<T, 16><<<L.n, RowCta<16>::kThreads, 0, st>>>(L, bit(xm, l), bit(rm, l), bit(dm, l), o);
-    launched(P);
+      launch_k(P, k_ph_post_first<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(xm, l), bit(rm, l), bit(dm, l), o);
     xm ^= 1u << l;
     for (int k = 1; k < post; ++k) {
       double c1, c2;
       cheb_coeffs(P->levels[l], k, c1, c2);
       double* ok = (l == 0 && k == post - 1) ? z : nullptr;
       if (L.bs == 9)
-        k_ph_step<T, 9><<<L.n, RowCta<9>::kThreads, 0, st>>>(L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2,
+        launch_k(P, k_ph_step<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2,
                                                              ok);
       else
-        k_ph_step<T, 16><<<L.n, RowCta<16>::kThreads, 0, st>>>(L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1,
+        launch_k(P, k_ph_step<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1,
                                                                (T)c2, ok);
-      launched(P);
       rm ^= 1u << l;
       dm ^= 1u << l;
     }
