@@ -138,6 +138,7 @@ struct ba_problem {
   int k3_grid_df = 0;           // the same for the paired-FP32 product
   bool l0_explicit = false;     // V-cycle level 0 uses the assembled S (set by the multigrid setup)
   bool vc_ready = false;        // the fused-phase V-cycle applies (set by the multigrid setup)
+  ba::DBuf lz_vec, lz_red, lz_cnt, lz_ptr;  // batched Lanczos vectors, reductions, counters, pointers
   unsigned k3_calls = 0;        // alternates the tile order of successive Schur products
   ba::DBuf tile_pt;             // int32 [n_tiles + 1] point ranges of <=32-obs warp tiles
   ba::DBuf tile_desc;           // int4 [n_tiles] {first obs, obs count, first point, start mask}
@@ -268,6 +269,7 @@ void matvec32_accumulate(ba_problem* P, const float* x, float* y);
 bool outer_df(ba_problem* P);                                         // mixed mode, paired-FP32 outer product
 void split_vector(ba_problem* P, const double* x, const double* Dc, double* y);  // xsplit = split(x); y = Dc o x
 void matvec_df_accumulate(ba_problem* P, double* y);                   // y += S x - Dc x from xsplit
+void lanczos_batched(ba_problem* P, int first, int last);  // levels first..last, all assembled
 void fused_vcycle_setup(ba_problem* P);
 void fused_vcycle(ba_problem* P, const double* r, double* z);
 void explicit_schur(ba_problem* P, Level& L0, bool fp32);

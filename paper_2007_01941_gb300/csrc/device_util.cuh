@@ -15,6 +15,14 @@ constexpr unsigned kFull = 0xffffffffu;
 // that kernel has completed and its writes are visible, pdl_trigger() lets the next
 // kernel be scheduled.  Both are no-ops for an ordinary launch.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// SplitMix64 (Steele, Lea & Flood 2014) of counter i: the Lanczos start vector
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long i) {
+  unsigned long long z = 0x9E3779B97F4A7C15ull * (i + 1ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Per-observation Jacobian record: F_o (2 x 9, row-major) then E_o (2 x 3, row-major),

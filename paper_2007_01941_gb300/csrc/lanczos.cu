@@ -1,0 +1,271 @@
+// Lanczos estimate of lambda_max(D^-1 A) in the D-inner product (Section 3.4), for all
+// assembled smoothed levels at once: each kernel of the recurrence covers the block rows
+// of every level (one CTA per block row), and the inner products are per-level
+// deterministic grid reductions written straight into the level's Chebyshev buffer
+// (alpha_j at slot 8 + j, beta_j at slot 16 + j).  The same recurrence, level by level,
+// is the path of mg_setup.cu for an implicit level 0:
+//   q_0 = v / |v|_D;  for j: Aq = A q_j, alpha_j = q_j^T A q_j,
+//   w = D^-1 Aq - alpha_j q_j - beta_{j-1} q_{j-1},  beta_j = |w|_D,  q_{j+1} = w / beta_j.
+// Scalings by 1/|.|_D are applied lazily by the kernel that next reads the vector, so a
+// step is two launches for every level together.
+#include <algorithm>
+
+#include "ba_internal.h"
+#include "device_util.cuh"
+
+namespace ba {
+
+constexpr int kLzMax = 16;
+constexpr int kLzBS = 128;
+
+template <typename T>
+struct LzLevel {
+  int n, bs, row0;   // rows, block size, first CTA of the level in the batched grid
+  const int* row_ptr;
+  const int* cols;
+  const T* vals;
+  const double* D;      // diagonal blocks [n][bs][bs]
+  const double* Dinv;   // their inverses
+  T* v;                 // start vector
+  T* w;                 // unscaled next direction
+  T* q[2];              // current / previous direction (by step parity)
+  T* Aq;
+  double* cheb;         // level buffer: [8 + j] alpha_j, [16 + j] beta_j
+  double* s;            // [0] |v|_D^2, [1 + j] |w_j|_D^2
+  double* partial;      // one slot per row
+  unsigned* counter;
+};
+
+template <typename T>
+struct LzArgs {
+  int nl;
+  LzLevel<T> L[kLzMax];
+};
+
+__device__ __forceinline__ int lz_level(const int* row0, int nl, int b) {
+  int l = 0;
+  while (l + 1 < nl && row0[l + 1] <= b) ++l;
+  return l;
+}
+
+// CTA-wide sum of one value per thread (result valid in thread 0)
+__device__ __forceinline__ double lz_block_sum(double v) {
+  __shared__ double red[kLzBS / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kLzBS / 32; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// deterministic per-level sum: every CTA of the level stores its partial (thread 0's
+// v), the last CTA to arrive adds them in a fixed order
+__device__ __forceinline__ void lz_reduce(double v, double* partial, unsigned* counter, int n, int row,
+                                          double* out) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partial[row] = v;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == (unsigned)(n - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += kLzBS) s += ((volatile double*)partial)[i];
+    s = lz_block_sum(s);
+    if (threadIdx.x == 0) {
+      *out = s;
+      *counter = 0u;
+    }
+  }
+}
+
+// y_i = B_i x_i for one block row (B double blocks); thread u < bs returns component u
+template <typename T>
+__device__ __forceinline__ double lz_block_row(const double* __restrict__ B, int bs, int i, const T* x) {
+  const int u = threadIdx.x;
+  if (u >= bs) return 0.0;
+  const double* b = B + ((size_t)i * bs + u) * bs;
+  const T* xi = x + (size_t)i * bs;
+  double acc = 0.0;
+  for (int c = 0; c < bs; ++c) acc += b[c] * (double)xi[c];
+  return acc;
+}
+
+// v = start vector (SplitMix64 of the level-local index, mapped to [-1, 1)); s[0] = v^T D v
+template <typename T>
+__global__ void __launch_bounds__(kLzBS) k_lz_init(LzArgs<T> A) {
+  pdl_wait();
+  pdl_trigger();
+  int row0[kLzMax];
+  for (int l = 0; l < A.nl; ++l) row0[l] = A.L[l].row0;
+  const int l = lz_level(row0, A.nl, blockIdx.x);
+  const LzLevel<T>& L = A.L[l];
+  const int i = blockIdx.x - L.row0, bs = L.bs, u = threadIdx.x;
+  if (u < bs) {
+    const size_t idx = (size_t)i * bs + u;
+    L.v[idx] = (T)(2.0 * ((double)(splitmix64(idx) >> 11) * 0x1.0p-53) - 1.0);
+  }
+  __syncthreads();
+  const double dv = lz_block_row(L.D, bs, i, L.v);
+  const double part = lz_block_sum(u < bs ? dv * (double)L.v[(size_t)i * bs + u] : 0.0);
+  lz_reduce(part, L.partial, L.counter, L.n, i, L.s);
+}
+
+// step j: q_j = src / sqrt(s[j]) (src = v for j = 0, w otherwise); Aq = A q_j; alpha_j
+template <typename T>
+__global__ void __launch_bounds__(kLzBS) k_lz_product(LzArgs<T> A, int j) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double part_sm[kLzBS];
+  int row0[kLzMax];
+  for (int l = 0; l < A.nl; ++l) row0[l] = A.L[l].row0;
+  const int l = lz_level(row0, A.nl, blockIdx.x);
+  const LzLevel<T>& L = A.L[l];
+  const int i = blockIdx.x - L.row0, bs = L.bs, t = threadIdx.x;
+  const T* src = j == 0 ? L.v : L.w;
+  const double scale = 1.0 / sqrt(L.s[j]);
+  // threads split the row's blocks: G groups of bs threads
+  const int G = kLzBS / bs;
+  const int u = t % bs, h = t / bs;
+  double acc = 0.0;
+  if (h < G) {
+    const int e1 = L.row_ptr[i + 1];
+    for (int e = L.row_ptr[i] + h; e < e1; e += G) {
+      const T* a = L.vals + (size_t)e * bs * bs + u * bs;
+      const T* xv = src + (size_t)L.cols[e] * bs;
+      for (int c = 0; c < bs; ++c) acc += (double)a[c] * (double)xv[c];
+    }
+  }
+  part_sm[t] = h < G ? acc : 0.0;
+  __syncthreads();
+  double contrib = 0.0;
+  if (t < bs) {
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += part_sm[g * bs + t];
+    const size_t idx = (size_t)i * bs + t;
+    const double aq = s * scale;
+    const double qv = (double)src[idx] * scale;
+    L.Aq[idx] = (T)aq;
+    L.q[j & 1][idx] = (T)qv;
+    contrib = qv * aq;
+  }
+  const double part = lz_block_sum(contrib);
+  lz_reduce(part, L.partial, L.counter, L.n, i, L.cheb + 8 + j);
+}
+
+// w = D^-1 Aq - alpha_j q_j - beta_{j-1} q_{j-1}; s[j + 1] = w^T D w; beta_j = sqrt(s[j + 1])
+template <typename T>
+__global__ void __launch_bounds__(kLzBS) k_lz_direction(LzArgs<T> A, int j) {
+  pdl_wait();
+  pdl_trigger();
+  int row0[kLzMax];
+  for (int l = 0; l < A.nl; ++l) row0[l] = A.L[l].row0;
+  const int l = lz_level(row0, A.nl, blockIdx.x);
+  const LzLevel<T>& L = A.L[l];
+  const int i = blockIdx.x - L.row0, bs = L.bs, u = threadIdx.x;
+  const double alpha = L.cheb[8 + j];
+  const double beta = j > 0 ? sqrt(L.s[j]) : 0.0;   // beta_{j-1} = |w_{j-1}|_D
+  double wv = lz_block_row(L.Dinv, bs, i, L.Aq);
+  if (u < bs) {
+    const size_t idx = (size_t)i * bs + u;
+    wv -= alpha * (double)L.q[j & 1][idx];
+    if (j > 0) wv -= beta * (double)L.q[(j + 1) & 1][idx];
+    L.w[idx] = (T)wv;
+  }
+  __syncthreads();
+  const double dw = lz_block_row(L.D, bs, i, L.w);
+  const double part = lz_block_sum(u < bs ? dw * (double)L.w[(size_t)i * bs + u] : 0.0);
+  lz_reduce(part, L.partial, L.counter, L.n, i, L.s + 1 + j);   // beta_j^2
+}
+
+__global__ void k_lz_betas(double* const* cheb, double* const* s, int nl, int m) {
+  const int l = threadIdx.x;
+  if (l >= nl) return;
+  for (int j = 0; j + 1 < m; ++j) cheb[l][16 + j] = sqrt(s[l][1 + j]);
+}
+
+bool level_fp32(ba_problem* P);
+
+// Lanczos for levels [first, last] of the hierarchy, all assembled.
+template <typename T>
+static void run(ba_problem* P, int first, int last) {
+  const int nl = last - first + 1;
+  const int m = std::min(std::max(P->opt.lanczos_steps, 1), 8);
+  LzArgs<T> A{};
+  A.nl = nl;
+  size_t vec = 0;
+  int rows = 0;
+  for (int k = 0; k < nl; ++k) {
+    Level& L = P->levels[first + k];
+    vec += (size_t)L.n * L.bs + 32;
+    rows += L.n;
+  }
+  P->lz_vec.ensure(sizeof(T) * vec * 5 + 256);
+  P->lz_red.ensure(sizeof(double) * ((size_t)rows + 16 * (size_t)nl) + 256);
+  P->lz_cnt.ensure(sizeof(unsigned) * (size_t)nl + 64);
+  BA_CUDA(cudaMemsetAsync(P->lz_cnt.p, 0, sizeof(unsigned) * nl, P->stream));
+  T* vb = P->lz_vec.as<T>();
+  double* red = P->lz_red.as<double>();
+  double* sbase = red + rows;
+  int row0 = 0;
+  for (int k = 0; k < nl; ++k) {
+    Level& L = P->levels[first + k];
+    L.cheb.ensure(sizeof(double) * kChebSlots);
+    const size_t n = (size_t)L.n * L.bs;
+    LzLevel<T>& d = A.L[k];
+    d.n = L.n;
+    d.bs = L.bs;
+    d.row0 = row0;
+    d.row_ptr = L.row_ptr.as<int>();
+    d.cols = L.cols.as<int>();
+    d.vals = sizeof(T) == 4 ? (const T*)L.vals32.p : (const T*)L.vals64.p;
+    d.D = L.Dblk.as<double>();
+    d.Dinv = L.Dinv64.as<double>();
+    d.v = vb;
+    d.w = vb + n;
+    d.q[0] = vb + 2 * n;
+    d.q[1] = vb + 3 * n;
+    d.Aq = vb + 4 * n;
+    vb += 5 * n + 32;
+    d.cheb = L.cheb.as<double>();
+    d.s = sbase + 16 * k;
+    d.partial = red + row0;
+    d.counter = P->lz_cnt.as<unsigned>() + k;
+    row0 += L.n;
+  }
+  // zero the alpha / beta slots so that unused ones read as 0
+  for (int k = 0; k < nl; ++k)
+    BA_CUDA(cudaMemsetAsync(A.L[k].cheb + 8, 0, sizeof(double) * 16, P->stream));
+  launch_k(P, k_lz_init<T>, rows, kLzBS, 0, A);
+  for (int j = 0; j < m; ++j) {
+    launch_k(P, k_lz_product<T>, rows, kLzBS, 0, A, j);
+    if (j == m - 1) break;
+    launch_k(P, k_lz_direction<T>, rows, kLzBS, 0, A, j);
+  }
+  // beta_j = sqrt(s[j + 1])
+  std::vector<double*> hc(nl), hs(nl);
+  for (int k = 0; k < nl; ++k) {
+    hc[k] = A.L[k].cheb;
+    hs[k] = A.L[k].s;
+  }
+  P->lz_ptr.ensure(sizeof(double*) * 2 * (size_t)nl + 64);
+  BA_CUDA(cudaMemcpyAsync(P->lz_ptr.p, hc.data(), sizeof(double*) * nl, cudaMemcpyHostToDevice, P->stream));
+  BA_CUDA(cudaMemcpyAsync((double**)P->lz_ptr.p + nl, hs.data(), sizeof(double*) * nl, cudaMemcpyHostToDevice,
+                          P->stream));
+  launch_k(P, k_lz_betas, 1, 32, 0, (double* const*)P->lz_ptr.p, (double* const*)((double**)P->lz_ptr.p + nl), nl,
+           m);
+}
+
+void lanczos_batched(ba_problem* P, int first, int last) {
+  if (last < first) return;
+  BA_REQUIRE(last - first + 1 <= kLzMax, BA_ERR_LIMIT, "too many levels for the batched Lanczos");
+  if (level_fp32(P)) run<float>(P, first, last);
+  else run<double>(P, first, last);
+}
+
+}  // namespace ba

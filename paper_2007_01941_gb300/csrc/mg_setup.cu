@@ -476,17 +476,23 @@ constexpr int kQrStride = kNull + 1;
 constexpr int kQrBS = 128;
 constexpr int kQrWarps = kQrBS / 32;
 
-// sum over the CTA of v (one value per thread); result in every thread
-__device__ __forceinline__ double qr_block_sum1(double v, double* red) {
+// sqrt of the sum over the CTA of v (one value per thread); result in every thread.
+// The square root runs once (thread 0): FP64 square roots and divisions are long
+// sequences on this GPU's narrow FP64 unit, which all CTAs of an SM share.
+__device__ __forceinline__ double qr_block_norm(double v, double* red) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
-  double s = 0.0;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
 #pragma unroll
-  for (int w = 0; w < kQrWarps; ++w) s += red[w];
-  return s;
+    for (int w = 0; w < kQrWarps; ++w) s += red[w];
+    red[kQrWarps * kNull] = sqrt(s);
+  }
+  __syncthreads();
+  return red[kQrWarps * kNull];
 }
 
 // sums over the CTA of p[0..15] (16 values per thread); h[0..15] in shared memory on
@@ -525,7 +531,7 @@ k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, const int* __res
                double* __restrict__ Kc, unsigned* __restrict__ kept_out) {
   extern __shared__ __align__(16) unsigned char qsm[];
   double* A = reinterpret_cast<double*>(qsm);  // [rows][kQrStride]
-  __shared__ double red[kQrWarps * kNull];
+  __shared__ double red[kQrWarps * kNull + 2];
   __shared__ double h[kNull];
   __shared__ double Rs[kNull][kNull + 1];
   const int a = blockIdx.x;
@@ -543,7 +549,7 @@ k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, const int* __res
   for (int j = 0; j < kNull; ++j) {
     double n2 = 0.0;
     for (int r = t; r < rows; r += kQrBS) n2 += A[r * kQrStride + j] * A[r * kQrStride + j];
-    const double n0 = sqrt(qr_block_sum1(n2, red));
+    const double n0 = qr_block_norm(n2, red);
     double rc[kNull];
 #pragma unroll
     for (int i = 0; i < kNull; ++i) rc[i] = 0.0;
@@ -574,9 +580,11 @@ k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, const int* __res
     }
     double v2 = 0.0;
     for (int r = t; r < rows; r += kQrBS) v2 += A[r * kQrStride + j] * A[r * kQrStride + j];
-    const double nv = sqrt(qr_block_sum1(v2, red));
+    const double nv = qr_block_norm(v2, red);
     const bool keep = n0 > 0.0 && nv > 1e-10 * n0;
-    const double scale = keep ? 1.0 / nv : 0.0;
+    if (threadIdx.x == 0) red[kQrWarps * kNull + 1] = keep ? 1.0 / nv : 0.0;
+    __syncthreads();
+    const double scale = red[kQrWarps * kNull + 1];
     for (int r = t; r < rows; r += kQrBS) A[r * kQrStride + j] *= scale;
     if (keep) {
       rc[j] = nv;
@@ -675,12 +683,6 @@ __global__ void k_extract_diag(int n, int bs, const int* __restrict__ row_ptr, c
 // Lanczos helpers (D-inner product): start vector from SplitMix64, block-diagonal
 // products, recurrence updates with scalars read from device memory.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long i) {
-  unsigned long long z = 0x9E3779B97F4A7C15ull * (i + 1ull);
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
 
 template <typename T>
 __global__ void k_start_vector(T* __restrict__ v, size_t n) {
@@ -955,6 +957,8 @@ __global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* __restrict__ A, 
                                                         int* flags) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double piv[kGJ][kGJ + 1];
+  __shared__ double gj_row[kGJ], gj_col[kGJ];
+  __shared__ double gj_ip;
   __shared__ double sa[kGJRows][kGJ + 1];
   __shared__ double sb[kGJ][kGJ + 1];
   constexpr int kPer = kGJRows * kGJ / kGJBS;   // outputs per thread in a work item
@@ -968,31 +972,35 @@ __global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* __restrict__ A, 
       pcol[idx] = A[(size_t)r * Np + K0 + c];
     }
     if (blockIdx.x == 0) {
+      // in place: each step reads its own element plus the pivot row (scaled) and the
+      // pivot column (old values) from shared copies; the reciprocal is formed once
       for (int e = t; e < kGJ * kGJ; e += kGJBS) piv[e / kGJ][e % kGJ] = A[(size_t)(K0 + e / kGJ) * Np + K0 + e % kGJ];
       __syncthreads();
       bool bad = false;
       for (int k = 0; k < kGJ; ++k) {
-        const double pk = piv[k][k];
-        if (!(pk > 0.0)) bad = true;
-        const double ip = 1.0 / pk;
+        if (t == 0) {
+          const double pk = piv[k][k];
+          if (!(pk > 0.0)) bad = true;
+          gj_ip = 1.0 / pk;
+        }
         __syncthreads();
-        double newv[kGJ * kGJ / kGJBS];
-        int cnt = 0;
+        const double ip = gj_ip;
+        if (t < kGJ) {
+          gj_row[t] = t == k ? ip : piv[k][t] * ip;
+          gj_col[t] = piv[t][k];
+        }
+        __syncthreads();
         for (int e = t; e < kGJ * kGJ; e += kGJBS) {
           const int i = e / kGJ, j = e % kGJ;
           double v;
-          if (i == k && j == k) v = ip;
-          else if (i == k) v = piv[k][j] * ip;
-          else if (j == k) v = -piv[i][k] * ip;
-          else v = piv[i][j] - piv[i][k] * (piv[k][j] * ip);
-          newv[cnt++] = v;
+          if (i == k) v = gj_row[j];
+          else if (j == k) v = -gj_col[i] * ip;
+          else v = piv[i][j] - gj_col[i] * gj_row[j];
+          piv[i][j] = v;
         }
         __syncthreads();
-        cnt = 0;
-        for (int e = t; e < kGJ * kGJ; e += kGJBS) piv[e / kGJ][e % kGJ] = newv[cnt++];
       }
-      __syncthreads();
-      if (bad && t == 0) flags[F_NOT_SPD_COARSE] = 1;
+      if (bad) flags[F_NOT_SPD_COARSE] = 1;
       for (int e = t; e < kGJ * kGJ; e += kGJBS) pinv[e] = piv[e / kGJ][e % kGJ];
     }
     grid.sync();
@@ -1237,8 +1245,11 @@ void mg_setup(ba_problem* P) {
       launched(P);
       block_inverse(P, L.Dblk.as<double>(), L.n, L.bs, L.Dinv64.as<double>(), L.Dinv32.as<float>(), F_NOT_SPD_JACOBI);
     }
-    if (fp32) lanczos<float>(P, l);
-    else lanczos<double>(P, l);
+    // assembled levels get their Lanczos estimate in one batch after the loop
+    if (l == 0 && !P->l0_explicit) {
+      if (fp32) lanczos<float>(P, l);
+      else lanczos<double>(P, l);
+    }
     Level& L1 = P->levels[l + 1];
     // QR prolongators, coarse nullspace and kept masks
     L.Q64.ensure(sizeof(double) * L.bs * kNull * (size_t)L.n + 64);
@@ -1270,6 +1281,7 @@ void mg_setup(ba_problem* P) {
     }
     launched(P);
   }
+  lanczos_batched(P, P->l0_explicit ? 0 : 1, P->n_levels - 2);
   finish_lanczos(P);
   check_flags(P);
   // V-cycle work vectors
