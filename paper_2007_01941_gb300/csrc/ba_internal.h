@@ -99,6 +99,7 @@ struct Level {
   int n_strength = 0;
   DBuf agg;                     // int32 [n] aggregate (= next-level node) of each node
   int n_agg = 0;
+  int agg_max = 1;              // members of the largest aggregate
   DBuf agg_ptr, agg_mem;        // member lists of the next-level nodes
   DBuf K;                       // double [n][bs][16] near-nullspace rows
   DBuf Q64, Q32;                // double/float [n][bs][16] prolongator blocks

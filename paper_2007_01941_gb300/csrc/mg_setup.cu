@@ -464,17 +464,130 @@ __global__ void k_nullspace0(const double* __restrict__ cams, int n_c, double* _
 // ---------------------------------------------------------------------------
 // per-aggregate thin QR (Section 3.3) by Gram-Schmidt with one re-orthogonalisation
 // pass; a column whose remaining norm is <= 1e-10 of its original norm is dropped
-// (zero Q column, zero R row).  One CTA of kQrBS threads per aggregate, rows spread
-// over the threads.  Each pass projects column j on all earlier columns at once
-// (classical Gram-Schmidt: the j inner products come out of one block reduction, so
-// the dependency chain per column is two reductions long instead of 2j); with the
-// second pass this is as accurate as the modified variant with re-orthogonalisation.
+// (zero Q column, zero R row).  One warp per aggregate (four per CTA), rows spread over
+// the lanes.  Each pass projects column j on all earlier columns at once (classical
+// Gram-Schmidt: the j inner products come out of one 16-value warp reduction, so the
+// dependency chain per column is two reductions long instead of 2j); with the second
+// pass this is as accurate as the modified variant with re-orthogonalisation.  FP64
+// throughput per SM is what limits this kernel, so no warp works on an empty share.
 // ---------------------------------------------------------------------------
 // row stride of the aggregate matrix in shared memory: 17 doubles, so the rows that
 // consecutive threads touch fall in different banks
 constexpr int kQrStride = kNull + 1;
+
+// sums over the warp of p[0..15] (16 values per lane), into every lane's h[0..15]: each
+// step halves the values a lane carries (it keeps one half and adds its partner's copy
+// of that half), so the 16 sums take 15 shuffles; 16 more broadcast them.
+__device__ __forceinline__ void qr_warp_sum16(double p[kNull], double h[kNull], int lane) {
+#pragma unroll
+  for (int half = 8, off = 16; half >= 1; half >>= 1, off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const double send = up ? p[k] : p[k + half];
+      const double keep = up ? p[k + half] : p[k];
+      p[k] = keep + __shfl_xor_sync(kFull, send, off);
+    }
+  }
+  // p[0] holds the partial of index idx(lane); lanes l and l ^ 1 hold the same index
+  const double v = p[0] + __shfl_xor_sync(kFull, p[0], 1);
+#pragma unroll
+  for (int i = 0; i < kNull; ++i) {
+    // lane holding index i: bits 4..1 of the lane are the bits 3..0 of i
+    const int src = ((i >> 3) & 1) << 4 | ((i >> 2) & 1) << 3 | ((i >> 1) & 1) << 2 | (i & 1) << 1;
+    h[i] = __shfl_sync(kFull, v, src);
+  }
+}
+
+constexpr int kQrWarps = 4;   // aggregates per CTA (one warp each)
+
+__global__ void __launch_bounds__(kQrWarps * 32)
+k_aggregate_qr(int n_agg, int bs, int max_rows, const int* __restrict__ mptr, const int* __restrict__ mem,
+               const double* __restrict__ K, double* __restrict__ Q64, float* __restrict__ Q32,
+               double* __restrict__ Kc, unsigned* __restrict__ kept_out) {
+  extern __shared__ __align__(16) unsigned char qsm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int a = blockIdx.x * kQrWarps + warp;
+  if (a >= n_agg) return;
+  double* A = reinterpret_cast<double*>(qsm) + (size_t)warp * max_rows * kQrStride;  // [rows][kQrStride]
+  const int mb = mptr[a], me = mptr[a + 1];
+  const int rows = (me - mb) * bs;
+  for (int e = lane; e < rows * kNull; e += 32) {
+    const int r = e / kNull, j = e - r * kNull;
+    const int s = r / bs, u = r - s * bs;
+    A[r * kQrStride + j] = K[((size_t)mem[mb + s] * bs + u) * kNull + j];
+  }
+  __shared__ double Rs[kQrWarps][kNull][kNull + 1];
+  double(*R)[kNull + 1] = Rs[warp];
+  for (int e = lane; e < kNull * kNull; e += 32) R[e / kNull][e % kNull] = 0.0;
+  __syncwarp();
+  unsigned kept = 0;
+  for (int j = 0; j < kNull; ++j) {
+    double n2 = 0.0;
+    for (int r = lane; r < rows; r += 32) n2 += A[r * kQrStride + j] * A[r * kQrStride + j];
+    const double n0 = sqrt(warp_sum(n2));
+    double rc[kNull];
+#pragma unroll
+    for (int i = 0; i < kNull; ++i) rc[i] = 0.0;
+    if (j > 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        double p[kNull], h[kNull];
+#pragma unroll
+        for (int i = 0; i < kNull; ++i) p[i] = 0.0;
+        for (int r = lane; r < rows; r += 32) {
+          const double aj = A[r * kQrStride + j];
+#pragma unroll
+          for (int i = 0; i < kNull; ++i)
+            if (i < j) p[i] += A[r * kQrStride + i] * aj;
+        }
+        qr_warp_sum16(p, h, lane);
+        for (int r = lane; r < rows; r += 32) {
+          double aj = A[r * kQrStride + j];
+#pragma unroll
+          for (int i = 0; i < kNull; ++i)
+            if (i < j) aj -= h[i] * A[r * kQrStride + i];
+          A[r * kQrStride + j] = aj;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < kNull; ++i)
+          if (i < j) rc[i] += h[i];
+      }
+    }
+    double v2 = 0.0;
+    for (int r = lane; r < rows; r += 32) v2 += A[r * kQrStride + j] * A[r * kQrStride + j];
+    const double nv = sqrt(warp_sum(v2));
+    const bool keep = n0 > 0.0 && nv > 1e-10 * n0;
+    const double scale = keep ? 1.0 / nv : 0.0;
+    for (int r = lane; r < rows; r += 32) A[r * kQrStride + j] *= scale;
+    __syncwarp();
+    if (keep) kept |= 1u << j;
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < kNull; ++i)
+        if (i < j) R[i][j] = rc[i];
+      R[j][j] = keep ? nv : 0.0;
+    }
+  }
+  __syncwarp();
+  // Q blocks back to the member nodes
+  for (int e = lane; e < rows * kNull; e += 32) {
+    const int r = e / kNull, j = e - r * kNull;
+    const int s = r / bs, u = r - s * bs;
+    const size_t dst = ((size_t)mem[mb + s] * bs + u) * kNull + j;
+    const double q = A[r * kQrStride + j];
+    Q64[dst] = q;
+    Q32[dst] = (float)q;
+  }
+  for (int e = lane; e < kNull * kNull; e += 32) Kc[(size_t)a * kNull * kNull + e] = R[e / kNull][e % kNull];
+  if (lane == 0) kept_out[a] = kept;
+}
+
+// The same factorisation with one CTA of kQrBS threads per aggregate, rows spread over
+// the threads: shorter dependency chains for the few large aggregates of the coarse
+// levels, where there are too few aggregates to fill the GPU with warps.
 constexpr int kQrBS = 128;
-constexpr int kQrWarps = kQrBS / 32;
+constexpr int kQrCtaWarps = kQrBS / 32;
 
 // sqrt of the sum over the CTA of v (one value per thread); result in every thread.
 // The square root runs once (thread 0): FP64 square roots and divisions are long
@@ -488,17 +601,17 @@ __device__ __forceinline__ double qr_block_norm(double v, double* red) {
   if (threadIdx.x == 0) {
     double s = 0.0;
 #pragma unroll
-    for (int w = 0; w < kQrWarps; ++w) s += red[w];
-    red[kQrWarps * kNull] = sqrt(s);
+    for (int w = 0; w < kQrCtaWarps; ++w) s += red[w];
+    red[kQrCtaWarps * kNull] = sqrt(s);
   }
   __syncthreads();
-  return red[kQrWarps * kNull];
+  return red[kQrCtaWarps * kNull];
 }
 
 // sums over the CTA of p[0..15] (16 values per thread); h[0..15] in shared memory on
 // return.  Within a warp, each step halves the values a lane carries (it keeps one half
 // and adds its partner's copy of that half), so the 16 sums take 15 shuffles.
-__device__ __forceinline__ void qr_block_sum16(double p[kNull], double* red /*[kQrWarps][16]*/, double* h) {
+__device__ __forceinline__ void qr_block_sum16(double p[kNull], double* red /*[kQrCtaWarps][16]*/, double* h) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int half = 8, off = 16; half >= 1; half >>= 1, off >>= 1) {
@@ -519,19 +632,19 @@ __device__ __forceinline__ void qr_block_sum16(double p[kNull], double* red /*[k
   if (threadIdx.x < kNull) {
     double s = 0.0;
 #pragma unroll
-    for (int w = 0; w < kQrWarps; ++w) s += red[w * kNull + threadIdx.x];
+    for (int w = 0; w < kQrCtaWarps; ++w) s += red[w * kNull + threadIdx.x];
     h[threadIdx.x] = s;
   }
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(kQrBS)
-k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, const int* __restrict__ mem,
+k_aggregate_qr_cta(int n_agg, int bs, const int* __restrict__ mptr, const int* __restrict__ mem,
                const double* __restrict__ K, double* __restrict__ Q64, float* __restrict__ Q32,
                double* __restrict__ Kc, unsigned* __restrict__ kept_out) {
   extern __shared__ __align__(16) unsigned char qsm[];
   double* A = reinterpret_cast<double*>(qsm);  // [rows][kQrStride]
-  __shared__ double red[kQrWarps * kNull + 2];
+  __shared__ double red[kQrCtaWarps * kNull + 2];
   __shared__ double h[kNull];
   __shared__ double Rs[kNull][kNull + 1];
   const int a = blockIdx.x;
@@ -582,16 +695,17 @@ k_aggregate_qr(int n_agg, int bs, const int* __restrict__ mptr, const int* __res
     for (int r = t; r < rows; r += kQrBS) v2 += A[r * kQrStride + j] * A[r * kQrStride + j];
     const double nv = qr_block_norm(v2, red);
     const bool keep = n0 > 0.0 && nv > 1e-10 * n0;
-    if (threadIdx.x == 0) red[kQrWarps * kNull + 1] = keep ? 1.0 / nv : 0.0;
+    if (threadIdx.x == 0) red[kQrCtaWarps * kNull + 1] = keep ? 1.0 / nv : 0.0;
     __syncthreads();
-    const double scale = red[kQrWarps * kNull + 1];
+    const double scale = red[kQrCtaWarps * kNull + 1];
     for (int r = t; r < rows; r += kQrBS) A[r * kQrStride + j] *= scale;
-    if (keep) {
-      rc[j] = nv;
-      kept |= 1u << j;
+    if (keep) kept |= 1u << j;
+    if (t == 0) {
+#pragma unroll
+      for (int i = 0; i < kNull; ++i)
+        if (i < j) Rs[i][j] = rc[i];
+      Rs[j][j] = keep ? nv : 0.0;
     }
-    if (t == 0)
-      for (int i = 0; i < kNull; ++i) Rs[i][j] = rc[i];
     __syncthreads();
   }
   // Q blocks back to the member nodes
@@ -922,16 +1036,17 @@ __global__ void k_dense_identity_pad(int N, int Np, double* __restrict__ A) {
   if (i >= N || j >= N) A[idx] = (i == j) ? 1.0 : 0.0;
 }
 
-constexpr int kGJ = 32;
+constexpr int kGJ = 16;   // pivot block: its inversion is the serial part of every step
 constexpr int kGJBS = 256;
 // Per pivot block K (kGJ wide):
 //   phase 1: CTA 0 inverts P = A_KK in shared memory (Gauss-Jordan, SPD, no pivoting) into
 //            pinv; every CTA copies the column panel A_IK into pcol;
 //   phase 2: new row panel prow_J = P^-1 A_KJ (J != K), prow_K = P^-1;
 //   phase 3: A_IJ <- A_IJ - A_IK prow_J and A_IK <- -A_IK P^-1 (I != K), A_KJ <- prow_J.
-// Products are split into work items of kGJ/4 rows of one tile; grid-wide syncs
-// separate the phases, and no phase writes a tile that it also reads.
-constexpr int kGJRows = kGJ / 4;
+// Work items are whole tiles (kGJSplit pieces each); grid-wide syncs separate the
+// phases, and no phase writes a tile that it also reads.
+constexpr int kGJSplit = 1;                 // work items per tile
+constexpr int kGJRows = kGJ / kGJSplit;
 
 // out (kGJRows x kGJ rows r0.. of the tile) = a (rows r0.. of an kGJ x kGJ tile, ld_a) * b (kGJ x kGJ, ld_b)
 __device__ __forceinline__ void gj_rows_product(const double* __restrict__ a, size_t ld_a, const double* __restrict__ b,
@@ -1005,8 +1120,8 @@ __global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* __restrict__ A, 
     }
     grid.sync();
     // phase 2: work items (J, row quarter) of the row panel
-    for (int w = blockIdx.x; w < nb * 4; w += gridDim.x) {
-      const int J = w >> 2, r0 = (w & 3) * kGJRows;
+    for (int w = blockIdx.x; w < nb * kGJSplit; w += gridDim.x) {
+      const int J = w / kGJSplit, r0 = (w % kGJSplit) * kGJRows;
       double acc[kPer];
       if (J == K) {
         for (int q = 0; q < kPer; ++q) {
@@ -1023,10 +1138,10 @@ __global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* __restrict__ A, 
     }
     grid.sync();
     // phase 3: work items (I, J, row quarter)
-    for (int w = blockIdx.x; w < nb * nb * 4; w += gridDim.x) {
-      const int I = w / (nb * 4);
-      const int rem = w - I * nb * 4;
-      const int J = rem >> 2, r0 = (rem & 3) * kGJRows;
+    for (int w = blockIdx.x; w < nb * nb * kGJSplit; w += gridDim.x) {
+      const int I = w / (nb * kGJSplit);
+      const int rem = w - I * nb * kGJSplit;
+      const int J = rem / kGJSplit, r0 = (rem % kGJSplit) * kGJRows;
       if (I == K) {
         for (int e = t; e < kGJRows * kGJ; e += kGJBS)
           A[(size_t)(K0 + r0 + e / kGJ) * Np + J * kGJ + e % kGJ] = prow[(size_t)(r0 + e / kGJ) * Np + J * kGJ + e % kGJ];
@@ -1078,7 +1193,7 @@ static void dense_inverse(ba_problem* P, Level& L) {
   int nblk = 0;
   BA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, k_gauss_jordan, kGJBS, 0));
   const int nbk = Np / kGJ;
-  int grid = std::max(1, std::min(nblk * P->n_sm, nbk * nbk * 4));
+  int grid = std::max(1, std::min(nblk * P->n_sm, nbk * nbk * kGJSplit));
   int* flags = P->flags.as<int>();
   void* args[] = {(void*)&A, (void*)&Np, (void*)&pinv, (void*)&pcol, (void*)&prow, (void*)&flags};
   BA_CUDA(cudaLaunchCooperativeKernel((void*)k_gauss_jordan, grid, kGJBS, args, 0, P->stream));
@@ -1173,6 +1288,13 @@ static void mg_symbolic(ba_problem* P) {
     k_count_members<<<cdiv(L.n, 256), 256, 0, P->stream>>>(L.n, L.agg.as<int>(), mc);
     launched(P);
     scan(P, mc, L.agg_ptr.as<int>(), L.n_agg);
+    {
+      std::vector<int> hp(L.n_agg + 1);
+      BA_CUDA(cudaMemcpyAsync(hp.data(), L.agg_ptr.p, sizeof(int) * (L.n_agg + 1), cudaMemcpyDeviceToHost, P->stream));
+      sync(P);
+      L.agg_max = 1;
+      for (int k = 0; k < L.n_agg; ++k) L.agg_max = std::max(L.agg_max, hp[k + 1] - hp[k]);
+    }
     k_fill_members<<<cdiv(L.n, 256), 256, 0, P->stream>>>(L.n, L.agg.as<int>(), L.agg_ptr.as<int>(), fill,
                                                           L.agg_mem.as<int>());
     launched(P);
@@ -1256,12 +1378,21 @@ void mg_setup(ba_problem* P) {
     L.Q32.ensure(sizeof(float) * L.bs * kNull * (size_t)L.n + 64);
     L1.K.ensure(sizeof(double) * kNull * kNull * (size_t)L1.n + 64);
     L1.kept.ensure(sizeof(unsigned) * (size_t)L1.n + 64);
-    const size_t qsm = sizeof(double) * (size_t)o.max_agg * L.bs * kQrStride;
-    BA_REQUIRE(qsm <= 200 * 1024, BA_ERR_LIMIT, "max_agg too large for the aggregate QR");
+    const int max_rows = std::max(1, L.agg_max) * L.bs;
+    const size_t qsm = sizeof(double) * (size_t)kQrWarps * max_rows * kQrStride;
+    BA_REQUIRE(qsm <= 200 * 1024, BA_ERR_LIMIT, "aggregates too large for the aggregate QR");
     BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
-    k_aggregate_qr<<<L1.n, kQrBS, qsm, P->stream>>>(L1.n, L.bs, L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
-                                                L.K.as<double>(), L.Q64.as<double>(), L.Q32.as<float>(),
-                                                L1.K.as<double>(), L1.kept.as<unsigned>());
+    if (L1.n >= 2 * P->n_sm) {
+      k_aggregate_qr<<<cdiv(L1.n, kQrWarps), kQrWarps * 32, qsm, P->stream>>>(
+          L1.n, L.bs, max_rows, L.agg_ptr.as<int>(), L.agg_mem.as<int>(), L.K.as<double>(), L.Q64.as<double>(),
+          L.Q32.as<float>(), L1.K.as<double>(), L1.kept.as<unsigned>());
+    } else {
+      const size_t csm = sizeof(double) * (size_t)max_rows * kQrStride;
+      BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+      k_aggregate_qr_cta<<<L1.n, kQrBS, csm, P->stream>>>(L1.n, L.bs, L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
+                                                          L.K.as<double>(), L.Q64.as<double>(), L.Q32.as<float>(),
+                                                          L1.K.as<double>(), L1.kept.as<unsigned>());
+    }
     launched(P);
     // Galerkin
     if (fp32) {
