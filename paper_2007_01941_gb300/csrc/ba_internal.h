@@ -101,6 +101,7 @@ struct Level {
   int n_agg = 0;
   int agg_max = 1;              // members of the largest aggregate
   DBuf agg_ptr, agg_mem;        // member lists of the next-level nodes
+  DBuf pair_ptr, pairs, blk_row; // level 0: observation pairs per block (int [nnzb+1], int2), block rows
   DBuf K;                       // double [n][bs][16] near-nullspace rows
   DBuf Q64, Q32;                // double/float [n][bs][16] prolongator blocks
   DBuf kept;                    // uint32 [n] kept-dof masks of this level's nodes
@@ -233,6 +234,14 @@ void fetch_scalars(ba_problem* P, int first, int count);  // async copy + sync
 void check_flags(ba_problem* P);                          // sync, read, raise
 void clear_flags(ba_problem* P);
 void launched(ba_problem* P);                              // count + check launch error
+
+// host vector -> device buffer (grown as needed) on the problem's stream
+template <typename T>
+void upload(ba_problem* P, DBuf& dst, const std::vector<T>& src) {
+  dst.ensure(sizeof(T) * std::max<size_t>(src.size(), 1));
+  if (!src.empty())
+    BA_CUDA(cudaMemcpyAsync(dst.p, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, P->stream));
+}
 
 // Launches kern on the problem's stream; with opt.overlap_launches as a programmatic
 // dependent launch (the kernel must call pdl_wait() before it touches memory).

@@ -9,15 +9,6 @@
 
 namespace ba {
 
-namespace {
-template <typename T>
-void upload(ba_problem* P, DBuf& dst, const std::vector<T>& src) {
-  dst.ensure(sizeof(T) * std::max<size_t>(src.size(), 1));
-  if (!src.empty())
-    BA_CUDA(cudaMemcpyAsync(dst.p, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice,
-                            P->stream));
-}
-}  // namespace
 
 void build_graph(ba_problem* P, const int32_t* cam_idx_dev, const int32_t* pt_idx_dev) {
   const int n_c = P->n_c, n_p = P->n_p, n_o = P->n_o;

@@ -616,13 +616,14 @@ void matvec32_accumulate(ba_problem* P, const float* x, float* y) {
 // finest level).  With C_p^-1 = L_p L_p^T (Cholesky) and W_o = L_p^T E_o^T F_o (3 x 9)
 // per observation o = (c, p), an off-diagonal block is
 //   S_cc' = - sum_{p seen by c and c'} W_(c,p)^T W_(c',p),
-// and the diagonal block S_cc is the one the Schur setup already formed.
-// k_schur_w writes W (one thread per observation); k_explicit_w takes one CTA per
-// camera row c: warp w walks the row's observations o in turn and, for every other
-// observation o' of the same point, lane (a, g) (27 lanes) adds entries (a, 3g..3g+2)
-// of -W_o^T W_o' to the block (c, cam(o')) in a shared-memory copy of the row.  A row
-// with more blocks than fit is done in several passes over block ranges.
+// and the diagonal block S_cc is the one the Schur setup already formed.  The pairs
+// (o, o') that meet in each block are listed once per problem (symbolic); k_schur_w
+// writes W (one thread per observation, rows padded to 28 entries) and k_explicit_pairs
+// gives each block to one warp, whose lane (a, g) (27 lanes) accumulates entries
+// (a, 3g .. 3g+2) over the block's pairs in registers.
 // ---------------------------------------------------------------------------
+constexpr int kWld = 28;   // W row stride (entries)
+
 template <typename T>
 __global__ void k_schur_w(const T* __restrict__ J, const T* __restrict__ Cinv, int ldp,
                           const int* __restrict__ obs_pt, int n_o, T* __restrict__ W) {
@@ -650,83 +651,127 @@ __global__ void k_schur_w(const T* __restrict__ J, const T* __restrict__ Cinv, i
   const T p22 = c22 - l20 * l20 - l21 * l21;
   const T l22 = sqrt(p22 > T(0) ? p22 : T(0));
   // W = L^T H
-  T* w = W + (size_t)o * 27;
+  T w[kWld];
 #pragma unroll
   for (int b = 0; b < 9; ++b) {
     w[b] = l00 * h[b] + l10 * h[9 + b] + l20 * h[18 + b];
     w[9 + b] = l11 * h[9 + b] + l21 * h[18 + b];
     w[18 + b] = l22 * h[18 + b];
   }
-}
-
-constexpr int kExBS = 256;
-
-template <typename T>
-__global__ void __launch_bounds__(kExBS)
-k_explicit_w(const T* __restrict__ W, const int* __restrict__ cam_ptr, const int* __restrict__ cam_obs,
-             const int* __restrict__ obs_pt, const int* __restrict__ obs_cam, const int* __restrict__ pt_ptr,
-             const int* __restrict__ row_ptr, const int* __restrict__ cols, const double* __restrict__ Scc,
-             int cap, T* __restrict__ vals) {
-  extern __shared__ __align__(16) unsigned char ew_smem[];
-  T* acc = reinterpret_cast<T*>(ew_smem);                       // [cap][81]
-  int* scol = reinterpret_cast<int*>(acc + (size_t)cap * 81);   // [cap]
-  const int c = blockIdx.x;
-  const int rb = row_ptr[c], nslots = row_ptr[c + 1] - rb;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int la = lane / 3, lg = lane - 3 * la;   // lane -> (row a, column group g)
-  const int ob0 = cam_ptr[c], nrow = cam_ptr[c + 1] - ob0;
-  for (int pass_base = 0; pass_base < nslots; pass_base += cap) {
-    const int pass_n = min(cap, nslots - pass_base);
-    for (int i = t; i < pass_n * 81; i += kExBS) acc[i] = T(0);
-    for (int i = t; i < pass_n; i += kExBS) scol[i] = cols[rb + pass_base + i];
-    __syncthreads();
-    for (int k = warp; k < nrow; k += kExBS / 32) {
-      const int o = cam_obs[ob0 + k];
-      const int ip = obs_pt[o];
-      T wi0 = T(0), wi1 = T(0), wi2 = T(0);
-      if (lane < 27) {
-        const T* wo = W + (size_t)o * 27 + la;
-        wi0 = wo[0];
-        wi1 = wo[9];
-        wi2 = wo[18];
-      }
-      for (int q = pt_ptr[ip]; q < pt_ptr[ip + 1]; ++q) {
-        if (q == o) continue;
-        const int c2 = obs_cam[q];
-        int lo = 0, hi = pass_n - 1, s = -1;
-        while (lo <= hi) {
-          const int mid = (lo + hi) >> 1;
-          const int v = scol[mid];
-          if (v == c2) {
-            s = mid;
-            break;
-          }
-          if (v < c2) lo = mid + 1;
-          else hi = mid - 1;
-        }
-        if (s < 0 || lane >= 27) continue;
-        const T* wq = W + (size_t)q * 27 + 3 * lg;
-        T* blk = acc + (size_t)s * 81 + 9 * la + 3 * lg;
+  w[27] = T(0);
+  T* out = W + (size_t)o * kWld;
+  if (sizeof(T) == 4) {
+    float4* o4 = reinterpret_cast<float4*>(out);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) atomicAdd(blk + j, -(wi0 * wq[j] + wi1 * wq[9 + j] + wi2 * wq[18 + j]));
-      }
-    }
-    __syncthreads();
-    for (int i = t; i < pass_n * 81; i += kExBS) {
-      const int s = i / 81, e = i - 81 * s;
-      const T v = scol[s] == c ? (T)Scc[(size_t)c * 81 + e] : acc[i];
-      vals[(size_t)(rb + pass_base + s) * 81 + e] = v;
-    }
-    __syncthreads();
+    for (int i = 0; i < kWld / 4; ++i) o4[i] = make_float4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+  } else {
+    double2* o2 = reinterpret_cast<double2*>(out);
+#pragma unroll
+    for (int i = 0; i < kWld / 2; ++i) o2[i] = make_double2(w[2 * i], w[2 * i + 1]);
   }
 }
 
+constexpr int kExWarps = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kExWarps * 32)
+k_explicit_pairs(const T* __restrict__ W, int nnzb, const int* __restrict__ blk_row, const int* __restrict__ cols,
+                 const int* __restrict__ pair_ptr, const int2* __restrict__ pairs, const double* __restrict__ Scc,
+                 T* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  const int e = blockIdx.x * kExWarps + (threadIdx.x >> 5);
+  if (e >= nnzb) return;
+  const int c = blk_row[e];
+  T* out = vals + (size_t)e * 81;
+  if (cols[e] == c) {
+    for (int i = lane; i < 81; i += 32) out[i] = (T)Scc[(size_t)c * 81 + i];
+    return;
+  }
+  const int la = lane / 3, lg = lane - 3 * la;   // lane -> (row a, column group g)
+  T s0 = T(0), s1 = T(0), s2 = T(0);
+  if (lane < 27) {
+    const int q1 = pair_ptr[e + 1];
+#pragma unroll 2
+    for (int q = pair_ptr[e]; q < q1; ++q) {
+      const int2 pr = __ldg(pairs + q);
+      const T* wi = W + (size_t)pr.x * kWld + la;
+      const T* wj = W + (size_t)pr.y * kWld + 3 * lg;
+      const T a0 = __ldg(wi), a1 = __ldg(wi + 9), a2 = __ldg(wi + 18);
+      s0 += a0 * __ldg(wj) + a1 * __ldg(wj + 9) + a2 * __ldg(wj + 18);
+      s1 += a0 * __ldg(wj + 1) + a1 * __ldg(wj + 10) + a2 * __ldg(wj + 19);
+      s2 += a0 * __ldg(wj + 2) + a1 * __ldg(wj + 11) + a2 * __ldg(wj + 20);
+    }
+    T* o = out + 9 * la + 3 * lg;
+    o[0] = -s0;
+    o[1] = -s1;
+    o[2] = -s2;
+  }
+}
+
+// pairs of observations of one point seen by different cameras, grouped by the level-0
+// block (camera of the first, camera of the second) they contribute to; built on the host
+// once per problem, in camera-row then observation order (deterministic sums)
+static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
+  const int n_c = P->n_c, n_o = P->n_o, n_p = P->n_p;
+  std::vector<int> row_ptr(n_c + 1), cols(std::max(L0.nnzb, 1)), cam_ptr(n_c + 1), cam_obs(std::max(n_o, 1)),
+      obs_pt(std::max(n_o, 1)), obs_cam(std::max(n_o, 1)), pt_ptr(n_p + 1);
+  auto down = [&](std::vector<int>& h, const DBuf& d, size_t n) {
+    if (n) BA_CUDA(cudaMemcpyAsync(h.data(), d.p, sizeof(int) * n, cudaMemcpyDeviceToHost, P->stream));
+  };
+  down(row_ptr, L0.row_ptr, n_c + 1);
+  down(cols, L0.cols, L0.nnzb);
+  down(cam_ptr, P->cam_ptr, n_c + 1);
+  down(cam_obs, P->cam_obs, n_o);
+  down(obs_pt, P->obs_pt, n_o);
+  down(obs_cam, P->obs_cam, n_o);
+  down(pt_ptr, P->pt_ptr, n_p + 1);
+  sync(P);
+  std::vector<int> blk_row(std::max(L0.nnzb, 1)), cnt(L0.nnzb + 1, 0);
+  for (int c = 0; c < n_c; ++c)
+    for (int e = row_ptr[c]; e < row_ptr[c + 1]; ++e) blk_row[e] = c;
+  auto block_of = [&](int c, int c2) {
+    int lo = row_ptr[c], hi = row_ptr[c + 1];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (cols[mid] < c2) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo;
+  };
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<int> fill;
+    std::vector<int2> pairs;
+    if (pass == 1) {
+      fill.assign(cnt.begin(), cnt.end() - 1);
+      pairs.resize(std::max(cnt[L0.nnzb], 1));
+    }
+    for (int c = 0; c < n_c; ++c)
+      for (int k = cam_ptr[c]; k < cam_ptr[c + 1]; ++k) {
+        const int o = cam_obs[k], p = obs_pt[o];
+        for (int q = pt_ptr[p]; q < pt_ptr[p + 1]; ++q) {
+          if (q == o) continue;
+          const int e = block_of(c, obs_cam[q]);
+          if (pass == 0) ++cnt[e + 1];
+          else pairs[fill[e]++] = make_int2(o, q);
+        }
+      }
+    if (pass == 0) {
+      for (int e = 0; e < L0.nnzb; ++e) cnt[e + 1] += cnt[e];
+      upload(P, L0.pair_ptr, cnt);
+      upload(P, L0.blk_row, blk_row);
+    } else {
+      upload(P, L0.pairs, pairs);
+    }
+  }
+  sync(P);
+}
+
 void explicit_schur(ba_problem* P, Level& L0, bool fp32) {
+  if (!L0.pairs.p) explicit_pairs_symbolic(P, L0);
   const size_t elem = fp32 ? 4 : 8;
-  const int cap = std::max(1, std::min(L0.maxrow, (int)((200 * 1024) / (81 * elem + 4))));
-  const size_t smem = (size_t)cap * 81 * elem + sizeof(int) * (size_t)cap;
-  P->scratch.ensure(elem * 27 * (size_t)std::max(P->n_o, 1) + 64);
+  P->scratch.ensure(elem * kWld * (size_t)std::max(P->n_o, 1) + 64);
   const int g = cdiv(std::max(P->n_o, 1), 128);
+  const int gb = cdiv(std::max(L0.nnzb, 1), kExWarps);
   if (fp32) {
     L0.vals32.ensure(sizeof(float) * 81 * (size_t)L0.nnzb + 64);
     float* W = P->scratch.as<float>();
@@ -735,11 +780,9 @@ void explicit_schur(ba_problem* P, Level& L0, bool fp32) {
                                                  P->obs_pt.as<int>(), P->n_o, W);
       launched(P);
     }
-    BA_CUDA(cudaFuncSetAttribute(k_explicit_w<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_explicit_w<float><<<P->n_c, kExBS, smem, P->stream>>>(
-        W, P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
-        P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Scc.as<double>(), cap,
-        L0.vals32.as<float>());
+    k_explicit_pairs<float><<<gb, kExWarps * 32, 0, P->stream>>>(
+        W, L0.nnzb, L0.blk_row.as<int>(), L0.cols.as<int>(), L0.pair_ptr.as<int>(), L0.pairs.as<int2>(),
+        P->Scc.as<double>(), L0.vals32.as<float>());
   } else {
     L0.vals64.ensure(sizeof(double) * 81 * (size_t)L0.nnzb + 64);
     double* W = P->scratch.as<double>();
@@ -748,11 +791,9 @@ void explicit_schur(ba_problem* P, Level& L0, bool fp32) {
                                                   P->obs_pt.as<int>(), P->n_o, W);
       launched(P);
     }
-    BA_CUDA(cudaFuncSetAttribute(k_explicit_w<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_explicit_w<double><<<P->n_c, kExBS, smem, P->stream>>>(
-        W, P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
-        P->pt_ptr.as<int>(), L0.row_ptr.as<int>(), L0.cols.as<int>(), P->Scc.as<double>(), cap,
-        L0.vals64.as<double>());
+    k_explicit_pairs<double><<<gb, kExWarps * 32, 0, P->stream>>>(
+        W, L0.nnzb, L0.blk_row.as<int>(), L0.cols.as<int>(), L0.pair_ptr.as<int>(), L0.pairs.as<int2>(),
+        P->Scc.as<double>(), L0.vals64.as<double>());
   }
   launched(P);
 }

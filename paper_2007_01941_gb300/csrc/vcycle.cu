@@ -173,23 +173,34 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_residual(VLevel<T> 
   }
 }
 
-// restriction b_c[a] = sum_{i in a} Q_i^T s_i (one warp per aggregate, lane s < 16)
+// restriction b_c[a] = sum_{i in a} Q_i^T s_i (one warp per aggregate, lane s < 16); when
+// the coarse level is smoothed, also its pre-smoothing step 0 for row a (x_c = 0):
+// r_c = b_c, d_c = D_c^-1 b_c / theta_c, x_c = d_c
 template <typename T, int BS>
 __global__ void __launch_bounds__(256) k_ph_restrict(VLevel<T> L, VLevel<T> C, const T* __restrict__ res) {
   pdl_wait();
   pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (a >= C.n || lane >= 16) return;
+  if (a >= C.n) return;
   T acc = T(0);
-  for (int m = L.agg_ptr[a]; m < L.agg_ptr[a + 1]; ++m) {
-    const int i = L.agg_mem[m];
-    const T* Qi = L.Q + (size_t)i * BS * 16 + lane;
-    const T* ri = res + (size_t)i * BS;
+  if (lane < 16)
+    for (int m = L.agg_ptr[a]; m < L.agg_ptr[a + 1]; ++m) {
+      const int i = L.agg_mem[m];
+      const T* Qi = L.Q + (size_t)i * BS * 16 + lane;
+      const T* ri = res + (size_t)i * BS;
 #pragma unroll
-    for (int u = 0; u < BS; ++u) acc += Qi[u * 16] * ri[u];
+      for (int u = 0; u < BS; ++u) acc += Qi[u * 16] * ri[u];
+    }
+  const size_t idx = (size_t)a * 16 + lane;
+  if (lane < 16) C.b[idx] = acc;
+  if (C.coarsest) return;
+  const T dv = block_apply<T, 16>(C.Dinv + (size_t)a * 256, acc, lane) * (T)(1.0 / C.cheb[0]);
+  if (lane < 16) {
+    C.r[0][idx] = acc;
+    C.d[0][idx] = dv;
+    C.x[0][idx] = dv;
   }
-  C.b[(size_t)a * 16 + lane] = acc;
 }
 
 template <typename T>
@@ -304,9 +315,12 @@ static void run(ba_problem* P, const double* r, double* z) {
   cudaStream_t st = P->stream;
   for (int l = 0; l + 1 < nl; ++l) {
     const VLevel<T>& L = V[l];
-    const int g = warps_grid(L.n);
-    if (L.bs == 9) launch_k(P, k_ph_first<T, 9>, g, kPhaseBS, 0, L, l == 0 ? r : nullptr);
-    else launch_k(P, k_ph_first<T, 16>, g, kPhaseBS, 0, L, l == 0 ? r : nullptr);
+    // step 0 of the coarse levels is done by the restriction that produces their b
+    if (l == 0) {
+      const int g = warps_grid(L.n);
+      if (L.bs == 9) launch_k(P, k_ph_first<T, 9>, g, kPhaseBS, 0, L, r);
+      else launch_k(P, k_ph_first<T, 16>, g, kPhaseBS, 0, L, r);
+    }
     for (int k = 1; k < pre; ++k) {
       double c1, c2;
       cheb_coeffs(P->levels[l], k, c1, c2);
