@@ -15,6 +15,27 @@ constexpr unsigned kFull = 0xffffffffu;
 // that kernel has completed and its writes are visible, pdl_trigger() lets the next
 // kernel be scheduled.  Both are no-ops for an ordinary launch.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// float with the sign, exponent and top 23 mantissa bits of the double with bits b (the
+// dropped bits are zero when called below); zero below the float range, infinity above
+__device__ __forceinline__ float bits_to_float(unsigned long long b) {
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  const unsigned m = (unsigned)(b >> 29) & 0x7fffffu;
+  const unsigned f = e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : (sign | ((unsigned)e << 23) | m));
+  return __uint_as_float(f);
+}
+
+// x = hi + lo with hi = x truncated to a float's 24 significant bits and lo the remainder
+// truncated likewise (|x - hi - lo| <= 2^-46 |x|): one exact FP64 subtraction and integer
+// bit operations, as FP64 conversions run on this GPU's narrow FP64 unit
+__device__ __forceinline__ void split_double(double x, float& hi, float& lo) {
+  const unsigned long long kKeep = 0xFFFFFFFFE0000000ull;
+  const unsigned long long hb = (unsigned long long)__double_as_longlong(x) & kKeep;
+  const double rem = x - __longlong_as_double((long long)hb);
+  hi = bits_to_float(hb);
+  lo = bits_to_float((unsigned long long)__double_as_longlong(rem) & kKeep);
+}
+
 // SplitMix64 (Steele, Lea & Flood 2014) of counter i: the Lanczos start vector
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long i) {
   unsigned long long z = 0x9E3779B97F4A7C15ull * (i + 1ull);

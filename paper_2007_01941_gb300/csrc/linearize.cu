@@ -10,13 +10,35 @@
 // d(RX)/dr = -[X]_x and d(RX)/dX = I + [r]_x.
 #include "ba_internal.h"
 #include "device_util.cuh"
+#include "dfloat.cuh"
 
 namespace ba {
 
 constexpr int kCamx = 24;   // doubles of per-camera rotation data
 constexpr int kLinBS = 256;
 
-__global__ void k_camera_rotation(const double* __restrict__ cams, int n_c, double* __restrict__ camx) {
+// per camera: R (9), J_l (9), first-order flag (1) in camx; with camdf also the same
+// values and the 9 parameters split into float pairs ([n_c][kCamdf]: 0..17 R and J_l,
+// 18 the flag, 19..27 the parameters), for the paired-FP32 linearisation
+constexpr int kCamdf = 28;
+
+__device__ __forceinline__ void camdf_write(float2* __restrict__ camdf, int c, const double* o, const double* cam) {
+  if (!camdf) return;
+  float2* d = camdf + (size_t)kCamdf * c;
+  for (int i = 0; i < 19; ++i) {
+    float h, l;
+    split_double(o[i], h, l);
+    d[i] = make_float2(h, l);
+  }
+  for (int i = 0; i < 9; ++i) {
+    float h, l;
+    split_double(cam[i], h, l);
+    d[19 + i] = make_float2(h, l);
+  }
+}
+
+__global__ void k_camera_rotation(const double* __restrict__ cams, int n_c, double* __restrict__ camx,
+                                  float2* __restrict__ camdf) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_c) return;
   const double r0 = cams[9 * c + 0], r1 = cams[9 * c + 1], r2 = cams[9 * c + 2];
@@ -28,6 +50,7 @@ __global__ void k_camera_rotation(const double* __restrict__ cams, int n_c, doub
     for (int i = 0; i < 9; ++i) o[i] = R[i];
     for (int i = 0; i < 9; ++i) o[9 + i] = (i % 4 == 0) ? 1.0 : 0.0;
     o[18] = 1.0;
+    camdf_write(camdf, c, o, cams + 9 * c);
     return;
   }
   const double th = sqrt(th2);
@@ -48,21 +71,26 @@ __global__ void k_camera_rotation(const double* __restrict__ cams, int n_c, doub
     o[9 + i] = I + a * K[i] + b * K2[i];       // J_l
   }
   o[18] = 0.0;
+  camdf_write(camdf, c, o, cams + 9 * c);
 }
 
-struct CamObs {
-  double res[2];
-  double F[18];
-  double E[6];
+template <typename R>
+struct CamObsT {
+  R res[2];
+  R F[18];
+  R E[6];
 };
+using CamObs = CamObsT<double>;
 
-template <bool JAC>
-__device__ __forceinline__ void project_obs(const double* __restrict__ cam, const double* __restrict__ cx,
-                                            const double X[3], const double ob[2], CamObs& out) {
-  const bool small = cx[18] != 0.0;
-  double RX[3];
+// residual and (JAC) Jacobian of one observation; cam: the 9 parameters, cx: R(r) (9),
+// J_l(r) (9), small: first-order rotation; R is double or DF (paired FP32)
+template <bool JAC, typename R>
+__device__ __forceinline__ void project_obs_t(const R cam[9], const R cx[18], bool small, const R X[3],
+                                              const R ob[2], CamObsT<R>& out) {
+  const R one = R(1.0), two = R(2.0);
+  R RX[3];
   if (small) {
-    const double r0 = cam[0], r1 = cam[1], r2 = cam[2];
+    const R r0 = cam[0], r1 = cam[1], r2 = cam[2];
     RX[0] = X[0] + (r1 * X[2] - r2 * X[1]);
     RX[1] = X[1] + (r2 * X[0] - r0 * X[2]);
     RX[2] = X[2] + (r0 * X[1] - r1 * X[0]);
@@ -70,22 +98,22 @@ __device__ __forceinline__ void project_obs(const double* __restrict__ cam, cons
 #pragma unroll
     for (int i = 0; i < 3; ++i) RX[i] = cx[3 * i] * X[0] + cx[3 * i + 1] * X[1] + cx[3 * i + 2] * X[2];
   }
-  const double P0 = RX[0] + cam[3], P1 = RX[1] + cam[4], P2 = RX[2] + cam[5];
-  const double iz = 1.0 / P2;
-  const double px = -P0 * iz, py = -P1 * iz;
-  const double f = cam[6], k1 = cam[7], k2 = cam[8];
-  const double r2 = px * px + py * py;
-  const double d = 1.0 + k1 * r2 + k2 * r2 * r2;
+  const R P0 = RX[0] + cam[3], P1 = RX[1] + cam[4], P2 = RX[2] + cam[5];
+  const R iz = one / P2;
+  const R px = -P0 * iz, py = -P1 * iz;
+  const R f = cam[6], k1 = cam[7], k2 = cam[8];
+  const R r2 = px * px + py * py;
+  const R d = one + k1 * r2 + k2 * r2 * r2;
   out.res[0] = f * d * px - ob[0];
   out.res[1] = f * d * py - ob[1];
   if (!JAC) return;
   // d pi / d p = f (d I + p (grad d)^T),  grad d = 2 (k1 + 2 k2 r2) p
-  const double gd = 2.0 * (k1 + 2.0 * k2 * r2);
-  const double A00 = f * (d + px * gd * px), A01 = f * (px * gd * py);
-  const double A10 = f * (py * gd * px), A11 = f * (d + py * gd * py);
+  const R gd = two * (k1 + two * k2 * r2);
+  const R A00 = f * (d + px * gd * px), A01 = f * (px * gd * py);
+  const R A10 = f * (py * gd * px), A11 = f * (d + py * gd * py);
   // d p / d P = [[-iz, 0, P0 iz^2], [0, -iz, P1 iz^2]]
-  const double iz2 = iz * iz;
-  double G[6];  // d pi / d P (2x3)
+  const R iz2 = iz * iz;
+  R G[6];  // d pi / d P (2x3)
   G[0] = -A00 * iz;
   G[1] = -A01 * iz;
   G[2] = (A00 * P0 + A01 * P1) * iz2;
@@ -93,30 +121,31 @@ __device__ __forceinline__ void project_obs(const double* __restrict__ cam, cons
   G[4] = -A11 * iz;
   G[5] = (A10 * P0 + A11 * P1) * iz2;
   // d P / d r
-  double Dr[9];
+  R Dr[9];
+  const R zero = R(0.0);
   if (small) {
     // -[X]_x
-    Dr[0] = 0.0;    Dr[1] = X[2];   Dr[2] = -X[1];
-    Dr[3] = -X[2];  Dr[4] = 0.0;    Dr[5] = X[0];
-    Dr[6] = X[1];   Dr[7] = -X[0];  Dr[8] = 0.0;
+    Dr[0] = zero;   Dr[1] = X[2];   Dr[2] = -X[1];
+    Dr[3] = -X[2];  Dr[4] = zero;   Dr[5] = X[0];
+    Dr[6] = X[1];   Dr[7] = -X[0];  Dr[8] = zero;
   } else {
     // -[RX]_x J_l : column j = -(RX x J_l[:, j])
-    const double* J = cx + 9;
+    const R* J = cx + 9;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const double m0 = J[j], m1 = J[3 + j], m2 = J[6 + j];
+      const R m0 = J[j], m1 = J[3 + j], m2 = J[6 + j];
       Dr[0 + j] = -(RX[1] * m2 - RX[2] * m1);
       Dr[3 + j] = -(RX[2] * m0 - RX[0] * m2);
       Dr[6 + j] = -(RX[0] * m1 - RX[1] * m0);
     }
   }
   // d P / d X
-  double Dx[9];
+  R Dx[9];
   if (small) {
-    const double r0 = cam[0], r1 = cam[1], r2c = cam[2];
-    Dx[0] = 1.0;  Dx[1] = -r2c; Dx[2] = r1;
-    Dx[3] = r2c;  Dx[4] = 1.0;  Dx[5] = -r0;
-    Dx[6] = -r1;  Dx[7] = r0;   Dx[8] = 1.0;
+    const R r0 = cam[0], r1 = cam[1], r2c = cam[2];
+    Dx[0] = one;  Dx[1] = -r2c; Dx[2] = r1;
+    Dx[3] = r2c;  Dx[4] = one;  Dx[5] = -r0;
+    Dx[6] = -r1;  Dx[7] = r0;   Dx[8] = one;
   } else {
 #pragma unroll
     for (int i = 0; i < 9; ++i) Dx[i] = cx[i];
@@ -136,6 +165,17 @@ __device__ __forceinline__ void project_obs(const double* __restrict__ cam, cons
   out.F[16] = f * r2 * py;
   out.F[8] = f * r2 * r2 * px;
   out.F[17] = f * r2 * r2 * py;
+}
+
+template <bool JAC>
+__device__ __forceinline__ void project_obs(const double* __restrict__ cam, const double* __restrict__ cx,
+                                            const double X[3], const double ob[2], CamObs& out) {
+  double c9[9], cr[18];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) c9[i] = cam[i];
+#pragma unroll
+  for (int i = 0; i < 18; ++i) cr[i] = cx[i];
+  project_obs_t<JAC, double>(c9, cr, cx[18] != 0.0, X, ob, out);
 }
 
 template <bool JAC, bool MIXED>
@@ -170,13 +210,10 @@ k_linearize(const double* __restrict__ cams, const double* __restrict__ pts,
 #pragma unroll
       for (int k = 0; k < kRec / 2; ++k) d64[k] = make_double2(rec[2 * k], rec[2 * k + 1]);
       if (MIXED) {
-        // FP32 copy (hi) and the rounding residual (lo): hi + lo carries ~48 bits
+        // FP32 copy (hi) and the remainder (lo): hi + lo carries ~47 bits
         float hi[kRec], lo[kRec];
 #pragma unroll
-        for (int k = 0; k < kRec; ++k) {
-          hi[k] = (float)rec[k];
-          lo[k] = (float)(rec[k] - (double)hi[k]);
-        }
+        for (int k = 0; k < kRec; ++k) split_double(rec[k], hi[k], lo[k]);
         float4* d32 = reinterpret_cast<float4*>(J32 + (size_t)o * kRec);
         float4* l32 = reinterpret_cast<float4*>(J32lo + (size_t)o * kRec);
 #pragma unroll
@@ -191,8 +228,68 @@ k_linearize(const double* __restrict__ cams, const double* __restrict__ pts,
   grid_sum_store<kLinBS>(acc, partial, counter, cost_out);
 }
 
-static void camera_rotation(ba_problem* P, const double* cams, double* camx) {
-  k_camera_rotation<<<cdiv(P->n_c, 128), 128, 0, P->stream>>>(cams, P->n_c, camx);
+// The mixed-precision linearisation: the camera model of project_obs_t in paired FP32
+// (DF), from the per-camera split of camdf and the points and observations split on
+// load.  Writes the residuals and the FP64 records (as hi + lo) and, directly from the
+// pairs, the FP32 records (hi) and their remainders (lo).
+template <bool JAC>
+__global__ void __launch_bounds__(kLinBS)
+k_linearize_df(const double* __restrict__ pts, const double* __restrict__ obs, const float2* __restrict__ camdf,
+               const int* __restrict__ obs_cam, const int* __restrict__ obs_ptu, const int* __restrict__ obs_user,
+               int n_o, double* __restrict__ fres, double* __restrict__ J64, float* __restrict__ J32,
+               float* __restrict__ J32lo, double* partial, unsigned* counter, double* cost_out, int* flags) {
+  double acc = 0.0;
+  for (int o = blockIdx.x * kLinBS + threadIdx.x; o < n_o; o += gridDim.x * kLinBS) {
+    const int c = obs_cam[o];
+    const int pu = obs_ptu[o];
+    const int ou = obs_user[o];
+    const float2* cd = camdf + (size_t)kCamdf * c;
+    DF cx[18], cam[9];
+#pragma unroll
+    for (int i = 0; i < 18; ++i) {
+      const float2 v = __ldg(cd + i);
+      cx[i] = DF(v.x, v.y);
+    }
+    const bool small = __ldg(cd + 18).x != 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const float2 v = __ldg(cd + 19 + i);
+      cam[i] = DF(v.x, v.y);
+    }
+    const DF X[3] = {DF(pts[3 * pu]), DF(pts[3 * pu + 1]), DF(pts[3 * pu + 2])};
+    const DF ob[2] = {DF(obs[2 * ou]), DF(obs[2 * ou + 1])};
+    CamObsT<DF> v;
+    project_obs_t<JAC, DF>(cam, cx, small, X, ob, v);
+    const double r0 = to_double(v.res[0]), r1 = to_double(v.res[1]);
+    acc += 0.5 * (r0 * r0 + r1 * r1);
+    if (fres) reinterpret_cast<double2*>(fres)[o] = make_double2(r0, r1);
+    if (JAC) {
+      bool finite = isfinite(r0) && isfinite(r1);
+      DF rec[kRec];
+#pragma unroll
+      for (int k = 0; k < 18; ++k) rec[k] = v.F[k];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) rec[18 + k] = v.E[k];
+#pragma unroll
+      for (int k = 0; k < kRec; ++k) finite = finite && isfinite(rec[k].h);
+      double2* d64 = reinterpret_cast<double2*>(J64 + (size_t)o * kRec);
+#pragma unroll
+      for (int k = 0; k < kRec / 2; ++k) d64[k] = make_double2(to_double(rec[2 * k]), to_double(rec[2 * k + 1]));
+      float4* d32 = reinterpret_cast<float4*>(J32 + (size_t)o * kRec);
+      float4* l32 = reinterpret_cast<float4*>(J32lo + (size_t)o * kRec);
+#pragma unroll
+      for (int k = 0; k < kRec / 4; ++k) {
+        d32[k] = make_float4(rec[4 * k].h, rec[4 * k + 1].h, rec[4 * k + 2].h, rec[4 * k + 3].h);
+        l32[k] = make_float4(rec[4 * k].l, rec[4 * k + 1].l, rec[4 * k + 2].l, rec[4 * k + 3].l);
+      }
+      if (!finite) flags[F_NONFINITE] = 1;
+    }
+  }
+  grid_sum_store<kLinBS>(acc, partial, counter, cost_out);
+}
+
+static void camera_rotation(ba_problem* P, const double* cams, double* camx, float2* camdf) {
+  k_camera_rotation<<<cdiv(P->n_c, 128), 128, 0, P->stream>>>(cams, P->n_c, camx, camdf);
   launched(P);
 }
 
@@ -222,15 +319,16 @@ void linearize(ba_problem* P, const double* cams, const double* pts, const doubl
   if (P->n_o)
     BA_CUDA(cudaMemcpyAsync(P->obs_lin.p, obs, sizeof(double) * 2 * P->n_o, cudaMemcpyDeviceToDevice, P->stream));
   clear_flags(P);
-  camera_rotation(P, cams, P->camx.as<double>());
+  if (mixed) P->camdf.ensure(sizeof(float2) * kCamdf * std::max(P->n_c, 1));
+  camera_rotation(P, cams, P->camx.as<double>(), mixed ? P->camdf.as<float2>() : nullptr);
   int g = lin_grid(P);
   double* cost = P->scal.as<double>() + S_COST;
   KernelTimer kt(P, BA_KT_LINEARIZE);
   if (mixed)
-    k_linearize<true, true><<<g, kLinBS, 0, P->stream>>>(
-        cams, pts, obs, P->camx.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
-        P->obs_user.as<int>(), P->n_o, ld, P->fres.as<double>(), P->J64.as<double>(), P->J32.as<float>(),
-        P->J32lo.as<float>(), P->partial.as<double>(), P->counter.as<unsigned>(), cost, P->flags.as<int>());
+    k_linearize_df<true><<<g, kLinBS, 0, P->stream>>>(
+        pts, obs, P->camdf.as<float2>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(), P->obs_user.as<int>(), P->n_o,
+        P->fres.as<double>(), P->J64.as<double>(), P->J32.as<float>(), P->J32lo.as<float>(), P->partial.as<double>(),
+        P->counter.as<unsigned>(), cost, P->flags.as<int>());
   else
     k_linearize<true, false><<<g, kLinBS, 0, P->stream>>>(
         cams, pts, obs, P->camx.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
@@ -240,14 +338,24 @@ void linearize(ba_problem* P, const double* cams, const double* pts, const doubl
 }
 
 double cost_at(ba_problem* P, const double* cams, const double* pts, const double* obs) {
-  P->scratch2.ensure(sizeof(double) * kCamx * std::max(P->n_c, 1));
-  camera_rotation(P, cams, P->scratch2.as<double>());
+  const bool mixed = P->opt.precision == BA_MIXED;
+  // rotation data in the front of scratch2, the camera split behind it
+  const size_t rot_bytes = (sizeof(double) * kCamx * std::max(P->n_c, 1) + 255) / 256 * 256;
+  P->scratch2.ensure(rot_bytes + sizeof(float2) * kCamdf * std::max(P->n_c, 1));
+  float2* camdf = mixed ? reinterpret_cast<float2*>(P->scratch2.as<char>() + rot_bytes) : nullptr;
+  camera_rotation(P, cams, P->scratch2.as<double>(), camdf);
   int g = lin_grid(P);
-  k_linearize<false, false><<<g, kLinBS, 0, P->stream>>>(
-      cams, pts, obs, P->scratch2.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
-      P->obs_user.as<int>(), P->n_o, P->ld, nullptr, nullptr, nullptr, nullptr,
-      P->partial.as<double>(), P->counter.as<unsigned>(), P->scal.as<double>() + S_COST_NEW,
-      P->flags.as<int>());
+  if (mixed)
+    k_linearize_df<false><<<g, kLinBS, 0, P->stream>>>(
+        pts, obs, camdf, P->obs_cam.as<int>(), P->obs_ptu.as<int>(), P->obs_user.as<int>(), P->n_o, nullptr, nullptr,
+        nullptr, nullptr, P->partial.as<double>(), P->counter.as<unsigned>(), P->scal.as<double>() + S_COST_NEW,
+        P->flags.as<int>());
+  else
+    k_linearize<false, false><<<g, kLinBS, 0, P->stream>>>(
+        cams, pts, obs, P->scratch2.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
+        P->obs_user.as<int>(), P->n_o, P->ld, nullptr, nullptr, nullptr, nullptr,
+        P->partial.as<double>(), P->counter.as<unsigned>(), P->scal.as<double>() + S_COST_NEW,
+        P->flags.as<int>());
   launched(P);
   fetch_scalars(P, S_COST_NEW, 1);
   return P->h_scal[S_COST_NEW];

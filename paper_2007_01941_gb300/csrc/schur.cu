@@ -64,9 +64,10 @@ __global__ void k_point_setup(const double* __restrict__ E, const double* __rest
   for (int k = 0; k < 6; ++k) {
     Cinv[k * ldp + ip] = inv[k];
     if (Cinv32) {
-      const float hi = (float)inv[k];
+      float hi, lo;
+      split_double(inv[k], hi, lo);
       Cinv32[k * ldp + ip] = hi;
-      Cinv32lo[k * ldp + ip] = (float)(inv[k] - (double)hi);
+      Cinv32lo[k * ldp + ip] = lo;
     }
   }
   wp[ip] = inv[0] * g0 + inv[1] * g1 + inv[2] * g2;

@@ -111,7 +111,7 @@ __device__ __forceinline__ void df_u(const F2 J[kRec], const float2* __restrict_
 
 constexpr int kDfWarps = 8;
 
-__global__ void __launch_bounds__(kDfWarps * 32, 2)
+__global__ void __launch_bounds__(kDfWarps * 32, 3)
 k_schur_matvec_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const float* __restrict__ Ch,
                   const float* __restrict__ Cl, int ldp, const int* __restrict__ obs_cam,
                   const int4* __restrict__ tile_desc, const unsigned char* __restrict__ tile_perm,
