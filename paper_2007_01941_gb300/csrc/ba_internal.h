@@ -168,6 +168,7 @@ struct ba_problem {
   ba::DBuf Cinv32lo;            // [6][ldp] float rounding residual Cinv64 - Cinv32
   ba::DBuf xsplit;              // float2 [n_c][9] hi/lo split of a camera vector
   ba::DBuf camdf;               // float2 [n_c][28] split rotation data and parameters (mixed)
+  ba::DBuf wpdf;                // float2 [3][ldp] split C_p^-1 g_p (mixed)
   ba::DBuf gc, gp, wp, rhs;     // g_c [n_c*9], g_p [3][ldp], C^-1 g_p [3][ldp], b [n_c*9]
   ba::DBuf Dc32;                // float copy of D_c
   ba::DBuf Scc;                 // double [n_c][81] diagonal blocks S_cc

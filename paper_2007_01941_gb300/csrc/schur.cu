@@ -7,6 +7,7 @@
 
 #include "ba_internal.h"
 #include "device_util.cuh"
+#include "dfloat.cuh"
 
 namespace ba {
 
@@ -264,6 +265,190 @@ void block_inverse(ba_problem* P, const double* in, int n, int bs, double* out64
   launched(P);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed precision: the per-observation sums of the Schur setup and of the point
+// back-substitution in paired FP32 (DF) from the FP32 records and their remainders, with
+// the FP64 results formed from the pairs.  The 3x3 inversions stay FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ DF rec_df(const float* __restrict__ h, const float* __restrict__ l, int o, int k) {
+  return DF(__ldg(h + (size_t)o * kRec + k), __ldg(l + (size_t)o * kRec + k));
+}
+
+__global__ void k_point_setup_df(const float* __restrict__ Jh, const float* __restrict__ Jl,
+                                 const double* __restrict__ fres, const int* __restrict__ pt_ptr, int n_p, int n_p_obs,
+                                 size_t ldp, double lambda, int damp_identity, double* __restrict__ Dp,
+                                 double* __restrict__ Cinv, float* __restrict__ Cinv32, float* __restrict__ Cinv32lo,
+                                 double* __restrict__ gp, double* __restrict__ wp, float2* __restrict__ wpdf,
+                                 int* flags) {
+  int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= n_p) return;
+  const DF z(0.f, 0.f);
+  DF c00 = z, c01 = z, c02 = z, c11 = z, c12 = z, c22 = z, g0 = z, g1 = z, g2 = z;
+  const int b = pt_ptr[ip], e = pt_ptr[ip + 1];
+  for (int o = b; o < e; ++o) {
+    const DF a0 = rec_df(Jh, Jl, o, 18), a1 = rec_df(Jh, Jl, o, 19), a2 = rec_df(Jh, Jl, o, 20);
+    const DF b0 = rec_df(Jh, Jl, o, 21), b1 = rec_df(Jh, Jl, o, 22), b2 = rec_df(Jh, Jl, o, 23);
+    const DF f0(fres[2 * (size_t)o]), f1(fres[2 * (size_t)o + 1]);
+    c00 += a0 * a0 + b0 * b0;
+    c01 += a0 * a1 + b0 * b1;
+    c02 += a0 * a2 + b0 * b2;
+    c11 += a1 * a1 + b1 * b1;
+    c12 += a1 * a2 + b1 * b2;
+    c22 += a2 * a2 + b2 * b2;
+    g0 -= a0 * f0 + b0 * f1;
+    g1 -= a1 * f0 + b1 * f1;
+    g2 -= a2 * f0 + b2 * f1;
+  }
+  const double C00 = to_double(c00), C01 = to_double(c01), C02 = to_double(c02);
+  const double C11 = to_double(c11), C12 = to_double(c12), C22 = to_double(c22);
+  const double G0 = to_double(g0), G1 = to_double(g1), G2 = to_double(g2);
+  double d0, d1, d2;
+  if (damp_identity) {
+    d0 = d1 = d2 = lambda;
+  } else {
+    d0 = lambda * fmax(C00, 1e-6);
+    d1 = lambda * fmax(C11, 1e-6);
+    d2 = lambda * fmax(C22, 1e-6);
+  }
+  Dp[ip] = d0;
+  Dp[ldp + ip] = d1;
+  Dp[2 * ldp + ip] = d2;
+  gp[ip] = G0;
+  gp[ldp + ip] = G1;
+  gp[2 * ldp + ip] = G2;
+  double inv[6] = {0, 0, 0, 0, 0, 0};
+  if (ip < n_p_obs) {
+    double a[9] = {C00 + d0, C01, C02, C01, C11 + d1, C12, C02, C12, C22 + d2};
+    if (!spd_inverse<3>(a, 3)) {
+      flags[F_NOT_SPD_POINT] = 1;
+    } else {
+      inv[0] = a[0]; inv[1] = a[1]; inv[2] = a[2]; inv[3] = a[4]; inv[4] = a[5]; inv[5] = a[8];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    Cinv[k * ldp + ip] = inv[k];
+    float hi, lo;
+    split_double(inv[k], hi, lo);
+    Cinv32[k * ldp + ip] = hi;
+    Cinv32lo[k * ldp + ip] = lo;
+  }
+  const double w[3] = {inv[0] * G0 + inv[1] * G1 + inv[2] * G2, inv[1] * G0 + inv[3] * G1 + inv[4] * G2,
+                       inv[2] * G0 + inv[4] * G1 + inv[5] * G2};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    wp[k * ldp + ip] = w[k];
+    float hi, lo;
+    split_double(w[k], hi, lo);
+    wpdf[k * ldp + ip] = make_float2(hi, lo);
+  }
+}
+
+__device__ __forceinline__ DF warp_sum_df(DF v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += DF(__shfl_xor_sync(kFull, v.h, d), __shfl_xor_sync(kFull, v.l, d));
+  return v;
+}
+
+__global__ void k_camera_setup_df(const float* __restrict__ Jh, const float* __restrict__ Jl,
+                                  const double* __restrict__ fres, const int* __restrict__ cam_ptr,
+                                  const int* __restrict__ cam_obs, const int* __restrict__ obs_pt,
+                                  const float2* __restrict__ wpdf, size_t ldp, int n_c, double lambda,
+                                  int damp_identity, double* __restrict__ Dc, float* __restrict__ Dc32,
+                                  double* __restrict__ gc, double* __restrict__ rhs) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= n_c) return;
+  const DF z(0.f, 0.f);
+  DF dg[9], g[9], bb[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) dg[k] = g[k] = bb[k] = z;
+  for (int i = cam_ptr[c] + lane; i < cam_ptr[c + 1]; i += 32) {
+    const int o = cam_obs[i];
+    const int ip = obs_pt[o];
+    const DF f0(fres[2 * (size_t)o]), f1(fres[2 * (size_t)o + 1]);
+    const float2 q0 = __ldg(wpdf + ip), q1 = __ldg(wpdf + ldp + ip), q2 = __ldg(wpdf + 2 * ldp + ip);
+    const DF w0(q0.x, q0.y), w1(q1.x, q1.y), w2(q2.x, q2.y);
+    const DF h0 = f0 + rec_df(Jh, Jl, o, 18) * w0 + rec_df(Jh, Jl, o, 19) * w1 + rec_df(Jh, Jl, o, 20) * w2;
+    const DF h1 = f1 + rec_df(Jh, Jl, o, 21) * w0 + rec_df(Jh, Jl, o, 22) * w1 + rec_df(Jh, Jl, o, 23) * w2;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const DF a = rec_df(Jh, Jl, o, k), b = rec_df(Jh, Jl, o, 9 + k);
+      dg[k] += a * a + b * b;
+      g[k] -= a * f0 + b * f1;
+      bb[k] -= a * h0 + b * h1;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    dg[k] = warp_sum_df(dg[k]);
+    g[k] = warp_sum_df(g[k]);
+    bb[k] = warp_sum_df(bb[k]);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const double dgk = to_double(dg[k]);
+      const double d = damp_identity ? lambda : lambda * fmax(dgk, 1e-6);
+      Dc[9 * c + k] = d;
+      Dc32[9 * c + k] = (float)d;
+      gc[9 * c + k] = to_double(g[k]);
+      rhs[9 * c + k] = to_double(bb[k]);
+    }
+  }
+}
+
+// delta_p = C_p^-1 (v_p - sum_{o in p} E_o^T F_o delta_c), delta_c given as float pairs
+__global__ void k_back_substitute_df(const float* __restrict__ Jh, const float* __restrict__ Jl,
+                                     const double* __restrict__ Cinv, size_t ldp, const int* __restrict__ pt_ptr,
+                                     const int* __restrict__ obs_cam, const int* __restrict__ pt_user,
+                                     const double* __restrict__ vp, int vp_user, const float2* __restrict__ dcs,
+                                     int n_p, double* __restrict__ out_int, double* __restrict__ out_user) {
+  int ip = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ip >= n_p) return;
+  const int pu = pt_user[ip];
+  DF h0, h1, h2;
+  if (vp_user) {
+    h0 = DF(vp[3 * pu]);
+    h1 = DF(vp[3 * pu + 1]);
+    h2 = DF(vp[3 * pu + 2]);
+  } else {
+    h0 = DF(vp[ip]);
+    h1 = DF(vp[ldp + ip]);
+    h2 = DF(vp[2 * ldp + ip]);
+  }
+  for (int o = pt_ptr[ip]; o < pt_ptr[ip + 1]; ++o) {
+    const float2* x = dcs + 9 * (size_t)obs_cam[o];
+    DF u0(0.f, 0.f), u1(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float2 xv = __ldg(x + k);
+      const DF xk(xv.x, xv.y);
+      u0 += rec_df(Jh, Jl, o, k) * xk;
+      u1 += rec_df(Jh, Jl, o, 9 + k) * xk;
+    }
+    h0 -= rec_df(Jh, Jl, o, 18) * u0 + rec_df(Jh, Jl, o, 21) * u1;
+    h1 -= rec_df(Jh, Jl, o, 19) * u0 + rec_df(Jh, Jl, o, 22) * u1;
+    h2 -= rec_df(Jh, Jl, o, 20) * u0 + rec_df(Jh, Jl, o, 23) * u1;
+  }
+  const double H0 = to_double(h0), H1 = to_double(h1), H2 = to_double(h2);
+  const double c00 = Cinv[ip], c01 = Cinv[ldp + ip], c02 = Cinv[2 * ldp + ip];
+  const double c11 = Cinv[3 * ldp + ip], c12 = Cinv[4 * ldp + ip], c22 = Cinv[5 * ldp + ip];
+  const double d0 = c00 * H0 + c01 * H1 + c02 * H2;
+  const double d1 = c01 * H0 + c11 * H1 + c12 * H2;
+  const double d2 = c02 * H0 + c12 * H1 + c22 * H2;
+  if (out_int) {
+    out_int[ip] = d0;
+    out_int[ldp + ip] = d1;
+    out_int[2 * ldp + ip] = d2;
+  }
+  if (out_user) {
+    out_user[3 * pu] = d0;
+    out_user[3 * pu + 1] = d1;
+    out_user[3 * pu + 2] = d2;
+  }
+}
+
 void schur_setup(ba_problem* P, double lambda) {
   const bool mixed = P->opt.precision == BA_MIXED;
   const int n_c = P->n_c, n_p = P->n_p;
@@ -288,17 +473,31 @@ void schur_setup(ba_problem* P, double lambda) {
   clear_flags(P);
   const int damp_id = P->opt.damping == BA_DAMP_IDENTITY;
   if (n_p) {
-    k_point_setup<<<cdiv(n_p, 128), 128, 0, P->stream>>>(
-        P->J64.as<double>(), P->fres.as<double>(), P->ld, P->pt_ptr.as<int>(), n_p, P->n_p_obs, ldp,
-        lambda, damp_id, P->Dp.as<double>(), P->Cinv64.as<double>(),
-        mixed ? P->Cinv32.as<float>() : nullptr, mixed ? P->Cinv32lo.as<float>() : nullptr,
-        P->gp.as<double>(), P->wp.as<double>(), P->flags.as<int>());
+    if (mixed) {
+      P->wpdf.ensure(sizeof(float2) * 3 * ldp);
+      k_point_setup_df<<<cdiv(n_p, 128), 128, 0, P->stream>>>(
+          P->J32.as<float>(), P->J32lo.as<float>(), P->fres.as<double>(), P->pt_ptr.as<int>(), n_p, P->n_p_obs, ldp,
+          lambda, damp_id, P->Dp.as<double>(), P->Cinv64.as<double>(), P->Cinv32.as<float>(),
+          P->Cinv32lo.as<float>(), P->gp.as<double>(), P->wp.as<double>(), P->wpdf.as<float2>(),
+          P->flags.as<int>());
+    } else {
+      k_point_setup<<<cdiv(n_p, 128), 128, 0, P->stream>>>(
+          P->J64.as<double>(), P->fres.as<double>(), P->ld, P->pt_ptr.as<int>(), n_p, P->n_p_obs, ldp,
+          lambda, damp_id, P->Dp.as<double>(), P->Cinv64.as<double>(), nullptr, nullptr, P->gp.as<double>(),
+          P->wp.as<double>(), P->flags.as<int>());
+    }
     launched(P);
   }
-  k_camera_setup<<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
-      P->J64.as<double>(), P->J64.as<double>(), P->fres.as<double>(), P->ld, P->cam_ptr.as<int>(),
-      P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->wp.as<double>(), ldp, n_c, lambda, damp_id,
-      P->Dc.as<double>(), P->Dc32.as<float>(), P->gc.as<double>(), P->rhs.as<double>());
+  if (mixed && n_p)
+    k_camera_setup_df<<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
+        P->J32.as<float>(), P->J32lo.as<float>(), P->fres.as<double>(), P->cam_ptr.as<int>(), P->cam_obs.as<int>(),
+        P->obs_pt.as<int>(), P->wpdf.as<float2>(), ldp, n_c, lambda, damp_id, P->Dc.as<double>(),
+        P->Dc32.as<float>(), P->gc.as<double>(), P->rhs.as<double>());
+  else
+    k_camera_setup<<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
+        P->J64.as<double>(), P->J64.as<double>(), P->fres.as<double>(), P->ld, P->cam_ptr.as<int>(),
+        P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->wp.as<double>(), ldp, n_c, lambda, damp_id,
+        P->Dc.as<double>(), P->Dc32.as<float>(), P->gc.as<double>(), P->rhs.as<double>());
   launched(P);
   // point-block-Jacobi blocks S_cc (in the mode's storage precision) and FP64 inverses
   double* Scc = P->Scc.as<double>();
@@ -852,23 +1051,29 @@ __global__ void k_back_substitute(const double* __restrict__ F, const double* __
   }
 }
 
-void back_substitute_to(ba_problem* P, const double* dc, double* out_int, double* out_user) {
+static void back_substitute_impl(ba_problem* P, const double* vp, int vp_user, const double* dc, double* out_int,
+                                 double* out_user) {
   if (P->n_p == 0) return;
-  k_back_substitute<<<cdiv(P->n_p, 128), 128, 0, P->stream>>>(
-      P->J64.as<double>(), P->J64.as<double>(), P->ld, P->Cinv64.as<double>(), P->ldp,
-      P->pt_ptr.as<int>(), P->obs_cam.as<int>(), P->pt_user.as<int>(), P->gp.as<double>(), 0, dc,
-      P->n_p, out_int, out_user);
+  if (P->opt.precision == BA_MIXED) {
+    split_vector(P, dc, nullptr, nullptr);
+    k_back_substitute_df<<<cdiv(P->n_p, 128), 128, 0, P->stream>>>(
+        P->J32.as<float>(), P->J32lo.as<float>(), P->Cinv64.as<double>(), P->ldp, P->pt_ptr.as<int>(),
+        P->obs_cam.as<int>(), P->pt_user.as<int>(), vp, vp_user, P->xsplit.as<float2>(), P->n_p, out_int, out_user);
+  } else {
+    k_back_substitute<<<cdiv(P->n_p, 128), 128, 0, P->stream>>>(
+        P->J64.as<double>(), P->J64.as<double>(), P->ld, P->Cinv64.as<double>(), P->ldp, P->pt_ptr.as<int>(),
+        P->obs_cam.as<int>(), P->pt_user.as<int>(), vp, vp_user, dc, P->n_p, out_int, out_user);
+  }
   launched(P);
+}
+
+void back_substitute_to(ba_problem* P, const double* dc, double* out_int, double* out_user) {
+  back_substitute_impl(P, P->gp.as<double>(), 0, dc, out_int, out_user);
 }
 
 void back_substitute_general(ba_problem* P, const double* vp_user, const double* dc, double* out_int,
                              double* out_user) {
-  if (P->n_p == 0) return;
-  k_back_substitute<<<cdiv(P->n_p, 128), 128, 0, P->stream>>>(
-      P->J64.as<double>(), P->J64.as<double>(), P->ld, P->Cinv64.as<double>(), P->ldp,
-      P->pt_ptr.as<int>(), P->obs_cam.as<int>(), P->pt_user.as<int>(), vp_user, 1, dc, P->n_p,
-      out_int, out_user);
-  launched(P);
+  back_substitute_impl(P, vp_user, 1, dc, out_int, out_user);
 }
 
 // reduced RHS for a general right-hand side: out_c = v_c - sum_o F_o^T E_o C_p^-1 v_p
