@@ -98,9 +98,13 @@ def residuals(cams, pts, cam_idx, pt_idx, obs):
     return project(cams[cam_idx], pts[pt_idx]) - obs
 
 
-def cost(cams, pts, cam_idx, pt_idx, obs) -> float:
-    """Objective 1/2 sum_o |f_o|^2 (the squared sum of Section 2.1)."""
+def cost(cams, pts, cam_idx, pt_idx, obs, huber=None) -> float:
+    """Objective 1/2 sum_o |f_o|^2 (the squared sum of Section 2.1); with huber = a, the
+    robust objective 1/2 sum_o loss(|f_o|^2) of Section 5."""
     f = residuals(cams, pts, cam_idx, pt_idx, obs)
+    if huber is not None:
+        from . import robust
+        return robust.cost(f, huber)
     return 0.5 * float(np.sum(f * f))
 
 

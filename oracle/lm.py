@@ -37,14 +37,15 @@ def solve_step(sch: schur.Schur, cams, precond="mg", rtol=1e-8, max_iters=1000, 
     return dc, dp, it, rel
 
 
-def lm_step(cams, pts, cam_idx, pt_idx, obs, lam, nu=2.0, precond="mg", rtol=1e-8, **kw):
-    """Returns (cams', pts', lam', nu', accepted, cost_before, cost_after_or_before, info)."""
-    sch = schur.linearize(cams, pts, cam_idx, pt_idx, obs, lam)
-    cost0 = 0.5 * float(np.sum(sch.f * sch.f))
+def lm_step(cams, pts, cam_idx, pt_idx, obs, lam, nu=2.0, precond="mg", rtol=1e-8, huber=None, **kw):
+    """Returns (cams', pts', lam', nu', accepted, cost_before, cost_after_or_before, info).
+    huber = a: the robust objective and corrected residuals of Section 5 (oracle/robust.py)."""
+    sch = schur.linearize(cams, pts, cam_idx, pt_idx, obs, lam, huber=huber)
+    cost0 = camera.cost(cams, pts, cam_idx, pt_idx, obs, huber=huber)
     dc, dp, it, rel = solve_step(sch, cams, precond, rtol, **kw)
     cams1 = cams + dc.reshape(-1, 9)
     pts1 = pts + dp.reshape(-1, 3)
-    cost1 = camera.cost(cams1, pts1, cam_idx, pt_idx, obs)
+    cost1 = camera.cost(cams1, pts1, cam_idx, pt_idx, obs, huber=huber)
     model = sch.model_reduction(dc, dp)
     rho = (cost0 - cost1) / model if model > 0 else -np.inf
     info = dict(iters=it, rel_res=rel, rho=rho, model=model, cost_new=cost1)

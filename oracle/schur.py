@@ -110,8 +110,15 @@ class Schur:
         return 0.5 * (dg + dDd)
 
 
-def linearize(cams, pts, cam_idx, pt_idx, obs, lam, damping_mode="marquardt", explicit=True):
-    from . import camera
+def linearize(cams, pts, cam_idx, pt_idx, obs, lam, damping_mode="marquardt", explicit=True, huber=None):
+    """huber = a: residuals and Jacobian rows scaled by sqrt(loss'(|f_o|^2)) of the Huber
+    loss with scale a (see oracle/robust.py); None: the squared loss."""
+    from . import camera, robust
     f = camera.residuals(cams, pts, cam_idx, pt_idx, obs)
     F, E = camera.jacobians(cams, pts, cam_idx, pt_idx)
+    if huber is not None:
+        w = robust.weights(f, huber)
+        f = f * w[:, None]
+        F = F * w[:, None, None]
+        E = E * w[:, None, None]
     return Schur(F, E, f, cam_idx, pt_idx, cams.shape[0], pts.shape[0], lam, damping_mode, explicit)

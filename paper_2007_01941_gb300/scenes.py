@@ -73,8 +73,11 @@ def _intrinsics(rng, n):
 
 
 def _assemble(name, rng, Rm, centres, f, k1, k2, X, cam_idx, pt_idx, sigma,
-              rel_pert, trans_pert, point_pert, lam, rtol, drift=None) -> Scene:
-    """Project, add noise, perturb, shuffle; returns a Scene."""
+              rel_pert, trans_pert, point_pert, lam, rtol, drift=None, outlier_frac=0.0,
+              outlier_px=30.0) -> Scene:
+    """Project, add noise, perturb, shuffle; returns a Scene.  outlier_frac > 0 gives that
+    fraction of the observations an extra N(0, outlier_px^2) error (wrong correspondences,
+    the outliers of Section 5's robust-loss experiment)."""
     n_c = Rm.shape[0]
     n_p = X.shape[0]
     t = -np.einsum("nij,nj->ni", Rm, centres)
@@ -83,6 +86,10 @@ def _assemble(name, rng, Rm, centres, f, k1, k2, X, cam_idx, pt_idx, sigma,
     if np.any(depth >= -1e-3):
         raise ValueError("generator produced a point behind a camera")
     obs = uv + rng.normal(0.0, sigma, uv.shape)
+    if outlier_frac > 0.0:
+        orng = np.random.default_rng(int(rng.integers(2**62)))
+        bad = orng.random(len(obs)) < outlier_frac
+        obs[bad] += orng.normal(0.0, outlier_px, (int(bad.sum()), 2))
     rvec = Rotation.from_matrix(Rm).as_rotvec()
     cams_true = np.concatenate([rvec, t, f[:, None], k1[:, None], k2[:, None]], axis=1)
 
@@ -118,7 +125,7 @@ def _assemble(name, rng, Rm, centres, f, k1, k2, X, cam_idx, pt_idx, sigma,
 
 
 def ring(seed=0, n_cams=32, n_pts=4000, kmin=4, kmax=8, radius=10.0, sigma=0.5,
-         lam=1e-4, rtol=1e-8) -> Scene:
+         lam=1e-4, rtol=1e-8, outlier_frac=0.0) -> Scene:
     """Cameras on a ring of ``radius`` looking at points uniform in [-2, 2]^3;
     each point is seen by kmin..kmax random cameras (tiny plain FP64 scene)."""
     rng = np.random.default_rng(seed)
@@ -138,7 +145,7 @@ def ring(seed=0, n_cams=32, n_pts=4000, kmin=4, kmax=8, radius=10.0, sigma=0.5,
     pt_idx = np.concatenate(pt_idx)
     return _assemble("ring", rng, Rm, centres, f, k1, k2, X, cam_idx, pt_idx, sigma,
                      rel_pert=0.01, trans_pert=0.01 * radius, point_pert=0.01 * radius * 0.2,
-                     lam=lam, rtol=rtol)
+                     lam=lam, rtol=rtol, outlier_frac=outlier_frac)
 
 
 def _path(n, spacing, wiggle_amp, wiggle_len, rng):
