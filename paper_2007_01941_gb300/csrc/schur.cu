@@ -887,20 +887,27 @@ k_explicit_pairs(const T* __restrict__ W, int nnzb, const int* __restrict__ blk_
     for (int i = lane; i < 81; i += 32) out[i] = (T)Scc[(size_t)c * 81 + i];
     return;
   }
-  const int la = lane / 3, lg = lane - 3 * la;   // lane -> (row a, column group g)
+  // lane -> (row a, column group g); lanes 27..31 repeat lane 0's loads and discard them
+  const int la = lane < 27 ? lane / 3 : 0, lg = lane < 27 ? lane - 3 * (lane / 3) : 0;
   T s0 = T(0), s1 = T(0), s2 = T(0);
-  if (lane < 27) {
-    const int q1 = pair_ptr[e + 1];
-#pragma unroll 2
-    for (int q = pair_ptr[e]; q < q1; ++q) {
-      const int2 pr = __ldg(pairs + q);
-      const T* wi = W + (size_t)pr.x * kWld + la;
-      const T* wj = W + (size_t)pr.y * kWld + 3 * lg;
+  const int q0 = pair_ptr[e], q1 = pair_ptr[e + 1];
+  // the warp reads 32 pairs' indices at once and hands them out by shuffles, so the
+  // gathers of consecutive pairs do not wait on each other's index loads
+  for (int base = q0; base < q1; base += 32) {
+    const int2 mine = base + lane < q1 ? __ldg(pairs + base + lane) : make_int2(0, 0);
+    const int cnt = min(32, q1 - base);
+#pragma unroll 4
+    for (int k = 0; k < cnt; ++k) {
+      const int pi = __shfl_sync(kFull, mine.x, k), pj = __shfl_sync(kFull, mine.y, k);
+      const T* wi = W + (size_t)pi * kWld + la;
+      const T* wj = W + (size_t)pj * kWld + 3 * lg;
       const T a0 = __ldg(wi), a1 = __ldg(wi + 9), a2 = __ldg(wi + 18);
       s0 += a0 * __ldg(wj) + a1 * __ldg(wj + 9) + a2 * __ldg(wj + 18);
       s1 += a0 * __ldg(wj + 1) + a1 * __ldg(wj + 10) + a2 * __ldg(wj + 19);
       s2 += a0 * __ldg(wj + 2) + a1 * __ldg(wj + 11) + a2 * __ldg(wj + 20);
     }
+  }
+  if (lane < 27) {
     T* o = out + 9 * la + 3 * lg;
     o[0] = -s0;
     o[1] = -s1;

@@ -183,15 +183,19 @@ __global__ void __launch_bounds__(256) k_ph_restrict(VLevel<T> L, VLevel<T> C, c
   const int lane = threadIdx.x & 31;
   const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (a >= C.n) return;
+  // lane s + 16h adds members h, h + 2, ... of the aggregate into output s
+  const int s = lane & 15, h = lane >> 4;
   T acc = T(0);
-  if (lane < 16)
-    for (int m = L.agg_ptr[a]; m < L.agg_ptr[a + 1]; ++m) {
-      const int i = L.agg_mem[m];
-      const T* Qi = L.Q + (size_t)i * BS * 16 + lane;
-      const T* ri = res + (size_t)i * BS;
+  const int m1 = L.agg_ptr[a + 1];
+  for (int m = L.agg_ptr[a] + h; m < m1; m += 2) {
+    const int i = L.agg_mem[m];
+    const T* Qi = L.Q + (size_t)i * BS * 16 + s;
+    const T* ri = res + (size_t)i * BS;
 #pragma unroll
-      for (int u = 0; u < BS; ++u) acc += Qi[u * 16] * ri[u];
-    }
+    for (int u = 0; u < BS; ++u) acc += Qi[u * 16] * ri[u];
+  }
+  acc += __shfl_xor_sync(kFull, acc, 16);
+  if (lane >= 16) acc = T(0);
   const size_t idx = (size_t)a * 16 + lane;
   if (lane < 16) C.b[idx] = acc;
   if (C.coarsest) return;
