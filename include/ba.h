@@ -69,6 +69,13 @@ typedef enum { BA_OUTER_FP64 = 0, BA_OUTER_PAIRED_FP32 = 1 } ba_outer_product;
  * quadratic model Q_i = 1/2 x_i^T S x_i - x_i^T b (Q_0 = 0), evaluated from the CG
  * recurrence Q_i - Q_{i-1} = -alpha_i (r_{i-1}^T z_{i-1}) / 2. */
 typedef enum { BA_STOP_RELRES = 0, BA_STOP_NASH_SOFER = 1 } ba_stop_rule;
+/* Loss on the squared residual norm s_o = |f_o|^2 (Section 5's robust error metric):
+ * SQUARED rho(s) = s; HUBER rho(s) = s for s <= a^2 and 2 a sqrt(s) - a^2 beyond
+ * (a = loss_scale; the paper's a = 1 pixel).  The objective is 1/2 sum_o rho(s_o).  With
+ * HUBER each residual and its Jacobian blocks are scaled by w_o = sqrt(rho'(s_o))
+ * (1 inside, (a^2 / s_o)^(1/4) outside) before the Schur reduction, the corrected
+ * Gauss-Newton model of Triggs et al. (exact here since rho'' <= 0). */
+typedef enum { BA_LOSS_SQUARED = 0, BA_LOSS_HUBER = 1 } ba_loss;
 
 typedef struct {
   double lambda;        /* LM damping used by ba_lm_step's first call (Section 5: 1/1e4) */
@@ -94,10 +101,16 @@ typedef struct {
   double tau;           /* Nash-Sofer tolerance (0.1; Section 5 uses 0.1 and 0.01) */
   int overlap_launches; /* 1: launch the PCG loop's kernels as programmatic dependent launches,
                            so each is scheduled while its predecessor finishes (1) */
+  int loss;             /* ba_loss (BA_LOSS_SQUARED) */
+  double loss_scale;    /* a of BA_LOSS_HUBER, in residual units (1.0) */
 } ba_options;
 
 /* Fills *opt with the defaults listed above. */
 void ba_default_options(ba_options* opt);
+
+/* sizeof(ba_options) and sizeof(ba_info) of this build, so that a binding can check its
+ * copy of the two layouts before passing them. */
+size_t ba_struct_size(int which); /* 0: ba_options, 1: ba_info; 0 for anything else */
 
 /* Creates a problem for a fixed observation graph (Section 2.1: cameras x_c, points x_p).
  * cam_idx, pt_idx: device int32 [n_obs], the camera and point of each observation; they
@@ -116,8 +129,9 @@ void ba_destroy(ba_problem* prob);
 const char* ba_last_error(const ba_problem* prob);
 
 /* Linearises at (cams, pts) (Section 2.1, Eq. 1-2): residuals f_o = pi(cam, X) - obs_o,
- * F_o = df_o/dcam (2x9), E_o = df_o/dX (2x3) for the 9-parameter angle-axis camera.
- * cost_out: host double, receives 1/2 sum |f_o|^2 (may be NULL). */
+ * F_o = df_o/dcam (2x9), E_o = df_o/dX (2x3) for the 9-parameter angle-axis camera,
+ * each scaled by w_o under BA_LOSS_HUBER.  cost_out: host double, receives
+ * 1/2 sum rho(|f_o|^2) (1/2 sum |f_o|^2 for the squared loss; may be NULL). */
 ba_status ba_linearize(ba_problem* prob, const double* cams, const double* pts,
                        const double* obs, double* cost_out);
 
@@ -154,7 +168,8 @@ ba_status ba_lm_step(ba_problem* prob, double* cams, double* pts, const double* 
  * (n_cams x 9) and dL/dpts (n_pts x 3) at the linearisation point, holding lambda
  * fixed and differentiating through D = lambda diag(J^T J).  Uses a second PCG solve
  * with S and the same multigrid hierarchy.  Requires a completed ba_pcg_solve with
- * rhs = NULL.  Any output may be NULL. */
+ * rhs = NULL and the squared loss (BA_ERR_INVALID_ARG under BA_LOSS_HUBER).  Any output
+ * may be NULL. */
 ba_status ba_adjoint(ba_problem* prob, const double* dL_ddelta, double* dL_dobs,
                      double* dL_dcams, double* dL_dpts);
 
@@ -218,7 +233,10 @@ typedef enum {
   BA_KT_SCHUR_FP32 = 1,  /* implicit Schur product, FP32 storage (inside the V-cycle) */
   BA_KT_LINEARIZE = 2,   /* residual + Jacobian kernel */
   BA_KT_SCHUR_DF = 3,    /* implicit Schur product in paired FP32 (outer operator, mixed mode) */
-  BA_KT_COUNT = 4
+  BA_KT_ASSEMBLY = 4,    /* off-diagonal blocks of the assembled level-0 S (observation pairs) */
+  BA_KT_OUTER_BSR = 5,   /* PCG product with the FP64 blocks of the assembled S */
+  BA_KT_VCYCLE = 6,      /* one whole preconditioner application (all of a V-cycle's kernels) */
+  BA_KT_COUNT = 7
 } ba_kernel_class;
 
 /* enable != 0 starts recording a CUDA event pair around every launch of the timed

@@ -17,8 +17,10 @@ BA_PRECOND_NONE, BA_PRECOND_JACOBI, BA_PRECOND_MG = 0, 1, 2
 BA_OP_IMPLICIT, BA_OP_EXPLICIT, BA_OP_AUTO = 0, 1, 2
 BA_DAMP_MARQUARDT, BA_DAMP_IDENTITY = 0, 1
 BA_KT_SCHUR_FP64, BA_KT_SCHUR_FP32, BA_KT_LINEARIZE, BA_KT_SCHUR_DF = 0, 1, 2, 3
+BA_KT_ASSEMBLY, BA_KT_OUTER_BSR, BA_KT_VCYCLE = 4, 5, 6
 BA_OUTER_FP64, BA_OUTER_PAIRED_FP32 = 0, 1
 BA_STOP_RELRES, BA_STOP_NASH_SOFER = 0, 1
+BA_LOSS_SQUARED, BA_LOSS_HUBER = 0, 1
 
 (BA_ARR_RESIDUAL, BA_ARR_JAC_F, BA_ARR_JAC_E, BA_ARR_DAMP_C, BA_ARR_DAMP_P, BA_ARR_CINV,
  BA_ARR_GRAD_C, BA_ARR_GRAD_P, BA_ARR_RHS, BA_ARR_LEVEL_ROWPTR, BA_ARR_LEVEL_COLS,
@@ -34,7 +36,8 @@ class Options(ctypes.Structure):
                 ("post_smooth", c_int), ("lanczos_steps", c_int), ("coarse_max_nodes", c_int),
                 ("max_levels", c_int), ("cheb_lo", c_double), ("cheb_hi", c_double),
                 ("level0_operator", c_int), ("fused_vcycle", c_int), ("outer_product", c_int),
-                ("stop_rule", c_int), ("tau", c_double), ("overlap_launches", c_int)]
+                ("stop_rule", c_int), ("tau", c_double), ("overlap_launches", c_int),
+                ("loss", c_int), ("loss_scale", c_double)]
 
 
 class Info(ctypes.Structure):
@@ -50,6 +53,7 @@ _lib = None
 # name -> (restype, argtypes)
 _SIGS = {
     "ba_default_options": (None, [POINTER(Options)]),
+    "ba_struct_size": (c_size_t, [c_int]),
     "ba_create": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, POINTER(Options), c_void_p,
                           POINTER(c_void_p)]),
     "ba_destroy": (None, [c_void_p]),
@@ -88,6 +92,10 @@ def load(path: Path | str | None = None):
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
+    for which, st in ((0, Options), (1, Info)):
+        if lib.ba_struct_size(which) != ctypes.sizeof(st):
+            raise RuntimeError(f"{p}: {st.__name__} layout differs from the library's "
+                               f"({ctypes.sizeof(st)} vs {lib.ba_struct_size(which)} bytes); rebuild")
     _lib = lib
     return lib
 

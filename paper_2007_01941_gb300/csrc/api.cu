@@ -1,6 +1,7 @@
 // extern "C" entry points of ba.h: argument checks, stage bookkeeping and the
 // conversion of internal errors into ba_status codes.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "ba_internal.h"
@@ -96,6 +97,12 @@ void ba_default_options(ba_options* o) {
   o->stop_rule = BA_STOP_RELRES;
   o->tau = 0.1;
   o->overlap_launches = 1;
+  o->loss = BA_LOSS_SQUARED;
+  o->loss_scale = 1.0;
+}
+
+size_t ba_struct_size(int which) {
+  return which == 0 ? sizeof(ba_options) : which == 1 ? sizeof(ba_info) : 0;
 }
 
 ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx, const int32_t* pt_idx,
@@ -128,6 +135,9 @@ ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx, co
                "bad outer_product");
     BA_REQUIRE(o.stop_rule == BA_STOP_RELRES || (o.stop_rule == BA_STOP_NASH_SOFER && o.tau > 0.0),
                BA_ERR_INVALID_ARG, "bad stop_rule / tau");
+    BA_REQUIRE(o.loss == BA_LOSS_SQUARED || (o.loss == BA_LOSS_HUBER && o.loss_scale > 0.0 &&
+                                             std::isfinite(o.loss_scale)),
+               BA_ERR_INVALID_ARG, "bad loss / loss_scale");
     int dev = 0;
     BA_CUDA(cudaGetDevice(&dev));
     BA_CUDA(cudaDeviceGetAttribute(&P->n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -166,7 +176,7 @@ void ba_destroy(ba_problem* P) {
     ba::DBuf* lb[] = {&L.row_ptr, &L.cols, &L.W, &L.vals64, &L.vals32, &L.sptr, &L.sidx, &L.agg, &L.agg_ptr,
                       &L.agg_mem, &L.K, &L.Q64, &L.Q32, &L.kept, &L.Dblk, &L.Dinv64, &L.Dinv32, &L.cheb,
                       &L.Ainv, &L.vx, &L.vb, &L.vr, &L.vd, &L.vq, &L.vt, &L.vs, &L.pair_ptr, &L.pairs,
-                      &L.blk_row};
+                      &L.blk_row, &L.up_blk, &L.mirror};
     for (ba::DBuf* b : lb) b->release();
   }
   if (P->h_scal) cudaFreeHost(P->h_scal);
@@ -272,6 +282,8 @@ ba_status ba_adjoint(ba_problem* P, const double* dL_ddelta, double* dL_dobs, do
   return guard(P, [&] {
     require_stage(P, 4, "ba_adjoint needs a completed solve (ba_pcg_solve with rhs = NULL, or ba_lm_step)");
     BA_REQUIRE(dL_ddelta, BA_ERR_INVALID_ARG, "null cotangent");
+    BA_REQUIRE(P->opt.loss == BA_LOSS_SQUARED, BA_ERR_INVALID_ARG,
+               "ba_adjoint differentiates the squared loss only");
     ba::adjoint(P, dL_ddelta, dL_dobs, dL_dcams, dL_dpts);
   });
 }
@@ -390,9 +402,9 @@ ba_status ba_get_array(ba_problem* P, int which, int level, void* dst, size_t by
       case BA_ARR_RESIDUAL:
         k_rec_to_user<<<go, 256, 0, P->stream>>>(P->fres.as<double>(), 2, 0, 2, n_o, P->obs_user.as<int>(), d); break;
       case BA_ARR_JAC_F:
-        k_rec_to_user<<<go, 256, 0, P->stream>>>(P->J64.as<double>(), ba::kRec, 0, 18, n_o, P->obs_user.as<int>(), d); break;
+        k_rec_to_user<<<go, 256, 0, P->stream>>>(ba::jacobian64(P), ba::kRec, 0, 18, n_o, P->obs_user.as<int>(), d); break;
       case BA_ARR_JAC_E:
-        k_rec_to_user<<<go, 256, 0, P->stream>>>(P->J64.as<double>(), ba::kRec, 18, 6, n_o, P->obs_user.as<int>(), d); break;
+        k_rec_to_user<<<go, 256, 0, P->stream>>>(ba::jacobian64(P), ba::kRec, 18, 6, n_o, P->obs_user.as<int>(), d); break;
       case BA_ARR_DAMP_C: D2D(P->Dc.p, need); break;
       case BA_ARR_GRAD_C: D2D(P->gc.p, need); break;
       case BA_ARR_RHS: D2D(P->rhs.p, need); break;
@@ -408,7 +420,7 @@ ba_status ba_get_array(ba_problem* P, int which, int level, void* dst, size_t by
       case BA_ARR_LEVEL_W: D2D(L->W.p, need); break;
       case BA_ARR_LEVEL_VALS: {
         const size_t n = (size_t)L->nnzb * L->bs * L->bs;
-        if (P->opt.precision == BA_MIXED)
+        if (P->opt.precision == BA_MIXED && !(level == 0 && P->outer_explicit))
           k_f2d<<<ba::cdiv((long long)std::max<size_t>(n, 1), 256), 256, 0, P->stream>>>(n, L->vals32.as<float>(), d);
         else
           D2D(L->vals64.p, need);

@@ -101,7 +101,9 @@ struct Level {
   int n_agg = 0;
   int agg_max = 1;              // members of the largest aggregate
   DBuf agg_ptr, agg_mem;        // member lists of the next-level nodes
-  DBuf pair_ptr, pairs, blk_row; // level 0: observation pairs per block (int [nnzb+1], int2), block rows
+  DBuf pair_ptr, pairs, blk_row; // level 0: observation pairs per work block (int [n_up+1], int2), block rows
+  DBuf up_blk, mirror;          // level 0: blocks on and above the diagonal and their transposes
+  int n_up = 0;
   DBuf K;                       // double [n][bs][16] near-nullspace rows
   DBuf Q64, Q32;                // double/float [n][bs][16] prolongator blocks
   DBuf kept;                    // uint32 [n] kept-dof masks of this level's nodes
@@ -139,7 +141,9 @@ struct ba_problem {
   int k3_grid[2] = {0, 0};       // Schur product CTAs per launch (FP32, FP64), set at first use
   int k3_grid_df = 0;           // the same for the paired-FP32 product
   bool l0_explicit = false;     // V-cycle level 0 uses the assembled S (set by the multigrid setup)
+  bool outer_explicit = false;  // the PCG product uses the FP64 blocks of the assembled S
   bool vc_ready = false;        // the fused-phase V-cycle applies (set by the multigrid setup)
+  bool j64_valid = false;       // J64 holds the current records (mixed precision forms it on demand)
   ba::DBuf lz_vec, lz_red, lz_cnt, lz_ptr;  // batched Lanczos vectors, reductions, counters, pointers
   unsigned k3_calls = 0;        // alternates the tile order of successive Schur products
   ba::DBuf tile_pt;             // int32 [n_tiles + 1] point ranges of <=32-obs warp tiles
@@ -269,6 +273,9 @@ void build_graph(ba_problem* P, const int32_t* cam_idx_dev, const int32_t* pt_id
 // ---- linearisation (linearize.cu) ------------------------------------------
 void linearize(ba_problem* P, const double* cams, const double* pts, const double* obs);
 double cost_at(ba_problem* P, const double* cams, const double* pts, const double* obs);
+// the FP64 Jacobian records; in mixed precision formed on first use from J32 + J32lo
+// (exactly the doubles the paired-FP32 linearisation computed), never inside a capture
+double* jacobian64(ba_problem* P);
 
 // ---- Schur reduction and implicit operator (schur.cu) -----------------------
 void schur_setup(ba_problem* P, double lambda);
@@ -284,7 +291,10 @@ void matvec_df_accumulate(ba_problem* P, double* y);                   // y += S
 void lanczos_batched(ba_problem* P, int first, int last);  // levels first..last, all assembled
 void fused_vcycle_setup(ba_problem* P);
 void fused_vcycle(ba_problem* P, const double* r, double* z);
-void explicit_schur(ba_problem* P, Level& L0, bool fp32);
+// assembled level-0 S: FP32 blocks only (the Galerkin product's input), FP64 blocks, or
+// paired-FP32 arithmetic giving the FP64 blocks and their FP32 roundings
+enum ExplicitMode { EX_FP32, EX_FP64, EX_PAIRED };
+void explicit_schur(ba_problem* P, Level& L0, ExplicitMode mode);
 void back_substitute_to(ba_problem* P, const double* dc, double* out_int, double* out_user);
 void reduced_rhs(ba_problem* P, const double* vc, const double* vp_user, double* out);
 

@@ -178,6 +178,19 @@ __device__ __forceinline__ void project_obs(const double* __restrict__ cam, cons
   project_obs_t<JAC, double>(c9, cr, cx[18] != 0.0, X, ob, out);
 }
 
+// Robust loss of Section 5 on s = |f_o|^2: returns w = sqrt(rho'(s)) and sets half_rho =
+// rho(s) / 2; ha > 0 selects Huber with scale ha (rho = s inside ha^2, 2 ha sqrt(s) - ha^2
+// beyond, so w = (ha^2 / s)^(1/4) there), ha <= 0 the squared loss (w = 1)
+__device__ __forceinline__ double robust_weight(double s, double ha, double& half_rho) {
+  if (ha > 0.0 && s > ha * ha) {
+    const double rs = sqrt(s);
+    half_rho = ha * rs - 0.5 * ha * ha;
+    return sqrt(ha / rs);
+  }
+  half_rho = 0.5 * s;
+  return 1.0;
+}
+
 template <bool JAC, bool MIXED>
 __global__ void __launch_bounds__(kLinBS)
 k_linearize(const double* __restrict__ cams, const double* __restrict__ pts,
@@ -185,7 +198,7 @@ k_linearize(const double* __restrict__ cams, const double* __restrict__ pts,
             const int* __restrict__ obs_cam, const int* __restrict__ obs_ptu,
             const int* __restrict__ obs_user, int n_o, size_t ld, double* __restrict__ fres,
             double* __restrict__ J64, float* __restrict__ J32, float* __restrict__ J32lo,
-            double* partial, unsigned* counter, double* cost_out, int* flags) {
+            double* partial, unsigned* counter, double* cost_out, int* flags, double ha) {
   double acc = 0.0;
   for (int o = blockIdx.x * kLinBS + threadIdx.x; o < n_o; o += gridDim.x * kLinBS) {
     const int c = obs_cam[o];
@@ -195,7 +208,19 @@ k_linearize(const double* __restrict__ cams, const double* __restrict__ pts,
     const double ob[2] = {obs[2 * ou], obs[2 * ou + 1]};
     CamObs v;
     project_obs<JAC>(cams + 9 * c, camx + (size_t)kCamx * c, X, ob, v);
-    acc += 0.5 * (v.res[0] * v.res[0] + v.res[1] * v.res[1]);
+    double half_rho;
+    const double w = robust_weight(v.res[0] * v.res[0] + v.res[1] * v.res[1], ha, half_rho);
+    acc += half_rho;
+    if (w != 1.0) {
+      v.res[0] *= w;
+      v.res[1] *= w;
+      if (JAC) {
+#pragma unroll
+        for (int k = 0; k < 18; ++k) v.F[k] *= w;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v.E[k] *= w;
+      }
+    }
     if (fres) reinterpret_cast<double2*>(fres)[o] = make_double2(v.res[0], v.res[1]);
     if (JAC) {
       bool finite = isfinite(v.res[0]) && isfinite(v.res[1]);
@@ -230,14 +255,15 @@ k_linearize(const double* __restrict__ cams, const double* __restrict__ pts,
 
 // The mixed-precision linearisation: the camera model of project_obs_t in paired FP32
 // (DF), from the per-camera split of camdf and the points and observations split on
-// load.  Writes the residuals and the FP64 records (as hi + lo) and, directly from the
-// pairs, the FP32 records (hi) and their remainders (lo).
+// load.  Writes the residuals and, directly from the pairs, the FP32 records (hi) and
+// their remainders (lo); the FP64 records (hi + lo) only when J64 is given.
 template <bool JAC>
 __global__ void __launch_bounds__(kLinBS)
 k_linearize_df(const double* __restrict__ pts, const double* __restrict__ obs, const float2* __restrict__ camdf,
                const int* __restrict__ obs_cam, const int* __restrict__ obs_ptu, const int* __restrict__ obs_user,
                int n_o, double* __restrict__ fres, double* __restrict__ J64, float* __restrict__ J32,
-               float* __restrict__ J32lo, double* partial, unsigned* counter, double* cost_out, int* flags) {
+               float* __restrict__ J32lo, double* partial, unsigned* counter, double* cost_out, int* flags,
+               double ha) {
   double acc = 0.0;
   for (int o = blockIdx.x * kLinBS + threadIdx.x; o < n_o; o += gridDim.x * kLinBS) {
     const int c = obs_cam[o];
@@ -260,8 +286,14 @@ k_linearize_df(const double* __restrict__ pts, const double* __restrict__ obs, c
     const DF ob[2] = {DF(obs[2 * ou]), DF(obs[2 * ou + 1])};
     CamObsT<DF> v;
     project_obs_t<JAC, DF>(cam, cx, small, X, ob, v);
-    const double r0 = to_double(v.res[0]), r1 = to_double(v.res[1]);
-    acc += 0.5 * (r0 * r0 + r1 * r1);
+    double r0 = to_double(v.res[0]), r1 = to_double(v.res[1]);
+    double half_rho;
+    const double w = robust_weight(r0 * r0 + r1 * r1, ha, half_rho);
+    acc += half_rho;
+    if (w != 1.0) {
+      r0 *= w;
+      r1 *= w;
+    }
     if (fres) reinterpret_cast<double2*>(fres)[o] = make_double2(r0, r1);
     if (JAC) {
       bool finite = isfinite(r0) && isfinite(r1);
@@ -270,11 +302,18 @@ k_linearize_df(const double* __restrict__ pts, const double* __restrict__ obs, c
       for (int k = 0; k < 18; ++k) rec[k] = v.F[k];
 #pragma unroll
       for (int k = 0; k < 6; ++k) rec[18 + k] = v.E[k];
+      if (w != 1.0) {
+        const DF wd(w);
+#pragma unroll
+        for (int k = 0; k < kRec; ++k) rec[k] = rec[k] * wd;
+      }
 #pragma unroll
       for (int k = 0; k < kRec; ++k) finite = finite && isfinite(rec[k].h);
-      double2* d64 = reinterpret_cast<double2*>(J64 + (size_t)o * kRec);
+      if (J64) {
+        double2* d64 = reinterpret_cast<double2*>(J64 + (size_t)o * kRec);
 #pragma unroll
-      for (int k = 0; k < kRec / 2; ++k) d64[k] = make_double2(to_double(rec[2 * k]), to_double(rec[2 * k + 1]));
+        for (int k = 0; k < kRec / 2; ++k) d64[k] = make_double2(to_double(rec[2 * k]), to_double(rec[2 * k + 1]));
+      }
       float4* d32 = reinterpret_cast<float4*>(J32 + (size_t)o * kRec);
       float4* l32 = reinterpret_cast<float4*>(J32lo + (size_t)o * kRec);
 #pragma unroll
@@ -293,6 +332,11 @@ static void camera_rotation(ba_problem* P, const double* cams, double* camx, flo
   launched(P);
 }
 
+// the kernels' loss argument: the Huber scale a, or 0 for the squared loss
+static double huber_scale(const ba_problem* P) {
+  return P->opt.loss == BA_LOSS_HUBER ? P->opt.loss_scale : 0.0;
+}
+
 static int lin_grid(ba_problem* P) {
   int g = cdiv(P->n_o, kLinBS);
   return std::max(1, std::min(g, P->n_sm * 8));
@@ -304,7 +348,8 @@ void linearize(ba_problem* P, const double* cams, const double* pts, const doubl
   P->graph_epoch++;
   P->camx.ensure(sizeof(double) * kCamx * std::max(P->n_c, 1));
   P->fres.ensure(sizeof(double) * 2 * ld);
-  P->J64.ensure(sizeof(double) * kRec * ld);
+  if (!mixed) P->J64.ensure(sizeof(double) * kRec * ld);
+  P->j64_valid = !mixed;
   if (mixed) {
     P->J32.ensure(sizeof(float) * kRec * ld);
     P->J32lo.ensure(sizeof(float) * kRec * ld);
@@ -327,14 +372,34 @@ void linearize(ba_problem* P, const double* cams, const double* pts, const doubl
   if (mixed)
     k_linearize_df<true><<<g, kLinBS, 0, P->stream>>>(
         pts, obs, P->camdf.as<float2>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(), P->obs_user.as<int>(), P->n_o,
-        P->fres.as<double>(), P->J64.as<double>(), P->J32.as<float>(), P->J32lo.as<float>(), P->partial.as<double>(),
-        P->counter.as<unsigned>(), cost, P->flags.as<int>());
+        P->fres.as<double>(), nullptr, P->J32.as<float>(), P->J32lo.as<float>(), P->partial.as<double>(),
+        P->counter.as<unsigned>(), cost, P->flags.as<int>(), huber_scale(P));
   else
     k_linearize<true, false><<<g, kLinBS, 0, P->stream>>>(
         cams, pts, obs, P->camx.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
         P->obs_user.as<int>(), P->n_o, ld, P->fres.as<double>(), P->J64.as<double>(), nullptr, nullptr,
-        P->partial.as<double>(), P->counter.as<unsigned>(), cost, P->flags.as<int>());
+        P->partial.as<double>(), P->counter.as<unsigned>(), cost, P->flags.as<int>(), huber_scale(P));
   launched(P);
+}
+
+__global__ void k_pair_sum(size_t n, const float* __restrict__ hi, const float* __restrict__ lo,
+                           double* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)hi[i] + (double)lo[i];
+}
+
+double* jacobian64(ba_problem* P) {
+  if (!P->j64_valid) {
+    P->J64.ensure(sizeof(double) * kRec * P->ld);
+    const size_t n = (size_t)kRec * P->n_o;
+    if (n) {
+      k_pair_sum<<<cdiv((long long)n, 256), 256, 0, P->stream>>>(n, P->J32.as<float>(), P->J32lo.as<float>(),
+                                                                 P->J64.as<double>());
+      launched(P);
+    }
+    P->j64_valid = true;
+  }
+  return P->J64.as<double>();
 }
 
 double cost_at(ba_problem* P, const double* cams, const double* pts, const double* obs) {
@@ -349,13 +414,13 @@ double cost_at(ba_problem* P, const double* cams, const double* pts, const doubl
     k_linearize_df<false><<<g, kLinBS, 0, P->stream>>>(
         pts, obs, camdf, P->obs_cam.as<int>(), P->obs_ptu.as<int>(), P->obs_user.as<int>(), P->n_o, nullptr, nullptr,
         nullptr, nullptr, P->partial.as<double>(), P->counter.as<unsigned>(), P->scal.as<double>() + S_COST_NEW,
-        P->flags.as<int>());
+        P->flags.as<int>(), huber_scale(P));
   else
     k_linearize<false, false><<<g, kLinBS, 0, P->stream>>>(
         cams, pts, obs, P->scratch2.as<double>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(),
         P->obs_user.as<int>(), P->n_o, P->ld, nullptr, nullptr, nullptr, nullptr,
         P->partial.as<double>(), P->counter.as<unsigned>(), P->scal.as<double>() + S_COST_NEW,
-        P->flags.as<int>());
+        P->flags.as<int>(), huber_scale(P));
   launched(P);
   fetch_scalars(P, S_COST_NEW, 1);
   return P->h_scal[S_COST_NEW];

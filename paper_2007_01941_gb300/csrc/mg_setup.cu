@@ -1323,15 +1323,19 @@ void mg_setup(ba_problem* P) {
   clear_flags(P);
   if (!P->sym_ready) mg_symbolic(P);
   Level& L0 = P->levels[0];
-  explicit_schur(P, L0, fp32);
   {
-    // Section 3.6: each level uses the cheaper of the implicit and the assembled operator
+    // Section 3.6: each level uses the cheaper of the implicit and the assembled operator;
+    // level 0 is S itself, so the choice covers the PCG product as well
     const size_t elem = fp32 ? 4 : 8;
     const double explicit_bytes = (double)L0.nnzb * (81.0 * elem + 4.0);
     const double implicit_bytes = (double)P->n_o * (24.0 * elem + 4.0) + (double)P->n_p * 6.0 * elem;
     P->l0_explicit = o.level0_operator == BA_OP_EXPLICIT ||
                      (o.level0_operator == BA_OP_AUTO && explicit_bytes < implicit_bytes);
+    P->outer_explicit = P->l0_explicit;
   }
+  // the Galerkin product needs S assembled in any case; the PCG product needs its FP64
+  // value, which mixed precision forms in paired FP32
+  explicit_schur(P, L0, !fp32 ? EX_FP64 : P->outer_explicit ? EX_PAIRED : EX_FP32);
   // level-0 smoother blocks: S_cc from the Schur setup
   L0.Dblk.ensure(sizeof(double) * 81 * (size_t)P->n_c + 64);
   L0.Dinv64.ensure(sizeof(double) * 81 * (size_t)P->n_c + 64);

@@ -398,6 +398,66 @@ __global__ void k_camera_setup_df(const float* __restrict__ Jh, const float* __r
   }
 }
 
+// S_cc = D_c + sum_{o in c} F_o^T N_o F_o, N_o = I - E_o C_p^-1 E_o^T, in DF (the
+// counterpart of k_scc): A_cc and the point terms cancel in S_cc, so its FP64 value,
+// which the assembled S and the point-block-Jacobi blocks take, needs the extra bits.
+// Warp per camera, lane per observation, the 45 upper entries summed over the warp.
+__global__ void __launch_bounds__(128)
+k_scc_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const float* __restrict__ Ch,
+         const float* __restrict__ Cl, size_t ldp, const int* __restrict__ cam_ptr, const int* __restrict__ cam_obs,
+         const int* __restrict__ obs_pt, const double* __restrict__ Dc, int n_c, double* __restrict__ Scc) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= n_c) return;
+  DF acc[45];
+#pragma unroll
+  for (int k = 0; k < 45; ++k) acc[k] = DF(0.f, 0.f);
+  for (int i = cam_ptr[c] + lane; i < cam_ptr[c + 1]; i += 32) {
+    const int o = cam_obs[i];
+    const int ip = obs_pt[o];
+    DF e[6], ci[6], f[18];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) e[k] = rec_df(Jh, Jl, o, 18 + k);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ci[k] = DF(__ldg(Ch + k * ldp + ip), __ldg(Cl + k * ldp + ip));
+#pragma unroll
+    for (int k = 0; k < 18; ++k) f[k] = rec_df(Jh, Jl, o, k);
+    // Y = E C^-1 (2x3), N = I - Y E^T (2x2, symmetric)
+    DF y0[3], y1[3];
+    y0[0] = e[0] * ci[0] + e[1] * ci[1] + e[2] * ci[2];
+    y0[1] = e[0] * ci[1] + e[1] * ci[3] + e[2] * ci[4];
+    y0[2] = e[0] * ci[2] + e[1] * ci[4] + e[2] * ci[5];
+    y1[0] = e[3] * ci[0] + e[4] * ci[1] + e[5] * ci[2];
+    y1[1] = e[3] * ci[1] + e[4] * ci[3] + e[5] * ci[4];
+    y1[2] = e[3] * ci[2] + e[4] * ci[4] + e[5] * ci[5];
+    const DF one(1.f, 0.f);
+    const DF n00 = one - (y0[0] * e[0] + y0[1] * e[1] + y0[2] * e[2]);
+    const DF n01 = -(y0[0] * e[3] + y0[1] * e[4] + y0[2] * e[5]);
+    const DF n11 = one - (y1[0] * e[3] + y1[1] * e[4] + y1[2] * e[5]);
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const DF ga0 = f[a] * n00 + f[9 + a] * n01;
+      const DF ga1 = f[a] * n01 + f[9 + a] * n11;
+#pragma unroll
+      for (int b = a; b < 9; ++b) acc[t++] += ga0 * f[b] + ga1 * f[9 + b];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 45; ++k) acc[k] = warp_sum_df(acc[k]);
+  if (lane == 0) {
+    double* out = Scc + 81 * (size_t)c;
+    int t = 0;
+    for (int a = 0; a < 9; ++a)
+      for (int b = a; b < 9; ++b) {
+        double v = to_double(acc[t++]);
+        if (a == b) v += Dc[9 * c + a];
+        out[9 * a + b] = v;
+        out[9 * b + a] = v;
+      }
+  }
+}
+
 // delta_p = C_p^-1 (v_p - sum_{o in p} E_o^T F_o delta_c), delta_c given as float pairs
 __global__ void k_back_substitute_df(const float* __restrict__ Jh, const float* __restrict__ Jl,
                                      const double* __restrict__ Cinv, size_t ldp, const int* __restrict__ pt_ptr,
@@ -495,22 +555,24 @@ void schur_setup(ba_problem* P, double lambda) {
         P->Dc32.as<float>(), P->gc.as<double>(), P->rhs.as<double>());
   else
     k_camera_setup<<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
-        P->J64.as<double>(), P->J64.as<double>(), P->fres.as<double>(), P->ld, P->cam_ptr.as<int>(),
+        jacobian64(P), jacobian64(P), P->fres.as<double>(), P->ld, P->cam_ptr.as<int>(),
         P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->wp.as<double>(), ldp, n_c, lambda, damp_id,
         P->Dc.as<double>(), P->Dc32.as<float>(), P->gc.as<double>(), P->rhs.as<double>());
   launched(P);
   // point-block-Jacobi blocks S_cc (in the mode's storage precision) and FP64 inverses
   double* Scc = P->Scc.as<double>();
   if (mixed)
-    k_scc<float><<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
-        P->J32.as<float>(), P->J32.as<float>(), P->ld, P->Cinv32.as<float>(), ldp, P->cam_ptr.as<int>(),
-        P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->Dc.as<double>(), n_c, Scc);
+    k_scc_df<<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
+        P->J32.as<float>(), P->J32lo.as<float>(), P->Cinv32.as<float>(), P->Cinv32lo.as<float>(), ldp,
+        P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->Dc.as<double>(), n_c, Scc);
   else
     k_scc<double><<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
         P->J64.as<double>(), P->J64.as<double>(), P->ld, P->Cinv64.as<double>(), ldp,
         P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->Dc.as<double>(), n_c, Scc);
   launched(P);
   block_inverse(P, Scc, n_c, 9, P->Scc_inv.as<double>(), P->Scc_inv32.as<float>(), F_NOT_SPD_JACOBI);
+  // the PCG graph captures the FP64 outer product, so its records must exist beforehand
+  if (mixed && !outer_df(P)) jacobian64(P);
   check_flags(P);
 }
 
@@ -788,7 +850,8 @@ void matvec64(ba_problem* P, const double* x, double* y) {
   const int n = 9 * P->n_c;
   k_diag_init<double, double><<<cdiv(n, 256), 256, 0, P->stream>>>(P->Dc.as<double>(), x, y, n);
   launched(P);
-  launch_matvec<double>(P, P->J64.as<double>(), P->J64.as<double>(), P->Cinv64.as<double>(), x, y);
+  double* J = jacobian64(P);
+  launch_matvec<double>(P, J, J, P->Cinv64.as<double>(), x, y);
 }
 
 void matvec32(ba_problem* P, const float* x, float* y) {
@@ -805,22 +868,25 @@ void matvec64_accumulate(ba_problem* P, const double* x, double* y) {
     matvec_df_accumulate(P, y);
     return;
   }
-  launch_matvec<double>(P, P->J64.as<double>(), P->J64.as<double>(), P->Cinv64.as<double>(), x, y);
+  double* J = jacobian64(P);
+  launch_matvec<double>(P, J, J, P->Cinv64.as<double>(), x, y);
 }
 void matvec32_accumulate(ba_problem* P, const float* x, float* y) {
   launch_matvec<float>(P, P->J32.as<float>(), P->J32.as<float>(), P->Cinv32.as<float>(), x, y);
 }
 
 // ---------------------------------------------------------------------------
-// explicit level-0 operator S (for the Galerkin product and, when chosen, the V-cycle's
-// finest level).  With C_p^-1 = L_p L_p^T (Cholesky) and W_o = L_p^T E_o^T F_o (3 x 9)
-// per observation o = (c, p), an off-diagonal block is
+// explicit level-0 operator S (for the Galerkin product and, when chosen, the PCG
+// product and the V-cycle's finest level).  With C_p^-1 = L_p L_p^T (Cholesky) and
+// W_o = L_p^T E_o^T F_o (3 x 9) per observation o = (c, p), an off-diagonal block is
 //   S_cc' = - sum_{p seen by c and c'} W_(c,p)^T W_(c',p),
-// and the diagonal block S_cc is the one the Schur setup already formed.  The pairs
-// (o, o') that meet in each block are listed once per problem (symbolic); k_schur_w
-// writes W (one thread per observation, rows padded to 28 entries) and k_explicit_pairs
-// gives each block to one warp, whose lane (a, g) (27 lanes) accumulates entries
-// (a, 3g .. 3g+2) over the block's pairs in registers.
+// and the diagonal block S_cc is the one the Schur setup already formed.  S is
+// symmetric, so only the blocks on and above the diagonal are work items: the pairs
+// (o, o') that meet in each upper block are listed once per problem (symbolic), and
+// each block is also written, transposed, to its mirror below the diagonal.  k_schur_w
+// writes W (one thread per observation, rows padded to 28 entries) and
+// k_explicit_pairs gives each block to one warp, whose lane (a, g) (27 lanes)
+// accumulates entries (a, 3g .. 3g+2) over the block's pairs in registers.
 // ---------------------------------------------------------------------------
 constexpr int kWld = 28;   // W row stride (entries)
 
@@ -871,53 +937,223 @@ __global__ void k_schur_w(const T* __restrict__ J, const T* __restrict__ Cinv, i
   }
 }
 
-constexpr int kExWarps = 8;
+// The same W in DF from the FP32 records and their remainders and the split C_p^-1;
+// row o holds its 27 entries as (hi, lo) pairs, padded to 28.
+__global__ void __launch_bounds__(128)
+k_schur_w_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const float* __restrict__ Ch,
+             const float* __restrict__ Cl, int ldp, const int* __restrict__ obs_pt, int n_o, float2* __restrict__ W2) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_o) return;
+  const int ip = obs_pt[o];
+  DF cv[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) cv[k] = DF(__ldg(Ch + (size_t)k * ldp + ip), __ldg(Cl + (size_t)k * ldp + ip));
+  const DF zero(0.f, 0.f), one(1.f, 0.f);
+  const DF l00 = df_sqrt(cv[0]);
+  const DF i00 = l00.h > 0.f ? one / l00 : zero;
+  const DF l10 = cv[1] * i00, l20 = cv[2] * i00;
+  const DF l11 = df_sqrt(cv[3] - l10 * l10);
+  const DF i11 = l11.h > 0.f ? one / l11 : zero;
+  const DF l21 = (cv[4] - l20 * l10) * i11;
+  const DF l22 = df_sqrt(cv[5] - l20 * l20 - l21 * l21);
+  DF e[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) e[k] = rec_df(Jh, Jl, o, 18 + k);
+  DF w[kWld];
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const DF f0 = rec_df(Jh, Jl, o, b), f1 = rec_df(Jh, Jl, o, 9 + b);
+    const DF h0 = e[0] * f0 + e[3] * f1, h1 = e[1] * f0 + e[4] * f1, h2 = e[2] * f0 + e[5] * f1;
+    w[b] = l00 * h0 + l10 * h1 + l20 * h2;
+    w[9 + b] = l11 * h1 + l21 * h2;
+    w[18 + b] = l22 * h2;
+  }
+  w[27] = zero;
+  float4* o4 = reinterpret_cast<float4*>(W2 + (size_t)o * kWld);
+#pragma unroll
+  for (int i = 0; i < kWld / 2; ++i) o4[i] = make_float4(w[2 * i].h, w[2 * i].l, w[2 * i + 1].h, w[2 * i + 1].l);
+}
+
+constexpr int kExWarps = 4;
+
+// 16-byte asynchronous global -> shared copies (completion per thread at wait_group;
+// a __syncwarp after it publishes them to the rest of the warp)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Double-buffered staging of a block's pair rows, shared by the kernels below: both W
+// rows of each of a batch's kB pairs (E bytes per entry) are copied into shared memory
+// with 16-byte asynchronous copies, so all of a batch's gathers are in flight at once
+// and the next batch loads while this one is summed.
+template <typename E, int kB>
+struct PairStage {
+  static constexpr int kV = 16 / (int)sizeof(E);   // entries per 16-byte copy
+  static constexpr int kCh = kWld / kV;            // copies per W row
+  E (*buf)[2 * kB][kWld];                          // [2][2 pair + side][entry]
+  const E* W;
+  const int2* pairs;
+  int q1, lane;
+  __device__ __forceinline__ void issue(int base, int b) {
+    const int nb = min(kB, q1 - base);
+    for (int t = lane; t < nb * 2 * kCh; t += 32) {
+      const int r = t / kCh, ch = t - r * kCh;
+      const int2 pq = __ldg(pairs + base + (r >> 1));
+      const int row = (r & 1) ? pq.y : pq.x;
+      cp_async16(&buf[b][r][ch * kV], W + (size_t)row * kWld + ch * kV);
+    }
+    cp_async_commit();
+  }
+  // waits for the batch at `base` (buffer b) after starting the next one
+  __device__ __forceinline__ void advance(int base, int b) {
+    if (base + kB < q1) {
+      issue(base + kB, b ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+  }
+};
 
 template <typename T>
 __global__ void __launch_bounds__(kExWarps * 32)
-k_explicit_pairs(const T* __restrict__ W, int nnzb, const int* __restrict__ blk_row, const int* __restrict__ cols,
-                 const int* __restrict__ pair_ptr, const int2* __restrict__ pairs, const double* __restrict__ Scc,
-                 T* __restrict__ vals) {
-  const int lane = threadIdx.x & 31;
-  const int e = blockIdx.x * kExWarps + (threadIdx.x >> 5);
-  if (e >= nnzb) return;
+k_explicit_pairs(const T* __restrict__ W, int n_up, const int* __restrict__ up_blk, const int* __restrict__ mirror,
+                 const int* __restrict__ blk_row, const int* __restrict__ cols, const int* __restrict__ pair_ptr,
+                 const int2* __restrict__ pairs, const double* __restrict__ Scc, T* __restrict__ vals) {
+  constexpr int kB = 64 / (int)sizeof(T);            // pairs per batch
+  __shared__ __align__(16) T stage[kExWarps][2][2 * kB][kWld];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int w = blockIdx.x * kExWarps + wid;
+  if (w >= n_up) return;
+  const int e = up_blk[w];
   const int c = blk_row[e];
   T* out = vals + (size_t)e * 81;
   if (cols[e] == c) {
     for (int i = lane; i < 81; i += 32) out[i] = (T)Scc[(size_t)c * 81 + i];
     return;
   }
-  // lane -> (row a, column group g); lanes 27..31 repeat lane 0's loads and discard them
+  // lane -> (row a, column group g); lanes 27..31 repeat lane 0's reads and discard them
   const int la = lane < 27 ? lane / 3 : 0, lg = lane < 27 ? lane - 3 * (lane / 3) : 0;
   T s0 = T(0), s1 = T(0), s2 = T(0);
-  const int q0 = pair_ptr[e], q1 = pair_ptr[e + 1];
-  // the warp reads 32 pairs' indices at once and hands them out by shuffles, so the
-  // gathers of consecutive pairs do not wait on each other's index loads
-  for (int base = q0; base < q1; base += 32) {
-    const int2 mine = base + lane < q1 ? __ldg(pairs + base + lane) : make_int2(0, 0);
-    const int cnt = min(32, q1 - base);
-#pragma unroll 4
-    for (int k = 0; k < cnt; ++k) {
-      const int pi = __shfl_sync(kFull, mine.x, k), pj = __shfl_sync(kFull, mine.y, k);
-      const T* wi = W + (size_t)pi * kWld + la;
-      const T* wj = W + (size_t)pj * kWld + 3 * lg;
-      const T a0 = __ldg(wi), a1 = __ldg(wi + 9), a2 = __ldg(wi + 18);
-      s0 += a0 * __ldg(wj) + a1 * __ldg(wj + 9) + a2 * __ldg(wj + 18);
-      s1 += a0 * __ldg(wj + 1) + a1 * __ldg(wj + 10) + a2 * __ldg(wj + 19);
-      s2 += a0 * __ldg(wj + 2) + a1 * __ldg(wj + 11) + a2 * __ldg(wj + 20);
+  const int q0 = pair_ptr[w], q1 = pair_ptr[w + 1];
+  PairStage<T, kB> st{stage[wid], W, pairs, q1, lane};
+  if (q0 < q1) st.issue(q0, 0);
+  int buf = 0;
+  for (int base = q0; base < q1; base += kB) {
+    st.advance(base, buf);
+    const int nb = min(kB, q1 - base);
+    for (int k = 0; k < nb; ++k) {
+      const T* wi = &stage[wid][buf][2 * k][la];
+      const T* wj = &stage[wid][buf][2 * k + 1][3 * lg];
+      const T a0 = wi[0], a1 = wi[9], a2 = wi[18];
+      s0 += a0 * wj[0] + a1 * wj[9] + a2 * wj[18];
+      s1 += a0 * wj[1] + a1 * wj[10] + a2 * wj[19];
+      s2 += a0 * wj[2] + a1 * wj[11] + a2 * wj[20];
     }
+    __syncwarp();  // every lane is done with this buffer before it is refilled
+    buf ^= 1;
   }
   if (lane < 27) {
     T* o = out + 9 * la + 3 * lg;
+    T* m = vals + (size_t)mirror[w] * 81 + la;
     o[0] = -s0;
     o[1] = -s1;
     o[2] = -s2;
+    m[9 * (3 * lg)] = -s0;
+    m[9 * (3 * lg + 1)] = -s1;
+    m[9 * (3 * lg + 2)] = -s2;
   }
 }
 
-// pairs of observations of one point seen by different cameras, grouped by the level-0
-// block (camera of the first, camera of the second) they contribute to; built on the host
-// once per problem, in camera-row then observation order (deterministic sums)
+// a += x * y with the product exact (Dekker through fma) and the running sum kept as an
+// unnormalised head s and correction c (two-sum of s and the product's head; its error
+// and the product's tail go into c), the compensated dot product of Ogita, Rump and
+// Oishi carried over DF operands
+__device__ __forceinline__ void dot2_fma(float& s, float& c, float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  float e = __fmaf_rn(x.x, y.x, -p);
+  e = __fmaf_rn(x.x, y.y, e);
+  e = __fmaf_rn(x.y, y.x, e);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// Paired-FP32 assembly (mixed precision): the same blocks from the DF rows of
+// k_schur_w_df, each batch's sums compensated (dot2_fma) and folded into DF
+// accumulators; writes the FP64 value of each block (for the PCG product) and its FP32
+// rounding (for the V-cycle and the Galerkin product).
+__global__ void __launch_bounds__(kExWarps * 32)
+k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restrict__ up_blk,
+                    const int* __restrict__ mirror, const int* __restrict__ blk_row, const int* __restrict__ cols,
+                    const int* __restrict__ pair_ptr, const int2* __restrict__ pairs, const double* __restrict__ Scc,
+                    double* __restrict__ vals64, float* __restrict__ vals32) {
+  constexpr int kB = 8;
+  __shared__ __align__(16) float2 stage[kExWarps][2][2 * kB][kWld];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int w = blockIdx.x * kExWarps + wid;
+  if (w >= n_up) return;
+  const int e = up_blk[w];
+  const int c = blk_row[e];
+  if (cols[e] == c) {
+    for (int i = lane; i < 81; i += 32) {
+      const double v = Scc[(size_t)c * 81 + i];
+      vals64[(size_t)e * 81 + i] = v;
+      vals32[(size_t)e * 81 + i] = (float)v;
+    }
+    return;
+  }
+  const int la = lane < 27 ? lane / 3 : 0, lg = lane < 27 ? lane - 3 * (lane / 3) : 0;
+  DF acc[3] = {DF(0.f, 0.f), DF(0.f, 0.f), DF(0.f, 0.f)};
+  const int q0 = pair_ptr[w], q1 = pair_ptr[w + 1];
+  PairStage<float2, kB> st{stage[wid], W2, pairs, q1, lane};
+  if (q0 < q1) st.issue(q0, 0);
+  int buf = 0;
+  for (int base = q0; base < q1; base += kB) {
+    st.advance(base, buf);
+    const int nb = min(kB, q1 - base);
+    float sh[3] = {0.f, 0.f, 0.f}, sc[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < nb; ++k) {
+      const float2* wi = &stage[wid][buf][2 * k][la];
+      const float2* wj = &stage[wid][buf][2 * k + 1][3 * lg];
+      const float2 a0 = wi[0], a1 = wi[9], a2 = wi[18];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        dot2_fma(sh[u], sc[u], a0, wj[u]);
+        dot2_fma(sh[u], sc[u], a1, wj[9 + u]);
+        dot2_fma(sh[u], sc[u], a2, wj[18 + u]);
+      }
+    }
+    __syncwarp();
+    buf ^= 1;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) acc[u] += DF(sh[u], 0.f) + DF(sc[u], 0.f);
+  }
+  if (lane < 27) {
+    const size_t o = (size_t)e * 81 + 9 * la + 3 * lg, m = (size_t)mirror[w] * 81 + la;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const DF v = -acc[u];
+      const double d = to_double(v);
+      vals64[o + u] = d;
+      vals32[o + u] = v.h;
+      vals64[m + 9 * (3 * lg + u)] = d;
+      vals32[m + 9 * (3 * lg + u)] = v.h;
+    }
+  }
+}
+
+// pairs of observations of one point seen by different cameras c < c', grouped by the
+// level-0 block (c, c') they contribute to, and the work list of blocks on and above
+// the diagonal with their mirrors; built on the host once per problem, in camera-row
+// then observation order (deterministic sums)
 static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
   const int n_c = P->n_c, n_o = P->n_o, n_p = P->n_p;
   std::vector<int> row_ptr(n_c + 1), cols(std::max(L0.nnzb, 1)), cam_ptr(n_c + 1), cam_obs(std::max(n_o, 1)),
@@ -933,9 +1169,6 @@ static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
   down(obs_cam, P->obs_cam, n_o);
   down(pt_ptr, P->pt_ptr, n_p + 1);
   sync(P);
-  std::vector<int> blk_row(std::max(L0.nnzb, 1)), cnt(L0.nnzb + 1, 0);
-  for (int c = 0; c < n_c; ++c)
-    for (int e = row_ptr[c]; e < row_ptr[c + 1]; ++e) blk_row[e] = c;
   auto block_of = [&](int c, int c2) {
     int lo = row_ptr[c], hi = row_ptr[c + 1];
     while (lo < hi) {
@@ -943,64 +1176,98 @@ static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
       if (cols[mid] < c2) lo = mid + 1;
       else hi = mid;
     }
+    BA_REQUIRE(lo < row_ptr[c + 1] && cols[lo] == c2, BA_ERR_STATE, "covisibility pattern is not symmetric");
     return lo;
   };
+  std::vector<int> blk_row(std::max(L0.nnzb, 1)), up_of(std::max(L0.nnzb, 1), -1), up_blk, mirror;
+  for (int c = 0; c < n_c; ++c)
+    for (int e = row_ptr[c]; e < row_ptr[c + 1]; ++e) {
+      blk_row[e] = c;
+      if (cols[e] >= c) {
+        up_of[e] = (int)up_blk.size();
+        up_blk.push_back(e);
+        mirror.push_back(block_of(cols[e], c));
+      }
+    }
+  const int n_up = (int)up_blk.size();
+  std::vector<int> cnt(n_up + 1, 0);
   for (int pass = 0; pass < 2; ++pass) {
     std::vector<int> fill;
     std::vector<int2> pairs;
     if (pass == 1) {
       fill.assign(cnt.begin(), cnt.end() - 1);
-      pairs.resize(std::max(cnt[L0.nnzb], 1));
+      pairs.resize(std::max(cnt[n_up], 1));
     }
     for (int c = 0; c < n_c; ++c)
       for (int k = cam_ptr[c]; k < cam_ptr[c + 1]; ++k) {
         const int o = cam_obs[k], p = obs_pt[o];
         for (int q = pt_ptr[p]; q < pt_ptr[p + 1]; ++q) {
-          if (q == o) continue;
-          const int e = block_of(c, obs_cam[q]);
-          if (pass == 0) ++cnt[e + 1];
-          else pairs[fill[e]++] = make_int2(o, q);
+          if (obs_cam[q] <= c) continue;
+          const int u = up_of[block_of(c, obs_cam[q])];
+          if (pass == 0) ++cnt[u + 1];
+          else pairs[fill[u]++] = make_int2(o, q);
         }
       }
     if (pass == 0) {
-      for (int e = 0; e < L0.nnzb; ++e) cnt[e + 1] += cnt[e];
+      for (int u = 0; u < n_up; ++u) cnt[u + 1] += cnt[u];
       upload(P, L0.pair_ptr, cnt);
       upload(P, L0.blk_row, blk_row);
+      upload(P, L0.up_blk, up_blk);
+      upload(P, L0.mirror, mirror);
     } else {
       upload(P, L0.pairs, pairs);
     }
   }
+  L0.n_up = n_up;
   sync(P);
 }
 
-void explicit_schur(ba_problem* P, Level& L0, bool fp32) {
+void explicit_schur(ba_problem* P, Level& L0, ExplicitMode mode) {
   if (!L0.pairs.p) explicit_pairs_symbolic(P, L0);
-  const size_t elem = fp32 ? 4 : 8;
-  P->scratch.ensure(elem * kWld * (size_t)std::max(P->n_o, 1) + 64);
   const int g = cdiv(std::max(P->n_o, 1), 128);
-  const int gb = cdiv(std::max(L0.nnzb, 1), kExWarps);
-  if (fp32) {
+  const int gb = cdiv(std::max(L0.n_up, 1), kExWarps);
+  const int ldp = (int)P->ldp;
+  if (mode == EX_PAIRED) {
     L0.vals32.ensure(sizeof(float) * 81 * (size_t)L0.nnzb + 64);
+    L0.vals64.ensure(sizeof(double) * 81 * (size_t)L0.nnzb + 64);
+    P->scratch.ensure(sizeof(float2) * kWld * (size_t)std::max(P->n_o, 1) + 64);
+    float2* W2 = P->scratch.as<float2>();
+    if (P->n_o) {
+      k_schur_w_df<<<g, 128, 0, P->stream>>>(P->J32.as<float>(), P->J32lo.as<float>(), P->Cinv32.as<float>(),
+                                             P->Cinv32lo.as<float>(), ldp, P->obs_pt.as<int>(), P->n_o, W2);
+      launched(P);
+    }
+    KernelTimer kt(P, BA_KT_ASSEMBLY);
+    k_explicit_pairs_df<<<gb, kExWarps * 32, 0, P->stream>>>(
+        W2, L0.n_up, L0.up_blk.as<int>(), L0.mirror.as<int>(), L0.blk_row.as<int>(), L0.cols.as<int>(),
+        L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(), L0.vals64.as<double>(),
+        L0.vals32.as<float>());
+  } else if (mode == EX_FP32) {
+    L0.vals32.ensure(sizeof(float) * 81 * (size_t)L0.nnzb + 64);
+    P->scratch.ensure(sizeof(float) * kWld * (size_t)std::max(P->n_o, 1) + 64);
     float* W = P->scratch.as<float>();
     if (P->n_o) {
-      k_schur_w<float><<<g, 128, 0, P->stream>>>(P->J32.as<float>(), P->Cinv32.as<float>(), (int)P->ldp,
+      k_schur_w<float><<<g, 128, 0, P->stream>>>(P->J32.as<float>(), P->Cinv32.as<float>(), ldp,
                                                  P->obs_pt.as<int>(), P->n_o, W);
       launched(P);
     }
+    KernelTimer kt(P, BA_KT_ASSEMBLY);
     k_explicit_pairs<float><<<gb, kExWarps * 32, 0, P->stream>>>(
-        W, L0.nnzb, L0.blk_row.as<int>(), L0.cols.as<int>(), L0.pair_ptr.as<int>(), L0.pairs.as<int2>(),
-        P->Scc.as<double>(), L0.vals32.as<float>());
+        W, L0.n_up, L0.up_blk.as<int>(), L0.mirror.as<int>(), L0.blk_row.as<int>(), L0.cols.as<int>(),
+        L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(), L0.vals32.as<float>());
   } else {
     L0.vals64.ensure(sizeof(double) * 81 * (size_t)L0.nnzb + 64);
+    P->scratch.ensure(sizeof(double) * kWld * (size_t)std::max(P->n_o, 1) + 64);
     double* W = P->scratch.as<double>();
     if (P->n_o) {
-      k_schur_w<double><<<g, 128, 0, P->stream>>>(P->J64.as<double>(), P->Cinv64.as<double>(), (int)P->ldp,
+      k_schur_w<double><<<g, 128, 0, P->stream>>>(jacobian64(P), P->Cinv64.as<double>(), ldp,
                                                   P->obs_pt.as<int>(), P->n_o, W);
       launched(P);
     }
+    KernelTimer kt(P, BA_KT_ASSEMBLY);
     k_explicit_pairs<double><<<gb, kExWarps * 32, 0, P->stream>>>(
-        W, L0.nnzb, L0.blk_row.as<int>(), L0.cols.as<int>(), L0.pair_ptr.as<int>(), L0.pairs.as<int2>(),
-        P->Scc.as<double>(), L0.vals64.as<double>());
+        W, L0.n_up, L0.up_blk.as<int>(), L0.mirror.as<int>(), L0.blk_row.as<int>(), L0.cols.as<int>(),
+        L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(), L0.vals64.as<double>());
   }
   launched(P);
 }
@@ -1131,8 +1398,9 @@ void reduced_rhs(ba_problem* P, const double* vc, const double* vp_user, double*
                                                                 P->pt_user.as<int>(), vp_user, P->n_p, w);
     launched(P);
   }
+  double* J = jacobian64(P);
   k_camera_reduce_rhs<<<cdiv((long long)P->n_c * 32, 128), 128, 0, P->stream>>>(
-      P->J64.as<double>(), P->J64.as<double>(), P->ld, P->cam_ptr.as<int>(), P->cam_obs.as<int>(),
+      J, J, P->ld, P->cam_ptr.as<int>(), P->cam_obs.as<int>(),
       P->obs_pt.as<int>(), w, P->ldp, vc, P->n_c, out);
   launched(P);
 }

@@ -42,6 +42,8 @@ __global__ void k_bsr16_spmv(int n, const int* __restrict__ row_ptr, const int* 
 template <typename T>
 __global__ void k_bsr9_spmv(int n, const int* __restrict__ row_ptr, const int* __restrict__ cols,
                             const T* __restrict__ vals, const T* __restrict__ x, T* __restrict__ y) {
+  pdl_wait();
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= n) return;
@@ -331,6 +333,7 @@ void precond_apply(ba_problem* P, const double* r, double* z) {
     return;
   }
   BA_REQUIRE(P->n_levels > 0, BA_ERR_STATE, "ba_mg_setup has not been run");
+  KernelTimer kt(P, BA_KT_VCYCLE);
   if (P->vc_ready) {
     fused_vcycle(P, r, z);
     return;
@@ -406,16 +409,29 @@ __global__ void k_pcg_direction(size_t n, double* __restrict__ p, const double* 
 }
 
 static float2* split_target(ba_problem* P) {
-  if (!outer_df(P)) return nullptr;
+  if (!outer_df(P) || P->outer_explicit) return nullptr;
   P->xsplit.ensure(sizeof(float2) * 9 * (size_t)P->n_c + 64);
   return P->xsplit.as<float2>();
+}
+
+// q = S p for the PCG: the FP64 blocks of the assembled S when level 0 is assembled
+// (overwriting q), else the implicit product added to q = D_c p, written with p
+static void outer_product(ba_problem* P, const double* p, double* q) {
+  if (P->outer_explicit) {
+    const Level& L0 = P->levels[0];
+    KernelTimer kt(P, BA_KT_OUTER_BSR);
+    launch_k(P, k_bsr9_spmv<double>, cdiv(L0.n, 4), 128, 0, L0.n, L0.row_ptr.as<int>(), L0.cols.as<int>(),
+             L0.vals64.as<double>(), p, q);
+    return;
+  }
+  matvec64_accumulate(P, p, q);
 }
 
 // one PCG iteration's head: q = S p; alpha = rz / p.q; x += alpha p; r -= alpha q; rr = r.r
 static void pcg_head(ba_problem* P, double* x) {
   const size_t n = (size_t)P->n_c * 9;
   double *r = P->r.as<double>(), *p = P->p.as<double>(), *q = P->q.as<double>();
-  matvec64_accumulate(P, p, q);  // q = D_c p was written with p
+  outer_product(P, p, q);
   dot64(P, p, q, n, S_PQ);
   launch_k(P, k_pcg_update, reduce_blocks(P, n), kVecBS, 0, n, x, r, p, q, P->scal.as<double>(), S_RZ,
                                                               P->partial.as<double>(), P->counter.as<unsigned>(),
@@ -588,7 +604,7 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
     }
   }
   while (it < P->opt.max_iters) {
-    matvec64_accumulate(P, p, q);  // q = D_c p was written with p
+    outer_product(P, p, q);
     dot64(P, p, q, n, S_PQ);
     launch_k(P, k_pcg_update, rg, kVecBS, 0, n, dc, r, p, q, scal, s_rz, P->partial.as<double>(),
                                                P->counter.as<unsigned>(), P->flags.as<int>());

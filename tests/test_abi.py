@@ -34,6 +34,14 @@ def test_binding_covers_the_header():
     assert sorted(_ffi.EXPORTED) == _declared()
 
 
+def test_struct_layouts_match_the_library(lib):
+    from paper_2007_01941_gb300 import _ffi
+    lib.ba_struct_size.restype = ctypes.c_size_t
+    assert lib.ba_struct_size(0) == ctypes.sizeof(_ffi.Options)
+    assert lib.ba_struct_size(1) == ctypes.sizeof(_ffi.Info)
+    assert lib.ba_struct_size(2) == 0
+
+
 def test_default_options_are_the_papers_constants(lib):
     from paper_2007_01941_gb300 import _ffi
     _ffi._lib = None
@@ -45,6 +53,7 @@ def test_default_options_are_the_papers_constants(lib):
     assert o.lanczos_steps == 5
     assert (o.cheb_lo, o.cheb_hi) == (0.3, 1.1)
     assert o.lambda_ == 1e-4          # 1 / initial trust radius 1e4 (Section 5)
+    assert o.loss == _ffi.BA_LOSS_SQUARED and o.loss_scale == 1.0   # Huber a = 1 (Section 5)
 
 
 def test_invalid_arguments_are_rejected_without_a_gpu(lib):
@@ -54,3 +63,13 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert lib2.ba_create(0, 0, 0, None, None, None, None, ctypes.byref(h)) == _ffi.BA_ERR_INVALID_ARG
     assert lib2.ba_create(4, 4, 3, None, None, None, None, ctypes.byref(h)) == _ffi.BA_ERR_INVALID_ARG
     assert not h.value
+    # option validation runs before any CUDA call
+    for bad in (dict(loss=7), dict(loss=_ffi.BA_LOSS_HUBER, loss_scale=-1.0),
+                dict(loss=_ffi.BA_LOSS_HUBER, loss_scale=float("inf")), dict(stop_rule=9)):
+        o = _ffi.Options()
+        lib2.ba_default_options(ctypes.byref(o))
+        for k, v in bad.items():
+            setattr(o, k, v)
+        assert lib2.ba_create(4, 4, 0, None, None, ctypes.byref(o), None, ctypes.byref(h)) == \
+            _ffi.BA_ERR_INVALID_ARG, bad
+        assert not h.value
