@@ -82,4 +82,30 @@ __device__ __forceinline__ double to_double(DF a) { return df_f2d(a.h) + df_f2d(
 __device__ __forceinline__ DF to_df(double x) { return DF(x); }
 __device__ __forceinline__ double to_double(double x) { return x; }
 
+// sum over the warp (every lane gets the total)
+__device__ __forceinline__ DF warp_sum_df(DF v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += DF(__shfl_xor_sync(kFull, v.h, d), __shfl_xor_sync(kFull, v.l, d));
+  return v;
+}
+
+// a += x * y with the product exact (Dekker through fma) and the running sum kept as an
+// unnormalised head s and correction c (two-sum of s and the product's head; its error
+// and the product's tail go into c), the compensated dot product of Ogita, Rump and
+// Oishi carried over DF operands
+__device__ __forceinline__ void dot2_fma(float& s, float& c, float2 x, float2 y) {
+  const float p = __fmul_rn(x.x, y.x);
+  float e = __fmaf_rn(x.x, y.x, -p);
+  e = __fmaf_rn(x.x, y.y, e);
+  e = __fmaf_rn(x.y, y.x, e);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+__device__ __forceinline__ void dot2_fma(float& s, float& c, DF x, DF y) {
+  dot2_fma(s, c, make_float2(x.h, x.l), make_float2(y.h, y.l));
+}
+
 }  // namespace ba

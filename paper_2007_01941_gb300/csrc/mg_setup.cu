@@ -13,6 +13,7 @@
 
 #include "ba_internal.h"
 #include "device_util.cuh"
+#include "dfloat.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -580,6 +581,103 @@ k_aggregate_qr(int n_agg, int bs, int max_rows, const int* __restrict__ mptr, co
     Q32[dst] = (float)q;
   }
   for (int e = lane; e < kNull * kNull; e += 32) Kc[(size_t)a * kNull * kNull + e] = R[e / kNull][e % kNull];
+  if (lane == 0) kept_out[a] = kept;
+}
+
+// The same factorisation in paired FP32 (DF) for the mixed-precision hierarchy: one
+// warp per aggregate, A in shared memory as (hi, lo) pairs.  The FP64 unit of this GPU
+// issues a warp's FMA over many cycles per SM sub-partition, so the FP64 kernel above
+// is bound by it even at these sizes; DF runs on the FP32 pipes.  The inner products of
+// a pass are spread over the lanes (lane i + 16h: column i, rows h, h + 2, ...), so
+// no lane computes products for columns at or after the current one.
+constexpr int kQrDfWarps = 4;
+
+__global__ void __launch_bounds__(kQrDfWarps * 32)
+k_aggregate_qr_df(int n_agg, int bs, int max_rows, const int* __restrict__ mptr, const int* __restrict__ mem,
+                  const double* __restrict__ K, double* __restrict__ Q64, float* __restrict__ Q32,
+                  double* __restrict__ Kc, unsigned* __restrict__ kept_out) {
+  extern __shared__ __align__(16) unsigned char qsm[];
+  __shared__ float2 Rs[kQrDfWarps][kNull][kNull + 1];
+  __shared__ float2 gs[kQrDfWarps][kNull];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int a = blockIdx.x * kQrDfWarps + warp;
+  if (a >= n_agg) return;
+  float2* A = reinterpret_cast<float2*>(qsm) + (size_t)warp * max_rows * kQrStride;  // [rows][kQrStride]
+  float2(*R)[kNull + 1] = Rs[warp];
+  float2* g = gs[warp];
+  const int mb = mptr[a], me = mptr[a + 1];
+  const int rows = (me - mb) * bs;
+  for (int e = lane; e < rows * kNull; e += 32) {
+    const int r = e / kNull, j = e - r * kNull;
+    const int s = r / bs, u = r - s * bs;
+    const DF v(K[((size_t)mem[mb + s] * bs + u) * kNull + j]);
+    A[r * kQrStride + j] = make_float2(v.h, v.l);
+  }
+  for (int e = lane; e < kNull * kNull; e += 32) R[e / kNull][e % kNull] = make_float2(0.f, 0.f);
+  __syncwarp();
+  auto at = [&](int r, int j) {
+    const float2 v = A[r * kQrStride + j];
+    return DF(v.x, v.y);
+  };
+  auto col_norm = [&](int j) {
+    float s = 0.f, c = 0.f;
+    for (int r = lane; r < rows; r += 32) {
+      const DF v = at(r, j);
+      dot2_fma(s, c, v, v);
+    }
+    return df_sqrt(warp_sum_df(DF(s, 0.f) + DF(c, 0.f)));
+  };
+  const int gi = lane & 15, gh = lane >> 4;
+  unsigned kept = 0;
+  for (int j = 0; j < kNull; ++j) {
+    const DF n0 = col_norm(j);
+    DF rc(0.f, 0.f);
+    if (j > 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        // g_i = A[:, i] . A[:, j] for i < j
+        float s = 0.f, c = 0.f;
+        if (gi < j)
+          for (int r = gh; r < rows; r += 2) dot2_fma(s, c, at(r, gi), at(r, j));
+        DF gv = DF(s, 0.f) + DF(c, 0.f);
+        gv += DF(__shfl_xor_sync(kFull, gv.h, 16), __shfl_xor_sync(kFull, gv.l, 16));
+        if (gh == 0 && gi < j) g[gi] = make_float2(gv.h, gv.l);
+        __syncwarp();
+        // A[:, j] -= sum_{i<j} g_i A[:, i]
+        for (int r = lane; r < rows; r += 32) {
+          float ps = 0.f, pc = 0.f;
+          for (int i = 0; i < j; ++i) dot2_fma(ps, pc, g[i], A[r * kQrStride + i]);
+          const DF v = at(r, j) - (DF(ps, 0.f) + DF(pc, 0.f));
+          A[r * kQrStride + j] = make_float2(v.h, v.l);
+        }
+        __syncwarp();
+        if (gi < j) rc += gv;
+      }
+    }
+    const DF nv = col_norm(j);
+    const bool keep = n0.h > 0.f && nv.h > 1e-10f * n0.h;
+    const DF scale = keep ? DF(1.f, 0.f) / nv : DF(0.f, 0.f);
+    for (int r = lane; r < rows; r += 32) {
+      const DF v = at(r, j) * scale;
+      A[r * kQrStride + j] = make_float2(v.h, v.l);
+    }
+    if (keep) kept |= 1u << j;
+    if (gh == 0 && gi < j) R[gi][j] = make_float2(rc.h, rc.l);
+    if (lane == 0) R[j][j] = keep ? make_float2(nv.h, nv.l) : make_float2(0.f, 0.f);
+    __syncwarp();
+  }
+  // Q blocks back to the member nodes
+  for (int e = lane; e < rows * kNull; e += 32) {
+    const int r = e / kNull, j = e - r * kNull;
+    const int s = r / bs, u = r - s * bs;
+    const size_t dst = ((size_t)mem[mb + s] * bs + u) * kNull + j;
+    const DF q = at(r, j);
+    Q64[dst] = to_double(q);
+    Q32[dst] = q.h;
+  }
+  for (int e = lane; e < kNull * kNull; e += 32) {
+    const float2 v = R[e / kNull][e % kNull];
+    Kc[(size_t)a * kNull * kNull + e] = to_double(DF(v.x, v.y));
+  }
   if (lane == 0) kept_out[a] = kept;
 }
 
@@ -1385,8 +1483,14 @@ void mg_setup(ba_problem* P) {
     const int max_rows = std::max(1, L.agg_max) * L.bs;
     const size_t qsm = sizeof(double) * (size_t)kQrWarps * max_rows * kQrStride;
     BA_REQUIRE(qsm <= 200 * 1024, BA_ERR_LIMIT, "aggregates too large for the aggregate QR");
-    BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
-    if (L1.n >= 2 * P->n_sm) {
+    if (fp32) {
+      // mixed precision: the DF factorisation, one warp per aggregate at every level
+      BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
+      k_aggregate_qr_df<<<cdiv(L1.n, kQrDfWarps), kQrDfWarps * 32, qsm, P->stream>>>(
+          L1.n, L.bs, max_rows, L.agg_ptr.as<int>(), L.agg_mem.as<int>(), L.K.as<double>(), L.Q64.as<double>(),
+          L.Q32.as<float>(), L1.K.as<double>(), L1.kept.as<unsigned>());
+    } else if (L1.n >= 2 * P->n_sm) {
+      BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
       k_aggregate_qr<<<cdiv(L1.n, kQrWarps), kQrWarps * 32, qsm, P->stream>>>(
           L1.n, L.bs, max_rows, L.agg_ptr.as<int>(), L.agg_mem.as<int>(), L.K.as<double>(), L.Q64.as<double>(),
           L.Q32.as<float>(), L1.K.as<double>(), L1.kept.as<unsigned>());

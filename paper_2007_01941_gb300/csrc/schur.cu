@@ -274,6 +274,35 @@ __device__ __forceinline__ DF rec_df(const float* __restrict__ h, const float* _
   return DF(__ldg(h + (size_t)o * kRec + k), __ldg(l + (size_t)o * kRec + k));
 }
 
+// record o (F row-major, then E) as DF, with 16-byte loads of the heads and remainders
+// (records are 96 bytes, so every record starts on a 16-byte boundary)
+__device__ __forceinline__ void rec_df_all(const float* __restrict__ h, const float* __restrict__ l, int o,
+                                           DF r[kRec]) {
+  const float4* H = reinterpret_cast<const float4*>(h + (size_t)o * kRec);
+  const float4* L = reinterpret_cast<const float4*>(l + (size_t)o * kRec);
+#pragma unroll
+  for (int k = 0; k < kRec / 4; ++k) {
+    const float4 a = __ldg(H + k), b = __ldg(L + k);
+    r[4 * k] = DF(a.x, b.x);
+    r[4 * k + 1] = DF(a.y, b.y);
+    r[4 * k + 2] = DF(a.z, b.z);
+    r[4 * k + 3] = DF(a.w, b.w);
+  }
+}
+
+// E_o (record entries 18..23) as DF
+__device__ __forceinline__ void rec_df_e(const float* __restrict__ h, const float* __restrict__ l, int o, DF e[6]) {
+  const float4* H = reinterpret_cast<const float4*>(h + (size_t)o * kRec);
+  const float4* L = reinterpret_cast<const float4*>(l + (size_t)o * kRec);
+  const float4 a4 = __ldg(H + 4), b4 = __ldg(L + 4), a5 = __ldg(H + 5), b5 = __ldg(L + 5);
+  e[0] = DF(a4.z, b4.z);
+  e[1] = DF(a4.w, b4.w);
+  e[2] = DF(a5.x, b5.x);
+  e[3] = DF(a5.y, b5.y);
+  e[4] = DF(a5.z, b5.z);
+  e[5] = DF(a5.w, b5.w);
+}
+
 __global__ void k_point_setup_df(const float* __restrict__ Jh, const float* __restrict__ Jl,
                                  const double* __restrict__ fres, const int* __restrict__ pt_ptr, int n_p, int n_p_obs,
                                  size_t ldp, double lambda, int damp_identity, double* __restrict__ Dp,
@@ -286,8 +315,9 @@ __global__ void k_point_setup_df(const float* __restrict__ Jh, const float* __re
   DF c00 = z, c01 = z, c02 = z, c11 = z, c12 = z, c22 = z, g0 = z, g1 = z, g2 = z;
   const int b = pt_ptr[ip], e = pt_ptr[ip + 1];
   for (int o = b; o < e; ++o) {
-    const DF a0 = rec_df(Jh, Jl, o, 18), a1 = rec_df(Jh, Jl, o, 19), a2 = rec_df(Jh, Jl, o, 20);
-    const DF b0 = rec_df(Jh, Jl, o, 21), b1 = rec_df(Jh, Jl, o, 22), b2 = rec_df(Jh, Jl, o, 23);
+    DF ev[6];
+    rec_df_e(Jh, Jl, o, ev);
+    const DF a0 = ev[0], a1 = ev[1], a2 = ev[2], b0 = ev[3], b1 = ev[4], b2 = ev[5];
     const DF f0(fres[2 * (size_t)o]), f1(fres[2 * (size_t)o + 1]);
     c00 += a0 * a0 + b0 * b0;
     c01 += a0 * a1 + b0 * b1;
@@ -344,11 +374,6 @@ __global__ void k_point_setup_df(const float* __restrict__ Jh, const float* __re
   }
 }
 
-__device__ __forceinline__ DF warp_sum_df(DF v) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v += DF(__shfl_xor_sync(kFull, v.h, d), __shfl_xor_sync(kFull, v.l, d));
-  return v;
-}
 
 __global__ void k_camera_setup_df(const float* __restrict__ Jh, const float* __restrict__ Jl,
                                   const double* __restrict__ fres, const int* __restrict__ cam_ptr,
@@ -369,11 +394,13 @@ __global__ void k_camera_setup_df(const float* __restrict__ Jh, const float* __r
     const DF f0(fres[2 * (size_t)o]), f1(fres[2 * (size_t)o + 1]);
     const float2 q0 = __ldg(wpdf + ip), q1 = __ldg(wpdf + ldp + ip), q2 = __ldg(wpdf + 2 * ldp + ip);
     const DF w0(q0.x, q0.y), w1(q1.x, q1.y), w2(q2.x, q2.y);
-    const DF h0 = f0 + rec_df(Jh, Jl, o, 18) * w0 + rec_df(Jh, Jl, o, 19) * w1 + rec_df(Jh, Jl, o, 20) * w2;
-    const DF h1 = f1 + rec_df(Jh, Jl, o, 21) * w0 + rec_df(Jh, Jl, o, 22) * w1 + rec_df(Jh, Jl, o, 23) * w2;
+    DF rv[kRec];
+    rec_df_all(Jh, Jl, o, rv);
+    const DF h0 = f0 + rv[18] * w0 + rv[19] * w1 + rv[20] * w2;
+    const DF h1 = f1 + rv[21] * w0 + rv[22] * w1 + rv[23] * w2;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      const DF a = rec_df(Jh, Jl, o, k), b = rec_df(Jh, Jl, o, 9 + k);
+      const DF a = rv[k], b = rv[9 + k];
       dg[k] += a * a + b * b;
       g[k] -= a * f0 + b * f1;
       bb[k] -= a * h0 + b * h1;
@@ -401,27 +428,29 @@ __global__ void k_camera_setup_df(const float* __restrict__ Jh, const float* __r
 // S_cc = D_c + sum_{o in c} F_o^T N_o F_o, N_o = I - E_o C_p^-1 E_o^T, in DF (the
 // counterpart of k_scc): A_cc and the point terms cancel in S_cc, so its FP64 value,
 // which the assembled S and the point-block-Jacobi blocks take, needs the extra bits.
-// Warp per camera, lane per observation, the 45 upper entries summed over the warp.
-__global__ void __launch_bounds__(128)
+// One CTA per camera, one thread per observation; each thread keeps the 45 upper
+// entries as compensated sums (dot2_fma), the CTA adds them up through shared memory.
+constexpr int kSccBS = 128;
+
+__global__ void __launch_bounds__(kSccBS)
 k_scc_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const float* __restrict__ Ch,
          const float* __restrict__ Cl, size_t ldp, const int* __restrict__ cam_ptr, const int* __restrict__ cam_obs,
          const int* __restrict__ obs_pt, const double* __restrict__ Dc, int n_c, double* __restrict__ Scc) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (c >= n_c) return;
-  DF acc[45];
+  __shared__ float2 part[45][kSccBS + 1];
+  const int c = blockIdx.x;
+  const int t = threadIdx.x;
+  float as[45], ac[45];
 #pragma unroll
-  for (int k = 0; k < 45; ++k) acc[k] = DF(0.f, 0.f);
-  for (int i = cam_ptr[c] + lane; i < cam_ptr[c + 1]; i += 32) {
+  for (int k = 0; k < 45; ++k) as[k] = ac[k] = 0.f;
+  for (int i = cam_ptr[c] + t; i < cam_ptr[c + 1]; i += kSccBS) {
     const int o = cam_obs[i];
     const int ip = obs_pt[o];
-    DF e[6], ci[6], f[18];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) e[k] = rec_df(Jh, Jl, o, 18 + k);
+    DF rv[kRec], ci[6];
+    rec_df_all(Jh, Jl, o, rv);
+    const DF* f = rv;
+    const DF* e = rv + 18;
 #pragma unroll
     for (int k = 0; k < 6; ++k) ci[k] = DF(__ldg(Ch + k * ldp + ip), __ldg(Cl + k * ldp + ip));
-#pragma unroll
-    for (int k = 0; k < 18; ++k) f[k] = rec_df(Jh, Jl, o, k);
     // Y = E C^-1 (2x3), N = I - Y E^T (2x2, symmetric)
     DF y0[3], y1[3];
     y0[0] = e[0] * ci[0] + e[1] * ci[1] + e[2] * ci[2];
@@ -434,27 +463,39 @@ k_scc_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const float
     const DF n00 = one - (y0[0] * e[0] + y0[1] * e[1] + y0[2] * e[2]);
     const DF n01 = -(y0[0] * e[3] + y0[1] * e[4] + y0[2] * e[5]);
     const DF n11 = one - (y1[0] * e[3] + y1[1] * e[4] + y1[2] * e[5]);
-    int t = 0;
+    int k = 0;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
       const DF ga0 = f[a] * n00 + f[9 + a] * n01;
       const DF ga1 = f[a] * n01 + f[9 + a] * n11;
 #pragma unroll
-      for (int b = a; b < 9; ++b) acc[t++] += ga0 * f[b] + ga1 * f[9 + b];
+      for (int b = a; b < 9; ++b, ++k) {
+        dot2_fma(as[k], ac[k], ga0, f[b]);
+        dot2_fma(as[k], ac[k], ga1, f[9 + b]);
+      }
     }
   }
 #pragma unroll
-  for (int k = 0; k < 45; ++k) acc[k] = warp_sum_df(acc[k]);
-  if (lane == 0) {
+  for (int k = 0; k < 45; ++k) {
+    const DF v = DF(as[k], 0.f) + DF(ac[k], 0.f);
+    part[k][t] = make_float2(v.h, v.l);
+  }
+  __syncthreads();
+  if (t < 45) {
+    DF v(0.f, 0.f);
+    for (int j = 0; j < kSccBS; ++j) v += DF(part[t][j].x, part[t][j].y);
+    // entry t of the upper triangle in row order -> (a, b)
+    int a = 0, r = t;
+    while (r >= 9 - a) {
+      r -= 9 - a;
+      ++a;
+    }
+    const int b = a + r;
+    double d = to_double(v);
+    if (a == b) d += Dc[9 * c + a];
     double* out = Scc + 81 * (size_t)c;
-    int t = 0;
-    for (int a = 0; a < 9; ++a)
-      for (int b = a; b < 9; ++b) {
-        double v = to_double(acc[t++]);
-        if (a == b) v += Dc[9 * c + a];
-        out[9 * a + b] = v;
-        out[9 * b + a] = v;
-      }
+    out[9 * a + b] = d;
+    out[9 * b + a] = d;
   }
 }
 
@@ -479,17 +520,19 @@ __global__ void k_back_substitute_df(const float* __restrict__ Jh, const float* 
   }
   for (int o = pt_ptr[ip]; o < pt_ptr[ip + 1]; ++o) {
     const float2* x = dcs + 9 * (size_t)obs_cam[o];
+    DF rv[kRec];
+    rec_df_all(Jh, Jl, o, rv);
     DF u0(0.f, 0.f), u1(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const float2 xv = __ldg(x + k);
       const DF xk(xv.x, xv.y);
-      u0 += rec_df(Jh, Jl, o, k) * xk;
-      u1 += rec_df(Jh, Jl, o, 9 + k) * xk;
+      u0 += rv[k] * xk;
+      u1 += rv[9 + k] * xk;
     }
-    h0 -= rec_df(Jh, Jl, o, 18) * u0 + rec_df(Jh, Jl, o, 21) * u1;
-    h1 -= rec_df(Jh, Jl, o, 19) * u0 + rec_df(Jh, Jl, o, 22) * u1;
-    h2 -= rec_df(Jh, Jl, o, 20) * u0 + rec_df(Jh, Jl, o, 23) * u1;
+    h0 -= rv[18] * u0 + rv[21] * u1;
+    h1 -= rv[19] * u0 + rv[22] * u1;
+    h2 -= rv[20] * u0 + rv[23] * u1;
   }
   const double H0 = to_double(h0), H1 = to_double(h1), H2 = to_double(h2);
   const double c00 = Cinv[ip], c01 = Cinv[ldp + ip], c02 = Cinv[2 * ldp + ip];
@@ -562,7 +605,7 @@ void schur_setup(ba_problem* P, double lambda) {
   // point-block-Jacobi blocks S_cc (in the mode's storage precision) and FP64 inverses
   double* Scc = P->Scc.as<double>();
   if (mixed)
-    k_scc_df<<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
+    k_scc_df<<<n_c, kSccBS, 0, P->stream>>>(
         P->J32.as<float>(), P->J32lo.as<float>(), P->Cinv32.as<float>(), P->Cinv32lo.as<float>(), ldp,
         P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->Dc.as<double>(), n_c, Scc);
   else
@@ -956,13 +999,13 @@ k_schur_w_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const f
   const DF i11 = l11.h > 0.f ? one / l11 : zero;
   const DF l21 = (cv[4] - l20 * l10) * i11;
   const DF l22 = df_sqrt(cv[5] - l20 * l20 - l21 * l21);
-  DF e[6];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) e[k] = rec_df(Jh, Jl, o, 18 + k);
+  DF rv[kRec];
+  rec_df_all(Jh, Jl, o, rv);
+  const DF* e = rv + 18;
   DF w[kWld];
 #pragma unroll
   for (int b = 0; b < 9; ++b) {
-    const DF f0 = rec_df(Jh, Jl, o, b), f1 = rec_df(Jh, Jl, o, 9 + b);
+    const DF f0 = rv[b], f1 = rv[9 + b];
     const DF h0 = e[0] * f0 + e[3] * f1, h1 = e[1] * f0 + e[4] * f1, h2 = e[2] * f0 + e[5] * f1;
     w[b] = l00 * h0 + l10 * h1 + l20 * h2;
     w[9 + b] = l11 * h1 + l21 * h2;
@@ -1070,22 +1113,6 @@ k_explicit_pairs(const T* __restrict__ W, int n_up, const int* __restrict__ up_b
   }
 }
 
-// a += x * y with the product exact (Dekker through fma) and the running sum kept as an
-// unnormalised head s and correction c (two-sum of s and the product's head; its error
-// and the product's tail go into c), the compensated dot product of Ogita, Rump and
-// Oishi carried over DF operands
-__device__ __forceinline__ void dot2_fma(float& s, float& c, float2 x, float2 y) {
-  const float p = __fmul_rn(x.x, y.x);
-  float e = __fmaf_rn(x.x, y.x, -p);
-  e = __fmaf_rn(x.x, y.y, e);
-  e = __fmaf_rn(x.y, y.x, e);
-  const float t = __fadd_rn(s, p);
-  const float bp = __fsub_rn(t, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
-  s = t;
-  c = __fadd_rn(c, __fadd_rn(err, e));
-}
-
 // Paired-FP32 assembly (mixed precision): the same blocks from the DF rows of
 // k_schur_w_df, each batch's sums compensated (dot2_fma) and folded into DF
 // accumulators; writes the FP64 value of each block (for the PCG product) and its FP32
@@ -1119,7 +1146,10 @@ k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restri
   for (int base = q0; base < q1; base += kB) {
     st.advance(base, buf);
     const int nb = min(kB, q1 - base);
-    float sh[3] = {0.f, 0.f, 0.f}, sc[3] = {0.f, 0.f, 0.f};
+    // two sets of compensated sums (terms 0, 2 and term 1 of each pair) for more
+    // independent dependency chains
+    float sh[3] = {0.f, 0.f, 0.f}, sc[3] = {0.f, 0.f, 0.f}, th[3] = {0.f, 0.f, 0.f}, tc[3] = {0.f, 0.f, 0.f};
+#pragma unroll 2
     for (int k = 0; k < nb; ++k) {
       const float2* wi = &stage[wid][buf][2 * k][la];
       const float2* wj = &stage[wid][buf][2 * k + 1][3 * lg];
@@ -1127,14 +1157,14 @@ k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restri
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
         dot2_fma(sh[u], sc[u], a0, wj[u]);
-        dot2_fma(sh[u], sc[u], a1, wj[9 + u]);
+        dot2_fma(th[u], tc[u], a1, wj[9 + u]);
         dot2_fma(sh[u], sc[u], a2, wj[18 + u]);
       }
     }
     __syncwarp();
     buf ^= 1;
 #pragma unroll
-    for (int u = 0; u < 3; ++u) acc[u] += DF(sh[u], 0.f) + DF(sc[u], 0.f);
+    for (int u = 0; u < 3; ++u) acc[u] += (DF(sh[u], 0.f) + DF(sc[u], 0.f)) + (DF(th[u], 0.f) + DF(tc[u], 0.f));
   }
   if (lane < 27) {
     const size_t o = (size_t)e * 81 + 9 * la + 3 * lg, m = (size_t)mirror[w] * 81 + la;
@@ -1191,10 +1221,35 @@ static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
     }
   const int n_up = (int)up_blk.size();
   std::vector<int> cnt(n_up + 1, 0);
-  for (int pass = 0; pass < 2; ++pass) {
+  for (int pass = 0; pass < 3; ++pass) {
+    if (pass == 1) {
+      // work items in decreasing order of their pair counts, so that the longest blocks
+      // start first and the grid's tail is short (each block's own pair order is kept)
+      std::vector<int> perm(n_up), rank(n_up);
+      for (int u = 0; u < n_up; ++u) perm[u] = u;
+      std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return cnt[a + 1] > cnt[b + 1]; });
+      std::vector<int> up2(n_up), mir2(n_up), cnt2(n_up + 1, 0);
+      for (int r = 0; r < n_up; ++r) {
+        rank[perm[r]] = r;
+        up2[r] = up_blk[perm[r]];
+        mir2[r] = mirror[perm[r]];
+        cnt2[r + 1] = cnt[perm[r] + 1];
+      }
+      for (int e = 0; e < L0.nnzb; ++e)
+        if (up_of[e] >= 0) up_of[e] = rank[up_of[e]];
+      up_blk.swap(up2);
+      mirror.swap(mir2);
+      cnt.swap(cnt2);
+      for (int u = 0; u < n_up; ++u) cnt[u + 1] += cnt[u];
+      upload(P, L0.pair_ptr, cnt);
+      upload(P, L0.blk_row, blk_row);
+      upload(P, L0.up_blk, up_blk);
+      upload(P, L0.mirror, mirror);
+      continue;
+    }
     std::vector<int> fill;
     std::vector<int2> pairs;
-    if (pass == 1) {
+    if (pass == 2) {
       fill.assign(cnt.begin(), cnt.end() - 1);
       pairs.resize(std::max(cnt[n_up], 1));
     }
@@ -1208,15 +1263,7 @@ static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
           else pairs[fill[u]++] = make_int2(o, q);
         }
       }
-    if (pass == 0) {
-      for (int u = 0; u < n_up; ++u) cnt[u + 1] += cnt[u];
-      upload(P, L0.pair_ptr, cnt);
-      upload(P, L0.blk_row, blk_row);
-      upload(P, L0.up_blk, up_blk);
-      upload(P, L0.mirror, mirror);
-    } else {
-      upload(P, L0.pairs, pairs);
-    }
+    if (pass == 2) upload(P, L0.pairs, pairs);
   }
   L0.n_up = n_up;
   sync(P);
