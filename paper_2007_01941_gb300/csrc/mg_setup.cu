@@ -636,8 +636,10 @@ k_aggregate_qr_df(int n_agg, int bs, int max_rows, const int* __restrict__ mptr,
       for (int pass = 0; pass < 2; ++pass) {
         // g_i = A[:, i] . A[:, j] for i < j
         float s = 0.f, c = 0.f;
-        if (gi < j)
+        if (gi < j) {
+#pragma unroll 4
           for (int r = gh; r < rows; r += 2) dot2_fma(s, c, at(r, gi), at(r, j));
+        }
         DF gv = DF(s, 0.f) + DF(c, 0.f);
         gv += DF(__shfl_xor_sync(kFull, gv.h, 16), __shfl_xor_sync(kFull, gv.l, 16));
         if (gh == 0 && gi < j) g[gi] = make_float2(gv.h, gv.l);
@@ -645,6 +647,7 @@ k_aggregate_qr_df(int n_agg, int bs, int max_rows, const int* __restrict__ mptr,
         // A[:, j] -= sum_{i<j} g_i A[:, i]
         for (int r = lane; r < rows; r += 32) {
           float ps = 0.f, pc = 0.f;
+#pragma unroll 4
           for (int i = 0; i < j; ++i) dot2_fma(ps, pc, g[i], A[r * kQrStride + i]);
           const DF v = at(r, j) - (DF(ps, 0.f) + DF(pc, 0.f));
           A[r * kQrStride + j] = make_float2(v.h, v.l);

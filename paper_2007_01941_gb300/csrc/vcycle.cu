@@ -49,13 +49,23 @@ struct VLevel {
 constexpr int kPhaseBS = 256;
 constexpr int kPhaseWarps = kPhaseBS / 32;
 
-// (D_i^-1 w)_u where lane v < BS holds w_v
+// Every kernel below first loads the data that no kernel of the cycle writes (block
+// rows of the operators, prolongator and Jacobi blocks, the coarse inverse, index
+// lists) into registers, then lets the next kernel of the stream launch, then waits for
+// its predecessor: with programmatic dependent launch those loads overlap the previous
+// kernel, and only the vector reads stay on the cycle's critical path.
+
+// row u of D_i^-1 (u = lane < BS) for block_apply
 template <typename T, int BS>
-__device__ __forceinline__ T block_apply(const T* __restrict__ Dinv_i, T w, int lane) {
+__device__ __forceinline__ void dinv_row(const T* __restrict__ Dinv_i, int lane, T dr[BS]) {
   const int u = lane < BS ? lane : 0;
-  T dr[BS];
 #pragma unroll
   for (int v = 0; v < BS; ++v) dr[v] = Dinv_i[u * BS + v];
+}
+
+// (D_i^-1 w)_u where lane v < BS holds w_v and dr is row u of D_i^-1
+template <typename T, int BS>
+__device__ __forceinline__ T block_apply(const T dr[BS], T w, int lane) {
   T acc = T(0);
 #pragma unroll
   for (int v = 0; v < BS; ++v) acc += dr[v] * __shfl_sync(kFull, w, v);
@@ -69,18 +79,61 @@ struct RowCta {
   static constexpr int kThreads = BS == 16 ? 128 : 96;
 };
 
-// q = (A v)_i by the whole CTA; on return q[u], u < BS, in shared memory (all threads)
+// the first kPre blocks of thread (u, h)'s share of block row i (row u of each) and
+// where its remaining blocks start
 template <typename T, int BS>
-__device__ __forceinline__ void cta_row_product(const VLevel<T>& L, int i, const T* __restrict__ v, T* part,
-                                                T* q) {
+struct RowPrefetch {
+  static constexpr int kPre = 2;
+  int e, e1, n;
+  int col[kPre];
+  T a[kPre][BS];
+};
+
+template <typename T, int BS>
+__device__ __forceinline__ void row_prefetch(const VLevel<T>& L, int i, RowPrefetch<T, BS>& p) {
+  constexpr int G = RowCta<BS>::G;
+  const int t = threadIdx.x;
+  const int u = t % BS, h = t / BS;
+  p.n = 0;
+  p.e = 0;
+  p.e1 = 0;
+  if (h >= G) return;
+  p.e1 = L.row_ptr[i + 1];
+  int e = L.row_ptr[i] + h;
+#pragma unroll
+  for (int k = 0; k < RowPrefetch<T, BS>::kPre; ++k) {
+    if (e < p.e1) {
+      p.col[k] = L.cols[e];
+      const T* a = L.vals + (size_t)e * (BS * BS) + u * BS;
+#pragma unroll
+      for (int c = 0; c < BS; ++c) p.a[k][c] = a[c];
+      p.n = k + 1;
+      e += G;
+    }
+  }
+  p.e = e;
+}
+
+// q = (A v)_i by the whole CTA from the prefetched blocks and the rest of the row; on
+// return q[u], u < BS, in shared memory (all threads)
+template <typename T, int BS>
+__device__ __forceinline__ void cta_row_product(const VLevel<T>& L, const RowPrefetch<T, BS>& p,
+                                                const T* __restrict__ v, T* part, T* q) {
   constexpr int G = RowCta<BS>::G;
   const int t = threadIdx.x;
   const int u = t % BS, h = t / BS;
   if (h < G) {
-    const int e1 = L.row_ptr[i + 1];
     T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < RowPrefetch<T, BS>::kPre; ++k) {
+      if (k < p.n) {
+        const T* xv = v + (size_t)p.col[k] * BS;
+#pragma unroll
+        for (int c = 0; c < BS; ++c) acc += p.a[k][c] * xv[c];
+      }
+    }
 #pragma unroll 2
-    for (int e = L.row_ptr[i] + h; e < e1; e += G) {
+    for (int e = p.e; e < p.e1; e += G) {
       const T* a = L.vals + (size_t)e * (BS * BS) + u * BS;
       const T* xv = v + (size_t)L.cols[e] * BS;
 #pragma unroll
@@ -98,12 +151,12 @@ __device__ __forceinline__ void cta_row_product(const VLevel<T>& L, int i, const
   __syncthreads();
 }
 
-// Dinv_i row u times the vector w held in shared memory
+// row u of Dinv_i times the vector w held in shared memory
 template <typename T, int BS>
-__device__ __forceinline__ T row_dinv(const T* __restrict__ Dinv_i, const T* w, int u) {
+__device__ __forceinline__ T row_dinv(const T dr[BS], const T* w) {
   T acc = T(0);
 #pragma unroll
-  for (int v = 0; v < BS; ++v) acc += Dinv_i[u * BS + v] * w[v];
+  for (int v = 0; v < BS; ++v) acc += dr[v] * w[v];
   return acc;
 }
 
@@ -111,19 +164,22 @@ __device__ __forceinline__ T row_dinv(const T* __restrict__ Dinv_i, const T* w, 
 // on level 0 b comes in as the FP64 right-hand side
 template <typename T, int BS>
 __global__ void __launch_bounds__(256) k_ph_first(VLevel<T> L, const double* __restrict__ in) {
-  pdl_wait();
-  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
   const T inv_theta = (T)(1.0 / L.cheb[0]);
+  T dr[BS];
+  if (gw < L.n) dinv_row<T, BS>(L.Dinv + (size_t)gw * BS * BS, lane, dr);
+  pdl_trigger();
+  pdl_wait();
   for (int i = gw; i < L.n; i += nw) {
+    if (i != gw) dinv_row<T, BS>(L.Dinv + (size_t)i * BS * BS, lane, dr);
     const size_t idx = (size_t)i * BS + lane;
     T bv = T(0);
     if (lane < BS) {
       bv = in ? (T)in[idx] : L.b[idx];
       if (in) L.b[idx] = bv;
     }
-    const T dv = block_apply<T, BS>(L.Dinv + (size_t)i * BS * BS, bv, lane) * inv_theta;
+    const T dv = block_apply<T, BS>(dr, bv, lane) * inv_theta;
     if (lane < BS) {
       L.r[0][idx] = bv;
       L.d[0][idx] = dv;
@@ -137,18 +193,22 @@ __global__ void __launch_bounds__(256) k_ph_first(VLevel<T> L, const double* __r
 template <typename T, int BS>
 __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_step(VLevel<T> L, int dc, int rc, int xc, T c1, T c2,
                                                                  double* __restrict__ out) {
-  pdl_wait();
-  pdl_trigger();
   __shared__ T part[RowCta<BS>::G * BS];
   __shared__ T q[BS], w[BS];
   const int i = blockIdx.x, t = threadIdx.x;
+  RowPrefetch<T, BS> pf;
+  row_prefetch<T, BS>(L, i, pf);
+  T dr[BS];
+  if (t < BS) dinv_row<T, BS>(L.Dinv + (size_t)i * BS * BS, t, dr);
+  pdl_trigger();
+  pdl_wait();
   const T* din = L.d[dc];
-  cta_row_product<T, BS>(L, i, din, part, q);
+  cta_row_product<T, BS>(L, pf, din, part, q);
   const size_t idx = (size_t)i * BS + t;
   if (t < BS) w[t] = L.r[rc][idx] - q[t];
   __syncthreads();
   if (t < BS) {
-    const T acc = row_dinv<T, BS>(L.Dinv + (size_t)i * BS * BS, w, t);
+    const T acc = row_dinv<T, BS>(dr, w);
     const T dn = c1 * din[idx] + c2 * acc;
     const T xn = L.x[xc][idx] + dn;
     L.r[1 - rc][idx] = w[t];
@@ -161,12 +221,14 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_step(VLevel<T> L, i
 // residual of the pre-smoothed iterate on row blockIdx.x: s = r - A d, into the free r buffer
 template <typename T, int BS>
 __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_residual(VLevel<T> L, int dc, int rc) {
-  pdl_wait();
-  pdl_trigger();
   __shared__ T part[RowCta<BS>::G * BS];
   __shared__ T q[BS];
   const int i = blockIdx.x, t = threadIdx.x;
-  cta_row_product<T, BS>(L, i, L.d[dc], part, q);
+  RowPrefetch<T, BS> pf;
+  row_prefetch<T, BS>(L, i, pf);
+  pdl_trigger();
+  pdl_wait();
+  cta_row_product<T, BS>(L, pf, L.d[dc], part, q);
   if (t < BS) {
     const size_t idx = (size_t)i * BS + t;
     L.r[1 - rc][idx] = L.r[rc][idx] - q[t];
@@ -178,16 +240,41 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_residual(VLevel<T> 
 // r_c = b_c, d_c = D_c^-1 b_c / theta_c, x_c = d_c
 template <typename T, int BS>
 __global__ void __launch_bounds__(256) k_ph_restrict(VLevel<T> L, VLevel<T> C, const T* __restrict__ res) {
-  pdl_wait();
-  pdl_trigger();
+  constexpr int kPre = 2;   // members per half-warp whose Q columns are prefetched
   const int lane = threadIdx.x & 31;
   const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (a >= C.n) return;
+  const bool live = a < C.n;
   // lane s + 16h adds members h, h + 2, ... of the aggregate into output s
   const int s = lane & 15, h = lane >> 4;
+  int m0 = 0, m1 = 0, mi[kPre];
+  T qa[kPre][BS];
+  T dr[16];
+  if (live) {
+    m0 = L.agg_ptr[a] + h;
+    m1 = L.agg_ptr[a + 1];
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      const int m = m0 + 2 * k;
+      mi[k] = m < m1 ? L.agg_mem[m] : 0;
+      const T* Qi = L.Q + (size_t)mi[k] * BS * 16 + s;
+#pragma unroll
+      for (int u = 0; u < BS; ++u) qa[k][u] = m < m1 ? Qi[u * 16] : T(0);
+    }
+    if (!C.coarsest) dinv_row<T, 16>(C.Dinv + (size_t)a * 256, lane, dr);
+  }
+  pdl_trigger();
+  pdl_wait();
+  if (!live) return;
   T acc = T(0);
-  const int m1 = L.agg_ptr[a + 1];
-  for (int m = L.agg_ptr[a] + h; m < m1; m += 2) {
+#pragma unroll
+  for (int k = 0; k < kPre; ++k) {
+    if (m0 + 2 * k < m1) {
+      const T* ri = res + (size_t)mi[k] * BS;
+#pragma unroll
+      for (int u = 0; u < BS; ++u) acc += qa[k][u] * ri[u];
+    }
+  }
+  for (int m = m0 + 2 * kPre; m < m1; m += 2) {
     const int i = L.agg_mem[m];
     const T* Qi = L.Q + (size_t)i * BS * 16 + s;
     const T* ri = res + (size_t)i * BS;
@@ -199,7 +286,7 @@ __global__ void __launch_bounds__(256) k_ph_restrict(VLevel<T> L, VLevel<T> C, c
   const size_t idx = (size_t)a * 16 + lane;
   if (lane < 16) C.b[idx] = acc;
   if (C.coarsest) return;
-  const T dv = block_apply<T, 16>(C.Dinv + (size_t)a * 256, acc, lane) * (T)(1.0 / C.cheb[0]);
+  const T dv = block_apply<T, 16>(dr, acc, lane) * (T)(1.0 / C.cheb[0]);
   if (lane < 16) {
     C.r[0][idx] = acc;
     C.d[0][idx] = dv;
@@ -207,16 +294,38 @@ __global__ void __launch_bounds__(256) k_ph_restrict(VLevel<T> L, VLevel<T> C, c
   }
 }
 
+// x_c = A_c^-1 b_c, one warp per row of the dense inverse (the row prefetched while the
+// previous kernel runs)
+constexpr int kCoarseRowMax = 16;   // doubles of an inverse row per lane held in registers
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_ph_coarsest(VLevel<T> C) {
-  pdl_wait();
-  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  double ar[kCoarseRowMax];
+  const bool pre = gw < C.N && C.N <= 32 * kCoarseRowMax;
+  if (pre) {
+    const double* a = C.Ainv + (size_t)gw * C.Np;
+#pragma unroll
+    for (int k = 0; k < kCoarseRowMax; ++k) {
+      const int j = lane + 32 * k;
+      ar[k] = j < C.N ? a[j] : 0.0;
+    }
+  }
+  pdl_trigger();
+  pdl_wait();
   for (int row = gw; row < C.N; row += nw) {
-    const double* a = C.Ainv + (size_t)row * C.Np;
     double acc = 0.0;
-    for (int j = lane; j < C.N; j += 32) acc += a[j] * (double)C.b[j];
+    if (pre && row == gw) {
+#pragma unroll
+      for (int k = 0; k < kCoarseRowMax; ++k) {
+        const int j = lane + 32 * k;
+        if (j < C.N) acc += ar[k] * (double)C.b[j];
+      }
+    } else {
+      const double* a = C.Ainv + (size_t)row * C.Np;
+      for (int j = lane; j < C.N; j += 32) acc += a[j] * (double)C.b[j];
+    }
     acc = warp_sum(acc);
     if (lane == 0) C.x[0][row] = (T)acc;
   }
@@ -225,18 +334,33 @@ __global__ void __launch_bounds__(256) k_ph_coarsest(VLevel<T> C) {
 // x_i += Q_i x_c[agg(i)]
 template <typename T>
 __global__ void __launch_bounds__(256) k_ph_prolong(VLevel<T> L, VLevel<T> C, int xl, int xcl) {
-  pdl_wait();
-  pdl_trigger();
   const int bs = L.bs;
+  const int idx0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  T qr[16];
+  int ag = 0;
+  if (idx0 < L.n * bs) {
+    const int i = idx0 / bs, u = idx0 - i * bs;
+    const T* Qi = L.Q + ((size_t)i * bs + u) * 16;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) qr[s] = Qi[s];
+    ag = L.agg[i];
+  }
+  pdl_trigger();
+  pdl_wait();
   T* x = L.x[xl];
   const T* xc = C.x[xcl];
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.n * bs; idx += gridDim.x * blockDim.x) {
-    const int i = idx / bs, u = idx - i * bs;
-    const T* Qi = L.Q + ((size_t)i * bs + u) * 16;
-    const T* xa = xc + (size_t)L.agg[i] * 16;
+  for (int idx = idx0; idx < L.n * bs; idx += stride) {
+    if (idx != idx0) {
+      const int i = idx / bs, u = idx - i * bs;
+      const T* Qi = L.Q + ((size_t)i * bs + u) * 16;
+#pragma unroll
+      for (int s = 0; s < 16; ++s) qr[s] = Qi[s];
+      ag = L.agg[i];
+    }
+    const T* xa = xc + (size_t)ag * 16;
     T acc = T(0);
 #pragma unroll
-    for (int s = 0; s < 16; ++s) acc += Qi[s] * xa[s];
+    for (int s = 0; s < 16; ++s) acc += qr[s] * xa[s];
     x[idx] += acc;
   }
 }
@@ -245,18 +369,22 @@ __global__ void __launch_bounds__(256) k_ph_prolong(VLevel<T> L, VLevel<T> C, in
 template <typename T, int BS>
 __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first(VLevel<T> L, int xc, int rc, int dc,
                                                                        double* __restrict__ out) {
-  pdl_wait();
-  pdl_trigger();
   __shared__ T part[RowCta<BS>::G * BS];
   __shared__ T q[BS], w[BS];
   const int i = blockIdx.x, t = threadIdx.x;
+  RowPrefetch<T, BS> pf;
+  row_prefetch<T, BS>(L, i, pf);
+  T dr[BS];
+  if (t < BS) dinv_row<T, BS>(L.Dinv + (size_t)i * BS * BS, t, dr);
+  pdl_trigger();
+  pdl_wait();
   const T* xin = L.x[xc];
-  cta_row_product<T, BS>(L, i, xin, part, q);
+  cta_row_product<T, BS>(L, pf, xin, part, q);
   const size_t idx = (size_t)i * BS + t;
   if (t < BS) w[t] = L.b[idx] - q[t];
   __syncthreads();
   if (t < BS) {
-    const T dv = row_dinv<T, BS>(L.Dinv + (size_t)i * BS * BS, w, t) * (T)(1.0 / L.cheb[0]);
+    const T dv = row_dinv<T, BS>(dr, w) * (T)(1.0 / L.cheb[0]);
     const T xn = xin[idx] + dv;
     L.r[rc][idx] = w[t];
     L.d[dc][idx] = dv;
