@@ -110,8 +110,8 @@ def k3_flops(n_o, n_p):
 
 def bsr_bytes(nnzb, n_c, w):
     # the assembled S: 81 values and a column index per block, a row pointer per camera;
-    # x read and y written once per camera
-    return nnzb * (81 * w + 4) + n_c * (4 + 2 * 9 * w)
+    # z and p read, the new direction and S times it written once per camera
+    return nnzb * (81 * w + 4) + n_c * (4 + 4 * 9 * w)
 
 
 # FP32 operations per term of the paired-FP32 assembly: the exact product (mul + 3 fma)
@@ -414,7 +414,7 @@ def gpu_main(args):
                     "peak_source": f"{n_sm} SMs x 128 FP32 lanes x max SM clock (FP32 lane operations)"}
     elif dom == "outer_bsr":
         k = kernels["outer_bsr"]
-        roofline = {"kernel": "k_bsr9_spmv<double>", "bound": "hbm", "achieved": k["achieved"], "peak": hbm,
+        roofline = {"kernel": "k_pcg_dir_spmv", "bound": "hbm", "achieved": k["achieved"], "peak": hbm,
                     "unit": "GB/s", "frac": k["achieved"] / hbm, "traffic": None, "peak_source": peak_note}
     elif dom == "schur_fp64":
         k = kernels["schur_fp64"]

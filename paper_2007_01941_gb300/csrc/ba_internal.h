@@ -194,6 +194,7 @@ struct ba_problem {
   // reductions and flags
   ba::DBuf scal;                // double [kScalars]
   ba::DBuf partial;             // double [partial_cap]
+  ba::DBuf partial2;            // double: per-CTA partial sums of the PCG's fused p.q
   ba::DBuf counter;             // unsigned [8]
   ba::DBuf flags;               // int [F_COUNT]
   double* h_scal = nullptr;     // pinned host mirror

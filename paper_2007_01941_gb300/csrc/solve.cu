@@ -400,7 +400,7 @@ __global__ void k_pcg_direction(size_t n, double* __restrict__ p, const double* 
   if (i < n) {
     const double pi = s_new >= 0 ? z[i] + beta * p[i] : z[i];
     p[i] = pi;
-    q[i] = Dc[i] * pi;
+    if (q) q[i] = Dc[i] * pi;
     if (ps) {
       const float h = (float)pi;
       ps[i] = make_float2(h, (float)(pi - (double)h));
@@ -476,6 +476,146 @@ static void pcg_tail(ba_problem* P) {
   launch_k(P, k_copy_slot, 1, 32, 0, P->scal.as<double>(), S_RZ, S_TMP2);
 }
 
+// ---------------------------------------------------------------------------
+// PCG with the assembled S (the PCG product of Section 3.6's choice when level 0 is
+// assembled): an iteration is the V-cycle, r.z, the direction update and two kernels,
+//   k_pcg_spmv_pq:       q = S p and p.q
+//   k_pcg_update_check:  alpha = r.z / p.q, x += alpha p, r -= alpha q, r.r, the
+//                        quadratic model, the stopping test and the graph condition
+// so the recurrences are the ones of the launch-per-operation path above, fused.
+// ---------------------------------------------------------------------------
+constexpr int kSpmvBS = 128;
+
+// q = S p with the FP64 blocks (one warp per block row: lane r + 9k takes row r of
+// blocks k, k + 3, ...; its first block is loaded before the programmatic wait) and p.q
+__global__ void __launch_bounds__(kSpmvBS)
+k_pcg_spmv_pq(int n, const int* __restrict__ row_ptr, const int* __restrict__ cols, const double* __restrict__ vals,
+              const double* __restrict__ p, double* __restrict__ q, double* partial, unsigned* counter,
+              double* pq_out) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (kSpmvBS / 32) + (threadIdx.x >> 5);
+  const int r = lane % 9, k = lane / 9;
+  const bool live = i < n && k < 3;
+  int e0 = 0, e1 = 0, c0 = 0;
+  double a0[9];
+  if (live) {
+    e0 = row_ptr[i] + k;
+    e1 = row_ptr[i + 1];
+    const int ef = min(e0, max(e1 - 1, 0));
+    c0 = cols[ef];
+    const double* a = vals + (size_t)ef * 81 + r * 9;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) a0[c] = a[c];
+  }
+  pdl_trigger();
+  pdl_wait();
+  double acc = 0.0;
+  if (live && e0 < e1) {
+    const double* x0 = p + (size_t)c0 * 9;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc += a0[c] * x0[c];
+    for (int e = e0 + 3; e < e1; e += 3) {
+      const double* a = vals + (size_t)e * 81 + r * 9;
+      const double* xv = p + (size_t)cols[e] * 9;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) acc += a[c] * xv[c];
+    }
+  }
+  const double a1 = __shfl_sync(kFull, acc, min(lane + 9, 31));
+  const double a2 = __shfl_sync(kFull, acc, min(lane + 18, 31));
+  double dot = 0.0;
+  if (i < n && lane < 9) {
+    const size_t idx = (size_t)i * 9 + r;
+    const double qi = acc + a1 + a2;
+    q[idx] = qi;
+    dot = p[idx] * qi;
+  }
+  grid_sum_store<kSpmvBS>(dot, partial, counter, pq_out);
+}
+
+__global__ void __launch_bounds__(kVecBS)
+k_pcg_update_check(size_t n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                   const double* __restrict__ q, double* scal, double* partial,
+                   unsigned* counter, int* flags, int max_iters, double rtol2, int rule, double tau, int use_cond,
+                   cudaGraphConditionalHandle h) {
+  pdl_trigger();
+  pdl_wait();
+  const double pq = scal[S_PQ], rz = scal[S_TMP2];
+  const double alpha = rz / pq;
+  const bool ok = pq > 0.0 && isfinite(alpha);
+  double acc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * kVecBS + threadIdx.x; i < n; i += (size_t)gridDim.x * kVecBS) {
+    double ri = r[i];
+    if (ok) {
+      x[i] += alpha * p[i];
+      ri -= alpha * q[i];
+      r[i] = ri;
+    }
+    acc += ri * ri;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!ok) flags[F_BREAKDOWN] = 1;
+    // quadratic model: Q_i - Q_{i-1} = -alpha (r.z) / 2
+    const double dq = ok ? -0.5 * alpha * rz : 0.0;
+    scal[S_DQ] = dq;
+    scal[S_Q] += dq;
+    scal[S_RZ] = rz;   // the next direction's beta divides by this r.z
+  }
+  // r.r by a deterministic grid reduction; the last block also counts the iteration and
+  // sets the loop condition (continue while not converged, no breakdown, below max_iters)
+  __shared__ bool am_last;
+  double s = block_sum<kVecBS>(acc);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    __threadfence();
+    am_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (am_last) {
+    __threadfence();
+    double t = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kVecBS) t += __ldcg(partial + b);
+    t = block_sum<kVecBS>(t);
+    if (threadIdx.x == 0) {
+      scal[S_RR] = t;
+      *counter = 0u;
+      const double it = scal[S_ITER] + 1.0;
+      scal[S_ITER] = it;
+      const bool stop = pcg_converged(rule, it, t, scal[S_BB], rtol2, __ldcg(scal + S_Q), __ldcg(scal + S_DQ), tau) ||
+                        __ldcg(flags + F_BREAKDOWN) != 0 || it >= (double)max_iters;
+      if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
+    }
+  }
+}
+
+// z = M r, r.z into scal[S_TMP2] and the direction p = z + (r.z / rz_old) p (p = z when
+// first); the r.z of the previous iteration is in scal[S_RZ]
+static void assembled_precond_direction(ba_problem* P, int first) {
+  const size_t n = (size_t)P->n_c * 9;
+  double *r = P->r.as<double>(), *z = P->z.as<double>(), *p = P->p.as<double>();
+  precond_apply(P, r, z);
+  dot64(P, r, z, n, S_TMP2);
+  launch_k(P, k_pcg_direction, cdiv((long long)n, 256), 256, 0, n, p, z, P->scal.as<double>(), first ? -1 : S_TMP2,
+           S_RZ, P->Dc.as<double>(), (double*)nullptr, (float2*)nullptr);
+}
+
+static void assembled_spmv(ba_problem* P) {
+  const Level& L0 = P->levels[0];
+  const int nb = cdiv(L0.n, kSpmvBS / 32);
+  KernelTimer kt(P, BA_KT_OUTER_BSR);
+  launch_k(P, k_pcg_spmv_pq, nb, kSpmvBS, 0, L0.n, L0.row_ptr.as<int>(), L0.cols.as<int>(), L0.vals64.as<double>(),
+           P->p.as<double>(), P->q.as<double>(), P->partial2.as<double>(), P->counter.as<unsigned>() + 1,
+           P->scal.as<double>() + S_PQ);
+}
+
+static void assembled_update(ba_problem* P, double* x, int use_cond, cudaGraphConditionalHandle h) {
+  const size_t n = (size_t)P->n_c * 9;
+  launch_k(P, k_pcg_update_check, reduce_blocks(P, n), kVecBS, 0, n, x, P->r.as<double>(), P->p.as<double>(),
+           P->q.as<double>(), P->scal.as<double>(), P->partial.as<double>(),
+           P->counter.as<unsigned>(), P->flags.as<int>(), P->opt.max_iters, P->opt.rtol * P->opt.rtol,
+           P->opt.stop_rule, P->opt.tau, use_cond, h);
+}
+
 // Builds [head, check] -> while(cond) { tail, head, check } as one executable graph that
 // works on the problem's own vectors (x = P->x).
 static void build_pcg_graph(ba_problem* P) {
@@ -494,10 +634,16 @@ static void build_pcg_graph(ba_problem* P) {
     cudaGraphConditionalHandle h;
     BA_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
     P->stream = P->cap_stream;
+    const bool assembled = P->outer_explicit;
     BA_CUDA(cudaStreamBeginCaptureToGraph(P->cap_stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    pcg_head(P, x);
-    launch_k(P, k_pcg_check, 1, 1, 0, P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2,
-                                         P->opt.stop_rule, P->opt.tau, h);
+    if (assembled) {
+      assembled_spmv(P);
+      assembled_update(P, x, 1, h);
+    } else {
+      pcg_head(P, x);
+      launch_k(P, k_pcg_check, 1, 1, 0, P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2,
+                                           P->opt.stop_rule, P->opt.tau, h);
+    }
     const long long head_kernels = P->launches - launches0;
     cudaStreamCaptureStatus status;
     const cudaGraphNode_t* deps = nullptr;
@@ -517,10 +663,16 @@ static void build_pcg_graph(ba_problem* P) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     BA_CUDA(cudaStreamBeginCaptureToGraph(P->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const long long body0 = P->launches;
-    pcg_tail(P);
-    pcg_head(P, x);
-    launch_k(P, k_pcg_check, 1, 1, 0, P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2,
-                                         P->opt.stop_rule, P->opt.tau, h);
+    if (assembled) {
+      assembled_precond_direction(P, 0);
+      assembled_spmv(P);
+      assembled_update(P, x, 1, h);
+    } else {
+      pcg_tail(P);
+      pcg_head(P, x);
+      launch_k(P, k_pcg_check, 1, 1, 0, P->scal.as<double>(), P->flags.as<int>(), P->opt.max_iters, rtol2,
+                                           P->opt.stop_rule, P->opt.tau, h);
+    }
     BA_CUDA(cudaStreamEndCapture(P->cap_stream, &body));
     BA_CUDA(cudaGraphInstantiate(&P->pcg_exec, g, 0));
     cudaGraphDestroy(g);
@@ -567,11 +719,18 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
     BA_REQUIRE(bb == 0.0, BA_ERR_INVALID_ARG, "non-finite right-hand side");
     return;
   }
-  precond_apply(P, r, z);
+  const bool assembled = P->outer_explicit;
   int s_rz = S_RZ, s_new = S_TMP2;
-  dot64(P, r, z, n, s_rz);
-  launch_k(P, k_pcg_direction, g, 256, 0, n, p, z, scal, -1, 0, P->Dc.as<double>(), q,
-                                            split_target(P));  // p = z
+  if (assembled) {
+    // per-row-group partial sums of the fused p.q, sized before any graph capture
+    P->partial2.ensure(sizeof(double) * ((size_t)cdiv(P->n_c, kSpmvBS / 32) + 64));
+    assembled_precond_direction(P, 1);
+  } else {
+    precond_apply(P, r, z);
+    dot64(P, r, z, n, s_rz);
+    launch_k(P, k_pcg_direction, g, 256, 0, n, p, z, scal, -1, 0, P->Dc.as<double>(), q,
+                                              split_target(P));  // p = z
+  }
   const int rg = reduce_blocks(P, n);
   const double rtol2 = P->opt.rtol * P->opt.rtol;
   double rel = 1.0;
@@ -604,10 +763,15 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
     }
   }
   while (it < P->opt.max_iters) {
-    outer_product(P, p, q);
-    dot64(P, p, q, n, S_PQ);
-    launch_k(P, k_pcg_update, rg, kVecBS, 0, n, dc, r, p, q, scal, s_rz, P->partial.as<double>(),
-                                               P->counter.as<unsigned>(), P->flags.as<int>());
+    if (assembled) {
+      assembled_spmv(P);
+      assembled_update(P, dc, 0, 0);
+    } else {
+      outer_product(P, p, q);
+      dot64(P, p, q, n, S_PQ);
+      launch_k(P, k_pcg_update, rg, kVecBS, 0, n, dc, r, p, q, scal, s_rz, P->partial.as<double>(),
+                                                 P->counter.as<unsigned>(), P->flags.as<int>());
+    }
     ++it;
     fetch_scalars(P, S_RR, S_DQ - S_RR + 1);
     rel = std::sqrt(P->h_scal[S_RR] / bb);
@@ -616,6 +780,10 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
     done = pcg_converged(P->opt.stop_rule, (double)it, P->h_scal[S_RR], bb, rtol2, P->h_scal[S_Q],
                          P->h_scal[S_DQ], P->opt.tau);
     if (done) break;
+    if (assembled) {
+      assembled_precond_direction(P, 0);
+      continue;
+    }
     precond_apply(P, r, z);
     dot64(P, r, z, n, s_new);
     launch_k(P, k_pcg_direction, g, 256, 0, n, p, z, scal, s_new, s_rz, P->Dc.as<double>(), q,
