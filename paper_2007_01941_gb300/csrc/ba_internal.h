@@ -108,6 +108,7 @@ struct Level {
   DBuf Q64, Q32;                // double/float [n][bs][16] prolongator blocks
   DBuf kept;                    // uint32 [n] kept-dof masks of this level's nodes
   DBuf Dblk, Dinv64, Dinv32;    // diagonal blocks and their inverses [n][bs][bs]
+  DBuf Dblk32;                  // FP32 copy of the diagonal blocks (mixed precision)
   DBuf cheb;                    // double[4]: theta, delta, sigma1, lambda_max
   double cheb_host[4] = {1, 1, 1, 1};  // host copy of the same
   double lam_max = 0.0;

@@ -24,8 +24,8 @@ struct LzLevel {
   const int* row_ptr;
   const int* cols;
   const T* vals;
-  const double* D;      // diagonal blocks [n][bs][bs]
-  const double* Dinv;   // their inverses
+  const T* D;           // diagonal blocks [n][bs][bs] in the level's precision
+  const T* Dinv;        // their inverses
   T* v;                 // start vector
   T* w;                 // unscaled next direction
   T* q[2];              // current / previous direction (by step parity)
@@ -84,16 +84,17 @@ __device__ __forceinline__ void lz_reduce(double v, double* partial, unsigned* c
   }
 }
 
-// y_i = B_i x_i for one block row (B double blocks); thread u < bs returns component u
+// y_i = B_i x_i for one block row, in the level's precision; thread u < bs returns
+// component u
 template <typename T>
-__device__ __forceinline__ double lz_block_row(const double* __restrict__ B, int bs, int i, const T* x) {
+__device__ __forceinline__ double lz_block_row(const T* __restrict__ B, int bs, int i, const T* x) {
   const int u = threadIdx.x;
   if (u >= bs) return 0.0;
-  const double* b = B + ((size_t)i * bs + u) * bs;
+  const T* b = B + ((size_t)i * bs + u) * bs;
   const T* xi = x + (size_t)i * bs;
-  double acc = 0.0;
-  for (int c = 0; c < bs; ++c) acc += b[c] * (double)xi[c];
-  return acc;
+  T acc = T(0);
+  for (int c = 0; c < bs; ++c) acc += b[c] * xi[c];
+  return (double)acc;
 }
 
 // v = start vector (SplitMix64 of the level-local index, mapped to [-1, 1)); s[0] = v^T D v
@@ -132,16 +133,18 @@ __global__ void __launch_bounds__(kLzBS) k_lz_product(LzArgs<T> A, int j) {
   // threads split the row's blocks: G groups of bs threads
   const int G = kLzBS / bs;
   const int u = t % bs, h = t / bs;
-  double acc = 0.0;
+  // the row's products in the level's precision (an estimate of lambda_max needs no
+  // more; FP32 arithmetic also keeps this off the GPU's narrow FP64 unit), their sum in FP64
+  T acc = T(0);
   if (h < G) {
     const int e1 = L.row_ptr[i + 1];
     for (int e = L.row_ptr[i] + h; e < e1; e += G) {
       const T* a = L.vals + (size_t)e * bs * bs + u * bs;
       const T* xv = src + (size_t)L.cols[e] * bs;
-      for (int c = 0; c < bs; ++c) acc += (double)a[c] * (double)xv[c];
+      for (int c = 0; c < bs; ++c) acc += a[c] * xv[c];
     }
   }
-  part_sm[t] = h < G ? acc : 0.0;
+  part_sm[t] = h < G ? (double)acc : 0.0;
   __syncthreads();
   double contrib = 0.0;
   if (t < bs) {
@@ -224,8 +227,8 @@ static void run(ba_problem* P, int first, int last) {
     d.row_ptr = L.row_ptr.as<int>();
     d.cols = L.cols.as<int>();
     d.vals = sizeof(T) == 4 ? (const T*)L.vals32.p : (const T*)L.vals64.p;
-    d.D = L.Dblk.as<double>();
-    d.Dinv = L.Dinv64.as<double>();
+    d.D = sizeof(T) == 4 ? (const T*)L.Dblk32.p : (const T*)L.Dblk.p;
+    d.Dinv = sizeof(T) == 4 ? (const T*)L.Dinv32.p : (const T*)L.Dinv64.p;
     d.v = vb;
     d.w = vb + n;
     d.q[0] = vb + 2 * n;

@@ -584,92 +584,120 @@ k_aggregate_qr(int n_agg, int bs, int max_rows, const int* __restrict__ mptr, co
   if (lane == 0) kept_out[a] = kept;
 }
 
-// The same factorisation in paired FP32 (DF) for the mixed-precision hierarchy: one
-// warp per aggregate, A in shared memory as (hi, lo) pairs.  The FP64 unit of this GPU
-// issues a warp's FMA over many cycles per SM sub-partition, so the FP64 kernel above
-// is bound by it even at these sizes; DF runs on the FP32 pipes.  The inner products of
-// a pass are spread over the lanes (lane i + 16h: column i, rows h, h + 2, ...), so
-// no lane computes products for columns at or after the current one.
-constexpr int kQrDfWarps = 4;
+// The same factorisation in paired FP32 (DF) for the mixed-precision hierarchy (the FP64
+// unit of this GPU issues a warp's FMA over many cycles per SM sub-partition, DF runs on
+// the FP32 pipes), with one CTA of kQrDfBS threads per aggregate: the inner products
+// of a pass are split over the CTA (thread i + 16 k: column i, rows k, k + 8, ...), the
+// projection over rows (one row per thread), so the dependency chain of a column is a few
+// block reductions long instead of one warp's walk over all rows.
+constexpr int kQrDfBS = 128;
+constexpr int kQrDfParts = kQrDfBS / 16;
 
-__global__ void __launch_bounds__(kQrDfWarps * 32)
-k_aggregate_qr_df(int n_agg, int bs, int max_rows, const int* __restrict__ mptr, const int* __restrict__ mem,
-                  const double* __restrict__ K, double* __restrict__ Q64, float* __restrict__ Q32,
-                  double* __restrict__ Kc, unsigned* __restrict__ kept_out) {
-  extern __shared__ __align__(16) unsigned char qsm[];
-  __shared__ float2 Rs[kQrDfWarps][kNull][kNull + 1];
-  __shared__ float2 gs[kQrDfWarps][kNull];
+// sum over the CTA of one DF value per thread; every thread gets the total
+__device__ __forceinline__ DF qr_block_sum_df(DF v, float2* red /*[kQrDfBS / 32]*/) {
+  v = warp_sum_df(v);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int a = blockIdx.x * kQrDfWarps + warp;
-  if (a >= n_agg) return;
-  float2* A = reinterpret_cast<float2*>(qsm) + (size_t)warp * max_rows * kQrStride;  // [rows][kQrStride]
-  float2(*R)[kNull + 1] = Rs[warp];
-  float2* g = gs[warp];
+  __syncthreads();
+  if (lane == 0) red[warp] = make_float2(v.h, v.l);
+  __syncthreads();
+  DF s(0.f, 0.f);
+#pragma unroll
+  for (int w = 0; w < kQrDfBS / 32; ++w) s += DF(red[w].x, red[w].y);
+  return s;
+}
+
+__global__ void __launch_bounds__(kQrDfBS)
+k_aggregate_qr_df_cta(int n_agg, int bs, const int* __restrict__ mptr, const int* __restrict__ mem,
+                      const double* __restrict__ K, double* __restrict__ Q64, float* __restrict__ Q32,
+                      double* __restrict__ Kc, unsigned* __restrict__ kept_out) {
+  extern __shared__ __align__(16) unsigned char qsm[];
+  float2* A = reinterpret_cast<float2*>(qsm);  // [rows][kQrStride]
+  __shared__ float2 R[kNull][kNull + 1];
+  __shared__ float2 gpart[kQrDfParts / 2][kNull];   // per-warp partial inner products
+  __shared__ float2 g[kNull];
+  __shared__ float2 red[kQrDfBS / 32];
+  __shared__ float2 scale_sm;
+  const int a = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int mb = mptr[a], me = mptr[a + 1];
   const int rows = (me - mb) * bs;
-  for (int e = lane; e < rows * kNull; e += 32) {
+  for (int e = t; e < rows * kNull; e += kQrDfBS) {
     const int r = e / kNull, j = e - r * kNull;
     const int s = r / bs, u = r - s * bs;
     const DF v(K[((size_t)mem[mb + s] * bs + u) * kNull + j]);
     A[r * kQrStride + j] = make_float2(v.h, v.l);
   }
-  for (int e = lane; e < kNull * kNull; e += 32) R[e / kNull][e % kNull] = make_float2(0.f, 0.f);
-  __syncwarp();
+  for (int e = t; e < kNull * kNull; e += kQrDfBS) R[e / kNull][e % kNull] = make_float2(0.f, 0.f);
+  __syncthreads();
   auto at = [&](int r, int j) {
     const float2 v = A[r * kQrStride + j];
     return DF(v.x, v.y);
   };
   auto col_norm = [&](int j) {
     float s = 0.f, c = 0.f;
-    for (int r = lane; r < rows; r += 32) {
+    for (int r = t; r < rows; r += kQrDfBS) {
       const DF v = at(r, j);
       dot2_fma(s, c, v, v);
     }
-    return df_sqrt(warp_sum_df(DF(s, 0.f) + DF(c, 0.f)));
+    return df_sqrt(qr_block_sum_df(DF(s, 0.f) + DF(c, 0.f), red));
   };
-  const int gi = lane & 15, gh = lane >> 4;
+  const int gi = t & 15, part = t >> 4;   // part = 2 warp + (lane >> 4)
   unsigned kept = 0;
+  DF rc(0.f, 0.f);   // threads t < 16: R[t][j] of the current column
   for (int j = 0; j < kNull; ++j) {
     const DF n0 = col_norm(j);
-    DF rc(0.f, 0.f);
+    rc = DF(0.f, 0.f);
     if (j > 0) {
       for (int pass = 0; pass < 2; ++pass) {
         // g_i = A[:, i] . A[:, j] for i < j
         float s = 0.f, c = 0.f;
         if (gi < j) {
-#pragma unroll 4
-          for (int r = gh; r < rows; r += 2) dot2_fma(s, c, at(r, gi), at(r, j));
+#pragma unroll 2
+          for (int r = part; r < rows; r += kQrDfParts) dot2_fma(s, c, at(r, gi), at(r, j));
         }
         DF gv = DF(s, 0.f) + DF(c, 0.f);
         gv += DF(__shfl_xor_sync(kFull, gv.h, 16), __shfl_xor_sync(kFull, gv.l, 16));
-        if (gh == 0 && gi < j) g[gi] = make_float2(gv.h, gv.l);
-        __syncwarp();
+        if (lane < 16) gpart[warp][lane] = make_float2(gv.h, gv.l);
+        __syncthreads();
+        if (t < kNull) {
+          DF tot(0.f, 0.f);
+#pragma unroll
+          for (int w = 0; w < kQrDfParts / 2; ++w) tot += DF(gpart[w][t].x, gpart[w][t].y);
+          if (t >= j) tot = DF(0.f, 0.f);
+          g[t] = make_float2(tot.h, tot.l);
+          rc += tot;
+        }
+        __syncthreads();
         // A[:, j] -= sum_{i<j} g_i A[:, i]
-        for (int r = lane; r < rows; r += 32) {
+        for (int r = t; r < rows; r += kQrDfBS) {
           float ps = 0.f, pc = 0.f;
 #pragma unroll 4
           for (int i = 0; i < j; ++i) dot2_fma(ps, pc, g[i], A[r * kQrStride + i]);
           const DF v = at(r, j) - (DF(ps, 0.f) + DF(pc, 0.f));
           A[r * kQrStride + j] = make_float2(v.h, v.l);
         }
-        __syncwarp();
-        if (gi < j) rc += gv;
+        __syncthreads();
       }
     }
     const DF nv = col_norm(j);
     const bool keep = n0.h > 0.f && nv.h > 1e-10f * n0.h;
-    const DF scale = keep ? DF(1.f, 0.f) / nv : DF(0.f, 0.f);
-    for (int r = lane; r < rows; r += 32) {
+    if (t == 0) {
+      const DF sc = keep ? DF(1.f, 0.f) / nv : DF(0.f, 0.f);
+      scale_sm = make_float2(sc.h, sc.l);
+    }
+    __syncthreads();
+    const DF scale(scale_sm.x, scale_sm.y);
+    for (int r = t; r < rows; r += kQrDfBS) {
       const DF v = at(r, j) * scale;
       A[r * kQrStride + j] = make_float2(v.h, v.l);
     }
     if (keep) kept |= 1u << j;
-    if (gh == 0 && gi < j) R[gi][j] = make_float2(rc.h, rc.l);
-    if (lane == 0) R[j][j] = keep ? make_float2(nv.h, nv.l) : make_float2(0.f, 0.f);
-    __syncwarp();
+    if (t < j) R[t][j] = make_float2(rc.h, rc.l);
+    if (t == 0) R[j][j] = keep ? make_float2(nv.h, nv.l) : make_float2(0.f, 0.f);
+    __syncthreads();
   }
   // Q blocks back to the member nodes
-  for (int e = lane; e < rows * kNull; e += 32) {
+  for (int e = t; e < rows * kNull; e += kQrDfBS) {
     const int r = e / kNull, j = e - r * kNull;
     const int s = r / bs, u = r - s * bs;
     const size_t dst = ((size_t)mem[mb + s] * bs + u) * kNull + j;
@@ -677,11 +705,11 @@ k_aggregate_qr_df(int n_agg, int bs, int max_rows, const int* __restrict__ mptr,
     Q64[dst] = to_double(q);
     Q32[dst] = q.h;
   }
-  for (int e = lane; e < kNull * kNull; e += 32) {
+  for (int e = t; e < kNull * kNull; e += kQrDfBS) {
     const float2 v = R[e / kNull][e % kNull];
     Kc[(size_t)a * kNull * kNull + e] = to_double(DF(v.x, v.y));
   }
-  if (lane == 0) kept_out[a] = kept;
+  if (t == 0) kept_out[a] = kept;
 }
 
 // The same factorisation with one CTA of kQrBS threads per aggregate, rows spread over
@@ -1269,6 +1297,11 @@ __global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* __restrict__ A, 
   }
 }
 
+__global__ void k_d2f_vec(size_t n, const double* __restrict__ a, float* __restrict__ b) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
 static void dense_inverse(ba_problem* P, Level& L) {
   const int N = L.n * L.bs;
   const int Np = (N + kGJ - 1) / kGJ * kGJ;
@@ -1472,6 +1505,14 @@ void mg_setup(ba_problem* P) {
       launched(P);
       block_inverse(P, L.Dblk.as<double>(), L.n, L.bs, L.Dinv64.as<double>(), L.Dinv32.as<float>(), F_NOT_SPD_JACOBI);
     }
+    if (fp32) {
+      // FP32 diagonal blocks for the batched Lanczos
+      const size_t nb2 = (size_t)L.bs * L.bs * L.n;
+      L.Dblk32.ensure(sizeof(float) * nb2 + 64);
+      k_d2f_vec<<<cdiv((long long)std::max<size_t>(nb2, 1), 256), 256, 0, P->stream>>>(nb2, L.Dblk.as<double>(),
+                                                                                       L.Dblk32.as<float>());
+      launched(P);
+    }
     // assembled levels get their Lanczos estimate in one batch after the loop
     if (l == 0 && !P->l0_explicit) {
       if (fp32) lanczos<float>(P, l);
@@ -1487,10 +1528,11 @@ void mg_setup(ba_problem* P) {
     const size_t qsm = sizeof(double) * (size_t)kQrWarps * max_rows * kQrStride;
     BA_REQUIRE(qsm <= 200 * 1024, BA_ERR_LIMIT, "aggregates too large for the aggregate QR");
     if (fp32) {
-      // mixed precision: the DF factorisation, one warp per aggregate at every level
-      BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
-      k_aggregate_qr_df<<<cdiv(L1.n, kQrDfWarps), kQrDfWarps * 32, qsm, P->stream>>>(
-          L1.n, L.bs, max_rows, L.agg_ptr.as<int>(), L.agg_mem.as<int>(), L.K.as<double>(), L.Q64.as<double>(),
+      // mixed precision: the DF factorisation, one CTA per aggregate at every level
+      const size_t dsm = sizeof(float2) * (size_t)max_rows * kQrStride;
+      BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr_df_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+      k_aggregate_qr_df_cta<<<L1.n, kQrDfBS, dsm, P->stream>>>(
+          L1.n, L.bs, L.agg_ptr.as<int>(), L.agg_mem.as<int>(), L.K.as<double>(), L.Q64.as<double>(),
           L.Q32.as<float>(), L1.K.as<double>(), L1.kept.as<unsigned>());
     } else if (L1.n >= 2 * P->n_sm) {
       BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));

@@ -255,9 +255,79 @@ __global__ void __launch_bounds__(256) k_block_inverse_warp(const double* __rest
   }
 }
 
+// The same Gauss-Jordan inversion in DF (mixed precision): the FP64 unit of this GPU
+// would take a warp's FP64 instruction over many cycles per SM sub-partition, while the
+// paired-FP32 steps run on the FP32 pipes.  The inverse is accurate to about 2^-48 times
+// the block's condition number, beyond what the FP32 smoother blocks it feeds can hold.
+template <int BS>
+__global__ void __launch_bounds__(256) k_block_inverse_warp_df(const double* __restrict__ in, int n,
+                                                               double* __restrict__ out64, float* __restrict__ out32,
+                                                               int* flags, int flag_slot) {
+  constexpr int PER = (BS * BS + 31) / 32;
+  __shared__ float2 sa[8][BS * BS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int blk = blockIdx.x * 8 + warp;
+  if (blk >= n) return;
+  float2* a = sa[warp];
+  const double* src = in + (size_t)blk * BS * BS;
+  for (int e = lane; e < BS * BS; e += 32) {
+    const DF v(src[e]);
+    a[e] = make_float2(v.h, v.l);
+  }
+  __syncwarp();
+  auto at = [&](int e) { return DF(a[e].x, a[e].y); };
+  bool ok = true;
+  for (int k = 0; k < BS; ++k) {
+    const DF p = at(k * BS + k);
+    if (!(p.h > 0.f)) ok = false;
+    const DF ip = DF(1.f, 0.f) / p;
+    DF nv[PER];
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int e = lane + 32 * t;
+      if (e < BS * BS) {
+        const int i = e / BS, j = e - (e / BS) * BS;
+        DF v;
+        if (i == k && j == k) v = ip;
+        else if (i == k) v = at(k * BS + j) * ip;
+        else if (j == k) v = -(at(i * BS + k) * ip);
+        else v = at(e) - at(i * BS + k) * (at(k * BS + j) * ip);
+        nv[t] = v;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int e = lane + 32 * t;
+      if (e < BS * BS) a[e] = make_float2(nv[t].h, nv[t].l);
+    }
+    __syncwarp();
+  }
+  if (!ok && lane == 0) flags[flag_slot] = 1;
+  for (int e = lane; e < BS * BS; e += 32) {
+    DF v(0.f, 0.f);
+    if (ok) {
+      const DF sym = at(e) + at((e % BS) * BS + e / BS);   // symmetrise
+      v = DF(0.5f * sym.h, 0.5f * sym.l);
+    }
+    out64[(size_t)blk * BS * BS + e] = to_double(v);
+    if (out32) out32[(size_t)blk * BS * BS + e] = v.h;
+  }
+}
+
 void block_inverse(ba_problem* P, const double* in, int n, int bs, double* out64, float* out32,
                    int flag_slot) {
   if (n == 0) return;
+  if (P->opt.precision == BA_MIXED) {
+    if (bs == 9)
+      k_block_inverse_warp_df<9><<<cdiv(n, 8), 256, 0, P->stream>>>(in, n, out64, out32, P->flags.as<int>(),
+                                                                     flag_slot);
+    else
+      k_block_inverse_warp_df<16><<<cdiv(n, 8), 256, 0, P->stream>>>(in, n, out64, out32, P->flags.as<int>(),
+                                                                      flag_slot);
+    launched(P);
+    return;
+  }
   if (bs == 9)
     k_block_inverse_warp<9><<<cdiv(n, 8), 256, 0, P->stream>>>(in, n, out64, out32, P->flags.as<int>(), flag_slot);
   else
