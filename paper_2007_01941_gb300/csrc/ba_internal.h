@@ -103,6 +103,7 @@ struct Level {
   DBuf agg_ptr, agg_mem;        // member lists of the next-level nodes
   DBuf pair_ptr, pairs, blk_row; // level 0: observation pairs per work block (int [n_up+1], int2), block rows
   DBuf up_blk, mirror;          // level 0: blocks on and above the diagonal and their transposes
+  DBuf gal_ptr, gal_list, gal_row;  // fine blocks (block, row) per block of the next level, its rows
   int n_up = 0;
   DBuf K;                       // double [n][bs][16] near-nullspace rows
   DBuf Q64, Q32;                // double/float [n][bs][16] prolongator blocks

@@ -851,13 +851,77 @@ k_aggregate_qr_cta(int n_agg, int bs, const int* __restrict__ mptr, const int* _
 }
 
 // ---------------------------------------------------------------------------
-// Galerkin product A_{l+1} = P^T A_l P (Section 2.3) on the coarse pattern; one CTA
-// per coarse row, thread (r, s) owns entry (r, s) of every block of the row.
+// Galerkin product A_{l+1} = P^T A_l P (Section 2.3) on the coarse pattern:
+//   A_{l+1}[a, b] = sum_{i in a} sum_{j in b, A_ij != 0} Q_i^T A_ij Q_j.
+// The fine blocks that meet in each coarse block are listed once per problem (members of
+// a in list order, then the row's blocks in order), and one warp owns a coarse block:
+// lane s + 16 h keeps entries (8 h .. 8 h + 7, s) in registers and adds each fine
+// block's Q_i^T (A_ij Q_j) to them.  A coarse dof dropped by the QR (zero Q column) gets
+// a unit diagonal, which decouples it.
 // ---------------------------------------------------------------------------
-constexpr int kGalBS = 256;
-template <typename T>
+constexpr int kGalBS = 128;
+
+template <typename T, int BS>
 __global__ void __launch_bounds__(kGalBS)
-k_galerkin(int bs, const int* __restrict__ row_ptr, const int* __restrict__ cols, const T* __restrict__ vals,
+k_galerkin(int nnzb_c, const int* __restrict__ gal_ptr, const int2* __restrict__ gal_list,
+           const int* __restrict__ gal_row, const int* __restrict__ ccols, const int* __restrict__ cols,
+           const T* __restrict__ vals, const T* __restrict__ Q, const unsigned* __restrict__ ckept,
+           T* __restrict__ cvals) {
+  const int lane = threadIdx.x & 31;
+  const int ce = blockIdx.x * (kGalBS / 32) + (threadIdx.x >> 5);
+  if (ce >= nnzb_c) return;
+  const int s = lane & 15, r0 = (lane >> 4) * 8;
+  T out[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) out[k] = T(0);
+  for (int q = gal_ptr[ce]; q < gal_ptr[ce + 1]; ++q) {
+    const int2 ei = gal_list[q];
+    const int e = ei.x, i = ei.y, j = cols[e];
+    // U[u] = (A_ij Q_j)[u][s]
+    T qj[BS];
+#pragma unroll
+    for (int v = 0; v < BS; ++v) qj[v] = Q[((size_t)j * BS + v) * 16 + s];
+    const T* A = vals + (size_t)e * BS * BS;
+    T U[BS];
+#pragma unroll
+    for (int u = 0; u < BS; ++u) {
+      T acc = T(0);
+#pragma unroll
+      for (int v = 0; v < BS; ++v) acc += A[u * BS + v] * qj[v];
+      U[u] = acc;
+    }
+    // (Q_i^T U)[r][s] for r = r0 .. r0 + 7
+    T acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = T(0);
+#pragma unroll
+    for (int u = 0; u < BS; ++u) {
+      const T* qi = Q + ((size_t)i * BS + u) * 16 + r0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] += qi[k] * U[u];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) out[k] += acc[k];
+  }
+  const int a = gal_row[ce];
+  const bool diag = ccols[ce] == a;
+  const unsigned kept = ckept[a];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int r = r0 + k;
+    T v = out[k];
+    if (diag && r == s && !((kept >> r) & 1u)) v = T(1);
+    cvals[(size_t)ce * 256 + r * 16 + s] = v;
+  }
+}
+
+// The same product with one CTA per coarse row, thread (r, s) owning entry (r, s) of every
+// block of the row: the faster form for the 16x16 blocks of the coarse levels, whose rows
+// gather many fine blocks.
+constexpr int kGalRowBS = 256;
+template <typename T>
+__global__ void __launch_bounds__(kGalRowBS)
+k_galerkin_rows(int bs, const int* __restrict__ row_ptr, const int* __restrict__ cols, const T* __restrict__ vals,
            const T* __restrict__ Q, const int* __restrict__ agg, const int* __restrict__ mptr,
            const int* __restrict__ mem, const int* __restrict__ crow_ptr, const int* __restrict__ ccols,
            const unsigned* __restrict__ ckept, T* __restrict__ cvals) {
@@ -907,6 +971,56 @@ k_galerkin(int bs, const int* __restrict__ row_ptr, const int* __restrict__ cols
     for (int e = cb; e < ce; ++e)
       if (ccols[e] == a) cvals[(size_t)e * 256 + t] = T(1);
   }
+}
+
+// the fine blocks of level L that meet in each block of level L1 (built on the host once)
+static void galerkin_symbolic(ba_problem* P, Level& L, Level& L1) {
+  auto down = [&](std::vector<int>& h, const DBuf& d, size_t n) {
+    h.resize(std::max<size_t>(n, 1));
+    if (n) BA_CUDA(cudaMemcpyAsync(h.data(), d.p, sizeof(int) * n, cudaMemcpyDeviceToHost, P->stream));
+  };
+  std::vector<int> rp, cl, agg, aptr, amem, crp, ccl;
+  down(rp, L.row_ptr, L.n + 1);
+  down(cl, L.cols, L.nnzb);
+  down(agg, L.agg, L.n);
+  down(aptr, L.agg_ptr, L1.n + 1);
+  down(amem, L.agg_mem, L.n);
+  down(crp, L1.row_ptr, L1.n + 1);
+  down(ccl, L1.cols, L1.nnzb);
+  sync(P);
+  std::vector<int> crow(std::max(L1.nnzb, 1)), cnt(L1.nnzb + 1, 0);
+  for (int a = 0; a < L1.n; ++a)
+    for (int c = crp[a]; c < crp[a + 1]; ++c) crow[c] = a;
+  auto slot = [&](int a, int b) {
+    int lo = crp[a], hi = crp[a + 1];
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (ccl[mid] < b) lo = mid + 1;
+      else hi = mid;
+    }
+    BA_REQUIRE(lo < crp[a + 1] && ccl[lo] == b, BA_ERR_STATE, "coarse pattern misses a Galerkin block");
+    return lo;
+  };
+  std::vector<int2> list(std::max(L.nnzb, 1));
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<int> fill;
+    if (pass == 1) fill.assign(cnt.begin(), cnt.end() - 1);
+    for (int a = 0; a < L1.n; ++a)
+      for (int m = aptr[a]; m < aptr[a + 1]; ++m) {
+        const int i = amem[m];
+        for (int e = rp[i]; e < rp[i + 1]; ++e) {
+          const int c = slot(a, agg[cl[e]]);
+          if (pass == 0) ++cnt[c + 1];
+          else list[fill[c]++] = make_int2(e, i);
+        }
+      }
+    if (pass == 0)
+      for (int c = 0; c < L1.nnzb; ++c) cnt[c + 1] += cnt[c];
+  }
+  upload(P, L.gal_ptr, cnt);
+  upload(P, L.gal_list, list);
+  upload(P, L.gal_row, crow);
+  sync(P);
 }
 
 // diagonal blocks of a BSR level as double
@@ -1141,9 +1255,8 @@ static void finish_lanczos(ba_problem* P) {
 
 // ---------------------------------------------------------------------------
 // coarsest level: dense FP64 matrix from the BSR blocks, padded with identity to a
-// multiple of 32, inverted in place by blocked Gauss-Jordan (SPD, no pivoting) in a
-// cooperative kernel: per 32-wide pivot block, the pivot row/column panels are
-// copied out, the grid synchronises, every tile is updated, the grid synchronises.
+// multiple of the pivot width, inverted by blocked Gauss-Jordan (SPD, no pivoting) in a
+// cooperative kernel with one grid barrier per pivot block.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_bsr_to_dense(int n, int bs, const int* __restrict__ row_ptr, const int* __restrict__ cols,
@@ -1166,132 +1279,108 @@ __global__ void k_dense_identity_pad(int N, int Np, double* __restrict__ A) {
 }
 
 constexpr int kGJ = 16;   // pivot block: its inversion is the serial part of every step
-constexpr int kGJBS = 256;
-// Per pivot block K (kGJ wide):
-//   phase 1: CTA 0 inverts P = A_KK in shared memory (Gauss-Jordan, SPD, no pivoting) into
-//            pinv; every CTA copies the column panel A_IK into pcol;
-//   phase 2: new row panel prow_J = P^-1 A_KJ (J != K), prow_K = P^-1;
-//   phase 3: A_IJ <- A_IJ - A_IK prow_J and A_IK <- -A_IK P^-1 (I != K), A_KJ <- prow_J.
-// Work items are whole tiles (kGJSplit pieces each); grid-wide syncs separate the
-// phases, and no phase writes a tile that it also reads.
-constexpr int kGJSplit = 1;                 // work items per tile
-constexpr int kGJRows = kGJ / kGJSplit;
-
-// out (kGJRows x kGJ rows r0.. of the tile) = a (rows r0.. of an kGJ x kGJ tile, ld_a) * b (kGJ x kGJ, ld_b)
-__device__ __forceinline__ void gj_rows_product(const double* __restrict__ a, size_t ld_a, const double* __restrict__ b,
-                                                size_t ld_b, double sa[kGJRows][kGJ + 1], double sb[kGJ][kGJ + 1],
-                                                double acc[kGJRows * kGJ / kGJBS]) {
-  const int t = threadIdx.x;
-  for (int e = t; e < kGJRows * kGJ; e += kGJBS) sa[e / kGJ][e % kGJ] = a[(size_t)(e / kGJ) * ld_a + e % kGJ];
-  for (int e = t; e < kGJ * kGJ; e += kGJBS) sb[e / kGJ][e % kGJ] = b[(size_t)(e / kGJ) * ld_b + e % kGJ];
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < kGJRows * kGJ / kGJBS; ++q) {
-    const int e = t + q * kGJBS, u = e / kGJ, v = e % kGJ;
-    double s = 0.0;
-#pragma unroll 8
-    for (int k = 0; k < kGJ; ++k) s += sa[u][k] * sb[k][v];
-    acc[q] = s;
+constexpr int kGJBS = kGJ * kGJ;
+// in-place inverse of the SPD kGJ x kGJ matrix in shared memory (Gauss-Jordan, no
+// pivoting; one thread per entry); returns false in thread 0 if a pivot is not positive
+__device__ __forceinline__ bool gj_invert(double piv[kGJ][kGJ + 1], double* gj_row, double* gj_col, double& gj_ip) {
+  const int t = threadIdx.x, u = t / kGJ, v = t % kGJ;
+  bool ok = true;
+  for (int k = 0; k < kGJ; ++k) {
+    if (t == 0) {
+      const double pk = piv[k][k];
+      if (!(pk > 0.0)) ok = false;
+      gj_ip = 1.0 / pk;
+    }
+    __syncthreads();
+    const double ip = gj_ip;
+    if (t < kGJ) {
+      gj_row[t] = t == k ? ip : piv[k][t] * ip;
+      gj_col[t] = piv[t][k];
+    }
+    __syncthreads();
+    double nv;
+    if (u == k) nv = gj_row[v];
+    else if (v == k) nv = -gj_col[u] * ip;
+    else nv = piv[u][v] - gj_col[u] * gj_row[v];
+    piv[u][v] = nv;
+    __syncthreads();
   }
-  __syncthreads();
+  return ok;
 }
 
-__global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* __restrict__ A, int Np, double* __restrict__ pinv,
-                                                        double* __restrict__ pcol, double* __restrict__ prow,
-                                                        int* flags) {
+// Per pivot block K (kGJ wide) every CTA reads P^-1 = (A_KK)^-1 and writes its tiles of
+// the next matrix:
+//   A'_KK = P^-1,  A'_KJ = P^-1 A_KJ,  A'_IK = -A_IK P^-1,  A'_IJ = A_IJ - A_IK (P^-1 A_KJ)
+// reading A and writing A' (two buffers that swap roles every step).  The CTA that
+// writes the next pivot block A'_{K+1,K+1} inverts it before the step's grid barrier, so
+// a step needs one barrier and the inversion overlaps the other CTAs' tiles.
+__global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* Aa, double* Ab, int Np, double* pinv, int* flags) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double piv[kGJ][kGJ + 1];
   __shared__ double gj_row[kGJ], gj_col[kGJ];
   __shared__ double gj_ip;
-  __shared__ double sa[kGJRows][kGJ + 1];
-  __shared__ double sb[kGJ][kGJ + 1];
-  constexpr int kPer = kGJRows * kGJ / kGJBS;   // outputs per thread in a work item
+  __shared__ double sa[kGJ][kGJ + 1], sb[kGJ][kGJ + 1], st[kGJ][kGJ + 1];
   const int nb = Np / kGJ;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, u = t / kGJ, v = t % kGJ;
+  if (blockIdx.x == 0) {
+    piv[u][v] = Aa[(size_t)u * Np + v];
+    __syncthreads();
+    const bool ok = gj_invert(piv, gj_row, gj_col, gj_ip);
+    if (t == 0 && !ok) flags[F_NOT_SPD_COARSE] = 1;
+    pinv[t] = piv[u][v];
+  }
+  grid.sync();
   for (int K = 0; K < nb; ++K) {
+    const double* A = (K & 1) ? Ab : Aa;
+    double* An = (K & 1) ? Aa : Ab;
     const int K0 = K * kGJ;
-    // phase 1
-    for (size_t idx = (size_t)blockIdx.x * kGJBS + t; idx < (size_t)Np * kGJ; idx += (size_t)gridDim.x * kGJBS) {
-      const int r = (int)(idx / kGJ), c = (int)(idx % kGJ);
-      pcol[idx] = A[(size_t)r * Np + K0 + c];
+    piv[u][v] = pinv[(size_t)(K & 1) * kGJBS + t];
+    __syncthreads();
+    bool owner = false;
+    for (int w = blockIdx.x; w < nb * nb; w += gridDim.x) {
+      const int I = w / nb, J = w - I * nb;
+      if (I == K + 1 && J == K + 1) owner = true;
+      double out;
+      if (I == K && J == K) {
+        out = piv[u][v];
+      } else if (I == K) {
+        sb[u][v] = A[(size_t)(K0 + u) * Np + J * kGJ + v];
+        __syncthreads();
+        out = 0.0;
+#pragma unroll
+        for (int k = 0; k < kGJ; ++k) out += piv[u][k] * sb[k][v];
+      } else if (J == K) {
+        sa[u][v] = A[(size_t)(I * kGJ + u) * Np + K0 + v];
+        __syncthreads();
+        out = 0.0;
+#pragma unroll
+        for (int k = 0; k < kGJ; ++k) out -= sa[u][k] * piv[k][v];
+      } else {
+        sa[u][v] = A[(size_t)(I * kGJ + u) * Np + K0 + v];
+        sb[u][v] = A[(size_t)(K0 + u) * Np + J * kGJ + v];
+        const double aij = A[(size_t)(I * kGJ + u) * Np + J * kGJ + v];
+        __syncthreads();
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < kGJ; ++k) s += piv[u][k] * sb[k][v];
+        st[u][v] = s;
+        __syncthreads();
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < kGJ; ++k) acc += sa[u][k] * st[k][v];
+        out = aij - acc;
+      }
+      An[(size_t)(I * kGJ + u) * Np + J * kGJ + v] = out;
+      __syncthreads();   // the tile buffers are refilled by the next work item
     }
-    if (blockIdx.x == 0) {
-      // in place: each step reads its own element plus the pivot row (scaled) and the
-      // pivot column (old values) from shared copies; the reciprocal is formed once
-      for (int e = t; e < kGJ * kGJ; e += kGJBS) piv[e / kGJ][e % kGJ] = A[(size_t)(K0 + e / kGJ) * Np + K0 + e % kGJ];
+    if (owner) {
+      // the next pivot block, just written by this CTA, inverted for every CTA's next step
+      const int K1 = K0 + kGJ;
+      piv[u][v] = An[(size_t)(K1 + u) * Np + K1 + v];
       __syncthreads();
-      bool bad = false;
-      for (int k = 0; k < kGJ; ++k) {
-        if (t == 0) {
-          const double pk = piv[k][k];
-          if (!(pk > 0.0)) bad = true;
-          gj_ip = 1.0 / pk;
-        }
-        __syncthreads();
-        const double ip = gj_ip;
-        if (t < kGJ) {
-          gj_row[t] = t == k ? ip : piv[k][t] * ip;
-          gj_col[t] = piv[t][k];
-        }
-        __syncthreads();
-        for (int e = t; e < kGJ * kGJ; e += kGJBS) {
-          const int i = e / kGJ, j = e % kGJ;
-          double v;
-          if (i == k) v = gj_row[j];
-          else if (j == k) v = -gj_col[i] * ip;
-          else v = piv[i][j] - gj_col[i] * gj_row[j];
-          piv[i][j] = v;
-        }
-        __syncthreads();
-      }
-      if (bad) flags[F_NOT_SPD_COARSE] = 1;
-      for (int e = t; e < kGJ * kGJ; e += kGJBS) pinv[e] = piv[e / kGJ][e % kGJ];
-    }
-    grid.sync();
-    // phase 2: work items (J, row quarter) of the row panel
-    for (int w = blockIdx.x; w < nb * kGJSplit; w += gridDim.x) {
-      const int J = w / kGJSplit, r0 = (w % kGJSplit) * kGJRows;
-      double acc[kPer];
-      if (J == K) {
-        for (int q = 0; q < kPer; ++q) {
-          const int e = t + q * kGJBS;
-          acc[q] = pinv[(r0 + e / kGJ) * kGJ + e % kGJ];
-        }
-      } else {
-        gj_rows_product(pinv + (size_t)r0 * kGJ, kGJ, A + (size_t)K0 * Np + J * kGJ, Np, sa, sb, acc);
-      }
-      for (int q = 0; q < kPer; ++q) {
-        const int e = t + q * kGJBS;
-        prow[(size_t)(r0 + e / kGJ) * Np + J * kGJ + e % kGJ] = acc[q];
-      }
-    }
-    grid.sync();
-    // phase 3: work items (I, J, row quarter)
-    for (int w = blockIdx.x; w < nb * nb * kGJSplit; w += gridDim.x) {
-      const int I = w / (nb * kGJSplit);
-      const int rem = w - I * nb * kGJSplit;
-      const int J = rem / kGJSplit, r0 = (rem % kGJSplit) * kGJRows;
-      if (I == K) {
-        for (int e = t; e < kGJRows * kGJ; e += kGJBS)
-          A[(size_t)(K0 + r0 + e / kGJ) * Np + J * kGJ + e % kGJ] = prow[(size_t)(r0 + e / kGJ) * Np + J * kGJ + e % kGJ];
-        continue;
-      }
-      double acc[kPer];
-      const double* a = pcol + (size_t)(I * kGJ + r0) * kGJ;   // old A_IK rows
-      if (J == K) {
-        gj_rows_product(a, kGJ, pinv, kGJ, sa, sb, acc);
-        for (int q = 0; q < kPer; ++q) {
-          const int e = t + q * kGJBS;
-          A[(size_t)(I * kGJ + r0 + e / kGJ) * Np + K0 + e % kGJ] = -acc[q];
-        }
-      } else {
-        gj_rows_product(a, kGJ, prow + (size_t)J * kGJ, Np, sa, sb, acc);
-        for (int q = 0; q < kPer; ++q) {
-          const int e = t + q * kGJBS;
-          double* dst = A + (size_t)(I * kGJ + r0 + e / kGJ) * Np + J * kGJ + e % kGJ;
-          *dst -= acc[q];
-        }
-      }
+      const bool ok = gj_invert(piv, gj_row, gj_col, gj_ip);
+      if (t == 0 && !ok) flags[F_NOT_SPD_COARSE] = 1;
+      pinv[(size_t)((K + 1) & 1) * kGJBS + t] = piv[u][v];
     }
     grid.sync();
   }
@@ -1320,18 +1409,20 @@ static void dense_inverse(ba_problem* P, Level& L) {
   launched(P);
   k_dense_identity_pad<<<cdiv((long long)Np * Np, 256), 256, 0, P->stream>>>(N, Np, A);
   launched(P);
-  P->scratch.ensure(sizeof(double) * (2 * (size_t)kGJ * Np + kGJ * kGJ) + 64);
-  double* pinv = P->scratch.as<double>();
-  double* pcol = pinv + (size_t)kGJ * kGJ;
-  double* prow = pcol + (size_t)kGJ * Np;
+  // second buffer of the ping-pong and the two pivot inverses
+  P->scratch.ensure(sizeof(double) * ((size_t)Np * Np + 2 * kGJBS) + 64);
+  double* B = P->scratch.as<double>();
+  double* pinv = B + (size_t)Np * Np;
   int nblk = 0;
   BA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, k_gauss_jordan, kGJBS, 0));
   const int nbk = Np / kGJ;
-  int grid = std::max(1, std::min(nblk * P->n_sm, nbk * nbk * kGJSplit));
+  int grid = std::max(1, std::min(nblk * P->n_sm, nbk * nbk));
   int* flags = P->flags.as<int>();
-  void* args[] = {(void*)&A, (void*)&Np, (void*)&pinv, (void*)&pcol, (void*)&prow, (void*)&flags};
+  void* args[] = {(void*)&A, (void*)&B, (void*)&Np, (void*)&pinv, (void*)&flags};
   BA_CUDA(cudaLaunchCooperativeKernel((void*)k_gauss_jordan, grid, kGJBS, args, 0, P->stream));
   launched(P);
+  // after an odd number of steps the inverse is in the second buffer
+  if (nbk & 1) BA_CUDA(cudaMemcpyAsync(A, B, sizeof(double) * (size_t)Np * Np, cudaMemcpyDeviceToDevice, P->stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -1547,21 +1638,34 @@ void mg_setup(ba_problem* P) {
                                                           L1.K.as<double>(), L1.kept.as<unsigned>());
     }
     launched(P);
-    // Galerkin
-    if (fp32) {
-      L1.vals32.ensure(sizeof(float) * 256 * (size_t)L1.nnzb + 64);
-      k_galerkin<float><<<L1.n, kGalBS, 0, P->stream>>>(L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
-                                                        L.vals32.as<float>(), L.Q32.as<float>(), L.agg.as<int>(),
-                                                        L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
-                                                        L1.row_ptr.as<int>(), L1.cols.as<int>(),
-                                                        L1.kept.as<unsigned>(), L1.vals32.as<float>());
+    // Galerkin: warp per coarse block from level 0 (9x9 fine blocks), CTA per coarse row below
+    if (fp32) L1.vals32.ensure(sizeof(float) * 256 * (size_t)L1.nnzb + 64);
+    else L1.vals64.ensure(sizeof(double) * 256 * (size_t)L1.nnzb + 64);
+    if (L.bs == 9) {
+      if (!L.gal_ptr.p) galerkin_symbolic(P, L, L1);
+      const int gg = cdiv(std::max(L1.nnzb, 1), kGalBS / 32);
+      if (fp32)
+        k_galerkin<float, 9><<<gg, kGalBS, 0, P->stream>>>(
+            L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(), L.gal_row.as<int>(), L1.cols.as<int>(),
+            L.cols.as<int>(), L.vals32.as<float>(), L.Q32.as<float>(), L1.kept.as<unsigned>(), L1.vals32.as<float>());
+      else
+        k_galerkin<double, 9><<<gg, kGalBS, 0, P->stream>>>(
+            L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(), L.gal_row.as<int>(), L1.cols.as<int>(),
+            L.cols.as<int>(), L.vals64.as<double>(), L.Q64.as<double>(), L1.kept.as<unsigned>(),
+            L1.vals64.as<double>());
+    } else if (fp32) {
+      k_galerkin_rows<float><<<L1.n, kGalRowBS, 0, P->stream>>>(L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                             L.vals32.as<float>(), L.Q32.as<float>(), L.agg.as<int>(),
+                                                             L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
+                                                             L1.row_ptr.as<int>(), L1.cols.as<int>(),
+                                                             L1.kept.as<unsigned>(), L1.vals32.as<float>());
     } else {
-      L1.vals64.ensure(sizeof(double) * 256 * (size_t)L1.nnzb + 64);
-      k_galerkin<double><<<L1.n, kGalBS, 0, P->stream>>>(L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
-                                                         L.vals64.as<double>(), L.Q64.as<double>(), L.agg.as<int>(),
-                                                         L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
-                                                         L1.row_ptr.as<int>(), L1.cols.as<int>(),
-                                                         L1.kept.as<unsigned>(), L1.vals64.as<double>());
+      k_galerkin_rows<double><<<L1.n, kGalRowBS, 0, P->stream>>>(L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                              L.vals64.as<double>(), L.Q64.as<double>(),
+                                                              L.agg.as<int>(), L.agg_ptr.as<int>(),
+                                                              L.agg_mem.as<int>(), L1.row_ptr.as<int>(),
+                                                              L1.cols.as<int>(), L1.kept.as<unsigned>(),
+                                                              L1.vals64.as<double>());
     }
     launched(P);
   }
