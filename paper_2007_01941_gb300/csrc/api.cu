@@ -60,6 +60,12 @@ __global__ void k_cinv_to_user(const double* __restrict__ src, size_t ldp, int n
   for (int k = 0; k < 9; ++k) d[k] = src[idx[k] * ldp + i];
 }
 
+// (hi, lo) float pairs -> their double sums
+__global__ void k_df2d(size_t n, const float2* __restrict__ in, double* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i].x + (double)in[i].y;
+}
+
 __global__ void k_f2d(size_t n, const float* __restrict__ a, double* __restrict__ b) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (double)a[i];
@@ -176,7 +182,7 @@ void ba_destroy(ba_problem* P) {
     ba::DBuf* lb[] = {&L.row_ptr, &L.cols, &L.W, &L.vals64, &L.vals32, &L.sptr, &L.sidx, &L.agg, &L.agg_ptr,
                       &L.agg_mem, &L.K, &L.Q64, &L.Q32, &L.kept, &L.Dblk, &L.Dinv64, &L.Dinv32, &L.cheb,
                       &L.Ainv, &L.vx, &L.vb, &L.vr, &L.vd, &L.vq, &L.vt, &L.vs, &L.pair_ptr, &L.pairs,
-                      &L.blk_row, &L.up_blk, &L.mirror, &L.Dblk32, &L.gal_ptr,
+                      &L.blk_row, &L.up_blk, &L.mirror, &L.Dblk32, &L.valsdf, &L.gal_ptr,
                       &L.gal_list, &L.gal_row};
     for (ba::DBuf* b : lb) b->release();
   }
@@ -421,7 +427,9 @@ ba_status ba_get_array(ba_problem* P, int which, int level, void* dst, size_t by
       case BA_ARR_LEVEL_W: D2D(L->W.p, need); break;
       case BA_ARR_LEVEL_VALS: {
         const size_t n = (size_t)L->nnzb * L->bs * L->bs;
-        if (P->opt.precision == BA_MIXED && !(level == 0 && P->outer_explicit))
+        if (P->opt.precision == BA_MIXED && level == 0 && P->outer_explicit)
+          k_df2d<<<ba::cdiv((long long)std::max<size_t>(n, 1), 256), 256, 0, P->stream>>>(n, L->valsdf.as<float2>(), d);
+        else if (P->opt.precision == BA_MIXED)
           k_f2d<<<ba::cdiv((long long)std::max<size_t>(n, 1), 256), 256, 0, P->stream>>>(n, L->vals32.as<float>(), d);
         else
           D2D(L->vals64.p, need);

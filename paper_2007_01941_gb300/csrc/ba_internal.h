@@ -95,6 +95,7 @@ struct Level {
   int maxrow = 1;               // longest block row
   DBuf row_ptr, cols, W;        // BSR pattern (int32) and covisibility counts (int64)
   DBuf vals64, vals32;          // operator blocks [nnzb][bs][bs]
+  DBuf valsdf;                  // level 0 in mixed precision: FP64 blocks as (hi, lo) float pairs
   DBuf sptr, sidx;              // strength-ordered neighbour lists
   int n_strength = 0;
   DBuf agg;                     // int32 [n] aggregate (= next-level node) of each node
@@ -143,7 +144,7 @@ struct ba_problem {
   int k3_grid[2] = {0, 0};       // Schur product CTAs per launch (FP32, FP64), set at first use
   int k3_grid_df = 0;           // the same for the paired-FP32 product
   bool l0_explicit = false;     // V-cycle level 0 uses the assembled S (set by the multigrid setup)
-  bool outer_explicit = false;  // the PCG product uses the FP64 blocks of the assembled S
+  bool outer_explicit = false;  // the PCG product uses the FP64-valued blocks of the assembled S
   bool vc_ready = false;        // the fused-phase V-cycle applies (set by the multigrid setup)
   bool j64_valid = false;       // J64 holds the current records (mixed precision forms it on demand)
   ba::DBuf lz_vec, lz_red, lz_cnt, lz_ptr;  // batched Lanczos vectors, reductions, counters, pointers

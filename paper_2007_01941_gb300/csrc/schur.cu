@@ -1185,13 +1185,13 @@ k_explicit_pairs(const T* __restrict__ W, int n_up, const int* __restrict__ up_b
 
 // Paired-FP32 assembly (mixed precision): the same blocks from the DF rows of
 // k_schur_w_df, each batch's sums compensated (dot2_fma) and folded into DF
-// accumulators; writes the FP64 value of each block (for the PCG product) and its FP32
-// rounding (for the V-cycle and the Galerkin product).
+// accumulators; writes each block as (hi, lo) float pairs (its FP64 value, for the PCG
+// product) and its FP32 rounding (for the V-cycle and the Galerkin product).
 __global__ void __launch_bounds__(kExWarps * 32)
 k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restrict__ up_blk,
                     const int* __restrict__ mirror, const int* __restrict__ blk_row, const int* __restrict__ cols,
                     const int* __restrict__ pair_ptr, const int2* __restrict__ pairs, const double* __restrict__ Scc,
-                    double* __restrict__ vals64, float* __restrict__ vals32) {
+                    float2* __restrict__ valsdf, float* __restrict__ vals32) {
   constexpr int kB = 8;
   __shared__ __align__(16) float2 stage[kExWarps][2][2 * kB][kWld];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1201,9 +1201,9 @@ k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restri
   const int c = blk_row[e];
   if (cols[e] == c) {
     for (int i = lane; i < 81; i += 32) {
-      const double v = Scc[(size_t)c * 81 + i];
-      vals64[(size_t)e * 81 + i] = v;
-      vals32[(size_t)e * 81 + i] = (float)v;
+      const DF v(Scc[(size_t)c * 81 + i]);
+      valsdf[(size_t)e * 81 + i] = make_float2(v.h, v.l);
+      vals32[(size_t)e * 81 + i] = v.h;
     }
     return;
   }
@@ -1241,10 +1241,10 @@ k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restri
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
       const DF v = -acc[u];
-      const double d = to_double(v);
-      vals64[o + u] = d;
+      const float2 d = make_float2(v.h, v.l);
+      valsdf[o + u] = d;
       vals32[o + u] = v.h;
-      vals64[m + 9 * (3 * lg + u)] = d;
+      valsdf[m + 9 * (3 * lg + u)] = d;
       vals32[m + 9 * (3 * lg + u)] = v.h;
     }
   }
@@ -1346,7 +1346,7 @@ void explicit_schur(ba_problem* P, Level& L0, ExplicitMode mode) {
   const int ldp = (int)P->ldp;
   if (mode == EX_PAIRED) {
     L0.vals32.ensure(sizeof(float) * 81 * (size_t)L0.nnzb + 64);
-    L0.vals64.ensure(sizeof(double) * 81 * (size_t)L0.nnzb + 64);
+    L0.valsdf.ensure(sizeof(float2) * 81 * (size_t)L0.nnzb + 64);
     P->scratch.ensure(sizeof(float2) * kWld * (size_t)std::max(P->n_o, 1) + 64);
     float2* W2 = P->scratch.as<float2>();
     if (P->n_o) {
@@ -1357,7 +1357,7 @@ void explicit_schur(ba_problem* P, Level& L0, ExplicitMode mode) {
     KernelTimer kt(P, BA_KT_ASSEMBLY);
     k_explicit_pairs_df<<<gb, kExWarps * 32, 0, P->stream>>>(
         W2, L0.n_up, L0.up_blk.as<int>(), L0.mirror.as<int>(), L0.blk_row.as<int>(), L0.cols.as<int>(),
-        L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(), L0.vals64.as<double>(),
+        L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(), L0.valsdf.as<float2>(),
         L0.vals32.as<float>());
   } else if (mode == EX_FP32) {
     L0.vals32.ensure(sizeof(float) * 81 * (size_t)L0.nnzb + 64);

@@ -5,6 +5,7 @@
 
 #include "ba_internal.h"
 #include "device_util.cuh"
+#include "dfloat.cuh"
 
 namespace ba {
 
@@ -414,18 +415,9 @@ static float2* split_target(ba_problem* P) {
   return P->xsplit.as<float2>();
 }
 
-// q = S p for the PCG: the FP64 blocks of the assembled S when level 0 is assembled
-// (overwriting q), else the implicit product added to q = D_c p, written with p
-static void outer_product(ba_problem* P, const double* p, double* q) {
-  if (P->outer_explicit) {
-    const Level& L0 = P->levels[0];
-    KernelTimer kt(P, BA_KT_OUTER_BSR);
-    launch_k(P, k_bsr9_spmv<double>, cdiv(L0.n, 4), 128, 0, L0.n, L0.row_ptr.as<int>(), L0.cols.as<int>(),
-             L0.vals64.as<double>(), p, q);
-    return;
-  }
-  matvec64_accumulate(P, p, q);
-}
+// q = S p for the PCG with the implicit operator: the product added to q = D_c p,
+// written with p
+static void outer_product(ba_problem* P, const double* p, double* q) { matvec64_accumulate(P, p, q); }
 
 // one PCG iteration's head: q = S p; alpha = rz / p.q; x += alpha p; r -= alpha q; rr = r.r
 static void pcg_head(ba_problem* P, double* x) {
@@ -588,6 +580,63 @@ k_pcg_update_check(size_t n, double* __restrict__ x, double* __restrict__ r, con
   }
 }
 
+// The same product in mixed precision from the blocks as (hi, lo) float pairs and the
+// direction split the same way (written with p): each lane's terms in a compensated sum
+// (dot2_fma), the three partial rows added in DF, q formed as a double.
+__global__ void __launch_bounds__(kSpmvBS)
+k_pcg_spmv_pq_df(int n, const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                 const float2* __restrict__ vals, const float2* __restrict__ ps, const double* __restrict__ p,
+                 double* __restrict__ q, double* partial, unsigned* counter, double* pq_out) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (kSpmvBS / 32) + (threadIdx.x >> 5);
+  const int r = lane % 9, k = lane / 9;
+  const bool live = i < n && k < 3;
+  int e0 = 0, e1 = 0, c0 = 0;
+  float2 a0[9];
+  if (live) {
+    e0 = row_ptr[i] + k;
+    e1 = row_ptr[i + 1];
+    const int ef = min(e0, max(e1 - 1, 0));
+    c0 = cols[ef];
+    const float2* a = vals + (size_t)ef * 81 + r * 9;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) a0[c] = a[c];
+  }
+  pdl_trigger();
+  pdl_wait();
+  float sh = 0.f, sc = 0.f;
+  if (live && e0 < e1) {
+    const float2* x0 = ps + (size_t)c0 * 9;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) dot2_fma(sh, sc, a0[c], x0[c]);
+    for (int e = e0 + 3; e < e1; e += 3) {
+      const float2* a = vals + (size_t)e * 81 + r * 9;
+      const float2* xv = ps + (size_t)cols[e] * 9;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) dot2_fma(sh, sc, a[c], xv[c]);
+    }
+  }
+  DF acc = DF(sh, 0.f) + DF(sc, 0.f);
+  const int l1 = min(lane + 9, 31), l2 = min(lane + 18, 31);
+  const DF a1(__shfl_sync(kFull, acc.h, l1), __shfl_sync(kFull, acc.l, l1));
+  const DF a2(__shfl_sync(kFull, acc.h, l2), __shfl_sync(kFull, acc.l, l2));
+  double dot = 0.0;
+  if (i < n && lane < 9) {
+    const size_t idx = (size_t)i * 9 + r;
+    const double qi = to_double(acc + a1 + a2);
+    q[idx] = qi;
+    dot = p[idx] * qi;
+  }
+  grid_sum_store<kSpmvBS>(dot, partial, counter, pq_out);
+}
+
+// the split of p that the mixed-precision product reads
+static float2* assembled_split(ba_problem* P) {
+  if (P->opt.precision != BA_MIXED) return nullptr;
+  P->xsplit.ensure(sizeof(float2) * 9 * (size_t)P->n_c + 64);
+  return P->xsplit.as<float2>();
+}
+
 // z = M r, r.z into scal[S_TMP2] and the direction p = z + (r.z / rz_old) p (p = z when
 // first); the r.z of the previous iteration is in scal[S_RZ]
 static void assembled_precond_direction(ba_problem* P, int first) {
@@ -596,16 +645,21 @@ static void assembled_precond_direction(ba_problem* P, int first) {
   precond_apply(P, r, z);
   dot64(P, r, z, n, S_TMP2);
   launch_k(P, k_pcg_direction, cdiv((long long)n, 256), 256, 0, n, p, z, P->scal.as<double>(), first ? -1 : S_TMP2,
-           S_RZ, P->Dc.as<double>(), (double*)nullptr, (float2*)nullptr);
+           S_RZ, P->Dc.as<double>(), (double*)nullptr, assembled_split(P));
 }
 
 static void assembled_spmv(ba_problem* P) {
   const Level& L0 = P->levels[0];
   const int nb = cdiv(L0.n, kSpmvBS / 32);
   KernelTimer kt(P, BA_KT_OUTER_BSR);
-  launch_k(P, k_pcg_spmv_pq, nb, kSpmvBS, 0, L0.n, L0.row_ptr.as<int>(), L0.cols.as<int>(), L0.vals64.as<double>(),
-           P->p.as<double>(), P->q.as<double>(), P->partial2.as<double>(), P->counter.as<unsigned>() + 1,
-           P->scal.as<double>() + S_PQ);
+  if (P->opt.precision == BA_MIXED)
+    launch_k(P, k_pcg_spmv_pq_df, nb, kSpmvBS, 0, L0.n, L0.row_ptr.as<int>(), L0.cols.as<int>(),
+             L0.valsdf.as<float2>(), P->xsplit.as<float2>(), P->p.as<double>(), P->q.as<double>(),
+             P->partial2.as<double>(), P->counter.as<unsigned>() + 1, P->scal.as<double>() + S_PQ);
+  else
+    launch_k(P, k_pcg_spmv_pq, nb, kSpmvBS, 0, L0.n, L0.row_ptr.as<int>(), L0.cols.as<int>(),
+             L0.vals64.as<double>(), P->p.as<double>(), P->q.as<double>(), P->partial2.as<double>(),
+             P->counter.as<unsigned>() + 1, P->scal.as<double>() + S_PQ);
 }
 
 static void assembled_update(ba_problem* P, double* x, int use_cond, cudaGraphConditionalHandle h) {
