@@ -1,6 +1,6 @@
 // Lanczos estimate of lambda_max(D^-1 A) in the D-inner product (Section 3.4), for all
 // assembled smoothed levels at once: each kernel of the recurrence covers the block rows
-// of every level (one CTA per block row), and the inner products are per-level
+// of every level (one warp per block row, each CTA within one level), and the inner products are per-level
 // deterministic grid reductions written straight into the level's Chebyshev buffer
 // (alpha_j at slot 8 + j, beta_j at slot 16 + j).  The same recurrence, level by level,
 // is the path of mg_setup.cu for an implicit level 0:
@@ -20,7 +20,7 @@ constexpr int kLzBS = 128;
 
 template <typename T>
 struct LzLevel {
-  int n, bs, row0;   // rows, block size, first CTA of the level in the batched grid
+  int n, bs, cta0, nct;   // rows, block size, first CTA of the level in the batched grid, its CTAs
   const int* row_ptr;
   const int* cols;
   const T* vals;
@@ -32,7 +32,7 @@ struct LzLevel {
   T* Aq;
   double* cheb;         // level buffer: [8 + j] alpha_j, [16 + j] beta_j
   double* s;            // [0] |v|_D^2, [1 + j] |w_j|_D^2
-  double* partial;      // one slot per row
+  double* partial;      // one slot per CTA of the level
   unsigned* counter;
 };
 
@@ -42,9 +42,13 @@ struct LzArgs {
   LzLevel<T> L[kLzMax];
 };
 
-__device__ __forceinline__ int lz_level(const int* row0, int nl, int b) {
+// one warp per block row, kLzBS / 32 rows per CTA; every CTA holds rows of one level
+constexpr int kLzRows = kLzBS / 32;
+
+template <typename T>
+__device__ __forceinline__ int lz_level(const LzArgs<T>& A, int b) {
   int l = 0;
-  while (l + 1 < nl && row0[l + 1] <= b) ++l;
+  while (l + 1 < A.nl && A.L[l + 1].cta0 <= b) ++l;
   return l;
 }
 
@@ -63,11 +67,11 @@ __device__ __forceinline__ double lz_block_sum(double v) {
 
 // deterministic per-level sum: every CTA of the level stores its partial (thread 0's
 // v), the last CTA to arrive adds them in a fixed order
-__device__ __forceinline__ void lz_reduce(double v, double* partial, unsigned* counter, int n, int row,
+__device__ __forceinline__ void lz_reduce(double v, double* partial, unsigned* counter, int n, int slot,
                                           double* out) {
   __shared__ bool last;
   if (threadIdx.x == 0) {
-    partial[row] = v;
+    partial[slot] = v;
     __threadfence();
     last = atomicAdd(counter, 1u) == (unsigned)(n - 1);
   }
@@ -84,17 +88,40 @@ __device__ __forceinline__ void lz_reduce(double v, double* partial, unsigned* c
   }
 }
 
-// y_i = B_i x_i for one block row, in the level's precision; thread u < bs returns
-// component u
+// (B x)_i row u for the warp's row i (lane u < bs), in the level's precision
 template <typename T>
-__device__ __forceinline__ double lz_block_row(const T* __restrict__ B, int bs, int i, const T* x) {
-  const int u = threadIdx.x;
-  if (u >= bs) return 0.0;
+__device__ __forceinline__ T lz_block_row(const T* __restrict__ B, int bs, int i, const T* x, int u) {
+  if (u >= bs) return T(0);
   const T* b = B + ((size_t)i * bs + u) * bs;
   const T* xi = x + (size_t)i * bs;
   T acc = T(0);
   for (int c = 0; c < bs; ++c) acc += b[c] * xi[c];
-  return (double)acc;
+  return acc;
+}
+
+// (A x)_i row u for the warp's row i: lane u + bs h takes blocks h, h + G, ... (G = 32 / bs)
+// and lane u < bs gets the row's sum
+template <typename T>
+__device__ __forceinline__ T lz_row_product(const LzLevel<T>& L, int i, const T* __restrict__ x, int lane) {
+  const int bs = L.bs, G = 32 / bs;
+  const int u = lane % bs, h = lane / bs;
+  T acc = T(0);
+  if (h < G) {
+    const int e1 = L.row_ptr[i + 1];
+    for (int e = L.row_ptr[i] + h; e < e1; e += G) {
+      const T* a = L.vals + (size_t)e * bs * bs + u * bs;
+      const T* xv = x + (size_t)L.cols[e] * bs;
+      for (int c = 0; c < bs; ++c) acc += a[c] * xv[c];
+    }
+  }
+  // groups h = 1 .. G-1 to group 0 (lane u)
+  T tot = acc;
+  for (int g = 1; g < 32 / 9 + 1; ++g) {
+    const int src = lane + g * bs;
+    const T o = __shfl_sync(kFull, acc, src < 32 ? src : 31);
+    if (g < G && src < G * bs) tot += o;
+  }
+  return tot;
 }
 
 // v = start vector (SplitMix64 of the level-local index, mapped to [-1, 1)); s[0] = v^T D v
@@ -102,19 +129,19 @@ template <typename T>
 __global__ void __launch_bounds__(kLzBS) k_lz_init(LzArgs<T> A) {
   pdl_wait();
   pdl_trigger();
-  int row0[kLzMax];
-  for (int l = 0; l < A.nl; ++l) row0[l] = A.L[l].row0;
-  const int l = lz_level(row0, A.nl, blockIdx.x);
+  const int l = lz_level(A, blockIdx.x);
   const LzLevel<T>& L = A.L[l];
-  const int i = blockIdx.x - L.row0, bs = L.bs, u = threadIdx.x;
-  if (u < bs) {
-    const size_t idx = (size_t)i * bs + u;
+  const int lane = threadIdx.x & 31;
+  const int i = (blockIdx.x - L.cta0) * kLzRows + (threadIdx.x >> 5), bs = L.bs;
+  const bool live = i < L.n;
+  if (live && lane < bs) {
+    const size_t idx = (size_t)i * bs + lane;
     L.v[idx] = (T)(2.0 * ((double)(splitmix64(idx) >> 11) * 0x1.0p-53) - 1.0);
   }
-  __syncthreads();
-  const double dv = lz_block_row(L.D, bs, i, L.v);
-  const double part = lz_block_sum(u < bs ? dv * (double)L.v[(size_t)i * bs + u] : 0.0);
-  lz_reduce(part, L.partial, L.counter, L.n, i, L.s);
+  __syncwarp();
+  double part = 0.0;
+  if (live && lane < bs) part = (double)lz_block_row(L.D, bs, i, L.v, lane) * (double)L.v[(size_t)i * bs + lane];
+  lz_reduce(lz_block_sum(part), L.partial, L.counter, L.nct, blockIdx.x - L.cta0, L.s);
 }
 
 // step j: q_j = src / sqrt(s[j]) (src = v for j = 0, w otherwise); Aq = A q_j; alpha_j
@@ -122,43 +149,26 @@ template <typename T>
 __global__ void __launch_bounds__(kLzBS) k_lz_product(LzArgs<T> A, int j) {
   pdl_wait();
   pdl_trigger();
-  __shared__ double part_sm[kLzBS];
-  int row0[kLzMax];
-  for (int l = 0; l < A.nl; ++l) row0[l] = A.L[l].row0;
-  const int l = lz_level(row0, A.nl, blockIdx.x);
+  const int l = lz_level(A, blockIdx.x);
   const LzLevel<T>& L = A.L[l];
-  const int i = blockIdx.x - L.row0, bs = L.bs, t = threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int i = (blockIdx.x - L.cta0) * kLzRows + (threadIdx.x >> 5), bs = L.bs;
+  const bool live = i < L.n;
   const T* src = j == 0 ? L.v : L.w;
   const double scale = 1.0 / sqrt(L.s[j]);
-  // threads split the row's blocks: G groups of bs threads
-  const int G = kLzBS / bs;
-  const int u = t % bs, h = t / bs;
   // the row's products in the level's precision (an estimate of lambda_max needs no
-  // more; FP32 arithmetic also keeps this off the GPU's narrow FP64 unit), their sum in FP64
-  T acc = T(0);
-  if (h < G) {
-    const int e1 = L.row_ptr[i + 1];
-    for (int e = L.row_ptr[i] + h; e < e1; e += G) {
-      const T* a = L.vals + (size_t)e * bs * bs + u * bs;
-      const T* xv = src + (size_t)L.cols[e] * bs;
-      for (int c = 0; c < bs; ++c) acc += a[c] * xv[c];
-    }
-  }
-  part_sm[t] = h < G ? (double)acc : 0.0;
-  __syncthreads();
+  // more; FP32 arithmetic also keeps this off the GPU's narrow FP64 unit)
+  const T rowsum = live ? lz_row_product(L, i, src, lane) : T(0);
   double contrib = 0.0;
-  if (t < bs) {
-    double s = 0.0;
-    for (int g = 0; g < G; ++g) s += part_sm[g * bs + t];
-    const size_t idx = (size_t)i * bs + t;
-    const double aq = s * scale;
+  if (live && lane < bs) {
+    const size_t idx = (size_t)i * bs + lane;
+    const double aq = (double)rowsum * scale;
     const double qv = (double)src[idx] * scale;
     L.Aq[idx] = (T)aq;
     L.q[j & 1][idx] = (T)qv;
     contrib = qv * aq;
   }
-  const double part = lz_block_sum(contrib);
-  lz_reduce(part, L.partial, L.counter, L.n, i, L.cheb + 8 + j);
+  lz_reduce(lz_block_sum(contrib), L.partial, L.counter, L.nct, blockIdx.x - L.cta0, L.cheb + 8 + j);
 }
 
 // w = D^-1 Aq - alpha_j q_j - beta_{j-1} q_{j-1}; s[j + 1] = w^T D w; beta_j = sqrt(s[j + 1])
@@ -166,24 +176,26 @@ template <typename T>
 __global__ void __launch_bounds__(kLzBS) k_lz_direction(LzArgs<T> A, int j) {
   pdl_wait();
   pdl_trigger();
-  int row0[kLzMax];
-  for (int l = 0; l < A.nl; ++l) row0[l] = A.L[l].row0;
-  const int l = lz_level(row0, A.nl, blockIdx.x);
+  const int l = lz_level(A, blockIdx.x);
   const LzLevel<T>& L = A.L[l];
-  const int i = blockIdx.x - L.row0, bs = L.bs, u = threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int i = (blockIdx.x - L.cta0) * kLzRows + (threadIdx.x >> 5), bs = L.bs;
+  const bool live = i < L.n;
   const double alpha = L.cheb[8 + j];
   const double beta = j > 0 ? sqrt(L.s[j]) : 0.0;   // beta_{j-1} = |w_{j-1}|_D
-  double wv = lz_block_row(L.Dinv, bs, i, L.Aq);
-  if (u < bs) {
-    const size_t idx = (size_t)i * bs + u;
+  double wv = 0.0;
+  if (live && lane < bs) {
+    const size_t idx = (size_t)i * bs + lane;
+    wv = (double)lz_block_row(L.Dinv, bs, i, L.Aq, lane);
     wv -= alpha * (double)L.q[j & 1][idx];
     if (j > 0) wv -= beta * (double)L.q[(j + 1) & 1][idx];
     L.w[idx] = (T)wv;
   }
-  __syncthreads();
-  const double dw = lz_block_row(L.D, bs, i, L.w);
-  const double part = lz_block_sum(u < bs ? dw * (double)L.w[(size_t)i * bs + u] : 0.0);
-  lz_reduce(part, L.partial, L.counter, L.n, i, L.s + 1 + j);   // beta_j^2
+  __syncwarp();
+  double part = 0.0;
+  if (live && lane < bs)
+    part = (double)lz_block_row(L.D, bs, i, L.w, lane) * (double)L.w[(size_t)i * bs + lane];
+  lz_reduce(lz_block_sum(part), L.partial, L.counter, L.nct, blockIdx.x - L.cta0, L.s + 1 + j);   // beta_j^2
 }
 
 __global__ void k_lz_betas(double* const* cheb, double* const* s, int nl, int m) {
@@ -202,20 +214,20 @@ static void run(ba_problem* P, int first, int last) {
   LzArgs<T> A{};
   A.nl = nl;
   size_t vec = 0;
-  int rows = 0;
+  int ctas = 0;
   for (int k = 0; k < nl; ++k) {
     Level& L = P->levels[first + k];
     vec += (size_t)L.n * L.bs + 32;
-    rows += L.n;
+    ctas += cdiv(L.n, kLzRows);
   }
   P->lz_vec.ensure(sizeof(T) * vec * 5 + 256);
-  P->lz_red.ensure(sizeof(double) * ((size_t)rows + 16 * (size_t)nl) + 256);
+  P->lz_red.ensure(sizeof(double) * ((size_t)ctas + 16 * (size_t)nl) + 256);
   P->lz_cnt.ensure(sizeof(unsigned) * (size_t)nl + 64);
   BA_CUDA(cudaMemsetAsync(P->lz_cnt.p, 0, sizeof(unsigned) * nl, P->stream));
   T* vb = P->lz_vec.as<T>();
   double* red = P->lz_red.as<double>();
-  double* sbase = red + rows;
-  int row0 = 0;
+  double* sbase = red + ctas;
+  int cta0 = 0;
   for (int k = 0; k < nl; ++k) {
     Level& L = P->levels[first + k];
     L.cheb.ensure(sizeof(double) * kChebSlots);
@@ -223,7 +235,8 @@ static void run(ba_problem* P, int first, int last) {
     LzLevel<T>& d = A.L[k];
     d.n = L.n;
     d.bs = L.bs;
-    d.row0 = row0;
+    d.cta0 = cta0;
+    d.nct = cdiv(L.n, kLzRows);
     d.row_ptr = L.row_ptr.as<int>();
     d.cols = L.cols.as<int>();
     d.vals = sizeof(T) == 4 ? (const T*)L.vals32.p : (const T*)L.vals64.p;
@@ -237,18 +250,18 @@ static void run(ba_problem* P, int first, int last) {
     vb += 5 * n + 32;
     d.cheb = L.cheb.as<double>();
     d.s = sbase + 16 * k;
-    d.partial = red + row0;
+    d.partial = red + cta0;
     d.counter = P->lz_cnt.as<unsigned>() + k;
-    row0 += L.n;
+    cta0 += d.nct;
   }
   // zero the alpha / beta slots so that unused ones read as 0
   for (int k = 0; k < nl; ++k)
     BA_CUDA(cudaMemsetAsync(A.L[k].cheb + 8, 0, sizeof(double) * 16, P->stream));
-  launch_k(P, k_lz_init<T>, rows, kLzBS, 0, A);
+  launch_k(P, k_lz_init<T>, ctas, kLzBS, 0, A);
   for (int j = 0; j < m; ++j) {
-    launch_k(P, k_lz_product<T>, rows, kLzBS, 0, A, j);
+    launch_k(P, k_lz_product<T>, ctas, kLzBS, 0, A, j);
     if (j == m - 1) break;
-    launch_k(P, k_lz_direction<T>, rows, kLzBS, 0, A, j);
+    launch_k(P, k_lz_direction<T>, ctas, kLzBS, 0, A, j);
   }
   // beta_j = sqrt(s[j + 1])
   std::vector<double*> hc(nl), hs(nl);

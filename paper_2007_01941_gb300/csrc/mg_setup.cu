@@ -1386,6 +1386,122 @@ __global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* Aa, double* Ab, 
   }
 }
 
+// The same inversion in paired FP32 (mixed precision): the matrix as (hi, lo) float pairs,
+// products as compensated sums, the pivot reciprocal as a DF division.  The FP64 unit of
+// this GPU takes a warp's FMA over many cycles per SM sub-partition; the pairs run on the
+// FP32 pipes and carry ~48 bits, well beyond what the FP32 coarse operator holds.
+__device__ __forceinline__ bool gj_invert_df(float2 piv[kGJ][kGJ + 1], float2* gj_row, float2* gj_col, float2& gj_ip) {
+  const int t = threadIdx.x, u = t / kGJ, v = t % kGJ;
+  bool ok = true;
+  for (int k = 0; k < kGJ; ++k) {
+    if (t == 0) {
+      const DF pk(piv[k][k].x, piv[k][k].y);
+      if (!(pk.h > 0.f)) ok = false;
+      const DF ip = DF(1.f, 0.f) / pk;
+      gj_ip = make_float2(ip.h, ip.l);
+    }
+    __syncthreads();
+    const DF ip(gj_ip.x, gj_ip.y);
+    if (t < kGJ) {
+      const DF r = t == k ? ip : DF(piv[k][t].x, piv[k][t].y) * ip;
+      gj_row[t] = make_float2(r.h, r.l);
+      gj_col[t] = piv[t][k];
+    }
+    __syncthreads();
+    DF nv;
+    const DF cu(gj_col[u].x, gj_col[u].y), rv(gj_row[v].x, gj_row[v].y);
+    if (u == k) nv = rv;
+    else if (v == k) nv = -(cu * ip);
+    else nv = DF(piv[u][v].x, piv[u][v].y) - cu * rv;
+    piv[u][v] = make_float2(nv.h, nv.l);
+    __syncthreads();
+  }
+  return ok;
+}
+
+// sum_k x[u][k] y[k][v] of two kGJ x kGJ tiles in shared memory, compensated
+__device__ __forceinline__ DF gj_tile_dot(const float2 x[kGJ][kGJ + 1], const float2 y[kGJ][kGJ + 1], int u, int v) {
+  float s = 0.f, c = 0.f;
+#pragma unroll
+  for (int k = 0; k < kGJ; ++k) dot2_fma(s, c, x[u][k], y[k][v]);
+  return DF(s, 0.f) + DF(c, 0.f);
+}
+
+__global__ void __launch_bounds__(kGJBS) k_gauss_jordan_df(float2* Aa, float2* Ab, int Np, float2* pinv, int* flags) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ float2 piv[kGJ][kGJ + 1];
+  __shared__ float2 gj_row[kGJ], gj_col[kGJ];
+  __shared__ float2 gj_ip;
+  __shared__ float2 sa[kGJ][kGJ + 1], sb[kGJ][kGJ + 1], st[kGJ][kGJ + 1];
+  const int nb = Np / kGJ;
+  const int t = threadIdx.x, u = t / kGJ, v = t % kGJ;
+  if (blockIdx.x == 0) {
+    piv[u][v] = Aa[(size_t)u * Np + v];
+    __syncthreads();
+    const bool ok = gj_invert_df(piv, gj_row, gj_col, gj_ip);
+    if (t == 0 && !ok) flags[F_NOT_SPD_COARSE] = 1;
+    pinv[t] = piv[u][v];
+  }
+  grid.sync();
+  for (int K = 0; K < nb; ++K) {
+    const float2* A = (K & 1) ? Ab : Aa;
+    float2* An = (K & 1) ? Aa : Ab;
+    const int K0 = K * kGJ;
+    piv[u][v] = pinv[(size_t)(K & 1) * kGJBS + t];
+    __syncthreads();
+    bool owner = false;
+    for (int w = blockIdx.x; w < nb * nb; w += gridDim.x) {
+      const int I = w / nb, J = w - I * nb;
+      if (I == K + 1 && J == K + 1) owner = true;
+      DF out;
+      if (I == K && J == K) {
+        out = DF(piv[u][v].x, piv[u][v].y);
+      } else if (I == K) {
+        sb[u][v] = A[(size_t)(K0 + u) * Np + J * kGJ + v];
+        __syncthreads();
+        out = gj_tile_dot(piv, sb, u, v);
+      } else if (J == K) {
+        sa[u][v] = A[(size_t)(I * kGJ + u) * Np + K0 + v];
+        __syncthreads();
+        out = -gj_tile_dot(sa, piv, u, v);
+      } else {
+        sa[u][v] = A[(size_t)(I * kGJ + u) * Np + K0 + v];
+        sb[u][v] = A[(size_t)(K0 + u) * Np + J * kGJ + v];
+        const float2 aij = A[(size_t)(I * kGJ + u) * Np + J * kGJ + v];
+        __syncthreads();
+        const DF sv = gj_tile_dot(piv, sb, u, v);
+        st[u][v] = make_float2(sv.h, sv.l);
+        __syncthreads();
+        out = DF(aij.x, aij.y) - gj_tile_dot(sa, st, u, v);
+      }
+      An[(size_t)(I * kGJ + u) * Np + J * kGJ + v] = make_float2(out.h, out.l);
+      __syncthreads();
+    }
+    if (owner) {
+      const int K1 = K0 + kGJ;
+      piv[u][v] = An[(size_t)(K1 + u) * Np + K1 + v];
+      __syncthreads();
+      const bool ok = gj_invert_df(piv, gj_row, gj_col, gj_ip);
+      if (t == 0 && !ok) flags[F_NOT_SPD_COARSE] = 1;
+      pinv[(size_t)((K + 1) & 1) * kGJBS + t] = piv[u][v];
+    }
+    grid.sync();
+  }
+}
+
+__global__ void k_d2df_vec(size_t n, const double* __restrict__ a, float2* __restrict__ b) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const DF v(a[i]);
+    b[i] = make_float2(v.h, v.l);
+  }
+}
+
+__global__ void k_df2d_vec(size_t n, const float2* __restrict__ a, double* __restrict__ b) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = to_double(DF(a[i].x, a[i].y));
+}
+
 __global__ void k_d2f_vec(size_t n, const double* __restrict__ a, float* __restrict__ b) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -1409,6 +1525,27 @@ static void dense_inverse(ba_problem* P, Level& L) {
   launched(P);
   k_dense_identity_pad<<<cdiv((long long)Np * Np, 256), 256, 0, P->stream>>>(N, Np, A);
   launched(P);
+  if (level_fp32(P)) {
+    // paired FP32: both buffers of the ping-pong and the pivot inverses as float pairs
+    const size_t nn = (size_t)Np * Np;
+    P->scratch.ensure(sizeof(float2) * (2 * nn + 2 * kGJBS) + 64);
+    float2* Da = P->scratch.as<float2>();
+    float2* Db = Da + nn;
+    float2* pinv = Db + nn;
+    k_d2df_vec<<<cdiv((long long)nn, 256), 256, 0, P->stream>>>(nn, A, Da);
+    launched(P);
+    int nblk = 0;
+    BA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, k_gauss_jordan_df, kGJBS, 0));
+    const int nbk = Np / kGJ;
+    int grid = std::max(1, std::min(nblk * P->n_sm, nbk * nbk));
+    int* flags = P->flags.as<int>();
+    void* args[] = {(void*)&Da, (void*)&Db, (void*)&Np, (void*)&pinv, (void*)&flags};
+    BA_CUDA(cudaLaunchCooperativeKernel((void*)k_gauss_jordan_df, grid, kGJBS, args, 0, P->stream));
+    launched(P);
+    k_df2d_vec<<<cdiv((long long)nn, 256), 256, 0, P->stream>>>(nn, (nbk & 1) ? Db : Da, A);
+    launched(P);
+    return;
+  }
   // second buffer of the ping-pong and the two pivot inverses
   P->scratch.ensure(sizeof(double) * ((size_t)Np * Np + 2 * kGJBS) + 64);
   double* B = P->scratch.as<double>();
