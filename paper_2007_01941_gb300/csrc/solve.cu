@@ -591,39 +591,64 @@ k_pcg_spmv_pq_df(int n, const int* __restrict__ row_ptr, const int* __restrict__
   const int i = blockIdx.x * (kSpmvBS / 32) + (threadIdx.x >> 5);
   const int r = lane % 9, k = lane / 9;
   const bool live = i < n && k < 3;
-  int e0 = 0, e1 = 0, c0 = 0;
-  float2 a0[9];
+  // the first two blocks of this lane's share (blocks k and k + 3 of the row), loaded
+  // before the wait; the rest two at a time into independent sums
+  int e0 = 0, e1 = 0, c0 = 0, c1 = 0;
+  float2 a0[9], a1[9];
   if (live) {
     e0 = row_ptr[i] + k;
     e1 = row_ptr[i + 1];
-    const int ef = min(e0, max(e1 - 1, 0));
-    c0 = cols[ef];
-    const float2* a = vals + (size_t)ef * 81 + r * 9;
+    const int last = max(e1 - 1, 0);
+    const int f0 = min(e0, last), f1 = min(e0 + 3, last);
+    c0 = cols[f0];
+    c1 = cols[f1];
+    const float2* x0 = vals + (size_t)f0 * 81 + r * 9;
+    const float2* x1 = vals + (size_t)f1 * 81 + r * 9;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) a0[c] = a[c];
+    for (int c = 0; c < 9; ++c) {
+      a0[c] = x0[c];
+      a1[c] = x1[c];
+    }
   }
   pdl_trigger();
   pdl_wait();
-  float sh = 0.f, sc = 0.f;
+  float sh = 0.f, sc = 0.f, th = 0.f, tc = 0.f;
   if (live && e0 < e1) {
     const float2* x0 = ps + (size_t)c0 * 9;
 #pragma unroll
     for (int c = 0; c < 9; ++c) dot2_fma(sh, sc, a0[c], x0[c]);
-    for (int e = e0 + 3; e < e1; e += 3) {
-      const float2* a = vals + (size_t)e * 81 + r * 9;
-      const float2* xv = ps + (size_t)cols[e] * 9;
+    if (e0 + 3 < e1) {
+      const float2* x1 = ps + (size_t)c1 * 9;
 #pragma unroll
-      for (int c = 0; c < 9; ++c) dot2_fma(sh, sc, a[c], xv[c]);
+      for (int c = 0; c < 9; ++c) dot2_fma(th, tc, a1[c], x1[c]);
+    }
+    int e = e0 + 6;
+    for (; e + 3 < e1; e += 6) {
+      const float2* a = vals + (size_t)e * 81 + r * 9;
+      const float2* b = vals + (size_t)(e + 3) * 81 + r * 9;
+      const float2* xa = ps + (size_t)cols[e] * 9;
+      const float2* xb = ps + (size_t)cols[e + 3] * 9;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        dot2_fma(sh, sc, a[c], xa[c]);
+        dot2_fma(th, tc, b[c], xb[c]);
+      }
+    }
+    if (e < e1) {
+      const float2* a = vals + (size_t)e * 81 + r * 9;
+      const float2* xa = ps + (size_t)cols[e] * 9;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) dot2_fma(sh, sc, a[c], xa[c]);
     }
   }
-  DF acc = DF(sh, 0.f) + DF(sc, 0.f);
+  DF acc = (DF(sh, 0.f) + DF(sc, 0.f)) + (DF(th, 0.f) + DF(tc, 0.f));
   const int l1 = min(lane + 9, 31), l2 = min(lane + 18, 31);
-  const DF a1(__shfl_sync(kFull, acc.h, l1), __shfl_sync(kFull, acc.l, l1));
-  const DF a2(__shfl_sync(kFull, acc.h, l2), __shfl_sync(kFull, acc.l, l2));
+  const DF s1(__shfl_sync(kFull, acc.h, l1), __shfl_sync(kFull, acc.l, l1));
+  const DF s2(__shfl_sync(kFull, acc.h, l2), __shfl_sync(kFull, acc.l, l2));
   double dot = 0.0;
   if (i < n && lane < 9) {
     const size_t idx = (size_t)i * 9 + r;
-    const double qi = to_double(acc + a1 + a2);
+    const double qi = to_double(acc + s1 + s2);
     q[idx] = qi;
     dot = p[idx] * qi;
   }
