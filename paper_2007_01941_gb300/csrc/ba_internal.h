@@ -176,6 +176,7 @@ struct ba_problem {
   ba::DBuf xsplit;              // float2 [n_c][9] hi/lo split of a camera vector
   ba::DBuf camdf;               // float2 [n_c][28] split rotation data and parameters (mixed)
   ba::DBuf wpdf;                // float2 [3][ldp] split C_p^-1 g_p (mixed)
+  ba::DBuf Xdf;                 // float2 [6][ldp] X = G^-1 (C_p + D_p = G G^T) as float pairs (mixed)
   ba::DBuf gc, gp, wp, rhs;     // g_c [n_c*9], g_p [3][ldp], C^-1 g_p [3][ldp], b [n_c*9]
   ba::DBuf Dc32;                // float copy of D_c
   ba::DBuf Scc;                 // double [n_c][81] diagonal blocks S_cc

@@ -373,35 +373,42 @@ __device__ __forceinline__ void rec_df_e(const float* __restrict__ h, const floa
   e[5] = DF(a5.w, b5.w);
 }
 
+// One thread per point: C_p = sum E_o^T E_o (+ D_p), g_p = -sum E_o^T f_o, in DF; then, in
+// DF as well, the Cholesky factor C_p = G G^T, X = G^-1 (lower triangular) and
+// C_p^-1 = X^T X, written as FP64, as FP32 heads and remainders, and X itself (the factor
+// W_o = X E_o^T F_o of the assembled S, since W_i^T W_j = F_i^T E_i C_p^-1 E_j^T F_j).
 __global__ void k_point_setup_df(const float* __restrict__ Jh, const float* __restrict__ Jl,
                                  const double* __restrict__ fres, const int* __restrict__ pt_ptr, int n_p, int n_p_obs,
                                  size_t ldp, double lambda, int damp_identity, double* __restrict__ Dp,
                                  double* __restrict__ Cinv, float* __restrict__ Cinv32, float* __restrict__ Cinv32lo,
                                  double* __restrict__ gp, double* __restrict__ wp, float2* __restrict__ wpdf,
-                                 int* flags) {
+                                 float2* __restrict__ Xdf, int* flags) {
   int ip = blockIdx.x * blockDim.x + threadIdx.x;
   if (ip >= n_p) return;
-  const DF z(0.f, 0.f);
-  DF c00 = z, c01 = z, c02 = z, c11 = z, c12 = z, c22 = z, g0 = z, g1 = z, g2 = z;
+  float ch[9], cc[9];   // C (6 unique) and g (3) as compensated sums
+#pragma unroll
+  for (int k = 0; k < 9; ++k) ch[k] = cc[k] = 0.f;
   const int b = pt_ptr[ip], e = pt_ptr[ip + 1];
   for (int o = b; o < e; ++o) {
     DF ev[6];
     rec_df_e(Jh, Jl, o, ev);
     const DF a0 = ev[0], a1 = ev[1], a2 = ev[2], b0 = ev[3], b1 = ev[4], b2 = ev[5];
     const DF f0(fres[2 * (size_t)o]), f1(fres[2 * (size_t)o + 1]);
-    c00 += a0 * a0 + b0 * b0;
-    c01 += a0 * a1 + b0 * b1;
-    c02 += a0 * a2 + b0 * b2;
-    c11 += a1 * a1 + b1 * b1;
-    c12 += a1 * a2 + b1 * b2;
-    c22 += a2 * a2 + b2 * b2;
-    g0 -= a0 * f0 + b0 * f1;
-    g1 -= a1 * f0 + b1 * f1;
-    g2 -= a2 * f0 + b2 * f1;
+    const DF nf0 = -f0, nf1 = -f1;
+    dot2_fma(ch[0], cc[0], a0, a0); dot2_fma(ch[0], cc[0], b0, b0);
+    dot2_fma(ch[1], cc[1], a0, a1); dot2_fma(ch[1], cc[1], b0, b1);
+    dot2_fma(ch[2], cc[2], a0, a2); dot2_fma(ch[2], cc[2], b0, b2);
+    dot2_fma(ch[3], cc[3], a1, a1); dot2_fma(ch[3], cc[3], b1, b1);
+    dot2_fma(ch[4], cc[4], a1, a2); dot2_fma(ch[4], cc[4], b1, b2);
+    dot2_fma(ch[5], cc[5], a2, a2); dot2_fma(ch[5], cc[5], b2, b2);
+    dot2_fma(ch[6], cc[6], a0, nf0); dot2_fma(ch[6], cc[6], b0, nf1);
+    dot2_fma(ch[7], cc[7], a1, nf0); dot2_fma(ch[7], cc[7], b1, nf1);
+    dot2_fma(ch[8], cc[8], a2, nf0); dot2_fma(ch[8], cc[8], b2, nf1);
   }
-  const double C00 = to_double(c00), C01 = to_double(c01), C02 = to_double(c02);
-  const double C11 = to_double(c11), C12 = to_double(c12), C22 = to_double(c22);
-  const double G0 = to_double(g0), G1 = to_double(g1), G2 = to_double(g2);
+  DF cv[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) cv[k] = DF(ch[k], 0.f) + DF(cc[k], 0.f);
+  const double C00 = to_double(cv[0]), C11 = to_double(cv[3]), C22 = to_double(cv[5]);
   double d0, d1, d2;
   if (damp_identity) {
     d0 = d1 = d2 = lambda;
@@ -413,52 +420,81 @@ __global__ void k_point_setup_df(const float* __restrict__ Jh, const float* __re
   Dp[ip] = d0;
   Dp[ldp + ip] = d1;
   Dp[2 * ldp + ip] = d2;
+  const double G0 = to_double(cv[6]), G1 = to_double(cv[7]), G2 = to_double(cv[8]);
   gp[ip] = G0;
   gp[ldp + ip] = G1;
   gp[2 * ldp + ip] = G2;
-  double inv[6] = {0, 0, 0, 0, 0, 0};
+  const DF zero(0.f, 0.f), one(1.f, 0.f);
+  DF inv[6] = {zero, zero, zero, zero, zero, zero}, X[6] = {zero, zero, zero, zero, zero, zero};
   if (ip < n_p_obs) {
-    double a[9] = {C00 + d0, C01, C02, C01, C11 + d1, C12, C02, C12, C22 + d2};
-    if (!spd_inverse<3>(a, 3)) {
+    const DF m00 = cv[0] + DF(d0), m11 = cv[3] + DF(d1), m22 = cv[5] + DF(d2);
+    const DF m01 = cv[1], m02 = cv[2], m12 = cv[4];
+    // Cholesky G (lower) and X = G^-1: x00, x10, x11, x20, x21, x22
+    const DF p1 = m00;
+    const DF g00 = df_sqrt(p1);
+    const DF i00 = p1.h > 0.f ? one / g00 : zero;
+    const DF g10 = m01 * i00, g20 = m02 * i00;
+    const DF p2 = m11 - g10 * g10;
+    const DF g11 = df_sqrt(p2);
+    const DF i11 = p2.h > 0.f ? one / g11 : zero;
+    const DF g21 = (m12 - g20 * g10) * i11;
+    const DF p3 = m22 - g20 * g20 - g21 * g21;
+    const DF g22 = df_sqrt(p3);
+    const DF i22 = p3.h > 0.f ? one / g22 : zero;
+    if (!(p1.h > 0.f && p2.h > 0.f && p3.h > 0.f)) {
       flags[F_NOT_SPD_POINT] = 1;
     } else {
-      inv[0] = a[0]; inv[1] = a[1]; inv[2] = a[2]; inv[3] = a[4]; inv[4] = a[5]; inv[5] = a[8];
+      const DF x10 = -(g10 * i00) * i11;
+      const DF x21 = -(g21 * i11) * i22;
+      const DF x20 = -(g20 * i00 + g21 * x10) * i22;
+      X[0] = i00; X[1] = x10; X[2] = i11; X[3] = x20; X[4] = x21; X[5] = i22;
+      // C^-1 = X^T X
+      inv[0] = i00 * i00 + x10 * x10 + x20 * x20;
+      inv[1] = x10 * i11 + x20 * x21;
+      inv[2] = x20 * i22;
+      inv[3] = i11 * i11 + x21 * x21;
+      inv[4] = x21 * i22;
+      inv[5] = i22 * i22;
     }
   }
+  double invd[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    Cinv[k * ldp + ip] = inv[k];
-    float hi, lo;
-    split_double(inv[k], hi, lo);
-    Cinv32[k * ldp + ip] = hi;
-    Cinv32lo[k * ldp + ip] = lo;
+    invd[k] = to_double(inv[k]);
+    Cinv[k * ldp + ip] = invd[k];
+    Cinv32[k * ldp + ip] = inv[k].h;
+    Cinv32lo[k * ldp + ip] = inv[k].l;
+    Xdf[k * ldp + ip] = make_float2(X[k].h, X[k].l);
   }
-  const double w[3] = {inv[0] * G0 + inv[1] * G1 + inv[2] * G2, inv[1] * G0 + inv[3] * G1 + inv[4] * G2,
-                       inv[2] * G0 + inv[4] * G1 + inv[5] * G2};
+  // w_p = C^-1 g_p
+  const DF g0(G0), g1(G1), g2(G2);
+  const DF w[3] = {inv[0] * g0 + inv[1] * g1 + inv[2] * g2, inv[1] * g0 + inv[3] * g1 + inv[4] * g2,
+                   inv[2] * g0 + inv[4] * g1 + inv[5] * g2};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    wp[k * ldp + ip] = w[k];
-    float hi, lo;
-    split_double(w[k], hi, lo);
-    wpdf[k * ldp + ip] = make_float2(hi, lo);
+    wp[k * ldp + ip] = to_double(w[k]);
+    wpdf[k * ldp + ip] = make_float2(w[k].h, w[k].l);
   }
 }
 
+constexpr int kCamBS = 128;
 
-__global__ void k_camera_setup_df(const float* __restrict__ Jh, const float* __restrict__ Jl,
-                                  const double* __restrict__ fres, const int* __restrict__ cam_ptr,
-                                  const int* __restrict__ cam_obs, const int* __restrict__ obs_pt,
-                                  const float2* __restrict__ wpdf, size_t ldp, int n_c, double lambda,
-                                  int damp_identity, double* __restrict__ Dc, float* __restrict__ Dc32,
-                                  double* __restrict__ gc, double* __restrict__ rhs) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (c >= n_c) return;
-  const DF z(0.f, 0.f);
-  DF dg[9], g[9], bb[9];
+// one CTA per camera (threads over its observations): D_c, g_c = -F^T f and the reduced
+// right-hand side b_c = g_c - F^T E w_p (w_p = C_p^-1 g_p, as float pairs), sums in DF
+__global__ void __launch_bounds__(kCamBS)
+k_camera_setup_df(const float* __restrict__ Jh, const float* __restrict__ Jl,
+                  const double* __restrict__ fres, const int* __restrict__ cam_ptr,
+                  const int* __restrict__ cam_obs, const int* __restrict__ obs_pt,
+                  const float2* __restrict__ wpdf, size_t ldp, int n_c, double lambda,
+                  int damp_identity, double* __restrict__ Dc, float* __restrict__ Dc32,
+                  double* __restrict__ gc, double* __restrict__ rhs) {
+  __shared__ float2 red[kCamBS / 32][27];
+  const int c = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  // dg (9), g (9), bb (9) as compensated sums
+  float hs[27], cs[27];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) dg[k] = g[k] = bb[k] = z;
-  for (int i = cam_ptr[c] + lane; i < cam_ptr[c + 1]; i += 32) {
+  for (int k = 0; k < 27; ++k) hs[k] = cs[k] = 0.f;
+  for (int i = cam_ptr[c] + t; i < cam_ptr[c + 1]; i += kCamBS) {
     const int o = cam_obs[i];
     const int ip = obs_pt[o];
     const DF f0(fres[2 * (size_t)o]), f1(fres[2 * (size_t)o + 1]);
@@ -468,29 +504,38 @@ __global__ void k_camera_setup_df(const float* __restrict__ Jh, const float* __r
     rec_df_all(Jh, Jl, o, rv);
     const DF h0 = f0 + rv[18] * w0 + rv[19] * w1 + rv[20] * w2;
     const DF h1 = f1 + rv[21] * w0 + rv[22] * w1 + rv[23] * w2;
+    const DF nf0 = -f0, nf1 = -f1, nh0 = -h0, nh1 = -h1;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const DF a = rv[k], b = rv[9 + k];
-      dg[k] += a * a + b * b;
-      g[k] -= a * f0 + b * f1;
-      bb[k] -= a * h0 + b * h1;
+      dot2_fma(hs[k], cs[k], a, a);
+      dot2_fma(hs[k], cs[k], b, b);
+      dot2_fma(hs[9 + k], cs[9 + k], a, nf0);
+      dot2_fma(hs[9 + k], cs[9 + k], b, nf1);
+      dot2_fma(hs[18 + k], cs[18 + k], a, nh0);
+      dot2_fma(hs[18 + k], cs[18 + k], b, nh1);
     }
   }
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    dg[k] = warp_sum_df(dg[k]);
-    g[k] = warp_sum_df(g[k]);
-    bb[k] = warp_sum_df(bb[k]);
+  for (int k = 0; k < 27; ++k) {
+    const DF v = warp_sum_df(DF(hs[k], 0.f) + DF(cs[k], 0.f));
+    if (lane == 0) red[warp][k] = make_float2(v.h, v.l);
   }
-  if (lane == 0) {
+  __syncthreads();
+  if (t < 27) {
+    DF v(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const double dgk = to_double(dg[k]);
-      const double d = damp_identity ? lambda : lambda * fmax(dgk, 1e-6);
-      Dc[9 * c + k] = d;
-      Dc32[9 * c + k] = (float)d;
-      gc[9 * c + k] = to_double(g[k]);
-      rhs[9 * c + k] = to_double(bb[k]);
+    for (int w = 0; w < kCamBS / 32; ++w) v += DF(red[w][t].x, red[w][t].y);
+    const int k = t % 9;
+    const double d = to_double(v);
+    if (t < 9) {
+      const double dd = damp_identity ? lambda : lambda * fmax(d, 1e-6);
+      Dc[9 * c + k] = dd;
+      Dc32[9 * c + k] = (float)dd;
+    } else if (t < 18) {
+      gc[9 * c + k] = d;
+    } else {
+      rhs[9 * c + k] = d;
     }
   }
 }
@@ -648,11 +693,12 @@ void schur_setup(ba_problem* P, double lambda) {
   if (n_p) {
     if (mixed) {
       P->wpdf.ensure(sizeof(float2) * 3 * ldp);
+      P->Xdf.ensure(sizeof(float2) * 6 * ldp);
       k_point_setup_df<<<cdiv(n_p, 128), 128, 0, P->stream>>>(
           P->J32.as<float>(), P->J32lo.as<float>(), P->fres.as<double>(), P->pt_ptr.as<int>(), n_p, P->n_p_obs, ldp,
           lambda, damp_id, P->Dp.as<double>(), P->Cinv64.as<double>(), P->Cinv32.as<float>(),
           P->Cinv32lo.as<float>(), P->gp.as<double>(), P->wp.as<double>(), P->wpdf.as<float2>(),
-          P->flags.as<int>());
+          P->Xdf.as<float2>(), P->flags.as<int>());
     } else {
       k_point_setup<<<cdiv(n_p, 128), 128, 0, P->stream>>>(
           P->J64.as<double>(), P->fres.as<double>(), P->ld, P->pt_ptr.as<int>(), n_p, P->n_p_obs, ldp,
@@ -662,7 +708,7 @@ void schur_setup(ba_problem* P, double lambda) {
     launched(P);
   }
   if (mixed && n_p)
-    k_camera_setup_df<<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
+    k_camera_setup_df<<<n_c, kCamBS, 0, P->stream>>>(
         P->J32.as<float>(), P->J32lo.as<float>(), P->fres.as<double>(), P->cam_ptr.as<int>(), P->cam_obs.as<int>(),
         P->obs_pt.as<int>(), P->wpdf.as<float2>(), ldp, n_c, lambda, damp_id, P->Dc.as<double>(),
         P->Dc32.as<float>(), P->gc.as<double>(), P->rhs.as<double>());
@@ -1050,25 +1096,22 @@ __global__ void k_schur_w(const T* __restrict__ J, const T* __restrict__ Cinv, i
   }
 }
 
-// The same W in DF from the FP32 records and their remainders and the split C_p^-1;
-// row o holds its 27 entries as (hi, lo) pairs, padded to 28.
+// The same W in DF from the FP32 records and their remainders, with the point's factor X
+// (C_p^-1 = X^T X, X lower triangular, from the point setup): W_o = X E_o^T F_o, so that
+// W_i^T W_j = F_i^T E_i C_p^-1 E_j^T F_j; row o holds its 27 entries as (hi, lo) pairs,
+// padded to 28.
 __global__ void __launch_bounds__(128)
-k_schur_w_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const float* __restrict__ Ch,
-             const float* __restrict__ Cl, int ldp, const int* __restrict__ obs_pt, int n_o, float2* __restrict__ W2) {
+k_schur_w_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const float2* __restrict__ Xdf, int ldp,
+             const int* __restrict__ obs_pt, int n_o, float2* __restrict__ W2) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n_o) return;
   const int ip = obs_pt[o];
-  DF cv[6];
+  DF x[6];
 #pragma unroll
-  for (int k = 0; k < 6; ++k) cv[k] = DF(__ldg(Ch + (size_t)k * ldp + ip), __ldg(Cl + (size_t)k * ldp + ip));
-  const DF zero(0.f, 0.f), one(1.f, 0.f);
-  const DF l00 = df_sqrt(cv[0]);
-  const DF i00 = l00.h > 0.f ? one / l00 : zero;
-  const DF l10 = cv[1] * i00, l20 = cv[2] * i00;
-  const DF l11 = df_sqrt(cv[3] - l10 * l10);
-  const DF i11 = l11.h > 0.f ? one / l11 : zero;
-  const DF l21 = (cv[4] - l20 * l10) * i11;
-  const DF l22 = df_sqrt(cv[5] - l20 * l20 - l21 * l21);
+  for (int k = 0; k < 6; ++k) {
+    const float2 v = __ldg(Xdf + (size_t)k * ldp + ip);
+    x[k] = DF(v.x, v.y);
+  }
   DF rv[kRec];
   rec_df_all(Jh, Jl, o, rv);
   const DF* e = rv + 18;
@@ -1077,11 +1120,11 @@ k_schur_w_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const f
   for (int b = 0; b < 9; ++b) {
     const DF f0 = rv[b], f1 = rv[9 + b];
     const DF h0 = e[0] * f0 + e[3] * f1, h1 = e[1] * f0 + e[4] * f1, h2 = e[2] * f0 + e[5] * f1;
-    w[b] = l00 * h0 + l10 * h1 + l20 * h2;
-    w[9 + b] = l11 * h1 + l21 * h2;
-    w[18 + b] = l22 * h2;
+    w[b] = x[0] * h0;
+    w[9 + b] = x[1] * h0 + x[2] * h1;
+    w[18 + b] = x[3] * h0 + x[4] * h1 + x[5] * h2;
   }
-  w[27] = zero;
+  w[27] = DF(0.f, 0.f);
   float4* o4 = reinterpret_cast<float4*>(W2 + (size_t)o * kWld);
 #pragma unroll
   for (int i = 0; i < kWld / 2; ++i) o4[i] = make_float4(w[2 * i].h, w[2 * i].l, w[2 * i + 1].h, w[2 * i + 1].l);
@@ -1350,8 +1393,8 @@ void explicit_schur(ba_problem* P, Level& L0, ExplicitMode mode) {
     P->scratch.ensure(sizeof(float2) * kWld * (size_t)std::max(P->n_o, 1) + 64);
     float2* W2 = P->scratch.as<float2>();
     if (P->n_o) {
-      k_schur_w_df<<<g, 128, 0, P->stream>>>(P->J32.as<float>(), P->J32lo.as<float>(), P->Cinv32.as<float>(),
-                                             P->Cinv32lo.as<float>(), ldp, P->obs_pt.as<int>(), P->n_o, W2);
+      k_schur_w_df<<<g, 128, 0, P->stream>>>(P->J32.as<float>(), P->J32lo.as<float>(), P->Xdf.as<float2>(), ldp,
+                                             P->obs_pt.as<int>(), P->n_o, W2);
       launched(P);
     }
     KernelTimer kt(P, BA_KT_ASSEMBLY);
