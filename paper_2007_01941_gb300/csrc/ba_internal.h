@@ -199,6 +199,7 @@ struct ba_problem {
   ba::DBuf scal;                // double [kScalars]
   ba::DBuf partial;             // double [partial_cap]
   ba::DBuf partial2;            // double: per-CTA partial sums of the PCG's fused p.q
+  ba::DBuf rzpart;              // double [n_c]: each level-0 row's share of r.z (fused V-cycle)
   ba::DBuf counter;             // unsigned [8]
   ba::DBuf flags;               // int [F_COUNT]
   double* h_scal = nullptr;     // pinned host mirror
@@ -295,7 +296,8 @@ void split_vector(ba_problem* P, const double* x, const double* Dc, double* y); 
 void matvec_df_accumulate(ba_problem* P, double* y);                   // y += S x - Dc x from xsplit
 void lanczos_batched(ba_problem* P, int first, int last);  // levels first..last, all assembled
 void fused_vcycle_setup(ba_problem* P);
-void fused_vcycle(ba_problem* P, const double* r, double* z);
+// z = M r; rz_part (optional): per level-0 row, its share of r.z (one value per block row)
+void fused_vcycle(ba_problem* P, const double* r, double* z, double* rz_part);
 // assembled level-0 S: FP32 blocks only (the Galerkin product's input), FP64 blocks, or
 // paired-FP32 arithmetic giving the FP64 blocks and their FP32 roundings
 enum ExplicitMode { EX_FP32, EX_FP64, EX_PAIRED };

@@ -336,7 +336,7 @@ void precond_apply(ba_problem* P, const double* r, double* z) {
   BA_REQUIRE(P->n_levels > 0, BA_ERR_STATE, "ba_mg_setup has not been run");
   KernelTimer kt(P, BA_KT_VCYCLE);
   if (P->vc_ready) {
-    fused_vcycle(P, r, z);
+    fused_vcycle(P, r, z, nullptr);
     return;
   }
   Level& L0 = P->levels[0];
@@ -655,6 +655,36 @@ k_pcg_spmv_pq_df(int n, const int* __restrict__ row_ptr, const int* __restrict__
   grid_sum_store<kSpmvBS>(dot, partial, counter, pq_out);
 }
 
+// p = z + beta p with beta = rz / scal[S_RZ] (p = z when first), rz the sum of the rows'
+// shares of r.z left by the V-cycle (every CTA adds them in the same order; CTA 0 stores
+// it for the update kernel); ps (if given) the float-pair split of p
+__global__ void __launch_bounds__(256)
+k_pcg_direction_rz(size_t n, double* __restrict__ p, const double* __restrict__ z, double* scal, int first,
+                   const double* __restrict__ part, int npart, float2* __restrict__ ps) {
+  pdl_wait();
+  pdl_trigger();
+  double s = 0.0;
+  for (int k = threadIdx.x; k < npart; k += 256) s += part[k];
+  __shared__ double rz_sm;
+  s = block_sum<256>(s);
+  if (threadIdx.x == 0) {
+    rz_sm = s;
+    if (blockIdx.x == 0) scal[S_TMP2] = s;
+  }
+  __syncthreads();
+  const double rz = rz_sm;
+  const double beta = first ? 0.0 : rz / scal[S_RZ];
+  const size_t i = (size_t)blockIdx.x * 256 + threadIdx.x;
+  if (i < n) {
+    const double pi = first ? z[i] : z[i] + beta * p[i];
+    p[i] = pi;
+    if (ps) {
+      const float h = (float)pi;
+      ps[i] = make_float2(h, (float)(pi - (double)h));
+    }
+  }
+}
+
 // the split of p that the mixed-precision product reads
 static float2* assembled_split(ba_problem* P) {
   if (P->opt.precision != BA_MIXED) return nullptr;
@@ -667,6 +697,18 @@ static float2* assembled_split(ba_problem* P) {
 static void assembled_precond_direction(ba_problem* P, int first) {
   const size_t n = (size_t)P->n_c * 9;
   double *r = P->r.as<double>(), *z = P->z.as<double>(), *p = P->p.as<double>();
+  if (P->opt.preconditioner == BA_PRECOND_MG && P->vc_ready) {
+    // the V-cycle's last kernel leaves each row's share of r.z; every CTA of the direction
+    // kernel adds them up in the same order
+    double* part = P->rzpart.as<double>();
+    {
+      KernelTimer kt(P, BA_KT_VCYCLE);
+      fused_vcycle(P, r, z, part);
+    }
+    launch_k(P, k_pcg_direction_rz, cdiv((long long)n, 256), 256, 0, n, p, z, P->scal.as<double>(), first,
+             (const double*)part, P->n_c, assembled_split(P));
+    return;
+  }
   precond_apply(P, r, z);
   dot64(P, r, z, n, S_TMP2);
   launch_k(P, k_pcg_direction, cdiv((long long)n, 256), 256, 0, n, p, z, P->scal.as<double>(), first ? -1 : S_TMP2,
@@ -801,8 +843,10 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
   const bool assembled = P->outer_explicit;
   int s_rz = S_RZ, s_new = S_TMP2;
   if (assembled) {
-    // per-row-group partial sums of the fused p.q, sized before any graph capture
+    // per-row-group partial sums of the fused p.q and the rows' shares of r.z, sized
+    // before any graph capture
     P->partial2.ensure(sizeof(double) * ((size_t)cdiv(P->n_c, kSpmvBS / 32) + 64));
+    P->rzpart.ensure(sizeof(double) * ((size_t)P->n_c + 64));
     assembled_precond_direction(P, 1);
   } else {
     precond_apply(P, r, z);

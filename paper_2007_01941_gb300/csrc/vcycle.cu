@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(256) k_ph_first(VLevel<T> L, const double* __r
 // dout = c1 din + c2 D^-1 rout; x += dout (out: FP64 copy of the new x, level 0's last step)
 template <typename T, int BS>
 __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_step(VLevel<T> L, int dc, int rc, int xc, T c1, T c2,
-                                                                 double* __restrict__ out) {
+                                                                 double* __restrict__ out, const double* __restrict__ rdot,
+                                                                 double* __restrict__ dpart) {
   __shared__ T part[RowCta<BS>::G * BS];
   __shared__ T q[BS], w[BS];
   const int i = blockIdx.x, t = threadIdx.x;
@@ -207,6 +208,7 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_step(VLevel<T> L, i
   const size_t idx = (size_t)i * BS + t;
   if (t < BS) w[t] = L.r[rc][idx] - q[t];
   __syncthreads();
+  double dot = 0.0;
   if (t < BS) {
     const T acc = row_dinv<T, BS>(dr, w);
     const T dn = c1 * din[idx] + c2 * acc;
@@ -214,7 +216,15 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_step(VLevel<T> L, i
     L.r[1 - rc][idx] = w[t];
     L.d[1 - dc][idx] = dn;
     L.x[xc][idx] = xn;
-    if (out) out[idx] = (double)xn;
+    if (out) {
+      out[idx] = (double)xn;
+      if (dpart) dot = (double)xn * rdot[idx];
+    }
+  }
+  // this row's share of r.z (rows are CTAs; no cross-CTA reduction here)
+  if (dpart && t < 32) {
+    dot = warp_sum(dot);
+    if (t == 0) dpart[i] = dot;
   }
 }
 
@@ -368,7 +378,9 @@ __global__ void __launch_bounds__(256) k_ph_prolong(VLevel<T> L, VLevel<T> C, in
 // post-smoothing step 0 on row blockIdx.x: q = A x; r = b - q; d = D^-1 r / theta; x' = x + d
 template <typename T, int BS>
 __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first(VLevel<T> L, int xc, int rc, int dc,
-                                                                       double* __restrict__ out) {
+                                                                       double* __restrict__ out,
+                                                                       const double* __restrict__ rdot,
+                                                                       double* __restrict__ dpart) {
   __shared__ T part[RowCta<BS>::G * BS];
   __shared__ T q[BS], w[BS];
   const int i = blockIdx.x, t = threadIdx.x;
@@ -383,13 +395,21 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first(VLevel<T
   const size_t idx = (size_t)i * BS + t;
   if (t < BS) w[t] = L.b[idx] - q[t];
   __syncthreads();
+  double dot = 0.0;
   if (t < BS) {
     const T dv = row_dinv<T, BS>(dr, w) * (T)(1.0 / L.cheb[0]);
     const T xn = xin[idx] + dv;
     L.r[rc][idx] = w[t];
     L.d[dc][idx] = dv;
     L.x[1 - xc][idx] = xn;
-    if (out) out[idx] = (double)xn;
+    if (out) {
+      out[idx] = (double)xn;
+      if (dpart) dot = (double)xn * rdot[idx];
+    }
+  }
+  if (dpart && t < 32) {
+    dot = warp_sum(dot);
+    if (t == 0) dpart[i] = dot;
   }
 }
 
@@ -437,7 +457,7 @@ static void cheb_coeffs(const Level& L, int k, double& c1, double& c2) {
 }
 
 template <typename T>
-static void run(ba_problem* P, const double* r, double* z) {
+static void run(ba_problem* P, const double* r, double* z, double* dpart) {
   const int nl = P->n_levels;
   const int pre = std::max(1, P->opt.pre_smooth), post = std::max(1, P->opt.post_smooth);
   std::vector<VLevel<T>> V(nl);
@@ -458,10 +478,11 @@ static void run(ba_problem* P, const double* r, double* z) {
       cheb_coeffs(P->levels[l], k, c1, c2);
       if (L.bs == 9)
         launch_k(P, k_ph_step<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2,
-                                                             nullptr);
+                                                             (double*)nullptr, (const double*)nullptr, (double*)nullptr);
       else
         launch_k(P, k_ph_step<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1,
-                                                               (T)c2, nullptr);
+                                                               (T)c2, (double*)nullptr, (const double*)nullptr,
+                                                               (double*)nullptr);
       rm ^= 1u << l;
       dm ^= 1u << l;
     }
@@ -479,21 +500,24 @@ static void run(ba_problem* P, const double* r, double* z) {
     launch_k(P, k_ph_prolong<T>, cdiv((long long)L.n * L.bs, kPhaseBS), kPhaseBS, 0, L, V[l + 1], bit(xm, l),
                                                                                bit(xm, l + 1));
     double* o = (l == 0 && post == 1) ? z : nullptr;
+    double* op = o ? dpart : nullptr;
     if (L.bs == 9)
-      launch_k(P, k_ph_post_first<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(xm, l), bit(rm, l), bit(dm, l), o);
+      launch_k(P, k_ph_post_first<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(xm, l), bit(rm, l), bit(dm, l), o, r, op);
     else
-      launch_k(P, k_ph_post_first<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(xm, l), bit(rm, l), bit(dm, l), o);
+      launch_k(P, k_ph_post_first<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(xm, l), bit(rm, l), bit(dm, l), o, r,
+               op);
     xm ^= 1u << l;
     for (int k = 1; k < post; ++k) {
       double c1, c2;
       cheb_coeffs(P->levels[l], k, c1, c2);
       double* ok = (l == 0 && k == post - 1) ? z : nullptr;
+      double* okp = ok ? dpart : nullptr;
       if (L.bs == 9)
         launch_k(P, k_ph_step<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2,
-                                                             ok);
+                                                             ok, r, okp);
       else
         launch_k(P, k_ph_step<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1,
-                                                               (T)c2, ok);
+                                                               (T)c2, ok, r, okp);
       rm ^= 1u << l;
       dm ^= 1u << l;
     }
@@ -513,9 +537,9 @@ void fused_vcycle_setup(ba_problem* P) {
   P->vc_ready = true;
 }
 
-void fused_vcycle(ba_problem* P, const double* r, double* z) {
-  if (level_fp32(P)) run<float>(P, r, z);
-  else run<double>(P, r, z);
+void fused_vcycle(ba_problem* P, const double* r, double* z, double* rz_part) {
+  if (level_fp32(P)) run<float>(P, r, z, rz_part);
+  else run<double>(P, r, z, rz_part);
 }
 
 }  // namespace ba
