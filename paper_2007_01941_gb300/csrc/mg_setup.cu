@@ -1429,7 +1429,7 @@ __device__ __forceinline__ DF gj_tile_dot(const float2 x[kGJ][kGJ + 1], const fl
 
 __global__ void __launch_bounds__(kGJBS) k_gauss_jordan_df(float2* Aa, float2* Ab, int Np, float2* pinv, int* flags) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ float2 piv[kGJ][kGJ + 1];
+  __shared__ float2 piv[kGJ][kGJ + 1], piv2[kGJ][kGJ + 1];
   __shared__ float2 gj_row[kGJ], gj_col[kGJ];
   __shared__ float2 gj_ip;
   __shared__ float2 sa[kGJ][kGJ + 1], sb[kGJ][kGJ + 1], st[kGJ][kGJ + 1];
@@ -1449,10 +1449,12 @@ __global__ void __launch_bounds__(kGJBS) k_gauss_jordan_df(float2* Aa, float2* A
     const int K0 = K * kGJ;
     piv[u][v] = pinv[(size_t)(K & 1) * kGJBS + t];
     __syncthreads();
-    bool owner = false;
-    for (int w = blockIdx.x; w < nb * nb; w += gridDim.x) {
+    // this CTA's tiles; the next pivot block first if it is one of them, so that its
+    // inverse is formed while the other CTAs update their tiles
+    const int wn = K + 1 < nb ? (K + 1) * nb + (K + 1) : -1;
+    const bool owner = wn >= 0 && wn % (int)gridDim.x == (int)blockIdx.x;
+    for (int it = 0, w = owner ? wn : (int)blockIdx.x; w < nb * nb; ++it) {
       const int I = w / nb, J = w - I * nb;
-      if (I == K + 1 && J == K + 1) owner = true;
       DF out;
       if (I == K && J == K) {
         out = DF(piv[u][v].x, piv[u][v].y);
@@ -1476,14 +1478,18 @@ __global__ void __launch_bounds__(kGJBS) k_gauss_jordan_df(float2* Aa, float2* A
       }
       An[(size_t)(I * kGJ + u) * Np + J * kGJ + v] = make_float2(out.h, out.l);
       __syncthreads();
-    }
-    if (owner) {
-      const int K1 = K0 + kGJ;
-      piv[u][v] = An[(size_t)(K1 + u) * Np + K1 + v];
-      __syncthreads();
-      const bool ok = gj_invert_df(piv, gj_row, gj_col, gj_ip);
-      if (t == 0 && !ok) flags[F_NOT_SPD_COARSE] = 1;
-      pinv[(size_t)((K + 1) & 1) * kGJBS + t] = piv[u][v];
+      if (w == wn) {
+        piv2[u][v] = make_float2(out.h, out.l);
+        __syncthreads();
+        const bool ok = gj_invert_df(piv2, gj_row, gj_col, gj_ip);
+        if (t == 0 && !ok) flags[F_NOT_SPD_COARSE] = 1;
+        pinv[(size_t)((K + 1) & 1) * kGJBS + t] = piv2[u][v];
+        __syncthreads();
+      }
+      // next tile in this CTA's order, the pivot block (done first) skipped
+      if (owner && it == 0) w = (int)blockIdx.x;
+      else w += gridDim.x;
+      if (owner && w == wn) w += gridDim.x;
     }
     grid.sync();
   }
