@@ -185,6 +185,30 @@ def reference_main(args):
 
 
 # ------------------------------------------------------------------------------
+# replicas (one process per GPU, each solving its own copy of the workload)
+# ------------------------------------------------------------------------------
+def replica_barrier(world, dev=None):
+    """All ranks reach this point (and this rank's device work is done)."""
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.barrier()
+    if dev is not None and dev.type == "cuda":
+        torch.cuda.synchronize(dev)
+
+
+def replica_max(v, world, dev):
+    """The largest v over all ranks (the timing of a replica run is its slowest rank)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------
 # GPU arm
 # ------------------------------------------------------------------------------
 def gpu_main(args):
@@ -224,16 +248,10 @@ def gpu_main(args):
         return p.lm_step(c, x, obs, s.lam)
 
     def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
+        replica_barrier(world, dev)
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(v, world, dev)
 
     for _ in range(args.warmup):
         step(prob, cams, pts)

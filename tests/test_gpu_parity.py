@@ -353,6 +353,23 @@ def test_pcg_assembled_level0_matches_oracle(gpu, precision):
     assert abs(it_imp - it_exp) <= max(1, it_imp // 10), (it_imp, it_exp)
 
 
+def test_mixed_implicit_fp64_outer_product_matches_oracle(gpu):
+    """Mixed precision with the implicit PCG product in FP64 arithmetic
+    (outer_product = BA_OUTER_FP64): the FP64 Jacobian records are formed from the stored
+    float pairs before the PCG graph is captured; the solve reaches the FP64 answer."""
+    api, F_ = _api()
+    s = scene("street_chain", **CHAIN)
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+    exact = sla.cho_solve(sla.cho_factor(sch.S.toarray()), sch.b)
+    prob, cams, pts, obs = _prob(s, gpu, precision=F_.BA_MIXED, coarse_max_nodes=16, rtol=1e-10,
+                                 level0_operator=F_.BA_OP_IMPLICIT, outer_product=F_.BA_OUTER_FP64)
+    dc, dp, it, relres = prob.solve(cams, pts, obs, s.lam)
+    assert relres <= 1e-10 and not prob.info()["level0_explicit"]
+    d = _np(dc).ravel()
+    assert np.linalg.norm(sch.b - sch.S @ d) <= 2e-10 * np.linalg.norm(sch.b)
+    assert np.linalg.norm(d - exact) <= 1e-6 * np.linalg.norm(exact)
+
+
 def test_lm_step_matches_oracle(gpu):
     api, F_ = _api()
     s = scene("ring", seed=0)
