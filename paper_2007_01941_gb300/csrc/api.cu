@@ -182,7 +182,8 @@ void ba_destroy(ba_problem* P) {
     ba::DBuf* lb[] = {&L.row_ptr, &L.cols, &L.W, &L.vals64, &L.vals32, &L.sptr, &L.sidx, &L.agg, &L.agg_ptr,
                       &L.agg_mem, &L.K, &L.Q64, &L.Q32, &L.kept, &L.Dblk, &L.Dinv64, &L.Dinv32, &L.cheb,
                       &L.Ainv, &L.vx, &L.vb, &L.vr, &L.vd, &L.vq, &L.vt, &L.vs, &L.pair_ptr, &L.pairs,
-                      &L.blk_row, &L.up_blk, &L.mirror, &L.Dblk32, &L.valsdf, &L.gal_ptr,
+                      &L.blk_row, &L.up_blk, &L.mirror, &L.Dblk32, &L.valsdf, &L.ap_ptr, &L.ap_cols, &L.ap_lptr,
+                      &L.ap_list, &L.ap_vals, &L.gal_ptr,
                       &L.gal_list, &L.gal_row};
     for (ba::DBuf* b : lb) b->release();
   }

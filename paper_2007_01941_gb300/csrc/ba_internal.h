@@ -105,6 +105,8 @@ struct Level {
   DBuf pair_ptr, pairs, blk_row; // level 0: observation pairs per work block (int [n_up+1], int2), block rows
   DBuf up_blk, mirror;          // level 0: blocks on and above the diagonal and their transposes
   DBuf gal_ptr, gal_list, gal_row;  // fine blocks (block, row) per block of the next level, its rows
+  DBuf ap_ptr, ap_cols, ap_lptr, ap_list, ap_vals;  // A P blocks (bs x 16) per fine row, their A blocks
+  int ap_nnzb = 0;
   int n_up = 0;
   DBuf K;                       // double [n][bs][16] near-nullspace rows
   DBuf Q64, Q32;                // double/float [n][bs][16] prolongator blocks

@@ -14,8 +14,8 @@
 //   residual:                s = r - A d
 //   restriction:             b_c[a] = sum_{i in a} Q_i^T s_i     (one warp per aggregate)
 //   coarsest:                x_c = A_c^-1 b_c
-//   prolongation:            x_i += Q_i x_c[agg(i)]
-//   post-smoothing step 0:   q = A x; r = b - q; d = D^-1 r / theta; x' = x + d
+//   prolongation and post-smoothing step 0, from A P and the residual s of the pre-smoothed
+//                            x: r = s - (A P) x_c; d = D^-1 r / theta; x' = x + Q x_c[agg] + d
 //                  step k:   as in pre-smoothing
 // d and r alternate between two buffers per level, and x moves to its second buffer
 // at post-smoothing step 0, so that no kernel writes a vector that its own warps read.
@@ -25,6 +25,8 @@
 #include "device_util.cuh"
 
 namespace ba {
+
+bool level_fp32(ba_problem* P);
 
 template <typename T>
 struct VLevel {
@@ -40,6 +42,9 @@ struct VLevel {
   const int* agg_mem;
   const double* cheb;
   const double* Ainv;  // coarsest: [N][Np]
+  const int* ap_ptr;   // A P: blocks (bs x 16) of fine row i, their aggregates and values
+  const int* ap_cols;
+  const T* ap_vals;
   T* b;
   T* x[2];
   T* r[2];
@@ -413,6 +418,175 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first(VLevel<T
   }
 }
 
+// Prolongation and post-smoothing step 0 in one launch, from A P (assembled with the
+// hierarchy): with s = b - A x the residual of the pre-smoothed iterate (left in the free
+// r buffer by the residual kernel) and x' = x + P x_c,
+//   r = b - A x' = s - (A P) x_c,  d = D^-1 r / theta,  x'' = x' + d,
+// so row i needs x_c only, not its neighbours' prolonged x'.
+template <typename T, int BS>
+__global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first_ap(VLevel<T> L, VLevel<T> C, int xc, int xcl,
+                                                                          int rc, int dc, double* __restrict__ out,
+                                                                          const double* __restrict__ rdot,
+                                                                          double* __restrict__ dpart) {
+  constexpr int G = RowCta<BS>::G;
+  constexpr int kPre = 2;
+  __shared__ T part[G * BS];
+  __shared__ T q[BS], w[BS];
+  const int i = blockIdx.x, t = threadIdx.x;
+  const int u = t % BS, h = t / BS;
+  // static data first: this thread's first kPre blocks of (A P)_i (row u), Q_i row u, D_i^-1
+  // row u and the aggregate of row i
+  int e = 0, e1 = 0, np = 0;
+  int pc[kPre];
+  T pa[kPre][16];
+  if (h < G) {
+    e1 = L.ap_ptr[i + 1];
+    e = L.ap_ptr[i] + h;
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      if (e < e1) {
+        pc[k] = L.ap_cols[e];
+        const T* a = L.ap_vals + (size_t)e * (BS * 16) + u * 16;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) pa[k][c] = a[c];
+        np = k + 1;
+        e += G;
+      }
+    }
+  }
+  T dr[BS], qr[16];
+  int ai = 0;
+  if (t < BS) {
+    dinv_row<T, BS>(L.Dinv + (size_t)i * BS * BS, t, dr);
+    const T* Qi = L.Q + ((size_t)i * BS + t) * 16;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) qr[c] = Qi[c];
+    ai = L.agg[i];
+  }
+  pdl_trigger();
+  pdl_wait();
+  const T* xcv = C.x[xcl];
+  if (h < G) {
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      if (k < np) {
+        const T* xa = xcv + (size_t)pc[k] * 16;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc += pa[k][c] * xa[c];
+      }
+    }
+    for (; e < e1; e += G) {
+      const T* a = L.ap_vals + (size_t)e * (BS * 16) + u * 16;
+      const T* xa = xcv + (size_t)L.ap_cols[e] * 16;
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc += a[c] * xa[c];
+    }
+    part[h * BS + u] = acc;
+  }
+  __syncthreads();
+  const size_t idx = (size_t)i * BS + t;
+  T xp = T(0);
+  if (t < BS) {
+    T sq = T(0);
+#pragma unroll
+    for (int g = 0; g < G; ++g) sq += part[g * BS + t];
+    const T* xa = xcv + (size_t)ai * 16;
+    T pq = T(0);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) pq += qr[c] * xa[c];
+    xp = L.x[xc][idx] + pq;
+    w[t] = L.r[1 - rc][idx] - sq;
+  }
+  __syncthreads();
+  double dot = 0.0;
+  if (t < BS) {
+    const T dv = row_dinv<T, BS>(dr, w) * (T)(1.0 / L.cheb[0]);
+    const T xn = xp + dv;
+    L.r[rc][idx] = w[t];
+    L.d[dc][idx] = dv;
+    L.x[1 - xc][idx] = xn;
+    if (out) {
+      out[idx] = (double)xn;
+      if (dpart) dot = (double)xn * rdot[idx];
+    }
+  }
+  if (dpart && t < 32) {
+    dot = warp_sum(dot);
+    if (t == 0) dpart[i] = dot;
+  }
+}
+
+// (A P) blocks of a level, one warp per block: sum over the listed A blocks of A_ij Q_j
+template <typename T, int BS>
+__global__ void __launch_bounds__(128) k_ap_values(int nap, const int* __restrict__ lptr, const int* __restrict__ list,
+                                                  const int* __restrict__ cols, const T* __restrict__ vals,
+                                                  const T* __restrict__ Q, T* __restrict__ ap) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (c >= nap) return;
+  for (int o = lane; o < BS * 16; o += 32) {
+    const int uu = o / 16, ss = o - uu * 16;
+    T acc = T(0);
+    for (int k = lptr[c]; k < lptr[c + 1]; ++k) {
+      const int e = list[k], j = cols[e];
+      const T* a = vals + (size_t)e * BS * BS + uu * BS;
+      const T* qj = Q + (size_t)j * BS * 16 + ss;
+#pragma unroll
+      for (int v = 0; v < BS; ++v) acc += a[v] * qj[v * 16];
+    }
+    ap[(size_t)c * BS * 16 + o] = acc;
+  }
+}
+
+// pattern of A P for a level (the distinct aggregates of each fine row's neighbours, in
+// increasing order) and, per block, its contributing A blocks in row order
+static void ap_symbolic(ba_problem* P, Level& L) {
+  std::vector<int> rp(L.n + 1), cl(std::max(L.nnzb, 1)), agg(std::max(L.n, 1));
+  BA_CUDA(cudaMemcpyAsync(rp.data(), L.row_ptr.p, sizeof(int) * (L.n + 1), cudaMemcpyDeviceToHost, P->stream));
+  if (L.nnzb)
+    BA_CUDA(cudaMemcpyAsync(cl.data(), L.cols.p, sizeof(int) * L.nnzb, cudaMemcpyDeviceToHost, P->stream));
+  BA_CUDA(cudaMemcpyAsync(agg.data(), L.agg.p, sizeof(int) * L.n, cudaMemcpyDeviceToHost, P->stream));
+  sync(P);
+  std::vector<int> ap_ptr(L.n + 1, 0), ap_cols, lptr(1, 0), list;
+  std::vector<int> aggs;
+  for (int i = 0; i < L.n; ++i) {
+    aggs.clear();
+    for (int e = rp[i]; e < rp[i + 1]; ++e) aggs.push_back(agg[cl[e]]);
+    std::sort(aggs.begin(), aggs.end());
+    aggs.erase(std::unique(aggs.begin(), aggs.end()), aggs.end());
+    for (int a : aggs) {
+      ap_cols.push_back(a);
+      for (int e = rp[i]; e < rp[i + 1]; ++e)
+        if (agg[cl[e]] == a) list.push_back(e);
+      lptr.push_back((int)list.size());
+    }
+    ap_ptr[i + 1] = (int)ap_cols.size();
+  }
+  L.ap_nnzb = (int)ap_cols.size();
+  upload(P, L.ap_ptr, ap_ptr);
+  upload(P, L.ap_cols, ap_cols);
+  upload(P, L.ap_lptr, lptr);
+  upload(P, L.ap_list, list);
+  sync(P);
+}
+
+template <typename T>
+static void ap_numeric(ba_problem* P, Level& L) {
+  const bool fp32 = sizeof(T) == 4;
+  L.ap_vals.ensure(sizeof(T) * (size_t)L.bs * 16 * std::max(L.ap_nnzb, 1) + 64);
+  const int g = cdiv(std::max(L.ap_nnzb, 1), 4);
+  const T* vals = fp32 ? (const T*)L.vals32.p : (const T*)L.vals64.p;
+  const T* Q = fp32 ? (const T*)L.Q32.p : (const T*)L.Q64.p;
+  if (L.bs == 9)
+    k_ap_values<T, 9><<<g, 128, 0, P->stream>>>(L.ap_nnzb, L.ap_lptr.as<int>(), L.ap_list.as<int>(), L.cols.as<int>(),
+                                               vals, Q, L.ap_vals.as<T>());
+  else
+    k_ap_values<T, 16><<<g, 128, 0, P->stream>>>(L.ap_nnzb, L.ap_lptr.as<int>(), L.ap_list.as<int>(),
+                                                L.cols.as<int>(), vals, Q, L.ap_vals.as<T>());
+  launched(P);
+}
+
 template <typename T>
 static VLevel<T> describe(Level& L) {
   const bool fp32 = sizeof(T) == 4;
@@ -432,6 +606,9 @@ static VLevel<T> describe(Level& L) {
   v.agg_mem = L.agg_mem.as<int>();
   v.cheb = L.cheb.as<double>();
   v.Ainv = L.Ainv.as<double>();
+  v.ap_ptr = L.ap_ptr.as<int>();
+  v.ap_cols = L.ap_cols.as<int>();
+  v.ap_vals = (const T*)L.ap_vals.p;
   v.b = L.vb.as<T>();
   v.x[0] = L.vx.as<T>();
   v.x[1] = L.vt.as<T>();
@@ -496,16 +673,14 @@ static void run(ba_problem* P, const double* r, double* z, double* dpart) {
   launch_k(P, k_ph_coarsest<T>, warps_grid(V[nl - 1].N), kPhaseBS, 0, V[nl - 1]);
   for (int l = nl - 2; l >= 0; --l) {
     const VLevel<T>& L = V[l];
-    const int g = warps_grid(L.n);
-    launch_k(P, k_ph_prolong<T>, cdiv((long long)L.n * L.bs, kPhaseBS), kPhaseBS, 0, L, V[l + 1], bit(xm, l),
-                                                                               bit(xm, l + 1));
     double* o = (l == 0 && post == 1) ? z : nullptr;
     double* op = o ? dpart : nullptr;
     if (L.bs == 9)
-      launch_k(P, k_ph_post_first<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(xm, l), bit(rm, l), bit(dm, l), o, r, op);
+      launch_k(P, k_ph_post_first_ap<T, 9>, L.n, RowCta<9>::kThreads, 0, L, V[l + 1], bit(xm, l), bit(xm, l + 1),
+               bit(rm, l), bit(dm, l), o, r, op);
     else
-      launch_k(P, k_ph_post_first<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(xm, l), bit(rm, l), bit(dm, l), o, r,
-               op);
+      launch_k(P, k_ph_post_first_ap<T, 16>, L.n, RowCta<16>::kThreads, 0, L, V[l + 1], bit(xm, l), bit(xm, l + 1),
+               bit(rm, l), bit(dm, l), o, r, op);
     xm ^= 1u << l;
     for (int k = 1; k < post; ++k) {
       double c1, c2;
@@ -524,8 +699,6 @@ static void run(ba_problem* P, const double* r, double* z, double* dpart) {
   }
 }
 
-bool level_fp32(ba_problem* P);
-
 // Called at the end of the multigrid setup: whether the fused-phase cycle applies.
 void fused_vcycle_setup(ba_problem* P) {
   P->vc_ready = false;
@@ -533,6 +706,14 @@ void fused_vcycle_setup(ba_problem* P) {
   for (int l = 0; l + 1 < P->n_levels; ++l) {
     const int bs = P->levels[l].bs;
     if (bs != 9 && bs != 16) return;
+  }
+  // A P of every smoothed level for the fused prolongation + post-smoothing start
+  const bool fp32 = level_fp32(P);
+  for (int l = 0; l + 1 < P->n_levels; ++l) {
+    Level& L = P->levels[l];
+    if (!L.ap_ptr.p) ap_symbolic(P, L);
+    if (fp32) ap_numeric<float>(P, L);
+    else ap_numeric<double>(P, L);
   }
   P->vc_ready = true;
 }
