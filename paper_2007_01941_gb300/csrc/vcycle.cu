@@ -517,26 +517,24 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first_ap(VLeve
   }
 }
 
-// (A P) blocks of a level, one warp per block: sum over the listed A blocks of A_ij Q_j
+// (A P) blocks of a level, one CTA per block and one thread per entry (u, s): the sum over
+// the listed A blocks of (A_ij Q_j)[u][s]
 template <typename T, int BS>
-__global__ void __launch_bounds__(128) k_ap_values(int nap, const int* __restrict__ lptr, const int* __restrict__ list,
+__global__ void __launch_bounds__(256) k_ap_values(int nap, const int* __restrict__ lptr, const int* __restrict__ list,
                                                   const int* __restrict__ cols, const T* __restrict__ vals,
                                                   const T* __restrict__ Q, T* __restrict__ ap) {
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (c >= nap) return;
-  for (int o = lane; o < BS * 16; o += 32) {
-    const int uu = o / 16, ss = o - uu * 16;
-    T acc = T(0);
-    for (int k = lptr[c]; k < lptr[c + 1]; ++k) {
-      const int e = list[k], j = cols[e];
-      const T* a = vals + (size_t)e * BS * BS + uu * BS;
-      const T* qj = Q + (size_t)j * BS * 16 + ss;
+  const int c = blockIdx.x, o = threadIdx.x;
+  if (o >= BS * 16) return;
+  const int uu = o / 16, ss = o - uu * 16;
+  T acc = T(0);
+  for (int k = lptr[c]; k < lptr[c + 1]; ++k) {
+    const int e = list[k], j = cols[e];
+    const T* a = vals + (size_t)e * BS * BS + uu * BS;
+    const T* qj = Q + (size_t)j * BS * 16 + ss;
 #pragma unroll
-      for (int v = 0; v < BS; ++v) acc += a[v] * qj[v * 16];
-    }
-    ap[(size_t)c * BS * 16 + o] = acc;
+    for (int v = 0; v < BS; ++v) acc += a[v] * qj[v * 16];
   }
+  ap[(size_t)c * BS * 16 + o] = acc;
 }
 
 // pattern of A P for a level (the distinct aggregates of each fine row's neighbours, in
@@ -575,14 +573,15 @@ template <typename T>
 static void ap_numeric(ba_problem* P, Level& L) {
   const bool fp32 = sizeof(T) == 4;
   L.ap_vals.ensure(sizeof(T) * (size_t)L.bs * 16 * std::max(L.ap_nnzb, 1) + 64);
-  const int g = cdiv(std::max(L.ap_nnzb, 1), 4);
+  const int g = std::max(L.ap_nnzb, 1);
   const T* vals = fp32 ? (const T*)L.vals32.p : (const T*)L.vals64.p;
   const T* Q = fp32 ? (const T*)L.Q32.p : (const T*)L.Q64.p;
+  if (L.ap_nnzb == 0) return;
   if (L.bs == 9)
-    k_ap_values<T, 9><<<g, 128, 0, P->stream>>>(L.ap_nnzb, L.ap_lptr.as<int>(), L.ap_list.as<int>(), L.cols.as<int>(),
+    k_ap_values<T, 9><<<g, 160, 0, P->stream>>>(L.ap_nnzb, L.ap_lptr.as<int>(), L.ap_list.as<int>(), L.cols.as<int>(),
                                                vals, Q, L.ap_vals.as<T>());
   else
-    k_ap_values<T, 16><<<g, 128, 0, P->stream>>>(L.ap_nnzb, L.ap_lptr.as<int>(), L.ap_list.as<int>(),
+    k_ap_values<T, 16><<<g, 256, 0, P->stream>>>(L.ap_nnzb, L.ap_lptr.as<int>(), L.ap_list.as<int>(),
                                                 L.cols.as<int>(), vals, Q, L.ap_vals.as<T>());
   launched(P);
 }
