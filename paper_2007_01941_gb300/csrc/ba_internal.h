@@ -104,7 +104,7 @@ struct Level {
   DBuf agg_ptr, agg_mem;        // member lists of the next-level nodes
   DBuf pair_ptr, pairs, blk_row; // level 0: observation pairs per work block (int [n_up+1], int2), block rows
   DBuf up_blk, mirror;          // level 0: blocks on and above the diagonal and their transposes
-  DBuf gal_ptr, gal_list, gal_row;  // fine blocks (block, row) per block of the next level, its rows
+  DBuf gal_ptr, gal_list, gal_row;  // A P blocks (block, fine row) per block of the next level, its rows
   DBuf ap_ptr, ap_cols, ap_lptr, ap_list, ap_vals;  // A P blocks (bs x 16) per fine row, their A blocks
   int ap_nnzb = 0;
   int n_up = 0;
@@ -297,6 +297,8 @@ bool outer_df(ba_problem* P);                                         // mixed m
 void split_vector(ba_problem* P, const double* x, const double* Dc, double* y);  // xsplit = split(x); y = Dc o x
 void matvec_df_accumulate(ba_problem* P, double* y);                   // y += S x - Dc x from xsplit
 void lanczos_batched(ba_problem* P, int first, int last);  // levels first..last, all assembled
+// A_l P_l of a smoothed level: pattern (once per problem) and blocks
+void build_ap(ba_problem* P, Level& L);
 void fused_vcycle_setup(ba_problem* P);
 // z = M r; rz_part (optional): per level-0 row, its share of r.z (one value per block row)
 void fused_vcycle(ba_problem* P, const double* r, double* z, double* rz_part);

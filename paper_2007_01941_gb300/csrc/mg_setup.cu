@@ -851,22 +851,21 @@ k_aggregate_qr_cta(int n_agg, int bs, const int* __restrict__ mptr, const int* _
 }
 
 // ---------------------------------------------------------------------------
-// Galerkin product A_{l+1} = P^T A_l P (Section 2.3) on the coarse pattern:
-//   A_{l+1}[a, b] = sum_{i in a} sum_{j in b, A_ij != 0} Q_i^T A_ij Q_j.
-// The fine blocks that meet in each coarse block are listed once per problem (members of
-// a in list order, then the row's blocks in order), and one warp owns a coarse block:
-// lane s + 16 h keeps entries (8 h .. 8 h + 7, s) in registers and adds each fine
-// block's Q_i^T (A_ij Q_j) to them.  A coarse dof dropped by the QR (zero Q column) gets
-// a unit diagonal, which decouples it.
+// Galerkin product A_{l+1} = P^T A_l P (Section 2.3) on the coarse pattern, from the
+// blocks of A_l P_l (assembled first, one per fine row and neighbouring aggregate):
+//   A_{l+1}[a, b] = sum_{i in a} Q_i^T (A P)[i, b].
+// The A P blocks that meet in each coarse block are listed once per problem (members of a
+// in list order), and one warp owns a coarse block: lane s + 16 h keeps entries
+// (8 h .. 8 h + 7, s) in registers.  A coarse dof dropped by the QR (zero Q column) gets a
+// unit diagonal, which decouples it.
 // ---------------------------------------------------------------------------
 constexpr int kGalBS = 128;
 
 template <typename T, int BS>
 __global__ void __launch_bounds__(kGalBS)
 k_galerkin(int nnzb_c, const int* __restrict__ gal_ptr, const int2* __restrict__ gal_list,
-           const int* __restrict__ gal_row, const int* __restrict__ ccols, const int* __restrict__ cols,
-           const T* __restrict__ vals, const T* __restrict__ Q, const unsigned* __restrict__ ckept,
-           T* __restrict__ cvals) {
+           const int* __restrict__ gal_row, const int* __restrict__ ccols, const T* __restrict__ ap,
+           const T* __restrict__ Q, const unsigned* __restrict__ ckept, T* __restrict__ cvals) {
   const int lane = threadIdx.x & 31;
   const int ce = blockIdx.x * (kGalBS / 32) + (threadIdx.x >> 5);
   if (ce >= nnzb_c) return;
@@ -875,30 +874,17 @@ k_galerkin(int nnzb_c, const int* __restrict__ gal_ptr, const int2* __restrict__
 #pragma unroll
   for (int k = 0; k < 8; ++k) out[k] = T(0);
   for (int q = gal_ptr[ce]; q < gal_ptr[ce + 1]; ++q) {
-    const int2 ei = gal_list[q];
-    const int e = ei.x, i = ei.y, j = cols[e];
-    // U[u] = (A_ij Q_j)[u][s]
-    T qj[BS];
-#pragma unroll
-    for (int v = 0; v < BS; ++v) qj[v] = Q[((size_t)j * BS + v) * 16 + s];
-    const T* A = vals + (size_t)e * BS * BS;
-    T U[BS];
-#pragma unroll
-    for (int u = 0; u < BS; ++u) {
-      T acc = T(0);
-#pragma unroll
-      for (int v = 0; v < BS; ++v) acc += A[u * BS + v] * qj[v];
-      U[u] = acc;
-    }
-    // (Q_i^T U)[r][s] for r = r0 .. r0 + 7
+    const int2 ci = gal_list[q];
+    const T* apc = ap + (size_t)ci.x * BS * 16 + s;
+    const T* qi = Q + (size_t)ci.y * BS * 16 + r0;
     T acc[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = T(0);
 #pragma unroll
     for (int u = 0; u < BS; ++u) {
-      const T* qi = Q + ((size_t)i * BS + u) * 16 + r0;
+      const T a = apc[u * 16];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) acc[k] += qi[k] * U[u];
+      for (int k = 0; k < 8; ++k) acc[k] += qi[u * 16 + k] * a;
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) out[k] += acc[k];
@@ -915,74 +901,15 @@ k_galerkin(int nnzb_c, const int* __restrict__ gal_ptr, const int2* __restrict__
   }
 }
 
-// The same product with one CTA per coarse row, thread (r, s) owning entry (r, s) of every
-// block of the row: the faster form for the 16x16 blocks of the coarse levels, whose rows
-// gather many fine blocks.
-constexpr int kGalRowBS = 256;
-template <typename T>
-__global__ void __launch_bounds__(kGalRowBS)
-k_galerkin_rows(int bs, const int* __restrict__ row_ptr, const int* __restrict__ cols, const T* __restrict__ vals,
-           const T* __restrict__ Q, const int* __restrict__ agg, const int* __restrict__ mptr,
-           const int* __restrict__ mem, const int* __restrict__ crow_ptr, const int* __restrict__ ccols,
-           const unsigned* __restrict__ ckept, T* __restrict__ cvals) {
-  __shared__ T sA[16 * 16];
-  __shared__ T sQj[16 * 16];
-  __shared__ T sQi[16 * 16];
-  __shared__ T sU[16 * 16];
-  const int a = blockIdx.x;
-  const int t = threadIdx.x;
-  const int r = t >> 4, s = t & 15;
-  const int cb = crow_ptr[a], ce = crow_ptr[a + 1];
-  for (int e = cb; e < ce; ++e) cvals[(size_t)e * 256 + t] = T(0);
-  for (int k = mptr[a]; k < mptr[a + 1]; ++k) {
-    const int i = mem[k];
-    __syncthreads();
-    if (t < bs * 16) sQi[t] = Q[(size_t)i * bs * 16 + t];
-    for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-      const int j = cols[e];
-      const int aj = agg[j];
-      // slot of aj in coarse row a
-      int lo = cb, hi = ce - 1, slot = -1;
-      while (lo <= hi) {
-        const int mid = (lo + hi) >> 1;
-        const int v = ccols[mid];
-        if (v == aj) { slot = mid; break; }
-        if (v < aj) lo = mid + 1; else hi = mid - 1;
-      }
-      __syncthreads();
-      if (t < bs * bs) sA[t] = vals[(size_t)e * bs * bs + t];
-      if (t < bs * 16) sQj[t] = Q[(size_t)j * bs * 16 + t];
-      __syncthreads();
-      if (t < bs * 16) {
-        const int u = t >> 4;
-        T acc = T(0);
-        for (int v = 0; v < bs; ++v) acc += sA[u * bs + v] * sQj[v * 16 + s];
-        sU[t] = acc;
-      }
-      __syncthreads();
-      T acc = T(0);
-      for (int u = 0; u < bs; ++u) acc += sQi[u * 16 + r] * sU[u * 16 + s];
-      if (slot >= 0) cvals[(size_t)slot * 256 + t] += acc;
-    }
-  }
-  __syncthreads();
-  // dropped coarse dofs: unit diagonal (decoupled)
-  if (r == s && !((ckept[a] >> r) & 1u)) {
-    for (int e = cb; e < ce; ++e)
-      if (ccols[e] == a) cvals[(size_t)e * 256 + t] = T(1);
-  }
-}
-
-// the fine blocks of level L that meet in each block of level L1 (built on the host once)
+// the A P blocks of level L that meet in each block of level L1 (built on the host once)
 static void galerkin_symbolic(ba_problem* P, Level& L, Level& L1) {
-  auto down = [&](std::vector<int>& h, const DBuf& d, size_t n) {
-    h.resize(std::max<size_t>(n, 1));
-    if (n) BA_CUDA(cudaMemcpyAsync(h.data(), d.p, sizeof(int) * n, cudaMemcpyDeviceToHost, P->stream));
+  auto down = [&](std::vector<int>& hv, const DBuf& d, size_t n) {
+    hv.resize(std::max<size_t>(n, 1));
+    if (n) BA_CUDA(cudaMemcpyAsync(hv.data(), d.p, sizeof(int) * n, cudaMemcpyDeviceToHost, P->stream));
   };
-  std::vector<int> rp, cl, agg, aptr, amem, crp, ccl;
-  down(rp, L.row_ptr, L.n + 1);
-  down(cl, L.cols, L.nnzb);
-  down(agg, L.agg, L.n);
+  std::vector<int> app, apc, aptr, amem, crp, ccl;
+  down(app, L.ap_ptr, L.n + 1);
+  down(apc, L.ap_cols, L.ap_nnzb);
   down(aptr, L.agg_ptr, L1.n + 1);
   down(amem, L.agg_mem, L.n);
   down(crp, L1.row_ptr, L1.n + 1);
@@ -1001,17 +928,17 @@ static void galerkin_symbolic(ba_problem* P, Level& L, Level& L1) {
     BA_REQUIRE(lo < crp[a + 1] && ccl[lo] == b, BA_ERR_STATE, "coarse pattern misses a Galerkin block");
     return lo;
   };
-  std::vector<int2> list(std::max(L.nnzb, 1));
+  std::vector<int2> list(std::max(L.ap_nnzb, 1));
   for (int pass = 0; pass < 2; ++pass) {
     std::vector<int> fill;
     if (pass == 1) fill.assign(cnt.begin(), cnt.end() - 1);
     for (int a = 0; a < L1.n; ++a)
       for (int m = aptr[a]; m < aptr[a + 1]; ++m) {
         const int i = amem[m];
-        for (int e = rp[i]; e < rp[i + 1]; ++e) {
-          const int c = slot(a, agg[cl[e]]);
-          if (pass == 0) ++cnt[c + 1];
-          else list[fill[c]++] = make_int2(e, i);
+        for (int c = app[i]; c < app[i + 1]; ++c) {
+          const int sl = slot(a, apc[c]);
+          if (pass == 0) ++cnt[sl + 1];
+          else list[fill[sl]++] = make_int2(c, i);
         }
       }
     if (pass == 0)
@@ -1781,34 +1708,34 @@ void mg_setup(ba_problem* P) {
                                                           L1.K.as<double>(), L1.kept.as<unsigned>());
     }
     launched(P);
-    // Galerkin: warp per coarse block from level 0 (9x9 fine blocks), CTA per coarse row below
-    if (fp32) L1.vals32.ensure(sizeof(float) * 256 * (size_t)L1.nnzb + 64);
-    else L1.vals64.ensure(sizeof(double) * 256 * (size_t)L1.nnzb + 64);
-    if (L.bs == 9) {
-      if (!L.gal_ptr.p) galerkin_symbolic(P, L, L1);
-      const int gg = cdiv(std::max(L1.nnzb, 1), kGalBS / 32);
-      if (fp32)
-        k_galerkin<float, 9><<<gg, kGalBS, 0, P->stream>>>(
-            L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(), L.gal_row.as<int>(), L1.cols.as<int>(),
-            L.cols.as<int>(), L.vals32.as<float>(), L.Q32.as<float>(), L1.kept.as<unsigned>(), L1.vals32.as<float>());
+    // Galerkin from A P (which the fused V-cycle also uses)
+    build_ap(P, L);
+    if (!L.gal_ptr.p) galerkin_symbolic(P, L, L1);
+    const int gg = cdiv(std::max(L1.nnzb, 1), kGalBS / 32);
+    if (fp32) {
+      L1.vals32.ensure(sizeof(float) * 256 * (size_t)L1.nnzb + 64);
+      if (L.bs == 9)
+        k_galerkin<float, 9><<<gg, kGalBS, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
+                                                          L.gal_row.as<int>(), L1.cols.as<int>(),
+                                                          L.ap_vals.as<float>(), L.Q32.as<float>(),
+                                                          L1.kept.as<unsigned>(), L1.vals32.as<float>());
       else
-        k_galerkin<double, 9><<<gg, kGalBS, 0, P->stream>>>(
-            L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(), L.gal_row.as<int>(), L1.cols.as<int>(),
-            L.cols.as<int>(), L.vals64.as<double>(), L.Q64.as<double>(), L1.kept.as<unsigned>(),
-            L1.vals64.as<double>());
-    } else if (fp32) {
-      k_galerkin_rows<float><<<L1.n, kGalRowBS, 0, P->stream>>>(L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
-                                                             L.vals32.as<float>(), L.Q32.as<float>(), L.agg.as<int>(),
-                                                             L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
-                                                             L1.row_ptr.as<int>(), L1.cols.as<int>(),
-                                                             L1.kept.as<unsigned>(), L1.vals32.as<float>());
+        k_galerkin<float, 16><<<gg, kGalBS, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
+                                                           L.gal_row.as<int>(), L1.cols.as<int>(),
+                                                           L.ap_vals.as<float>(), L.Q32.as<float>(),
+                                                           L1.kept.as<unsigned>(), L1.vals32.as<float>());
     } else {
-      k_galerkin_rows<double><<<L1.n, kGalRowBS, 0, P->stream>>>(L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
-                                                              L.vals64.as<double>(), L.Q64.as<double>(),
-                                                              L.agg.as<int>(), L.agg_ptr.as<int>(),
-                                                              L.agg_mem.as<int>(), L1.row_ptr.as<int>(),
-                                                              L1.cols.as<int>(), L1.kept.as<unsigned>(),
-                                                              L1.vals64.as<double>());
+      L1.vals64.ensure(sizeof(double) * 256 * (size_t)L1.nnzb + 64);
+      if (L.bs == 9)
+        k_galerkin<double, 9><<<gg, kGalBS, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
+                                                           L.gal_row.as<int>(), L1.cols.as<int>(),
+                                                           L.ap_vals.as<double>(), L.Q64.as<double>(),
+                                                           L1.kept.as<unsigned>(), L1.vals64.as<double>());
+      else
+        k_galerkin<double, 16><<<gg, kGalBS, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
+                                                            L.gal_row.as<int>(), L1.cols.as<int>(),
+                                                            L.ap_vals.as<double>(), L.Q64.as<double>(),
+                                                            L1.kept.as<unsigned>(), L1.vals64.as<double>());
     }
     launched(P);
   }

@@ -586,6 +586,12 @@ static void ap_numeric(ba_problem* P, Level& L) {
   launched(P);
 }
 
+void build_ap(ba_problem* P, Level& L) {
+  if (!L.ap_ptr.p) ap_symbolic(P, L);
+  if (level_fp32(P)) ap_numeric<float>(P, L);
+  else ap_numeric<double>(P, L);
+}
+
 template <typename T>
 static VLevel<T> describe(Level& L) {
   const bool fp32 = sizeof(T) == 4;
@@ -706,14 +712,8 @@ void fused_vcycle_setup(ba_problem* P) {
     const int bs = P->levels[l].bs;
     if (bs != 9 && bs != 16) return;
   }
-  // A P of every smoothed level for the fused prolongation + post-smoothing start
-  const bool fp32 = level_fp32(P);
-  for (int l = 0; l + 1 < P->n_levels; ++l) {
-    Level& L = P->levels[l];
-    if (!L.ap_ptr.p) ap_symbolic(P, L);
-    if (fp32) ap_numeric<float>(P, L);
-    else ap_numeric<double>(P, L);
-  }
+  // (A P of every smoothed level, for the fused prolongation + post-smoothing start, was
+  // assembled with the Galerkin products)
   P->vc_ready = true;
 }
 
