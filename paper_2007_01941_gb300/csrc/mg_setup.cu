@@ -855,25 +855,26 @@ k_aggregate_qr_cta(int n_agg, int bs, const int* __restrict__ mptr, const int* _
 // blocks of A_l P_l (assembled first, one per fine row and neighbouring aggregate):
 //   A_{l+1}[a, b] = sum_{i in a} Q_i^T (A P)[i, b].
 // The A P blocks that meet in each coarse block are listed once per problem (members of a
-// in list order), and one warp owns a coarse block: lane s + 16 h keeps entries
-// (8 h .. 8 h + 7, s) in registers.  A coarse dof dropped by the QR (zero Q column) gets a
+// in list order), and one CTA owns a coarse block: its warps take every kGalWarps-th A P
+// block, lane s + 16 h keeping entries (8 h .. 8 h + 7, s) in registers, and the warps'
+// sums are added in warp order.  A coarse dof dropped by the QR (zero Q column) gets a
 // unit diagonal, which decouples it.
 // ---------------------------------------------------------------------------
-constexpr int kGalBS = 128;
+constexpr int kGalWarps = 4;   // warps per coarse block; each takes every kGalWarps-th A P block
 
 template <typename T, int BS>
-__global__ void __launch_bounds__(kGalBS)
+__global__ void __launch_bounds__(kGalWarps * 32)
 k_galerkin(int nnzb_c, const int* __restrict__ gal_ptr, const int2* __restrict__ gal_list,
            const int* __restrict__ gal_row, const int* __restrict__ ccols, const T* __restrict__ ap,
            const T* __restrict__ Q, const unsigned* __restrict__ ckept, T* __restrict__ cvals) {
-  const int lane = threadIdx.x & 31;
-  const int ce = blockIdx.x * (kGalBS / 32) + (threadIdx.x >> 5);
-  if (ce >= nnzb_c) return;
+  __shared__ T part[kGalWarps][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ce = blockIdx.x;
   const int s = lane & 15, r0 = (lane >> 4) * 8;
   T out[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) out[k] = T(0);
-  for (int q = gal_ptr[ce]; q < gal_ptr[ce + 1]; ++q) {
+  for (int q = gal_ptr[ce] + warp; q < gal_ptr[ce + 1]; q += kGalWarps) {
     const int2 ci = gal_list[q];
     const T* apc = ap + (size_t)ci.x * BS * 16 + s;
     const T* qi = Q + (size_t)ci.y * BS * 16 + r0;
@@ -889,15 +890,20 @@ k_galerkin(int nnzb_c, const int* __restrict__ gal_ptr, const int2* __restrict__
 #pragma unroll
     for (int k = 0; k < 8; ++k) out[k] += acc[k];
   }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) part[warp][(r0 + k) * 16 + s] = out[k];
+  __syncthreads();
+  // the warps' partial blocks in warp order; entry e = r * 16 + s per thread
   const int a = gal_row[ce];
   const bool diag = ccols[ce] == a;
   const unsigned kept = ckept[a];
+  for (int e = threadIdx.x; e < 256; e += kGalWarps * 32) {
+    T v = T(0);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int r = r0 + k;
-    T v = out[k];
-    if (diag && r == s && !((kept >> r) & 1u)) v = T(1);
-    cvals[(size_t)ce * 256 + r * 16 + s] = v;
+    for (int w = 0; w < kGalWarps; ++w) v += part[w][e];
+    const int r = e >> 4, sc = e & 15;
+    if (diag && r == sc && !((kept >> r) & 1u)) v = T(1);
+    cvals[(size_t)ce * 256 + e] = v;
   }
 }
 
@@ -1711,28 +1717,28 @@ void mg_setup(ba_problem* P) {
     // Galerkin from A P (which the fused V-cycle also uses)
     build_ap(P, L);
     if (!L.gal_ptr.p) galerkin_symbolic(P, L, L1);
-    const int gg = cdiv(std::max(L1.nnzb, 1), kGalBS / 32);
+    const int gg = std::max(L1.nnzb, 1);
     if (fp32) {
       L1.vals32.ensure(sizeof(float) * 256 * (size_t)L1.nnzb + 64);
       if (L.bs == 9)
-        k_galerkin<float, 9><<<gg, kGalBS, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
+        k_galerkin<float, 9><<<gg, kGalWarps * 32, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
                                                           L.gal_row.as<int>(), L1.cols.as<int>(),
                                                           L.ap_vals.as<float>(), L.Q32.as<float>(),
                                                           L1.kept.as<unsigned>(), L1.vals32.as<float>());
       else
-        k_galerkin<float, 16><<<gg, kGalBS, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
+        k_galerkin<float, 16><<<gg, kGalWarps * 32, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
                                                            L.gal_row.as<int>(), L1.cols.as<int>(),
                                                            L.ap_vals.as<float>(), L.Q32.as<float>(),
                                                            L1.kept.as<unsigned>(), L1.vals32.as<float>());
     } else {
       L1.vals64.ensure(sizeof(double) * 256 * (size_t)L1.nnzb + 64);
       if (L.bs == 9)
-        k_galerkin<double, 9><<<gg, kGalBS, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
+        k_galerkin<double, 9><<<gg, kGalWarps * 32, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
                                                            L.gal_row.as<int>(), L1.cols.as<int>(),
                                                            L.ap_vals.as<double>(), L.Q64.as<double>(),
                                                            L1.kept.as<unsigned>(), L1.vals64.as<double>());
       else
-        k_galerkin<double, 16><<<gg, kGalBS, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
+        k_galerkin<double, 16><<<gg, kGalWarps * 32, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
                                                             L.gal_row.as<int>(), L1.cols.as<int>(),
                                                             L.ap_vals.as<double>(), L.Q64.as<double>(),
                                                             L1.kept.as<unsigned>(), L1.vals64.as<double>());
