@@ -346,78 +346,6 @@ __global__ void __launch_bounds__(256) k_ph_coarsest(VLevel<T> C) {
   }
 }
 
-// x_i += Q_i x_c[agg(i)]
-template <typename T>
-__global__ void __launch_bounds__(256) k_ph_prolong(VLevel<T> L, VLevel<T> C, int xl, int xcl) {
-  const int bs = L.bs;
-  const int idx0 = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-  T qr[16];
-  int ag = 0;
-  if (idx0 < L.n * bs) {
-    const int i = idx0 / bs, u = idx0 - i * bs;
-    const T* Qi = L.Q + ((size_t)i * bs + u) * 16;
-#pragma unroll
-    for (int s = 0; s < 16; ++s) qr[s] = Qi[s];
-    ag = L.agg[i];
-  }
-  pdl_trigger();
-  pdl_wait();
-  T* x = L.x[xl];
-  const T* xc = C.x[xcl];
-  for (int idx = idx0; idx < L.n * bs; idx += stride) {
-    if (idx != idx0) {
-      const int i = idx / bs, u = idx - i * bs;
-      const T* Qi = L.Q + ((size_t)i * bs + u) * 16;
-#pragma unroll
-      for (int s = 0; s < 16; ++s) qr[s] = Qi[s];
-      ag = L.agg[i];
-    }
-    const T* xa = xc + (size_t)ag * 16;
-    T acc = T(0);
-#pragma unroll
-    for (int s = 0; s < 16; ++s) acc += qr[s] * xa[s];
-    x[idx] += acc;
-  }
-}
-
-// post-smoothing step 0 on row blockIdx.x: q = A x; r = b - q; d = D^-1 r / theta; x' = x + d
-template <typename T, int BS>
-__global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first(VLevel<T> L, int xc, int rc, int dc,
-                                                                       double* __restrict__ out,
-                                                                       const double* __restrict__ rdot,
-                                                                       double* __restrict__ dpart) {
-  __shared__ T part[RowCta<BS>::G * BS];
-  __shared__ T q[BS], w[BS];
-  const int i = blockIdx.x, t = threadIdx.x;
-  RowPrefetch<T, BS> pf;
-  row_prefetch<T, BS>(L, i, pf);
-  T dr[BS];
-  if (t < BS) dinv_row<T, BS>(L.Dinv + (size_t)i * BS * BS, t, dr);
-  pdl_trigger();
-  pdl_wait();
-  const T* xin = L.x[xc];
-  cta_row_product<T, BS>(L, pf, xin, part, q);
-  const size_t idx = (size_t)i * BS + t;
-  if (t < BS) w[t] = L.b[idx] - q[t];
-  __syncthreads();
-  double dot = 0.0;
-  if (t < BS) {
-    const T dv = row_dinv<T, BS>(dr, w) * (T)(1.0 / L.cheb[0]);
-    const T xn = xin[idx] + dv;
-    L.r[rc][idx] = w[t];
-    L.d[dc][idx] = dv;
-    L.x[1 - xc][idx] = xn;
-    if (out) {
-      out[idx] = (double)xn;
-      if (dpart) dot = (double)xn * rdot[idx];
-    }
-  }
-  if (dpart && t < 32) {
-    dot = warp_sum(dot);
-    if (t == 0) dpart[i] = dot;
-  }
-}
-
 // Prolongation and post-smoothing step 0 in one launch, from A P (assembled with the
 // hierarchy): with s = b - A x the residual of the pre-smoothed iterate (left in the free
 // r buffer by the residual kernel) and x' = x + P x_c,
