@@ -114,9 +114,10 @@ def bsr_bytes(nnzb, n_c, w):
     return nnzb * (81 * w + 4) + n_c * (4 + 4 * 9 * w)
 
 
-# FP32 operations per term of the paired-FP32 assembly: the exact product (mul + 3 fma)
-# and the compensated sum (two-sum: 6, correction: 2)
-DF_TERM_OPS = 12
+# FP32 operations per term of the paired-FP32 assembly's offset accumulator: the head's
+# fma and the exact step difference (2), the step error and the two cross terms with the
+# tails (3 fma), the tail sum (1)
+DF_TERM_OPS = 6
 
 
 def upper_pairs(pt_idx, n_pts):

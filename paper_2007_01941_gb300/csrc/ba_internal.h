@@ -14,6 +14,20 @@
 namespace ba {
 
 constexpr int kNull = 16;        // near-nullspace dimension (Section 3.3)
+
+// arrays of dense blocks inverted by one launch (each: n blocks from `in`, written to
+// out64 and, if given, out32; `start` is the first block's index in the launch)
+struct BlockInvSeg {
+  const double* in;
+  double* out64;
+  float* out32;
+  int n, start;
+};
+constexpr int kMaxInvSegs = 16;
+struct BlockInvBatch {
+  BlockInvSeg s[kMaxInvSegs];
+  int nseg, total;
+};
 constexpr int kChebSlots = 24;   // per level: theta, delta, sigma_1, lambda_max, pad, alphas, betas
 constexpr int kScalars = 64;     // device scalar slots per problem
 
@@ -183,6 +197,7 @@ struct ba_problem {
   ba::DBuf Dc32;                // float copy of D_c
   ba::DBuf Scc;                 // double [n_c][81] diagonal blocks S_cc
   ba::DBuf Scc_inv, Scc_inv32;  // their inverses (point-block-Jacobi), FP64 and FP32
+  ba::DBuf cam_ubnd;            // float [n_c][9]: diag(sum_o F_o^T F_o), bounds of the assembly's column sums
 
   // multigrid hierarchy
   std::vector<ba::Level> levels;

@@ -108,4 +108,34 @@ __device__ __forceinline__ void dot2_fma(float& s, float& c, DF x, DF y) {
   dot2_fma(s, c, make_float2(x.h, x.l), make_float2(y.h, y.l));
 }
 
+// In-place Gauss-Jordan inverse of a BS x BS block without pivoting (the block is SPD),
+// held by BS lanes of a warp: lane base + j keeps column j, with row (k + i) mod BS of it
+// in a[i] during step k.  Step k takes the pivot and column k from lane base + k by
+// shuffles; the rows then rotate by one register, so the pivot row is always a[0] and
+// BS rotations restore the order.  The step loop stays rolled: unrolled over the pivots
+// the code outgrows the instruction cache, and each warp runs it once.  Every lane of the
+// warp must call it (full-mask shuffles); returns false if a pivot is not positive.
+template <int BS>
+__device__ __forceinline__ bool df_gauss_jordan_cols(DF (&a)[BS], int base, int j) {
+  bool ok = true;
+#pragma unroll 1
+  for (int k = 0; k < BS; ++k) {
+    const int src = base + k;
+    const DF p(__shfl_sync(kFull, a[0].h, src), __shfl_sync(kFull, a[0].l, src));
+    if (!(p.h > 0.f)) ok = false;
+    const DF ip = DF(1.f, 0.f) / p;
+    const bool piv = j == k;
+    // row k: a_kj / p; column k: -a_ik / p (the pivot lane, from a zero start); others
+    // a_ij - a_ik (a_kj / p)
+    const DF f = piv ? ip : a[0] * ip;
+#pragma unroll
+    for (int i = 1; i < BS; ++i) {
+      const DF ci(__shfl_sync(kFull, a[i].h, src), __shfl_sync(kFull, a[i].l, src));
+      a[i - 1] = (piv ? DF(0.f, 0.f) : a[i]) - ci * f;
+    }
+    a[BS - 1] = f;
+  }
+  return ok;
+}
+
 }  // namespace ba

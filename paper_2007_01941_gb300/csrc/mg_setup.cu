@@ -21,6 +21,7 @@ namespace ba {
 
 void block_inverse(ba_problem* P, const double* in, int n, int bs, double* out64, float* out32,
                    int flag_slot);
+void block_inverse_batch(ba_problem* P, const BlockInvBatch& B, int bs, int flag_slot);
 void level_matvec(ba_problem* P, int l, const void* x, void* y, bool ready);
 bool level_fp32(ba_problem* P);
 
@@ -616,7 +617,7 @@ k_aggregate_qr_df_cta(int n_agg, int bs, const int* __restrict__ mptr, const int
   __shared__ float2 gpart[kQrDfParts / 2][kNull];   // per-warp partial inner products
   __shared__ float2 g[kNull];
   __shared__ float2 red[kQrDfBS / 32];
-  __shared__ float2 scale_sm;
+  __shared__ float2 n0s[kNull];
   const int a = blockIdx.x;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int mb = mptr[a], me = mptr[a + 1];
@@ -633,19 +634,32 @@ k_aggregate_qr_df_cta(int n_agg, int bs, const int* __restrict__ mptr, const int
     const float2 v = A[r * kQrStride + j];
     return DF(v.x, v.y);
   };
-  auto col_norm = [&](int j) {
+  const int gi = t & 15, part = t >> 4;   // part = 2 warp + (lane >> 4)
+  // the rank test's reference: every column's norm before orthogonalisation, at once
+  {
     float s = 0.f, c = 0.f;
-    for (int r = t; r < rows; r += kQrDfBS) {
-      const DF v = at(r, j);
+    for (int r = part; r < rows; r += kQrDfParts) {
+      const DF v = at(r, gi);
       dot2_fma(s, c, v, v);
     }
-    return df_sqrt(qr_block_sum_df(DF(s, 0.f) + DF(c, 0.f), red));
-  };
-  const int gi = t & 15, part = t >> 4;   // part = 2 warp + (lane >> 4)
+    DF nv = DF(s, 0.f) + DF(c, 0.f);
+    nv += DF(__shfl_xor_sync(kFull, nv.h, 16), __shfl_xor_sync(kFull, nv.l, 16));
+    if (lane < 16) gpart[warp][lane] = make_float2(nv.h, nv.l);
+    __syncthreads();
+    if (t < kNull) {
+      DF tot(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < kQrDfParts / 2; ++w) tot += DF(gpart[w][t].x, gpart[w][t].y);
+      const DF n = df_sqrt(tot);
+      n0s[t] = make_float2(n.h, n.l);
+    }
+    __syncthreads();
+  }
   unsigned kept = 0;
   DF rc(0.f, 0.f);   // threads t < 16: R[t][j] of the current column
   for (int j = 0; j < kNull; ++j) {
-    const DF n0 = col_norm(j);
+    const DF n0(n0s[j].x, n0s[j].y);
+    DF nv = n0;
     rc = DF(0.f, 0.f);
     if (j > 0) {
       for (int pass = 0; pass < 2; ++pass) {
@@ -668,25 +682,23 @@ k_aggregate_qr_df_cta(int n_agg, int bs, const int* __restrict__ mptr, const int
           rc += tot;
         }
         __syncthreads();
-        // A[:, j] -= sum_{i<j} g_i A[:, i]
+        // A[:, j] -= sum_{i<j} g_i A[:, i]; the second pass also sums the new column's
+        // squares, and the reduction's first barrier orders the column's writes
+        float ns = 0.f, nc = 0.f;
         for (int r = t; r < rows; r += kQrDfBS) {
           float ps = 0.f, pc = 0.f;
 #pragma unroll 4
           for (int i = 0; i < j; ++i) dot2_fma(ps, pc, g[i], A[r * kQrStride + i]);
           const DF v = at(r, j) - (DF(ps, 0.f) + DF(pc, 0.f));
           A[r * kQrStride + j] = make_float2(v.h, v.l);
+          dot2_fma(ns, nc, v, v);
         }
-        __syncthreads();
+        if (pass == 0) __syncthreads();
+        else nv = df_sqrt(qr_block_sum_df(DF(ns, 0.f) + DF(nc, 0.f), red));
       }
     }
-    const DF nv = col_norm(j);
     const bool keep = n0.h > 0.f && nv.h > 1e-10f * n0.h;
-    if (t == 0) {
-      const DF sc = keep ? DF(1.f, 0.f) / nv : DF(0.f, 0.f);
-      scale_sm = make_float2(sc.h, sc.l);
-    }
-    __syncthreads();
-    const DF scale(scale_sm.x, scale_sm.y);
+    const DF scale = keep ? DF(1.f, 0.f) / nv : DF(0.f, 0.f);
     for (int r = t; r < rows; r += kQrDfBS) {
       const DF v = at(r, j) * scale;
       A[r * kQrStride + j] = make_float2(v.h, v.l);
@@ -1326,6 +1338,7 @@ __global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* Aa, double* Ab, 
 __device__ __forceinline__ bool gj_invert_df(float2 piv[kGJ][kGJ + 1], float2* gj_row, float2* gj_col, float2& gj_ip) {
   const int t = threadIdx.x, u = t / kGJ, v = t % kGJ;
   bool ok = true;
+#pragma unroll 1
   for (int k = 0; k < kGJ; ++k) {
     if (t == 0) {
       const DF pk(piv[k][k].x, piv[k][k].y);
@@ -1650,6 +1663,8 @@ void mg_setup(ba_problem* P) {
   L0.kept.ensure(sizeof(unsigned) * P->n_c + 64);
   BA_CUDA(cudaMemsetAsync(L0.kept.p, 0xff, sizeof(unsigned) * P->n_c, P->stream));
 
+  const bool batch_inv = P->opt.precision == BA_MIXED;
+  BlockInvBatch inv{};
   for (int l = 0; l < P->n_levels; ++l) {
     Level& L = P->levels[l];
     if (l > 0) {
@@ -1670,7 +1685,16 @@ void mg_setup(ba_problem* P) {
         k_extract_diag<double><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
                                                            L.vals64.as<double>(), L.Dblk.as<double>());
       launched(P);
-      block_inverse(P, L.Dblk.as<double>(), L.n, L.bs, L.Dinv64.as<double>(), L.Dinv32.as<float>(), F_NOT_SPD_JACOBI);
+      if (batch_inv && L.bs == 16 && inv.nseg < kMaxInvSegs) {
+        // inverted with the other coarse levels' blocks in one launch after the loop (only
+        // the batched Lanczos and the V-cycle read them)
+        inv.s[inv.nseg++] = BlockInvSeg{L.Dblk.as<double>(), L.Dinv64.as<double>(), L.Dinv32.as<float>(), L.n,
+                                        inv.total};
+        inv.total += L.n;
+      } else {
+        block_inverse(P, L.Dblk.as<double>(), L.n, L.bs, L.Dinv64.as<double>(), L.Dinv32.as<float>(),
+                      F_NOT_SPD_JACOBI);
+      }
     }
     if (fp32) {
       // FP32 diagonal blocks for the batched Lanczos
@@ -1745,6 +1769,7 @@ void mg_setup(ba_problem* P) {
     }
     launched(P);
   }
+  block_inverse_batch(P, inv, 16, F_NOT_SPD_JACOBI);
   lanczos_batched(P, P->l0_explicit ? 0 : 1, P->n_levels - 2);
   finish_lanczos(P);
   check_flags(P);

@@ -259,73 +259,65 @@ __global__ void __launch_bounds__(256) k_block_inverse_warp(const double* __rest
 // would take a warp's FP64 instruction over many cycles per SM sub-partition, while the
 // paired-FP32 steps run on the FP32 pipes.  The inverse is accurate to about 2^-48 times
 // the block's condition number, beyond what the FP32 smoother blocks it feeds can hold.
+// One block per group of BS lanes (32 / BS groups per warp), inverted in registers by
+// df_gauss_jordan_cols: no shared-memory round trip or warp barrier per pivot step.  One
+// launch covers a list of block arrays (every level's smoother blocks at once).
 template <int BS>
-__global__ void __launch_bounds__(256) k_block_inverse_warp_df(const double* __restrict__ in, int n,
-                                                               double* __restrict__ out64, float* __restrict__ out32,
-                                                               int* flags, int flag_slot) {
-  constexpr int PER = (BS * BS + 31) / 32;
-  __shared__ float2 sa[8][BS * BS];
+__global__ void __launch_bounds__(256) k_block_inverse_cols_df(BlockInvBatch B, int* flags, int flag_slot) {
+  constexpr int G = 32 / BS;
+  __shared__ float2 tile[8][G][BS][BS + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int blk = blockIdx.x * 8 + warp;
-  if (blk >= n) return;
-  float2* a = sa[warp];
-  const double* src = in + (size_t)blk * BS * BS;
-  for (int e = lane; e < BS * BS; e += 32) {
-    const DF v(src[e]);
-    a[e] = make_float2(v.h, v.l);
+  const int g = lane / BS, j = lane - (lane / BS) * BS;
+  const int base = g < G ? g * BS : 0;      // lanes past the last group shadow group 0
+  const int blk = (blockIdx.x * 8 + warp) * G + g;
+  const bool live = g < G && blk < B.total;
+  int si = 0;
+  for (int q = 1; q < B.nseg; ++q)
+    if (blk >= B.s[q].start) si = q;
+  const BlockInvSeg S = B.s[si];
+  const size_t o = ((size_t)(blk - S.start) * BS) * BS + j;
+  DF a[BS];
+#pragma unroll
+  for (int i = 0; i < BS; ++i) a[i] = live ? DF(S.in[o + (size_t)i * BS]) : DF(i == j ? 1.f : 0.f, 0.f);
+  const bool ok = df_gauss_jordan_cols<BS>(a, base, j);
+  if (g < G) {
+#pragma unroll
+    for (int i = 0; i < BS; ++i) tile[warp][g][i][j] = make_float2(a[i].h, a[i].l);
   }
   __syncwarp();
-  auto at = [&](int e) { return DF(a[e].x, a[e].y); };
-  bool ok = true;
-  for (int k = 0; k < BS; ++k) {
-    const DF p = at(k * BS + k);
-    if (!(p.h > 0.f)) ok = false;
-    const DF ip = DF(1.f, 0.f) / p;
-    DF nv[PER];
+  if (!live) return;
+  if (!ok && j == 0) flags[flag_slot] = 1;
 #pragma unroll
-    for (int t = 0; t < PER; ++t) {
-      const int e = lane + 32 * t;
-      if (e < BS * BS) {
-        const int i = e / BS, j = e - (e / BS) * BS;
-        DF v;
-        if (i == k && j == k) v = ip;
-        else if (i == k) v = at(k * BS + j) * ip;
-        else if (j == k) v = -(at(i * BS + k) * ip);
-        else v = at(e) - at(i * BS + k) * (at(k * BS + j) * ip);
-        nv[t] = v;
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int t = 0; t < PER; ++t) {
-      const int e = lane + 32 * t;
-      if (e < BS * BS) a[e] = make_float2(nv[t].h, nv[t].l);
-    }
-    __syncwarp();
-  }
-  if (!ok && lane == 0) flags[flag_slot] = 1;
-  for (int e = lane; e < BS * BS; e += 32) {
+  for (int i = 0; i < BS; ++i) {
     DF v(0.f, 0.f);
     if (ok) {
-      const DF sym = at(e) + at((e % BS) * BS + e / BS);   // symmetrise
+      const float2 t = tile[warp][g][j][i];
+      const DF sym = a[i] + DF(t.x, t.y);   // symmetrise
       v = DF(0.5f * sym.h, 0.5f * sym.l);
     }
-    out64[(size_t)blk * BS * BS + e] = to_double(v);
-    if (out32) out32[(size_t)blk * BS * BS + e] = v.h;
+    S.out64[o + (size_t)i * BS] = to_double(v);
+    if (S.out32) S.out32[o + (size_t)i * BS] = v.h;
   }
+}
+
+void block_inverse_batch(ba_problem* P, const BlockInvBatch& B, int bs, int flag_slot) {
+  if (B.total == 0) return;
+  if (bs == 9)
+    k_block_inverse_cols_df<9><<<cdiv(B.total, 8 * 3), 256, 0, P->stream>>>(B, P->flags.as<int>(), flag_slot);
+  else
+    k_block_inverse_cols_df<16><<<cdiv(B.total, 8 * 2), 256, 0, P->stream>>>(B, P->flags.as<int>(), flag_slot);
+  launched(P);
 }
 
 void block_inverse(ba_problem* P, const double* in, int n, int bs, double* out64, float* out32,
                    int flag_slot) {
   if (n == 0) return;
   if (P->opt.precision == BA_MIXED) {
-    if (bs == 9)
-      k_block_inverse_warp_df<9><<<cdiv(n, 8), 256, 0, P->stream>>>(in, n, out64, out32, P->flags.as<int>(),
-                                                                     flag_slot);
-    else
-      k_block_inverse_warp_df<16><<<cdiv(n, 8), 256, 0, P->stream>>>(in, n, out64, out32, P->flags.as<int>(),
-                                                                      flag_slot);
-    launched(P);
+    BlockInvBatch B{};
+    B.s[0] = BlockInvSeg{in, out64, out32, n, 0};
+    B.nseg = 1;
+    B.total = n;
+    block_inverse_batch(P, B, bs, flag_slot);
     return;
   }
   if (bs == 9)
@@ -550,13 +542,16 @@ constexpr int kSccBS = 128;
 __global__ void __launch_bounds__(kSccBS)
 k_scc_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const float* __restrict__ Ch,
          const float* __restrict__ Cl, size_t ldp, const int* __restrict__ cam_ptr, const int* __restrict__ cam_obs,
-         const int* __restrict__ obs_pt, const double* __restrict__ Dc, int n_c, double* __restrict__ Scc) {
+         const int* __restrict__ obs_pt, const double* __restrict__ Dc, int n_c, double* __restrict__ Scc,
+         float* __restrict__ ubnd) {
   __shared__ float2 part[45][kSccBS + 1];
   const int c = blockIdx.x;
   const int t = threadIdx.x;
-  float as[45], ac[45];
+  float as[45], ac[45], ub[9];
 #pragma unroll
   for (int k = 0; k < 45; ++k) as[k] = ac[k] = 0.f;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) ub[a] = 0.f;
   for (int i = cam_ptr[c] + t; i < cam_ptr[c + 1]; i += kSccBS) {
     const int o = cam_obs[i];
     const int ip = obs_pt[o];
@@ -578,6 +573,8 @@ k_scc_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const float
     const DF n00 = one - (y0[0] * e[0] + y0[1] * e[1] + y0[2] * e[2]);
     const DF n01 = -(y0[0] * e[3] + y0[1] * e[4] + y0[2] * e[5]);
     const DF n11 = one - (y1[0] * e[3] + y1[1] * e[4] + y1[2] * e[5]);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) ub[a] = fmaf(f[a].h, f[a].h, fmaf(f[9 + a].h, f[9 + a].h, ub[a]));
     int k = 0;
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
@@ -611,6 +608,17 @@ k_scc_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const float
     double* out = Scc + 81 * (size_t)c;
     out[9 * a + b] = d;
     out[9 * b + a] = d;
+  }
+  // diag(sum_o F_o^T F_o): since E_o C_p^-1 E_o^T <= I for every observation, it bounds
+  // the column sums sum_o |W_o(:, a)|^2 of the assembly's factors W_o = L_p^T E_o^T F_o
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 9; ++a) part[a][t].x = ub[a];
+  __syncthreads();
+  if (t < 9) {
+    float v = 0.f;
+    for (int j = 0; j < kSccBS; ++j) v += part[t][j].x;
+    ubnd[9 * (size_t)c + t] = v;
   }
 }
 
@@ -688,6 +696,7 @@ void schur_setup(ba_problem* P, double lambda) {
   P->Scc.ensure(sizeof(double) * 81 * n_c + 64);
   P->Scc_inv.ensure(sizeof(double) * 81 * n_c + 64);
   P->Scc_inv32.ensure(sizeof(float) * 81 * n_c + 64);
+  if (mixed) P->cam_ubnd.ensure(sizeof(float) * 9 * n_c + 64);
   clear_flags(P);
   const int damp_id = P->opt.damping == BA_DAMP_IDENTITY;
   if (n_p) {
@@ -723,7 +732,8 @@ void schur_setup(ba_problem* P, double lambda) {
   if (mixed)
     k_scc_df<<<n_c, kSccBS, 0, P->stream>>>(
         P->J32.as<float>(), P->J32lo.as<float>(), P->Cinv32.as<float>(), P->Cinv32lo.as<float>(), ldp,
-        P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->Dc.as<double>(), n_c, Scc);
+        P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->Dc.as<double>(), n_c, Scc,
+        P->cam_ubnd.as<float>());
   else
     k_scc<double><<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
         P->J64.as<double>(), P->J64.as<double>(), P->ld, P->Cinv64.as<double>(), ldp,
@@ -1227,22 +1237,50 @@ k_explicit_pairs(const T* __restrict__ W, int n_up, const int* __restrict__ up_b
 }
 
 // Paired-FP32 assembly (mixed precision): the same blocks from the DF rows of
-// k_schur_w_df, each batch's sums compensated (dot2_fma) and folded into DF
-// accumulators; writes each block as (hi, lo) float pairs (its FP64 value, for the PCG
+// k_schur_w_df; writes each block as (hi, lo) float pairs (its FP64 value, for the PCG
 // product) and its FP32 rounding (for the V-cycle and the Galerkin product).
+//
+// The sums use an offset accumulator.  By Cauchy-Schwarz every partial sum of entry
+// (a, b) of block (c, c'), and every product in it, is bounded by
+// M = sqrt(V_c(a) V_c'(b)) with V_c(a) = sum_o |W_o(:, a)|^2 <= diag(F^T F)_c(a, a).
+// With sigma a power of two >= 4 M the head s starts at sigma and takes each product
+// of the heads with one fma, s' = fl(x y + s); s and s' both stay in [sigma/2, 2 sigma],
+// so d = s' - s is exact (Sterbenz) and the heads' total is s - sigma exactly, while
+// fma(x, y, -d) recovers the step's rounding error to within 2^-48 sigma (the same
+// error-free-transformation idea as the two-sum, with the exponent fixed in advance as
+// in Rump, Ogita and Oishi's extraction of a sum's leading part).  The step errors and
+// the cross terms with the tails go into a plain FP32 sum that is folded into a DF
+// accumulator after every batch of pairs.  Six FP32 operations per term instead of
+// the twelve of the compensated dot product.
+__device__ __forceinline__ float assembly_offset(float m) {
+  const unsigned e = (__float_as_uint(m * 1.01f) >> 23) & 0xffu;   // 1.01 m < 2^(e - 126)
+  const unsigned es = min(e + 3u, 252u);
+  return __uint_as_float(es << 23);                                 // 2^(es - 127) > 4 m
+}
+
+__device__ __forceinline__ void offset_term(float& s, float& c, float2 x, float2 y) {
+  const float sn = __fmaf_rn(x.x, y.x, s);
+  const float d = __fsub_rn(sn, s);
+  float t = __fmaf_rn(x.x, y.x, -d);
+  t = __fmaf_rn(x.x, y.y, t);
+  t = __fmaf_rn(x.y, y.x, t);
+  c = __fadd_rn(c, t);
+  s = sn;
+}
+
 __global__ void __launch_bounds__(kExWarps * 32)
 k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restrict__ up_blk,
                     const int* __restrict__ mirror, const int* __restrict__ blk_row, const int* __restrict__ cols,
                     const int* __restrict__ pair_ptr, const int2* __restrict__ pairs, const double* __restrict__ Scc,
-                    float2* __restrict__ valsdf, float* __restrict__ vals32) {
+                    const float* __restrict__ ubnd, float2* __restrict__ valsdf, float* __restrict__ vals32) {
   constexpr int kB = 8;
   __shared__ __align__(16) float2 stage[kExWarps][2][2 * kB][kWld];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int w = blockIdx.x * kExWarps + wid;
   if (w >= n_up) return;
   const int e = up_blk[w];
-  const int c = blk_row[e];
-  if (cols[e] == c) {
+  const int c = blk_row[e], c2 = cols[e];
+  if (c2 == c) {
     for (int i = lane; i < 81; i += 32) {
       const DF v(Scc[(size_t)c * 81 + i]);
       valsdf[(size_t)e * 81 + i] = make_float2(v.h, v.l);
@@ -1251,6 +1289,14 @@ k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restri
     return;
   }
   const int la = lane < 27 ? lane / 3 : 0, lg = lane < 27 ? lane - 3 * (lane / 3) : 0;
+  // two heads per entry (terms 0, 2 and term 1 of each pair) for more independent chains
+  float sig[3], sh[3], th[3];
+  const float va = ubnd[9 * (size_t)c + la];
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    sig[u] = assembly_offset(sqrtf(va * ubnd[9 * (size_t)c2 + 3 * lg + u]));
+    sh[u] = th[u] = sig[u];
+  }
   DF acc[3] = {DF(0.f, 0.f), DF(0.f, 0.f), DF(0.f, 0.f)};
   const int q0 = pair_ptr[w], q1 = pair_ptr[w + 1];
   PairStage<float2, kB> st{stage[wid], W2, pairs, q1, lane};
@@ -1259,9 +1305,7 @@ k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restri
   for (int base = q0; base < q1; base += kB) {
     st.advance(base, buf);
     const int nb = min(kB, q1 - base);
-    // two sets of compensated sums (terms 0, 2 and term 1 of each pair) for more
-    // independent dependency chains
-    float sh[3] = {0.f, 0.f, 0.f}, sc[3] = {0.f, 0.f, 0.f}, th[3] = {0.f, 0.f, 0.f}, tc[3] = {0.f, 0.f, 0.f};
+    float sc[3] = {0.f, 0.f, 0.f}, tc[3] = {0.f, 0.f, 0.f};
 #pragma unroll 2
     for (int k = 0; k < nb; ++k) {
       const float2* wi = &stage[wid][buf][2 * k][la];
@@ -1269,21 +1313,22 @@ k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restri
       const float2 a0 = wi[0], a1 = wi[9], a2 = wi[18];
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
-        dot2_fma(sh[u], sc[u], a0, wj[u]);
-        dot2_fma(th[u], tc[u], a1, wj[9 + u]);
-        dot2_fma(sh[u], sc[u], a2, wj[18 + u]);
+        offset_term(sh[u], sc[u], a0, wj[u]);
+        offset_term(th[u], tc[u], a1, wj[9 + u]);
+        offset_term(sh[u], sc[u], a2, wj[18 + u]);
       }
     }
     __syncwarp();
     buf ^= 1;
 #pragma unroll
-    for (int u = 0; u < 3; ++u) acc[u] += (DF(sh[u], 0.f) + DF(sc[u], 0.f)) + (DF(th[u], 0.f) + DF(tc[u], 0.f));
+    for (int u = 0; u < 3; ++u) acc[u] += DF(sc[u], 0.f) + DF(tc[u], 0.f);
   }
   if (lane < 27) {
     const size_t o = (size_t)e * 81 + 9 * la + 3 * lg, m = (size_t)mirror[w] * 81 + la;
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
-      const DF v = -acc[u];
+      // the heads' totals s - sigma are exact
+      const DF v = -((DF(__fsub_rn(sh[u], sig[u]), 0.f) + DF(__fsub_rn(th[u], sig[u]), 0.f)) + acc[u]);
       const float2 d = make_float2(v.h, v.l);
       valsdf[o + u] = d;
       vals32[o + u] = v.h;
@@ -1400,8 +1445,8 @@ void explicit_schur(ba_problem* P, Level& L0, ExplicitMode mode) {
     KernelTimer kt(P, BA_KT_ASSEMBLY);
     k_explicit_pairs_df<<<gb, kExWarps * 32, 0, P->stream>>>(
         W2, L0.n_up, L0.up_blk.as<int>(), L0.mirror.as<int>(), L0.blk_row.as<int>(), L0.cols.as<int>(),
-        L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(), L0.valsdf.as<float2>(),
-        L0.vals32.as<float>());
+        L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(), P->cam_ubnd.as<float>(),
+        L0.valsdf.as<float2>(), L0.vals32.as<float>());
   } else if (mode == EX_FP32) {
     L0.vals32.ensure(sizeof(float) * 81 * (size_t)L0.nnzb + 64);
     P->scratch.ensure(sizeof(float) * kWld * (size_t)std::max(P->n_o, 1) + 64);
