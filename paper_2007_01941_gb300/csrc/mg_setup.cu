@@ -1335,31 +1335,27 @@ __global__ void __launch_bounds__(kGJBS) k_gauss_jordan(double* Aa, double* Ab, 
 // products as compensated sums, the pivot reciprocal as a DF division.  The FP64 unit of
 // this GPU takes a warp's FMA over many cycles per SM sub-partition; the pairs run on the
 // FP32 pipes and carry ~48 bits, well beyond what the FP32 coarse operator holds.
-__device__ __forceinline__ bool gj_invert_df(float2 piv[kGJ][kGJ + 1], float2* gj_row, float2* gj_col, float2& gj_ip) {
+// the pivot block's inverse in place, alternating between piv and tmp (kGJ is even, so the
+// result ends in piv): every thread forms the pivot's reciprocal and reads row and column
+// k of the current tile itself, so a step has one barrier
+__device__ __forceinline__ bool gj_invert_df(float2 piv[kGJ][kGJ + 1], float2 tmp[kGJ][kGJ + 1]) {
+  static_assert(kGJ % 2 == 0, "the ping-pong must end in the input tile");
   const int t = threadIdx.x, u = t / kGJ, v = t % kGJ;
   bool ok = true;
 #pragma unroll 1
   for (int k = 0; k < kGJ; ++k) {
-    if (t == 0) {
-      const DF pk(piv[k][k].x, piv[k][k].y);
-      if (!(pk.h > 0.f)) ok = false;
-      const DF ip = DF(1.f, 0.f) / pk;
-      gj_ip = make_float2(ip.h, ip.l);
-    }
-    __syncthreads();
-    const DF ip(gj_ip.x, gj_ip.y);
-    if (t < kGJ) {
-      const DF r = t == k ? ip : DF(piv[k][t].x, piv[k][t].y) * ip;
-      gj_row[t] = make_float2(r.h, r.l);
-      gj_col[t] = piv[t][k];
-    }
-    __syncthreads();
+    float2 (*src)[kGJ + 1] = (k & 1) ? tmp : piv;
+    float2 (*dst)[kGJ + 1] = (k & 1) ? piv : tmp;
+    const DF pk(src[k][k].x, src[k][k].y);
+    if (!(pk.h > 0.f)) ok = false;
+    const DF ip = DF(1.f, 0.f) / pk;
+    const DF rv = v == k ? ip : DF(src[k][v].x, src[k][v].y) * ip;
+    const DF cu(src[u][k].x, src[u][k].y);
     DF nv;
-    const DF cu(gj_col[u].x, gj_col[u].y), rv(gj_row[v].x, gj_row[v].y);
     if (u == k) nv = rv;
     else if (v == k) nv = -(cu * ip);
-    else nv = DF(piv[u][v].x, piv[u][v].y) - cu * rv;
-    piv[u][v] = make_float2(nv.h, nv.l);
+    else nv = DF(src[u][v].x, src[u][v].y) - cu * rv;
+    dst[u][v] = make_float2(nv.h, nv.l);
     __syncthreads();
   }
   return ok;
@@ -1375,16 +1371,14 @@ __device__ __forceinline__ DF gj_tile_dot(const float2 x[kGJ][kGJ + 1], const fl
 
 __global__ void __launch_bounds__(kGJBS) k_gauss_jordan_df(float2* Aa, float2* Ab, int Np, float2* pinv, int* flags) {
   cg::grid_group grid = cg::this_grid();
-  __shared__ float2 piv[kGJ][kGJ + 1], piv2[kGJ][kGJ + 1];
-  __shared__ float2 gj_row[kGJ], gj_col[kGJ];
-  __shared__ float2 gj_ip;
+  __shared__ float2 piv[kGJ][kGJ + 1], piv2[kGJ][kGJ + 1], gj_tmp[kGJ][kGJ + 1];
   __shared__ float2 sa[kGJ][kGJ + 1], sb[kGJ][kGJ + 1], st[kGJ][kGJ + 1];
   const int nb = Np / kGJ;
   const int t = threadIdx.x, u = t / kGJ, v = t % kGJ;
   if (blockIdx.x == 0) {
     piv[u][v] = Aa[(size_t)u * Np + v];
     __syncthreads();
-    const bool ok = gj_invert_df(piv, gj_row, gj_col, gj_ip);
+    const bool ok = gj_invert_df(piv, gj_tmp);
     if (t == 0 && !ok) flags[F_NOT_SPD_COARSE] = 1;
     pinv[t] = piv[u][v];
   }
@@ -1427,7 +1421,7 @@ __global__ void __launch_bounds__(kGJBS) k_gauss_jordan_df(float2* Aa, float2* A
       if (w == wn) {
         piv2[u][v] = make_float2(out.h, out.l);
         __syncthreads();
-        const bool ok = gj_invert_df(piv2, gj_row, gj_col, gj_ip);
+        const bool ok = gj_invert_df(piv2, gj_tmp);
         if (t == 0 && !ok) flags[F_NOT_SPD_COARSE] = 1;
         pinv[(size_t)((K + 1) & 1) * kGJBS + t] = piv2[u][v];
         __syncthreads();

@@ -1142,16 +1142,6 @@ k_schur_w_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const f
 
 constexpr int kExWarps = 4;
 
-// 16-byte asynchronous global -> shared copies (completion per thread at wait_group;
-// a __syncwarp after it publishes them to the rest of the warp)
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 // Double-buffered staging of a block's pair rows, shared by the kernels below: both W
 // rows of each of a batch's kB pairs (E bytes per entry) are copied into shared memory
 // with 16-byte asynchronous copies, so all of a batch's gathers are in flight at once
