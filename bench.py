@@ -433,14 +433,17 @@ def gpu_main(args):
                     "peak_source": f"{n_sm} SMs x 128 FP32 lanes x max SM clock (FP32 lane operations)"}
     elif dom == "outer_bsr":
         k = kernels["outer_bsr"]
-        roofline = {"kernel": "k_pcg_dir_spmv", "bound": "hbm", "achieved": k["achieved"], "peak": hbm,
-                    "unit": "GB/s", "frac": k["achieved"] / hbm, "traffic": None, "peak_source": peak_note}
+        roofline = {"kernel": "k_pcg_spmv_pq_df" if prec == _ffi.BA_MIXED else "k_pcg_spmv_pq", "bound": "hbm",
+                    "achieved": k["achieved"], "peak": hbm, "unit": "GB/s", "frac": k["achieved"] / hbm,
+                    "traffic": None, "peak_source": peak_note,
+                    "note": "blocks L2-resident across PCG iterations; latency-bound (one warp per block row)"}
     elif dom == "schur_fp64":
         k = kernels["schur_fp64"]
         roofline = {"kernel": "k_schur_matvec<double>", "bound": "alu", "achieved": k["achieved"],
                     "peak": fp64_peak_tflops, "unit": "TFLOP/s", "frac": k["achieved"] / fp64_peak_tflops,
                     "traffic": None, "peak_source": "measured FP64 FMA probe"}
-    traffic = _traffic_from_profiles(dom)
+    # the recorded counters are the paired-FP32 kernels' (mixed precision)
+    traffic = _traffic_from_profiles(dom) if prec == _ffi.BA_MIXED else None
     if roofline is not None and traffic is not None:
         roofline["traffic"] = traffic
 
