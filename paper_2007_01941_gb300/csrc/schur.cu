@@ -486,9 +486,14 @@ k_camera_setup_df(const float* __restrict__ Jh, const float* __restrict__ Jl,
   float hs[27], cs[27];
 #pragma unroll
   for (int k = 0; k < 27; ++k) hs[k] = cs[k] = 0.f;
-  for (int i = cam_ptr[c] + t; i < cam_ptr[c + 1]; i += kCamBS) {
-    const int o = cam_obs[i];
-    const int ip = obs_pt[o];
+  // the next observation's indices are fetched one iteration ahead
+  const int iend = cam_ptr[c + 1];
+  int i = cam_ptr[c] + t;
+  int o = i < iend ? cam_obs[i] : 0;
+  int ip = i < iend ? obs_pt[o] : 0;
+  for (; i < iend; i += kCamBS) {
+    const int on = i + kCamBS < iend ? __ldg(cam_obs + i + kCamBS) : 0;
+    const int ipn = i + kCamBS < iend ? __ldg(obs_pt + on) : 0;
     const DF f0(fres[2 * (size_t)o]), f1(fres[2 * (size_t)o + 1]);
     const float2 q0 = __ldg(wpdf + ip), q1 = __ldg(wpdf + ldp + ip), q2 = __ldg(wpdf + 2 * ldp + ip);
     const DF w0(q0.x, q0.y), w1(q1.x, q1.y), w2(q2.x, q2.y);
@@ -507,6 +512,8 @@ k_camera_setup_df(const float* __restrict__ Jh, const float* __restrict__ Jl,
       dot2_fma(hs[18 + k], cs[18 + k], a, nh0);
       dot2_fma(hs[18 + k], cs[18 + k], b, nh1);
     }
+    o = on;
+    ip = ipn;
   }
 #pragma unroll
   for (int k = 0; k < 27; ++k) {
@@ -552,9 +559,14 @@ k_scc_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const float
   for (int k = 0; k < 45; ++k) as[k] = ac[k] = 0.f;
 #pragma unroll
   for (int a = 0; a < 9; ++a) ub[a] = 0.f;
-  for (int i = cam_ptr[c] + t; i < cam_ptr[c + 1]; i += kSccBS) {
-    const int o = cam_obs[i];
-    const int ip = obs_pt[o];
+  // the next observation's indices are fetched one iteration ahead
+  const int iend = cam_ptr[c + 1];
+  int i = cam_ptr[c] + t;
+  int o = i < iend ? cam_obs[i] : 0;
+  int ip = i < iend ? obs_pt[o] : 0;
+  for (; i < iend; i += kSccBS) {
+    const int on = i + kSccBS < iend ? __ldg(cam_obs + i + kSccBS) : 0;
+    const int ipn = i + kSccBS < iend ? __ldg(obs_pt + on) : 0;
     DF rv[kRec], ci[6];
     rec_df_all(Jh, Jl, o, rv);
     const DF* f = rv;
@@ -586,6 +598,8 @@ k_scc_df(const float* __restrict__ Jh, const float* __restrict__ Jl, const float
         dot2_fma(as[k], ac[k], ga1, f[9 + b]);
       }
     }
+    o = on;
+    ip = ipn;
   }
 #pragma unroll
   for (int k = 0; k < 45; ++k) {
@@ -641,10 +655,26 @@ __global__ void k_back_substitute_df(const float* __restrict__ Jh, const float* 
     h1 = DF(vp[ldp + ip]);
     h2 = DF(vp[2 * ldp + ip]);
   }
-  for (int o = pt_ptr[ip]; o < pt_ptr[ip + 1]; ++o) {
-    const float2* x = dcs + 9 * (size_t)obs_cam[o];
-    DF rv[kRec];
+  // the next observation's record and camera index are loaded one iteration ahead
+  const int oe = pt_ptr[ip + 1];
+  int o = pt_ptr[ip];
+  DF rv[kRec];
+  int cam = 0;
+  if (o < oe) {
+    cam = obs_cam[o];
     rec_df_all(Jh, Jl, o, rv);
+  }
+  for (; o < oe; ++o) {
+    DF rn[kRec];
+    int camn = 0;
+    if (o + 1 < oe) {
+      camn = obs_cam[o + 1];
+      rec_df_all(Jh, Jl, o + 1, rn);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kRec; ++k) rn[k] = DF(0.f, 0.f);
+    }
+    const float2* x = dcs + 9 * (size_t)cam;
     DF u0(0.f, 0.f), u1(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -656,6 +686,9 @@ __global__ void k_back_substitute_df(const float* __restrict__ Jh, const float* 
     h0 -= rv[18] * u0 + rv[21] * u1;
     h1 -= rv[19] * u0 + rv[22] * u1;
     h2 -= rv[20] * u0 + rv[23] * u1;
+#pragma unroll
+    for (int k = 0; k < kRec; ++k) rv[k] = rn[k];
+    cam = camn;
   }
   const double H0 = to_double(h0), H1 = to_double(h1), H2 = to_double(h2);
   const double c00 = Cinv[ip], c01 = Cinv[ldp + ip], c02 = Cinv[2 * ldp + ip];
