@@ -101,27 +101,49 @@ __device__ __forceinline__ T lz_block_row(const T* __restrict__ B, int bs, int i
 
 // (A x)_i row u for the warp's row i: lane u + bs h takes blocks h, h + G, ... (G = 32 / bs)
 // and lane u < bs gets the row's sum
-template <typename T>
-__device__ __forceinline__ T lz_row_product(const LzLevel<T>& L, int i, const T* __restrict__ x, int lane) {
-  const int bs = L.bs, G = 32 / bs;
-  const int u = lane % bs, h = lane / bs;
-  T acc = T(0);
+// lane (h, u) adds row u of blocks h, h + G, ... (G = 32 / BS groups); two blocks per
+// iteration into independent sums, so that their loads are in flight together
+template <typename T, int BS>
+__device__ __forceinline__ T lz_row_product_bs(const LzLevel<T>& L, int i, const T* __restrict__ x, int lane) {
+  constexpr int G = 32 / BS;
+  const int u = lane % BS, h = lane / BS;
+  T acc0 = T(0), acc1 = T(0);
   if (h < G) {
     const int e1 = L.row_ptr[i + 1];
-    for (int e = L.row_ptr[i] + h; e < e1; e += G) {
-      const T* a = L.vals + (size_t)e * bs * bs + u * bs;
-      const T* xv = x + (size_t)L.cols[e] * bs;
-      for (int c = 0; c < bs; ++c) acc += a[c] * xv[c];
+    int e = L.row_ptr[i] + h;
+    for (; e + G < e1; e += 2 * G) {
+      const T* a = L.vals + (size_t)e * BS * BS + u * BS;
+      const T* b = L.vals + (size_t)(e + G) * BS * BS + u * BS;
+      const T* xa = x + (size_t)L.cols[e] * BS;
+      const T* xb = x + (size_t)L.cols[e + G] * BS;
+#pragma unroll
+      for (int c = 0; c < BS; ++c) {
+        acc0 += a[c] * xa[c];
+        acc1 += b[c] * xb[c];
+      }
+    }
+    if (e < e1) {
+      const T* a = L.vals + (size_t)e * BS * BS + u * BS;
+      const T* xa = x + (size_t)L.cols[e] * BS;
+#pragma unroll
+      for (int c = 0; c < BS; ++c) acc0 += a[c] * xa[c];
     }
   }
+  const T acc = acc0 + acc1;
   // groups h = 1 .. G-1 to group 0 (lane u)
   T tot = acc;
+#pragma unroll
   for (int g = 1; g < 32 / 9 + 1; ++g) {
-    const int src = lane + g * bs;
+    const int src = lane + g * BS;
     const T o = __shfl_sync(kFull, acc, src < 32 ? src : 31);
-    if (g < G && src < G * bs) tot += o;
+    if (g < G && src < G * BS) tot += o;
   }
   return tot;
+}
+
+template <typename T>
+__device__ __forceinline__ T lz_row_product(const LzLevel<T>& L, int i, const T* __restrict__ x, int lane) {
+  return L.bs == 9 ? lz_row_product_bs<T, 9>(L, i, x, lane) : lz_row_product_bs<T, 16>(L, i, x, lane);
 }
 
 // v = start vector (SplitMix64 of the level-local index, mapped to [-1, 1)); s[0] = v^T D v
@@ -233,6 +255,7 @@ static void run(ba_problem* P, int first, int last) {
     L.cheb.ensure(sizeof(double) * kChebSlots);
     const size_t n = (size_t)L.n * L.bs;
     LzLevel<T>& d = A.L[k];
+    BA_REQUIRE(L.bs == 9 || L.bs == 16, BA_ERR_STATE, "Lanczos: block size other than 9 or 16");
     d.n = L.n;
     d.bs = L.bs;
     d.cta0 = cta0;
