@@ -175,7 +175,7 @@ void ba_destroy(ba_problem* P) {
                       &P->cam_obs, &P->tile_pt, &P->tile_desc, &P->tile_perm, &P->lz_vec, &P->lz_red, &P->lz_cnt, &P->lz_ptr, &P->chunk_tile, &P->chunk_cam, &P->camx, &P->fres, &P->J64,
                       &P->J64, &P->J32, &P->J32lo, &P->cams_lin, &P->pts_lin, &P->obs_lin, &P->Dc, &P->Dp,
                       &P->Cinv64, &P->Cinv32, &P->Cinv32lo, &P->xsplit, &P->camdf, &P->wpdf, &P->Xdf, &P->gc, &P->gp, &P->wp, &P->rhs, &P->Dc32, &P->Scc, &P->Scc_inv,
-                      &P->Scc_inv32, &P->cam_ubnd, &P->x, &P->r, &P->z, &P->p, &P->q, &P->y32a, &P->y32b, &P->delta_c,
+                      &P->Scc_inv32, &P->cam_ubnd, &P->ptsdf, &P->x, &P->r, &P->z, &P->p, &P->q, &P->y32a, &P->y32b, &P->delta_c,
                       &P->delta_p, &P->scal, &P->partial, &P->partial2, &P->rzpart, &P->counter, &P->flags, &P->scratch, &P->scratch2};
   for (ba::DBuf* b : bufs) b->release();
   for (ba::Level& L : P->levels) {

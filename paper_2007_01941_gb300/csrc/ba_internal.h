@@ -197,6 +197,7 @@ struct ba_problem {
   ba::DBuf Dc32;                // float copy of D_c
   ba::DBuf Scc;                 // double [n_c][81] diagonal blocks S_cc
   ba::DBuf Scc_inv, Scc_inv32;  // their inverses (point-block-Jacobi), FP64 and FP32
+  ba::DBuf ptsdf;               // float2 [n_p][3]: the points of the current linearisation as float pairs
   ba::DBuf cam_ubnd;            // float [n_c][9]: diag(sum_o F_o^T F_o), bounds of the assembly's column sums
 
   // multigrid hierarchy

@@ -253,18 +253,30 @@ k_linearize(const double* __restrict__ cams, const double* __restrict__ pts,
   grid_sum_store<kLinBS>(acc, partial, counter, cost_out);
 }
 
+// points as float pairs, once per point (the observations of a point share the split)
+__global__ void k_split_points(size_t n, const double* __restrict__ pts, float2* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const DF v(pts[i]);
+    out[i] = make_float2(v.h, v.l);
+  }
+}
+
 // The mixed-precision linearisation: the camera model of project_obs_t in paired FP32
-// (DF), from the per-camera split of camdf and the points and observations split on
-// load.  Writes the residuals and, directly from the pairs, the FP32 records (hi) and
-// their remainders (lo); the FP64 records (hi + lo) only when J64 is given.
+// (DF), from the per-camera split of camdf, the point split of ptsdf and the observations
+// split on load.  Writes the residuals and, directly from the pairs, the FP32 records (hi)
+// and their remainders (lo); the FP64 records (hi + lo) only when J64 is given.  With the
+// squared loss the cost terms are summed in DF too, so that an observation takes only the
+// FP64 additions that form its residual.
 template <bool JAC>
 __global__ void __launch_bounds__(kLinBS)
-k_linearize_df(const double* __restrict__ pts, const double* __restrict__ obs, const float2* __restrict__ camdf,
+k_linearize_df(const float2* __restrict__ ptsdf, const double* __restrict__ obs, const float2* __restrict__ camdf,
                const int* __restrict__ obs_cam, const int* __restrict__ obs_ptu, const int* __restrict__ obs_user,
                int n_o, double* __restrict__ fres, double* __restrict__ J64, float* __restrict__ J32,
                float* __restrict__ J32lo, double* partial, unsigned* counter, double* cost_out, int* flags,
                double ha) {
   double acc = 0.0;
+  DF accdf(0.f, 0.f);
   for (int o = blockIdx.x * kLinBS + threadIdx.x; o < n_o; o += gridDim.x * kLinBS) {
     const int c = obs_cam[o];
     const int pu = obs_ptu[o];
@@ -282,17 +294,27 @@ k_linearize_df(const double* __restrict__ pts, const double* __restrict__ obs, c
       const float2 v = __ldg(cd + 19 + i);
       cam[i] = DF(v.x, v.y);
     }
-    const DF X[3] = {DF(pts[3 * pu]), DF(pts[3 * pu + 1]), DF(pts[3 * pu + 2])};
+    const float2 x0 = __ldg(ptsdf + 3 * (size_t)pu), x1 = __ldg(ptsdf + 3 * (size_t)pu + 1),
+                 x2 = __ldg(ptsdf + 3 * (size_t)pu + 2);
+    const DF X[3] = {DF(x0.x, x0.y), DF(x1.x, x1.y), DF(x2.x, x2.y)};
     const DF ob[2] = {DF(obs[2 * ou]), DF(obs[2 * ou + 1])};
     CamObsT<DF> v;
     project_obs_t<JAC, DF>(cam, cx, small, X, ob, v);
     double r0 = to_double(v.res[0]), r1 = to_double(v.res[1]);
-    double half_rho;
-    const double w = robust_weight(r0 * r0 + r1 * r1, ha, half_rho);
-    acc += half_rho;
-    if (w != 1.0) {
-      r0 *= w;
-      r1 *= w;
+    double w = 1.0;
+    bool scaled = false;
+    if (ha > 0.0) {
+      double half_rho;
+      w = robust_weight(r0 * r0 + r1 * r1, ha, half_rho);
+      acc += half_rho;
+      scaled = w != 1.0;
+      if (scaled) {
+        r0 *= w;
+        r1 *= w;
+      }
+    } else {
+      const DF s2 = v.res[0] * v.res[0] + v.res[1] * v.res[1];
+      accdf += DF(0.5f * s2.h, 0.5f * s2.l);
     }
     if (fres) reinterpret_cast<double2*>(fres)[o] = make_double2(r0, r1);
     if (JAC) {
@@ -302,7 +324,7 @@ k_linearize_df(const double* __restrict__ pts, const double* __restrict__ obs, c
       for (int k = 0; k < 18; ++k) rec[k] = v.F[k];
 #pragma unroll
       for (int k = 0; k < 6; ++k) rec[18 + k] = v.E[k];
-      if (w != 1.0) {
+      if (scaled) {
         const DF wd(w);
 #pragma unroll
         for (int k = 0; k < kRec; ++k) rec[k] = rec[k] * wd;
@@ -324,6 +346,7 @@ k_linearize_df(const double* __restrict__ pts, const double* __restrict__ obs, c
       if (!finite) flags[F_NONFINITE] = 1;
     }
   }
+  acc += to_double(accdf);
   grid_sum_store<kLinBS>(acc, partial, counter, cost_out);
 }
 
@@ -335,6 +358,15 @@ static void camera_rotation(ba_problem* P, const double* cams, double* camx, flo
 // the kernels' loss argument: the Huber scale a, or 0 for the squared loss
 static double huber_scale(const ba_problem* P) {
   return P->opt.loss == BA_LOSS_HUBER ? P->opt.loss_scale : 0.0;
+}
+
+static void split_points(ba_problem* P, const double* pts) {
+  const size_t n = 3 * (size_t)P->n_p;
+  P->ptsdf.ensure(sizeof(float2) * std::max<size_t>(n, 1) + 64);
+  if (n) {
+    k_split_points<<<cdiv((long long)n, 256), 256, 0, P->stream>>>(n, pts, P->ptsdf.as<float2>());
+    launched(P);
+  }
 }
 
 static int lin_grid(ba_problem* P) {
@@ -369,9 +401,10 @@ void linearize(ba_problem* P, const double* cams, const double* pts, const doubl
   int g = lin_grid(P);
   double* cost = P->scal.as<double>() + S_COST;
   KernelTimer kt(P, BA_KT_LINEARIZE);
+  if (mixed) split_points(P, pts);
   if (mixed)
     k_linearize_df<true><<<g, kLinBS, 0, P->stream>>>(
-        pts, obs, P->camdf.as<float2>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(), P->obs_user.as<int>(), P->n_o,
+        P->ptsdf.as<float2>(), obs, P->camdf.as<float2>(), P->obs_cam.as<int>(), P->obs_ptu.as<int>(), P->obs_user.as<int>(), P->n_o,
         P->fres.as<double>(), nullptr, P->J32.as<float>(), P->J32lo.as<float>(), P->partial.as<double>(),
         P->counter.as<unsigned>(), cost, P->flags.as<int>(), huber_scale(P));
   else
@@ -410,9 +443,10 @@ double cost_at(ba_problem* P, const double* cams, const double* pts, const doubl
   float2* camdf = mixed ? reinterpret_cast<float2*>(P->scratch2.as<char>() + rot_bytes) : nullptr;
   camera_rotation(P, cams, P->scratch2.as<double>(), camdf);
   int g = lin_grid(P);
+  if (mixed) split_points(P, pts);
   if (mixed)
     k_linearize_df<false><<<g, kLinBS, 0, P->stream>>>(
-        pts, obs, camdf, P->obs_cam.as<int>(), P->obs_ptu.as<int>(), P->obs_user.as<int>(), P->n_o, nullptr, nullptr,
+        P->ptsdf.as<float2>(), obs, camdf, P->obs_cam.as<int>(), P->obs_ptu.as<int>(), P->obs_user.as<int>(), P->n_o, nullptr, nullptr,
         nullptr, nullptr, P->partial.as<double>(), P->counter.as<unsigned>(), P->scal.as<double>() + S_COST_NEW,
         P->flags.as<int>(), huber_scale(P));
   else
