@@ -220,6 +220,12 @@ def test_hierarchy_matches_oracle(gpu, prec):
             ref = np.linalg.inv(L.dense)
             assert rel(Ainv.reshape(Np, Np)[:N, :N], ref) < (1e-7 if prec == "fp64" else 5e-3)
             continue
+        # smoother blocks: the inverses of this level's own diagonal blocks (batched over
+        # the coarse levels in mixed precision)
+        b = L.b
+        Dinv = _np(prob.get_array(F_.BA_ARR_JACOBI_INV, l)).reshape(L.n, b, b)
+        Dref = np.linalg.inv(np.stack([Ad[b * i:b * i + b, b * i:b * i + b] for i in range(L.n)]))
+        assert rel(Dinv, Dref) < (1e-6 if prec == "mixed" else 1e-9), l
         sptr = _np(prob.get_array(F_.BA_ARR_STRENGTH_PTR, l))
         sidx = _np(prob.get_array(F_.BA_ARR_STRENGTH_IDX, l))
         for i in range(L.n):
