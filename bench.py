@@ -374,7 +374,7 @@ def gpu_main(args):
     hbm = peaks.get("hbm_gbs")
     peak_note = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
-    fp64_peak_tflops = 1.205   # FMA-chain probe on this machine's GB300
+    fp64_peak_tflops = 1.205   # FP64 FMA rate measured on a GB300 with independent FMA chains
     n_o, n_p, n_c = s.n_obs, s.n_pts, s.n_cams
     nnzb = info["level_nnzb"][0]
     n_pairs = upper_pairs(s.pt_idx, n_p)
