@@ -28,6 +28,7 @@ WORKLOADS = {
     "street_chain": dict(fn="street_chain", kw={}, rtol=1e-6),
     "city_grid": dict(fn="city_grid", kw={}, rtol=1e-6),
     "ring": dict(fn="ring", kw={}, rtol=1e-8),
+    "loop_closure": dict(fn="loop_closure", kw={}, rtol=1e-6),
 }
 
 
