@@ -429,21 +429,19 @@ __global__ void k_nullspace0(const double* __restrict__ cams, int n_c, double* _
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) K2[3 * i + j] = rv[i] * rv[j] - (i == j ? th2 : 0.0);
   double R[9], Jli[9];
+  // one sine and cosine serve R and J_l^-1 (the FP64 unit bounds this kernel)
+  const double th = sqrt(th2);
+  double s = 0.0, co = 1.0;
+  if (th2 >= 1e-16) sincos(th, &s, &co);
   if (th2 < 1e-16) {
     for (int i = 0; i < 9; ++i) R[i] = ((i % 4 == 0) ? 1.0 : 0.0) + Km[i];
   } else {
-    const double th = sqrt(th2);
-    double s, co;
-    sincos(th, &s, &co);
     for (int i = 0; i < 9; ++i) R[i] = ((i % 4 == 0) ? 1.0 : 0.0) + s / th * Km[i] + (1.0 - co) / th2 * K2[i];
   }
   double coef;
-  if (sqrt(th2) < 1e-6) {
+  if (th < 1e-6) {
     coef = 1.0 / 12.0;
   } else {
-    const double th = sqrt(th2);
-    double s, co;
-    sincos(th, &s, &co);
     coef = 1.0 / th2 - (1.0 + co) / (2.0 * th * s);
   }
   for (int i = 0; i < 9; ++i) Jli[i] = ((i % 4 == 0) ? 1.0 : 0.0) - 0.5 * Km[i] + coef * K2[i];
@@ -1652,7 +1650,8 @@ void mg_setup(ba_problem* P) {
   BA_CUDA(cudaMemcpyAsync(L0.Dinv64.p, P->Scc_inv.p, sizeof(double) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
   BA_CUDA(cudaMemcpyAsync(L0.Dinv32.p, P->Scc_inv32.p, sizeof(float) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
   L0.K.ensure(sizeof(double) * 9 * kNull * (size_t)P->n_c + 64);
-  k_nullspace0<<<cdiv(P->n_c, 128), 128, 0, P->stream>>>(P->cams_lin.as<double>(), P->n_c, L0.K.as<double>());
+  // one warp per CTA: the cameras' FP64 work spread over as many SMs as possible
+  k_nullspace0<<<cdiv(P->n_c, 32), 32, 0, P->stream>>>(P->cams_lin.as<double>(), P->n_c, L0.K.as<double>());
   launched(P);
   L0.kept.ensure(sizeof(unsigned) * P->n_c + 64);
   BA_CUDA(cudaMemsetAsync(L0.kept.p, 0xff, sizeof(unsigned) * P->n_c, P->stream));
