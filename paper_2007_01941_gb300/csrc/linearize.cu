@@ -351,7 +351,8 @@ k_linearize_df(const float2* __restrict__ ptsdf, const double* __restrict__ obs,
 }
 
 static void camera_rotation(ba_problem* P, const double* cams, double* camx, float2* camdf) {
-  k_camera_rotation<<<cdiv(P->n_c, 128), 128, 0, P->stream>>>(cams, P->n_c, camx, camdf);
+  // one warp per CTA: the cameras' FP64 work spread over as many SMs as possible
+  k_camera_rotation<<<cdiv(P->n_c, 32), 32, 0, P->stream>>>(cams, P->n_c, camx, camdf);
   launched(P);
 }
 
