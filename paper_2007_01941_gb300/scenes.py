@@ -328,6 +328,19 @@ def subscene(scene: Scene, n_cams: int, n_pts: int, seed: int = 0) -> Scene:
                  pts_true=scene.pts_true[good].copy(), lam=scene.lam, rtol=scene.rtol)
 
 
+def rotated_start(scene: Scene, sigma: float, seed: int = 0) -> Scene:
+    """The same scene with N(0, sigma^2) added to every angle-axis component of the
+    starting cameras: a start far from the optimum whose Gauss-Newton steps overshoot
+    (points cross the cameras' image planes), so that LM steps get rejected."""
+    rng = np.random.default_rng(seed)
+    cams = scene.cams.copy()
+    cams[:, :3] += sigma * rng.normal(size=(scene.n_cams, 3))
+    return Scene(name=scene.name + "_rot", n_cams=scene.n_cams, n_pts=scene.n_pts, n_obs=scene.n_obs,
+                 cam_idx=scene.cam_idx, pt_idx=scene.pt_idx, obs=scene.obs, cams=cams,
+                 pts=scene.pts.copy(), cams_true=scene.cams_true, pts_true=scene.pts_true,
+                 lam=scene.lam, rtol=scene.rtol)
+
+
 def tiny(seed=0, n_cams=6, n_pts=40, kmin=2, kmax=4) -> Scene:
     """A few-camera ring for brute-force and dense checks."""
     return ring(seed=seed, n_cams=n_cams, n_pts=n_pts, kmin=kmin, kmax=kmax)

@@ -102,16 +102,55 @@ def test_lm_step_decreases_cost_and_updates_lambda():
     assert np.isclose(camera.cost(c1, p1, s.cam_idx, s.pt_idx, s.obs), cost1)
 
 
+def test_lm_step_near_the_optimum_has_unit_gain_ratio():
+    """Close to the optimum the Gauss-Newton model is exact to second order, so the gain
+    ratio (actual over predicted decrease, each computed its own way: the cost from the
+    camera model, the prediction from g and D) tends to 1 and lambda falls by the factor
+    1/3 that the update rule gives at rho = 1."""
+    s = scene("ring", seed=0, n_cams=16, n_pts=800)
+    x, p, lam, nu = s.cams, s.pts, 1e-4, 2.0
+    for _ in range(2):   # two steps bring the start within the quadratic region
+        x, p, lam, nu, acc, *_ = lm.lm_step(x, p, s.cam_idx, s.pt_idx, s.obs, lam, nu, rtol=1e-12,
+                                            coarse_max_nodes=4)
+        assert acc
+    c1, p1, lam1, nu1, acc, cost0, cost1, info = lm.lm_step(x, p, s.cam_idx, s.pt_idx, s.obs, lam, nu,
+                                                            rtol=1e-12, coarse_max_nodes=4)
+    assert acc and cost1 < cost0 and nu1 == 2.0
+    assert abs(info["rho"] - 1.0) < 1e-2
+    assert abs(lam1 / lam - 1.0 / 3.0) < 1e-6
+
+
+def rejecting_scene():
+    # a 16-camera ring whose starting rotations are off by N(0, 0.8^2) per component: the
+    # first step is accepted, the next three overshoot (points cross the image planes)
+    from paper_2007_01941_gb300 import scenes
+    return scenes.rotated_start(scene("ring", seed=0, n_cams=16, n_pts=800), 0.8, seed=11)
+
+
 def test_lm_step_rejects_and_raises_lambda():
-    s = scene("ring", seed=0)
-    # a huge damping step that overshoots is impossible; instead force rejection by a tiny
-    # damping on a badly perturbed start
-    cams = s.cams.copy()
-    cams[:, 3:6] += 3.0
-    out = lm.lm_step(cams, s.pts, s.cam_idx, s.pt_idx, s.obs, 1e-12, rtol=1e-10, coarse_max_nodes=4)
-    c1, p1, lam1, nu1, acc = out[:5]
-    if not acc:
-        assert lam1 == 1e-12 * 2.0 and nu1 == 4.0 and np.all(c1 == cams)
+    """The reject branch: when the cost at x + delta exceeds the cost at x, the step is
+    refused, x is unchanged, lambda is multiplied by nu and nu doubles (each rejection in
+    a row doubles the factor)."""
+    s = rejecting_scene()
+    x, p, lam, nu = s.cams, s.pts, 1e-4, 2.0
+    x, p, lam, nu, acc, *_ = lm.lm_step(x, p, s.cam_idx, s.pt_idx, s.obs, lam, nu, rtol=1e-10,
+                                        coarse_max_nodes=4)
+    assert acc
+    for k in range(2):
+        sch = schur.linearize(x, p, s.cam_idx, s.pt_idx, s.obs, lam)
+        dc, dp, _, _ = lm.solve_step(sch, x, "mg", rtol=1e-10, coarse_max_nodes=4)
+        cost_x = camera.cost(x, p, s.cam_idx, s.pt_idx, s.obs)
+        cost_trial = camera.cost(x + dc.reshape(-1, 9), p + dp.reshape(-1, 3), s.cam_idx, s.pt_idx, s.obs)
+        assert cost_trial > cost_x          # the step overshoots: the cost rises
+        x1, p1, lam1, nu1, acc, cost0, cost1, info = lm.lm_step(x, p, s.cam_idx, s.pt_idx, s.obs, lam, nu,
+                                                                rtol=1e-10, coarse_max_nodes=4)
+        assert not acc
+        assert info["rho"] < 0
+        assert x1 is x and p1 is p
+        assert lam1 == lam * nu and nu1 == 2.0 * nu
+        assert cost0 == cost1 == cost_x
+        lam, nu = lam1, nu1
+    assert nu == 8.0
 
 
 def _fd_loss(s, vbar, cams, pts, obs, lam):
