@@ -55,8 +55,10 @@ typedef enum { BA_DAMP_MARQUARDT = 0, BA_DAMP_IDENTITY = 1 } ba_damping;
  * implicitly from the Jacobian blocks against assembling it): IMPLICIT streams the
  * per-observation blocks on every product; EXPLICIT uses the 9x9 block-sparse S that
  * ba_mg_setup assembles anyway for the Galerkin product; AUTO picks EXPLICIT when its
- * blocks take fewer bytes than one implicit pass over the Jacobian.  The outer PCG
- * product is implicit in every case. */
+ * blocks take fewer bytes than one implicit pass over the Jacobian.  The level 0 is the
+ * PCG's own operator S, so the same choice decides the outer PCG product: with the
+ * assembled level 0 the PCG multiplies by its blocks (FP64 blocks in BA_FP64, float-pair
+ * blocks in BA_MIXED), otherwise by the implicit product. */
 typedef enum { BA_OP_IMPLICIT = 0, BA_OP_EXPLICIT = 1, BA_OP_AUTO = 2 } ba_operator;
 /* Arithmetic of the outer PCG product S p in BA_MIXED (BA_FP64 always uses FP64):
  * FP64 instructions, or FP64-valued operands carried as pairs of floats (hi + lo, about
@@ -89,7 +91,7 @@ typedef struct {
   int pre_smooth;       /* Chebyshev steps before the coarse correction (2, Section 3.4) */
   int post_smooth;      /* Chebyshev steps after (2) */
   int lanczos_steps;    /* operator applications for lambda_max (5, Section 3.4) */
-  int coarse_max_nodes; /* stop coarsening at <= this many nodes (64) */
+  int coarse_max_nodes; /* stop coarsening at <= this many nodes (32) */
   int max_levels;       /* hierarchy depth cap (10) */
   double cheb_lo;       /* Chebyshev interval [cheb_lo, cheb_hi] * lambda_max (0.3, 1.1) */
   double cheb_hi;
@@ -279,7 +281,12 @@ ba_status ba_get_array(ba_problem* prob, int which, int level, void* dst, size_t
  * Scratch lives in a fixed array inside the library that every GPU loading the library
  * keeps until the process exits.  The first call on a device looks up that array's
  * device address (with the device current), so make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents; the call
+ * capture.  With CUDA's default lazy module loading, that first call is also when the
+ * driver loads the array onto the device: it allocates the array's memory then, may
+ * synchronise, and can fail there for lack of memory.  So make the first call at
+ * start-up, before the memory budget is in force.  The looked-up address belongs to the
+ * device's primary context and does not survive cudaDeviceReset: do not call this entry
+ * point again in a process after resetting the device.  All calls share the array and it keeps the last call's contents; the call
  * clears the parts that must start at zero.  Calls whose GPU work overlaps (on different
  * streams without ordering) race on the array and give wrong results.
  * Returns BA_ERR_LIMIT if n_cams > BA_NOALLOC_MAX_CAMS, BA_ERR_INVALID_ARG for bad

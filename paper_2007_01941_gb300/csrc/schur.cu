@@ -1021,14 +1021,13 @@ static void launch_matvec(ba_problem* P, const T* F, const T* E, const T* Cinv, 
   if (P->n_chunks == 0) return;
   constexpr bool window = sizeof(T) == 4;
   const size_t smem = window ? sizeof(T) * 9 * (size_t)P->k3_window : 0;
-  static bool attr_set = false;
-  if (window && !attr_set) {
-    BA_CUDA(cudaFuncSetAttribute(k_schur_matvec<T, window>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(T) * 9 * 1024)));
-    attr_set = true;
-  }
   int& grid = P->k3_grid[sizeof(T) == 8];
   if (grid == 0) {
+    // first product of this problem: the shared-memory limit is an attribute of the
+    // kernel on the problem's device (a problem lives on one device)
+    if (window)
+      BA_CUDA(cudaFuncSetAttribute(k_schur_matvec<T, window>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(T) * 9 * 1024)));
     // one wave: every SM holds as many CTAs as registers and shared memory allow
     int per_sm = 0;
     BA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_schur_matvec<T, window>,
