@@ -56,7 +56,8 @@ k_noalloc_cost(int n_c, int n_p, int n_o, const double* __restrict__ cams, const
                const int32_t* __restrict__ pt_idx, const double* __restrict__ rot, double* partial,
                unsigned* counter, unsigned* bad, double* out) {
   double acc = 0.0;
-  for (int o = blockIdx.x * kBS + threadIdx.x; o < n_o; o += gridDim.x * kBS) {
+  // 64-bit index: n_o may come within one grid stride of INT_MAX
+  for (long long o = (long long)blockIdx.x * kBS + threadIdx.x; o < n_o; o += (long long)gridDim.x * kBS) {
     const int c = cam_idx[o], p = pt_idx[o];
     if (c < 0 || c >= n_c || p < 0 || p >= n_p) {
       atomicExch(bad, 1u);
@@ -106,7 +107,11 @@ k_noalloc_cost(int n_c, int n_p, int n_o, const double* __restrict__ cams, const
 }
 
 // device address of the scratch array, looked up once per device (with that device
-// current); later calls reuse it
+// current); later calls reuse it.  The address belongs to the device's primary context:
+// it does not survive cudaDeviceReset (or any other destruction of that context), after
+// which this entry point must not be called again in the process.  Under lazy module
+// loading the lookup is also what makes the driver load this file's module on the
+// device, which is when the array itself is allocated.
 std::mutex g_mu;
 double* g_addr[64] = {nullptr};
 

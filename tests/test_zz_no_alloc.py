@@ -20,19 +20,35 @@ def _call(lib, s, cams, pts, obs, ci, pi, out, stream):
                                ci.data_ptr(), pi.data_ptr(), out.data_ptr(), ctypes.c_void_p(stream))
 
 
+def _small_angle_ring():
+    # camera 0 exactly unrotated and camera 1 with theta^2 = 3e-18: both take the
+    # first-order rotation branch (theta^2 < 1e-16) in both entry points
+    import dataclasses
+    s = scene("ring", seed=0)
+    cams = s.cams.copy()
+    cams[0, :3] = 0.0
+    cams[1, :3] = 1e-9
+    return dataclasses.replace(s, cams=cams)
+
+
 def test_noalloc_cost_matches_linearize_twice_in_a_row(gpu):
     from paper_2007_01941_gb300 import _ffi, api
     lib = _ffi.load()
-    for s in (scene("street_chain", n_cams=300, n_pts=30000), scene("ring", seed=0)):
+    for s in (scene("street_chain", n_cams=300, n_pts=30000), scene("ring", seed=0), _small_angle_ring()):
         prob, cams, pts, obs = api.from_scene(s, device=gpu)
         ref = prob.linearize(cams, pts, obs)                      # existing entry point
         ci = torch.as_tensor(s.cam_idx, device=gpu)
         pi = torch.as_tensor(s.pt_idx, device=gpu)
         stream = torch.cuda.current_stream(gpu).cuda_stream
-        for _ in range(2):                                        # two calls in a row
+        for k in range(2):                                        # two calls in a row
             out = torch.full((1,), -1.0, dtype=torch.float64, device=gpu)
+            torch.cuda.synchronize(gpu)
+            free0 = torch.cuda.mem_get_info(gpu)[0]
             assert _call(lib, s, cams, pts, obs, ci, pi, out, stream) == _ffi.BA_OK
             torch.cuda.synchronize(gpu)
+            if k == 1:
+                # after the first call has loaded the array, a call takes no device memory
+                assert torch.cuda.mem_get_info(gpu)[0] == free0
             got = float(out.item())
             assert abs(got - ref) <= 1e-12 * ref, (got, ref)
         prob.close()
