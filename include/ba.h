@@ -86,7 +86,13 @@ typedef struct {
   int precision;        /* ba_precision: BA_FP64 all-double; BA_MIXED FP32 V-cycle */
   int preconditioner;   /* ba_precond (BA_PRECOND_MG) */
   int damping;          /* ba_damping: D = lambda*max(diag(J^T J),1e-6) or lambda*I */
-  int recompute_jacobian; /* ba_adjoint rebuilds F, E from cams/pts (always on); reserved */
+  int recompute_jacobian; /* 1: the FP64 implicit Schur product (the PCG product and the V-cycle's
+                           level 0 when implicit; BA_OUTER_FP64 in BA_MIXED) rebuilds F and E of
+                           each observation from the cameras and points instead of reading stored
+                           blocks, trading 192 streamed bytes per observation for about 300 FP64
+                           operations, and the FP64 blocks are then never formed in BA_MIXED.
+                           The paired-FP32 and FP32 products read stored blocks either way (0);
+                           ba_adjoint always rebuilds its blocks */
   int max_agg;          /* Algorithm 2 aggregate size cap (20, Section 3.2) */
   int pre_smooth;       /* Chebyshev steps before the coarse correction (2, Section 3.4) */
   int post_smooth;      /* Chebyshev steps after (2) */
@@ -105,6 +111,11 @@ typedef struct {
                            so each is scheduled while its predecessor finishes (1) */
   int loss;             /* ba_loss (BA_LOSS_SQUARED) */
   double loss_scale;    /* a of BA_LOSS_HUBER, in residual units (1.0) */
+  double precond_lambda_min; /* BA_MIXED: the FP32 multigrid hierarchy is built from S at damping
+                           max(lambda, precond_lambda_min); PCG still solves S at lambda.  Below
+                           about 1e-6 the damping that keeps S's near-null (gauge) eigenvalues
+                           apart from zero falls under the FP32 rounding of S's entries and the
+                           FP32 hierarchy stops preconditioning (1e-5; 0 disables) */
 } ba_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -238,7 +249,8 @@ typedef enum {
   BA_KT_ASSEMBLY = 4,    /* off-diagonal blocks of the assembled level-0 S (observation pairs) */
   BA_KT_OUTER_BSR = 5,   /* PCG product with the FP64 blocks of the assembled S */
   BA_KT_VCYCLE = 6,      /* one whole preconditioner application (all of a V-cycle's kernels) */
-  BA_KT_COUNT = 7
+  BA_KT_SCHUR_RECOMPUTE = 7, /* implicit Schur product, FP64, blocks rebuilt (recompute_jacobian) */
+  BA_KT_COUNT = 8
 } ba_kernel_class;
 
 /* enable != 0 starts recording a CUDA event pair around every launch of the timed

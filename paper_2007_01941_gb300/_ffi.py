@@ -17,7 +17,7 @@ BA_PRECOND_NONE, BA_PRECOND_JACOBI, BA_PRECOND_MG = 0, 1, 2
 BA_OP_IMPLICIT, BA_OP_EXPLICIT, BA_OP_AUTO = 0, 1, 2
 BA_DAMP_MARQUARDT, BA_DAMP_IDENTITY = 0, 1
 BA_KT_SCHUR_FP64, BA_KT_SCHUR_FP32, BA_KT_LINEARIZE, BA_KT_SCHUR_DF = 0, 1, 2, 3
-BA_KT_ASSEMBLY, BA_KT_OUTER_BSR, BA_KT_VCYCLE = 4, 5, 6
+BA_KT_ASSEMBLY, BA_KT_OUTER_BSR, BA_KT_VCYCLE, BA_KT_SCHUR_RECOMPUTE = 4, 5, 6, 7
 BA_OUTER_FP64, BA_OUTER_PAIRED_FP32 = 0, 1
 BA_STOP_RELRES, BA_STOP_NASH_SOFER = 0, 1
 BA_LOSS_SQUARED, BA_LOSS_HUBER = 0, 1
@@ -37,7 +37,8 @@ class Options(ctypes.Structure):
                 ("max_levels", c_int), ("cheb_lo", c_double), ("cheb_hi", c_double),
                 ("level0_operator", c_int), ("fused_vcycle", c_int), ("outer_product", c_int),
                 ("stop_rule", c_int), ("tau", c_double), ("overlap_launches", c_int),
-                ("loss", c_int), ("loss_scale", c_double)]
+                ("loss", c_int), ("loss_scale", c_double),
+                ("precond_lambda_min", c_double)]
 
 
 class Info(ctypes.Structure):

@@ -159,6 +159,7 @@ struct ba_problem {
   int n_tiles = 0, n_chunks = 0, k3_window = 0;
   int k3_grid[2] = {0, 0};       // Schur product CTAs per launch (FP32, FP64), set at first use
   int k3_grid_df = 0;           // the same for the paired-FP32 product
+  int k3_grid_rc = 0;           // the same for the FP64 product in recompute mode
   bool l0_explicit = false;     // V-cycle level 0 uses the assembled S (set by the multigrid setup)
   bool outer_explicit = false;  // the PCG product uses the FP64-valued blocks of the assembled S
   bool vc_ready = false;        // the fused-phase V-cycle applies (set by the multigrid setup)
@@ -199,6 +200,9 @@ struct ba_problem {
   ba::DBuf Scc_inv, Scc_inv32;  // their inverses (point-block-Jacobi), FP64 and FP32
   ba::DBuf ptsdf;               // float2 [n_p][3]: the points of the current linearisation as float pairs
   ba::DBuf cam_ubnd;            // float [n_c][9]: diag(sum_o F_o^T F_o), bounds of the assembly's column sums
+  ba::DBuf pc_diag;             // float [n_c][9]: the mixed-precision hierarchy's extra damping (see below)
+  ba::DBuf Scc_pc;              // double [2][n_c][81]: S_cc with that damping, and its FP64 inverse (scratch)
+  bool pc_shift = false;        // pc_diag holds (mu - lambda) max(diag(J^T J), 1e-6), mu = precond_lambda_min
 
   // multigrid hierarchy
   std::vector<ba::Level> levels;

@@ -8,6 +8,7 @@
 #include "ba_internal.h"
 #include "device_util.cuh"
 #include "dfloat.cuh"
+#include "camera_model.cuh"
 
 namespace ba {
 
@@ -708,6 +709,27 @@ __global__ void k_back_substitute_df(const float* __restrict__ Jh, const float* 
   }
 }
 
+// The mixed-precision hierarchy is built from S at damping mu = max(lambda,
+// precond_lambda_min): its diagonal gets s_i = (mu - lambda) max(diag(J^T J)_i, 1e-6)
+// (s_i = mu - lambda with identity damping), the difference between D at mu and at
+// lambda.  FP32 copies only: the PCG's own operator keeps the damping lambda.
+__global__ void k_precond_shift(int n, float s, int damp_identity, const float* __restrict__ ubnd,
+                                float* __restrict__ pcd, float* __restrict__ Dc32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = damp_identity ? s : s * fmaxf(ubnd[i], 1e-6f);
+  pcd[i] = v;
+  Dc32[i] += v;
+}
+
+__global__ void k_add_block_diag(int n_c, const double* __restrict__ Scc, const float* __restrict__ pcd,
+                                 double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 81 * n_c) return;
+  const int c = i / 81, k = i - 81 * c;
+  out[i] = Scc[i] + ((k % 10 == 0) ? (double)pcd[9 * c + k / 10] : 0.0);
+}
+
 void schur_setup(ba_problem* P, double lambda) {
   const bool mixed = P->opt.precision == BA_MIXED;
   const int n_c = P->n_c, n_p = P->n_p;
@@ -772,9 +794,27 @@ void schur_setup(ba_problem* P, double lambda) {
         P->J64.as<double>(), P->J64.as<double>(), P->ld, P->Cinv64.as<double>(), ldp,
         P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->Dc.as<double>(), n_c, Scc);
   launched(P);
+  // mixed precision: the FP32 hierarchy's extra damping below precond_lambda_min
+  const double mu = P->opt.precond_lambda_min;
+  P->pc_shift = mixed && mu > lambda;
+  if (P->pc_shift) {
+    P->pc_diag.ensure(sizeof(float) * 9 * n_c + 64);
+    k_precond_shift<<<cdiv(9 * n_c, 256), 256, 0, P->stream>>>(9 * n_c, (float)(mu - lambda), damp_id,
+                                                                 P->cam_ubnd.as<float>(), P->pc_diag.as<float>(),
+                                                                 P->Dc32.as<float>());
+    launched(P);
+  }
   block_inverse(P, Scc, n_c, 9, P->Scc_inv.as<double>(), P->Scc_inv32.as<float>(), F_NOT_SPD_JACOBI);
+  if (P->pc_shift) {
+    // the hierarchy's level-0 Jacobi blocks (the FP32 inverses) are those of the damped copy
+    P->Scc_pc.ensure(sizeof(double) * 81 * (2 * (size_t)n_c) + 64);
+    double* shifted = P->Scc_pc.as<double>();
+    k_add_block_diag<<<cdiv(81 * n_c, 256), 256, 0, P->stream>>>(n_c, Scc, P->pc_diag.as<float>(), shifted);
+    launched(P);
+    block_inverse(P, shifted, n_c, 9, shifted + 81 * (size_t)n_c, P->Scc_inv32.as<float>(), F_NOT_SPD_JACOBI);
+  }
   // the PCG graph captures the FP64 outer product, so its records must exist beforehand
-  if (mixed && !outer_df(P)) jacobian64(P);
+  if (mixed && !outer_df(P) && !P->opt.recompute_jacobian) jacobian64(P);
   check_flags(P);
 }
 
@@ -801,6 +841,51 @@ __device__ __forceinline__ int rot_index(int rot, int k) {
   return j >= 9 ? j - 9 : j;
 }
 
+// Recompute mode of the product (FP64): instead of streaming each observation's stored
+// record (192 bytes), F and E are rebuilt in registers from the camera's rotation data and
+// parameters (read from L2: few cameras) and the point (shared by the point's lanes), the
+// same camera model as the linearisation, scaled by the robust weight under the Huber
+// loss.  It trades 192 streamed bytes per observation for about 300 FP64 operations.
+struct RecompSrc {
+  const double* camx;     // [n_c][kCamx] R, J_l, first-order flag of the linearisation point
+  const double* cams;     // [n_c][9] the linearisation point's cameras
+  const double* pts;      // [n_p][3] its points, in the caller's point order
+  const double* obs;      // [n_o][2] observations, in the caller's order (Huber weights only)
+  const int* obs_ptu;     // internal observation -> caller point
+  const int* obs_user;    // internal observation -> caller observation
+  double huber;           // Huber scale a, or 0 for the squared loss
+};
+
+__device__ __forceinline__ void recompute_record(const RecompSrc& r, int o, int c, double f[18], double e[6]) {
+  const double* cx = r.camx + (size_t)kCamx * c;
+  const double* cp = r.cams + 9 * (size_t)c;
+  double c9[9], cr[18];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) c9[i] = __ldg(cp + i);
+#pragma unroll
+  for (int i = 0; i < 18; ++i) cr[i] = __ldg(cx + i);
+  const int pu = __ldg(r.obs_ptu + o);
+  const double X[3] = {__ldg(r.pts + 3 * (size_t)pu), __ldg(r.pts + 3 * (size_t)pu + 1),
+                       __ldg(r.pts + 3 * (size_t)pu + 2)};
+  double ob[2] = {0.0, 0.0};
+  if (r.huber > 0.0) {
+    const int ou = __ldg(r.obs_user + o);
+    ob[0] = __ldg(r.obs + 2 * (size_t)ou);
+    ob[1] = __ldg(r.obs + 2 * (size_t)ou + 1);
+  }
+  CamObsT<double> v;
+  project_obs_t<true, double>(c9, cr, __ldg(cx + 18) != 0.0, X, ob, v);
+  double w = 1.0;
+  if (r.huber > 0.0) {
+    double half_rho;
+    w = robust_weight(v.res[0] * v.res[0] + v.res[1] * v.res[1], r.huber, half_rho);
+  }
+#pragma unroll
+  for (int k = 0; k < 18; ++k) f[k] = w * v.F[k];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) e[k] = w * v.E[k];
+}
+
 template <typename T, bool WINDOW>
 __device__ __forceinline__ void k3_scatter(T* acc, T* __restrict__ y, int c, int cam_lo, int span,
                                            const T yv[9], int rot) {
@@ -810,13 +895,14 @@ __device__ __forceinline__ void k3_scatter(T* acc, T* __restrict__ y, int c, int
   for (int k = 0; k < 9; ++k) atomicAdd(dst + rot_index(rot, k), yv[k]);
 }
 
-template <typename T, bool WINDOW>
-__global__ void __launch_bounds__(kK3Warps * 32, sizeof(T) == 4 ? 4 : 3)
+template <typename T, bool WINDOW, bool RECOMP = false>
+__global__ void __launch_bounds__(kK3Warps * 32, sizeof(T) == 4 ? 4 : (RECOMP ? 2 : 3))
 k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, int ld,
                const T* __restrict__ Cinv, int ldp, const int* __restrict__ obs_cam,
                const int4* __restrict__ tile_desc, const unsigned char* __restrict__ tile_perm,
                const int* __restrict__ chunk_tile, const int* __restrict__ chunk_cam, int n_chunks, const T* __restrict__ x,
-               T* __restrict__ y, int win, int reverse) {
+               T* __restrict__ y, int win, int reverse, RecompSrc rs) {
+  static_assert(!RECOMP || sizeof(T) == 8, "the recompute mode is the FP64 product");
   constexpr bool kPermute = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char k3_smem[];
   T* acc = reinterpret_cast<T*>(k3_smem);
@@ -859,10 +945,13 @@ k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, int ld,
         }
         const int c = __ldg(obs_cam + o);
         // FP64: lane l visits the 9 camera components starting at l mod 9, so that lanes
-        // of one camera add into different words of y at the same time
-        const int rot = kPermute ? 0 : lane % 9;
+        // of one camera add into different words of y at the same time (not in the
+        // recompute mode, whose rebuilt blocks sit in registers in their natural order)
+        const int rot = (kPermute || RECOMP) ? 0 : lane % 9;
         T f[18], e[6];
-        if constexpr (kPermute) {
+        if constexpr (RECOMP) {
+          recompute_record(rs, o, c, f, e);
+        } else if constexpr (kPermute) {
           load_record(F + (size_t)o * kRec, f, e);
         } else {
           const T* r = F + (size_t)o * kRec;
@@ -949,21 +1038,33 @@ k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, int ld,
       } else {
         // one point with more than 32 observations
         const int ip = p0;
+        auto blocks = [&](int o, int c, T f[18], T e[6]) {
+          if constexpr (RECOMP) {
+            recompute_record(rs, o, c, f, e);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 18; ++k) f[k] = JF(F, o, k);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) e[k] = JE(E, o, k);
+          }
+        };
         T s0 = T(0), s1 = T(0), s2 = T(0);
         for (int base = 0; base < nobs; base += 32) {
           const int o = ob + base + lane;
           if (base + lane < nobs) {
             const int c = obs_cam[o];
             const T* xc = x + 9 * (size_t)c;
+            T f[18], e[6];
+            blocks(o, c, f, e);
             T u0 = T(0), u1 = T(0);
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
-              u0 += JF(F, o, k) * xc[k];
-              u1 += JF(F, o, 9 + k) * xc[k];
+              u0 += f[k] * xc[k];
+              u1 += f[9 + k] * xc[k];
             }
-            s0 += JE(E, o, 0) * u0 + JE(E, o, 3) * u1;
-            s1 += JE(E, o, 1) * u0 + JE(E, o, 4) * u1;
-            s2 += JE(E, o, 2) * u0 + JE(E, o, 5) * u1;
+            s0 += e[0] * u0 + e[3] * u1;
+            s1 += e[1] * u0 + e[4] * u1;
+            s2 += e[2] * u0 + e[5] * u1;
           }
         }
         s0 = warp_sum(s0);
@@ -979,17 +1080,16 @@ k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, int ld,
           if (base + lane < nobs) {
             const int c = obs_cam[o];
             const T* xc = x + 9 * (size_t)c;
-            T f[18];
-#pragma unroll
-            for (int k = 0; k < 18; ++k) f[k] = JF(F, o, k);
+            T f[18], e[6];
+            blocks(o, c, f, e);
             T u0 = T(0), u1 = T(0);
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
               u0 += f[k] * xc[k];
               u1 += f[9 + k] * xc[k];
             }
-            const T w0 = u0 - (JE(E, o, 0) * z0 + JE(E, o, 1) * z1 + JE(E, o, 2) * z2);
-            const T w1 = u1 - (JE(E, o, 3) * z0 + JE(E, o, 4) * z1 + JE(E, o, 5) * z2);
+            const T w0 = u0 - (e[0] * z0 + e[1] * z1 + e[2] * z2);
+            const T w1 = u1 - (e[3] * z0 + e[4] * z1 + e[5] * z2);
             T yv[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) yv[k] = f[k] * w0 + f[9 + k] * w1;
@@ -1034,13 +1134,37 @@ static void launch_matvec(ba_problem* P, const T* F, const T* E, const T* Cinv, 
                                                           kK3Warps * 32, smem));
     grid = std::max(1, std::min(P->n_chunks, P->n_sm * std::max(per_sm, 1)));
   }
+  if constexpr (sizeof(T) == 8) {
+    if (P->opt.recompute_jacobian) {
+      int& g = P->k3_grid_rc;
+      if (g == 0) {
+        int per_sm = 0;
+        BA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_schur_matvec<double, false, true>,
+                                                              kK3Warps * 32, 0));
+        g = std::max(1, std::min(P->n_chunks, P->n_sm * std::max(per_sm, 1)));
+      }
+      const RecompSrc rs{P->camx.as<double>(), P->cams_lin.as<double>(), P->pts_lin.as<double>(),
+                         P->obs_lin.as<double>(), P->obs_ptu.as<int>(), P->obs_user.as<int>(),
+                         P->opt.loss == BA_LOSS_HUBER ? P->opt.loss_scale : 0.0};
+      KernelTimer kt(P, BA_KT_SCHUR_RECOMPUTE);
+      k_schur_matvec<double, false, true><<<g, kK3Warps * 32, 0, P->stream>>>(
+          nullptr, nullptr, (int)P->ld, Cinv, (int)P->ldp, P->obs_cam.as<int>(), P->tile_desc.as<int4>(),
+          P->tile_perm.as<unsigned char>(), P->chunk_tile.as<int>(), P->chunk_cam.as<int>(), P->n_chunks, x, y,
+          P->k3_window, (P->k3_calls++) & 1, rs);
+      launched(P);
+      return;
+    }
+  }
   KernelTimer kt(P, sizeof(T) == 8 ? BA_KT_SCHUR_FP64 : BA_KT_SCHUR_FP32);
   k_schur_matvec<T, window><<<grid, kK3Warps * 32, smem, P->stream>>>(
       F, E, (int)P->ld, Cinv, (int)P->ldp, P->obs_cam.as<int>(), P->tile_desc.as<int4>(),
       P->tile_perm.as<unsigned char>(), P->chunk_tile.as<int>(), P->chunk_cam.as<int>(), P->n_chunks, x, y, P->k3_window,
-      (P->k3_calls++) & 1);
+      (P->k3_calls++) & 1, RecompSrc{});
   launched(P);
 }
+
+// the FP64 records, unless the product rebuilds its blocks (recompute mode)
+static double* records64(ba_problem* P) { return P->opt.recompute_jacobian ? nullptr : jacobian64(P); }
 
 void matvec64(ba_problem* P, const double* x, double* y) {
   if (outer_df(P)) {
@@ -1051,7 +1175,7 @@ void matvec64(ba_problem* P, const double* x, double* y) {
   const int n = 9 * P->n_c;
   k_diag_init<double, double><<<cdiv(n, 256), 256, 0, P->stream>>>(P->Dc.as<double>(), x, y, n);
   launched(P);
-  double* J = jacobian64(P);
+  double* J = records64(P);
   launch_matvec<double>(P, J, J, P->Cinv64.as<double>(), x, y);
 }
 
@@ -1069,7 +1193,7 @@ void matvec64_accumulate(ba_problem* P, const double* x, double* y) {
     matvec_df_accumulate(P, y);
     return;
   }
-  double* J = jacobian64(P);
+  double* J = records64(P);
   launch_matvec<double>(P, J, J, P->Cinv64.as<double>(), x, y);
 }
 void matvec32_accumulate(ba_problem* P, const float* x, float* y) {
@@ -1212,7 +1336,8 @@ template <typename T>
 __global__ void __launch_bounds__(kExWarps * 32)
 k_explicit_pairs(const T* __restrict__ W, int n_up, const int* __restrict__ up_blk, const int* __restrict__ mirror,
                  const int* __restrict__ blk_row, const int* __restrict__ cols, const int* __restrict__ pair_ptr,
-                 const int2* __restrict__ pairs, const double* __restrict__ Scc, T* __restrict__ vals) {
+                 const int2* __restrict__ pairs, const double* __restrict__ Scc, const float* __restrict__ pcd,
+                 T* __restrict__ vals) {
   constexpr int kB = 64 / (int)sizeof(T);            // pairs per batch
   __shared__ __align__(16) T stage[kExWarps][2][2 * kB][kWld];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1222,7 +1347,9 @@ k_explicit_pairs(const T* __restrict__ W, int n_up, const int* __restrict__ up_b
   const int c = blk_row[e];
   T* out = vals + (size_t)e * 81;
   if (cols[e] == c) {
-    for (int i = lane; i < 81; i += 32) out[i] = (T)Scc[(size_t)c * 81 + i];
+    // (pcd: the mixed-precision hierarchy's extra damping on the FP32 diagonal)
+    for (int i = lane; i < 81; i += 32)
+      out[i] = (T)Scc[(size_t)c * 81 + i] + ((pcd && i % 10 == 0) ? (T)pcd[9 * (size_t)c + i / 10] : T(0));
     return;
   }
   // lane -> (row a, column group g); lanes 27..31 repeat lane 0's reads and discard them
@@ -1294,7 +1421,8 @@ __global__ void __launch_bounds__(kExWarps * 32)
 k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restrict__ up_blk,
                     const int* __restrict__ mirror, const int* __restrict__ blk_row, const int* __restrict__ cols,
                     const int* __restrict__ pair_ptr, const int2* __restrict__ pairs, const double* __restrict__ Scc,
-                    const float* __restrict__ ubnd, float2* __restrict__ valsdf, float* __restrict__ vals32) {
+                    const float* __restrict__ ubnd, const float* __restrict__ pcd, float2* __restrict__ valsdf,
+                    float* __restrict__ vals32) {
   constexpr int kB = 8;
   __shared__ __align__(16) float2 stage[kExWarps][2][2 * kB][kWld];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1306,7 +1434,8 @@ k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restri
     for (int i = lane; i < 81; i += 32) {
       const DF v(Scc[(size_t)c * 81 + i]);
       valsdf[(size_t)e * 81 + i] = make_float2(v.h, v.l);
-      vals32[(size_t)e * 81 + i] = v.h;
+      // the FP32 copy feeds the hierarchy: with its extra damping on the diagonal
+      vals32[(size_t)e * 81 + i] = (pcd && i % 10 == 0) ? v.h + pcd[9 * (size_t)c + i / 10] : v.h;
     }
     return;
   }
@@ -1404,7 +1533,10 @@ static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
   for (int pass = 0; pass < 3; ++pass) {
     if (pass == 1) {
       // work items in decreasing order of their pair counts, so that the longest blocks
-      // start first and the grid's tail is short (each block's own pair order is kept)
+      // start first and the grid's tail is short (each block's own pair order is kept).
+      // Block-row order, which keeps the blocks that share W rows together in L2, was
+      // measured slower (0.37 -> 0.59 ms on the street chain): the tail costs more than
+      // the re-reads
       std::vector<int> perm(n_up), rank(n_up);
       for (int u = 0; u < n_up; ++u) perm[u] = u;
       std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return cnt[a + 1] > cnt[b + 1]; });
@@ -1468,7 +1600,7 @@ void explicit_schur(ba_problem* P, Level& L0, ExplicitMode mode) {
     k_explicit_pairs_df<<<gb, kExWarps * 32, 0, P->stream>>>(
         W2, L0.n_up, L0.up_blk.as<int>(), L0.mirror.as<int>(), L0.blk_row.as<int>(), L0.cols.as<int>(),
         L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(), P->cam_ubnd.as<float>(),
-        L0.valsdf.as<float2>(), L0.vals32.as<float>());
+        P->pc_shift ? P->pc_diag.as<float>() : nullptr, L0.valsdf.as<float2>(), L0.vals32.as<float>());
   } else if (mode == EX_FP32) {
     L0.vals32.ensure(sizeof(float) * 81 * (size_t)L0.nnzb + 64);
     P->scratch.ensure(sizeof(float) * kWld * (size_t)std::max(P->n_o, 1) + 64);
@@ -1481,7 +1613,8 @@ void explicit_schur(ba_problem* P, Level& L0, ExplicitMode mode) {
     KernelTimer kt(P, BA_KT_ASSEMBLY);
     k_explicit_pairs<float><<<gb, kExWarps * 32, 0, P->stream>>>(
         W, L0.n_up, L0.up_blk.as<int>(), L0.mirror.as<int>(), L0.blk_row.as<int>(), L0.cols.as<int>(),
-        L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(), L0.vals32.as<float>());
+        L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(),
+        P->pc_shift ? P->pc_diag.as<float>() : nullptr, L0.vals32.as<float>());
   } else {
     L0.vals64.ensure(sizeof(double) * 81 * (size_t)L0.nnzb + 64);
     P->scratch.ensure(sizeof(double) * kWld * (size_t)std::max(P->n_o, 1) + 64);
@@ -1494,7 +1627,7 @@ void explicit_schur(ba_problem* P, Level& L0, ExplicitMode mode) {
     KernelTimer kt(P, BA_KT_ASSEMBLY);
     k_explicit_pairs<double><<<gb, kExWarps * 32, 0, P->stream>>>(
         W, L0.n_up, L0.up_blk.as<int>(), L0.mirror.as<int>(), L0.blk_row.as<int>(), L0.cols.as<int>(),
-        L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(), L0.vals64.as<double>());
+        L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(), nullptr, L0.vals64.as<double>());
   }
   launched(P);
 }
