@@ -7,7 +7,8 @@ standard gain-ratio update (Madsen, Nielsen & Tingleff 2004, as used by Ceres):
     accept if rho > 1e-3:  lam <- lam * max(1/3, 1 - (2 rho - 1)^3),  nu <- 2
     else:                  lam <- lam * nu,                           nu <- 2 nu
 
-with lam_0 = 1 / (initial trust radius 1e4) = 1e-4 (Section 5).
+with lam_0 = 1 / (initial trust radius 1e4) = 1e-4 (Section 5).  A step whose linear
+solve fails is unsuccessful and handled like a rejection (Ceres does the same).
 """
 from __future__ import annotations
 
@@ -42,7 +43,14 @@ def lm_step(cams, pts, cam_idx, pt_idx, obs, lam, nu=2.0, precond="mg", rtol=1e-
     huber = a: the robust objective and corrected residuals of Section 5 (oracle/robust.py)."""
     sch = schur.linearize(cams, pts, cam_idx, pt_idx, obs, lam, huber=huber)
     cost0 = camera.cost(cams, pts, cam_idx, pt_idx, obs, huber=huber)
-    dc, dp, it, rel = solve_step(sch, cams, precond, rtol, **kw)
+    try:
+        dc, dp, it, rel = solve_step(sch, cams, precond, rtol, **kw)
+    except (np.linalg.LinAlgError, FloatingPointError) as ex:
+        # a linear solve that fails (the coarsest factorisation finds the operator not
+        # positive definite, or CG breaks down) is an unsuccessful step, as in the Ceres
+        # trust-region loop the paper uses: x is kept and lambda grows as after a rejection
+        info = dict(iters=0, rel_res=np.inf, rho=-np.inf, model=0.0, cost_new=cost0, failed=str(ex))
+        return cams, pts, lam * nu, 2.0 * nu, False, cost0, cost0, info
     cams1 = cams + dc.reshape(-1, 9)
     pts1 = pts + dp.reshape(-1, 3)
     cost1 = camera.cost(cams1, pts1, cam_idx, pt_idx, obs, huber=huber)

@@ -105,6 +105,7 @@ void ba_default_options(ba_options* o) {
   o->overlap_launches = 1;
   o->loss = BA_LOSS_SQUARED;
   o->loss_scale = 1.0;
+  o->precond_lambda_min = 1e-5;
 }
 
 size_t ba_struct_size(int which) {
@@ -144,6 +145,8 @@ ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx, co
     BA_REQUIRE(o.loss == BA_LOSS_SQUARED || (o.loss == BA_LOSS_HUBER && o.loss_scale > 0.0 &&
                                              std::isfinite(o.loss_scale)),
                BA_ERR_INVALID_ARG, "bad loss / loss_scale");
+    BA_REQUIRE(o.precond_lambda_min >= 0.0 && std::isfinite(o.precond_lambda_min), BA_ERR_INVALID_ARG,
+               "bad precond_lambda_min");
     int dev = 0;
     BA_CUDA(cudaGetDevice(&dev));
     BA_CUDA(cudaDeviceGetAttribute(&P->n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -175,7 +178,7 @@ void ba_destroy(ba_problem* P) {
                       &P->cam_obs, &P->tile_pt, &P->tile_desc, &P->tile_perm, &P->lz_vec, &P->lz_red, &P->lz_cnt, &P->lz_ptr, &P->chunk_tile, &P->chunk_cam, &P->camx, &P->fres, &P->J64,
                       &P->J64, &P->J32, &P->J32lo, &P->cams_lin, &P->pts_lin, &P->obs_lin, &P->Dc, &P->Dp,
                       &P->Cinv64, &P->Cinv32, &P->Cinv32lo, &P->xsplit, &P->camdf, &P->wpdf, &P->Xdf, &P->gc, &P->gp, &P->wp, &P->rhs, &P->Dc32, &P->Scc, &P->Scc_inv,
-                      &P->Scc_inv32, &P->cam_ubnd, &P->ptsdf, &P->x, &P->r, &P->z, &P->p, &P->q, &P->y32a, &P->y32b, &P->delta_c,
+                      &P->Scc_inv32, &P->cam_ubnd, &P->pc_diag, &P->Scc_pc, &P->ptsdf, &P->x, &P->r, &P->z, &P->p, &P->q, &P->y32a, &P->y32b, &P->delta_c,
                       &P->delta_p, &P->scal, &P->partial, &P->partial2, &P->rzpart, &P->counter, &P->flags, &P->scratch, &P->scratch2};
   for (ba::DBuf* b : bufs) b->release();
   for (ba::Level& L : P->levels) {
@@ -281,7 +284,7 @@ ba_status ba_lm_step(ba_problem* P, double* cams, double* pts, const double* obs
     BA_REQUIRE(*lambda_inout >= 0.0, BA_ERR_INVALID_ARG, "lambda must be >= 0");
     P->stage = 0;
     ba::lm_step(P, cams, pts, obs, lambda_inout, accepted, cost_out);
-    P->stage = 4;
+    if (P->stage != 1) P->stage = 4;   // 1: the step's linear solve failed (step rejected)
   });
 }
 

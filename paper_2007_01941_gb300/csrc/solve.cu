@@ -954,14 +954,34 @@ void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double
   check_flags(P);
   const double cost0 = P->h_scal[S_COST];
   P->cost = cost0;
-  schur_setup(P, *lam);
-  if (P->opt.preconditioner == BA_PRECOND_MG) mg_setup(P);
   const size_t nc = (size_t)P->n_c * 9, np = (size_t)P->n_p * 3;
   P->delta_c.ensure(sizeof(double) * nc + 64);
+  // A linear solve that fails (a block found not positive definite by its pivots, or a
+  // PCG breakdown; near the optimum lambda becomes small enough for S to be numerically
+  // singular along the gauge and the focal-length / depth directions) makes the step
+  // unsuccessful, as in the Ceres trust-region loop the paper uses: x is kept and lambda
+  // grows as after a rejection.
+  bool solved = true;
   try {
-    pcg(P, P->rhs.as<double>(), P->delta_c.as<double>());
+    schur_setup(P, *lam);
+    if (P->opt.preconditioner == BA_PRECOND_MG) mg_setup(P);
+    try {
+      pcg(P, P->rhs.as<double>(), P->delta_c.as<double>());
+    } catch (const Error& e) {
+      if (e.status != BA_ERR_NOT_CONVERGED) throw;  // an inexact step is still a step
+    }
   } catch (const Error& e) {
-    if (e.status != BA_ERR_NOT_CONVERGED) throw;  // an inexact step is still a step
+    if (e.status != BA_ERR_NOT_SPD && e.status != BA_ERR_BREAKDOWN) throw;
+    solved = false;
+  }
+  if (!solved) {
+    *lam = *lam * P->lm_nu;
+    P->lm_nu *= 2.0;
+    *accepted = 0;
+    *cost_out = cost0;
+    P->stage = 1;   // linearised; the setup must run again before a solve
+    sync(P);
+    return;
   }
   P->scratch.ensure(sizeof(double) * (nc + 2 * np) + 64);
   double* cams1 = P->scratch.as<double>();

@@ -193,3 +193,17 @@ def test_adjoint_is_linear_in_the_cotangent():
     c = adjoint.adjoint(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, 1e-3, 2 * v1 - v2)
     for k in range(3):
         assert np.allclose(c[k], 2 * a[k] - b[k], rtol=1e-9, atol=1e-9 * np.abs(a[k]).max())
+
+
+def test_lm_step_with_a_failed_solve_is_a_rejection(monkeypatch):
+    """A solve that fails (here: the coarsest factorisation raising, planted in the oracle)
+    leaves x unchanged and grows lambda as a rejection does."""
+    s = scene("ring", seed=0, n_cams=16, n_pts=800)
+
+    def failing(*a, **k):
+        raise np.linalg.LinAlgError("planted: not positive definite")
+    monkeypatch.setattr(lm, "solve_step", failing)
+    x1, p1, lam1, nu1, acc, cost0, cost1, info = lm.lm_step(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, 1e-4, 4.0)
+    assert not acc and x1 is s.cams and p1 is s.pts
+    assert lam1 == 4e-4 and nu1 == 8.0
+    assert cost0 == cost1 == camera.cost(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs)
