@@ -29,6 +29,10 @@ WORKLOADS = {
     "city_grid": dict(fn="city_grid", kw={}, rtol=1e-6),
     "ring": dict(fn="ring", kw={}, rtol=1e-8),
     "loop_closure": dict(fn="loop_closure", kw={}, rtol=1e-6),
+    # the city grid's 20,000-camera graph with a quarter of its points: the level
+    # operators keep their size (above the L2), the per-observation data shrinks to a few
+    # GB (the case for multi-pass profiler captures)
+    "city_grid_1m": dict(fn="city_grid", kw={"n_pts": 1_000_000}, rtol=1e-6),
 }
 
 
@@ -113,6 +117,41 @@ def bsr_bytes(nnzb, n_c, w):
     # the assembled S: 81 values and a column index per block, a row pointer per camera;
     # z and p read, the new direction and S times it written once per camera
     return nnzb * (81 * w + 4) + n_c * (4 + 4 * 9 * w)
+
+
+def vcycle_bytes(prob, F_, w):
+    """Algorithmic bytes of one V-cycle application of the fused-phase cycle (Algorithm 1,
+    2 + 2 Chebyshev steps), from the hierarchy's own structure.  Per smoothed level l with
+    n_l nodes of bs dofs and nnzb_l operator blocks: three passes over the operator
+    (pre-smoothing step 1, the residual, post-smoothing step 1), the A P blocks once
+    (prolongation fused into post-smoothing step 0), the prolongator blocks twice
+    (restriction, prolongation), the Jacobi blocks four times (every smoothing step) and
+    24 vector passes of n_l bs values (the phases' reads and writes of x, r, d, b and the
+    residual); the coarsest level reads its FP64 inverse once.  Returns (bytes, detail)."""
+    info = prob.info()
+    nl = info["n_levels"]
+    total, per = 0, []
+    for l in range(nl):
+        n, bs, nnzb = info["level_nodes"][l], info["level_block"][l], info["level_nnzb"][l]
+        if l == nl - 1:
+            N = n * bs
+            b = N * N * 8 + 2 * N * w
+            per.append({"level": l, "coarsest_inverse": N * N * 8})
+            total += b
+            break
+        rp = prob.get_array(F_.BA_ARR_LEVEL_ROWPTR, l).cpu().numpy()
+        cols = prob.get_array(F_.BA_ARR_LEVEL_COLS, l).cpu().numpy()
+        agg = prob.get_array(F_.BA_ARR_AGG, l).cpu().numpy()
+        row = np.repeat(np.arange(n), np.diff(rp))
+        ap_nnzb = len(np.unique(row.astype(np.int64) * (int(agg.max()) + 1) + agg[cols]))
+        ops = 3 * (nnzb * (bs * bs * w + 4) + (n + 1) * 4)
+        ap = ap_nnzb * (bs * 16 * w + 4) + (n + 1) * 4
+        q = 2 * n * bs * 16 * w
+        dinv = 4 * n * bs * bs * w
+        vec = 24 * n * bs * w
+        per.append({"level": l, "operator_passes": ops, "ap": ap, "prolongator": q, "jacobi": dinv, "vectors": vec})
+        total += ops + ap + q + dinv + vec
+    return total, per
 
 
 # FP32 operations per term of the paired-FP32 assembly's offset accumulator: the head's
@@ -315,6 +354,21 @@ def gpu_main(args):
     t_mg, _ = timed(lambda: prob.mg_setup())
     t_pcg, (dc, iters, rel) = timed(lambda: prob.pcg_solve())
 
+    # the adjoint of that solve (a second PCG solve on the same hierarchy plus the
+    # per-observation Hessian-vector pass) for a seeded cotangent
+    adjoint = None
+    if not args.skip_variants and args.precision == "mixed":
+        g = torch.Generator(device=dev)
+        g.manual_seed(0)
+        vbar = torch.randn(9 * s.n_cams + 3 * s.n_pts, dtype=torch.float64, device=dev, generator=g)
+        prob.adjoint(vbar)
+        ta = []
+        for _ in range(3):
+            t_adj, _ = timed(lambda: prob.adjoint(vbar))
+            ta.append(t_adj)
+        adjoint = {"ms": min(ta), "note": "ba_adjoint after the step's solve: mu = H^-1 vbar through the Schur "
+                                          "complement and the same hierarchy, then dL/d(obs, cams, pts)"}
+
     # all-FP64 GPU solve of the same step for comparison
     fp64 = None
     if prec == _ffi.BA_MIXED and not args.skip_fp64:
@@ -399,70 +453,16 @@ def gpu_main(args):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     # FP32 lane operations per second: 128 FP32 lanes per SM at the highest SM clock seen
     fp32_peak_tops = n_sm * 128 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
-    kernels = {}
-    for name, (tot, n) in list(kt.items()) + list(kt_var.items()):
-        if n == 0:
-            continue
-        avg = tot / n
-        d = {"launches": n, "avg_ms": avg}
-        if name in kt_var:
-            d["run"] = "implicit level-0 variant"
-        if name == "schur_fp32":
-            b = k3_bytes(n_o, n_p, n_c, 4)
-            d.update(bound="hbm", achieved=b / avg / 1e6, unit="GB/s", algo_bytes=b)
-        elif name == "schur_df":
-            b = k3_bytes(n_o, n_p, n_c, 8)   # hi + lo floats: the FP64 byte count
-            d.update(bound="hbm", achieved=b / avg / 1e6, unit="GB/s", algo_bytes=b)
-        elif name == "schur_fp64":
-            b = k3_bytes(n_o, n_p, n_c, 8)
-            fl = k3_flops(n_o, n_p)
-            d.update(bound="alu", achieved=fl / avg / 1e9, unit="TFLOP/s", algo_flops=fl,
-                     hbm_gbs=b / avg / 1e6, algo_bytes=b)
-        elif name == "assembly" and prec == _ffi.BA_MIXED and info["level0_explicit"]:
-            # 81 entries x 3 terms per pair, each term DF_TERM_OPS FP32 lane operations
-            ops = n_pairs * 243 * DF_TERM_OPS
-            d.update(bound="alu", achieved=ops / avg / 1e9, unit="TFLOP/s", algo_flops=ops, pairs=n_pairs,
-                     note="FP32 lane operations of the paired-FP32 pair sums")
-        elif name == "outer_bsr":
-            b = bsr_bytes(nnzb, n_c, 8)
-            d.update(bound="hbm", achieved=b / avg / 1e6, unit="GB/s", algo_bytes=b,
-                     note="the FP64 blocks stay L2-resident across PCG iterations")
-        elif name == "vcycle":
-            d.update(note="all kernels of one V-cycle application")
-        kernels[name] = d
-    # dominant kernel class by total time (single kernels with a roofline model)
-    dom = max((k for k in kernels if k in kt and kt[k][1] > 0 and "bound" in kernels[k]),
-              key=lambda k: kt[k][0], default=None)
-    roofline = None
-    if dom == "schur_fp32" or (dom == "linearize" and "schur_fp32" in kernels):
-        k = kernels["schur_fp32"]
-        roofline = {"kernel": "k_schur_matvec<float>", "bound": "hbm", "achieved": k["achieved"], "peak": hbm,
-                    "unit": "GB/s", "frac": k["achieved"] / hbm, "traffic": None, "peak_source": peak_note}
-    elif dom == "schur_df":
-        k = kernels["schur_df"]
-        roofline = {"kernel": "k_schur_matvec_df", "bound": "hbm", "achieved": k["achieved"], "peak": hbm,
-                    "unit": "GB/s", "frac": k["achieved"] / hbm, "traffic": None, "peak_source": peak_note}
-    elif dom == "assembly":
-        k = kernels["assembly"]
-        roofline = {"kernel": "k_explicit_pairs_df", "bound": "alu", "achieved": k["achieved"],
-                    "peak": fp32_peak_tops, "unit": "TFLOP/s", "frac": k["achieved"] / fp32_peak_tops,
-                    "traffic": None,
-                    "peak_source": f"{n_sm} SMs x 128 FP32 lanes x max SM clock (FP32 lane operations)"}
-    elif dom == "outer_bsr":
-        k = kernels["outer_bsr"]
-        roofline = {"kernel": "k_pcg_spmv_pq_df" if prec == _ffi.BA_MIXED else "k_pcg_spmv_pq", "bound": "hbm",
-                    "achieved": k["achieved"], "peak": hbm, "unit": "GB/s", "frac": k["achieved"] / hbm,
-                    "traffic": None, "peak_source": peak_note,
-                    "note": "blocks L2-resident across PCG iterations; latency-bound (one warp per block row)"}
-    elif dom == "schur_fp64":
-        k = kernels["schur_fp64"]
-        roofline = {"kernel": "k_schur_matvec<double>", "bound": "alu", "achieved": k["achieved"],
-                    "peak": fp64_peak_tflops, "unit": "TFLOP/s", "frac": k["achieved"] / fp64_peak_tflops,
-                    "traffic": None, "peak_source": "cuBLAS DGEMM 4096^3 measured in this run"}
-    # the recorded counters are the paired-FP32 kernels' (mixed precision)
-    traffic = _traffic_from_profiles(dom) if prec == _ffi.BA_MIXED else None
-    if roofline is not None and traffic is not None:
-        roofline["traffic"] = traffic
+    kernels, roofline = kernel_table(prob, _ffi, s, info, prec, kt, kt_var, hbm, peak_note, fp32_peak_tops,
+                                     fp64_peak_tflops, n_sm)
+
+    # the other single-GPU workloads, measured in the same run: the city grid (the largest
+    # single-GPU configuration) and a 50-iteration LM run on the loop-closure scene
+    extra = []
+    if rank == 0 and world == 1 and not args.skip_extra and args.workload == "street_chain":
+        prob.close()
+        extra.append(measure_config("city_grid", dev, args))
+        extra.append(lm_run("loop_closure", dev, args))
 
     cpu = None
     parity = None
@@ -511,6 +511,8 @@ def gpu_main(args):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "parity": parity,
+            "adjoint": adjoint,
+            "configs": extra,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks,
@@ -518,6 +520,256 @@ def gpu_main(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def kernel_table(prob, _ffi, s, info, prec, kt, kt_var, hbm, peak_note, fp32_peak_tops, fp64_peak_tflops, n_sm):
+    """Per kernel class: launches, average ms and, where a model exists, the algorithmic
+    bytes (or operations) per launch and the achieved rate; and the roofline entry of the
+    class with the largest total time per step among those with a model."""
+    n_o, n_p, n_c = s.n_obs, s.n_pts, s.n_cams
+    nnzb = info["level_nnzb"][0]
+    n_pairs = upper_pairs(s.pt_idx, n_p)
+    vbytes, vc_launches = None, None
+    if info["n_levels"] > 1 and info["level0_explicit"]:
+        vbytes, vdetail = vcycle_bytes(prob, _ffi, 4 if prec == _ffi.BA_MIXED else 8)
+        nl = info["n_levels"]
+        # fused phases: level 0 first/step/residual/restrict, each coarser smoothed level
+        # step/residual/restrict, the coarsest, and two post-smoothing phases per level
+        vc_launches = 4 + 3 * (nl - 2) + 1 + 2 * (nl - 1)
+    kernels = {}
+    for name, (tot, n) in list(kt.items()) + list(kt_var.items()):
+        if n == 0:
+            continue
+        avg = tot / n
+        d = {"launches": n, "avg_ms": avg}
+        if name in kt_var:
+            d["run"] = "implicit level-0 variant"
+        if name == "schur_fp32":
+            b = k3_bytes(n_o, n_p, n_c, 4)
+            d.update(bound="hbm", achieved=b / avg / 1e6, unit="GB/s", algo_bytes=b)
+        elif name == "schur_df":
+            b = k3_bytes(n_o, n_p, n_c, 8)   # hi + lo floats: the FP64 byte count
+            d.update(bound="hbm", achieved=b / avg / 1e6, unit="GB/s", algo_bytes=b)
+        elif name == "schur_fp64":
+            b = k3_bytes(n_o, n_p, n_c, 8)
+            fl = k3_flops(n_o, n_p)
+            d.update(bound="alu", achieved=fl / avg / 1e9, unit="TFLOP/s", algo_flops=fl,
+                     hbm_gbs=b / avg / 1e6, algo_bytes=b)
+        elif name == "assembly" and prec == _ffi.BA_MIXED and info["level0_explicit"]:
+            # 81 entries x 3 terms per pair, each term DF_TERM_OPS FP32 lane operations
+            ops = n_pairs * 243 * DF_TERM_OPS
+            d.update(bound="alu", achieved=ops / avg / 1e9, unit="TFLOP/s", algo_flops=ops, pairs=n_pairs,
+                     note="FP32 lane operations of the paired-FP32 pair sums")
+        elif name == "outer_bsr":
+            b = bsr_bytes(nnzb, n_c, 8)
+            d.update(bound="hbm", achieved=b / avg / 1e6, unit="GB/s", algo_bytes=b,
+                     note="the FP64 blocks stay L2-resident across PCG iterations")
+        elif name == "vcycle" and vbytes:
+            d.update(bound="hbm", achieved=vbytes / avg / 1e6, unit="GB/s", algo_bytes=vbytes,
+                     note="all kernels of one V-cycle application; algorithmic bytes from the hierarchy "
+                          "(operator passes, A P, prolongator, Jacobi blocks, vectors, coarsest inverse)")
+        kernels[name] = d
+    # dominant kernel class by total time (single kernels with a roofline model)
+    dom = max((k for k in kernels if k in kt and kt[k][1] > 0 and "bound" in kernels[k]),
+              key=lambda k: kt[k][0], default=None)
+    roofline = None
+    if dom == "schur_fp32" or (dom == "linearize" and "schur_fp32" in kernels):
+        k = kernels["schur_fp32"]
+        roofline = {"kernel": "k_schur_matvec<float>", "bound": "hbm", "achieved": k["achieved"], "peak": hbm,
+                    "unit": "GB/s", "frac": k["achieved"] / hbm, "traffic": None, "peak_source": peak_note}
+    elif dom == "schur_df":
+        k = kernels["schur_df"]
+        roofline = {"kernel": "k_schur_matvec_df", "bound": "hbm", "achieved": k["achieved"], "peak": hbm,
+                    "unit": "GB/s", "frac": k["achieved"] / hbm, "traffic": None, "peak_source": peak_note}
+    elif dom == "assembly":
+        k = kernels["assembly"]
+        roofline = {"kernel": "k_explicit_pairs_df", "bound": "alu", "achieved": k["achieved"],
+                    "peak": fp32_peak_tops, "unit": "TFLOP/s", "frac": k["achieved"] / fp32_peak_tops,
+                    "traffic": None,
+                    "peak_source": f"{n_sm} SMs x 128 FP32 lanes x max SM clock (FP32 lane operations)"}
+    elif dom == "outer_bsr":
+        k = kernels["outer_bsr"]
+        roofline = {"kernel": "k_pcg_spmv_pq_df" if prec == _ffi.BA_MIXED else "k_pcg_spmv_pq", "bound": "hbm",
+                    "achieved": k["achieved"], "peak": hbm, "unit": "GB/s", "frac": k["achieved"] / hbm,
+                    "traffic": None, "peak_source": peak_note,
+                    "note": "blocks L2-resident across PCG iterations; latency-bound (one warp per block row)"}
+    elif dom == "vcycle":
+        k = kernels["vcycle"]
+        roofline = {"kernel": "V-cycle (fused phase kernels)", "bound": "hbm", "achieved": k["achieved"],
+                    "peak": hbm, "unit": "GB/s", "frac": k["achieved"] / hbm, "traffic": None,
+                    "peak_source": peak_note, "launches_per_application": vc_launches}
+    elif dom == "schur_fp64":
+        k = kernels["schur_fp64"]
+        roofline = {"kernel": "k_schur_matvec<double>", "bound": "alu", "achieved": k["achieved"],
+                    "peak": fp64_peak_tflops, "unit": "TFLOP/s", "frac": k["achieved"] / fp64_peak_tflops,
+                    "traffic": None, "peak_source": "cuBLAS DGEMM 4096^3 measured in this run"}
+    # the recorded counters are the paired-FP32 kernels' (mixed precision)
+    traffic = _traffic_from_profiles(dom) if prec == _ffi.BA_MIXED else None
+    if roofline is not None and traffic is not None:
+        roofline["traffic"] = traffic
+    return kernels, roofline
+
+
+KT_CLASSES = (("schur_fp32", "BA_KT_SCHUR_FP32"), ("schur_fp64", "BA_KT_SCHUR_FP64"), ("schur_df", "BA_KT_SCHUR_DF"),
+              ("linearize", "BA_KT_LINEARIZE"), ("assembly", "BA_KT_ASSEMBLY"), ("outer_bsr", "BA_KT_OUTER_BSR"),
+              ("vcycle", "BA_KT_VCYCLE"))
+
+
+def _event_ms(dev, fn):
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    r = fn()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b), r
+
+
+def _solver_run(s, dev, args, precision, level0, steps, warmup, rtol, timing_steps=0):
+    """A problem on scene s, its first LM step (with the symbolic hierarchy build), then
+    `warmup` untimed and `steps` timed steps that all restart from the scene's start,
+    kernel-class timing over `timing_steps` more, and the stage split of one step."""
+    from paper_2007_01941_gb300 import _ffi, api
+    L0 = {"implicit": _ffi.BA_OP_IMPLICIT, "explicit": _ffi.BA_OP_EXPLICIT, "auto": _ffi.BA_OP_AUTO}
+    prob, cams, pts, obs = api.from_scene(s, device=dev, precision=precision, rtol=rtol, max_iters=2000,
+                                          coarse_max_nodes=args.coarse_max_nodes, level0_operator=L0[level0])
+    cams0, pts0 = cams.clone(), pts.clone()
+
+    def step():
+        cams.copy_(cams0)
+        pts.copy_(pts0)
+        return prob.lm_step(cams, pts, obs, s.lam)
+    first, _ = _event_ms(dev, step)
+    for _ in range(warmup):
+        step()
+
+    def many():
+        for _ in range(steps):
+            step()
+    total, _ = _event_ms(dev, many)
+    out = {"ms_per_step": total / steps, "first_step_ms": first, "steps": steps}
+    kt = {}
+    if timing_steps:
+        prob.set_kernel_timing(True)
+        for _ in range(timing_steps):
+            step()
+        kt = {k: prob.kernel_timing(getattr(_ffi, c)) for k, c in KT_CLASSES}
+        prob.set_kernel_timing(False)
+    cams.copy_(cams0)
+    pts.copy_(pts0)
+    t_lin, _ = _event_ms(dev, lambda: prob.linearize(cams, pts, obs))
+    t_sch, _ = _event_ms(dev, lambda: prob.schur_setup(s.lam))
+    t_mg, _ = _event_ms(dev, lambda: prob.mg_setup())
+    t_pcg, (_, iters, _) = _event_ms(dev, lambda: prob.pcg_solve())
+    out["parts_ms"] = {"linearize": t_lin, "schur_setup": t_sch, "mg_setup": t_mg, "pcg_solve": t_pcg,
+                       "pcg_iters": iters}
+    return prob, out, kt
+
+
+def measure_config(workload, dev, args):
+    """Another single-GPU workload in the same run: ms per LM step in mixed precision and in
+    FP64, the stage split, kernel classes with their rooflines, and the implicit-level-0
+    variant's FP32 Schur product."""
+    import torch
+    from paper_2007_01941_gb300 import _ffi, scenes
+    wl = WORKLOADS[workload]
+    t0 = time.time()
+    s = getattr(scenes, wl["fn"])(**wl["kw"])
+    gen_s = time.time() - t0
+    res = {"workload": workload, "n_cams": s.n_cams, "n_pts": s.n_pts, "n_obs": s.n_obs, "rtol": wl["rtol"],
+           "precision": "mixed", "scene_generation_s": gen_s}
+    prob, out, kt = _solver_run(s, dev, args, _ffi.BA_MIXED, "auto", steps=5, warmup=3, rtol=wl["rtol"],
+                                timing_steps=2)
+    info = prob.info()
+    res.update(out)
+    res.update(levels=info["level_nodes"], level0_operator="assembled" if info["level0_explicit"] else "implicit")
+    kt_var = {}
+    pim, oim, ktim = _solver_run(s, dev, args, _ffi.BA_MIXED, "implicit", steps=2, warmup=1, rtol=wl["rtol"],
+                                 timing_steps=1)
+    pim.close()
+    res["implicit_level0"] = {"ms_per_step": oim["ms_per_step"], "pcg_iters": oim["parts_ms"]["pcg_iters"]}
+    kt_var["schur_fp32"] = ktim["schur_fp32"]
+    hbm = _peaks().get("hbm_gbs") or 6800.0
+    peak_note = "measured" if _peaks().get("hbm_gbs") else "fallback"
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    kernels, roofline = kernel_table(prob, _ffi, s, info, _ffi.BA_MIXED, kt, kt_var, hbm, peak_note,
+                                     n_sm * 128 * 2070.0 * 1e6 / 1e12, None, n_sm)
+    prob.close()
+    res["kernels"] = kernels
+    res["roofline"] = roofline
+    p64, o64, _ = _solver_run(s, dev, args, _ffi.BA_FP64, "auto", steps=3, warmup=2, rtol=wl["rtol"])
+    p64.close()
+    res["fp64_ms_per_step"] = o64["ms_per_step"]
+    res["mixed_speedup_vs_fp64"] = o64["ms_per_step"] / res["ms_per_step"]
+    res["fp64_implicit_product"] = fp64_products(s, dev, args)
+    return res
+
+
+def fp64_products(s, dev, args, reps=3):
+    """The FP64 implicit Schur product (Section 3.6) with stored Jacobian blocks against the
+    recompute mode, which rebuilds F and E per observation: kernel time and algorithmic
+    bytes of each."""
+    import torch
+    from paper_2007_01941_gb300 import _ffi, api
+    out = {}
+    x = torch.randn(s.n_cams, 9, dtype=torch.float64, device=dev)
+    for name, rc, cls in (("stored", 0, _ffi.BA_KT_SCHUR_FP64), ("recompute", 1, _ffi.BA_KT_SCHUR_RECOMPUTE)):
+        prob, cams, pts, obs = api.from_scene(s, device=dev, precision=_ffi.BA_FP64, level0_operator=_ffi.BA_OP_IMPLICIT,
+                                              recompute_jacobian=rc, coarse_max_nodes=args.coarse_max_nodes)
+        prob.linearize(cams, pts, obs)
+        prob.schur_setup(s.lam)
+        prob.schur_matvec(x)
+        prob.set_kernel_timing(True)
+        for _ in range(reps):
+            prob.schur_matvec(x)
+        tot, n = prob.kernel_timing(cls)
+        prob.set_kernel_timing(False)
+        prob.close()
+        avg = tot / max(n, 1)
+        if rc:
+            # camera and point index per observation, the point (one lane per observation
+            # reads it) and C^-1 per point, rotation data and parameters per camera, x and y
+            b = s.n_obs * (4 + 4 + 24) + s.n_pts * (6 * 8 + 4) + s.n_cams * (28 * 8 + 2 * 9 * 8)
+        else:
+            b = k3_bytes(s.n_obs, s.n_pts, s.n_cams, 8)
+        out[name] = {"avg_ms": avg, "launches": n, "algo_bytes": b, "achieved_gbs": b / avg / 1e6}
+    out["note"] = ("FP64 arithmetic runs at 1/58 of the FP32 rate on this GPU, so rebuilding the blocks "
+                   "(about 300 FP64 operations per observation) trades streamed bytes for the slowest unit")
+    return out
+
+
+def lm_run(workload, dev, args, n_iter=50):
+    """A full LM run: n_iter consecutive ba_lm_step calls from the scene's start (cameras and
+    points updated by accepted steps, lambda by the gain-ratio rule), in mixed precision
+    and in FP64; ms per iteration, accepted steps and the final costs."""
+    from paper_2007_01941_gb300 import _ffi, api, scenes
+    wl = WORKLOADS[workload]
+    s = getattr(scenes, wl["fn"])(**wl["kw"])
+    res = {"workload": workload, "run": f"{n_iter} LM iterations", "n_cams": s.n_cams, "n_pts": s.n_pts,
+           "n_obs": s.n_obs, "rtol": wl["rtol"]}
+    for name, code in (("mixed", _ffi.BA_MIXED), ("fp64", _ffi.BA_FP64)):
+        prob, cams, pts, obs = api.from_scene(s, device=dev, precision=code, rtol=wl["rtol"], max_iters=2000,
+                                              coarse_max_nodes=args.coarse_max_nodes)
+        cost0 = prob.linearize(cams, pts, obs)
+        lam = s.lam
+        trace = []
+
+        def run():
+            nonlocal lam
+            c = None
+            for _ in range(n_iter):
+                lam, acc, c = prob.lm_step(cams, pts, obs, lam)
+                inf = prob.info()
+                trace.append((bool(acc), c, inf["pcg_iters"], lam))
+            return c
+        ms, cost = _event_ms(dev, run)
+        prob.close()
+        res[name] = {"ms_per_iteration": ms / n_iter, "accepted": sum(t[0] for t in trace), "initial_cost": cost0,
+                     "final_cost": cost, "costs": [t[1] for t in trace], "pcg_iters": [t[2] for t in trace],
+                     "lambda": [t[3] for t in trace]}
+    res["final_cost_rel_diff"] = abs(res["mixed"]["final_cost"] - res["fp64"]["final_cost"]) / res["fp64"]["final_cost"]
+    return res
 
 
 def measure_dgemm_tflops(dev, n=4096, reps=5):
@@ -569,6 +821,7 @@ def main():
                     help="V-cycle finest-level operator: implicit Jacobian stream, the assembled S, "
                          "or the cheaper of the two (Section 3.6)")
     ap.add_argument("--skip-variants", action="store_true", help="skip the implicit level-0 comparison run")
+    ap.add_argument("--skip-extra", action="store_true", help="skip the city-grid and loop-closure legs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

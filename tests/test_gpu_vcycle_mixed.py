@@ -165,3 +165,45 @@ def test_mixed_vcycle_matches_oracle(gpu, level0):
             eta_g = _inf(sim_g - ref_g) / _inf(ref_g)
             err_g = _inf(z - ref_g) / _inf(ref_g)
             assert err_g <= 10 * eta_g, (seed, err_g, eta_g)
+
+
+def test_mixed_hierarchy_below_the_damping_floor(gpu):
+    """Below precond_lambda_min (1e-5) the mixed-precision hierarchy is built from S at
+    that damping while PCG solves S at the step's lambda: the FP32 cycle at lambda = 1e-8
+    matches the oracle's cycle built from S(1e-5) at the bound above, and the solve of
+    S(1e-8) reaches its residual in about the iterations of the all-FP64 solve, whose
+    hierarchy is built at lambda itself."""
+    import scipy.sparse.linalg as spla
+    api, F_ = _api()
+    s = scene("street_chain", **CHAIN)
+    lam, mu = 1e-8, 1e-5
+    prob, cams, pts, obs = api.from_scene(s, device=gpu, precision=F_.BA_MIXED, coarse_max_nodes=CMAX,
+                                          level0_operator=F_.BA_OP_EXPLICIT, rtol=1e-8, max_iters=3000)
+    assert prob.options.precond_lambda_min == mu
+    prob.linearize(cams, pts, obs)
+    prob.schur_setup(lam)
+    prob.mg_setup()
+    lams = prob.info()["level_lambda_max"]
+    sch_mu = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, mu)
+    W = multigrid.covisibility(s.cam_idx, s.pt_idx, s.n_cams, s.n_pts)
+    H = multigrid.Hierarchy(sch_mu.S, W, s.cams, coarse_max_nodes=CMAX)
+    Ps = [L.P for L in H.levels[:-1]]
+    lev64 = _levels_from([L.A for L in H.levels], Ps, lams, np.float64)
+    lev32 = _levels_from(_fp32_operators(sch_mu.S.astype(np.float32), H), [P.astype(np.float32) for P in Ps],
+                         lams, np.float32)
+    for seed in range(2):
+        r = np.random.default_rng(seed).normal(size=9 * s.n_cams)
+        z = _np(prob.precond_apply(torch.tensor(r, device=gpu)))
+        ref = _cycle(lev64, r, np.float64)
+        eta = _inf(_cycle(lev32, r, np.float32).astype(np.float64) - ref) / _inf(ref)
+        assert eta < 1e-2 and _inf(z - ref) / _inf(ref) <= 10 * eta, (seed, eta)
+    # the solve is of S(lambda), not S(mu)
+    dc, it_mixed, rel = prob.pcg_solve()
+    assert rel <= 1e-8
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, lam)
+    d = _np(dc).ravel()
+    assert np.linalg.norm(sch.b - sch.S @ d) <= 2e-8 * np.linalg.norm(sch.b)
+    p64, c64, x64, o64 = api.from_scene(s, device=gpu, precision=F_.BA_FP64, coarse_max_nodes=CMAX,
+                                        rtol=1e-8, max_iters=3000)
+    _, _, it64, _ = p64.solve(c64, x64, o64, lam)
+    assert it_mixed <= 1.3 * it64 + 2, (it_mixed, it64)
