@@ -168,9 +168,10 @@ def test_mixed_vcycle_matches_oracle(gpu, level0):
 
 
 def test_mixed_hierarchy_below_the_damping_floor(gpu):
-    """Below precond_lambda_min (1e-5) the mixed-precision hierarchy is built from S at
-    that damping while PCG solves S at the step's lambda: the FP32 cycle at lambda = 1e-8
-    matches the oracle's cycle built from S(1e-5) at the bound above, and the solve of
+    """Below precond_lambda_min (1e-5) the mixed-precision hierarchy is built from S with
+    its camera diagonal damped at that floor, S(lambda) + (mu - lambda) max(diag(J^T J),
+    1e-6), while PCG solves S at the step's lambda: the FP32 cycle at lambda = 1e-8 matches
+    the oracle's cycle built from that operator at the bound above, and the solve of
     S(1e-8) reaches its residual in about the iterations of the all-FP64 solve, whose
     hierarchy is built at lambda itself."""
     import scipy.sparse.linalg as spla
@@ -184,12 +185,14 @@ def test_mixed_hierarchy_below_the_damping_floor(gpu):
     prob.schur_setup(lam)
     prob.mg_setup()
     lams = prob.info()["level_lambda_max"]
-    sch_mu = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, mu)
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, lam)
+    # D_c = lam max(diag, 1e-6): the floor's extra camera damping is (mu - lam) / lam D_c
+    S_mu = (sch.S + sp.diags((mu - lam) / lam * sch.Dc)).tocsr()
     W = multigrid.covisibility(s.cam_idx, s.pt_idx, s.n_cams, s.n_pts)
-    H = multigrid.Hierarchy(sch_mu.S, W, s.cams, coarse_max_nodes=CMAX)
+    H = multigrid.Hierarchy(S_mu, W, s.cams, coarse_max_nodes=CMAX)
     Ps = [L.P for L in H.levels[:-1]]
     lev64 = _levels_from([L.A for L in H.levels], Ps, lams, np.float64)
-    lev32 = _levels_from(_fp32_operators(sch_mu.S.astype(np.float32), H), [P.astype(np.float32) for P in Ps],
+    lev32 = _levels_from(_fp32_operators(S_mu.astype(np.float32), H), [P.astype(np.float32) for P in Ps],
                          lams, np.float32)
     for seed in range(2):
         r = np.random.default_rng(seed).normal(size=9 * s.n_cams)
@@ -200,7 +203,6 @@ def test_mixed_hierarchy_below_the_damping_floor(gpu):
     # the solve is of S(lambda), not S(mu)
     dc, it_mixed, rel = prob.pcg_solve()
     assert rel <= 1e-8
-    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, lam)
     d = _np(dc).ravel()
     assert np.linalg.norm(sch.b - sch.S @ d) <= 2e-8 * np.linalg.norm(sch.b)
     p64, c64, x64, o64 = api.from_scene(s, device=gpu, precision=F_.BA_FP64, coarse_max_nodes=CMAX,
