@@ -20,6 +20,7 @@
 // d and r alternate between two buffers per level, and x moves to its second buffer
 // at post-smoothing step 0, so that no kernel writes a vector that its own warps read.
 #include <algorithm>
+#include <type_traits>
 
 #include "ba_internal.h"
 #include "device_util.cuh"
@@ -82,10 +83,15 @@ template <int BS>
 struct RowCta {
   static constexpr int G = BS == 16 ? 8 : 10;
   static constexpr int kThreads = BS == 16 ? 128 : 96;
+  // 9 x 9 blocks are read by columns (kCol): the per-column partial rows of every group,
+  // then each group's row sums, meet in shared memory
+  static constexpr bool kCol = BS == 9;
+  static constexpr int kPart = kCol ? G * BS * BS + G * BS : G * BS;
 };
 
-// the first kPre blocks of thread (u, h)'s share of block row i (row u of each) and
-// where its remaining blocks start
+// the first kPre blocks of thread (u, h)'s share of block row i (row u of each; column u
+// for 9 x 9 blocks, so that a group's loads cover its block contiguously) and where its
+// remaining blocks start
 template <typename T, int BS>
 struct RowPrefetch {
   static constexpr int kPre = 2;
@@ -109,9 +115,10 @@ __device__ __forceinline__ void row_prefetch(const VLevel<T>& L, int i, RowPrefe
   for (int k = 0; k < RowPrefetch<T, BS>::kPre; ++k) {
     if (e < p.e1) {
       p.col[k] = L.cols[e];
-      const T* a = L.vals + (size_t)e * (BS * BS) + u * BS;
+      constexpr bool kCol = RowCta<BS>::kCol;
+      const T* a = L.vals + (size_t)e * (BS * BS) + (kCol ? u : u * BS);
 #pragma unroll
-      for (int c = 0; c < BS; ++c) p.a[k][c] = a[c];
+      for (int c = 0; c < BS; ++c) p.a[k][c] = a[kCol ? c * BS : c];
       p.n = k + 1;
       e += G;
     }
@@ -127,6 +134,49 @@ __device__ __forceinline__ void cta_row_product(const VLevel<T>& L, const RowPre
   constexpr int G = RowCta<BS>::G;
   const int t = threadIdx.x;
   const int u = t % BS, h = t / BS;
+  if constexpr (RowCta<BS>::kCol) {
+    // thread (u, h) holds column u of its blocks: acc[c] += A_i,col(c, u) v_col(u)
+    if (h < G) {
+      T acc[BS];
+#pragma unroll
+      for (int c = 0; c < BS; ++c) acc[c] = T(0);
+#pragma unroll
+      for (int k = 0; k < RowPrefetch<T, BS>::kPre; ++k) {
+        if (k < p.n) {
+          const T xu = v[(size_t)p.col[k] * BS + u];
+#pragma unroll
+          for (int c = 0; c < BS; ++c) acc[c] += p.a[k][c] * xu;
+        }
+      }
+#pragma unroll 2
+      for (int e = p.e; e < p.e1; e += G) {
+        const T* a = L.vals + (size_t)e * (BS * BS) + u;
+        const T xu = v[(size_t)L.cols[e] * BS + u];
+#pragma unroll
+        for (int c = 0; c < BS; ++c) acc[c] += a[c * BS] * xu;
+      }
+#pragma unroll
+      for (int c = 0; c < BS; ++c) part[(h * BS + c) * BS + u] = acc[c];   // [group][row][column]
+    }
+    __syncthreads();
+    T* rows = part + G * BS * BS;
+    if (t < G * BS) {
+      const T* pr = part + (size_t)t * BS;   // group t / BS, row t % BS
+      T s = T(0);
+#pragma unroll
+      for (int c = 0; c < BS; ++c) s += pr[c];
+      rows[t] = s;
+    }
+    __syncthreads();
+    if (t < BS) {
+      T s = T(0);
+#pragma unroll
+      for (int g = 0; g < G; ++g) s += rows[g * BS + t];
+      q[t] = s;
+    }
+    __syncthreads();
+    return;
+  }
   if (h < G) {
     T acc = T(0);
 #pragma unroll
@@ -151,6 +201,90 @@ __device__ __forceinline__ void cta_row_product(const VLevel<T>& L, const RowPre
     T s = T(0);
 #pragma unroll
     for (int g = 0; g < G; ++g) s += part[g * BS + t];
+    q[t] = s;
+  }
+  __syncthreads();
+}
+
+// ROWS x 16 FP32 blocks (16 x 16 operator blocks of the coarse levels; A P blocks, 9 x 16
+// on level 0 and 16 x 16 below): the NW warps of the row's CTA take its blocks in turn,
+// and a warp reads a block (ROWS x 64 bytes, 16-byte aligned) with 16-byte loads: lane l
+// holds float4 l (row l / 4, columns 4 (l % 4) .. + 3) and, for the rows past 8, float4
+// 32 + l (row 8 + l / 4), multiplies them by the four matching entries of v (one 16-byte
+// load) and the four lanes of each row add their sums by shuffles.  (Per-thread rows of
+// 16 scalar loads made each warp load touch 32 separate 64-byte rows.)
+template <int ROWS>
+struct RowPrefetch16 {
+  static constexpr int kPre = 2;
+  int e, e1, n;
+  int col[kPre];
+  float4 a[kPre][2];
+};
+
+template <int ROWS, int NW>
+__device__ __forceinline__ void row_prefetch16(const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                                               const float* __restrict__ vals, int i, RowPrefetch16<ROWS>& p) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kSecond = (ROWS - 8) * 4;   // lanes holding a float4 of rows 8 ..
+  p.n = 0;
+  p.e1 = row_ptr[i + 1];
+  int e = row_ptr[i] + w;
+#pragma unroll
+  for (int k = 0; k < RowPrefetch16<ROWS>::kPre; ++k) {
+    if (e < p.e1) {
+      p.col[k] = cols[e];
+      const float4* a = reinterpret_cast<const float4*>(vals + (size_t)e * (ROWS * 16));
+      p.a[k][0] = a[lane];
+      p.a[k][1] = lane < kSecond ? a[32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+      p.n = k + 1;
+      e += NW;
+    }
+  }
+  p.e = e;
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+
+// q = (A v)_i (ROWS values in shared memory on return, all threads) for an NW-warp CTA;
+// part holds at least 16 NW floats
+template <int ROWS, int NW>
+__device__ __forceinline__ void cta_row_product16(const int* __restrict__ cols, const float* __restrict__ vals,
+                                                  const RowPrefetch16<ROWS>& p, const float* __restrict__ v,
+                                                  float* part, float* q) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, cq = 4 * (lane & 3);
+  constexpr int kSecond = (ROWS - 8) * 4;
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int k = 0; k < RowPrefetch16<ROWS>::kPre; ++k) {
+    if (k < p.n) {
+      const float4 xv = *reinterpret_cast<const float4*>(v + (size_t)p.col[k] * 16 + cq);
+      s0 += dot4(p.a[k][0], xv);
+      s1 += dot4(p.a[k][1], xv);
+    }
+  }
+#pragma unroll 2
+  for (int e = p.e; e < p.e1; e += NW) {
+    const float4* a = reinterpret_cast<const float4*>(vals + (size_t)e * (ROWS * 16));
+    const float4 a0 = a[lane];
+    const float4 a1 = lane < kSecond ? a[32 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 xv = *reinterpret_cast<const float4*>(v + (size_t)cols[e] * 16 + cq);
+    s0 += dot4(a0, xv);
+    s1 += dot4(a1, xv);
+  }
+  s0 += __shfl_xor_sync(kFull, s0, 1);
+  s0 += __shfl_xor_sync(kFull, s0, 2);
+  s1 += __shfl_xor_sync(kFull, s1, 1);
+  s1 += __shfl_xor_sync(kFull, s1, 2);
+  if ((lane & 3) == 0) {
+    part[w * 16 + (lane >> 2)] = s0;
+    if (lane < kSecond) part[w * 16 + 8 + (lane >> 2)] = s1;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < ROWS) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) s += part[k * 16 + t];
     q[t] = s;
   }
   __syncthreads();
@@ -199,17 +333,21 @@ template <typename T, int BS>
 __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_step(VLevel<T> L, int dc, int rc, int xc, T c1, T c2,
                                                                  double* __restrict__ out, const double* __restrict__ rdot,
                                                                  double* __restrict__ dpart) {
-  __shared__ T part[RowCta<BS>::G * BS];
+  __shared__ T part[RowCta<BS>::kPart];
   __shared__ T q[BS], w[BS];
   const int i = blockIdx.x, t = threadIdx.x;
-  RowPrefetch<T, BS> pf;
-  row_prefetch<T, BS>(L, i, pf);
+  constexpr bool kVec = BS == 16 && sizeof(T) == 4;
+  constexpr int kNW = RowCta<BS>::kThreads / 32;
+  std::conditional_t<kVec, RowPrefetch16<16>, RowPrefetch<T, BS>> pf;
+  if constexpr (kVec) row_prefetch16<16, kNW>(L.row_ptr, L.cols, L.vals, i, pf);
+  else row_prefetch<T, BS>(L, i, pf);
   T dr[BS];
   if (t < BS) dinv_row<T, BS>(L.Dinv + (size_t)i * BS * BS, t, dr);
   pdl_trigger();
   pdl_wait();
   const T* din = L.d[dc];
-  cta_row_product<T, BS>(L, pf, din, part, q);
+  if constexpr (kVec) cta_row_product16<16, kNW>(L.cols, L.vals, pf, din, part, q);
+  else cta_row_product<T, BS>(L, pf, din, part, q);
   const size_t idx = (size_t)i * BS + t;
   if (t < BS) w[t] = L.r[rc][idx] - q[t];
   __syncthreads();
@@ -236,14 +374,18 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_step(VLevel<T> L, i
 // residual of the pre-smoothed iterate on row blockIdx.x: s = r - A d, into the free r buffer
 template <typename T, int BS>
 __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_residual(VLevel<T> L, int dc, int rc) {
-  __shared__ T part[RowCta<BS>::G * BS];
+  __shared__ T part[RowCta<BS>::kPart];
   __shared__ T q[BS];
   const int i = blockIdx.x, t = threadIdx.x;
-  RowPrefetch<T, BS> pf;
-  row_prefetch<T, BS>(L, i, pf);
+  constexpr bool kVec = BS == 16 && sizeof(T) == 4;
+  constexpr int kNW = RowCta<BS>::kThreads / 32;
+  std::conditional_t<kVec, RowPrefetch16<16>, RowPrefetch<T, BS>> pf;
+  if constexpr (kVec) row_prefetch16<16, kNW>(L.row_ptr, L.cols, L.vals, i, pf);
+  else row_prefetch<T, BS>(L, i, pf);
   pdl_trigger();
   pdl_wait();
-  cta_row_product<T, BS>(L, pf, L.d[dc], part, q);
+  if constexpr (kVec) cta_row_product16<16, kNW>(L.cols, L.vals, pf, L.d[dc], part, q);
+  else cta_row_product<T, BS>(L, pf, L.d[dc], part, q);
   if (t < BS) {
     const size_t idx = (size_t)i * BS + t;
     L.r[1 - rc][idx] = L.r[rc][idx] - q[t];
@@ -358,7 +500,9 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first_ap(VLeve
                                                                           double* __restrict__ dpart) {
   constexpr int G = RowCta<BS>::G;
   constexpr int kPre = 2;
-  __shared__ T part[G * BS];
+  constexpr bool kVec = sizeof(T) == 4;   // A P blocks are BS x 16 floats, 16-byte aligned
+  constexpr int kNW = RowCta<BS>::kThreads / 32;
+  __shared__ T part[RowCta<BS>::kPart];
   __shared__ T q[BS], w[BS];
   const int i = blockIdx.x, t = threadIdx.x;
   const int u = t % BS, h = t / BS;
@@ -367,7 +511,10 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first_ap(VLeve
   int e = 0, e1 = 0, np = 0;
   int pc[kPre];
   T pa[kPre][16];
-  if (h < G) {
+  RowPrefetch16<BS> pf16;
+  if constexpr (kVec) {
+    row_prefetch16<BS, kNW>(L.ap_ptr, L.ap_cols, L.ap_vals, i, pf16);
+  } else if (h < G) {
     e1 = L.ap_ptr[i + 1];
     e = L.ap_ptr[i] + h;
 #pragma unroll
@@ -394,31 +541,41 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first_ap(VLeve
   pdl_trigger();
   pdl_wait();
   const T* xcv = C.x[xcl];
-  if (h < G) {
-    T acc = T(0);
+  if constexpr (kVec) {
+    // (A P x_c)_i in q (the product synchronises the CTA)
+    cta_row_product16<BS, kNW>(L.ap_cols, L.ap_vals, pf16, xcv, part, q);
+  } else {
+    if (h < G) {
+      T acc = T(0);
 #pragma unroll
-    for (int k = 0; k < kPre; ++k) {
-      if (k < np) {
-        const T* xa = xcv + (size_t)pc[k] * 16;
+      for (int k = 0; k < kPre; ++k) {
+        if (k < np) {
+          const T* xa = xcv + (size_t)pc[k] * 16;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) acc += pa[k][c] * xa[c];
+          for (int c = 0; c < 16; ++c) acc += pa[k][c] * xa[c];
+        }
       }
-    }
-    for (; e < e1; e += G) {
-      const T* a = L.ap_vals + (size_t)e * (BS * 16) + u * 16;
-      const T* xa = xcv + (size_t)L.ap_cols[e] * 16;
+      for (; e < e1; e += G) {
+        const T* a = L.ap_vals + (size_t)e * (BS * 16) + u * 16;
+        const T* xa = xcv + (size_t)L.ap_cols[e] * 16;
 #pragma unroll
-      for (int c = 0; c < 16; ++c) acc += a[c] * xa[c];
+        for (int c = 0; c < 16; ++c) acc += a[c] * xa[c];
+      }
+      part[h * BS + u] = acc;
     }
-    part[h * BS + u] = acc;
+    __syncthreads();
+    if (t < BS) {
+      T sq = T(0);
+#pragma unroll
+      for (int g = 0; g < G; ++g) sq += part[g * BS + t];
+      q[t] = sq;
+    }
   }
   __syncthreads();
   const size_t idx = (size_t)i * BS + t;
   T xp = T(0);
   if (t < BS) {
-    T sq = T(0);
-#pragma unroll
-    for (int g = 0; g < G; ++g) sq += part[g * BS + t];
+    const T sq = q[t];
     const T* xa = xcv + (size_t)ai * 16;
     T pq = T(0);
 #pragma unroll
