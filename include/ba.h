@@ -187,6 +187,37 @@ ba_status ba_adjoint(ba_problem* prob, const double* dL_ddelta, double* dL_dobs,
                      double* dL_dcams, double* dL_dpts);
 
 /* ---------------------------------------------------------------------------------
+ * Point-partitioned solve (several ranks share one LM step).
+ * --------------------------------------------------------------------------------- */
+
+/* Sums `count` doubles of buf (HOST memory) over all ranks of a partitioned solve, in
+ * place (an all-reduce), and returns 0 on success.  Called by the library on every rank at
+ * the same points of each call, with the same counts. */
+typedef int (*ba_allreduce_fn)(double* buf, size_t count, void* user);
+
+/* Makes the problem one rank's part of a point-partitioned solve: the points are split
+ * among the ranks, each point with all of its observations on one rank, and every rank
+ * solves the same LM step.  This rank's problem was created (ba_create) on its own points
+ * (ids 0 .. n_pts - 1) and their observations, with the global camera ids and count.
+ * cam_idx_all, pt_idx_all (HOST int32 [n_obs_all]) describe every rank's observations
+ * (global point ids, any order); the covisibility of Section 3.2, and with it the whole
+ * multigrid hierarchy, is built from them, identically on every rank.  Each rank forms its
+ * points' residuals, Jacobian blocks and point blocks C_p, and its share of every
+ * camera-space sum: the gradient and reduced right-hand side, diag(J^T J) for the
+ * damping, the diagonal blocks S_cc and the off-diagonal blocks of the assembled S, the
+ * costs and the model decrease; `allreduce` adds the shares (the exchange step of the
+ * point-partitioned Schur complement).  The PCG then runs on every rank on the same
+ * assembled S, with no exchange inside the loop, and ba_back_substitute / ba_lm_step
+ * produce this rank's points.  Call once, after ba_create and before the first
+ * ba_linearize.  Requires precision BA_FP64 and level0_operator BA_OP_EXPLICIT or
+ * BA_OP_AUTO (the assembled level 0 is then always used); ba_adjoint, the implicit PCG
+ * product and the inspection product ba_schur_matvec are not available on a partitioned
+ * problem (BA_ERR_INVALID_ARG), and the preconditioner must be BA_PRECOND_MG.  A hook that
+ * returns nonzero makes the call fail with BA_ERR_STATE. */
+ba_status ba_set_partition(ba_problem* prob, int n_obs_all, const int32_t* cam_idx_all,
+                           const int32_t* pt_idx_all, ba_allreduce_fn allreduce, void* user);
+
+/* ---------------------------------------------------------------------------------
  * Inspection entry points (used by the parity tests; not needed to solve).
  * --------------------------------------------------------------------------------- */
 

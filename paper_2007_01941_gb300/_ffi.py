@@ -75,6 +75,7 @@ _SIGS = {
     "ba_get_array": (c_int, [c_void_p, c_int, c_int, c_void_p, c_size_t, POINTER(c_size_t)]),
     "ba_cost_noalloc": (c_int, [c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p, c_void_p]),
+    "ba_set_partition": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 EXPORTED = tuple(_SIGS)

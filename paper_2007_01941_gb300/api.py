@@ -144,6 +144,19 @@ class Problem:
         self._check(self._lib.ba_adjoint(self._h, _ptr(dL_ddelta.contiguous()), _ptr(go), _ptr(gc), _ptr(gp)))
         return go, gc, gp
 
+    def set_partition(self, cam_idx_all, pt_idx_all, hook):
+        """Makes this problem one rank's part of a point-partitioned solve (ba_set_partition):
+        cam_idx_all, pt_idx_all are the whole problem's observations (global point ids;
+        host arrays), hook the all-reduce callback (see partition.gloo_allreduce_hook)."""
+        import numpy as np
+        ci = np.ascontiguousarray(np.asarray(cam_idx_all, dtype=np.int32))
+        pi = np.ascontiguousarray(np.asarray(pt_idx_all, dtype=np.int32))
+        if ci.shape != pi.shape or ci.ndim != 1:
+            raise ValueError("cam_idx_all and pt_idx_all must be 1-D arrays of equal length")
+        self._check(self._lib.ba_set_partition(self._h, int(ci.size), ci.ctypes.data, pi.ctypes.data,
+                                               ctypes.cast(hook, c_void_p), None))
+        self._part = (ci, pi, hook)   # the hook must outlive the problem
+
     # -- inspection -----------------------------------------------------------
     def schur_matvec(self, x, precision=_ffi.BA_FP64):
         y = torch.empty_like(x)

@@ -211,9 +211,8 @@ ba_status ba_linearize(ba_problem* P, const double* cams, const double* pts, con
     BA_REQUIRE(cams && (pts || P->n_p == 0) && (obs || P->n_o == 0), BA_ERR_INVALID_ARG, "null array");
     P->stage = 0;
     ba::linearize(P, cams, pts, obs);
-    ba::fetch_scalars(P, ba::S_COST, 1);
     ba::check_flags(P);
-    P->cost = P->h_scal[ba::S_COST];
+    P->cost = ba::fetch_sum(P, ba::S_COST);
     if (cost_out) *cost_out = P->cost;
     P->stage = 1;
   });
@@ -288,6 +287,31 @@ ba_status ba_lm_step(ba_problem* P, double* cams, double* pts, const double* obs
   });
 }
 
+ba_status ba_set_partition(ba_problem* P, int n_obs_all, const int32_t* cam_idx_all, const int32_t* pt_idx_all,
+                           ba_allreduce_fn allreduce, void* user) {
+  if (!P) return BA_ERR_INVALID_ARG;
+  return guard(P, [&] {
+    BA_REQUIRE(P->stage == 0 && !P->sym_ready && !P->part_fn, BA_ERR_STATE,
+               "ba_set_partition must come once, after ba_create and before the first ba_linearize");
+    BA_REQUIRE(allreduce, BA_ERR_INVALID_ARG, "null all-reduce hook");
+    BA_REQUIRE(n_obs_all >= P->n_o && (n_obs_all == 0 || (cam_idx_all && pt_idx_all)), BA_ERR_INVALID_ARG,
+               "the whole problem's observation graph must include this rank's observations");
+    BA_REQUIRE(P->opt.precision == BA_FP64, BA_ERR_INVALID_ARG, "a partitioned solve runs in BA_FP64");
+    BA_REQUIRE(P->opt.preconditioner == BA_PRECOND_MG, BA_ERR_INVALID_ARG,
+               "a partitioned solve needs the multigrid preconditioner (its assembled S)");
+    BA_REQUIRE(P->opt.level0_operator != BA_OP_IMPLICIT, BA_ERR_INVALID_ARG,
+               "a partitioned solve uses the assembled level-0 operator");
+    for (int o = 0; o < n_obs_all; ++o)
+      BA_REQUIRE(cam_idx_all[o] >= 0 && cam_idx_all[o] < P->n_c && pt_idx_all[o] >= 0, BA_ERR_INVALID_ARG,
+                 "observation index out of range in the partition's observation graph");
+    P->part_cam.assign(cam_idx_all, cam_idx_all + n_obs_all);
+    P->part_pt.assign(pt_idx_all, pt_idx_all + n_obs_all);
+    P->opt.level0_operator = BA_OP_EXPLICIT;
+    P->part_user = user;
+    P->part_fn = allreduce;
+  });
+}
+
 ba_status ba_adjoint(ba_problem* P, const double* dL_ddelta, double* dL_dobs, double* dL_dcams, double* dL_dpts) {
   if (!P) return BA_ERR_INVALID_ARG;
   return guard(P, [&] {
@@ -295,6 +319,7 @@ ba_status ba_adjoint(ba_problem* P, const double* dL_ddelta, double* dL_dobs, do
     BA_REQUIRE(dL_ddelta, BA_ERR_INVALID_ARG, "null cotangent");
     BA_REQUIRE(P->opt.loss == BA_LOSS_SQUARED, BA_ERR_INVALID_ARG,
                "ba_adjoint differentiates the squared loss only");
+    BA_REQUIRE(!ba::partitioned(P), BA_ERR_INVALID_ARG, "ba_adjoint is not available on a partitioned problem");
     ba::adjoint(P, dL_ddelta, dL_dobs, dL_dcams, dL_dpts);
   });
 }
@@ -304,6 +329,8 @@ ba_status ba_schur_matvec(ba_problem* P, const double* x, double* y, int precisi
   return guard(P, [&] {
     require_stage(P, 2, "ba_schur_matvec needs ba_schur_setup first");
     BA_REQUIRE(x && y, BA_ERR_INVALID_ARG, "null array");
+    BA_REQUIRE(!ba::partitioned(P), BA_ERR_INVALID_ARG,
+               "the implicit product of a partitioned problem holds only this rank's points");
     const size_t n = (size_t)P->n_c * 9;
     if (precision == BA_MIXED) {
       BA_REQUIRE(P->opt.precision == BA_MIXED, BA_ERR_STATE, "FP32 Jacobian storage exists only in mixed precision");

@@ -239,6 +239,13 @@ struct ba_problem {
   bool graphs_ok = true;        // false after a failed build: eager fallback
   long long pcg_graph_head = 0, pcg_graph_body = 0;  // kernels per graph part
 
+  // point-partitioned solve: the all-reduce hook and the whole problem's observation graph
+  // (host, global point ids), from which the level-0 covisibility is built
+  ba_allreduce_fn part_fn = nullptr;
+  void* part_user = nullptr;
+  std::vector<int> part_cam, part_pt;
+  std::vector<double> part_buf;
+
   // optional CUDA-event timing of selected kernel classes
   bool ktime = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -265,6 +272,11 @@ namespace ba {
 // ---- stream helpers -------------------------------------------------------
 void sync(ba_problem* P);
 void fetch_scalars(ba_problem* P, int first, int count);  // async copy + sync
+// point-partitioned solve: sum a device array (n doubles, in place) or a scalar slot over
+// the ranks through the caller's hook (no-ops on an unpartitioned problem)
+void part_allreduce(ba_problem* P, double* dev, size_t n);
+double fetch_sum(ba_problem* P, int slot);
+inline bool partitioned(const ba_problem* P) { return P->part_fn != nullptr; }
 void check_flags(ba_problem* P);                          // sync, read, raise
 void clear_flags(ba_problem* P);
 void launched(ba_problem* P);                              // count + check launch error

@@ -351,8 +351,7 @@ double cost_at(ba_problem* P, const double* cams, const double* pts, const doubl
         P->partial.as<double>(), P->counter.as<unsigned>(), P->scal.as<double>() + S_COST_NEW,
         P->flags.as<int>(), huber_scale(P));
   launched(P);
-  fetch_scalars(P, S_COST_NEW, 1);
-  return P->h_scal[S_COST_NEW];
+  return fetch_sum(P, S_COST_NEW);
 }
 
 }  // namespace ba

@@ -208,9 +208,70 @@ static void row_hash(ba_problem* P, int n_rows, int H, const int* a_ptr, const i
   check_flags(P);
 }
 
+// Partitioned solve: W = V^T V of the whole problem from its observation graph (host,
+// global point ids), by a sparse accumulator per camera row; every rank builds the same.
+static void covisibility_level0_host(ba_problem* P, Level& L) {
+  const int n_c = P->n_c;
+  const size_t n_o = P->part_cam.size();
+  int n_pts = 0;
+  for (size_t o = 0; o < n_o; ++o) n_pts = std::max(n_pts, P->part_pt[o] + 1);
+  std::vector<int> pptr(n_pts + 1, 0), cptr(n_c + 1, 0);
+  for (size_t o = 0; o < n_o; ++o) {
+    ++pptr[P->part_pt[o] + 1];
+    ++cptr[P->part_cam[o] + 1];
+  }
+  for (int p = 0; p < n_pts; ++p) pptr[p + 1] += pptr[p];
+  for (int c = 0; c < n_c; ++c) cptr[c + 1] += cptr[c];
+  std::vector<int> pcam(std::max<size_t>(n_o, 1)), cpt(std::max<size_t>(n_o, 1));
+  {
+    std::vector<int> pf(pptr.begin(), pptr.end() - 1), cf(cptr.begin(), cptr.end() - 1);
+    for (size_t o = 0; o < n_o; ++o) {
+      pcam[pf[P->part_pt[o]]++] = P->part_cam[o];
+      cpt[cf[P->part_cam[o]]++] = P->part_pt[o];
+    }
+  }
+  std::vector<long long> acc(n_c, 0);
+  std::vector<int> touched, rp(n_c + 1, 0), cols;
+  std::vector<long long> W;
+  for (int c = 0; c < n_c; ++c) {
+    touched.clear();
+    for (int k = cptr[c]; k < cptr[c + 1]; ++k) {
+      const int p = cpt[k];
+      for (int q = pptr[p]; q < pptr[p + 1]; ++q) {
+        const int c2 = pcam[q];
+        if (acc[c2]++ == 0) touched.push_back(c2);
+      }
+    }
+    std::sort(touched.begin(), touched.end());
+    for (int c2 : touched) {
+      // a point seen twice by camera c counts twice on the diagonal: duplicates are invalid
+      BA_REQUIRE(c2 != c || acc[c2] == cptr[c + 1] - cptr[c], BA_ERR_INVALID_ARG,
+                 "duplicate (camera, point) pair in the partition's observation graph");
+      cols.push_back(c2);
+      W.push_back(acc[c2]);
+      acc[c2] = 0;
+    }
+    rp[c + 1] = (int)cols.size();
+  }
+  L.nnzb = (int)cols.size();
+  L.row_ptr.ensure(sizeof(int) * ((size_t)n_c + 1));
+  L.cols.ensure(sizeof(int) * (size_t)std::max(L.nnzb, 1));
+  L.W.ensure(sizeof(long long) * (size_t)std::max(L.nnzb, 1));
+  BA_CUDA(cudaMemcpyAsync(L.row_ptr.p, rp.data(), sizeof(int) * (n_c + 1), cudaMemcpyHostToDevice, P->stream));
+  if (L.nnzb) {
+    BA_CUDA(cudaMemcpyAsync(L.cols.p, cols.data(), sizeof(int) * L.nnzb, cudaMemcpyHostToDevice, P->stream));
+    BA_CUDA(cudaMemcpyAsync(L.W.p, W.data(), sizeof(long long) * L.nnzb, cudaMemcpyHostToDevice, P->stream));
+  }
+  sync(P);
+}
+
 void covisibility_level0(ba_problem* P, Level& L) {
   L.n = P->n_c;
   L.bs = 9;
+  if (partitioned(P)) {
+    covisibility_level0_host(P, L);
+    return;
+  }
   const int H = hash_size(std::min(P->n_c, std::max(P->max_row_contrib, 1)));
   row_hash<0>(P, P->n_c, H, P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->pt_ptr.as<int>(),
               P->obs_pt.as<int>(), P->obs_cam.as<int>(), nullptr, L);

@@ -105,6 +105,26 @@ void fetch_scalars(ba_problem* P, int first, int count) {
   sync(P);
 }
 
+void part_allreduce(ba_problem* P, double* dev, size_t n) {
+  if (!P->part_fn || n == 0) return;
+  P->part_buf.resize(n);
+  BA_CUDA(cudaMemcpyAsync(P->part_buf.data(), dev, sizeof(double) * n, cudaMemcpyDeviceToHost, P->stream));
+  sync(P);
+  BA_REQUIRE(P->part_fn(P->part_buf.data(), n, P->part_user) == 0, BA_ERR_STATE, "the all-reduce hook failed");
+  BA_CUDA(cudaMemcpyAsync(dev, P->part_buf.data(), sizeof(double) * n, cudaMemcpyHostToDevice, P->stream));
+  sync(P);
+}
+
+double fetch_sum(ba_problem* P, int slot) {
+  fetch_scalars(P, slot, 1);
+  if (P->part_fn) {
+    double v = P->h_scal[slot];
+    BA_REQUIRE(P->part_fn(&v, 1, P->part_user) == 0, BA_ERR_STATE, "the all-reduce hook failed");
+    P->h_scal[slot] = v;
+  }
+  return P->h_scal[slot];
+}
+
 void clear_flags(ba_problem* P) {
   BA_CUDA(cudaMemsetAsync(P->flags.p, 0, sizeof(int) * F_COUNT, P->stream));
 }
@@ -113,6 +133,14 @@ void check_flags(ba_problem* P) {
   BA_CUDA(cudaMemcpyAsync(P->h_flags, P->flags.p, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost,
                           P->stream));
   sync(P);
+  if (P->part_fn) {
+    // partitioned solve: every rank raises the same error at the same point (a rank that
+    // stopped alone would leave the others waiting in their next reduction)
+    double fs[F_COUNT];
+    for (int i = 0; i < F_COUNT; ++i) fs[i] = P->h_flags[i];
+    BA_REQUIRE(P->part_fn(fs, F_COUNT, P->part_user) == 0, BA_ERR_STATE, "the all-reduce hook failed");
+    for (int i = 0; i < F_COUNT; ++i) P->h_flags[i] = fs[i] > 0.0 ? 1 : 0;
+  }
   const int* f = P->h_flags;
   if (f[F_HASH_OVERFLOW])
     throw Error(BA_ERR_LIMIT, "a covisibility row has more distinct neighbours than the hash capacity");

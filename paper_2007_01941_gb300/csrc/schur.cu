@@ -86,7 +86,9 @@ __global__ void k_camera_setup(const double* __restrict__ F, const double* __res
                                const int* __restrict__ obs_pt, const double* __restrict__ wp,
                                size_t ldp, int n_c, double lambda, int damp_identity,
                                double* __restrict__ Dc, float* __restrict__ Dc32,
-                               double* __restrict__ gc, double* __restrict__ rhs) {
+                               double* __restrict__ gc, double* __restrict__ rhs, int raw_diag) {
+  // raw_diag (partitioned solve): Dc receives this rank's share of diag(J^T J); the damping
+  // is applied once the shares are summed (k_finalize_damping)
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= n_c) return;
@@ -117,7 +119,7 @@ __global__ void k_camera_setup(const double* __restrict__ F, const double* __res
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      const double d = damp_identity ? lambda : lambda * fmax(dg[k], 1e-6);
+      const double d = raw_diag ? dg[k] : (damp_identity ? lambda : lambda * fmax(dg[k], 1e-6));
       Dc[9 * c + k] = d;
       Dc32[9 * c + k] = (float)d;
       gc[9 * c + k] = g[k];
@@ -179,7 +181,7 @@ __global__ void k_scc(const T* __restrict__ F, const T* __restrict__ E, size_t l
     for (int a = 0; a < 9; ++a)
       for (int b = a; b < 9; ++b) {
         double v = (double)acc[t++];
-        if (a == b) v += Dc[9 * c + a];
+        if (a == b && Dc) v += Dc[9 * c + a];
         out[9 * a + b] = v;
         out[9 * b + a] = v;
       }
@@ -722,6 +724,22 @@ __global__ void k_precond_shift(int n, float s, int damp_identity, const float* 
   Dc32[i] += v;
 }
 
+// partitioned solve: D_c from the summed diag(J^T J), and its addition to the summed S_cc
+__global__ void k_finalize_damping(int n, double lambda, int damp_identity, double* __restrict__ Dc,
+                                   float* __restrict__ Dc32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double d = damp_identity ? lambda : lambda * fmax(Dc[i], 1e-6);
+  Dc[i] = d;
+  Dc32[i] = (float)d;
+}
+
+__global__ void k_scc_add_damping(int n_c, const double* __restrict__ Dc, double* __restrict__ Scc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 9 * n_c) return;
+  Scc[81 * (size_t)(i / 9) + 10 * (i % 9)] += Dc[i];
+}
+
 __global__ void k_add_block_diag(int n_c, const double* __restrict__ Scc, const float* __restrict__ pcd,
                                  double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -780,8 +798,17 @@ void schur_setup(ba_problem* P, double lambda) {
     k_camera_setup<<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
         jacobian64(P), jacobian64(P), P->fres.as<double>(), P->ld, P->cam_ptr.as<int>(),
         P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->wp.as<double>(), ldp, n_c, lambda, damp_id,
-        P->Dc.as<double>(), P->Dc32.as<float>(), P->gc.as<double>(), P->rhs.as<double>());
+        P->Dc.as<double>(), P->Dc32.as<float>(), P->gc.as<double>(), P->rhs.as<double>(), partitioned(P) ? 1 : 0);
   launched(P);
+  if (partitioned(P)) {
+    // the camera sums over all ranks' points, then the damping from the summed diagonal
+    part_allreduce(P, P->Dc.as<double>(), 9 * (size_t)n_c);
+    part_allreduce(P, P->gc.as<double>(), 9 * (size_t)n_c);
+    part_allreduce(P, P->rhs.as<double>(), 9 * (size_t)n_c);
+    k_finalize_damping<<<cdiv(9 * n_c, 256), 256, 0, P->stream>>>(9 * n_c, lambda, damp_id, P->Dc.as<double>(),
+                                                                   P->Dc32.as<float>());
+    launched(P);
+  }
   // point-block-Jacobi blocks S_cc (in the mode's storage precision) and FP64 inverses
   double* Scc = P->Scc.as<double>();
   if (mixed)
@@ -792,8 +819,14 @@ void schur_setup(ba_problem* P, double lambda) {
   else
     k_scc<double><<<cdiv((long long)n_c * 32, 128), 128, 0, P->stream>>>(
         P->J64.as<double>(), P->J64.as<double>(), P->ld, P->Cinv64.as<double>(), ldp,
-        P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->Dc.as<double>(), n_c, Scc);
+        P->cam_ptr.as<int>(), P->cam_obs.as<int>(), P->obs_pt.as<int>(),
+        partitioned(P) ? nullptr : P->Dc.as<double>(), n_c, Scc);
   launched(P);
+  if (partitioned(P)) {
+    part_allreduce(P, Scc, 81 * (size_t)n_c);
+    k_scc_add_damping<<<cdiv(9 * n_c, 256), 256, 0, P->stream>>>(n_c, P->Dc.as<double>(), Scc);
+    launched(P);
+  }
   // mixed precision: the FP32 hierarchy's extra damping below precond_lambda_min
   const double mu = P->opt.precond_lambda_min;
   P->pc_shift = mixed && mu > lambda;
@@ -1534,9 +1567,11 @@ static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
     if (pass == 1) {
       // work items in decreasing order of their pair counts, so that the longest blocks
       // start first and the grid's tail is short (each block's own pair order is kept).
-      // Block-row order, which keeps the blocks that share W rows together in L2, was
-      // measured slower (0.37 -> 0.59 ms on the street chain): the tail costs more than
-      // the re-reads
+      // This order re-reads each W row from DRAM about k_p - 1 times (4x the algorithmic
+      // bytes), but the two orders that keep the blocks sharing a row together were both
+      // slower on the street chain: block-row order 0.59 ms, groups of 256 block rows each
+      // in decreasing pair count 0.52 ms, against 0.37 ms (3.6 against 4.8 and 3.7 ms on
+      // the city grid)
       std::vector<int> perm(n_up), rank(n_up);
       for (int u = 0; u < n_up; ++u) perm[u] = u;
       std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return cnt[a + 1] > cnt[b + 1]; });
@@ -1579,6 +1614,22 @@ static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
   }
   L0.n_up = n_up;
   sync(P);
+}
+
+// partitioned solve: after the ranks' block shares are summed, the diagonal blocks (copied
+// from S_cc, which every rank already holds summed) are written again
+__global__ void k_restore_diag_blocks(int n_c, const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                                      const double* __restrict__ Scc, double* __restrict__ vals) {
+  const int c = blockIdx.x;
+  __shared__ int diag;
+  if (threadIdx.x == 0) {
+    diag = -1;
+    for (int e = row_ptr[c]; e < row_ptr[c + 1]; ++e)
+      if (cols[e] == c) diag = e;
+  }
+  __syncthreads();
+  if (diag < 0) return;
+  for (int i = threadIdx.x; i < 81; i += blockDim.x) vals[81 * (size_t)diag + i] = Scc[81 * (size_t)c + i];
 }
 
 void explicit_schur(ba_problem* P, Level& L0, ExplicitMode mode) {
@@ -1630,6 +1681,12 @@ void explicit_schur(ba_problem* P, Level& L0, ExplicitMode mode) {
         L0.pair_ptr.as<int>(), L0.pairs.as<int2>(), P->Scc.as<double>(), nullptr, L0.vals64.as<double>());
   }
   launched(P);
+  if (partitioned(P) && mode == EX_FP64) {
+    part_allreduce(P, L0.vals64.as<double>(), 81 * (size_t)L0.nnzb);
+    k_restore_diag_blocks<<<P->n_c, 128, 0, P->stream>>>(P->n_c, L0.row_ptr.as<int>(), L0.cols.as<int>(),
+                                                          P->Scc.as<double>(), L0.vals64.as<double>());
+    launched(P);
+  }
 }
 
 // ---------------------------------------------------------------------------

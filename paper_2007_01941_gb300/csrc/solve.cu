@@ -950,9 +950,8 @@ k_model_terms(int n_c9, const double* __restrict__ dc, const double* __restrict_
 void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double* lam, int* accepted,
              double* cost_out) {
   linearize(P, cams, pts, obs);
-  fetch_scalars(P, S_COST, 1);
   check_flags(P);
-  const double cost0 = P->h_scal[S_COST];
+  const double cost0 = fetch_sum(P, S_COST);
   P->cost = cost0;
   const size_t nc = (size_t)P->n_c * 9, np = (size_t)P->n_p * 3;
   P->delta_c.ensure(sizeof(double) * nc + 64);
@@ -996,13 +995,28 @@ void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double
     launched(P);
   }
   const double cost1 = cost_at(P, cams1, pts1, obs);
-  k_model_terms<<<reduce_blocks(P, nc + np), kVecBS, 0, P->stream>>>(
-      (int)nc, P->delta_c.as<double>(), P->gc.as<double>(), P->Dc.as<double>(), P->n_p, P->ldp,
-      P->delta_p.as<double>(), P->gp.as<double>(), P->Dp.as<double>(), P->partial.as<double>(),
-      P->counter.as<unsigned>(), P->scal.as<double>() + S_MODEL);
-  launched(P);
-  fetch_scalars(P, S_MODEL, 1);
-  const double model = 0.5 * P->h_scal[S_MODEL];
+  // the model decrease 1/2 (delta.g + delta.D.delta); partitioned: the point terms are this
+  // rank's share (summed over the ranks), the camera terms are the same on every rank
+  auto model_terms = [&](int n_c9, int n_pts) {
+    k_model_terms<<<reduce_blocks(P, (size_t)n_c9 + 3 * (size_t)n_pts), kVecBS, 0, P->stream>>>(
+        n_c9, P->delta_c.as<double>(), P->gc.as<double>(), P->Dc.as<double>(), n_pts, P->ldp,
+        P->delta_p.as<double>(), P->gp.as<double>(), P->Dp.as<double>(), P->partial.as<double>(),
+        P->counter.as<unsigned>(), P->scal.as<double>() + S_MODEL);
+    launched(P);
+  };
+  double model_sum;
+  if (partitioned(P)) {
+    model_terms(0, P->n_p);
+    model_sum = fetch_sum(P, S_MODEL);
+    model_terms((int)nc, 0);
+    fetch_scalars(P, S_MODEL, 1);
+    model_sum += P->h_scal[S_MODEL];
+  } else {
+    model_terms((int)nc, P->n_p);
+    fetch_scalars(P, S_MODEL, 1);
+    model_sum = P->h_scal[S_MODEL];
+  }
+  const double model = 0.5 * model_sum;
   const double rho = model > 0.0 ? (cost0 - cost1) / model : -INFINITY;
   if (rho > 1e-3 && std::isfinite(cost1)) {
     BA_CUDA(cudaMemcpyAsync(cams, cams1, sizeof(double) * nc, cudaMemcpyDeviceToDevice, P->stream));
