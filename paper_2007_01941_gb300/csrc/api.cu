@@ -174,6 +174,12 @@ ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx, co
 void ba_destroy(ba_problem* P) {
   if (!P) return;
   cudaStreamSynchronize(P->stream);
+  if (P->side_stream) {
+    cudaStreamSynchronize(P->side_stream);
+    cudaStreamDestroy(P->side_stream);
+    cudaEventDestroy(P->ev_fork);
+    cudaEventDestroy(P->ev_join);
+  }
   ba::DBuf* bufs[] = {&P->obs_user, &P->obs_cam, &P->obs_ptu, &P->obs_pt, &P->pt_ptr, &P->pt_user, &P->cam_ptr,
                       &P->cam_obs, &P->tile_pt, &P->tile_desc, &P->tile_perm, &P->lz_vec, &P->lz_red, &P->lz_cnt, &P->lz_ptr, &P->chunk_tile, &P->chunk_cam, &P->camx, &P->fres, &P->J64,
                       &P->J64, &P->J32, &P->J32lo, &P->cams_lin, &P->pts_lin, &P->obs_lin, &P->Dc, &P->Dp,

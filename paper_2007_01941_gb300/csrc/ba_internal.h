@@ -239,6 +239,10 @@ struct ba_problem {
   bool graphs_ok = true;        // false after a failed build: eager fallback
   long long pcg_graph_head = 0, pcg_graph_body = 0;  // kernels per graph part
 
+  // side stream of the multigrid setup (the prolongator QR chain runs beside the assembly)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
   // point-partitioned solve: the all-reduce hook and the whole problem's observation graph
   // (host, global point ids), from which the level-0 covisibility is built
   ba_allreduce_fn part_fn = nullptr;

@@ -1683,6 +1683,53 @@ static void mg_symbolic(ba_problem* P) {
   P->sym_ready = true;
 }
 
+// The near-nullspace of level 0 and every level's per-aggregate QR (Section 3.3): they need
+// only the cameras and the aggregates, not the operators, so they run on the side stream
+// while the main stream assembles S.
+static void prolongator_chain(ba_problem* P, cudaStream_t st) {
+  const bool fp32 = level_fp32(P);
+  Level& L0 = P->levels[0];
+  L0.K.ensure(sizeof(double) * 9 * kNull * (size_t)P->n_c + 64);
+  // one warp per CTA: the cameras' FP64 work spread over as many SMs as possible
+  k_nullspace0<<<cdiv(P->n_c, 32), 32, 0, st>>>(P->cams_lin.as<double>(), P->n_c, L0.K.as<double>());
+  launched(P);
+  L0.kept.ensure(sizeof(unsigned) * P->n_c + 64);
+  BA_CUDA(cudaMemsetAsync(L0.kept.p, 0xff, sizeof(unsigned) * P->n_c, st));
+  for (int l = 0; l < P->n_levels; ++l) {
+    Level& L = P->levels[l];
+    if (L.coarsest) break;
+    Level& L1 = P->levels[l + 1];
+    // QR prolongators, coarse nullspace and kept masks
+    L.Q64.ensure(sizeof(double) * L.bs * kNull * (size_t)L.n + 64);
+    L.Q32.ensure(sizeof(float) * L.bs * kNull * (size_t)L.n + 64);
+    L1.K.ensure(sizeof(double) * kNull * kNull * (size_t)L1.n + 64);
+    L1.kept.ensure(sizeof(unsigned) * (size_t)L1.n + 64);
+    const int max_rows = std::max(1, L.agg_max) * L.bs;
+    const size_t qsm = sizeof(double) * (size_t)kQrWarps * max_rows * kQrStride;
+    BA_REQUIRE(qsm <= 200 * 1024, BA_ERR_LIMIT, "aggregates too large for the aggregate QR");
+    if (fp32) {
+      // mixed precision: the DF factorisation, one CTA per aggregate at every level
+      const size_t dsm = sizeof(float2) * (size_t)max_rows * kQrStride;
+      BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr_df_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+      k_aggregate_qr_df_cta<<<L1.n, kQrDfBS, dsm, st>>>(
+          L1.n, L.bs, L.agg_ptr.as<int>(), L.agg_mem.as<int>(), L.K.as<double>(), L.Q64.as<double>(),
+          L.Q32.as<float>(), L1.K.as<double>(), L1.kept.as<unsigned>());
+    } else if (L1.n >= 2 * P->n_sm) {
+      BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
+      k_aggregate_qr<<<cdiv(L1.n, kQrWarps), kQrWarps * 32, qsm, st>>>(
+          L1.n, L.bs, max_rows, L.agg_ptr.as<int>(), L.agg_mem.as<int>(), L.K.as<double>(), L.Q64.as<double>(),
+          L.Q32.as<float>(), L1.K.as<double>(), L1.kept.as<unsigned>());
+    } else {
+      const size_t csm = sizeof(double) * (size_t)max_rows * kQrStride;
+      BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+      k_aggregate_qr_cta<<<L1.n, kQrBS, csm, st>>>(L1.n, L.bs, L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
+                                                          L.K.as<double>(), L.Q64.as<double>(), L.Q32.as<float>(),
+                                                          L1.K.as<double>(), L1.kept.as<unsigned>());
+    }
+    launched(P);
+  }
+}
+
 void mg_setup(ba_problem* P) {
   const bool fp32 = level_fp32(P);
   const ba_options& o = P->opt;
@@ -1700,6 +1747,17 @@ void mg_setup(ba_problem* P) {
                      (o.level0_operator == BA_OP_AUTO && explicit_bytes < implicit_bytes);
     P->outer_explicit = P->l0_explicit;
   }
+  // the prolongators beside the assembly: fork the side stream after everything the main
+  // stream has queued (the cameras of the linearisation, the aggregates)
+  if (!P->side_stream) {
+    BA_CUDA(cudaStreamCreateWithFlags(&P->side_stream, cudaStreamNonBlocking));
+    BA_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+    BA_CUDA(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+  }
+  BA_CUDA(cudaEventRecord(P->ev_fork, P->stream));
+  BA_CUDA(cudaStreamWaitEvent(P->side_stream, P->ev_fork, 0));
+  prolongator_chain(P, P->side_stream);
+  BA_CUDA(cudaEventRecord(P->ev_join, P->side_stream));
   // the Galerkin product needs S assembled in any case; the PCG product needs its FP64
   // value, which mixed precision forms in paired FP32
   explicit_schur(P, L0, !fp32 ? EX_FP64 : P->outer_explicit ? EX_PAIRED : EX_FP32);
@@ -1710,15 +1768,10 @@ void mg_setup(ba_problem* P) {
   BA_CUDA(cudaMemcpyAsync(L0.Dblk.p, P->Scc.p, sizeof(double) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
   BA_CUDA(cudaMemcpyAsync(L0.Dinv64.p, P->Scc_inv.p, sizeof(double) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
   BA_CUDA(cudaMemcpyAsync(L0.Dinv32.p, P->Scc_inv32.p, sizeof(float) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
-  L0.K.ensure(sizeof(double) * 9 * kNull * (size_t)P->n_c + 64);
-  // one warp per CTA: the cameras' FP64 work spread over as many SMs as possible
-  k_nullspace0<<<cdiv(P->n_c, 32), 32, 0, P->stream>>>(P->cams_lin.as<double>(), P->n_c, L0.K.as<double>());
-  launched(P);
-  L0.kept.ensure(sizeof(unsigned) * P->n_c + 64);
-  BA_CUDA(cudaMemsetAsync(L0.kept.p, 0xff, sizeof(unsigned) * P->n_c, P->stream));
 
   const bool batch_inv = P->opt.precision == BA_MIXED;
   BlockInvBatch inv{};
+  BA_CUDA(cudaStreamWaitEvent(P->stream, P->ev_join, 0));
   for (int l = 0; l < P->n_levels; ++l) {
     Level& L = P->levels[l];
     if (l > 0) {
@@ -1764,34 +1817,6 @@ void mg_setup(ba_problem* P) {
       else lanczos<double>(P, l);
     }
     Level& L1 = P->levels[l + 1];
-    // QR prolongators, coarse nullspace and kept masks
-    L.Q64.ensure(sizeof(double) * L.bs * kNull * (size_t)L.n + 64);
-    L.Q32.ensure(sizeof(float) * L.bs * kNull * (size_t)L.n + 64);
-    L1.K.ensure(sizeof(double) * kNull * kNull * (size_t)L1.n + 64);
-    L1.kept.ensure(sizeof(unsigned) * (size_t)L1.n + 64);
-    const int max_rows = std::max(1, L.agg_max) * L.bs;
-    const size_t qsm = sizeof(double) * (size_t)kQrWarps * max_rows * kQrStride;
-    BA_REQUIRE(qsm <= 200 * 1024, BA_ERR_LIMIT, "aggregates too large for the aggregate QR");
-    if (fp32) {
-      // mixed precision: the DF factorisation, one CTA per aggregate at every level
-      const size_t dsm = sizeof(float2) * (size_t)max_rows * kQrStride;
-      BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr_df_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
-      k_aggregate_qr_df_cta<<<L1.n, kQrDfBS, dsm, P->stream>>>(
-          L1.n, L.bs, L.agg_ptr.as<int>(), L.agg_mem.as<int>(), L.K.as<double>(), L.Q64.as<double>(),
-          L.Q32.as<float>(), L1.K.as<double>(), L1.kept.as<unsigned>());
-    } else if (L1.n >= 2 * P->n_sm) {
-      BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsm));
-      k_aggregate_qr<<<cdiv(L1.n, kQrWarps), kQrWarps * 32, qsm, P->stream>>>(
-          L1.n, L.bs, max_rows, L.agg_ptr.as<int>(), L.agg_mem.as<int>(), L.K.as<double>(), L.Q64.as<double>(),
-          L.Q32.as<float>(), L1.K.as<double>(), L1.kept.as<unsigned>());
-    } else {
-      const size_t csm = sizeof(double) * (size_t)max_rows * kQrStride;
-      BA_CUDA(cudaFuncSetAttribute(k_aggregate_qr_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
-      k_aggregate_qr_cta<<<L1.n, kQrBS, csm, P->stream>>>(L1.n, L.bs, L.agg_ptr.as<int>(), L.agg_mem.as<int>(),
-                                                          L.K.as<double>(), L.Q64.as<double>(), L.Q32.as<float>(),
-                                                          L1.K.as<double>(), L1.kept.as<unsigned>());
-    }
-    launched(P);
     // Galerkin from A P (which the fused V-cycle also uses)
     build_ap(P, L);
     if (!L.gal_ptr.p) galerkin_symbolic(P, L, L1);
