@@ -116,6 +116,10 @@ typedef struct {
                            about 1e-6 the damping that keeps S's near-null (gauge) eigenvalues
                            apart from zero falls under the FP32 rounding of S's entries and the
                            FP32 hierarchy stops preconditioning (1e-5; 0 disables) */
+  int schur_staging;    /* FP32 implicit product (BA_OP_IMPLICIT in BA_MIXED): 1 stages each warp's
+                           coming observation records into a double buffer in shared memory with
+                           asynchronous bulk copies; 0 loads them straight into registers, which
+                           keeps twice the warps resident and is faster (0) */
 } ba_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
                 ("level0_operator", c_int), ("fused_vcycle", c_int), ("outer_product", c_int),
                 ("stop_rule", c_int), ("tau", c_double), ("overlap_launches", c_int),
                 ("loss", c_int), ("loss_scale", c_double),
-                ("precond_lambda_min", c_double)]
+                ("precond_lambda_min", c_double), ("schur_staging", c_int)]
 
 
 class Info(ctypes.Structure):

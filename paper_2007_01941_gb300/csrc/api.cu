@@ -106,6 +106,7 @@ void ba_default_options(ba_options* o) {
   o->loss = BA_LOSS_SQUARED;
   o->loss_scale = 1.0;
   o->precond_lambda_min = 1e-5;
+  o->schur_staging = 0;
 }
 
 size_t ba_struct_size(int which) {
@@ -147,6 +148,7 @@ ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx, co
                BA_ERR_INVALID_ARG, "bad loss / loss_scale");
     BA_REQUIRE(o.precond_lambda_min >= 0.0 && std::isfinite(o.precond_lambda_min), BA_ERR_INVALID_ARG,
                "bad precond_lambda_min");
+    BA_REQUIRE(o.schur_staging == 0 || o.schur_staging == 1, BA_ERR_INVALID_ARG, "bad schur_staging");
     int dev = 0;
     BA_CUDA(cudaGetDevice(&dev));
     BA_CUDA(cudaDeviceGetAttribute(&P->n_sm, cudaDevAttrMultiProcessorCount, dev));

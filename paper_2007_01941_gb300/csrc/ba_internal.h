@@ -100,6 +100,7 @@ enum Flag : int {
   F_BREAKDOWN = 3,
   F_HASH_OVERFLOW = 4,
   F_NONFINITE = 5,
+  F_WAIT_TIMEOUT = 6,   // a bounded wait in a kernel gave up (its results are not valid)
   F_COUNT = 8
 };
 
@@ -158,6 +159,7 @@ struct ba_problem {
   ba::DBuf cam_ptr, cam_obs;    // camera-major CSR over internal obs
   int n_tiles = 0, n_chunks = 0, k3_window = 0;
   int k3_grid[2] = {0, 0};       // Schur product CTAs per launch (FP32, FP64), set at first use
+  int k3_grid_bulk = 0;          // the same for the FP32 product with bulk-staged records
   int k3_grid_df = 0;           // the same for the paired-FP32 product
   int k3_grid_rc = 0;           // the same for the FP64 product in recompute mode
   bool l0_explicit = false;     // V-cycle level 0 uses the assembled S (set by the multigrid setup)

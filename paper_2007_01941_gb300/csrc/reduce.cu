@@ -149,6 +149,7 @@ void check_flags(ba_problem* P) {
   if (f[F_NOT_SPD_JACOBI]) throw Error(BA_ERR_NOT_SPD, "a block-Jacobi diagonal block is not positive definite");
   if (f[F_NOT_SPD_COARSE]) throw Error(BA_ERR_NOT_SPD, "the coarsest operator is not positive definite");
   if (f[F_BREAKDOWN]) throw Error(BA_ERR_BREAKDOWN, "PCG breakdown");
+  if (f[F_WAIT_TIMEOUT]) throw Error(BA_ERR_CUDA, "a kernel's bounded wait for its staged data gave up");
 }
 
 }  // namespace ba

@@ -874,6 +874,41 @@ __device__ __forceinline__ int rot_index(int rot, int k) {
   return j >= 9 ? j - 9 : j;
 }
 
+// Bulk staging of the FP32 product's records (one 1-D cp.async.bulk per warp tile into
+// shared memory, completion counted on an mbarrier).  Every wait has an iteration limit,
+// after which the kernel sets F_WAIT_TIMEOUT and goes on without the data.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* m) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(m)) : "memory");
+}
+
+// lane-0 issue of a bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned),
+// after the warp's reads of the destination (generic proxy) and before the copy's writes
+// (async proxy)
+__device__ __forceinline__ void bulk_stage(void* dst, const void* src, unsigned bytes, unsigned long long* m) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(m))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long* m, unsigned parity) {
+  const unsigned a = smem_addr(m);
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // Recompute mode of the product (FP64): instead of streaming each observation's stored
 // record (192 bytes), F and E are rebuilt in registers from the camera's rotation data and
 // parameters (read from L2: few cameras) and the point (shared by the point's lanes), the
@@ -928,18 +963,50 @@ __device__ __forceinline__ void k3_scatter(T* acc, T* __restrict__ y, int c, int
   for (int k = 0; k < 9; ++k) atomicAdd(dst + rot_index(rot, k), yv[k]);
 }
 
-template <typename T, bool WINDOW, bool RECOMP = false>
-__global__ void __launch_bounds__(kK3Warps * 32, sizeof(T) == 4 ? 4 : (RECOMP ? 2 : 3))
+// STAGES > 0 (BULK; FP32 with the camera window): each warp stages the records of its
+// coming tiles (at most 32 x 96 contiguous bytes each) into a ring of STAGES shared-memory
+// buffers with 1-D bulk copies, STAGES - 1 tiles ahead of the one it reduces, so the
+// record stream stays in flight without holding registers.  stage_off: byte offset of the
+// buffers after the camera window; then kK3Warps x STAGES buffers, then as many mbarriers.
+// Measured on the street chain and the city grid, the ring costs the product a third of its
+// speed: its shared memory halves the resident warps, and the tile reduction, not the load
+// latency, bounds the product (register loads keep 32 warps per SM).
+constexpr int kK3StageFloats = 32 * kRec;   // one buffer: 32 records
+constexpr int kK3BulkStages = 2;
+
+template <typename T, bool WINDOW, bool RECOMP = false, int STAGES = 0>
+__global__ void __launch_bounds__(kK3Warps * 32, STAGES ? 2 : (sizeof(T) == 4 ? 4 : (RECOMP ? 2 : 3)))
 k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, int ld,
                const T* __restrict__ Cinv, int ldp, const int* __restrict__ obs_cam,
                const int4* __restrict__ tile_desc, const unsigned char* __restrict__ tile_perm,
                const int* __restrict__ chunk_tile, const int* __restrict__ chunk_cam, int n_chunks, const T* __restrict__ x,
-               T* __restrict__ y, int win, int reverse, RecompSrc rs) {
+               T* __restrict__ y, int win, int reverse, RecompSrc rs, int stage_off, int* flags) {
+  constexpr bool BULK = STAGES > 0;
+  constexpr int kK3Stages = BULK ? STAGES : 1;
   static_assert(!RECOMP || sizeof(T) == 8, "the recompute mode is the FP64 product");
+  static_assert(!BULK || (sizeof(T) == 4 && WINDOW && !RECOMP), "bulk staging is for the FP32 product");
   constexpr bool kPermute = sizeof(T) == 4;
-  extern __shared__ __align__(16) unsigned char k3_smem[];
+  extern __shared__ __align__(128) unsigned char k3_smem[];
   T* acc = reinterpret_cast<T*>(k3_smem);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // BULK: narrow tiles take the buffers in turn, in the order the warp visits its tiles;
+  // the producer (pbuf) runs kK3Stages - 1 narrow tiles ahead of the consumer (cbuf)
+  float* stage = nullptr;
+  unsigned long long* mbar = nullptr;
+  int pbuf = 0, cbuf = 0;
+  unsigned ph = 0;        // bit b: parity of buffer b's next phase
+  unsigned pending = 0;   // bit b: a copy into buffer b not yet waited for
+  bool stalled = false;   // a wait ran out: stage nothing more
+  if constexpr (BULK) {
+    stage = reinterpret_cast<float*>(k3_smem + stage_off) + (size_t)warp * kK3Stages * kK3StageFloats;
+    mbar = reinterpret_cast<unsigned long long*>(k3_smem + stage_off +
+                                                 sizeof(float) * kK3Warps * kK3Stages * kK3StageFloats) +
+           kK3Stages * warp;
+    if (lane == 0)
+      for (int b = 0; b < kK3Stages; ++b) mbar_init(mbar + b);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+  }
   // a CTA takes chunks blockIdx.x, blockIdx.x + gridDim.x, ...: the grid is one wave of
   // resident CTAs and the chunks are small enough to balance the SMs
   for (int chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
@@ -953,8 +1020,27 @@ k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, int ld,
     // reverse != 0 walks the chunk's tiles from its end, where the previous product left
     // the most recently used lines in L2
     const int t_begin = chunk_tile[chunk], t_end = chunk_tile[chunk + 1];
+    // BULK: stage the chunk's i-th tile if it exists and is narrow (a point with more than
+    // 32 observations is read directly); its buffer held the narrow tile kK3Stages before,
+    // which this warp has finished
+    auto stage_tile = [&](int i) {
+      if (i >= t_end - t_begin) return;
+      const int4 d = __ldg(tile_desc + (reverse ? t_end - 1 - i : t_begin + i));
+      if (d.y > 32) return;
+      const int b = pbuf;
+      pbuf = pbuf + 1 == kK3Stages ? 0 : pbuf + 1;
+      if (stalled) return;
+      pending |= 1u << b;
+      if (lane == 0)
+        bulk_stage(stage + (size_t)b * kK3StageFloats, F + (size_t)d.x * kRec, (unsigned)(d.y * kRec * 4), mbar + b);
+    };
+    if constexpr (BULK) {
+#pragma unroll
+      for (int s = 0; s < kK3Stages - 1; ++s) stage_tile(warp + s * kK3Warps);
+    }
     for (int i = warp; i < t_end - t_begin; i += kK3Warps) {
       const int t = reverse ? t_end - 1 - i : t_begin + i;
+      if constexpr (BULK) stage_tile(i + (kK3Stages - 1) * kK3Warps);
       const int4 desc = __ldg(tile_desc + t);
       const unsigned pb = kPermute ? (unsigned)__ldg(tile_perm + (size_t)t * 32 + lane) : 0u;
       const int ob = desc.x, nobs = desc.y, p0 = desc.z;
@@ -984,6 +1070,33 @@ k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, int ld,
         T f[18], e[6];
         if constexpr (RECOMP) {
           recompute_record(rs, o, c, f, e);
+        } else if constexpr (BULK) {
+          const int b = cbuf;
+          cbuf = cbuf + 1 == kK3Stages ? 0 : cbuf + 1;
+          bool ok = false;
+          if (!stalled) {
+            ok = mbar_wait(mbar + b, (ph >> b) & 1u);
+            if (ok) {
+              ph ^= 1u << b;
+              pending &= ~(1u << b);
+            } else {
+              stalled = true;
+              if (lane == 0) atomicExch(flags + F_WAIT_TIMEOUT, 1);
+            }
+          }
+          // every lane reads a record it owns (inactive lanes: the tile's first)
+          const float4* r = reinterpret_cast<const float4*>(stage + (size_t)b * kK3StageFloats +
+                                                            (size_t)(active ? lane : 0) * kRec);
+          float t[24];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            const float4 q = ok ? r[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+            t[4 * k] = q.x, t[4 * k + 1] = q.y, t[4 * k + 2] = q.z, t[4 * k + 3] = q.w;
+          }
+#pragma unroll
+          for (int k = 0; k < 18; ++k) f[k] = t[k];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) e[k] = t[18 + k];
         } else if constexpr (kPermute) {
           load_record(F + (size_t)o * kRec, f, e);
         } else {
@@ -1068,6 +1181,8 @@ k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, int ld,
         } else if (active) {
           k3_scatter<T, WINDOW>(acc, y, c, cam_lo, span, yv, rot);
         }
+        // BULK: every lane has read this buffer before the next staging refills it
+        if constexpr (BULK) __syncwarp();
       } else {
         // one point with more than 32 observations
         const int ip = p0;
@@ -1141,12 +1256,44 @@ k_schur_matvec(const T* __restrict__ F, const T* __restrict__ E, int ld,
       __syncthreads();
     }
   }
+  // BULK: after a wait that ran out, let the copies still in flight land (again bounded)
+  // before the CTA's shared memory is released
+  if constexpr (BULK) {
+    for (int b = 0; b < kK3Stages; ++b)
+      if ((pending >> b) & 1u) (void)mbar_wait(mbar + b, (ph >> b) & 1u);
+  }
 }
 
 template <typename TD, typename T>
 __global__ void k_diag_init(const TD* __restrict__ Dc, const T* __restrict__ x, T* __restrict__ y, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = (T)Dc[i] * x[i];
+}
+
+// the FP32 product with STAGES record buffers per warp
+template <int STAGES>
+static void launch_bulk(ba_problem* P, const float* F, const float* Cinv, const float* x, float* y) {
+  auto kern = k_schur_matvec<float, true, false, STAGES>;
+  // window, then the warps' record buffers (16-byte aligned), then their mbarriers
+  const int stage_off = (int)((sizeof(float) * 9 * (size_t)P->k3_window + 127) / 128 * 128);
+  const size_t smem_b = stage_off + sizeof(float) * kK3Warps * STAGES * kK3StageFloats +
+                        sizeof(unsigned long long) * kK3Warps * STAGES;
+  int& g = P->k3_grid_bulk;
+  if (g == 0) {
+    constexpr size_t kMax = sizeof(float) * 9 * 1024 + sizeof(float) * kK3Warps * STAGES * kK3StageFloats +
+                            sizeof(unsigned long long) * kK3Warps * STAGES;
+    BA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMax));
+    int per_sm = 0;
+    BA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kK3Warps * 32, smem_b));
+    g = std::max(1, std::min(P->n_chunks, P->n_sm * std::max(per_sm, 1)));
+  }
+  KernelTimer kt(P, BA_KT_SCHUR_FP32);
+  kern<<<g, kK3Warps * 32, smem_b, P->stream>>>(F, F, (int)P->ld, Cinv, (int)P->ldp, P->obs_cam.as<int>(),
+                                                P->tile_desc.as<int4>(), P->tile_perm.as<unsigned char>(),
+                                                P->chunk_tile.as<int>(), P->chunk_cam.as<int>(), P->n_chunks, x, y,
+                                                P->k3_window, (P->k3_calls++) & 1, RecompSrc{}, stage_off,
+                                                P->flags.as<int>());
+  launched(P);
 }
 
 template <typename T>
@@ -1183,8 +1330,14 @@ static void launch_matvec(ba_problem* P, const T* F, const T* E, const T* Cinv, 
       k_schur_matvec<double, false, true><<<g, kK3Warps * 32, 0, P->stream>>>(
           nullptr, nullptr, (int)P->ld, Cinv, (int)P->ldp, P->obs_cam.as<int>(), P->tile_desc.as<int4>(),
           P->tile_perm.as<unsigned char>(), P->chunk_tile.as<int>(), P->chunk_cam.as<int>(), P->n_chunks, x, y,
-          P->k3_window, (P->k3_calls++) & 1, rs);
+          P->k3_window, (P->k3_calls++) & 1, rs, 0, nullptr);
       launched(P);
+      return;
+    }
+  }
+  if constexpr (sizeof(T) == 4) {
+    if (P->opt.schur_staging) {
+      launch_bulk<kK3BulkStages>(P, F, Cinv, x, y);
       return;
     }
   }
@@ -1192,7 +1345,7 @@ static void launch_matvec(ba_problem* P, const T* F, const T* E, const T* Cinv, 
   k_schur_matvec<T, window><<<grid, kK3Warps * 32, smem, P->stream>>>(
       F, E, (int)P->ld, Cinv, (int)P->ldp, P->obs_cam.as<int>(), P->tile_desc.as<int4>(),
       P->tile_perm.as<unsigned char>(), P->chunk_tile.as<int>(), P->chunk_cam.as<int>(), P->n_chunks, x, y, P->k3_window,
-      (P->k3_calls++) & 1, RecompSrc{});
+      (P->k3_calls++) & 1, RecompSrc{}, 0, nullptr);
   launched(P);
 }
 

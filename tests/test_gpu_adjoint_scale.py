@@ -10,11 +10,12 @@ pass instead of reading them back.  Checked two ways:
     at random among those whose derivative stands above the differences' rounding
     floor, at damping lambda = 1e-2.  At the scene's lambda = 1e-4 the street chain's S
     is so ill-conditioned that central differences in FP64 cannot resolve 1e-5 even with
-    exact dense solves: the oracle's own differences of camera coordinates reach 2e-5
-    at best and 1e-3 at h = 1e-7, rounding amplified by kappa(S).  At lambda = 1e-2
-    they reach 4e-6 with h = 1e-5 (1e-6 already shows 3e-5 of rounding), so camera
-    coordinates take h = 1e-5 and observation coordinates, in which delta is linear
-    (no truncation error), h = 1e-6, each scaled by the coordinate's magnitude;
+    exact solves: the oracle's own differences of camera coordinates reach 2e-5 at best
+    and 1e-3 at h = 1e-7, rounding amplified by kappa(S).  Observation coordinates, in
+    which delta is linear, take plain central differences with h = 1e-6; camera
+    coordinates the fourth-order combination of central differences at h = 2e-5 and
+    2h (both scaled by the coordinate's magnitude), since delta is strongly nonlinear in
+    some of them;
   * the oracle's dense adjoint on the 200-camera / 10,000-point subscene, in FP64 and
     in mixed precision.
 """
@@ -68,8 +69,8 @@ def test_adjoint_matches_central_differences_at_street_chain_size(gpu, chain):
     go, gc, _ = prob.adjoint(vbar, want_pts=False)
     go, gc = _np(go), _np(gc)
 
-    def loss(c, p, o):
-        dc, dp, it, rel = prob.solve(c, p, o, lam)
+    def loss(cams, obs):
+        dc, dp, it, rel = prob.solve(cams, pts, obs, lam)
         assert rel <= 1e-13
         return float(torch.dot(vbar, torch.cat([dc.reshape(-1), dp.reshape(-1)])).item())
 
@@ -78,15 +79,25 @@ def test_adjoint_matches_central_differences_at_street_chain_size(gpu, chain):
         scale = np.abs(grad).max()
         for flat in _pick(rng, grad, 16):
             i, j = np.unravel_index(flat, grad.shape)
-            h = (1e-6 if which == "obs" else 1e-5) * max(1.0, abs(float(base[i, j])))
-            lp_args = {"cams": cams, "obs": obs}
-            plus = base.clone()
-            plus[i, j] += h
-            minus = base.clone()
-            minus[i, j] -= h
-            args_p = dict(lp_args, **{which: plus})
-            args_m = dict(lp_args, **{which: minus})
-            fd = (loss(args_p["cams"], pts, args_p["obs"]) - loss(args_m["cams"], pts, args_m["obs"])) / (2 * h)
+            def central(h):
+                args = {"cams": cams, "obs": obs}
+                plus, minus = base.clone(), base.clone()
+                plus[i, j] += h
+                minus[i, j] -= h
+                lp = loss(**dict(args, **{which: plus}))
+                lm = loss(**dict(args, **{which: minus}))
+                return (lp - lm) / (2 * h)
+            if which == "obs":
+                # delta is linear in the observations: the central difference is exact
+                fd = central(1e-6 * max(1.0, abs(float(base[i, j]))))
+            else:
+                # camera coordinates: the fourth-order (Richardson) combination of central
+                # differences at h and 2h.  delta is very nonlinear in some of them (cameras
+                # near the chain's end: the oracle's exact sparse solves give 0.58, 9e-3 and
+                # 1e-4 relative error at h = 1e-3, 1e-4, 1e-5 for one), so the second-order
+                # difference alone would need an h where rounding already dominates
+                h = 2e-5 * max(1.0, abs(float(base[i, j])))
+                fd = (4.0 * central(h) - central(2.0 * h)) / 3.0
             g = float(grad[i, j])
             # 1e-5 relative, over the differences' rounding floor (2e-7 of the largest
             # derivative, a third above the 1.5e-7 measured)

@@ -140,19 +140,25 @@ def test_implicit_schur_product_matches_explicit_oracle(gpu, which):
          "chain": lambda: scene("street_chain", **CHAIN),
          # points seen by up to 48 cameras: the >32-observation tile path
          "bigpoints": lambda: scene("ring", seed=7, n_cams=48, n_pts=300, kmin=20, kmax=48)}[which]()
-    for prec in (F_.BA_FP64, F_.BA_MIXED):
-        prob, cams, pts, obs = _prob(s, gpu, precision=prec)
+    sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
+    x = np.random.default_rng(3).normal(size=(s.n_cams, 9))
+    ref = sch.S @ x.ravel()
+    y32s = []
+    # the FP32 product with records staged through shared memory by bulk copies (1) and
+    # loaded into registers (0)
+    for prec, staging in ((F_.BA_FP64, 1), (F_.BA_MIXED, 0), (F_.BA_MIXED, 1)):
+        prob, cams, pts, obs = _prob(s, gpu, precision=prec, schur_staging=staging)
         prob.linearize(cams, pts, obs)
         prob.schur_setup(s.lam)
-        sch = schur.linearize(s.cams, s.pts, s.cam_idx, s.pt_idx, s.obs, s.lam)
-        x = np.random.default_rng(3).normal(size=(s.n_cams, 9))
-        ref = sch.S @ x.ravel()
         xt = torch.tensor(x, device=gpu)
         y = _np(prob.schur_matvec(xt)).ravel()
         assert np.linalg.norm(y - ref) <= 1e-12 * np.linalg.norm(ref)
         if prec == F_.BA_MIXED:
             y32 = _np(prob.schur_matvec(xt, F_.BA_MIXED)).ravel()
             assert np.linalg.norm(y32 - ref) <= 1e-4 * np.linalg.norm(ref)
+            y32s.append(y32)
+    # the same FP32 arithmetic either way; only the order of the window's atomic sums differs
+    assert np.linalg.norm(y32s[0] - y32s[1]) <= 1e-6 * np.linalg.norm(y32s[0])
 
 
 def _bsr_dense(rowptr, cols, vals, b):
