@@ -454,7 +454,7 @@ def gpu_main(args):
     # FP32 lane operations per second: 128 FP32 lanes per SM at the highest SM clock seen
     fp32_peak_tops = n_sm * 128 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
     kernels, roofline = kernel_table(prob, _ffi, s, info, prec, kt, kt_var, hbm, peak_note, fp32_peak_tops,
-                                     fp64_peak_tflops, n_sm)
+                                     fp64_peak_tflops, n_sm, args.workload)
 
     # the other single-GPU workloads, measured in the same run: the city grid (the largest
     # single-GPU configuration) and a 50-iteration LM run on the loop-closure scene
@@ -522,7 +522,8 @@ def gpu_main(args):
         dist.destroy_process_group()
 
 
-def kernel_table(prob, _ffi, s, info, prec, kt, kt_var, hbm, peak_note, fp32_peak_tops, fp64_peak_tflops, n_sm):
+def kernel_table(prob, _ffi, s, info, prec, kt, kt_var, hbm, peak_note, fp32_peak_tops, fp64_peak_tflops, n_sm,
+                 workload):
     """Per kernel class: launches, average ms and, where a model exists, the algorithmic
     bytes (or operations) per launch and the achieved rate; and the roofline entry of the
     class with the largest total time per step among those with a model."""
@@ -604,7 +605,7 @@ def kernel_table(prob, _ffi, s, info, prec, kt, kt_var, hbm, peak_note, fp32_pea
                     "peak": fp64_peak_tflops, "unit": "TFLOP/s", "frac": k["achieved"] / fp64_peak_tflops,
                     "traffic": None, "peak_source": "cuBLAS DGEMM 4096^3 measured in this run"}
     # the recorded counters are the paired-FP32 kernels' (mixed precision)
-    traffic = _traffic_from_profiles(dom) if prec == _ffi.BA_MIXED else None
+    traffic = _traffic_from_profiles(dom, workload) if prec == _ffi.BA_MIXED else None
     if roofline is not None and traffic is not None:
         roofline["traffic"] = traffic
     return kernels, roofline
@@ -694,7 +695,7 @@ def measure_config(workload, dev, args):
     peak_note = "measured" if _peaks().get("hbm_gbs") else "fallback"
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     kernels, roofline = kernel_table(prob, _ffi, s, info, _ffi.BA_MIXED, kt, kt_var, hbm, peak_note,
-                                     n_sm * 128 * 2070.0 * 1e6 / 1e12, None, n_sm)
+                                     n_sm * 128 * 2070.0 * 1e6 / 1e12, None, n_sm, workload)
     prob.close()
     res["kernels"] = kernels
     res["roofline"] = roofline
@@ -791,13 +792,16 @@ def measure_dgemm_tflops(dev, n=4096, reps=5):
     return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
-def _traffic_from_profiles(dom):
-    """DRAM bytes per launch of the dominant kernel class from the committed ncu summary,
-    if the kernel's source file is still the one the counters were taken on (else None)."""
+def _traffic_from_profiles(dom, workload):
+    """DRAM bytes per launch of the dominant kernel class from the committed ncu summary of
+    this workload, if the kernel's source file is still the one the counters were taken on
+    (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         entry = json.load(open(path))["kernels"][dom]
+        if entry.get("workload") != workload:
+            return None
         src = open(os.path.join(ROOT, "paper_2007_01941_gb300", entry["file"]), "rb").read()
         if hashlib.sha256(src).hexdigest() != entry["sha256"]:
             return None
