@@ -284,6 +284,12 @@ void part_allreduce(ba_problem* P, double* dev, size_t n);
 double fetch_sum(ba_problem* P, int slot);
 inline bool partitioned(const ba_problem* P) { return P->part_fn != nullptr; }
 void check_flags(ba_problem* P);                          // sync, read, raise
+// check_flags without its own synchronisation: raises from the flags last copied to the host
+void raise_flags(ba_problem* P);
+// scalars [first, first + count) and the flags to the host in one synchronisation, then
+// raise_flags; fetch_sum_checked also sums the slot over a partitioned problem's ranks
+void fetch_checked(ba_problem* P, int first, int count);
+double fetch_sum_checked(ba_problem* P, int slot);
 void clear_flags(ba_problem* P);
 void launched(ba_problem* P);                              // count + check launch error
 
@@ -319,12 +325,15 @@ void build_graph(ba_problem* P, const int32_t* cam_idx_dev, const int32_t* pt_id
 // ---- linearisation (linearize.cu) ------------------------------------------
 void linearize(ba_problem* P, const double* cams, const double* pts, const double* obs);
 double cost_at(ba_problem* P, const double* cams, const double* pts, const double* obs);
+// the same cost into scalar S_COST_NEW, not fetched
+void cost_at_async(ba_problem* P, const double* cams, const double* pts, const double* obs);
 // the FP64 Jacobian records; in mixed precision formed on first use from J32 + J32lo
 // (exactly the doubles the paired-FP32 linearisation computed), never inside a capture
 double* jacobian64(ba_problem* P);
 
 // ---- Schur reduction and implicit operator (schur.cu) -----------------------
-void schur_setup(ba_problem* P, double lambda);
+// check = false leaves the flags for the caller's next fetch_checked (the LM step's PCG)
+void schur_setup(ba_problem* P, double lambda, bool check = true);
 // y = S x on internal camera vectors; T selects the FP64 or FP32 storage kernel.
 void matvec64(ba_problem* P, const double* x, double* y);
 void matvec32(ba_problem* P, const float* x, float* y);
@@ -339,7 +348,13 @@ void lanczos_batched(ba_problem* P, int first, int last);  // levels first..last
 void build_ap(ba_problem* P, Level& L);
 void fused_vcycle_setup(ba_problem* P);
 // z = M r; rz_part (optional): per level-0 row, its share of r.z (one value per block row)
-void fused_vcycle(ba_problem* P, const double* r, double* z, double* rz_part);
+// first_done: the level-0 pre-smoothing step 0 on r was already formed (by
+// fused_update_first), so the cycle starts at step 1
+void fused_vcycle(ba_problem* P, const double* r, double* z, double* rz_part, bool first_done);
+struct PcgCheck;
+// the PCG update with the assembled S (x += alpha p, r -= alpha q, r.r, the stopping test)
+// fused with the next V-cycle's level-0 pre-smoothing step 0 on the new r
+void fused_update_first(ba_problem* P, double* x, double* r, const double* p, const double* q, const PcgCheck& ck);
 // assembled level-0 S: FP32 blocks only (the Galerkin product's input), FP64 blocks, or
 // paired-FP32 arithmetic giving the FP64 blocks and their FP32 roundings
 enum ExplicitMode { EX_FP32, EX_FP64, EX_PAIRED };
@@ -348,13 +363,14 @@ void back_substitute_to(ba_problem* P, const double* dc, double* out_int, double
 void reduced_rhs(ba_problem* P, const double* vc, const double* vp_user, double* out);
 
 // ---- multigrid setup (mg_setup.cu) ------------------------------------------
-void mg_setup(ba_problem* P);
+void mg_setup(ba_problem* P, bool check = true);
 void covisibility_level0(ba_problem* P, Level& L);
 void jacobi_blocks(ba_problem* P, Level& L, bool from_vals64);
 
 // ---- solve (solve.cu) -------------------------------------------------------
 void precond_apply(ba_problem* P, const double* r, double* z);
-void pcg(ba_problem* P, const double* rhs, double* dc);
+// check_setup: raise the flags left by an unchecked schur_setup / mg_setup first
+void pcg(ba_problem* P, const double* rhs, double* dc, bool check_setup = false);
 void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double* lam,
              int* accepted, double* cost);
 

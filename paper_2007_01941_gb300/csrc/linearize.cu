@@ -331,6 +331,11 @@ double* jacobian64(ba_problem* P) {
 }
 
 double cost_at(ba_problem* P, const double* cams, const double* pts, const double* obs) {
+  cost_at_async(P, cams, pts, obs);
+  return fetch_sum(P, S_COST_NEW);
+}
+
+void cost_at_async(ba_problem* P, const double* cams, const double* pts, const double* obs) {
   const bool mixed = P->opt.precision == BA_MIXED;
   // rotation data in the front of scratch2, the camera split behind it
   const size_t rot_bytes = (sizeof(double) * kCamx * std::max(P->n_c, 1) + 255) / 256 * 256;
@@ -351,7 +356,6 @@ double cost_at(ba_problem* P, const double* cams, const double* pts, const doubl
         P->partial.as<double>(), P->counter.as<unsigned>(), P->scal.as<double>() + S_COST_NEW,
         P->flags.as<int>(), huber_scale(P));
   launched(P);
-  return fetch_sum(P, S_COST_NEW);
 }
 
 }  // namespace ba

@@ -1730,7 +1730,7 @@ static void prolongator_chain(ba_problem* P, cudaStream_t st) {
   }
 }
 
-void mg_setup(ba_problem* P) {
+void mg_setup(ba_problem* P, bool check) {
   const bool fp32 = level_fp32(P);
   const ba_options& o = P->opt;
   P->graph_epoch++;
@@ -1851,7 +1851,7 @@ void mg_setup(ba_problem* P) {
   block_inverse_batch(P, inv, 16, F_NOT_SPD_JACOBI);
   lanczos_batched(P, P->l0_explicit ? 0 : 1, P->n_levels - 2);
   finish_lanczos(P);
-  check_flags(P);
+  if (check) check_flags(P);
   // V-cycle work vectors
   for (int k = 0; k < P->n_levels; ++k) {
     Level& L = P->levels[k];

@@ -129,10 +129,35 @@ void clear_flags(ba_problem* P) {
   BA_CUDA(cudaMemsetAsync(P->flags.p, 0, sizeof(int) * F_COUNT, P->stream));
 }
 
-void check_flags(ba_problem* P) {
-  BA_CUDA(cudaMemcpyAsync(P->h_flags, P->flags.p, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost,
-                          P->stream));
+static void read_flags_async(ba_problem* P) {
+  BA_CUDA(cudaMemcpyAsync(P->h_flags, P->flags.p, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, P->stream));
+}
+
+void fetch_checked(ba_problem* P, int first, int count) {
+  BA_CUDA(cudaMemcpyAsync(P->h_scal + first, P->scal.as<double>() + first, sizeof(double) * count,
+                          cudaMemcpyDeviceToHost, P->stream));
+  read_flags_async(P);
   sync(P);
+  raise_flags(P);
+}
+
+double fetch_sum_checked(ba_problem* P, int slot) {
+  fetch_checked(P, slot, 1);
+  if (P->part_fn) {
+    double v = P->h_scal[slot];
+    BA_REQUIRE(P->part_fn(&v, 1, P->part_user) == 0, BA_ERR_STATE, "the all-reduce hook failed");
+    P->h_scal[slot] = v;
+  }
+  return P->h_scal[slot];
+}
+
+void check_flags(ba_problem* P) {
+  read_flags_async(P);
+  sync(P);
+  raise_flags(P);
+}
+
+void raise_flags(ba_problem* P) {
   if (P->part_fn) {
     // partitioned solve: every rank raises the same error at the same point (a rank that
     // stopped alone would leave the others waiting in their next reduction)

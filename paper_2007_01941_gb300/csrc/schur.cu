@@ -748,7 +748,7 @@ __global__ void k_add_block_diag(int n_c, const double* __restrict__ Scc, const 
   out[i] = Scc[i] + ((k % 10 == 0) ? (double)pcd[9 * c + k / 10] : 0.0);
 }
 
-void schur_setup(ba_problem* P, double lambda) {
+void schur_setup(ba_problem* P, double lambda, bool check) {
   const bool mixed = P->opt.precision == BA_MIXED;
   const int n_c = P->n_c, n_p = P->n_p;
   const size_t ldp = P->ldp;
@@ -848,7 +848,7 @@ void schur_setup(ba_problem* P, double lambda) {
   }
   // the PCG graph captures the FP64 outer product, so its records must exist beforehand
   if (mixed && !outer_df(P) && !P->opt.recompute_jacobian) jacobian64(P);
-  check_flags(P);
+  if (check) check_flags(P);
 }
 
 // ---------------------------------------------------------------------------

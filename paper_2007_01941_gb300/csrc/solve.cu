@@ -6,6 +6,7 @@
 #include "ba_internal.h"
 #include "device_util.cuh"
 #include "dfloat.cuh"
+#include "pcg_update.cuh"
 
 namespace ba {
 
@@ -336,7 +337,7 @@ void precond_apply(ba_problem* P, const double* r, double* z) {
   BA_REQUIRE(P->n_levels > 0, BA_ERR_STATE, "ba_mg_setup has not been run");
   KernelTimer kt(P, BA_KT_VCYCLE);
   if (P->vc_ready) {
-    fused_vcycle(P, r, z, nullptr);
+    fused_vcycle(P, r, z, nullptr, false);
     return;
   }
   Level& L0 = P->levels[0];
@@ -430,14 +431,8 @@ static void pcg_head(ba_problem* P, double* x) {
                                                               P->flags.as<int>());
 }
 
-// counts the iteration and sets the loop condition: continue while |r|^2 > rtol^2 |b|^2,
-// no breakdown and fewer than max_iters iterations
-__device__ __host__ inline bool pcg_converged(int rule, double it, double rr, double bb, double rtol2, double q,
-                                              double dq, double tau) {
-  if (rule == BA_STOP_NASH_SOFER) return q < 0.0 && it * dq / q <= tau;
-  return !(rr > rtol2 * bb);
-}
-
+// counts the iteration and sets the loop condition: continue while not converged
+// (pcg_converged), no breakdown and fewer than max_iters iterations
 __global__ void k_pcg_check(double* scal, const int* flags, int max_iters, double rtol2, int rule, double tau,
                             cudaGraphConditionalHandle h) {
   pdl_wait();
@@ -527,12 +522,10 @@ k_pcg_spmv_pq(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
 
 __global__ void __launch_bounds__(kVecBS)
 k_pcg_update_check(size_t n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                   const double* __restrict__ q, double* scal, double* partial,
-                   unsigned* counter, int* flags, int max_iters, double rtol2, int rule, double tau, int use_cond,
-                   cudaGraphConditionalHandle h) {
+                   const double* __restrict__ q, PcgCheck ck) {
   pdl_trigger();
   pdl_wait();
-  const double pq = scal[S_PQ], rz = scal[S_TMP2];
+  const double pq = ck.scal[S_PQ], rz = ck.scal[S_TMP2];
   const double alpha = rz / pq;
   const bool ok = pq > 0.0 && isfinite(alpha);
   double acc = 0.0;
@@ -545,39 +538,7 @@ k_pcg_update_check(size_t n, double* __restrict__ x, double* __restrict__ r, con
     }
     acc += ri * ri;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (!ok) flags[F_BREAKDOWN] = 1;
-    // quadratic model: Q_i - Q_{i-1} = -alpha (r.z) / 2
-    const double dq = ok ? -0.5 * alpha * rz : 0.0;
-    scal[S_DQ] = dq;
-    scal[S_Q] += dq;
-    scal[S_RZ] = rz;   // the next direction's beta divides by this r.z
-  }
-  // r.r by a deterministic grid reduction; the last block also counts the iteration and
-  // sets the loop condition (continue while not converged, no breakdown, below max_iters)
-  __shared__ bool am_last;
-  double s = block_sum<kVecBS>(acc);
-  if (threadIdx.x == 0) {
-    partial[blockIdx.x] = s;
-    __threadfence();
-    am_last = atomicAdd(counter, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (am_last) {
-    __threadfence();
-    double t = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += kVecBS) t += __ldcg(partial + b);
-    t = block_sum<kVecBS>(t);
-    if (threadIdx.x == 0) {
-      scal[S_RR] = t;
-      *counter = 0u;
-      const double it = scal[S_ITER] + 1.0;
-      scal[S_ITER] = it;
-      const bool stop = pcg_converged(rule, it, t, scal[S_BB], rtol2, __ldcg(scal + S_Q), __ldcg(scal + S_DQ), tau) ||
-                        __ldcg(flags + F_BREAKDOWN) != 0 || it >= (double)max_iters;
-      if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
-    }
-  }
+  pcg_update_finish<kVecBS>(acc, ok, alpha, rz, ck);
 }
 
 // The same product in mixed precision from the blocks as (hi, lo) float pairs and the
@@ -703,7 +664,8 @@ static void assembled_precond_direction(ba_problem* P, int first) {
     double* part = P->rzpart.as<double>();
     {
       KernelTimer kt(P, BA_KT_VCYCLE);
-      fused_vcycle(P, r, z, part);
+      // after the first iteration the update kernel has done the cycle's first phase
+      fused_vcycle(P, r, z, part, !first);
     }
     launch_k(P, k_pcg_direction_rz, cdiv((long long)n, 256), 256, 0, n, p, z, P->scal.as<double>(), first,
              (const double*)part, P->n_c, assembled_split(P));
@@ -729,12 +691,20 @@ static void assembled_spmv(ba_problem* P) {
              P->counter.as<unsigned>() + 1, P->scal.as<double>() + S_PQ);
 }
 
+// the update kernel; with the fused V-cycle it also forms the next cycle's level-0
+// pre-smoothing step 0 from the new r (the cycle then starts at step 1)
+static bool update_starts_vcycle(ba_problem* P) { return P->opt.preconditioner == BA_PRECOND_MG && P->vc_ready; }
+
 static void assembled_update(ba_problem* P, double* x, int use_cond, cudaGraphConditionalHandle h) {
   const size_t n = (size_t)P->n_c * 9;
+  const PcgCheck ck{P->scal.as<double>(), P->partial.as<double>(), P->counter.as<unsigned>(), P->flags.as<int>(),
+                    P->opt.max_iters, P->opt.rtol * P->opt.rtol, P->opt.stop_rule, P->opt.tau, use_cond, h};
+  if (update_starts_vcycle(P)) {
+    fused_update_first(P, x, P->r.as<double>(), P->p.as<double>(), P->q.as<double>(), ck);
+    return;
+  }
   launch_k(P, k_pcg_update_check, reduce_blocks(P, n), kVecBS, 0, n, x, P->r.as<double>(), P->p.as<double>(),
-           P->q.as<double>(), P->scal.as<double>(), P->partial.as<double>(),
-           P->counter.as<unsigned>(), P->flags.as<int>(), P->opt.max_iters, P->opt.rtol * P->opt.rtol,
-           P->opt.stop_rule, P->opt.tau, use_cond, h);
+           P->q.as<double>(), ck);
 }
 
 // Builds [head, check] -> while(cond) { tail, head, check } as one executable graph that
@@ -818,7 +788,7 @@ static void build_pcg_graph(ba_problem* P) {
   }
 }
 
-void pcg(ba_problem* P, const double* rhs, double* dc) {
+void pcg(ba_problem* P, const double* rhs, double* dc, bool check_setup) {
   const size_t n = (size_t)P->n_c * 9;
   const int g = cdiv((long long)n, 256);
   P->r.ensure(sizeof(double) * n + 64);
@@ -828,11 +798,17 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
   P->x.ensure(sizeof(double) * n + 64);
   double *r = P->r.as<double>(), *z = P->z.as<double>(), *p = P->p.as<double>(), *q = P->q.as<double>();
   double* scal = P->scal.as<double>();
-  clear_flags(P);
+  if (!check_setup) clear_flags(P);
   BA_CUDA(cudaMemsetAsync(dc, 0, sizeof(double) * n, P->stream));
   BA_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream));
   dot64(P, r, r, n, S_BB);
-  fetch_scalars(P, S_BB, 1);
+  if (check_setup) {
+    // the setup's flags come back with b.b (one synchronisation), then start clean
+    fetch_checked(P, S_BB, 1);
+    clear_flags(P);
+  } else {
+    fetch_scalars(P, S_BB, 1);
+  }
   const double bb = P->h_scal[S_BB];
   P->pcg_iters = 0;
   P->pcg_rel = 0.0;
@@ -870,8 +846,7 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
       BA_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, P->stream));
       BA_CUDA(cudaGraphLaunch(P->pcg_exec, P->stream));
       BA_CUDA(cudaMemcpyAsync(dc, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream));
-      fetch_scalars(P, S_RR, S_DQ - S_RR + 1);
-      check_flags(P);
+      fetch_checked(P, S_RR, S_DQ - S_RR + 1);
       it = (int)P->h_scal[S_ITER];
       P->launches += P->pcg_graph_head + (long long)std::max(it - 1, 0) * P->pcg_graph_body;
       rel = std::sqrt(P->h_scal[S_RR] / bb);
@@ -896,9 +871,8 @@ void pcg(ba_problem* P, const double* rhs, double* dc) {
                                                  P->counter.as<unsigned>(), P->flags.as<int>());
     }
     ++it;
-    fetch_scalars(P, S_RR, S_DQ - S_RR + 1);
+    fetch_checked(P, S_RR, S_DQ - S_RR + 1);
     rel = std::sqrt(P->h_scal[S_RR] / bb);
-    check_flags(P);
     BA_REQUIRE(std::isfinite(rel), BA_ERR_BREAKDOWN, "non-finite PCG residual");
     done = pcg_converged(P->opt.stop_rule, (double)it, P->h_scal[S_RR], bb, rtol2, P->h_scal[S_Q],
                          P->h_scal[S_DQ], P->opt.tau);
@@ -950,8 +924,10 @@ k_model_terms(int n_c9, const double* __restrict__ dc, const double* __restrict_
 void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double* lam, int* accepted,
              double* cost_out) {
   linearize(P, cams, pts, obs);
-  check_flags(P);
-  const double cost0 = fetch_sum(P, S_COST);
+  // one synchronisation per stage boundary that needs the host: the linearisation's flags
+  // with its cost; the setups' flags with the PCG's b.b; the PCG's result with its flags;
+  // the trial cost with the model decrease
+  const double cost0 = fetch_sum_checked(P, S_COST);
   P->cost = cost0;
   const size_t nc = (size_t)P->n_c * 9, np = (size_t)P->n_p * 3;
   P->delta_c.ensure(sizeof(double) * nc + 64);
@@ -962,10 +938,10 @@ void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double
   // grows as after a rejection.
   bool solved = true;
   try {
-    schur_setup(P, *lam);
-    if (P->opt.preconditioner == BA_PRECOND_MG) mg_setup(P);
+    schur_setup(P, *lam, false);
+    if (P->opt.preconditioner == BA_PRECOND_MG) mg_setup(P, false);
     try {
-      pcg(P, P->rhs.as<double>(), P->delta_c.as<double>());
+      pcg(P, P->rhs.as<double>(), P->delta_c.as<double>(), true);
     } catch (const Error& e) {
       if (e.status != BA_ERR_NOT_CONVERGED) throw;  // an inexact step is still a step
     }
@@ -994,7 +970,6 @@ void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double
     k_add<<<cdiv((long long)np, 256), 256, 0, P->stream>>>(np, pts, dp_user, pts1);
     launched(P);
   }
-  const double cost1 = cost_at(P, cams1, pts1, obs);
   // the model decrease 1/2 (delta.g + delta.D.delta); partitioned: the point terms are this
   // rank's share (summed over the ranks), the camera terms are the same on every rank
   auto model_terms = [&](int n_c9, int n_pts) {
@@ -1004,17 +979,21 @@ void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double
         P->counter.as<unsigned>(), P->scal.as<double>() + S_MODEL);
     launched(P);
   };
-  double model_sum;
+  double model_sum, cost1;
   if (partitioned(P)) {
+    cost1 = cost_at(P, cams1, pts1, obs);
     model_terms(0, P->n_p);
     model_sum = fetch_sum(P, S_MODEL);
     model_terms((int)nc, 0);
     fetch_scalars(P, S_MODEL, 1);
     model_sum += P->h_scal[S_MODEL];
   } else {
+    cost_at_async(P, cams1, pts1, obs);
     model_terms((int)nc, P->n_p);
-    fetch_scalars(P, S_MODEL, 1);
+    static_assert(S_COST_NEW == S_MODEL + 1, "scalar slots");
+    fetch_scalars(P, S_MODEL, 2);
     model_sum = P->h_scal[S_MODEL];
+    cost1 = P->h_scal[S_COST_NEW];
   }
   const double model = 0.5 * model_sum;
   const double rho = model > 0.0 ? (cost0 - cost1) / model : -INFINITY;

@@ -24,6 +24,7 @@
 
 #include "ba_internal.h"
 #include "device_util.cuh"
+#include "pcg_update.cuh"
 
 namespace ba {
 
@@ -325,6 +326,66 @@ __global__ void __launch_bounds__(256) k_ph_first(VLevel<T> L, const double* __r
       L.x[0][idx] = dv;
     }
   }
+}
+
+// The PCG update with the assembled S (alpha = r.z / p.q, x += alpha p, r -= alpha q,
+// r.r and the stopping test) fused with the next V-cycle's level-0 pre-smoothing step 0 on
+// the new r (the work of k_ph_first with `in` = r): each CTA takes groups of kUpdRows
+// block rows, thread (row, u) entry u of its row; the row's new r meets in shared memory
+// for D_i^-1 r.  The graph's last iteration forms a step 0 that no cycle uses.
+constexpr int kUpdRows = 32;
+constexpr int kUpdBS = kUpdRows * 9;
+
+template <typename T>
+__global__ void __launch_bounds__(kUpdBS)
+k_pcg_update_first(VLevel<T> L, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                   const double* __restrict__ q, PcgCheck ck) {
+  __shared__ T bsm[kUpdBS];
+  const int t = threadIdx.x, lr = t / 9, u = t - 9 * lr;
+  const int ngroups = (L.n + kUpdRows - 1) / kUpdRows;
+  const T inv_theta = (T)(1.0 / L.cheb[0]);
+  T dr[9];
+  {
+    const int row = blockIdx.x * kUpdRows + lr;
+    if (row < L.n) dinv_row<T, 9>(L.Dinv + (size_t)row * 81, u, dr);
+  }
+  pdl_trigger();
+  pdl_wait();
+  const double pq = ck.scal[S_PQ], rz = ck.scal[S_TMP2];
+  const double alpha = rz / pq;
+  const bool ok = pq > 0.0 && isfinite(alpha);
+  double acc = 0.0;
+  for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const int row = g * kUpdRows + lr;
+    const bool live = row < L.n;
+    if (live && g != (int)blockIdx.x) dinv_row<T, 9>(L.Dinv + (size_t)row * 81, u, dr);
+    const size_t idx = (size_t)row * 9 + u;
+    double ri = 0.0;
+    if (live) {
+      ri = r[idx];
+      if (ok) {
+        x[idx] += alpha * p[idx];
+        ri -= alpha * q[idx];
+        r[idx] = ri;
+      }
+      acc += ri * ri;
+    }
+    const T bv = (T)ri;
+    bsm[t] = bv;
+    __syncthreads();
+    if (live) {
+      T s = T(0);
+#pragma unroll
+      for (int v = 0; v < 9; ++v) s += dr[v] * bsm[9 * lr + v];
+      const T dv = s * inv_theta;
+      L.b[idx] = bv;
+      L.r[0][idx] = bv;
+      L.d[0][idx] = dv;
+      L.x[0][idx] = dv;
+    }
+    __syncthreads();
+  }
+  pcg_update_finish<kUpdBS>(acc, ok, alpha, rz, ck);
 }
 
 // Chebyshev step k >= 1 on row blockIdx.x: q = A din; rout = rin - q;
@@ -724,7 +785,7 @@ static void cheb_coeffs(const Level& L, int k, double& c1, double& c2) {
 }
 
 template <typename T>
-static void run(ba_problem* P, const double* r, double* z, double* dpart) {
+static void run(ba_problem* P, const double* r, double* z, double* dpart, bool first_done) {
   const int nl = P->n_levels;
   const int pre = std::max(1, P->opt.pre_smooth), post = std::max(1, P->opt.post_smooth);
   std::vector<VLevel<T>> V(nl);
@@ -734,8 +795,9 @@ static void run(ba_problem* P, const double* r, double* z, double* dpart) {
   cudaStream_t st = P->stream;
   for (int l = 0; l + 1 < nl; ++l) {
     const VLevel<T>& L = V[l];
-    // step 0 of the coarse levels is done by the restriction that produces their b
-    if (l == 0) {
+    // step 0 of the coarse levels is done by the restriction that produces their b, and of
+    // level 0 by the PCG update when first_done
+    if (l == 0 && !first_done) {
       const int g = warps_grid(L.n);
       if (L.bs == 9) launch_k(P, k_ph_first<T, 9>, g, kPhaseBS, 0, L, r);
       else launch_k(P, k_ph_first<T, 16>, g, kPhaseBS, 0, L, r);
@@ -802,9 +864,23 @@ void fused_vcycle_setup(ba_problem* P) {
   P->vc_ready = true;
 }
 
-void fused_vcycle(ba_problem* P, const double* r, double* z, double* rz_part) {
-  if (level_fp32(P)) run<float>(P, r, z, rz_part);
-  else run<double>(P, r, z, rz_part);
+void fused_vcycle(ba_problem* P, const double* r, double* z, double* rz_part, bool first_done) {
+  if (level_fp32(P)) run<float>(P, r, z, rz_part, first_done);
+  else run<double>(P, r, z, rz_part, first_done);
+}
+
+template <typename T>
+static void update_first(ba_problem* P, double* x, double* r, const double* p, const double* q, const PcgCheck& ck) {
+  const VLevel<T> L = describe<T>(P->levels[0]);
+  // at most 16 CTAs per SM: the r.r partials have one slot per CTA
+  const int grid = std::max(1, std::min(cdiv((long long)L.n, kUpdRows), 8 * P->n_sm));
+  launch_k(P, k_pcg_update_first<T>, grid, kUpdBS, 0, L, x, r, p, q, ck);
+}
+
+void fused_update_first(ba_problem* P, double* x, double* r, const double* p, const double* q, const PcgCheck& ck) {
+  BA_REQUIRE(P->vc_ready && P->levels[0].bs == 9, BA_ERR_STATE, "fused update without the fused V-cycle");
+  if (level_fp32(P)) update_first<float>(P, x, r, p, q, ck);
+  else update_first<double>(P, x, r, p, q, ck);
 }
 
 }  // namespace ba
