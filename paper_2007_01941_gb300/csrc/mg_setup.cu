@@ -192,7 +192,8 @@ static void row_hash(ba_problem* P, int n_rows, int H, const int* a_ptr, const i
   // pass 1: counts
   P->scratch.ensure(sizeof(int) * ((size_t)n_rows + 1) * 2 + 64);
   int* cnt = P->scratch.as<int>();
-  clear_flags(P);
+  // (the flags are not cleared here: a setup whose check is deferred keeps its earlier
+  // flags, which this check then raises)
   k_row_hash<MODE><<<n_rows, kHashBS, smem, P->stream>>>(n_rows, H, a_ptr, a_list, b_ptr, b_idx, map, Win,
                                                          nullptr, cnt, nullptr, nullptr, P->flags.as<int>());
   launched(P);
@@ -1734,7 +1735,9 @@ void mg_setup(ba_problem* P, bool check) {
   const bool fp32 = level_fp32(P);
   const ba_options& o = P->opt;
   P->graph_epoch++;
-  clear_flags(P);
+  // check = false (the LM step): the flags of the linearisation and the Schur setup stay
+  // for the step's next fetch_checked
+  if (check) clear_flags(P);
   if (!P->sym_ready) mg_symbolic(P);
   Level& L0 = P->levels[0];
   {

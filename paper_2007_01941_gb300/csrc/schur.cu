@@ -770,7 +770,7 @@ void schur_setup(ba_problem* P, double lambda, bool check) {
   P->Scc_inv.ensure(sizeof(double) * 81 * n_c + 64);
   P->Scc_inv32.ensure(sizeof(float) * 81 * n_c + 64);
   if (mixed) P->cam_ubnd.ensure(sizeof(float) * 9 * n_c + 64);
-  clear_flags(P);
+  if (check) clear_flags(P);   // else the linearisation's flags stay for the caller's check
   const int damp_id = P->opt.damping == BA_DAMP_IDENTITY;
   if (n_p) {
     if (mixed) {

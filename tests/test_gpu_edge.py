@@ -114,3 +114,28 @@ def test_single_level_hierarchy_is_a_direct_solve(gpu):
     assert prob.info()["n_levels"] == 1 and it <= 2
     sch, ex = _exact(s, s.lam)
     assert np.linalg.norm(_np(dc).ravel() - ex) <= 1e-7 * np.linalg.norm(ex)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_lm_step_with_a_singular_jacobi_block_is_rejected(gpu, precision):
+    """An unobserved camera at lambda = 0 has a zero diagonal block of S, which the Schur
+    setup's block inverse finds not positive definite; inside ba_lm_step that failed solve
+    is a rejection (x kept, cost unchanged, lambda times nu), and the next step at lambda >
+    0 starts clean."""
+    api, F_ = _api()
+    base = scene("ring", seed=1, n_cams=20, n_pts=1500)
+    s = _drop_camera_obs(base, 7)
+    prec = F_.BA_FP64 if precision == "fp64" else F_.BA_MIXED
+    prob, cams, pts, obs = api.from_scene(s, device=gpu, precision=prec, coarse_max_nodes=4)
+    cost0 = prob.linearize(cams, pts, obs)
+    c0, p0 = cams.clone(), pts.clone()
+    lam, acc, cost = prob.lm_step(cams, pts, obs, 0.0)
+    assert acc == 0 and lam == 0.0 and cost == cost0
+    assert torch.equal(cams, c0) and torch.equal(pts, p0)
+    with pytest.raises(api.BAError):
+        prob.pcg_solve()        # the failed step left no setup to solve with
+    # at lambda > 0 the step goes through and the observed cameras move
+    lam, acc, cost = prob.lm_step(cams, pts, obs, 1e-3)
+    assert acc == 1 and cost < cost0
+    moved = np.abs(_np(cams) - _np(c0)).max(axis=1)
+    assert np.all(np.delete(moved, 7) > 0.0)
