@@ -47,6 +47,10 @@ struct VLevel {
   const int* ap_ptr;   // A P: blocks (bs x 16) of fine row i, their aggregates and values
   const int* ap_cols;
   const T* ap_vals;
+  const int* gptr;     // folded coarse level: fine members of each block's aggregate
+  const int* gmem;
+  const T* mvals;      // folded coarse level: M_aj = A_aj D_j^-1 / theta
+  T* rt;               // level above a folded one: t_i = Q_i^T s_i [n][16]
   T* b;
   T* x[2];
   T* r[2];
@@ -432,24 +436,46 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_step(VLevel<T> L, i
   }
 }
 
-// residual of the pre-smoothed iterate on row blockIdx.x: s = r - A d, into the free r buffer
-template <typename T, int BS>
+// residual of the pre-smoothed iterate on row blockIdx.x: s = r - A d, into the free r buffer;
+// RT (the next level's restriction folded into its first smoothing kernel): also this
+// row's restriction term t_i = Q_i^T s_i into L.rt
+template <typename T, int BS, bool RT = false>
 __global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_residual(VLevel<T> L, int dc, int rc) {
   __shared__ T part[RowCta<BS>::kPart];
-  __shared__ T q[BS];
+  __shared__ T q[BS], sv[BS];
   const int i = blockIdx.x, t = threadIdx.x;
   constexpr bool kVec = BS == 16 && sizeof(T) == 4;
   constexpr int kNW = RowCta<BS>::kThreads / 32;
   std::conditional_t<kVec, RowPrefetch16<16>, RowPrefetch<T, BS>> pf;
   if constexpr (kVec) row_prefetch16<16, kNW>(L.row_ptr, L.cols, L.vals, i, pf);
   else row_prefetch<T, BS>(L, i, pf);
+  // RT: column t of Q_i (t < 16)
+  T qc[RT ? BS : 1];
+  if constexpr (RT) {
+    if (t < 16) {
+      const T* Qi = L.Q + (size_t)i * BS * 16 + t;
+#pragma unroll
+      for (int u = 0; u < BS; ++u) qc[u] = Qi[u * 16];
+    }
+  }
   pdl_trigger();
   pdl_wait();
   if constexpr (kVec) cta_row_product16<16, kNW>(L.cols, L.vals, pf, L.d[dc], part, q);
   else cta_row_product<T, BS>(L, pf, L.d[dc], part, q);
   if (t < BS) {
     const size_t idx = (size_t)i * BS + t;
-    L.r[1 - rc][idx] = L.r[rc][idx] - q[t];
+    const T s = L.r[rc][idx] - q[t];
+    L.r[1 - rc][idx] = s;
+    if constexpr (RT) sv[t] = s;
+  }
+  if constexpr (RT) {
+    __syncthreads();
+    if (t < 16) {
+      T acc = T(0);
+#pragma unroll
+      for (int u = 0; u < BS; ++u) acc += qc[u] * sv[u];
+      L.rt[(size_t)i * 16 + t] = acc;
+    }
   }
 }
 
@@ -509,6 +535,139 @@ __global__ void __launch_bounds__(256) k_ph_restrict(VLevel<T> L, VLevel<T> C, c
     C.r[0][idx] = acc;
     C.d[0][idx] = dv;
     C.x[0][idx] = dv;
+  }
+}
+
+// Restriction folded into the coarse level's first smoothing kernel (FP32 hierarchy).  The
+// fine level's residual kernel leaves t_i = Q_i^T s_i per fine row, so b_a = sum_{i in a}
+// t_i, and with x = 0 the coarse pre-smoothing steps 0 and 1 on row a are
+//   d0 = D_a^-1 b_a / theta,  q = (A d0)_a = sum_j M_aj b_j  (M_aj = A_aj D_j^-1 / theta),
+//   r1 = b_a - q,  d1 = c1 d0 + c2 D_a^-1 r1,  x = d0 + d1:
+// the same iterate as the restriction kernel followed by step 1, one launch fewer.  The NW
+// warps split row a's blocks; a warp reads a 16 x 16 block of M with 16-byte loads (lane
+// l: float4 l and 32 + l, as cta_row_product16) and the matching four entries of b_j as
+// the sum of t over j's fine members (listed per block in gptr / gmem).
+constexpr int kGMem = 4;   // members per prefetched block kept in registers
+
+struct GatherPrefetch {
+  static constexpr int kPre = 2;
+  int e, e1, n;
+  int g0[kPre], g1[kPre];
+  int m[kPre][kGMem];
+  float4 a[kPre][2];
+};
+
+// sum over the members [g0, g1) (the first kGMem of them in m) of t's float4 at column cq
+__device__ __forceinline__ float4 gather_t4(const float* __restrict__ rt, const int* __restrict__ gmem, int g0,
+                                            int g1, const int* m, int cq) {
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < kGMem; ++k) {
+    if (g0 + k < g1) {
+      const float4 v = *reinterpret_cast<const float4*>(rt + (size_t)m[k] * 16 + cq);
+      s.x += v.x, s.y += v.y, s.z += v.z, s.w += v.w;
+    }
+  }
+  for (int g = g0 + kGMem; g < g1; ++g) {
+    const float4 v = *reinterpret_cast<const float4*>(rt + (size_t)gmem[g] * 16 + cq);
+    s.x += v.x, s.y += v.y, s.z += v.z, s.w += v.w;
+  }
+  return s;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_ph_cstep(VLevel<float> F, VLevel<float> C, int dc, int rc, int xc,
+                                                      float c1, float c2) {
+  __shared__ float part[16 * NW];
+  __shared__ float q[16], bsm[16], w[16];
+  const int a = blockIdx.x, t = threadIdx.x, wi = t >> 5, lane = t & 31, cq = 4 * (lane & 3);
+  // static data first: this warp's first blocks of row a of M with their member lists, row
+  // t of D_a^-1 and the aggregate's own members
+  GatherPrefetch p;
+  p.n = 0;
+  p.e1 = C.row_ptr[a + 1];
+  int e = C.row_ptr[a] + wi;
+#pragma unroll
+  for (int k = 0; k < GatherPrefetch::kPre; ++k) {
+    if (e < p.e1) {
+      p.g0[k] = C.gptr[e];
+      p.g1[k] = C.gptr[e + 1];
+#pragma unroll
+      for (int j = 0; j < kGMem; ++j) p.m[k][j] = p.g0[k] + j < p.g1[k] ? C.gmem[p.g0[k] + j] : 0;
+      const float4* ab = reinterpret_cast<const float4*>(C.mvals + (size_t)e * 256);
+      p.a[k][0] = ab[lane];
+      p.a[k][1] = ab[32 + lane];
+      p.n = k + 1;
+      e += NW;
+    }
+  }
+  p.e = e;
+  float dr[16];
+  int o0 = 0, o1 = 0, om[kGMem];
+  if (t < 16) {
+    dinv_row<float, 16>(C.Dinv + (size_t)a * 256, t, dr);
+    o0 = F.agg_ptr[a];
+    o1 = F.agg_ptr[a + 1];
+#pragma unroll
+    for (int j = 0; j < kGMem; ++j) om[j] = o0 + j < o1 ? F.agg_mem[o0 + j] : 0;
+  }
+  const float inv_theta = (float)(1.0 / C.cheb[0]);
+  pdl_trigger();
+  pdl_wait();
+  // b_a
+  if (t < 16) {
+    float b = 0.f;
+#pragma unroll
+    for (int j = 0; j < kGMem; ++j)
+      if (o0 + j < o1) b += F.rt[(size_t)om[j] * 16 + t];
+    for (int g = o0 + kGMem; g < o1; ++g) b += F.rt[(size_t)F.agg_mem[g] * 16 + t];
+    bsm[t] = b;
+  }
+  // q = sum_j M_aj b_j
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int k = 0; k < GatherPrefetch::kPre; ++k) {
+    if (k < p.n) {
+      const float4 xv = gather_t4(F.rt, C.gmem, p.g0[k], p.g1[k], p.m[k], cq);
+      s0 += dot4(p.a[k][0], xv);
+      s1 += dot4(p.a[k][1], xv);
+    }
+  }
+  for (int e2 = p.e; e2 < p.e1; e2 += NW) {
+    const float4* ab = reinterpret_cast<const float4*>(C.mvals + (size_t)e2 * 256);
+    const float4 a0 = ab[lane], a1 = ab[32 + lane];
+    const int g0 = C.gptr[e2], g1 = C.gptr[e2 + 1];
+    int m[kGMem];
+#pragma unroll
+    for (int j = 0; j < kGMem; ++j) m[j] = g0 + j < g1 ? C.gmem[g0 + j] : 0;
+    const float4 xv = gather_t4(F.rt, C.gmem, g0, g1, m, cq);
+    s0 += dot4(a0, xv);
+    s1 += dot4(a1, xv);
+  }
+  s0 += __shfl_xor_sync(kFull, s0, 1);
+  s0 += __shfl_xor_sync(kFull, s0, 2);
+  s1 += __shfl_xor_sync(kFull, s1, 1);
+  s1 += __shfl_xor_sync(kFull, s1, 2);
+  if ((lane & 3) == 0) {
+    part[wi * 16 + (lane >> 2)] = s0;
+    part[wi * 16 + 8 + (lane >> 2)] = s1;
+  }
+  __syncthreads();
+  float d0 = 0.f;
+  if (t < 16) {
+    float qs = 0.f;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) qs += part[k * 16 + t];
+    d0 = row_dinv<float, 16>(dr, bsm) * inv_theta;
+    w[t] = bsm[t] - qs;
+  }
+  __syncthreads();
+  if (t < 16) {
+    const float d1 = c1 * d0 + c2 * row_dinv<float, 16>(dr, w);
+    const size_t idx = (size_t)a * 16 + t;
+    C.r[1 - rc][idx] = w[t];
+    C.d[1 - dc][idx] = d1;
+    C.x[xc][idx] = d0 + d1;
   }
 }
 
@@ -760,6 +919,10 @@ static VLevel<T> describe(Level& L) {
   v.ap_ptr = L.ap_ptr.as<int>();
   v.ap_cols = L.ap_cols.as<int>();
   v.ap_vals = (const T*)L.ap_vals.p;
+  v.gptr = L.gptr.as<int>();
+  v.gmem = L.gmem.as<int>();
+  v.mvals = (const T*)L.mvals32.p;
+  v.rt = (T*)L.rt.p;
   v.b = L.vb.as<T>();
   v.x[0] = L.vx.as<T>();
   v.x[1] = L.vt.as<T>();
@@ -795,14 +958,28 @@ static void run(ba_problem* P, const double* r, double* z, double* dpart, bool f
   cudaStream_t st = P->stream;
   for (int l = 0; l + 1 < nl; ++l) {
     const VLevel<T>& L = V[l];
-    // step 0 of the coarse levels is done by the restriction that produces their b, and of
-    // level 0 by the PCG update when first_done
+    const bool folded = P->levels[l].folded, fold_next = P->levels[l + 1].folded;
+    // step 0 of the coarse levels is done by the restriction that produces their b (on a
+    // folded level: with step 1, by k_ph_cstep), and of level 0 by the PCG update when
+    // first_done
     if (l == 0 && !first_done) {
       const int g = warps_grid(L.n);
       if (L.bs == 9) launch_k(P, k_ph_first<T, 9>, g, kPhaseBS, 0, L, r);
       else launch_k(P, k_ph_first<T, 16>, g, kPhaseBS, 0, L, r);
     }
-    for (int k = 1; k < pre; ++k) {
+    int k1 = 1;
+    if constexpr (std::is_same_v<T, float>) {
+      if (folded) {
+        double c1, c2;
+        cheb_coeffs(P->levels[l], 1, c1, c2);
+        launch_k(P, k_ph_cstep<RowCta<16>::kThreads / 32>, L.n, RowCta<16>::kThreads, 0, V[l - 1], L, bit(dm, l),
+                 bit(rm, l), bit(xm, l), (float)c1, (float)c2);
+        rm ^= 1u << l;
+        dm ^= 1u << l;
+        k1 = 2;
+      }
+    }
+    for (int k = k1; k < pre; ++k) {
       double c1, c2;
       cheb_coeffs(P->levels[l], k, c1, c2);
       if (L.bs == 9)
@@ -814,6 +991,12 @@ static void run(ba_problem* P, const double* r, double* z, double* dpart, bool f
                                                                (double*)nullptr);
       rm ^= 1u << l;
       dm ^= 1u << l;
+    }
+    if (fold_next) {
+      // the next level's restriction terms with the residual; no restriction launch
+      if (L.bs == 9) launch_k(P, k_ph_residual<T, 9, true>, L.n, RowCta<9>::kThreads, 0, L, bit(dm, l), bit(rm, l));
+      else launch_k(P, k_ph_residual<T, 16, true>, L.n, RowCta<16>::kThreads, 0, L, bit(dm, l), bit(rm, l));
+      continue;
     }
     if (L.bs == 9) launch_k(P, k_ph_residual<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(dm, l), bit(rm, l));
     else launch_k(P, k_ph_residual<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(dm, l), bit(rm, l));
@@ -851,9 +1034,59 @@ static void run(ba_problem* P, const double* r, double* z, double* dpart, bool f
   }
 }
 
-// Called at the end of the multigrid setup: whether the fused-phase cycle applies.
+// M_aj = A_aj D_j^-1 / theta of a folded coarse level: one CTA per block, thread (u, v)
+__global__ void __launch_bounds__(256) k_fold_blocks(int nnzb, const int* __restrict__ cols,
+                                                     const float* __restrict__ vals, const float* __restrict__ Dinv,
+                                                     const double* __restrict__ cheb, float* __restrict__ out) {
+  __shared__ float A[256], D[256];
+  const int e = blockIdx.x, t = threadIdx.x, u = t >> 4, v = t & 15;
+  if (e >= nnzb) return;
+  A[t] = vals[(size_t)e * 256 + t];
+  D[t] = Dinv[(size_t)cols[e] * 256 + t];
+  __syncthreads();
+  float s = 0.f;
+#pragma unroll
+  for (int w = 0; w < 16; ++w) s += A[u * 16 + w] * D[w * 16 + v];
+  out[(size_t)e * 256 + t] = s * (float)(1.0 / cheb[0]);
+}
+
+// per block (a, j) of coarse level C, the fine members of aggregate j (F's member lists),
+// once per hierarchy
+static void fold_symbolic(ba_problem* P, Level& F, Level& C) {
+  std::vector<int> rp(C.n + 1), cl(std::max(C.nnzb, 1)), ap(C.n + 1), am(std::max(F.n, 1));
+  BA_CUDA(cudaMemcpyAsync(rp.data(), C.row_ptr.p, sizeof(int) * (C.n + 1), cudaMemcpyDeviceToHost, P->stream));
+  if (C.nnzb) BA_CUDA(cudaMemcpyAsync(cl.data(), C.cols.p, sizeof(int) * C.nnzb, cudaMemcpyDeviceToHost, P->stream));
+  BA_CUDA(cudaMemcpyAsync(ap.data(), F.agg_ptr.p, sizeof(int) * (C.n + 1), cudaMemcpyDeviceToHost, P->stream));
+  if (F.n) BA_CUDA(cudaMemcpyAsync(am.data(), F.agg_mem.p, sizeof(int) * F.n, cudaMemcpyDeviceToHost, P->stream));
+  sync(P);
+  BA_REQUIRE(ap[C.n] == F.n, BA_ERR_STATE, "aggregates do not cover the fine level");
+  std::vector<int> gptr(1, 0), gmem;
+  gmem.reserve((size_t)C.nnzb * 4);
+  for (int e = 0; e < C.nnzb; ++e) {
+    const int j = cl[e];
+    for (int g = ap[j]; g < ap[j + 1]; ++g) gmem.push_back(am[g]);
+    gptr.push_back((int)gmem.size());
+  }
+  if (gmem.empty()) gmem.push_back(0);
+  upload(P, C.gptr, gptr);
+  upload(P, C.gmem, gmem);
+  sync(P);
+}
+
+// A folded level's first step reads M instead of A, so A loses its L2 reuse between that
+// step and the residual, and M is formed at every setup: the fold saves a launch only on
+// levels whose operator costs less than a launch (about 2.5 us) to stream again.  Measured:
+// street chain (levels of 11, 3 and 0.6 MB) V-cycle 67.0 -> 63.8 us; city grid with every
+// level folded (level 1: 110 MB) PCG 9.0 -> 9.3 ms and setup 8.0 -> 8.3 ms.
+constexpr size_t kFoldMaxBytes = size_t(16) << 20;
+
+// Called at the end of the multigrid setup: whether the fused-phase cycle applies, and
+// which coarse levels take their restriction folded into their first smoothing kernel
+// (FP32 hierarchy with at least two pre-smoothing steps; smoothed coarse levels whose FP32
+// operator is at most kFoldMaxBytes)
 void fused_vcycle_setup(ba_problem* P) {
   P->vc_ready = false;
+  for (int l = 0; l < P->n_levels; ++l) P->levels[l].folded = false;
   if (!P->opt.fused_vcycle || !P->l0_explicit || P->n_levels < 2) return;
   for (int l = 0; l + 1 < P->n_levels; ++l) {
     const int bs = P->levels[l].bs;
@@ -862,6 +1095,20 @@ void fused_vcycle_setup(ba_problem* P) {
   // (A P of every smoothed level, for the fused prolongation + post-smoothing start, was
   // assembled with the Galerkin products)
   P->vc_ready = true;
+  if (!level_fp32(P) || P->opt.pre_smooth < 2) return;
+  for (int l = 1; l + 1 < P->n_levels; ++l) {
+    Level& C = P->levels[l];
+    Level& F = P->levels[l - 1];
+    if (C.coarsest || C.bs != 16 || sizeof(float) * 256 * (size_t)C.nnzb > kFoldMaxBytes) continue;
+    if (!C.gptr.p) fold_symbolic(P, F, C);
+    C.mvals32.ensure(sizeof(float) * 256 * (size_t)std::max(C.nnzb, 1) + 64);
+    F.rt.ensure(sizeof(float) * 16 * (size_t)std::max(F.n, 1) + 64);
+    k_fold_blocks<<<std::max(C.nnzb, 1), 256, 0, P->stream>>>(C.nnzb, C.cols.as<int>(), C.vals32.as<float>(),
+                                                             C.Dinv32.as<float>(), C.cheb.as<double>(),
+                                                             C.mvals32.as<float>());
+    launched(P);
+    C.folded = true;
+  }
 }
 
 void fused_vcycle(ba_problem* P, const double* r, double* z, double* rz_part, bool first_done) {
