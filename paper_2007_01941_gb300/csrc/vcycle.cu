@@ -94,6 +94,11 @@ struct RowCta {
   static constexpr int kPart = kCol ? G * BS * BS + G * BS : G * BS;
 };
 
+// FP32 level-0 phases: at least N CTAs per SM (N x 152 >= 2,000 rows), so that a
+// 2,000-camera level runs in one wave (the step kernel had 13 per SM at 48 registers)
+template <typename T, int BS, int N>
+constexpr int phase_min_blocks() { return BS == 9 && sizeof(T) == 4 ? N : 1; }
+
 // the first kPre blocks of thread (u, h)'s share of block row i (row u of each; column u
 // for 9 x 9 blocks, so that a group's loads cover its block contiguously) and where its
 // remaining blocks start
@@ -395,7 +400,7 @@ k_pcg_update_first(VLevel<T> L, double* __restrict__ x, double* __restrict__ r, 
 // Chebyshev step k >= 1 on row blockIdx.x: q = A din; rout = rin - q;
 // dout = c1 din + c2 D^-1 rout; x += dout (out: FP64 copy of the new x, level 0's last step)
 template <typename T, int BS>
-__global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_step(VLevel<T> L, int dc, int rc, int xc, T c1, T c2,
+__global__ void __launch_bounds__(RowCta<BS>::kThreads, phase_min_blocks<T, BS, 16>()) k_ph_step(VLevel<T> L, int dc, int rc, int xc, T c1, T c2,
                                                                  double* __restrict__ out, const double* __restrict__ rdot,
                                                                  double* __restrict__ dpart) {
   __shared__ T part[RowCta<BS>::kPart];
@@ -714,7 +719,7 @@ __global__ void __launch_bounds__(256) k_ph_coarsest(VLevel<T> C) {
 //   r = b - A x' = s - (A P) x_c,  d = D^-1 r / theta,  x'' = x' + d,
 // so row i needs x_c only, not its neighbours' prolonged x'.
 template <typename T, int BS>
-__global__ void __launch_bounds__(RowCta<BS>::kThreads) k_ph_post_first_ap(VLevel<T> L, VLevel<T> C, int xc, int xcl,
+__global__ void __launch_bounds__(RowCta<BS>::kThreads, phase_min_blocks<T, BS, 14>()) k_ph_post_first_ap(VLevel<T> L, VLevel<T> C, int xc, int xcl,
                                                                           int rc, int dc, double* __restrict__ out,
                                                                           const double* __restrict__ rdot,
                                                                           double* __restrict__ dpart) {
