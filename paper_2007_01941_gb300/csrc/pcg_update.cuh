@@ -28,7 +28,26 @@ struct PcgCheck {
   double tau;
   int use_cond;       // 1: set the graph's while condition
   cudaGraphConditionalHandle h;
+  const double* pq_part;  // the product's per-CTA shares of p.q (n_pq_part > 0), else
+  int n_pq_part;          // p.q is in scal[S_PQ]
 };
+
+// p.q for every thread of the CTA: the product's per-CTA shares added in the same order by
+// every CTA (so that the product needs no grid-wide reduction of its own), or scal[S_PQ]
+template <int BS>
+__device__ __forceinline__ double pcg_pq(const PcgCheck& ck) {
+  if (ck.n_pq_part == 0) return ck.scal[S_PQ];
+  __shared__ double pq_sm;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < ck.n_pq_part; k += BS) s += __ldcg(ck.pq_part + k);
+  s = block_sum<BS>(s);
+  if (threadIdx.x == 0) {
+    pq_sm = s;
+    if (blockIdx.x == 0) ck.scal[S_PQ] = s;
+  }
+  __syncthreads();
+  return pq_sm;
+}
 
 // acc: this thread's share of r.r; ok: alpha was usable (p.q > 0, finite)
 template <int BS>

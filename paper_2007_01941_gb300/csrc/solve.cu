@@ -473,6 +473,17 @@ static void pcg_tail(ba_problem* P) {
 // ---------------------------------------------------------------------------
 constexpr int kSpmvBS = 128;
 
+// the product's p.q: summed over the grid by its last CTA into pq_out, or (pq_out null)
+// left as one share per CTA for the update kernel to add
+__device__ __forceinline__ void spmv_pq_store(double dot, double* partial, unsigned* counter, double* pq_out) {
+  if (pq_out) {
+    grid_sum_store<kSpmvBS>(dot, partial, counter, pq_out);
+    return;
+  }
+  const double s = block_sum<kSpmvBS>(dot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
 // q = S p with the FP64 blocks (one warp per block row: lane r + 9k takes row r of
 // blocks k, k + 3, ...; its first block is loaded before the programmatic wait) and p.q
 __global__ void __launch_bounds__(kSpmvBS)
@@ -517,7 +528,7 @@ k_pcg_spmv_pq(int n, const int* __restrict__ row_ptr, const int* __restrict__ co
     q[idx] = qi;
     dot = p[idx] * qi;
   }
-  grid_sum_store<kSpmvBS>(dot, partial, counter, pq_out);
+  spmv_pq_store(dot, partial, counter, pq_out);
 }
 
 __global__ void __launch_bounds__(kVecBS)
@@ -525,7 +536,7 @@ k_pcg_update_check(size_t n, double* __restrict__ x, double* __restrict__ r, con
                    const double* __restrict__ q, PcgCheck ck) {
   pdl_trigger();
   pdl_wait();
-  const double pq = ck.scal[S_PQ], rz = ck.scal[S_TMP2];
+  const double pq = pcg_pq<kVecBS>(ck), rz = ck.scal[S_TMP2];
   const double alpha = rz / pq;
   const bool ok = pq > 0.0 && isfinite(alpha);
   double acc = 0.0;
@@ -613,7 +624,7 @@ k_pcg_spmv_pq_df(int n, const int* __restrict__ row_ptr, const int* __restrict__
     q[idx] = qi;
     dot = p[idx] * qi;
   }
-  grid_sum_store<kSpmvBS>(dot, partial, counter, pq_out);
+  spmv_pq_store(dot, partial, counter, pq_out);
 }
 
 // p = z + beta p with beta = rz / scal[S_RZ] (p = z when first), rz the sum of the rows'
@@ -677,18 +688,24 @@ static void assembled_precond_direction(ba_problem* P, int first) {
            S_RZ, P->Dc.as<double>(), (double*)nullptr, assembled_split(P));
 }
 
+// CTAs of the product; up to kPqShares of them, the update kernel adds their p.q shares
+// (in every CTA: a few hundred loads each) instead of the product's last CTA
+constexpr int kPqShares = 1024;
+static int spmv_blocks(ba_problem* P) { return cdiv(P->levels[0].n, kSpmvBS / 32); }
+
 static void assembled_spmv(ba_problem* P) {
   const Level& L0 = P->levels[0];
-  const int nb = cdiv(L0.n, kSpmvBS / 32);
+  const int nb = spmv_blocks(P);
+  double* pq_out = nb <= kPqShares ? nullptr : P->scal.as<double>() + S_PQ;
   KernelTimer kt(P, BA_KT_OUTER_BSR);
   if (P->opt.precision == BA_MIXED)
     launch_k(P, k_pcg_spmv_pq_df, nb, kSpmvBS, 0, L0.n, L0.row_ptr.as<int>(), L0.cols.as<int>(),
              L0.valsdf.as<float2>(), P->xsplit.as<float2>(), P->p.as<double>(), P->q.as<double>(),
-             P->partial2.as<double>(), P->counter.as<unsigned>() + 1, P->scal.as<double>() + S_PQ);
+             P->partial2.as<double>(), P->counter.as<unsigned>() + 1, pq_out);
   else
     launch_k(P, k_pcg_spmv_pq, nb, kSpmvBS, 0, L0.n, L0.row_ptr.as<int>(), L0.cols.as<int>(),
              L0.vals64.as<double>(), P->p.as<double>(), P->q.as<double>(), P->partial2.as<double>(),
-             P->counter.as<unsigned>() + 1, P->scal.as<double>() + S_PQ);
+             P->counter.as<unsigned>() + 1, pq_out);
 }
 
 // the update kernel; with the fused V-cycle it also forms the next cycle's level-0
@@ -697,8 +714,10 @@ static bool update_starts_vcycle(ba_problem* P) { return P->opt.preconditioner =
 
 static void assembled_update(ba_problem* P, double* x, int use_cond, cudaGraphConditionalHandle h) {
   const size_t n = (size_t)P->n_c * 9;
+  const int nb = spmv_blocks(P);
   const PcgCheck ck{P->scal.as<double>(), P->partial.as<double>(), P->counter.as<unsigned>(), P->flags.as<int>(),
-                    P->opt.max_iters, P->opt.rtol * P->opt.rtol, P->opt.stop_rule, P->opt.tau, use_cond, h};
+                    P->opt.max_iters, P->opt.rtol * P->opt.rtol, P->opt.stop_rule, P->opt.tau, use_cond, h,
+                    P->partial2.as<double>(), nb <= kPqShares ? nb : 0};
   if (update_starts_vcycle(P)) {
     fused_update_first(P, x, P->r.as<double>(), P->p.as<double>(), P->q.as<double>(), ck);
     return;

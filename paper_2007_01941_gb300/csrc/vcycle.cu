@@ -360,7 +360,7 @@ k_pcg_update_first(VLevel<T> L, double* __restrict__ x, double* __restrict__ r, 
   }
   pdl_trigger();
   pdl_wait();
-  const double pq = ck.scal[S_PQ], rz = ck.scal[S_TMP2];
+  const double pq = pcg_pq<kUpdBS>(ck), rz = ck.scal[S_TMP2];
   const double alpha = rz / pq;
   const bool ok = pq > 0.0 && isfinite(alpha);
   double acc = 0.0;
