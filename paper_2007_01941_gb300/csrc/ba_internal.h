@@ -135,9 +135,11 @@ struct Level {
   int N = 0;                    // coarsest: dense size n*bs
   DBuf Ainv;                    // coarsest: double [N][N]
   DBuf vx, vb, vr, vd, vq, vt, vs;  // V-cycle vectors in the level's precision
-  // restriction folded into the V-cycle's kernels (FP32 hierarchy, >= 2 pre-smoothing
-  // steps): on a smoothed coarse level, its fine members per operator block (gptr, gmem)
-  // and the blocks M_aj = A_aj D_j^-1 / theta; on the level above it, t_i = Q_i^T s_i
+  // restriction into this level folded into the V-cycle's next kernel (a small coarsest
+  // level's solve; the first smoothing kernel of a smoothed coarse level, FP32 hierarchy,
+  // >= 2 pre-smoothing steps): on a smoothed coarse level, its fine members per operator
+  // block (gptr, gmem) and the blocks M_aj = A_aj D_j^-1 / theta; on the level above it,
+  // t_i = Q_i^T s_i
   bool folded = false;
   DBuf gptr, gmem, mvals32;
   DBuf rt;

@@ -713,6 +713,74 @@ __global__ void __launch_bounds__(256) k_ph_coarsest(VLevel<T> C) {
   }
 }
 
+// The coarsest solve with the restriction into it folded in (coarsest level of at most
+// kCoarseFoldMax dofs): every CTA forms b_c[16 a + s] = sum_{i in a} t_i[s] in shared
+// memory from the t left by the last smoothed level's residual kernel, then x_c = A_c^-1
+// b_c as k_ph_coarsest.  (Every CTA repeats the 4.6 KB gather of a 21-node coarsest
+// level; the restriction launch it replaces cost about as much as a V-cycle phase.)
+constexpr int kCoarseFoldMax = 32 * kCoarseRowMax;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ph_coarsest_t(VLevel<T> F, VLevel<T> C) {
+  __shared__ T bsm[kCoarseFoldMax];
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  // static data first: this warp's row of the inverse, and for this thread's entries of
+  // b_c (k = threadIdx.x + 256 h) their members
+  double ar[kCoarseRowMax];
+  if (gw < C.N) {
+    const double* a = C.Ainv + (size_t)gw * C.Np;
+#pragma unroll
+    for (int k = 0; k < kCoarseRowMax; ++k) {
+      const int j = lane + 32 * k;
+      ar[k] = j < C.N ? a[j] : 0.0;
+    }
+  }
+  constexpr int kH = kCoarseFoldMax / 256;
+  int g0[kH], g1[kH], m[kH][kGMem];
+#pragma unroll
+  for (int h = 0; h < kH; ++h) {
+    const int k = threadIdx.x + 256 * h;
+    g0[h] = g1[h] = 0;
+    if (k < C.N) {
+      g0[h] = F.agg_ptr[k >> 4];
+      g1[h] = F.agg_ptr[(k >> 4) + 1];
+    }
+#pragma unroll
+    for (int j = 0; j < kGMem; ++j) m[h][j] = g0[h] + j < g1[h] ? F.agg_mem[g0[h] + j] : 0;
+  }
+  pdl_trigger();
+  pdl_wait();
+#pragma unroll
+  for (int h = 0; h < kH; ++h) {
+    const int k = threadIdx.x + 256 * h;
+    if (k < C.N) {
+      T s = T(0);
+#pragma unroll
+      for (int j = 0; j < kGMem; ++j)
+        if (g0[h] + j < g1[h]) s += F.rt[(size_t)m[h][j] * 16 + (k & 15)];
+      for (int g = g0[h] + kGMem; g < g1[h]; ++g) s += F.rt[(size_t)F.agg_mem[g] * 16 + (k & 15)];
+      bsm[k] = s;
+    }
+  }
+  __syncthreads();
+  for (int row = gw; row < C.N; row += nw) {
+    double acc = 0.0;
+    if (row == gw) {
+#pragma unroll
+      for (int k = 0; k < kCoarseRowMax; ++k) {
+        const int j = lane + 32 * k;
+        if (j < C.N) acc += ar[k] * (double)bsm[j];
+      }
+    } else {
+      const double* a = C.Ainv + (size_t)row * C.Np;
+      for (int j = lane; j < C.N; j += 32) acc += a[j] * (double)bsm[j];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) C.x[0][row] = (T)acc;
+  }
+}
+
 // Prolongation and post-smoothing step 0 in one launch, from A P (assembled with the
 // hierarchy): with s = b - A x the residual of the pre-smoothed iterate (left in the free
 // r buffer by the residual kernel) and x' = x + P x_c,
@@ -1010,7 +1078,10 @@ static void run(ba_problem* P, const double* r, double* z, double* dpart, bool f
     if (L.bs == 9) launch_k(P, k_ph_restrict<T, 9>, gc, kPhaseBS, 0, L, V[l + 1], res);
     else launch_k(P, k_ph_restrict<T, 16>, gc, kPhaseBS, 0, L, V[l + 1], res);
   }
-  launch_k(P, k_ph_coarsest<T>, warps_grid(V[nl - 1].N), kPhaseBS, 0, V[nl - 1]);
+  if (P->levels[nl - 1].folded)
+    launch_k(P, k_ph_coarsest_t<T>, warps_grid(V[nl - 1].N), kPhaseBS, 0, V[nl - 2], V[nl - 1]);
+  else
+    launch_k(P, k_ph_coarsest<T>, warps_grid(V[nl - 1].N), kPhaseBS, 0, V[nl - 1]);
   for (int l = nl - 2; l >= 0; --l) {
     const VLevel<T>& L = V[l];
     double* o = (l == 0 && post == 1) ? z : nullptr;
@@ -1100,6 +1171,15 @@ void fused_vcycle_setup(ba_problem* P) {
   // (A P of every smoothed level, for the fused prolongation + post-smoothing start, was
   // assembled with the Galerkin products)
   P->vc_ready = true;
+  {
+    // the restriction into a small coarsest level goes into its solve (k_ph_coarsest_t)
+    Level& C = P->levels[P->n_levels - 1];
+    Level& F = P->levels[P->n_levels - 2];
+    if (C.coarsest && C.bs == 16 && C.n * C.bs <= kCoarseFoldMax) {
+      F.rt.ensure((level_fp32(P) ? sizeof(float) : sizeof(double)) * 16 * (size_t)std::max(F.n, 1) + 64);
+      C.folded = true;
+    }
+  }
   if (!level_fp32(P) || P->opt.pre_smooth < 2) return;
   for (int l = 1; l + 1 < P->n_levels; ++l) {
     Level& C = P->levels[l];
