@@ -533,10 +533,12 @@ def kernel_table(prob, _ffi, s, info, prec, kt, kt_var, hbm, peak_note, fp32_pea
     vbytes, vc_launches = None, None
     if info["n_levels"] > 1 and info["level0_explicit"]:
         vbytes, vdetail = vcycle_bytes(prob, _ffi, 4 if prec == _ffi.BA_MIXED else 8)
-        nl = info["n_levels"]
-        # fused phases: level 0 first/step/residual/restrict, each coarser smoothed level
-        # step/residual/restrict, the coarsest, and two post-smoothing phases per level
-        vc_launches = 4 + 3 * (nl - 2) + 1 + 2 * (nl - 1)
+        # launches of one application inside the PCG: those of a standalone application
+        # (ba_precond_apply) less its level-0 step 0, which the PCG's update kernel forms
+        import torch
+        k0 = prob.info()["kernel_launches"]
+        prob.precond_apply(torch.ones(n_c, 9, dtype=torch.float64, device=prob.device))
+        vc_launches = prob.info()["kernel_launches"] - k0 - 1
     kernels = {}
     for name, (tot, n) in list(kt.items()) + list(kt_var.items()):
         if n == 0:
