@@ -94,8 +94,8 @@ typedef struct {
                            The paired-FP32 and FP32 products read stored blocks either way (0);
                            ba_adjoint always rebuilds its blocks */
   int max_agg;          /* Algorithm 2 aggregate size cap (20, Section 3.2) */
-  int pre_smooth;       /* Chebyshev steps before the coarse correction (2, Section 3.4) */
-  int post_smooth;      /* Chebyshev steps after (2) */
+  int pre_smooth;       /* Chebyshev steps before the coarse correction, 1 .. 8 (2, Section 3.4) */
+  int post_smooth;      /* Chebyshev steps after, 1 .. 8 (2) */
   int lanczos_steps;    /* operator applications for lambda_max (5, Section 3.4) */
   int coarse_max_nodes; /* stop coarsening at <= this many nodes (32) */
   int max_levels;       /* hierarchy depth cap (10) */

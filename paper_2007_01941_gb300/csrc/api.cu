@@ -132,7 +132,9 @@ ba_status ba_create(int n_cams, int n_pts, int n_obs, const int32_t* cam_idx, co
     BA_REQUIRE(o.precision == BA_FP64 || o.precision == BA_MIXED, BA_ERR_INVALID_ARG, "bad precision");
     BA_REQUIRE(o.preconditioner >= 0 && o.preconditioner <= 2, BA_ERR_INVALID_ARG, "bad preconditioner");
     BA_REQUIRE(o.max_agg >= 2 && o.max_agg <= 64, BA_ERR_INVALID_ARG, "max_agg must be in [2, 64]");
-    BA_REQUIRE(o.pre_smooth >= 1 && o.post_smooth >= 1, BA_ERR_INVALID_ARG, "smoothing steps must be >= 1");
+    BA_REQUIRE(o.pre_smooth >= 1 && o.post_smooth >= 1 && o.pre_smooth <= ba::kMaxSmooth &&
+                   o.post_smooth <= ba::kMaxSmooth,
+               BA_ERR_INVALID_ARG, "smoothing steps must be in 1 .. 8");
     BA_REQUIRE(o.lanczos_steps >= 1 && o.lanczos_steps <= 8, BA_ERR_INVALID_ARG, "lanczos_steps in [1, 8]");
     BA_REQUIRE(o.max_iters >= 1 && o.rtol >= 0.0, BA_ERR_INVALID_ARG, "bad PCG limits");
     BA_REQUIRE(o.cheb_hi > o.cheb_lo && o.cheb_lo > 0.0, BA_ERR_INVALID_ARG, "bad Chebyshev interval");
@@ -182,22 +184,8 @@ void ba_destroy(ba_problem* P) {
     cudaEventDestroy(P->ev_fork);
     cudaEventDestroy(P->ev_join);
   }
-  ba::DBuf* bufs[] = {&P->obs_user, &P->obs_cam, &P->obs_ptu, &P->obs_pt, &P->pt_ptr, &P->pt_user, &P->cam_ptr,
-                      &P->cam_obs, &P->tile_pt, &P->tile_desc, &P->tile_perm, &P->lz_vec, &P->lz_red, &P->lz_cnt, &P->lz_ptr, &P->chunk_tile, &P->chunk_cam, &P->camx, &P->fres, &P->J64,
-                      &P->J64, &P->J32, &P->J32lo, &P->cams_lin, &P->pts_lin, &P->obs_lin, &P->Dc, &P->Dp,
-                      &P->Cinv64, &P->Cinv32, &P->Cinv32lo, &P->xsplit, &P->camdf, &P->wpdf, &P->Xdf, &P->gc, &P->gp, &P->wp, &P->rhs, &P->Dc32, &P->Scc, &P->Scc_inv,
-                      &P->Scc_inv32, &P->cam_ubnd, &P->pc_diag, &P->Scc_pc, &P->ptsdf, &P->x, &P->r, &P->z, &P->p, &P->q, &P->y32a, &P->y32b, &P->delta_c,
-                      &P->delta_p, &P->scal, &P->partial, &P->partial2, &P->rzpart, &P->counter, &P->flags, &P->scratch, &P->scratch2};
-  for (ba::DBuf* b : bufs) b->release();
-  for (ba::Level& L : P->levels) {
-    ba::DBuf* lb[] = {&L.row_ptr, &L.cols, &L.W, &L.vals64, &L.vals32, &L.sptr, &L.sidx, &L.agg, &L.agg_ptr,
-                      &L.agg_mem, &L.K, &L.Q64, &L.Q32, &L.kept, &L.Dblk, &L.Dinv64, &L.Dinv32, &L.cheb,
-                      &L.Ainv, &L.vx, &L.vb, &L.vr, &L.vd, &L.vq, &L.vt, &L.vs, &L.pair_ptr, &L.pairs,
-                      &L.blk_row, &L.up_blk, &L.mirror, &L.Dblk32, &L.valsdf, &L.ap_ptr, &L.ap_cols, &L.ap_lptr,
-                      &L.ap_list, &L.ap_vals, &L.gal_ptr,
-                      &L.gal_list, &L.gal_row};
-    for (ba::DBuf* b : lb) b->release();
-  }
+  ba::for_each_problem_buf(P, [](ba::DBuf& b) { b.release(); });
+  for (ba::Level& L : P->levels) ba::for_each_level_buf(L, [](ba::DBuf& b) { b.release(); });
   if (P->h_scal) cudaFreeHost(P->h_scal);
   if (P->h_flags) cudaFreeHost(P->h_flags);
   if (P->h_cheb) cudaFreeHost(P->h_cheb);
@@ -390,7 +378,13 @@ ba_status ba_get_info(ba_problem* P, ba_info* info) {
     info->level_nodes[l] = L.n;
     info->level_block[l] = L.bs;
     info->level_nnzb[l] = L.nnzb;
-    info->level_lambda_max[l] = L.coarsest ? 0.0 : L.lam_max;
+    // the Lanczos estimate lives on the device (slot 3 of the level's Chebyshev data)
+    double lam = 0.0;
+    if (!L.coarsest && L.cheb.p &&
+        cudaMemcpyAsync(P->h_cheb, L.cheb.p, sizeof(double) * 4, cudaMemcpyDeviceToHost, P->stream) == cudaSuccess &&
+        cudaStreamSynchronize(P->stream) == cudaSuccess)
+      lam = P->h_cheb[3];
+    info->level_lambda_max[l] = lam;
   }
   info->pcg_iters = P->pcg_iters;
   info->pcg_rel_res = P->pcg_rel;

@@ -28,7 +28,10 @@ struct BlockInvBatch {
   BlockInvSeg s[kMaxInvSegs];
   int nseg, total;
 };
-constexpr int kChebSlots = 24;   // per level: theta, delta, sigma_1, lambda_max, pad, alphas, betas
+constexpr int kMaxSmooth = 8;    // Chebyshev steps per smoothing pass
+// per level: theta, delta, sigma_1, lambda_max, pad, Lanczos alphas (8..15) and betas
+// (16..23), then (c1, c2) of Chebyshev steps 1 .. kMaxSmooth - 1 (24 + 2 (k - 1))
+constexpr int kChebSlots = 24 + 2 * kMaxSmooth;
 constexpr int kScalars = 64;     // device scalar slots per problem
 
 // Error raised inside the library; converted to a ba_status at the C boundary.
@@ -128,9 +131,7 @@ struct Level {
   DBuf kept;                    // uint32 [n] kept-dof masks of this level's nodes
   DBuf Dblk, Dinv64, Dinv32;    // diagonal blocks and their inverses [n][bs][bs]
   DBuf Dblk32;                  // FP32 copy of the diagonal blocks (mixed precision)
-  DBuf cheb;                    // double[4]: theta, delta, sigma1, lambda_max
-  double cheb_host[4] = {1, 1, 1, 1};  // host copy of the same
-  double lam_max = 0.0;
+  DBuf cheb;                    // double[kChebSlots]: Chebyshev parameters, Lanczos data, step coefficients
   bool coarsest = false;
   int N = 0;                    // coarsest: dense size n*bs
   DBuf Ainv;                    // coarsest: double [N][N]
@@ -235,7 +236,7 @@ struct ba_problem {
   ba::DBuf counter;             // unsigned [8]
   ba::DBuf flags;               // int [F_COUNT]
   double* h_scal = nullptr;     // pinned host mirror
-  double* h_cheb = nullptr;     // pinned [16][kChebSlots] Lanczos data of the levels
+  double* h_cheb = nullptr;     // pinned [16][kChebSlots] host copies of the levels' Chebyshev data
   int* h_flags = nullptr;
   ba::DBuf scratch;             // general scratch
   ba::DBuf scratch2;
@@ -244,8 +245,7 @@ struct ba_problem {
   // rebuilt whenever a setup call may have moved buffers
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t pcg_exec = nullptr;
-  int graph_epoch = 0;          // bumped by every setup call
-  int pcg_graph_epoch = -1;     // epoch the graph was built for
+  uint64_t pcg_graph_key = 0;   // signature of what the PCG graph was captured with
   bool graphs_ok = true;        // false after a failed build: eager fallback
   long long pcg_graph_head = 0, pcg_graph_body = 0;  // kernels per graph part
 
@@ -393,5 +393,30 @@ void dot32(ba_problem* P, const float* a, const float* b, size_t n, int slot);
 int reduce_blocks(ba_problem* P, size_t n);
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Every device buffer of a problem and of a level (released by ba_destroy; their addresses
+// and capacities are part of the PCG graph's signature).
+template <class F>
+void for_each_problem_buf(ba_problem* P, F&& f) {
+  DBuf* bufs[] = {&P->obs_user, &P->obs_cam, &P->obs_ptu, &P->obs_pt, &P->pt_ptr, &P->pt_user, &P->cam_ptr,
+                  &P->cam_obs, &P->tile_pt, &P->tile_desc, &P->tile_perm, &P->lz_vec, &P->lz_red, &P->lz_cnt,
+                  &P->lz_ptr, &P->chunk_tile, &P->chunk_cam, &P->camx, &P->fres, &P->J64, &P->J32, &P->J32lo,
+                  &P->cams_lin, &P->pts_lin, &P->obs_lin, &P->Dc, &P->Dp, &P->Cinv64, &P->Cinv32, &P->Cinv32lo,
+                  &P->xsplit, &P->camdf, &P->wpdf, &P->Xdf, &P->gc, &P->gp, &P->wp, &P->rhs, &P->Dc32, &P->Scc,
+                  &P->Scc_inv, &P->Scc_inv32, &P->cam_ubnd, &P->pc_diag, &P->Scc_pc, &P->ptsdf, &P->x, &P->r,
+                  &P->z, &P->p, &P->q, &P->y32a, &P->y32b, &P->delta_c, &P->delta_p, &P->scal, &P->partial,
+                  &P->partial2, &P->rzpart, &P->counter, &P->flags, &P->scratch, &P->scratch2};
+  for (DBuf* b : bufs) f(*b);
+}
+
+template <class F>
+void for_each_level_buf(Level& L, F&& f) {
+  DBuf* bufs[] = {&L.row_ptr, &L.cols, &L.W, &L.vals64, &L.vals32, &L.sptr, &L.sidx, &L.agg, &L.agg_ptr,
+                  &L.agg_mem, &L.K, &L.Q64, &L.Q32, &L.kept, &L.Dblk, &L.Dinv64, &L.Dinv32, &L.cheb, &L.Ainv,
+                  &L.vx, &L.vb, &L.vr, &L.vd, &L.vq, &L.vt, &L.vs, &L.pair_ptr, &L.pairs, &L.blk_row, &L.up_blk,
+                  &L.mirror, &L.Dblk32, &L.valsdf, &L.ap_ptr, &L.ap_cols, &L.ap_lptr, &L.ap_list, &L.ap_vals,
+                  &L.gal_ptr, &L.gal_list, &L.gal_row, &L.gptr, &L.gmem, &L.mvals32, &L.rt};
+  for (DBuf* b : bufs) f(*b);
+}
 
 }  // namespace ba

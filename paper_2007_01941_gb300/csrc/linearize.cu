@@ -272,7 +272,6 @@ static int lin_grid(ba_problem* P) {
 void linearize(ba_problem* P, const double* cams, const double* pts, const double* obs) {
   const size_t ld = P->ld;
   const bool mixed = P->opt.precision == BA_MIXED;
-  P->graph_epoch++;
   P->camx.ensure(sizeof(double) * kCamx * std::max(P->n_c, 1));
   P->fres.ensure(sizeof(double) * 2 * ld);
   if (!mixed) P->J64.ensure(sizeof(double) * kRec * ld);

@@ -1194,68 +1194,93 @@ static void lanczos(ba_problem* P, int l) {
                           P->stream));
 }
 
-// Largest eigenvalue of the symmetric tridiagonal (alpha[0..m), beta[0..m-1)) by bisection
-// with Sturm counts (host); returns the Chebyshev parameters {theta, delta, sigma_1, lam}.
-static void tridiag_cheb(const double* al_in, const double* be_in, int m, double lo_f, double hi_f, double out[4]) {
-  double al[16], be[16];
+// Largest eigenvalue of each level's Lanczos tridiagonal (alpha_0..m-1 in slots 8..,
+// beta_0..m-2 in slots 16..) by multisection with Sturm counts, and from it the Chebyshev
+// parameters {theta, delta, sigma_1, lambda_max} of the interval [lo_f, hi_f] lambda_max
+// (Section 3.4) in slots 0..3 and the step coefficients in slots 24...  One warp per level,
+// on the device, so that the V-cycle's kernels read them there and the setup needs no host
+// round trip: each round the 32 lanes count the eigenvalues below 32 points of the current
+// interval and keep the sub-interval where the count reaches m, a factor 33 per round.
+struct ChebLevels {
+  double* cheb[16];
+  int n;
+};
+
+__global__ void __launch_bounds__(512) k_cheb_params(ChebLevels CL, int m, double lo_f, double hi_f) {
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (k >= CL.n) return;
+  double* c = CL.cheb[k];
+  double al[8], be[8];
   int mm = m;
-  for (int j = 0; j < m; ++j) al[j] = al_in[j];
+  for (int j = 0; j < m; ++j) al[j] = c[8 + j];
   for (int j = 0; j + 1 < m; ++j) {
-    be[j] = be_in[j];
+    be[j] = c[16 + j];
     if (!(be[j] > 0.0)) {  // invariant subspace found: truncate
       mm = j + 1;
       break;
     }
   }
+  // Gershgorin interval
   double lo = al[0], hi = al[0];
   for (int j = 0; j < mm; ++j) {
-    const double rad = (j > 0 ? std::fabs(be[j - 1]) : 0.0) + (j + 1 < mm ? std::fabs(be[j]) : 0.0);
-    lo = std::min(lo, al[j] - rad);
-    hi = std::max(hi, al[j] + rad);
+    const double rad = (j > 0 ? fabs(be[j - 1]) : 0.0) + (j + 1 < mm ? fabs(be[j]) : 0.0);
+    lo = fmin(lo, al[j] - rad);
+    hi = fmax(hi, al[j] + rad);
   }
-  auto count_below = [&](double x) {
-    int c = 0;
+  for (int round = 0; round < 64; ++round) {
+    // lane j tests lo + (j + 1) (hi - lo) / 33: are all mm eigenvalues below it?
+    const double x = lo + (double)(lane + 1) * ((hi - lo) / 33.0);
+    int below = 0;
     double d = al[0] - x;
-    if (d < 0) ++c;
+    if (d < 0) ++below;
     for (int j = 1; j < mm; ++j) {
       const double prev = (d == 0.0) ? 1e-300 : d;
       d = (al[j] - x) - be[j - 1] * be[j - 1] / prev;
-      if (d < 0) ++c;
+      if (d < 0) ++below;
     }
-    return c;
-  };
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (count_below(mid) >= mm) hi = mid;
-    else lo = mid;
+    const bool all_below = below >= mm && x > lo && x < hi;
+    const unsigned ball = __ballot_sync(0xffffffffu, all_below);
+    double nlo, nhi;
+    if (ball) {
+      const int f = __ffs(ball) - 1;   // first point with every eigenvalue below it
+      nhi = __shfl_sync(0xffffffffu, x, f);
+      nlo = f > 0 ? __shfl_sync(0xffffffffu, x, f - 1) : lo;
+    } else {
+      nlo = __shfl_sync(0xffffffffu, x, 31);
+      nhi = hi;
+    }
+    if (!(nlo > lo || nhi < hi)) break;   // the interval no longer shrinks
+    lo = fmax(lo, nlo);
+    hi = fmin(hi, nhi);
   }
+  if (lane != 0) return;
   const double lam = hi;
   const double a = lo_f * lam, b = hi_f * lam;
-  out[0] = 0.5 * (b + a);
-  out[1] = 0.5 * (b - a);
-  out[2] = out[0] / out[1];
-  out[3] = lam;
+  c[0] = 0.5 * (b + a);
+  c[1] = 0.5 * (b - a);
+  c[2] = c[0] / c[1];
+  c[3] = lam;
+  // step coefficients (Saad, Alg. 12.1): d_k = c1 d_{k-1} + c2 D^-1 r_k with rho_0 = 1 /
+  // sigma_1, rho_j = 1 / (2 sigma_1 - rho_{j-1}), c1 = rho_k rho_{k-1}, c2 = 2 rho_k / delta
+  double rho = 1.0 / c[2];
+  for (int j = 1; j < kMaxSmooth; ++j) {
+    const double rho_prev = rho;
+    rho = 1.0 / (2.0 * c[2] - rho);
+    c[24 + 2 * (j - 1)] = rho * rho_prev;
+    c[25 + 2 * (j - 1)] = 2.0 * rho / c[1];
+  }
 }
 
-// Ritz values of every smoothed level (one synchronisation for all levels) and their
-// Chebyshev parameters written back to the devices' level buffers.
 static void finish_lanczos(ba_problem* P) {
   const int nl = P->n_levels - 1;
   if (nl <= 0) return;
-  double* h = P->h_cheb;
-  for (int k = 0; k < nl; ++k)
-    BA_CUDA(cudaMemcpyAsync(h + kChebSlots * k, P->levels[k].cheb.p, sizeof(double) * kChebSlots,
-                            cudaMemcpyDeviceToHost, P->stream));
-  sync(P);
+  BA_REQUIRE(nl <= 16, BA_ERR_LIMIT, "more than 16 smoothed levels");
+  ChebLevels CL{};
+  CL.n = nl;
+  for (int k = 0; k < nl; ++k) CL.cheb[k] = P->levels[k].cheb.as<double>();
   const int m = std::min(std::max(P->opt.lanczos_steps, 1), 8);
-  for (int k = 0; k < nl; ++k) {
-    double* c = h + kChebSlots * k;
-    tridiag_cheb(c + 8, c + 16, m, P->opt.cheb_lo, P->opt.cheb_hi, c);
-    P->levels[k].lam_max = c[3];
-    for (int j = 0; j < 4; ++j) P->levels[k].cheb_host[j] = c[j];
-    BA_CUDA(cudaMemcpyAsync(P->levels[k].cheb.p, c, sizeof(double) * 4, cudaMemcpyHostToDevice, P->stream));
-  }
+  k_cheb_params<<<1, 32 * nl, 0, P->stream>>>(CL, m, P->opt.cheb_lo, P->opt.cheb_hi);
+  launched(P);
 }
 
 // ---------------------------------------------------------------------------
@@ -1734,7 +1759,6 @@ static void prolongator_chain(ba_problem* P, cudaStream_t st) {
 void mg_setup(ba_problem* P, bool check) {
   const bool fp32 = level_fp32(P);
   const ba_options& o = P->opt;
-  P->graph_epoch++;
   // check = false (the LM step): the flags of the linearisation and the Schur setup stay
   // for the step's next fetch_checked
   if (check) clear_flags(P);

@@ -753,7 +753,6 @@ void schur_setup(ba_problem* P, double lambda, bool check) {
   const int n_c = P->n_c, n_p = P->n_p;
   const size_t ldp = P->ldp;
   P->lambda = lambda;
-  P->graph_epoch++;
   P->Dc.ensure(sizeof(double) * 9 * n_c + 64);
   P->Dc32.ensure(sizeof(float) * 9 * n_c + 64);
   P->Dp.ensure(sizeof(double) * 3 * ldp);

@@ -726,6 +726,82 @@ static void assembled_update(ba_problem* P, double* x, int use_cond, cudaGraphCo
            P->q.as<double>(), ck);
 }
 
+// Signature of what the captured PCG graph takes from the host: every buffer's address and
+// capacity, the hierarchy's shape, the launch geometry and the options.  The numbers a
+// setup changes (operators, Jacobi blocks, Chebyshev coefficients, the coarse inverse) are
+// read on the device, so the graph is captured again only when this signature changes.
+static uint64_t pcg_graph_key(ba_problem* P) {
+  uint64_t h = 1469598103934665603ull;   // FNV-1a
+  auto val = [&](auto v) {
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+    for (size_t i = 0; i < sizeof(v); ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  };
+  for_each_problem_buf(P, [&](DBuf& b) {
+    val(b.p);
+    val(b.cap);
+  });
+  val(P->n_levels);
+  for (int l = 0; l < P->n_levels; ++l) {
+    Level& L = P->levels[l];
+    val(L.n);
+    val(L.bs);
+    val(L.nnzb);
+    val(L.coarsest);
+    val(L.N);
+    val(L.folded);
+    val(L.ap_nnzb);
+    for_each_level_buf(L, [&](DBuf& b) {
+      val(b.p);
+      val(b.cap);
+    });
+  }
+  val(P->n_c);
+  val(P->n_p);
+  val(P->n_o);
+  val(P->n_sm);
+  val(P->vc_ready);
+  val(P->l0_explicit);
+  val(P->outer_explicit);
+  val(P->pc_shift);
+  val(P->n_chunks);
+  val(P->k3_window);
+  val(P->k3_grid[0]);
+  val(P->k3_grid[1]);
+  val(P->k3_grid_bulk);
+  val(P->k3_grid_df);
+  val(P->k3_grid_rc);
+  const ba_options& o = P->opt;
+  val(o.lambda);
+  val(o.rtol);
+  val(o.max_iters);
+  val(o.precision);
+  val(o.preconditioner);
+  val(o.damping);
+  val(o.recompute_jacobian);
+  val(o.max_agg);
+  val(o.pre_smooth);
+  val(o.post_smooth);
+  val(o.lanczos_steps);
+  val(o.coarse_max_nodes);
+  val(o.max_levels);
+  val(o.cheb_lo);
+  val(o.cheb_hi);
+  val(o.level0_operator);
+  val(o.fused_vcycle);
+  val(o.outer_product);
+  val(o.stop_rule);
+  val(o.tau);
+  val(o.overlap_launches);
+  val(o.loss);
+  val(o.loss_scale);
+  val(o.precond_lambda_min);
+  val(o.schur_staging);
+  return h;
+}
+
 // Builds [head, check] -> while(cond) { tail, head, check } as one executable graph that
 // works on the problem's own vectors (x = P->x).
 static void build_pcg_graph(ba_problem* P) {
@@ -790,7 +866,7 @@ static void build_pcg_graph(ba_problem* P) {
     P->pcg_graph_body = P->launches - body0;
     P->stream = user;
     P->launches = launches0;
-    P->pcg_graph_epoch = P->graph_epoch;
+    P->pcg_graph_key = pcg_graph_key(P);
   } catch (...) {
     cudaStreamCaptureStatus st;
     if (cudaStreamIsCapturing(P->cap_stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
@@ -859,7 +935,7 @@ void pcg(ba_problem* P, const double* rhs, double* dc, bool check_setup) {
   BA_CUDA(cudaMemsetAsync(scal + S_ITER, 0, 3 * sizeof(double), P->stream));
   // graph-driven loop: no host round trip per iteration
   if (!P->ktime && P->graphs_ok) {
-    if (P->pcg_graph_epoch != P->graph_epoch || !P->pcg_exec) build_pcg_graph(P);
+    if (!P->pcg_exec || P->pcg_graph_key != pcg_graph_key(P)) build_pcg_graph(P);
     if (P->pcg_exec) {
       double* x = P->x.as<double>();
       BA_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, P->stream));

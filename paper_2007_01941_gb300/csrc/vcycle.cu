@@ -66,6 +66,13 @@ constexpr int kPhaseWarps = kPhaseBS / 32;
 // its predecessor: with programmatic dependent launch those loads overlap the previous
 // kernel, and only the vector reads stay on the cycle's critical path.
 
+// Chebyshev coefficients (c1, c2) of step k >= 1, d_k = c1 d_{k-1} + c2 D^-1 r_k, from the
+// level's table (formed on the device at each setup, so that a captured cycle stays valid)
+__device__ __forceinline__ void cheb_step(const double* __restrict__ ch, int k, double& c1, double& c2) {
+  c1 = ch[24 + 2 * (k - 1)];
+  c2 = ch[25 + 2 * (k - 1)];
+}
+
 // row u of D_i^-1 (u = lane < BS) for block_apply
 template <typename T, int BS>
 __device__ __forceinline__ void dinv_row(const T* __restrict__ Dinv_i, int lane, T dr[BS]) {
@@ -400,7 +407,7 @@ k_pcg_update_first(VLevel<T> L, double* __restrict__ x, double* __restrict__ r, 
 // Chebyshev step k >= 1 on row blockIdx.x: q = A din; rout = rin - q;
 // dout = c1 din + c2 D^-1 rout; x += dout (out: FP64 copy of the new x, level 0's last step)
 template <typename T, int BS>
-__global__ void __launch_bounds__(RowCta<BS>::kThreads, phase_min_blocks<T, BS, 16>()) k_ph_step(VLevel<T> L, int dc, int rc, int xc, T c1, T c2,
+__global__ void __launch_bounds__(RowCta<BS>::kThreads, phase_min_blocks<T, BS, 16>()) k_ph_step(VLevel<T> L, int dc, int rc, int xc, int k,
                                                                  double* __restrict__ out, const double* __restrict__ rdot,
                                                                  double* __restrict__ dpart) {
   __shared__ T part[RowCta<BS>::kPart];
@@ -412,7 +419,14 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads, phase_min_blocks<T, BS, 
   if constexpr (kVec) row_prefetch16<16, kNW>(L.row_ptr, L.cols, L.vals, i, pf);
   else row_prefetch<T, BS>(L, i, pf);
   T dr[BS];
+  __shared__ T cc[2];   // this step's (c1, c2), read after the product's barriers
   if (t < BS) dinv_row<T, BS>(L.Dinv + (size_t)i * BS * BS, t, dr);
+  if (t == 32) {
+    double c1d, c2d;
+    cheb_step(L.cheb, k, c1d, c2d);
+    cc[0] = (T)c1d;
+    cc[1] = (T)c2d;
+  }
   pdl_trigger();
   pdl_wait();
   const T* din = L.d[dc];
@@ -424,7 +438,7 @@ __global__ void __launch_bounds__(RowCta<BS>::kThreads, phase_min_blocks<T, BS, 
   double dot = 0.0;
   if (t < BS) {
     const T acc = row_dinv<T, BS>(dr, w);
-    const T dn = c1 * din[idx] + c2 * acc;
+    const T dn = cc[0] * din[idx] + cc[1] * acc;
     const T xn = L.x[xc][idx] + dn;
     L.r[1 - rc][idx] = w[t];
     L.d[1 - dc][idx] = dn;
@@ -581,8 +595,7 @@ __device__ __forceinline__ float4 gather_t4(const float* __restrict__ rt, const 
 }
 
 template <int NW>
-__global__ void __launch_bounds__(NW * 32) k_ph_cstep(VLevel<float> F, VLevel<float> C, int dc, int rc, int xc,
-                                                      float c1, float c2) {
+__global__ void __launch_bounds__(NW * 32) k_ph_cstep(VLevel<float> F, VLevel<float> C, int dc, int rc, int xc) {
   __shared__ float part[16 * NW];
   __shared__ float q[16], bsm[16], w[16];
   const int a = blockIdx.x, t = threadIdx.x, wi = t >> 5, lane = t & 31, cq = 4 * (lane & 3);
@@ -617,6 +630,13 @@ __global__ void __launch_bounds__(NW * 32) k_ph_cstep(VLevel<float> F, VLevel<fl
     for (int j = 0; j < kGMem; ++j) om[j] = o0 + j < o1 ? F.agg_mem[o0 + j] : 0;
   }
   const float inv_theta = (float)(1.0 / C.cheb[0]);
+  float c1 = 0.f, c2 = 0.f;
+  if (t < 16) {
+    double c1d, c2d;
+    cheb_step(C.cheb, 1, c1d, c2d);
+    c1 = (float)c1d;
+    c2 = (float)c2d;
+  }
   pdl_trigger();
   pdl_wait();
   // b_a
@@ -1008,18 +1028,6 @@ static VLevel<T> describe(Level& L) {
 
 static int warps_grid(int warps) { return std::max(1, cdiv((long long)warps, kPhaseWarps)); }
 
-// host-side Chebyshev coefficients of step k (the same recurrence as vc_rho)
-static void cheb_coeffs(const Level& L, int k, double& c1, double& c2) {
-  const double* ch = L.cheb_host;
-  double rho = 1.0 / ch[2], rho_prev = 0.0;
-  for (int j = 1; j <= k; ++j) {
-    rho_prev = rho;
-    rho = 1.0 / (2.0 * ch[2] - rho);
-  }
-  c1 = rho * rho_prev;
-  c2 = 2.0 * rho / ch[1];
-}
-
 template <typename T>
 static void run(ba_problem* P, const double* r, double* z, double* dpart, bool first_done) {
   const int nl = P->n_levels;
@@ -1043,25 +1051,20 @@ static void run(ba_problem* P, const double* r, double* z, double* dpart, bool f
     int k1 = 1;
     if constexpr (std::is_same_v<T, float>) {
       if (folded) {
-        double c1, c2;
-        cheb_coeffs(P->levels[l], 1, c1, c2);
         launch_k(P, k_ph_cstep<RowCta<16>::kThreads / 32>, L.n, RowCta<16>::kThreads, 0, V[l - 1], L, bit(dm, l),
-                 bit(rm, l), bit(xm, l), (float)c1, (float)c2);
+                 bit(rm, l), bit(xm, l));
         rm ^= 1u << l;
         dm ^= 1u << l;
         k1 = 2;
       }
     }
     for (int k = k1; k < pre; ++k) {
-      double c1, c2;
-      cheb_coeffs(P->levels[l], k, c1, c2);
       if (L.bs == 9)
-        launch_k(P, k_ph_step<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2,
-                                                             (double*)nullptr, (const double*)nullptr, (double*)nullptr);
+        launch_k(P, k_ph_step<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), k,
+                 (double*)nullptr, (const double*)nullptr, (double*)nullptr);
       else
-        launch_k(P, k_ph_step<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1,
-                                                               (T)c2, (double*)nullptr, (const double*)nullptr,
-                                                               (double*)nullptr);
+        launch_k(P, k_ph_step<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), k,
+                 (double*)nullptr, (const double*)nullptr, (double*)nullptr);
       rm ^= 1u << l;
       dm ^= 1u << l;
     }
@@ -1094,16 +1097,14 @@ static void run(ba_problem* P, const double* r, double* z, double* dpart, bool f
                bit(rm, l), bit(dm, l), o, r, op);
     xm ^= 1u << l;
     for (int k = 1; k < post; ++k) {
-      double c1, c2;
-      cheb_coeffs(P->levels[l], k, c1, c2);
       double* ok = (l == 0 && k == post - 1) ? z : nullptr;
       double* okp = ok ? dpart : nullptr;
       if (L.bs == 9)
-        launch_k(P, k_ph_step<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1, (T)c2,
-                                                             ok, r, okp);
+        launch_k(P, k_ph_step<T, 9>, L.n, RowCta<9>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), k, ok, r,
+                 okp);
       else
-        launch_k(P, k_ph_step<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), (T)c1,
-                                                               (T)c2, ok, r, okp);
+        launch_k(P, k_ph_step<T, 16>, L.n, RowCta<16>::kThreads, 0, L, bit(dm, l), bit(rm, l), bit(xm, l), k, ok, r,
+                 okp);
       rm ^= 1u << l;
       dm ^= 1u << l;
     }
