@@ -1019,11 +1019,18 @@ k_model_terms(int n_c9, const double* __restrict__ dc, const double* __restrict_
 void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double* lam, int* accepted,
              double* cost_out) {
   linearize(P, cams, pts, obs);
-  // one synchronisation per stage boundary that needs the host: the linearisation's flags
-  // with its cost; the setups' flags with the PCG's b.b; the PCG's result with its flags;
-  // the trial cost with the model decrease
-  const double cost0 = fetch_sum_checked(P, S_COST);
-  P->cost = cost0;
+  // one synchronisation per stage boundary that needs the host: the flags of the
+  // linearisation and the setups with the PCG's b.b; the PCG's result with its flags; the
+  // trial cost with the model decrease and (unpartitioned) the cost at x.  A partitioned
+  // problem sums the cost over its ranks here, in the same order on every rank.
+  const bool part = partitioned(P);
+  double cost0 = part ? fetch_sum_checked(P, S_COST) : 0.0;
+  auto fetch_cost0 = [&] {
+    if (!part) {
+      fetch_scalars(P, S_COST, 1);
+      cost0 = P->h_scal[S_COST];
+    }
+  };
   const size_t nc = (size_t)P->n_c * 9, np = (size_t)P->n_p * 3;
   P->delta_c.ensure(sizeof(double) * nc + 64);
   // A linear solve that fails (a block found not positive definite by its pivots, or a
@@ -1045,6 +1052,8 @@ void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double
     solved = false;
   }
   if (!solved) {
+    fetch_cost0();
+    P->cost = cost0;
     *lam = *lam * P->lm_nu;
     P->lm_nu *= 2.0;
     *accepted = 0;
@@ -1085,11 +1094,13 @@ void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double
   } else {
     cost_at_async(P, cams1, pts1, obs);
     model_terms((int)nc, P->n_p);
-    static_assert(S_COST_NEW == S_MODEL + 1, "scalar slots");
-    fetch_scalars(P, S_MODEL, 2);
+    static_assert(S_COST == 0 && S_COST_NEW == S_MODEL + 1, "scalar slots");
+    fetch_scalars(P, S_COST, S_COST_NEW + 1);
+    cost0 = P->h_scal[S_COST];
     model_sum = P->h_scal[S_MODEL];
     cost1 = P->h_scal[S_COST_NEW];
   }
+  P->cost = cost0;
   const double model = 0.5 * model_sum;
   const double rho = model > 0.0 ? (cost0 - cost1) / model : -INFINITY;
   if (rho > 1e-3 && std::isfinite(cost1)) {
