@@ -81,9 +81,12 @@ __device__ __forceinline__ void pcg_update_finish(double acc, bool ok, double al
       *ck.counter = 0u;
       const double it = scal[S_ITER] + 1.0;
       scal[S_ITER] = it;
+      // a setup whose check was deferred (the LM step) may have failed: stop at once
+      const bool setup_failed = __ldcg(ck.flags + F_NOT_SPD_POINT) != 0 || __ldcg(ck.flags + F_NOT_SPD_JACOBI) != 0 ||
+                                __ldcg(ck.flags + F_NOT_SPD_COARSE) != 0 || __ldcg(ck.flags + F_NONFINITE) != 0;
       const bool stop =
           pcg_converged(ck.rule, it, t, scal[S_BB], ck.rtol2, __ldcg(scal + S_Q), __ldcg(scal + S_DQ), ck.tau) ||
-          __ldcg(ck.flags + F_BREAKDOWN) != 0 || it >= (double)ck.max_iters;
+          __ldcg(ck.flags + F_BREAKDOWN) != 0 || setup_failed || it >= (double)ck.max_iters;
       if (ck.use_cond) cudaGraphSetConditional(ck.h, stop ? 0u : 1u);
     }
   }

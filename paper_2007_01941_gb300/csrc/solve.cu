@@ -883,20 +883,78 @@ static void build_pcg_graph(ba_problem* P) {
   }
 }
 
-void pcg(ba_problem* P, const double* rhs, double* dc, bool check_setup) {
+// PCG pieces shared by the synchronous solve and the LM step's enqueue-only path.
+// pcg_begin: buffers, delta_c = 0, r = rhs, b.b into S_BB (not fetched)
+static void pcg_begin(ba_problem* P, const double* rhs, double* dc) {
   const size_t n = (size_t)P->n_c * 9;
-  const int g = cdiv((long long)n, 256);
   P->r.ensure(sizeof(double) * n + 64);
   P->z.ensure(sizeof(double) * n + 64);
   P->p.ensure(sizeof(double) * n + 64);
   P->q.ensure(sizeof(double) * n + 64);
   P->x.ensure(sizeof(double) * n + 64);
+  BA_CUDA(cudaMemsetAsync(dc, 0, sizeof(double) * n, P->stream));
+  BA_CUDA(cudaMemcpyAsync(P->r.as<double>(), rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream));
+  dot64(P, P->r.as<double>(), P->r.as<double>(), n, S_BB);
+}
+
+// the first preconditioning and direction p = z, and the loop's scalars S_ITER, S_Q, S_DQ
+// set to 0
+static void pcg_first_direction(ba_problem* P) {
+  const size_t n = (size_t)P->n_c * 9;
+  double* scal = P->scal.as<double>();
+  if (P->outer_explicit) {
+    // per-row-group partial sums of the fused p.q and the rows' shares of r.z, sized
+    // before any graph capture
+    P->partial2.ensure(sizeof(double) * ((size_t)cdiv(P->n_c, kSpmvBS / 32) + 64));
+    P->rzpart.ensure(sizeof(double) * ((size_t)P->n_c + 64));
+    assembled_precond_direction(P, 1);
+  } else {
+    precond_apply(P, P->r.as<double>(), P->z.as<double>());
+    dot64(P, P->r.as<double>(), P->z.as<double>(), n, S_RZ);
+    launch_k(P, k_pcg_direction, cdiv((long long)n, 256), 256, 0, n, P->p.as<double>(), P->z.as<double>(), scal,
+             -1, 0, P->Dc.as<double>(), P->q.as<double>(), split_target(P));  // p = z
+  }
+  static_assert(S_Q == S_ITER + 1 && S_DQ == S_ITER + 2, "scalar slots");
+  BA_CUDA(cudaMemsetAsync(scal + S_ITER, 0, 3 * sizeof(double), P->stream));
+}
+
+// the graph path: captured (again) when its signature changed; false when graphs are not
+// used (kernel timing) or the capture failed
+static bool pcg_graph_ready(ba_problem* P) {
+  if (P->ktime || !P->graphs_ok) return false;
+  if (!P->pcg_exec || P->pcg_graph_key != pcg_graph_key(P)) build_pcg_graph(P);
+  return P->pcg_exec != nullptr;
+}
+
+// the whole loop as one graph launch, then delta_c = x
+static void pcg_graph_launch(ba_problem* P, double* dc) {
+  const size_t n = (size_t)P->n_c * 9;
+  double* x = P->x.as<double>();
+  BA_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, P->stream));
+  BA_CUDA(cudaGraphLaunch(P->pcg_exec, P->stream));
+  BA_CUDA(cudaMemcpyAsync(dc, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream));
+}
+
+// iterations and relative residual of a graph solve from the fetched scalars (bb > 0);
+// whether it converged
+static bool pcg_graph_result(ba_problem* P, double bb) {
+  const int it = (int)P->h_scal[S_ITER];
+  P->launches += P->pcg_graph_head + (long long)std::max(it - 1, 0) * P->pcg_graph_body;
+  const double rel = std::sqrt(P->h_scal[S_RR] / bb);
+  P->pcg_iters = it;
+  P->pcg_rel = rel;
+  BA_REQUIRE(std::isfinite(rel), BA_ERR_BREAKDOWN, "non-finite PCG residual");
+  return pcg_converged(P->opt.stop_rule, (double)it, P->h_scal[S_RR], bb, P->opt.rtol * P->opt.rtol,
+                       P->h_scal[S_Q], P->h_scal[S_DQ], P->opt.tau);
+}
+
+void pcg(ba_problem* P, const double* rhs, double* dc, bool check_setup) {
+  const size_t n = (size_t)P->n_c * 9;
+  const int g = cdiv((long long)n, 256);
+  if (!check_setup) clear_flags(P);
+  pcg_begin(P, rhs, dc);
   double *r = P->r.as<double>(), *z = P->z.as<double>(), *p = P->p.as<double>(), *q = P->q.as<double>();
   double* scal = P->scal.as<double>();
-  if (!check_setup) clear_flags(P);
-  BA_CUDA(cudaMemsetAsync(dc, 0, sizeof(double) * n, P->stream));
-  BA_CUDA(cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream));
-  dot64(P, r, r, n, S_BB);
   if (check_setup) {
     // the setup's flags come back with b.b (one synchronisation), then start clean
     fetch_checked(P, S_BB, 1);
@@ -913,47 +971,20 @@ void pcg(ba_problem* P, const double* rhs, double* dc, bool check_setup) {
   }
   const bool assembled = P->outer_explicit;
   int s_rz = S_RZ, s_new = S_TMP2;
-  if (assembled) {
-    // per-row-group partial sums of the fused p.q and the rows' shares of r.z, sized
-    // before any graph capture
-    P->partial2.ensure(sizeof(double) * ((size_t)cdiv(P->n_c, kSpmvBS / 32) + 64));
-    P->rzpart.ensure(sizeof(double) * ((size_t)P->n_c + 64));
-    assembled_precond_direction(P, 1);
-  } else {
-    precond_apply(P, r, z);
-    dot64(P, r, z, n, s_rz);
-    launch_k(P, k_pcg_direction, g, 256, 0, n, p, z, scal, -1, 0, P->Dc.as<double>(), q,
-                                              split_target(P));  // p = z
-  }
+  pcg_first_direction(P);
   const int rg = reduce_blocks(P, n);
   const double rtol2 = P->opt.rtol * P->opt.rtol;
   double rel = 1.0;
   int it = 0;
   bool done = false;
-  // S_ITER, S_Q, S_DQ start at 0
-  static_assert(S_Q == S_ITER + 1 && S_DQ == S_ITER + 2, "scalar slots");
-  BA_CUDA(cudaMemsetAsync(scal + S_ITER, 0, 3 * sizeof(double), P->stream));
   // graph-driven loop: no host round trip per iteration
-  if (!P->ktime && P->graphs_ok) {
-    if (!P->pcg_exec || P->pcg_graph_key != pcg_graph_key(P)) build_pcg_graph(P);
-    if (P->pcg_exec) {
-      double* x = P->x.as<double>();
-      BA_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, P->stream));
-      BA_CUDA(cudaGraphLaunch(P->pcg_exec, P->stream));
-      BA_CUDA(cudaMemcpyAsync(dc, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, P->stream));
-      fetch_checked(P, S_RR, S_DQ - S_RR + 1);
-      it = (int)P->h_scal[S_ITER];
-      P->launches += P->pcg_graph_head + (long long)std::max(it - 1, 0) * P->pcg_graph_body;
-      rel = std::sqrt(P->h_scal[S_RR] / bb);
-      BA_REQUIRE(std::isfinite(rel), BA_ERR_BREAKDOWN, "non-finite PCG residual");
-      done = pcg_converged(P->opt.stop_rule, (double)it, P->h_scal[S_RR], bb, rtol2, P->h_scal[S_Q],
-                           P->h_scal[S_DQ], P->opt.tau);
-      P->pcg_iters = it;
-      P->pcg_rel = rel;
-      if (!done)
-        throw Error(BA_ERR_NOT_CONVERGED, "PCG reached max_iters with relative residual " + std::to_string(rel));
-      return;
-    }
+  if (pcg_graph_ready(P)) {
+    pcg_graph_launch(P, dc);
+    fetch_checked(P, S_RR, S_DQ - S_RR + 1);
+    if (!pcg_graph_result(P, bb))
+      throw Error(BA_ERR_NOT_CONVERGED,
+                  "PCG reached max_iters with relative residual " + std::to_string(P->pcg_rel));
+    return;
   }
   while (it < P->opt.max_iters) {
     if (assembled) {
@@ -1019,47 +1050,65 @@ k_model_terms(int n_c9, const double* __restrict__ dc, const double* __restrict_
 void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double* lam, int* accepted,
              double* cost_out) {
   linearize(P, cams, pts, obs);
-  // one synchronisation per stage boundary that needs the host: the flags of the
-  // linearisation and the setups with the PCG's b.b; the PCG's result with its flags; the
-  // trial cost with the model decrease and (unpartitioned) the cost at x.  A partitioned
-  // problem sums the cost over its ranks here, in the same order on every rank.
+  // An unpartitioned step with the PCG graph is enqueued whole (linearisation, setups, the
+  // PCG graph, back-substitution, trial cost and model decrease) and synchronises once for
+  // its decision: the scalars and flags of every stage come back together, the deferred
+  // setup checks are raised then (the PCG loop itself stops at once when a setup flag is
+  // set), and a zero right-hand side gives delta_c = 0.  Otherwise the stages synchronise
+  // where the host needs them: the flags of the linearisation and the setups with the
+  // PCG's b.b, the PCG's result with its flags, the trial cost with the model decrease.  A
+  // partitioned problem sums the cost over its ranks here, in the same order on every rank.
   const bool part = partitioned(P);
   double cost0 = part ? fetch_sum_checked(P, S_COST) : 0.0;
-  auto fetch_cost0 = [&] {
-    if (!part) {
-      fetch_scalars(P, S_COST, 1);
-      cost0 = P->h_scal[S_COST];
-    }
-  };
   const size_t nc = (size_t)P->n_c * 9, np = (size_t)P->n_p * 3;
   P->delta_c.ensure(sizeof(double) * nc + 64);
+  double* dc = P->delta_c.as<double>();
   // A linear solve that fails (a block found not positive definite by its pivots, or a
   // PCG breakdown; near the optimum lambda becomes small enough for S to be numerically
   // singular along the gauge and the focal-length / depth directions) makes the step
   // unsuccessful, as in the Ceres trust-region loop the paper uses: x is kept and lambda
   // grows as after a rejection.
-  bool solved = true;
+  bool solved = true, enqueued = false;
   try {
     schur_setup(P, *lam, false);
     if (P->opt.preconditioner == BA_PRECOND_MG) mg_setup(P, false);
-    try {
-      pcg(P, P->rhs.as<double>(), P->delta_c.as<double>(), true);
-    } catch (const Error& e) {
-      if (e.status != BA_ERR_NOT_CONVERGED) throw;  // an inexact step is still a step
+    if (!part) {
+      pcg_begin(P, P->rhs.as<double>(), dc);
+      pcg_first_direction(P);
+      enqueued = pcg_graph_ready(P);
+      if (enqueued) {
+        pcg_graph_launch(P, dc);
+        // the flags as the solve left them (the trial cost below may flag a non-finite
+        // residual, which only rejects the step), into pinned memory in stream order
+        BA_CUDA(cudaMemcpyAsync(P->h_flags, P->flags.p, sizeof(int) * F_COUNT, cudaMemcpyDeviceToHost, P->stream));
+      }
+    }
+    if (!enqueued) {
+      try {
+        pcg(P, P->rhs.as<double>(), dc, true);
+      } catch (const Error& e) {
+        if (e.status != BA_ERR_NOT_CONVERGED) throw;  // an inexact step is still a step
+      }
     }
   } catch (const Error& e) {
     if (e.status != BA_ERR_NOT_SPD && e.status != BA_ERR_BREAKDOWN) throw;
     solved = false;
   }
-  if (!solved) {
-    fetch_cost0();
+  auto reject = [&](bool failed_solve) {
     P->cost = cost0;
     *lam = *lam * P->lm_nu;
     P->lm_nu *= 2.0;
     *accepted = 0;
     *cost_out = cost0;
-    P->stage = 1;   // linearised; the setup must run again before a solve
+    if (failed_solve) P->stage = 1;   // linearised; the setup must run again before a solve
     sync(P);
+  };
+  if (!solved) {
+    if (!part) {
+      fetch_scalars(P, S_COST, 1);
+      cost0 = P->h_scal[S_COST];
+    }
+    reject(true);
     return;
   }
   P->scratch.ensure(sizeof(double) * (nc + 2 * np) + 64);
@@ -1067,8 +1116,8 @@ void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double
   double* dp_user = cams1 + nc;
   double* pts1 = dp_user + np;
   P->delta_p.ensure(sizeof(double) * 3 * P->ldp);
-  back_substitute_to(P, P->delta_c.as<double>(), P->delta_p.as<double>(), dp_user);
-  k_add<<<cdiv((long long)nc, 256), 256, 0, P->stream>>>(nc, cams, P->delta_c.as<double>(), cams1);
+  back_substitute_to(P, dc, P->delta_p.as<double>(), dp_user);
+  k_add<<<cdiv((long long)nc, 256), 256, 0, P->stream>>>(nc, cams, dc, cams1);
   launched(P);
   if (np) {
     k_add<<<cdiv((long long)np, 256), 256, 0, P->stream>>>(np, pts, dp_user, pts1);
@@ -1078,13 +1127,13 @@ void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double
   // rank's share (summed over the ranks), the camera terms are the same on every rank
   auto model_terms = [&](int n_c9, int n_pts) {
     k_model_terms<<<reduce_blocks(P, (size_t)n_c9 + 3 * (size_t)n_pts), kVecBS, 0, P->stream>>>(
-        n_c9, P->delta_c.as<double>(), P->gc.as<double>(), P->Dc.as<double>(), n_pts, P->ldp,
-        P->delta_p.as<double>(), P->gp.as<double>(), P->Dp.as<double>(), P->partial.as<double>(),
-        P->counter.as<unsigned>(), P->scal.as<double>() + S_MODEL);
+        n_c9, dc, P->gc.as<double>(), P->Dc.as<double>(), n_pts, P->ldp, P->delta_p.as<double>(),
+        P->gp.as<double>(), P->Dp.as<double>(), P->partial.as<double>(), P->counter.as<unsigned>(),
+        P->scal.as<double>() + S_MODEL);
     launched(P);
   };
   double model_sum, cost1;
-  if (partitioned(P)) {
+  if (part) {
     cost1 = cost_at(P, cams1, pts1, obs);
     model_terms(0, P->n_p);
     model_sum = fetch_sum(P, S_MODEL);
@@ -1094,11 +1143,37 @@ void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double
   } else {
     cost_at_async(P, cams1, pts1, obs);
     model_terms((int)nc, P->n_p);
-    static_assert(S_COST == 0 && S_COST_NEW == S_MODEL + 1, "scalar slots");
-    fetch_scalars(P, S_COST, S_COST_NEW + 1);
+    static_assert(S_COST == 0 && S_COST_NEW == S_MODEL + 1 && S_DQ > S_COST_NEW && S_BB < S_MODEL,
+                  "scalar slots");
+    if (enqueued) {
+      // the step's one synchronisation: every scalar up to the PCG's (the flags were copied
+      // after the solve)
+      fetch_scalars(P, S_COST, S_DQ + 1);
+      const double bb = P->h_scal[S_BB];
+      BA_REQUIRE(bb >= 0.0 && std::isfinite(bb), BA_ERR_INVALID_ARG, "non-finite right-hand side");
+      if (bb == 0.0) P->h_flags[F_BREAKDOWN] = 0;   // r = 0: delta_c = 0, no iteration
+      try {
+        raise_flags(P);
+        if (bb > 0.0) {
+          pcg_graph_result(P, bb);   // not converged: an inexact step is still a step
+        } else {
+          P->pcg_iters = 0;
+          P->pcg_rel = 0.0;
+        }
+      } catch (const Error& e) {
+        if (e.status != BA_ERR_NOT_SPD && e.status != BA_ERR_BREAKDOWN) throw;
+        solved = false;
+      }
+    } else {
+      fetch_scalars(P, S_COST, S_COST_NEW + 1);
+    }
     cost0 = P->h_scal[S_COST];
     model_sum = P->h_scal[S_MODEL];
     cost1 = P->h_scal[S_COST_NEW];
+    if (!solved) {
+      reject(true);
+      return;
+    }
   }
   P->cost = cost0;
   const double model = 0.5 * model_sum;
@@ -1111,13 +1186,10 @@ void lm_step(ba_problem* P, double* cams, double* pts, const double* obs, double
     P->lm_nu = 2.0;
     *accepted = 1;
     *cost_out = cost1;
+    sync(P);
   } else {
-    *lam = *lam * P->lm_nu;
-    P->lm_nu *= 2.0;
-    *accepted = 0;
-    *cost_out = cost0;
+    reject(false);
   }
-  sync(P);
 }
 
 }  // namespace ba
