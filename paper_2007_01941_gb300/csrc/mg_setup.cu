@@ -1099,53 +1099,6 @@ __global__ void k_sqrt_slot(double* scal, int src, int dst) {
   if (threadIdx.x == 0) scal[dst] = sqrt(scal[src]);
 }
 
-// largest eigenvalue of the symmetric tridiagonal (alpha[0..m), beta[0..m-1)) by
-// bisection with Sturm counts; writes Chebyshev parameters
-__global__ void k_tridiag_lambda_max(const double* __restrict__ scal, int s_alpha, int s_beta, int m,
-                                     double lo_f, double hi_f, double* __restrict__ cheb) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double al[16], be[16];
-  int mm = m;
-  for (int j = 0; j < m; ++j) al[j] = scal[s_alpha + j];
-  for (int j = 0; j + 1 < m; ++j) {
-    be[j] = scal[s_beta + j];
-    if (!(be[j] > 0.0)) {  // invariant subspace found: truncate
-      mm = j + 1;
-      break;
-    }
-  }
-  double lo = al[0], hi = al[0];
-  for (int j = 0; j < mm; ++j) {
-    const double rad = (j > 0 ? fabs(be[j - 1]) : 0.0) + (j + 1 < mm ? fabs(be[j]) : 0.0);
-    lo = fmin(lo, al[j] - rad);
-    hi = fmax(hi, al[j] + rad);
-  }
-  // count of eigenvalues < x
-  auto count_below = [&](double x) {
-    int c = 0;
-    double d = al[0] - x;
-    if (d < 0) ++c;
-    for (int j = 1; j < mm; ++j) {
-      const double prev = (d == 0.0) ? 1e-300 : d;
-      d = (al[j] - x) - be[j - 1] * be[j - 1] / prev;
-      if (d < 0) ++c;
-    }
-    return c;
-  };
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi || hi - lo <= 1e-14 * fmax(fabs(lo), fabs(hi))) break;
-    if (count_below(mid) >= mm) hi = mid;
-    else lo = mid;
-  }
-  const double lam = hi;
-  const double a = lo_f * lam, b = hi_f * lam;
-  cheb[0] = 0.5 * (b + a);          // theta
-  cheb[1] = 0.5 * (b - a);          // delta
-  cheb[2] = cheb[0] / cheb[1];      // sigma_1
-  cheb[3] = lam;
-}
-
 template <typename T>
 static void lanczos(ba_problem* P, int l) {
   Level& L = P->levels[l];
@@ -1210,33 +1163,44 @@ __global__ void __launch_bounds__(512) k_cheb_params(ChebLevels CL, int m, doubl
   const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k >= CL.n) return;
   double* c = CL.cheb[k];
-  double al[8], be[8];
+  double al[8], be2[8];
   int mm = m;
   for (int j = 0; j < m; ++j) al[j] = c[8 + j];
   for (int j = 0; j + 1 < m; ++j) {
-    be[j] = c[16 + j];
-    if (!(be[j] > 0.0)) {  // invariant subspace found: truncate
+    const double b = c[16 + j];
+    be2[j] = b;
+    if (!(b > 0.0)) {  // invariant subspace found: truncate
       mm = j + 1;
       break;
     }
   }
-  // Gershgorin interval
+  // Gershgorin interval, and the matrix scaled by its bound s so that the characteristic
+  // polynomials below stay within range
   double lo = al[0], hi = al[0];
   for (int j = 0; j < mm; ++j) {
-    const double rad = (j > 0 ? fabs(be[j - 1]) : 0.0) + (j + 1 < mm ? fabs(be[j]) : 0.0);
+    const double rad = (j > 0 ? fabs(be2[j - 1]) : 0.0) + (j + 1 < mm ? fabs(be2[j]) : 0.0);
     lo = fmin(lo, al[j] - rad);
     hi = fmax(hi, al[j] + rad);
   }
+  const double s = fmax(fabs(lo), fabs(hi)) > 0.0 ? fmax(fabs(lo), fabs(hi)) : 1.0;
+  for (int j = 0; j < mm; ++j) al[j] /= s;
+  for (int j = 0; j + 1 < mm; ++j) be2[j] = (be2[j] / s) * (be2[j] / s);
+  lo /= s;
+  hi /= s;
   for (int round = 0; round < 64; ++round) {
-    // lane j tests lo + (j + 1) (hi - lo) / 33: are all mm eigenvalues below it?
+    if (hi - lo <= 4.0 * 2.220446049250313e-16 * fabs(hi)) break;
+    // lane j tests x = lo + (j + 1) (hi - lo) / 33: the eigenvalues below x are the sign
+    // changes of p_0 = 1, p_1 = a_0 - x, p_j = (a_{j-1} - x) p_{j-1} - b_{j-2}^2 p_{j-2}
+    // (a zero p_j takes the sign opposite to p_{j-1})
     const double x = lo + (double)(lane + 1) * ((hi - lo) / 33.0);
     int below = 0;
-    double d = al[0] - x;
-    if (d < 0) ++below;
+    double pm2 = 1.0, pm1 = al[0] - x;
+    if (!(pm1 > 0.0)) ++below;
     for (int j = 1; j < mm; ++j) {
-      const double prev = (d == 0.0) ? 1e-300 : d;
-      d = (al[j] - x) - be[j - 1] * be[j - 1] / prev;
-      if (d < 0) ++below;
+      const double pj = (al[j] - x) * pm1 - be2[j - 1] * pm2;
+      if (pm1 == 0.0 ? true : (pm1 > 0.0 ? !(pj > 0.0) : (pj > 0.0))) ++below;
+      pm2 = pm1;
+      pm1 = pj == 0.0 ? -copysign(1e-300, pm2) : pj;
     }
     const bool all_below = below >= mm && x > lo && x < hi;
     const unsigned ball = __ballot_sync(0xffffffffu, all_below);
@@ -1253,6 +1217,7 @@ __global__ void __launch_bounds__(512) k_cheb_params(ChebLevels CL, int m, doubl
     lo = fmax(lo, nlo);
     hi = fmin(hi, nhi);
   }
+  hi *= s;
   if (lane != 0) return;
   const double lam = hi;
   const double a = lo_f * lam, b = hi_f * lam;
