@@ -245,17 +245,22 @@ def test_hierarchy_matches_oracle(gpu, prec):
         assert abs(lam_gpu - L.lam_max) <= (1e-9 if prec == "fp64" else 1e-3) * L.lam_max, l
 
 
-@pytest.mark.parametrize("level0", ["implicit", "explicit"])
-def test_vcycle_matches_oracle(gpu, level0):
+# coarse_max_nodes 40: a 36-node coarsest level (576 dofs), above the size whose restriction
+# is folded into the coarsest solve, so the restriction kernel and the plain coarsest solve run
+@pytest.mark.parametrize("level0,cmax", [("implicit", 16), ("explicit", 16), ("explicit", 40)])
+def test_vcycle_matches_oracle(gpu, level0, cmax):
     api, F_ = _api()
     s = scene("street_chain", **CHAIN)
     op = {"implicit": F_.BA_OP_IMPLICIT, "explicit": F_.BA_OP_EXPLICIT}[level0]
-    prob, cams, pts, obs = _prob(s, gpu, coarse_max_nodes=16, level0_operator=op)
+    prob, cams, pts, obs = _prob(s, gpu, coarse_max_nodes=cmax, level0_operator=op)
     prob.linearize(cams, pts, obs)
     prob.schur_setup(s.lam)
     prob.mg_setup()
-    assert prob.info()["level0_explicit"] == (level0 == "explicit")
-    sch, H = _oracle_hierarchy(s, 16)
+    info = prob.info()
+    assert info["level0_explicit"] == (level0 == "explicit")
+    if cmax == 40:
+        assert info["level_nodes"][info["n_levels"] - 1] * 16 > 512
+    sch, H = _oracle_hierarchy(s, cmax)
     for seed in range(2):
         r = np.random.default_rng(seed).normal(size=9 * s.n_cams)
         z = _np(prob.precond_apply(torch.tensor(r, device=gpu)))
