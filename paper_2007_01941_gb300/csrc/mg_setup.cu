@@ -1150,8 +1150,8 @@ static void lanczos(ba_problem* P, int l) {
 // Largest eigenvalue of each level's Lanczos tridiagonal (alpha_0..m-1 in slots 8..,
 // beta_0..m-2 in slots 16..) by multisection with Sturm counts, and from it the Chebyshev
 // parameters {theta, delta, sigma_1, lambda_max} of the interval [lo_f, hi_f] lambda_max
-// (Section 3.4) in slots 0..3 and the step coefficients in slots 24...  One warp per level,
-// on the device, so that the V-cycle's kernels read them there and the setup needs no host
+// (Section 3.4) in slots 0..3 and the step coefficients in slots 24...  One warp per level
+// (each in its own CTA), on the device, so that the V-cycle's kernels read them there and the setup needs no host
 // round trip: each round the 32 lanes count the eigenvalues below 32 points of the current
 // interval and keep the sub-interval where the count reaches m, a factor 33 per round.
 struct ChebLevels {
@@ -1159,8 +1159,9 @@ struct ChebLevels {
   int n;
 };
 
-__global__ void __launch_bounds__(512) k_cheb_params(ChebLevels CL, int m, double lo_f, double hi_f) {
-  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(32) k_cheb_params(ChebLevels CL, int m, double lo_f, double hi_f) {
+  // one CTA (one warp) per level, so that the levels' FP64 recurrences run on different SMs
+  const int k = blockIdx.x, lane = threadIdx.x;
   if (k >= CL.n) return;
   double* c = CL.cheb[k];
   double al[8], be2[8];
@@ -1244,7 +1245,7 @@ static void finish_lanczos(ba_problem* P) {
   CL.n = nl;
   for (int k = 0; k < nl; ++k) CL.cheb[k] = P->levels[k].cheb.as<double>();
   const int m = std::min(std::max(P->opt.lanczos_steps, 1), 8);
-  k_cheb_params<<<1, 32 * nl, 0, P->stream>>>(CL, m, P->opt.cheb_lo, P->opt.cheb_hi);
+  k_cheb_params<<<nl, 32, 0, P->stream>>>(CL, m, P->opt.cheb_lo, P->opt.cheb_hi);
   launched(P);
 }
 
