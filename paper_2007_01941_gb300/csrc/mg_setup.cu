@@ -1031,7 +1031,7 @@ static void galerkin_symbolic(ba_problem* P, Level& L, Level& L1) {
 // diagonal blocks of a BSR level as double
 template <typename T>
 __global__ void k_extract_diag(int n, int bs, const int* __restrict__ row_ptr, const int* __restrict__ cols,
-                               const T* __restrict__ vals, double* __restrict__ D) {
+                               const T* __restrict__ vals, double* __restrict__ D, float* __restrict__ D32) {
   int i = blockIdx.x;
   int t = threadIdx.x;
   if (t >= bs * bs) return;
@@ -1039,6 +1039,18 @@ __global__ void k_extract_diag(int n, int bs, const int* __restrict__ row_ptr, c
   for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
     if (cols[e] == i) v = (double)vals[(size_t)e * bs * bs + t];
   D[(size_t)i * bs * bs + t] = v;
+  if (D32) D32[(size_t)i * bs * bs + t] = (float)v;   // the FP32 copy the batched Lanczos reads
+}
+
+// level 0's Jacobi data from the Schur setup's: S_cc blocks and their FP64 and FP32 inverses
+__global__ void k_copy_jacobi0(size_t n, const double* __restrict__ s, const double* __restrict__ si,
+                               const float* __restrict__ si32, double* __restrict__ d, double* __restrict__ di,
+                               float* __restrict__ di32) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    d[i] = s[i];
+    di[i] = si[i];
+    di32[i] = si32[i];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1486,14 +1498,6 @@ __global__ void __launch_bounds__(kGJBS) k_gauss_jordan_df(float2* Aa, float2* A
   }
 }
 
-__global__ void k_d2df_vec(size_t n, const double* __restrict__ a, float2* __restrict__ b) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    const DF v(a[i]);
-    b[i] = make_float2(v.h, v.l);
-  }
-}
-
 __global__ void k_df2d_vec(size_t n, const float2* __restrict__ a, double* __restrict__ b) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = to_double(DF(a[i].x, a[i].y));
@@ -1504,6 +1508,24 @@ __global__ void k_d2f_vec(size_t n, const double* __restrict__ a, float* __restr
   if (i < n) b[i] = (float)a[i];
 }
 
+// the coarsest operator's FP32 blocks as a dense float-pair matrix (value, 0), padded with
+// the identity up to Np (Da zeroed beforehand)
+__global__ void k_bsr_to_dense_df(int n, int bs, const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                                  const float* __restrict__ vals, int N, int Np, float2* __restrict__ Da) {
+  const int i = blockIdx.x;
+  if (i < n) {
+    for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int j = cols[e];
+      for (int t = threadIdx.x; t < bs * bs; t += blockDim.x) {
+        const int u = t / bs, v = t - u * bs;
+        Da[(size_t)(i * bs + u) * Np + j * bs + v] = make_float2(vals[(size_t)e * bs * bs + t], 0.f);
+      }
+    }
+  } else {
+    for (int k = N + (int)threadIdx.x; k < Np; k += blockDim.x) Da[(size_t)k * Np + k] = make_float2(1.f, 0.f);
+  }
+}
+
 static void dense_inverse(ba_problem* P, Level& L) {
   const int N = L.n * L.bs;
   const int Np = (N + kGJ - 1) / kGJ * kGJ;
@@ -1511,25 +1533,18 @@ static void dense_inverse(ba_problem* P, Level& L) {
   L.N = Np;
   L.Ainv.ensure(sizeof(double) * (size_t)Np * Np);
   double* A = L.Ainv.as<double>();
-  BA_CUDA(cudaMemsetAsync(A, 0, sizeof(double) * (size_t)Np * Np, P->stream));
-  if (level_fp32(P) && !L.vals32.p) throw Error(BA_ERR_STATE, "missing coarse operator");
-  if (level_fp32(P))
-    k_bsr_to_dense<float><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
-                                                      L.vals32.as<float>(), Np, A);
-  else
-    k_bsr_to_dense<double><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
-                                                       L.vals64.as<double>(), Np, A);
-  launched(P);
-  k_dense_identity_pad<<<cdiv((long long)Np * Np, 256), 256, 0, P->stream>>>(N, Np, A);
-  launched(P);
   if (level_fp32(P)) {
-    // paired FP32: both buffers of the ping-pong and the pivot inverses as float pairs
+    if (!L.vals32.p) throw Error(BA_ERR_STATE, "missing coarse operator");
+    // paired FP32: both buffers of the ping-pong and the pivot inverses as float pairs; the
+    // matrix goes straight from the blocks into the first buffer
     const size_t nn = (size_t)Np * Np;
     P->scratch.ensure(sizeof(float2) * (2 * nn + 2 * kGJBS) + 64);
     float2* Da = P->scratch.as<float2>();
     float2* Db = Da + nn;
     float2* pinv = Db + nn;
-    k_d2df_vec<<<cdiv((long long)nn, 256), 256, 0, P->stream>>>(nn, A, Da);
+    BA_CUDA(cudaMemsetAsync(Da, 0, sizeof(float2) * nn, P->stream));
+    k_bsr_to_dense_df<<<L.n + 1, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                       L.vals32.as<float>(), N, Np, Da);
     launched(P);
     int nblk = 0;
     BA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, k_gauss_jordan_df, kGJBS, 0));
@@ -1543,6 +1558,12 @@ static void dense_inverse(ba_problem* P, Level& L) {
     launched(P);
     return;
   }
+  BA_CUDA(cudaMemsetAsync(A, 0, sizeof(double) * (size_t)Np * Np, P->stream));
+  k_bsr_to_dense<double><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+                                                     L.vals64.as<double>(), Np, A);
+  launched(P);
+  k_dense_identity_pad<<<cdiv((long long)Np * Np, 256), 256, 0, P->stream>>>(N, Np, A);
+  launched(P);
   // second buffer of the ping-pong and the two pivot inverses
   P->scratch.ensure(sizeof(double) * ((size_t)Np * Np + 2 * kGJBS) + 64);
   double* B = P->scratch.as<double>();
@@ -1758,9 +1779,13 @@ void mg_setup(ba_problem* P, bool check) {
   L0.Dblk.ensure(sizeof(double) * 81 * (size_t)P->n_c + 64);
   L0.Dinv64.ensure(sizeof(double) * 81 * (size_t)P->n_c + 64);
   L0.Dinv32.ensure(sizeof(float) * 81 * (size_t)P->n_c + 64);
-  BA_CUDA(cudaMemcpyAsync(L0.Dblk.p, P->Scc.p, sizeof(double) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
-  BA_CUDA(cudaMemcpyAsync(L0.Dinv64.p, P->Scc_inv.p, sizeof(double) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
-  BA_CUDA(cudaMemcpyAsync(L0.Dinv32.p, P->Scc_inv32.p, sizeof(float) * 81 * P->n_c, cudaMemcpyDeviceToDevice, P->stream));
+  {
+    const size_t n81 = 81 * (size_t)P->n_c;
+    k_copy_jacobi0<<<std::max(1, std::min(cdiv((long long)n81, 256), 4 * P->n_sm)), 256, 0, P->stream>>>(
+        n81, P->Scc.as<double>(), P->Scc_inv.as<double>(), P->Scc_inv32.as<float>(), L0.Dblk.as<double>(),
+        L0.Dinv64.as<double>(), L0.Dinv32.as<float>());
+    launched(P);
+  }
 
   const bool batch_inv = P->opt.precision == BA_MIXED;
   BlockInvBatch inv{};
@@ -1776,14 +1801,18 @@ void mg_setup(ba_problem* P, bool check) {
       dense_inverse(P, L);
       break;
     }
-    // smoother for this level
+    // smoother for this level (FP32 levels also get the FP32 copy of the diagonal blocks
+    // that the batched Lanczos reads)
+    const size_t nb2 = (size_t)L.bs * L.bs * L.n;
+    if (fp32) L.Dblk32.ensure(sizeof(float) * nb2 + 64);
     if (l > 0) {
       if (fp32)
         k_extract_diag<float><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
-                                                          L.vals32.as<float>(), L.Dblk.as<double>());
+                                                          L.vals32.as<float>(), L.Dblk.as<double>(),
+                                                          L.Dblk32.as<float>());
       else
         k_extract_diag<double><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
-                                                           L.vals64.as<double>(), L.Dblk.as<double>());
+                                                           L.vals64.as<double>(), L.Dblk.as<double>(), nullptr);
       launched(P);
       if (batch_inv && L.bs == 16 && inv.nseg < kMaxInvSegs) {
         // inverted with the other coarse levels' blocks in one launch after the loop (only
@@ -1796,10 +1825,8 @@ void mg_setup(ba_problem* P, bool check) {
                       F_NOT_SPD_JACOBI);
       }
     }
-    if (fp32) {
-      // FP32 diagonal blocks for the batched Lanczos
-      const size_t nb2 = (size_t)L.bs * L.bs * L.n;
-      L.Dblk32.ensure(sizeof(float) * nb2 + 64);
+    if (fp32 && l == 0) {
+      // FP32 diagonal blocks for the batched Lanczos (level 0's come from S_cc)
       k_d2f_vec<<<cdiv((long long)std::max<size_t>(nb2, 1), 256), 256, 0, P->stream>>>(nb2, L.Dblk.as<double>(),
                                                                                        L.Dblk32.as<float>());
       launched(P);

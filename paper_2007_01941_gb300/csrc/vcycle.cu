@@ -1111,20 +1111,32 @@ static void run(ba_problem* P, const double* r, double* z, double* dpart, bool f
   }
 }
 
-// M_aj = A_aj D_j^-1 / theta of a folded coarse level: one CTA per block, thread (u, v)
-__global__ void __launch_bounds__(256) k_fold_blocks(int nnzb, const int* __restrict__ cols,
-                                                     const float* __restrict__ vals, const float* __restrict__ Dinv,
-                                                     const double* __restrict__ cheb, float* __restrict__ out) {
+// M_aj = A_aj D_j^-1 / theta of the folded coarse levels, all in one launch: CTA b is block
+// b - off[k] of level k (off[k] <= b < off[k + 1]), thread (u, v) entry (u, v)
+struct FoldBatch {
+  int n;
+  int off[17];
+  const int* cols[16];
+  const float* vals[16];
+  const float* dinv[16];
+  const double* cheb[16];
+  float* out[16];
+};
+
+__global__ void __launch_bounds__(256) k_fold_blocks(FoldBatch FB) {
   __shared__ float A[256], D[256];
-  const int e = blockIdx.x, t = threadIdx.x, u = t >> 4, v = t & 15;
-  if (e >= nnzb) return;
-  A[t] = vals[(size_t)e * 256 + t];
-  D[t] = Dinv[(size_t)cols[e] * 256 + t];
+  const int t = threadIdx.x, u = t >> 4, v = t & 15;
+  int k = 0;
+  while (k + 1 < FB.n && (int)blockIdx.x >= FB.off[k + 1]) ++k;
+  const int e = (int)blockIdx.x - FB.off[k];
+  if (e >= FB.off[k + 1] - FB.off[k]) return;
+  A[t] = FB.vals[k][(size_t)e * 256 + t];
+  D[t] = FB.dinv[k][(size_t)FB.cols[k][e] * 256 + t];
   __syncthreads();
   float s = 0.f;
 #pragma unroll
   for (int w = 0; w < 16; ++w) s += A[u * 16 + w] * D[w * 16 + v];
-  out[(size_t)e * 256 + t] = s * (float)(1.0 / cheb[0]);
+  FB.out[k][(size_t)e * 256 + t] = s * (float)(1.0 / FB.cheb[k][0]);
 }
 
 // per block (a, j) of coarse level C, the fine members of aggregate j (F's member lists),
@@ -1182,18 +1194,27 @@ void fused_vcycle_setup(ba_problem* P) {
     }
   }
   if (!level_fp32(P) || P->opt.pre_smooth < 2) return;
-  for (int l = 1; l + 1 < P->n_levels; ++l) {
+  FoldBatch FB{};
+  FB.off[0] = 0;
+  for (int l = 1; l + 1 < P->n_levels && FB.n < 16; ++l) {
     Level& C = P->levels[l];
     Level& F = P->levels[l - 1];
     if (C.coarsest || C.bs != 16 || sizeof(float) * 256 * (size_t)C.nnzb > kFoldMaxBytes) continue;
     if (!C.gptr.p) fold_symbolic(P, F, C);
     C.mvals32.ensure(sizeof(float) * 256 * (size_t)std::max(C.nnzb, 1) + 64);
     F.rt.ensure(sizeof(float) * 16 * (size_t)std::max(F.n, 1) + 64);
-    k_fold_blocks<<<std::max(C.nnzb, 1), 256, 0, P->stream>>>(C.nnzb, C.cols.as<int>(), C.vals32.as<float>(),
-                                                             C.Dinv32.as<float>(), C.cheb.as<double>(),
-                                                             C.mvals32.as<float>());
-    launched(P);
+    const int k = FB.n++;
+    FB.cols[k] = C.cols.as<int>();
+    FB.vals[k] = C.vals32.as<float>();
+    FB.dinv[k] = C.Dinv32.as<float>();
+    FB.cheb[k] = C.cheb.as<double>();
+    FB.out[k] = C.mvals32.as<float>();
+    FB.off[k + 1] = FB.off[k] + C.nnzb;
     C.folded = true;
+  }
+  if (FB.n > 0 && FB.off[FB.n] > 0) {
+    k_fold_blocks<<<FB.off[FB.n], 256, 0, P->stream>>>(FB);
+    launched(P);
   }
 }
 
