@@ -104,6 +104,7 @@ enum Flag : int {
   F_HASH_OVERFLOW = 4,
   F_NONFINITE = 5,
   F_WAIT_TIMEOUT = 6,   // a bounded wait in a kernel gave up (its results are not valid)
+  F_PATTERN = 7,        // a level-0 block's mirror is missing from the covisibility pattern
   F_COUNT = 8
 };
 

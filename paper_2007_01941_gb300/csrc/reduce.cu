@@ -175,6 +175,7 @@ void raise_flags(ba_problem* P) {
   if (f[F_NOT_SPD_COARSE]) throw Error(BA_ERR_NOT_SPD, "the coarsest operator is not positive definite");
   if (f[F_BREAKDOWN]) throw Error(BA_ERR_BREAKDOWN, "PCG breakdown");
   if (f[F_WAIT_TIMEOUT]) throw Error(BA_ERR_CUDA, "a kernel's bounded wait for its staged data gave up");
+  if (f[F_PATTERN]) throw Error(BA_ERR_STATE, "covisibility pattern is not symmetric");
 }
 
 }  // namespace ba

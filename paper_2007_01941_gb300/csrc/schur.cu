@@ -1674,24 +1674,58 @@ k_explicit_pairs_df(const float2* __restrict__ W2, int n_up, const int* __restri
   }
 }
 
+// index of block (c, c2) in camera row c of the level-0 pattern (columns ascending), or -1
+__device__ __forceinline__ int pattern_block(const int* __restrict__ row_ptr, const int* __restrict__ cols, int c,
+                                             int c2) {
+  int lo = row_ptr[c], hi = row_ptr[c + 1];
+  const int end = hi;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cols[mid] < c2) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < end && cols[lo] == c2 ? lo : -1;
+}
+
+// The observation pairs (o, q) of block (c, c') with c < c': the observations o of camera c
+// in its order, for each the observations q of the same point seen by c' > c.  One thread
+// per camera: every block of row c is camera c's alone, so the counts need no atomics and
+// the fill keeps that order.  COUNT: cnt[up_of[e]] += pairs; else pairs[pos[e]++] = (o, q).
+template <bool COUNT>
+__global__ void k_pair_lists(int n_c, const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                             const int* __restrict__ cam_ptr, const int* __restrict__ cam_obs,
+                             const int* __restrict__ obs_pt, const int* __restrict__ obs_cam,
+                             const int* __restrict__ pt_ptr, const int* __restrict__ up_of, int* __restrict__ cnt,
+                             int* __restrict__ pos, int2* __restrict__ pairs, int* flags) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_c) return;
+  for (int k = cam_ptr[c]; k < cam_ptr[c + 1]; ++k) {
+    const int o = cam_obs[k], p = obs_pt[o];
+    for (int q = pt_ptr[p]; q < pt_ptr[p + 1]; ++q) {
+      const int c2 = obs_cam[q];
+      if (c2 <= c) continue;
+      const int e = pattern_block(row_ptr, cols, c, c2);
+      if (e < 0) {
+        flags[F_PATTERN] = 1;
+        continue;
+      }
+      if (COUNT) ++cnt[up_of[e]];
+      else pairs[pos[e]++] = make_int2(o, q);
+    }
+  }
+}
+
 // pairs of observations of one point seen by different cameras c < c', grouped by the
 // level-0 block (c, c') they contribute to, and the work list of blocks on and above
-// the diagonal with their mirrors; built on the host once per problem, in camera-row
-// then observation order (deterministic sums)
+// the diagonal with their mirrors; built once per problem, in camera-row then observation
+// order (deterministic sums).  The block lists are formed on the host (O(blocks)), the
+// pairs on the device (k_pair_lists: two passes over every pair).
 static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
-  const int n_c = P->n_c, n_o = P->n_o, n_p = P->n_p;
-  std::vector<int> row_ptr(n_c + 1), cols(std::max(L0.nnzb, 1)), cam_ptr(n_c + 1), cam_obs(std::max(n_o, 1)),
-      obs_pt(std::max(n_o, 1)), obs_cam(std::max(n_o, 1)), pt_ptr(n_p + 1);
-  auto down = [&](std::vector<int>& h, const DBuf& d, size_t n) {
-    if (n) BA_CUDA(cudaMemcpyAsync(h.data(), d.p, sizeof(int) * n, cudaMemcpyDeviceToHost, P->stream));
-  };
-  down(row_ptr, L0.row_ptr, n_c + 1);
-  down(cols, L0.cols, L0.nnzb);
-  down(cam_ptr, P->cam_ptr, n_c + 1);
-  down(cam_obs, P->cam_obs, n_o);
-  down(obs_pt, P->obs_pt, n_o);
-  down(obs_cam, P->obs_cam, n_o);
-  down(pt_ptr, P->pt_ptr, n_p + 1);
+  const int n_c = P->n_c;
+  std::vector<int> row_ptr(n_c + 1), cols(std::max(L0.nnzb, 1));
+  BA_CUDA(cudaMemcpyAsync(row_ptr.data(), L0.row_ptr.p, sizeof(int) * (n_c + 1), cudaMemcpyDeviceToHost, P->stream));
+  if (L0.nnzb)
+    BA_CUDA(cudaMemcpyAsync(cols.data(), L0.cols.p, sizeof(int) * L0.nnzb, cudaMemcpyDeviceToHost, P->stream));
   sync(P);
   auto block_of = [&](int c, int c2) {
     int lo = row_ptr[c], hi = row_ptr[c + 1];
@@ -1714,56 +1748,54 @@ static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
       }
     }
   const int n_up = (int)up_blk.size();
+  const int nz = std::max(L0.nnzb, 1);
+  // device scratch: up_of [nnzb], then the counts [n_up + 1], then the fill positions [nnzb]
+  P->scratch.ensure(sizeof(int) * (2 * (size_t)nz + n_up + 1) + 64);
+  int* d_up_of = P->scratch.as<int>();
+  int* d_cnt = d_up_of + nz;
+  int* d_pos = d_cnt + n_up + 1;
+  BA_CUDA(cudaMemcpyAsync(d_up_of, up_of.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, P->stream));
+  BA_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int) * (n_up + 1), P->stream));
+  const int g = cdiv(std::max(n_c, 1), 128);
+  k_pair_lists<true><<<g, 128, 0, P->stream>>>(n_c, L0.row_ptr.as<int>(), L0.cols.as<int>(), P->cam_ptr.as<int>(),
+                                               P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
+                                               P->pt_ptr.as<int>(), d_up_of, d_cnt, nullptr, nullptr,
+                                               P->flags.as<int>());
+  launched(P);
   std::vector<int> cnt(n_up + 1, 0);
-  for (int pass = 0; pass < 3; ++pass) {
-    if (pass == 1) {
-      // work items in decreasing order of their pair counts, so that the longest blocks
-      // start first and the grid's tail is short (each block's own pair order is kept).
-      // This order re-reads each W row from DRAM about k_p - 1 times (4x the algorithmic
-      // bytes), but the two orders that keep the blocks sharing a row together were both
-      // slower on the street chain: block-row order 0.59 ms, groups of 256 block rows each
-      // in decreasing pair count 0.52 ms, against 0.37 ms (3.6 against 4.8 and 3.7 ms on
-      // the city grid)
-      std::vector<int> perm(n_up), rank(n_up);
-      for (int u = 0; u < n_up; ++u) perm[u] = u;
-      std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return cnt[a + 1] > cnt[b + 1]; });
-      std::vector<int> up2(n_up), mir2(n_up), cnt2(n_up + 1, 0);
-      for (int r = 0; r < n_up; ++r) {
-        rank[perm[r]] = r;
-        up2[r] = up_blk[perm[r]];
-        mir2[r] = mirror[perm[r]];
-        cnt2[r + 1] = cnt[perm[r] + 1];
-      }
-      for (int e = 0; e < L0.nnzb; ++e)
-        if (up_of[e] >= 0) up_of[e] = rank[up_of[e]];
-      up_blk.swap(up2);
-      mirror.swap(mir2);
-      cnt.swap(cnt2);
-      for (int u = 0; u < n_up; ++u) cnt[u + 1] += cnt[u];
-      upload(P, L0.pair_ptr, cnt);
-      upload(P, L0.blk_row, blk_row);
-      upload(P, L0.up_blk, up_blk);
-      upload(P, L0.mirror, mirror);
-      continue;
-    }
-    std::vector<int> fill;
-    std::vector<int2> pairs;
-    if (pass == 2) {
-      fill.assign(cnt.begin(), cnt.end() - 1);
-      pairs.resize(std::max(cnt[n_up], 1));
-    }
-    for (int c = 0; c < n_c; ++c)
-      for (int k = cam_ptr[c]; k < cam_ptr[c + 1]; ++k) {
-        const int o = cam_obs[k], p = obs_pt[o];
-        for (int q = pt_ptr[p]; q < pt_ptr[p + 1]; ++q) {
-          if (obs_cam[q] <= c) continue;
-          const int u = up_of[block_of(c, obs_cam[q])];
-          if (pass == 0) ++cnt[u + 1];
-          else pairs[fill[u]++] = make_int2(o, q);
-        }
-      }
-    if (pass == 2) upload(P, L0.pairs, pairs);
+  if (n_up) BA_CUDA(cudaMemcpyAsync(cnt.data() + 1, d_cnt, sizeof(int) * n_up, cudaMemcpyDeviceToHost, P->stream));
+  sync(P);
+  // work items in decreasing order of their pair counts, so that the longest blocks start
+  // first and the grid's tail is short (each block's own pair order is kept).  This order
+  // re-reads each W row from DRAM about k_p - 1 times (4x the algorithmic bytes), but the
+  // two orders that keep the blocks sharing a row together were both slower on the street
+  // chain: block-row order 0.59 ms, groups of 256 block rows each in decreasing pair count
+  // 0.52 ms, against 0.37 ms (3.6 against 4.8 and 3.7 ms on the city grid)
+  std::vector<int> perm(n_up), rank(n_up);
+  for (int u = 0; u < n_up; ++u) perm[u] = u;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return cnt[a + 1] > cnt[b + 1]; });
+  std::vector<int> up2(n_up), mir2(n_up), ptr(n_up + 1, 0);
+  for (int r = 0; r < n_up; ++r) {
+    rank[perm[r]] = r;
+    up2[r] = up_blk[perm[r]];
+    mir2[r] = mirror[perm[r]];
+    ptr[r + 1] = ptr[r] + cnt[perm[r] + 1];
   }
+  // each block's first pair slot, for the fill
+  std::vector<int> pos(nz, 0);
+  for (int e = 0; e < L0.nnzb; ++e)
+    if (up_of[e] >= 0) pos[e] = ptr[rank[up_of[e]]];
+  upload(P, L0.pair_ptr, ptr);
+  upload(P, L0.blk_row, blk_row);
+  upload(P, L0.up_blk, up2);
+  upload(P, L0.mirror, mir2);
+  L0.pairs.ensure(sizeof(int2) * (size_t)std::max(ptr[n_up], 1) + 64);
+  BA_CUDA(cudaMemcpyAsync(d_pos, pos.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, P->stream));
+  k_pair_lists<false><<<g, 128, 0, P->stream>>>(n_c, L0.row_ptr.as<int>(), L0.cols.as<int>(), P->cam_ptr.as<int>(),
+                                                P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
+                                                P->pt_ptr.as<int>(), d_up_of, nullptr, d_pos,
+                                                L0.pairs.as<int2>(), P->flags.as<int>());
+  launched(P);
   L0.n_up = n_up;
   sync(P);
 }
