@@ -374,7 +374,6 @@ void reduced_rhs(ba_problem* P, const double* vc, const double* vp_user, double*
 // ---- multigrid setup (mg_setup.cu) ------------------------------------------
 void mg_setup(ba_problem* P, bool check = true);
 void covisibility_level0(ba_problem* P, Level& L);
-void jacobi_blocks(ba_problem* P, Level& L, bool from_vals64);
 
 // ---- solve (solve.cu) -------------------------------------------------------
 void precond_apply(ba_problem* P, const double* r, double* z);

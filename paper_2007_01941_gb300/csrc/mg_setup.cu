@@ -930,7 +930,8 @@ k_aggregate_qr_cta(int n_agg, int bs, const int* __restrict__ mptr, const int* _
 // in list order), and one CTA owns a coarse block: its warps take every kGalWarps-th A P
 // block, lane s + 16 h keeping entries (8 h .. 8 h + 7, s) in registers, and the warps'
 // sums are added in warp order.  A coarse dof dropped by the QR (zero Q column) gets a
-// unit diagonal, which decouples it.
+// unit diagonal, which decouples it.  The diagonal blocks also go to cD (FP64) and cD32
+// (FP32, if given): the coarse level's Jacobi blocks.
 // ---------------------------------------------------------------------------
 constexpr int kGalWarps = 4;   // warps per coarse block; each takes every kGalWarps-th A P block
 
@@ -938,7 +939,8 @@ template <typename T, int BS>
 __global__ void __launch_bounds__(kGalWarps * 32)
 k_galerkin(int nnzb_c, const int* __restrict__ gal_ptr, const int2* __restrict__ gal_list,
            const int* __restrict__ gal_row, const int* __restrict__ ccols, const T* __restrict__ ap,
-           const T* __restrict__ Q, const unsigned* __restrict__ ckept, T* __restrict__ cvals) {
+           const T* __restrict__ Q, const unsigned* __restrict__ ckept, T* __restrict__ cvals, double* __restrict__ cD,
+           float* __restrict__ cD32) {
   __shared__ T part[kGalWarps][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ce = blockIdx.x;
@@ -976,6 +978,10 @@ k_galerkin(int nnzb_c, const int* __restrict__ gal_ptr, const int2* __restrict__
     const int r = e >> 4, sc = e & 15;
     if (diag && r == sc && !((kept >> r) & 1u)) v = T(1);
     cvals[(size_t)ce * 256 + e] = v;
+    if (diag && cD) {
+      cD[(size_t)a * 256 + e] = (double)v;
+      if (cD32) cD32[(size_t)a * 256 + e] = (float)v;
+    }
   }
 }
 
@@ -1029,25 +1035,15 @@ static void galerkin_symbolic(ba_problem* P, Level& L, Level& L1) {
 }
 
 // diagonal blocks of a BSR level as double
-template <typename T>
-__global__ void k_extract_diag(int n, int bs, const int* __restrict__ row_ptr, const int* __restrict__ cols,
-                               const T* __restrict__ vals, double* __restrict__ D, float* __restrict__ D32) {
-  int i = blockIdx.x;
-  int t = threadIdx.x;
-  if (t >= bs * bs) return;
-  double v = 0.0;
-  for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
-    if (cols[e] == i) v = (double)vals[(size_t)e * bs * bs + t];
-  D[(size_t)i * bs * bs + t] = v;
-  if (D32) D32[(size_t)i * bs * bs + t] = (float)v;   // the FP32 copy the batched Lanczos reads
-}
-
-// level 0's Jacobi data from the Schur setup's: S_cc blocks and their FP64 and FP32 inverses
+// level 0's Jacobi data from the Schur setup's: S_cc blocks (and their FP32 copy, if d32 is
+// given, for the batched Lanczos) and their FP64 and FP32 inverses
 __global__ void k_copy_jacobi0(size_t n, const double* __restrict__ s, const double* __restrict__ si,
-                               const float* __restrict__ si32, double* __restrict__ d, double* __restrict__ di,
-                               float* __restrict__ di32) {
+                               const float* __restrict__ si32, double* __restrict__ d, float* __restrict__ d32,
+                               double* __restrict__ di, float* __restrict__ di32) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    d[i] = s[i];
+    const double v = s[i];
+    d[i] = v;
+    if (d32) d32[i] = (float)v;
     di[i] = si[i];
     di32[i] = si32[i];
   }
@@ -1781,9 +1777,10 @@ void mg_setup(ba_problem* P, bool check) {
   L0.Dinv32.ensure(sizeof(float) * 81 * (size_t)P->n_c + 64);
   {
     const size_t n81 = 81 * (size_t)P->n_c;
+    if (fp32) L0.Dblk32.ensure(sizeof(float) * n81 + 64);
     k_copy_jacobi0<<<std::max(1, std::min(cdiv((long long)n81, 256), 4 * P->n_sm)), 256, 0, P->stream>>>(
         n81, P->Scc.as<double>(), P->Scc_inv.as<double>(), P->Scc_inv32.as<float>(), L0.Dblk.as<double>(),
-        L0.Dinv64.as<double>(), L0.Dinv32.as<float>());
+        fp32 ? L0.Dblk32.as<float>() : nullptr, L0.Dinv64.as<double>(), L0.Dinv32.as<float>());
     launched(P);
   }
 
@@ -1801,19 +1798,11 @@ void mg_setup(ba_problem* P, bool check) {
       dense_inverse(P, L);
       break;
     }
-    // smoother for this level (FP32 levels also get the FP32 copy of the diagonal blocks
-    // that the batched Lanczos reads)
+    // smoother for this level: its diagonal blocks (FP64, and FP32 for the batched Lanczos)
+    // were written by the Galerkin product that formed the level
     const size_t nb2 = (size_t)L.bs * L.bs * L.n;
     if (fp32) L.Dblk32.ensure(sizeof(float) * nb2 + 64);
     if (l > 0) {
-      if (fp32)
-        k_extract_diag<float><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
-                                                          L.vals32.as<float>(), L.Dblk.as<double>(),
-                                                          L.Dblk32.as<float>());
-      else
-        k_extract_diag<double><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
-                                                           L.vals64.as<double>(), L.Dblk.as<double>(), nullptr);
-      launched(P);
       if (batch_inv && L.bs == 16 && inv.nseg < kMaxInvSegs) {
         // inverted with the other coarse levels' blocks in one launch after the loop (only
         // the batched Lanczos and the V-cycle read them)
@@ -1825,12 +1814,6 @@ void mg_setup(ba_problem* P, bool check) {
                       F_NOT_SPD_JACOBI);
       }
     }
-    if (fp32 && l == 0) {
-      // FP32 diagonal blocks for the batched Lanczos (level 0's come from S_cc)
-      k_d2f_vec<<<cdiv((long long)std::max<size_t>(nb2, 1), 256), 256, 0, P->stream>>>(nb2, L.Dblk.as<double>(),
-                                                                                       L.Dblk32.as<float>());
-      launched(P);
-    }
     // assembled levels get their Lanczos estimate in one batch after the loop
     if (l == 0 && !P->l0_explicit) {
       if (fp32) lanczos<float>(P, l);
@@ -1841,30 +1824,43 @@ void mg_setup(ba_problem* P, bool check) {
     build_ap(P, L);
     if (!L.gal_ptr.p) galerkin_symbolic(P, L, L1);
     const int gg = std::max(L1.nnzb, 1);
+    // the next level's Jacobi blocks come out of the same product (not for the coarsest,
+    // which is inverted whole)
+    double* cD = nullptr;
+    float* cD32 = nullptr;
+    if (!L1.coarsest) {
+      const size_t nb2c = (size_t)L1.bs * L1.bs * L1.n;
+      L1.Dblk.ensure(sizeof(double) * nb2c + 64);
+      cD = L1.Dblk.as<double>();
+      if (fp32) {
+        L1.Dblk32.ensure(sizeof(float) * nb2c + 64);
+        cD32 = L1.Dblk32.as<float>();
+      }
+    }
     if (fp32) {
       L1.vals32.ensure(sizeof(float) * 256 * (size_t)L1.nnzb + 64);
       if (L.bs == 9)
         k_galerkin<float, 9><<<gg, kGalWarps * 32, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
                                                           L.gal_row.as<int>(), L1.cols.as<int>(),
                                                           L.ap_vals.as<float>(), L.Q32.as<float>(),
-                                                          L1.kept.as<unsigned>(), L1.vals32.as<float>());
+                                                          L1.kept.as<unsigned>(), L1.vals32.as<float>(), cD, cD32);
       else
         k_galerkin<float, 16><<<gg, kGalWarps * 32, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
                                                            L.gal_row.as<int>(), L1.cols.as<int>(),
                                                            L.ap_vals.as<float>(), L.Q32.as<float>(),
-                                                           L1.kept.as<unsigned>(), L1.vals32.as<float>());
+                                                           L1.kept.as<unsigned>(), L1.vals32.as<float>(), cD, cD32);
     } else {
       L1.vals64.ensure(sizeof(double) * 256 * (size_t)L1.nnzb + 64);
       if (L.bs == 9)
         k_galerkin<double, 9><<<gg, kGalWarps * 32, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
                                                            L.gal_row.as<int>(), L1.cols.as<int>(),
                                                            L.ap_vals.as<double>(), L.Q64.as<double>(),
-                                                           L1.kept.as<unsigned>(), L1.vals64.as<double>());
+                                                           L1.kept.as<unsigned>(), L1.vals64.as<double>(), cD, nullptr);
       else
         k_galerkin<double, 16><<<gg, kGalWarps * 32, 0, P->stream>>>(L1.nnzb, L.gal_ptr.as<int>(), L.gal_list.as<int2>(),
                                                             L.gal_row.as<int>(), L1.cols.as<int>(),
                                                             L.ap_vals.as<double>(), L.Q64.as<double>(),
-                                                            L1.kept.as<unsigned>(), L1.vals64.as<double>());
+                                                            L1.kept.as<unsigned>(), L1.vals64.as<double>(), cD, nullptr);
     }
     launched(P);
   }
