@@ -1149,7 +1149,7 @@ static void lanczos(ba_problem* P, int l) {
     launched(P);
   }
   // park alpha_0..7 and beta_0..7 in the level's buffer (slots 8..23); the largest Ritz
-  // value is computed on the host once every level is done (finish_lanczos)
+  // value is found on the device once every level is done (finish_lanczos, k_cheb_params)
   L.cheb.ensure(sizeof(double) * kChebSlots);
   BA_CUDA(cudaMemcpyAsync(L.cheb.as<double>() + 8, scal + S_LANCZOS, sizeof(double) * 16, cudaMemcpyDeviceToDevice,
                           P->stream));
@@ -1245,6 +1245,7 @@ __global__ void __launch_bounds__(32) k_cheb_params(ChebLevels CL, int m, double
   }
 }
 
+// the Chebyshev parameters of every smoothed level from its Lanczos coefficients
 static void finish_lanczos(ba_problem* P) {
   const int nl = P->n_levels - 1;
   if (nl <= 0) return;
