@@ -176,7 +176,10 @@ ba_status ba_back_substitute(ba_problem* prob, const double* delta_c, double* de
 /* One LM step (Section 2.1; step control of Section 5 read as the gain-ratio rule):
  * linearise at (cams, pts), solve with damping *lambda_inout, evaluate the cost at
  * x + delta, accept if rho > 1e-3 (cams/pts updated in place) and update lambda.
- * accepted, cost_out: host outputs (cost at the returned cams/pts). */
+ * accepted, cost_out: host outputs (cost at the returned cams/pts).  A solve that fails
+ * (a block not positive definite, a PCG breakdown) rejects the step.  The step is queued
+ * on the problem's stream and synchronised with the host once for its decision; it has
+ * completed when the call returns. */
 ba_status ba_lm_step(ba_problem* prob, double* cams, double* pts, const double* obs,
                      double* lambda_inout, int* accepted, double* cost_out);
 
