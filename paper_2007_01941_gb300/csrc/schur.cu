@@ -1688,31 +1688,81 @@ __device__ __forceinline__ int pattern_block(const int* __restrict__ row_ptr, co
 }
 
 // The observation pairs (o, q) of block (c, c') with c < c': the observations o of camera c
-// in its order, for each the observations q of the same point seen by c' > c.  One thread
-// per camera: every block of row c is camera c's alone, so the counts need no atomics and
-// the fill keeps that order.  COUNT: cnt[up_of[e]] += pairs; else pairs[pos[e]++] = (o, q).
+// in its order, for each the observations q of the same point seen by c' > c.  One warp per
+// camera: lane j takes the j-th of 32 contiguous segments of the camera's observations and
+// counts its pairs per block of row c in shared memory (every block of row c is camera c's
+// alone); COUNT adds the lanes' counts into cnt[up_of[e]], the fill gives each lane its
+// start in each block (the earlier lanes' counts added to pos[e]) and writes its segment's
+// pairs in order, so the lists are those of a sequential walk.  Rows of more than
+// kPairRowMax blocks are walked by lane 0 alone.
+constexpr int kPairRowMax = 64;
+constexpr int kPairWarps = 4;
+
 template <bool COUNT>
-__global__ void k_pair_lists(int n_c, const int* __restrict__ row_ptr, const int* __restrict__ cols,
-                             const int* __restrict__ cam_ptr, const int* __restrict__ cam_obs,
-                             const int* __restrict__ obs_pt, const int* __restrict__ obs_cam,
-                             const int* __restrict__ pt_ptr, const int* __restrict__ up_of, int* __restrict__ cnt,
-                             int* __restrict__ pos, int2* __restrict__ pairs, int* flags) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kPairWarps * 32)
+k_pair_lists(int n_c, const int* __restrict__ row_ptr, const int* __restrict__ cols, const int* __restrict__ cam_ptr,
+             const int* __restrict__ cam_obs, const int* __restrict__ obs_pt, const int* __restrict__ obs_cam,
+             const int* __restrict__ pt_ptr, const int* __restrict__ up_of, int* __restrict__ cnt,
+             int* __restrict__ pos, int2* __restrict__ pairs, int* flags) {
+  __shared__ int lc[kPairWarps][kPairRowMax][33];   // [warp][block of the row][lane]
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int c = blockIdx.x * kPairWarps + wi;
   if (c >= n_c) return;
-  for (int k = cam_ptr[c]; k < cam_ptr[c + 1]; ++k) {
-    const int o = cam_obs[k], p = obs_pt[o];
-    for (int q = pt_ptr[p]; q < pt_ptr[p + 1]; ++q) {
-      const int c2 = obs_cam[q];
-      if (c2 <= c) continue;
-      const int e = pattern_block(row_ptr, cols, c, c2);
-      if (e < 0) {
-        flags[F_PATTERN] = 1;
-        continue;
+  const int r0 = row_ptr[c], R = row_ptr[c + 1] - r0;
+  const int k0 = cam_ptr[c], k1 = cam_ptr[c + 1];
+  // visits the pairs of observations [ka, kb) of camera c in order
+  auto walk = [&](int ka, int kb, auto&& f) {
+    for (int k = ka; k < kb; ++k) {
+      const int o = cam_obs[k], p = obs_pt[o];
+      for (int q = pt_ptr[p]; q < pt_ptr[p + 1]; ++q) {
+        const int c2 = obs_cam[q];
+        if (c2 <= c) continue;
+        const int e = pattern_block(row_ptr, cols, c, c2);
+        if (e < 0) {
+          flags[F_PATTERN] = 1;
+          continue;
+        }
+        f(e, o, q);
       }
-      if (COUNT) ++cnt[up_of[e]];
-      else pairs[pos[e]++] = make_int2(o, q);
+    }
+  };
+  if (R > kPairRowMax) {
+    if (lane != 0) return;
+    if (COUNT) {
+      walk(k0, k1, [&](int e, int, int) { ++cnt[up_of[e]]; });
+    } else {
+      // this row's start slots, advanced in place (the row is this thread's alone)
+      walk(k0, k1, [&](int e, int o, int q) { pairs[pos[e]++] = make_int2(o, q); });
+    }
+    return;
+  }
+  // lane j's segment [ka, kb) and its counts per block of the row
+  const int nk = k1 - k0, per = (nk + 31) / 32;
+  const int ka = min(k0 + lane * per, k1), kb = min(ka + per, k1);
+  for (int s = 0; s < R; ++s) lc[wi][s][lane] = 0;
+  walk(ka, kb, [&](int e, int, int) { ++lc[wi][e - r0][lane]; });
+  __syncwarp();
+  if (COUNT) {
+    for (int s = lane; s < R; s += 32) {
+      const int e = r0 + s;
+      if (up_of[e] < 0) continue;
+      int t = 0;
+      for (int j = 0; j < 32; ++j) t += lc[wi][s][j];
+      cnt[up_of[e]] += t;
+    }
+    return;
+  }
+  // exclusive prefix over the lanes, per block: lane j's first slot in each block
+  for (int s = lane; s < R; s += 32) {
+    int run = pos[r0 + s];
+    for (int j = 0; j < 32; ++j) {
+      const int v = lc[wi][s][j];
+      lc[wi][s][j] = run;
+      run += v;
     }
   }
+  __syncwarp();
+  walk(ka, kb, [&](int e, int o, int q) { pairs[lc[wi][e - r0][lane]++] = make_int2(o, q); });
 }
 
 // pairs of observations of one point seen by different cameras c < c', grouped by the
@@ -1756,8 +1806,8 @@ static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
   int* d_pos = d_cnt + n_up + 1;
   BA_CUDA(cudaMemcpyAsync(d_up_of, up_of.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, P->stream));
   BA_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int) * (n_up + 1), P->stream));
-  const int g = cdiv(std::max(n_c, 1), 128);
-  k_pair_lists<true><<<g, 128, 0, P->stream>>>(n_c, L0.row_ptr.as<int>(), L0.cols.as<int>(), P->cam_ptr.as<int>(),
+  const int g = cdiv(std::max(n_c, 1), kPairWarps);
+  k_pair_lists<true><<<g, kPairWarps * 32, 0, P->stream>>>(n_c, L0.row_ptr.as<int>(), L0.cols.as<int>(), P->cam_ptr.as<int>(),
                                                P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
                                                P->pt_ptr.as<int>(), d_up_of, d_cnt, nullptr, nullptr,
                                                P->flags.as<int>());
@@ -1791,7 +1841,7 @@ static void explicit_pairs_symbolic(ba_problem* P, Level& L0) {
   upload(P, L0.mirror, mir2);
   L0.pairs.ensure(sizeof(int2) * (size_t)std::max(ptr[n_up], 1) + 64);
   BA_CUDA(cudaMemcpyAsync(d_pos, pos.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, P->stream));
-  k_pair_lists<false><<<g, 128, 0, P->stream>>>(n_c, L0.row_ptr.as<int>(), L0.cols.as<int>(), P->cam_ptr.as<int>(),
+  k_pair_lists<false><<<g, kPairWarps * 32, 0, P->stream>>>(n_c, L0.row_ptr.as<int>(), L0.cols.as<int>(), P->cam_ptr.as<int>(),
                                                 P->cam_obs.as<int>(), P->obs_pt.as<int>(), P->obs_cam.as<int>(),
                                                 P->pt_ptr.as<int>(), d_up_of, nullptr, d_pos,
                                                 L0.pairs.as<int2>(), P->flags.as<int>());
