@@ -1523,7 +1523,7 @@ __global__ void k_bsr_to_dense_df(int n, int bs, const int* __restrict__ row_ptr
   }
 }
 
-static void dense_inverse(ba_problem* P, Level& L) {
+static void dense_inverse(ba_problem* P, Level& L, cudaStream_t st) {
   const int N = L.n * L.bs;
   const int Np = (N + kGJ - 1) / kGJ * kGJ;
   BA_REQUIRE(Np <= 16384, BA_ERR_LIMIT, "coarsest level too large for the dense solver (" + std::to_string(N) + " dofs)");
@@ -1539,8 +1539,8 @@ static void dense_inverse(ba_problem* P, Level& L) {
     float2* Da = P->scratch.as<float2>();
     float2* Db = Da + nn;
     float2* pinv = Db + nn;
-    BA_CUDA(cudaMemsetAsync(Da, 0, sizeof(float2) * nn, P->stream));
-    k_bsr_to_dense_df<<<L.n + 1, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+    BA_CUDA(cudaMemsetAsync(Da, 0, sizeof(float2) * nn, st));
+    k_bsr_to_dense_df<<<L.n + 1, 256, 0, st>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
                                                        L.vals32.as<float>(), N, Np, Da);
     launched(P);
     int nblk = 0;
@@ -1549,17 +1549,17 @@ static void dense_inverse(ba_problem* P, Level& L) {
     int grid = std::max(1, std::min(nblk * P->n_sm, nbk * nbk));
     int* flags = P->flags.as<int>();
     void* args[] = {(void*)&Da, (void*)&Db, (void*)&Np, (void*)&pinv, (void*)&flags};
-    BA_CUDA(cudaLaunchCooperativeKernel((void*)k_gauss_jordan_df, grid, kGJBS, args, 0, P->stream));
+    BA_CUDA(cudaLaunchCooperativeKernel((void*)k_gauss_jordan_df, grid, kGJBS, args, 0, st));
     launched(P);
-    k_df2d_vec<<<cdiv((long long)nn, 256), 256, 0, P->stream>>>(nn, (nbk & 1) ? Db : Da, A);
+    k_df2d_vec<<<cdiv((long long)nn, 256), 256, 0, st>>>(nn, (nbk & 1) ? Db : Da, A);
     launched(P);
     return;
   }
-  BA_CUDA(cudaMemsetAsync(A, 0, sizeof(double) * (size_t)Np * Np, P->stream));
-  k_bsr_to_dense<double><<<L.n, 256, 0, P->stream>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
+  BA_CUDA(cudaMemsetAsync(A, 0, sizeof(double) * (size_t)Np * Np, st));
+  k_bsr_to_dense<double><<<L.n, 256, 0, st>>>(L.n, L.bs, L.row_ptr.as<int>(), L.cols.as<int>(),
                                                      L.vals64.as<double>(), Np, A);
   launched(P);
-  k_dense_identity_pad<<<cdiv((long long)Np * Np, 256), 256, 0, P->stream>>>(N, Np, A);
+  k_dense_identity_pad<<<cdiv((long long)Np * Np, 256), 256, 0, st>>>(N, Np, A);
   launched(P);
   // second buffer of the ping-pong and the two pivot inverses
   P->scratch.ensure(sizeof(double) * ((size_t)Np * Np + 2 * kGJBS) + 64);
@@ -1571,10 +1571,10 @@ static void dense_inverse(ba_problem* P, Level& L) {
   int grid = std::max(1, std::min(nblk * P->n_sm, nbk * nbk));
   int* flags = P->flags.as<int>();
   void* args[] = {(void*)&A, (void*)&B, (void*)&Np, (void*)&pinv, (void*)&flags};
-  BA_CUDA(cudaLaunchCooperativeKernel((void*)k_gauss_jordan, grid, kGJBS, args, 0, P->stream));
+  BA_CUDA(cudaLaunchCooperativeKernel((void*)k_gauss_jordan, grid, kGJBS, args, 0, st));
   launched(P);
   // after an odd number of steps the inverse is in the second buffer
-  if (nbk & 1) BA_CUDA(cudaMemcpyAsync(A, B, sizeof(double) * (size_t)Np * Np, cudaMemcpyDeviceToDevice, P->stream));
+  if (nbk & 1) BA_CUDA(cudaMemcpyAsync(A, B, sizeof(double) * (size_t)Np * Np, cudaMemcpyDeviceToDevice, st));
 }
 
 // ---------------------------------------------------------------------------
@@ -1788,6 +1788,7 @@ void mg_setup(ba_problem* P, bool check) {
   const bool batch_inv = P->opt.precision == BA_MIXED;
   BlockInvBatch inv{};
   BA_CUDA(cudaStreamWaitEvent(P->stream, P->ev_join, 0));
+  bool coarse_forked = false;
   for (int l = 0; l < P->n_levels; ++l) {
     Level& L = P->levels[l];
     if (l > 0) {
@@ -1796,7 +1797,13 @@ void mg_setup(ba_problem* P, bool check) {
       L.Dinv32.ensure(sizeof(float) * L.bs * L.bs * (size_t)L.n + 64);
     }
     if (L.coarsest) {
-      dense_inverse(P, L);
+      // the coarsest inverse (a cooperative kernel of nb = N / 16 grid barriers) beside the
+      // smoother blocks and the Lanczos runs, which do not read it; joined below
+      BA_CUDA(cudaEventRecord(P->ev_fork, P->stream));
+      BA_CUDA(cudaStreamWaitEvent(P->side_stream, P->ev_fork, 0));
+      dense_inverse(P, L, P->side_stream);
+      BA_CUDA(cudaEventRecord(P->ev_join, P->side_stream));
+      coarse_forked = true;
       break;
     }
     // smoother for this level: its diagonal blocks (FP64, and FP32 for the batched Lanczos)
@@ -1868,6 +1875,7 @@ void mg_setup(ba_problem* P, bool check) {
   block_inverse_batch(P, inv, 16, F_NOT_SPD_JACOBI);
   lanczos_batched(P, P->l0_explicit ? 0 : 1, P->n_levels - 2);
   finish_lanczos(P);
+  if (coarse_forked) BA_CUDA(cudaStreamWaitEvent(P->stream, P->ev_join, 0));
   if (check) check_flags(P);
   // V-cycle work vectors
   for (int k = 0; k < P->n_levels; ++k) {
